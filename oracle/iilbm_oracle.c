@@ -1,0 +1,722 @@
+/*
+ * iilbm_oracle.c -- plain, slow FP64 CPU oracle of one immersed interface–lattice
+ * Boltzmann (II-LBM) time step (Qin, Kolahdouz & Griffith, arXiv 2003.12186).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this file.  It shares no code, header,
+ * table or constant with the CUDA library; it is compiled on its own with gcc
+ * (-ffp-contract=off so the host never fuses multiply-adds).
+ *
+ * Every routine below is a direct transcription of a definition in the paper
+ * (section / equation given beside it) in FP64, with plain loops and no blocking,
+ * fusion or reordering beyond what the definition states.  Where the paper is
+ * silent or garbled the reading taken is stated in the routine's comment.
+ *
+ * Notation follows the paper: D2Q9 velocities e_i, weights w_i (Eq. 9),
+ * c_s^2 = 1/3, relaxation time lambda (here "tau"), Lagrangian markers X_k,
+ * Lagrangian force density G_k, Eulerian force density g, delta kernel delta_h.
+ *
+ * Populations are held as shifted deviations df_i = f_i - w_i*rho0.  This is an
+ * exact change of variables (sum_i w_i = 1, sum_i w_i e_i = 0); it keeps the
+ * FP64 rounding of the O(1) rest state out of the O(u) flow quantities.
+ *
+ * Layout: df[i*ny*nx + y*nx + x]  (structure of arrays, natural "pull" order).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- D2Q9 lattice, section 2.2.1 (velocity set), Eq. 9 (weights) ----------
+ * Ordering: 0 rest, 1 E, 2 N, 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE.  This is the
+ * ordering the schematic of the paper implies (point P1 of its first figure
+ * receives the jump on f3 and f7, point P2 on f1, f5, f8). */
+static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double WT[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#define CS2 (1.0 / 3.0)
+
+/* ---------------------------------------------------------------- config --- */
+enum { ORC_SRT = 0, ORC_MRT = 1 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_WALLS_Y = 1, ORC_BC_CHANNEL = 2 };
+enum { ORC_SPRING = 0, ORC_SPRING_REST = 1, ORC_PRESCRIBED = 2, ORC_DIRECT = 3 };
+
+typedef struct {
+  int nx, ny;
+  int collision;   /* ORC_SRT or ORC_MRT */
+  double tau;      /* relaxation time lambda (Eq. 7) */
+  double s[9];     /* MRT rates, moment order (rho, e, eps, jx, qx, jy, qy, pxx, pxy) */
+  double rho0;     /* reference density of the shifted storage */
+  int bc;          /* ORC_BC_* */
+  double u_max;    /* channel: centre-line inflow speed */
+  double body_x, body_y; /* uniform body force density added to g */
+  int jump;        /* 1: II-LBM (normal force through the jump, tangential spread);
+                      0: IB-LBM with Guo forcing (whole G spread) */
+} orc_cfg;
+
+typedef struct {
+  int n;           /* number of markers (closed polygon, counter-clockwise) */
+  int model;       /* ORC_SPRING / ORC_SPRING_REST / ORC_PRESCRIBED / ORC_DIRECT */
+  int moves;       /* 1: markers advected (membrane); 0: fixed (rigid, at rest) */
+  double kappa;    /* spring stiffness */
+  double dX;       /* Lagrangian parameter spacing Delta X */
+  double l0;       /* rest length (ORC_SPRING_REST) */
+  double eta;      /* direct-forcing gain (ORC_DIRECT) */
+  int mdf_iters;   /* direct forcing: maximum iterations */
+  double mdf_tol;  /* direct forcing: stop when max_k |U^D - U_k| < tol (0: run all) */
+  double *X;       /* [n][2] */
+  double *Gp;      /* prescribed G [n][2] (ORC_PRESCRIBED) / warm-start G (ORC_DIRECT) */
+  double *UD;      /* desired velocity [n][2] (ORC_DIRECT) */
+} orc_iface;
+
+typedef struct {
+  orc_cfg c;
+  double *df;      /* [9][ny][nx] state: streamed populations, jump not yet added */
+  double *tmp;     /* [9][ny][nx] scratch */
+  double *f;       /* [9][ny][nx] populations of the current step (state + jump) */
+  double *gx, *gy; /* Eulerian force density of the current step */
+  double *rho, *ux, *uy; /* current step's drho = rho - rho0 and u (Eqs. 11, 24) */
+  double M[81], Minv[81];
+  int has_iface;
+  orc_iface I;
+  double *G;       /* [n][2] Lagrangian force of the current step */
+  double *Fn;      /* [n] normal traction G.n/|X_s| */
+  double *Gpar;    /* [n][2] tangential force G - (G.n)n */
+  double *U;       /* [n][2] interpolated marker velocity */
+  int mdf_last_iters;
+  double mdf_last_res;
+  long step;
+} orc_state;
+
+/* ------------------------------------------------------------ MRT matrix ---
+ * Lallemand & Luo D2Q9 moment basis (cited in section 2.1.1 / 2.2.1): rows are
+ * the polynomials 1, -4+3|e|^2, 4-21/2|e|^2+9/2|e|^4, e_x, (-5+3|e|^2)e_x, e_y,
+ * (-5+3|e|^2)e_y, e_x^2-e_y^2, e_x e_y evaluated on the nine velocities.
+ * The rates s_0..s_8 of section 2.2.1 index these rows in this order. */
+void orc_mrt_matrix(double *M) {
+  for (int i = 0; i < 9; i++) {
+    double ex = EX[i], ey = EY[i], e2 = ex * ex + ey * ey;
+    M[0 * 9 + i] = 1.0;
+    M[1 * 9 + i] = -4.0 + 3.0 * e2;
+    M[2 * 9 + i] = 4.0 - 10.5 * e2 + 4.5 * e2 * e2;
+    M[3 * 9 + i] = ex;
+    M[4 * 9 + i] = (-5.0 + 3.0 * e2) * ex;
+    M[5 * 9 + i] = ey;
+    M[6 * 9 + i] = (-5.0 + 3.0 * e2) * ey;
+    M[7 * 9 + i] = ex * ex - ey * ey;
+    M[8 * 9 + i] = ex * ey;
+  }
+}
+
+/* Gauss–Jordan inverse with partial pivoting (library-style primitive). */
+int orc_invert9(const double *A, double *Ainv) {
+  double a[9][18];
+  for (int r = 0; r < 9; r++)
+    for (int c = 0; c < 18; c++)
+      a[r][c] = c < 9 ? A[r * 9 + c] : (c - 9 == r ? 1.0 : 0.0);
+  for (int col = 0; col < 9; col++) {
+    int piv = col;
+    for (int r = col + 1; r < 9; r++)
+      if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+    if (fabs(a[piv][col]) < 1e-300) return -1;
+    if (piv != col)
+      for (int c = 0; c < 18; c++) { double t = a[col][c]; a[col][c] = a[piv][c]; a[piv][c] = t; }
+    double p = a[col][col];
+    for (int c = 0; c < 18; c++) a[col][c] /= p;
+    for (int r = 0; r < 9; r++) {
+      if (r == col) continue;
+      double m = a[r][col];
+      if (m != 0.0)
+        for (int c = 0; c < 18; c++) a[r][c] -= m * a[col][c];
+    }
+  }
+  for (int r = 0; r < 9; r++)
+    for (int c = 0; c < 9; c++) Ainv[r * 9 + c] = a[r][c + 9];
+  return 0;
+}
+
+/* ------------------------------------------------------ equilibrium, force --
+ * Guo-form equilibrium, Eq. 23: f_eq_i = w_i (p/c_s^2)[1 + e.u/c_s^2 +
+ * (e.u)^2/(2c_s^4) - u^2/(2c_s^2)], with p/c_s^2 = rho = sum_i f_i (Eq. 11; the
+ * sum runs over every i including the rest population -- the printed lower limit
+ * 1 is read as a typo).  Returned shifted by w_i*rho0, from the density deviation
+ * drho = rho - rho0 = sum_i df_i (carried as such, never formed as a difference). */
+void orc_feq_shifted(double drho, double rho0, double ux, double uy, double *dfeq) {
+  double u2 = ux * ux + uy * uy;
+  double rho = rho0 + drho;
+  for (int i = 0; i < 9; i++) {
+    double eu = EX[i] * ux + EY[i] * uy;
+    double poly = eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - u2 / (2.0 * CS2);
+    dfeq[i] = WT[i] * (drho + rho * poly);
+  }
+}
+
+/* Guo source without its relaxation prefactor, Eqs. 21-22:
+ * Gt_i = w_i [ (e_i - u)/c_s^2 + (e_i.u) e_i / c_s^4 ] . g */
+void orc_guo_source(double ux, double uy, double gx, double gy, double *Gt) {
+  for (int i = 0; i < 9; i++) {
+    double eu = EX[i] * ux + EY[i] * uy;
+    double t1 = ((EX[i] - ux) * gx + (EY[i] - uy) * gy) / CS2;
+    double t2 = eu * (EX[i] * gx + EY[i] * gy) / (CS2 * CS2);
+    Gt[i] = WT[i] * (t1 + t2);
+  }
+}
+
+/* Macroscopic density deviation and velocity of one cell: drho = sum df
+ * (Eq. 11 less rho0), rho u = sum_i e_i f_i + g/2 (Eq. 24), rho = rho0 + drho. */
+void orc_cell_macros(const double *dfc, double rho0, double gx, double gy,
+                     double *drho, double *ux, double *uy) {
+  double s = 0, jx = 0, jy = 0;
+  for (int i = 0; i < 9; i++) {
+    s += dfc[i];
+    jx += EX[i] * dfc[i];
+    jy += EY[i] * dfc[i];
+  }
+  *drho = s;
+  *ux = (jx + 0.5 * gx) / (rho0 + s);
+  *uy = (jy + 0.5 * gy) / (rho0 + s);
+}
+
+/* Collision of one cell (shifted populations in and out).
+ *  SRT, Eq. 14 with Guo's term Eq. 21:
+ *    f* = f - (f - f_eq)/lambda + (1 - 1/(2 lambda)) Gt
+ *  MRT, Eq. 15 with Guo's term Eq. 22:
+ *    f* = f - M^-1 S (M f - M f_eq) + M^-1 (I - S/2) M Gt
+ * The shift w_i rho0 cancels in f - f_eq and passes through M^-1 M unchanged. */
+void orc_collide_cell(const orc_cfg *c, const double *M, const double *Minv,
+                      const double *dfc, double gx, double gy, double *out) {
+  double drho, ux, uy, dfeq[9], Gt[9];
+  orc_cell_macros(dfc, c->rho0, gx, gy, &drho, &ux, &uy);
+  orc_feq_shifted(drho, c->rho0, ux, uy, dfeq);
+  orc_guo_source(ux, uy, gx, gy, Gt);
+  if (c->collision == ORC_SRT) {
+    double lam = c->tau;
+    for (int i = 0; i < 9; i++)
+      out[i] = dfc[i] - (dfc[i] - dfeq[i]) / lam + (1.0 - 1.0 / (2.0 * lam)) * Gt[i];
+  } else {
+    double m[9], meq[9], mG[9], ms[9];
+    for (int r = 0; r < 9; r++) {
+      m[r] = meq[r] = mG[r] = 0;
+      for (int i = 0; i < 9; i++) {
+        m[r] += M[r * 9 + i] * dfc[i];
+        meq[r] += M[r * 9 + i] * dfeq[i];
+        mG[r] += M[r * 9 + i] * Gt[i];
+      }
+    }
+    for (int r = 0; r < 9; r++)
+      ms[r] = m[r] - c->s[r] * (m[r] - meq[r]) + (1.0 - 0.5 * c->s[r]) * mG[r];
+    for (int i = 0; i < 9; i++) {
+      out[i] = 0;
+      for (int r = 0; r < 9; r++) out[i] += Minv[i * 9 + r] * ms[r];
+    }
+  }
+}
+
+/* --------------------------------------------------- Peskin delta kernel ---
+ * Four-point regularised delta of Peskin (Acta Numerica 2002), the kernel the
+ * paper names after Eq. 6: delta_h(x) = phi(x) phi(y) with
+ *   phi(r) = (3 - 2|r| + sqrt(1 + 4|r| - 4r^2)) / 8,   |r| <= 1
+ *          = (5 - 2|r| - sqrt(-7 + 12|r| - 4r^2)) / 8,  1 <= |r| <= 2
+ *          = 0 otherwise. */
+double orc_phi(double r) {
+  double a = fabs(r);
+  if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
+  if (a <= 2.0) return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;
+  return 0.0;
+}
+
+/* Map a lattice coordinate to a cell index along one axis; -1 if outside a
+ * non-periodic axis. */
+static int wrap_axis(int v, int n, int periodic) {
+  if (periodic) { v %= n; if (v < 0) v += n; return v; }
+  return (v >= 0 && v < n) ? v : -1;
+}
+static int periodic_x(const orc_cfg *c) { return c->bc == ORC_BC_PERIODIC || c->bc == ORC_BC_WALLS_Y; }
+static int periodic_y(const orc_cfg *c) { return c->bc == ORC_BC_PERIODIC; }
+
+/* Force spreading, Eq. 17 / Eq. 46: g(x) += sum_k P_k delta_h(x - X_k), where
+ * P_k = G_k Delta X is the point force of marker k (lattice units, Delta x = 1). */
+void orc_spread(const orc_cfg *c, const double *X, int n, const double *P,
+                double *gx, double *gy) {
+  for (int k = 0; k < n; k++) {
+    int x0 = (int)floor(X[2 * k]) - 1, y0 = (int)floor(X[2 * k + 1]) - 1;
+    for (int b = 0; b < 4; b++)
+      for (int a = 0; a < 4; a++) {
+        int xi = wrap_axis(x0 + a, c->nx, periodic_x(c));
+        int yi = wrap_axis(y0 + b, c->ny, periodic_y(c));
+        if (xi < 0 || yi < 0) continue;
+        double d = orc_phi(x0 + a - X[2 * k]) * orc_phi(y0 + b - X[2 * k + 1]);
+        gx[yi * c->nx + xi] += P[2 * k] * d;
+        gy[yi * c->nx + xi] += P[2 * k + 1] * d;
+      }
+  }
+}
+
+/* Velocity interpolation, Eq. 20 (and U* of Eq. 18): U_k = sum_x u(x) delta_h(x - X_k). */
+void orc_interp(const orc_cfg *c, const double *X, int n, const double *ux,
+                const double *uy, double *U) {
+  for (int k = 0; k < n; k++) {
+    int x0 = (int)floor(X[2 * k]) - 1, y0 = (int)floor(X[2 * k + 1]) - 1;
+    double sx = 0, sy = 0;
+    for (int b = 0; b < 4; b++)
+      for (int a = 0; a < 4; a++) {
+        int xi = wrap_axis(x0 + a, c->nx, periodic_x(c));
+        int yi = wrap_axis(y0 + b, c->ny, periodic_y(c));
+        if (xi < 0 || yi < 0) continue;
+        double d = orc_phi(x0 + a - X[2 * k]) * orc_phi(y0 + b - X[2 * k + 1]);
+        sx += ux[yi * c->nx + xi] * d;
+        sy += uy[yi * c->nx + xi] * d;
+      }
+    U[2 * k] = sx;
+    U[2 * k + 1] = sy;
+  }
+}
+
+/* --------------------------------------------------- Lagrangian forces -----
+ * Membrane spring force, Eq. 19: G_k = kappa (X_{k+1} - 2 X_k + X_{k-1}) / dX^2.
+ * Rest-length spring (a linear spring of rest length l0 on every segment, a
+ * variant the paper's Eq. 19 reduces to at l0 = 0): segment tension
+ * T = kappa (l/l0 - 1) along the segment, point force on marker k
+ * P_k = T_k t_k - T_{k-1} t_{k-1}, G_k = P_k / dX. */
+void orc_spring_forces(const orc_iface *I, double *G) {
+  int n = I->n;
+  for (int k = 0; k < n; k++) {
+    int kp = (k + 1) % n, km = (k + n - 1) % n;
+    const double *Xk = I->X + 2 * k, *Xp = I->X + 2 * kp, *Xm = I->X + 2 * km;
+    if (I->model == ORC_SPRING) {
+      G[2 * k] = I->kappa * (Xp[0] - 2.0 * Xk[0] + Xm[0]) / (I->dX * I->dX);
+      G[2 * k + 1] = I->kappa * (Xp[1] - 2.0 * Xk[1] + Xm[1]) / (I->dX * I->dX);
+    } else {
+      double ax = Xp[0] - Xk[0], ay = Xp[1] - Xk[1];
+      double bx = Xk[0] - Xm[0], by = Xk[1] - Xm[1];
+      double la = sqrt(ax * ax + ay * ay), lb = sqrt(bx * bx + by * by);
+      double Ta = I->kappa * (la / I->l0 - 1.0), Tb = I->kappa * (lb / I->l0 - 1.0);
+      G[2 * k] = (Ta * ax / la - Tb * bx / lb) / I->dX;
+      G[2 * k + 1] = (Ta * ay / la - Tb * by / lb) / I->dX;
+    }
+  }
+}
+
+/* Normal / tangential split, Eqs. 31-32 and Eq. 46.
+ * n_k: outward unit normal of the counter-clockwise polygon at marker k, the
+ * central tangent X_{k+1} - X_{k-1} turned by -90 degrees (Eq. 31 in 2D).
+ * |X_s|_k = |X_{k+1} - X_{k-1}| / (2 dX) (Eq. 31's |X_r x X_s| for a curve);
+ * for a rigid body it is 1 as the paper states after Eq. 31.
+ * Fn_k = G_k.n_k / |X_s|_k  (the jump strength of Eq. 32),
+ * Gpar_k = G_k - (G_k.n_k) n_k  (the printed "G - G.n" after Eq. 46 read as
+ * the vector tangential part). */
+void orc_normal_split(const orc_iface *I, const double *G, double *Fn, double *Gpar,
+                      double *nrm) {
+  int n = I->n;
+  for (int k = 0; k < n; k++) {
+    int kp = (k + 1) % n, km = (k + n - 1) % n;
+    double tx = I->X[2 * kp] - I->X[2 * km], ty = I->X[2 * kp + 1] - I->X[2 * km + 1];
+    double tl = sqrt(tx * tx + ty * ty);
+    double nx = ty / tl, ny = -tx / tl;
+    double Xs = I->moves ? tl / (2.0 * I->dX) : 1.0;
+    double Gn = G[2 * k] * nx + G[2 * k + 1] * ny;
+    Fn[k] = Gn / Xs;
+    Gpar[2 * k] = G[2 * k] - Gn * nx;
+    Gpar[2 * k + 1] = G[2 * k + 1] - Gn * ny;
+    if (nrm) { nrm[2 * k] = nx; nrm[2 * k + 1] = ny; }
+  }
+}
+
+/* ------------------------------------------------------------ cut links ----
+ * Which streamed populations carry the jump (section 3.2, Eq. 47 and the P1/P2
+ * example): f_i arriving at node x gets [[f_i]] when the streaming path
+ * x - e_i -> x crosses the interface.  The interface is the marker polygon and
+ * the jump strength Fn is linear in the segment parameter.
+ *
+ * Sign (Eq. 30: [[psi]] = psi(+) - psi(-), + = exterior): a population that
+ * passes from the interior (-) to the exterior (+) gains +[[f_i]], one passing
+ * the other way gains -[[f_i]].  Value (Eq. 32): [[f_i]] = w_i/c_s^2 Fn.
+ *
+ * Predicate (reading; the paper uses a spline and gives no crossing rule):
+ * marker coordinates are snapped to multiples of 2^-24 lattice units, so every
+ * orientation test is exact 64-bit integer arithmetic, and degenerate contacts
+ * are resolved by symbolically displacing every lattice node by (eps, eps^2),
+ * eps -> 0+.  With this rule the signed number of crossings on a link equals
+ * winding(x - e_i) - winding(x) of the polygon, exactly. */
+#define ORC_QSCALE 16777216.0 /* 2^24 */
+
+static int sgn64(int64_t v) { return v > 0 ? 1 : (v < 0 ? -1 : 0); }
+
+/* orient(A, B, P + (eps, eps^2)) = cross(B - A, P - A) + dx eps^2 - dy eps */
+int orc_orient_seg_node(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t px, int64_t py) {
+  int64_t dx = bx - ax, dy = by - ay;
+  int64_t o = dx * (py - ay) - dy * (px - ax);
+  if (o != 0) return sgn64(o);
+  if (dy != 0) return -sgn64(dy);
+  return sgn64(dx);
+}
+/* orient(P + d, P + e + d, A) with d = (eps, eps^2) = cross(e, A - P) + ey eps - ex eps^2 */
+int orc_orient_link_pt(int64_t px, int64_t py, int ex, int ey, int64_t ax, int64_t ay) {
+  int64_t o = (int64_t)ex * (ay - py) - (int64_t)ey * (ax - px);
+  if (o != 0) return sgn64(o);
+  if (ey != 0) return ey > 0 ? 1 : -1;
+  return ex > 0 ? -1 : 1;
+}
+
+int64_t orc_quantize(double v) { return (int64_t)llrint(v * ORC_QSCALE); }
+
+/* Test one lattice link (source node p, direction i) against one segment A->B
+ * (quantised).  Returns 0 if it does not cross, else the sign s and the crossing
+ * parameter t along A->B. */
+int orc_link_crosses(int64_t ax, int64_t ay, int64_t bx, int64_t by, int px, int py,
+                     int i, int *s, double *t) {
+  int64_t Px = (int64_t)px * (int64_t)ORC_QSCALE, Py = (int64_t)py * (int64_t)ORC_QSCALE;
+  int64_t Qx = (int64_t)(px + EX[i]) * (int64_t)ORC_QSCALE, Qy = (int64_t)(py + EY[i]) * (int64_t)ORC_QSCALE;
+  int s1 = orc_orient_seg_node(ax, ay, bx, by, Px, Py);
+  int s2 = orc_orient_seg_node(ax, ay, bx, by, Qx, Qy);
+  if (s1 == s2) return 0;
+  int s3 = orc_orient_link_pt(Px, Py, EX[i], EY[i], ax, ay);
+  int s4 = orc_orient_link_pt(Px, Py, EX[i], EY[i], bx, by);
+  if (s3 == s4) return 0;
+  int64_t o3 = (int64_t)EX[i] * (ay - Py) - (int64_t)EY[i] * (ax - Px);
+  int64_t o4 = (int64_t)EX[i] * (by - Py) - (int64_t)EY[i] * (bx - Px);
+  *t = (double)o3 / ((double)o3 - (double)o4);
+  if (*t < 0.0) *t = 0.0;
+  if (*t > 1.0) *t = 1.0;
+  *s = s1; /* source left of A->B = interior of a CCW polygon: - to +, sign +1 */
+  return 1;
+}
+
+/* Enumerate every crossing of every segment.  Output records: destination cell
+ * (row-major y*nx+x), direction i, coefficient s * w_i / c_s^2 * Fn(t).
+ * Candidates per segment: destination nodes within one node of the segment's
+ * bounding box (a crossing lies in both the segment's box and the link's unit
+ * box).  Returns the number of records, or -1 if cap is exceeded. */
+int orc_cut_links(const orc_cfg *c, const double *X, int n, const double *Fn,
+                  int *cell, int *dir, double *coef, int cap) {
+  int cnt = 0;
+  for (int k = 0; k < n; k++) {
+    int kp = (k + 1) % n;
+    int64_t ax = orc_quantize(X[2 * k]), ay = orc_quantize(X[2 * k + 1]);
+    int64_t bx = orc_quantize(X[2 * kp]), by = orc_quantize(X[2 * kp + 1]);
+    double minx = fmin(X[2 * k], X[2 * kp]), maxx = fmax(X[2 * k], X[2 * kp]);
+    double miny = fmin(X[2 * k + 1], X[2 * kp + 1]), maxy = fmax(X[2 * k + 1], X[2 * kp + 1]);
+    int x0 = (int)floor(minx) - 1, x1 = (int)ceil(maxx) + 1;
+    int y0 = (int)floor(miny) - 1, y1 = (int)ceil(maxy) + 1;
+    for (int qy = y0; qy <= y1; qy++)
+      for (int qx = x0; qx <= x1; qx++)
+        for (int i = 1; i < 9; i++) {
+          int s; double t;
+          if (!orc_link_crosses(ax, ay, bx, by, qx - EX[i], qy - EY[i], i, &s, &t)) continue;
+          int xd = wrap_axis(qx, c->nx, periodic_x(c)), yd = wrap_axis(qy, c->ny, periodic_y(c));
+          int xs = wrap_axis(qx - EX[i], c->nx, periodic_x(c)), ys = wrap_axis(qy - EY[i], c->ny, periodic_y(c));
+          if (xd < 0 || yd < 0 || xs < 0 || ys < 0) continue;
+          if (cnt >= cap) return -1;
+          double F = (1.0 - t) * Fn[k] + t * Fn[kp];
+          cell[cnt] = yd * c->nx + xd;
+          dir[cnt] = i;
+          coef[cnt] = (double)s * WT[i] / CS2 * F;
+          cnt++;
+        }
+  }
+  return cnt;
+}
+
+/* Winding number of the closed polygon around node (px, py) displaced by
+ * (eps, eps^2), by the crossing-parity rule on the horizontal ray to +x
+ * (used only by tests as an independent check of the cut-link signs). */
+int orc_winding(const double *X, int n, int px, int py) {
+  int64_t Px = (int64_t)px * (int64_t)ORC_QSCALE, Py = (int64_t)py * (int64_t)ORC_QSCALE;
+  int w = 0;
+  for (int k = 0; k < n; k++) {
+    int kp = (k + 1) % n;
+    int64_t ax = orc_quantize(X[2 * k]), ay = orc_quantize(X[2 * k + 1]);
+    int64_t bx = orc_quantize(X[2 * kp]), by = orc_quantize(X[2 * kp + 1]);
+    /* node y + eps^2 against the vertex heights: a vertex is "above" iff ay > Py
+     * (equal heights count as below, since the node sits eps^2 higher) */
+    int aup = ay > Py, bup = by > Py;
+    if (aup == bup) continue;
+    int o = orc_orient_seg_node(ax, ay, bx, by, Px, Py);
+    if (bup && o > 0) w += 1;  /* upward edge with the node on its left */
+    if (!bup && o < 0) w -= 1; /* downward edge with the node on its right */
+  }
+  return w;
+}
+
+/* ------------------------------------------------------------- streaming ---
+ * Collide-then-stream form of Eqs. 14-15 and Eq. 47: f_i(x, t+1) = f*_i(x - e_i).
+ * Eq. 47 places RHS at the destination; the standard collide-at-source form is
+ * taken (section 2.2.1 discretisation read as the usual lattice update).
+ * Walls (ORC_BC_WALLS_Y, ORC_BC_CHANNEL): halfway bounce-back at y = -1/2 and
+ * y = ny - 1/2: a population whose source lies beyond a wall is the reflected
+ * post-collision population of the destination node, f_i(x) = f*_{opp(i)}(x).
+ * Channel: populations whose source lies beyond x = 0 or x = nx - 1 are left as
+ * the post-collision value of the node itself and are overwritten by
+ * orc_channel_bc. */
+static void stream(const orc_cfg *c, const double *fs, double *out) {
+  int nx = c->nx, ny = c->ny, N = nx * ny;
+  for (int i = 0; i < 9; i++)
+    for (int y = 0; y < ny; y++)
+      for (int x = 0; x < nx; x++) {
+        int sx = x - EX[i], sy = y - EY[i];
+        int wy = (sy < 0 || sy >= ny) && !periodic_y(c);
+        int wx = (sx < 0 || sx >= nx) && !periodic_x(c);
+        double v;
+        if (wy) {
+          v = fs[OPP[i] * N + y * nx + x];
+        } else if (wx) {
+          v = fs[i * N + y * nx + x];
+        } else {
+          sx = ((sx % nx) + nx) % nx;
+          sy = ((sy % ny) + ny) % ny;
+          v = fs[i * N + sy * nx + sx];
+        }
+        out[i * N + y * nx + x] = v;
+      }
+}
+
+/* Channel inflow / outflow on the streamed state.
+ * Inflow column x = 0: non-equilibrium extrapolation of Guo, Zheng & Shi (the
+ * paper's boundary method for open and wall boundaries in section 4):
+ *   f_i(0,y) = f_eq_i(rho(1,y), u_in(y)) + [f_i(1,y) - f_eq_i(rho(1,y), u(1,y))]
+ * with the parabolic profile u_in(y) = 4 u_max (y+1/2)(ny-y-1/2)/ny^2, v = 0.
+ * Outflow column x = nx-1: zero gradient on the unknown populations (e_x < 0),
+ * f_i(nx-1,y) = f_i(nx-2,y). */
+static void channel_bc(const orc_cfg *c, double *df) {
+  int nx = c->nx, ny = c->ny, N = nx * ny;
+  for (int y = 0; y < ny; y++) {
+    double dfc[9], r, ux, uy, a[9], b[9];
+    for (int i = 0; i < 9; i++) dfc[i] = df[i * N + y * nx + 1];
+    orc_cell_macros(dfc, c->rho0, 0.0, 0.0, &r, &ux, &uy);
+    double yy = y + 0.5;
+    double uin = 4.0 * c->u_max * yy * (ny - yy) / ((double)ny * ny);
+    orc_feq_shifted(r, c->rho0, uin, 0.0, a);  /* r is the deviation drho(1,y) */
+    orc_feq_shifted(r, c->rho0, ux, uy, b);
+    for (int i = 0; i < 9; i++) df[i * N + y * nx + 0] = a[i] + (dfc[i] - b[i]);
+    for (int i = 0; i < 9; i++)
+      if (EX[i] < 0) df[i * N + y * nx + nx - 1] = df[i * N + y * nx + nx - 2];
+  }
+}
+
+/* --------------------------------------------------------------- state ---- */
+orc_state *orc_create(const orc_cfg *cfg) {
+  orc_state *S = (orc_state *)calloc(1, sizeof(orc_state));
+  S->c = *cfg;
+  size_t N = (size_t)cfg->nx * cfg->ny;
+  S->df = (double *)calloc(9 * N, sizeof(double));
+  S->tmp = (double *)calloc(9 * N, sizeof(double));
+  S->f = (double *)calloc(9 * N, sizeof(double));
+  S->gx = (double *)calloc(N, sizeof(double));
+  S->gy = (double *)calloc(N, sizeof(double));
+  S->rho = (double *)calloc(N, sizeof(double));
+  S->ux = (double *)calloc(N, sizeof(double));
+  S->uy = (double *)calloc(N, sizeof(double));
+  orc_mrt_matrix(S->M);
+  orc_invert9(S->M, S->Minv);
+  return S;
+}
+
+static void free_iface(orc_state *S) {
+  if (!S->has_iface) return;
+  free(S->I.X); free(S->I.Gp); free(S->I.UD);
+  free(S->G); free(S->Fn); free(S->Gpar); free(S->U);
+  S->has_iface = 0;
+}
+
+void orc_destroy(orc_state *S) {
+  if (!S) return;
+  free_iface(S);
+  free(S->df); free(S->tmp); free(S->f); free(S->gx); free(S->gy);
+  free(S->rho); free(S->ux); free(S->uy);
+  free(S);
+}
+
+void orc_set_df(orc_state *S, const double *df) {
+  memcpy(S->df, df, 9 * (size_t)S->c.nx * S->c.ny * sizeof(double));
+}
+void orc_get_df(const orc_state *S, double *df) {
+  memcpy(df, S->df, 9 * (size_t)S->c.nx * S->c.ny * sizeof(double));
+}
+
+/* Equilibrium initial state at density rho(x), velocity u(x) (arrays may be NULL
+ * for rho0 / zero). */
+void orc_init_equilibrium(orc_state *S, const double *rho, const double *ux, const double *uy) {
+  int N = S->c.nx * S->c.ny;
+  for (int p = 0; p < N; p++) {
+    double e[9];
+    orc_feq_shifted(rho ? rho[p] - S->c.rho0 : 0.0, S->c.rho0, ux ? ux[p] : 0.0, uy ? uy[p] : 0.0, e);
+    for (int i = 0; i < 9; i++) S->df[i * N + p] = e[i];
+  }
+}
+
+int orc_set_interface(orc_state *S, const double *X, int n, int model, int moves,
+                      double kappa, double dX, double l0, double eta, int mdf_iters,
+                      double mdf_tol, const double *Gp, const double *UD) {
+  free_iface(S);
+  if (n <= 0) return 0;
+  orc_iface *I = &S->I;
+  I->n = n; I->model = model; I->moves = moves; I->kappa = kappa; I->dX = dX; I->l0 = l0;
+  I->eta = eta; I->mdf_iters = mdf_iters; I->mdf_tol = mdf_tol;
+  I->X = (double *)malloc(2 * n * sizeof(double));
+  I->Gp = (double *)calloc(2 * n, sizeof(double));
+  I->UD = (double *)calloc(2 * n, sizeof(double));
+  memcpy(I->X, X, 2 * n * sizeof(double));
+  if (Gp) memcpy(I->Gp, Gp, 2 * n * sizeof(double));
+  if (UD) memcpy(I->UD, UD, 2 * n * sizeof(double));
+  S->G = (double *)calloc(2 * n, sizeof(double));
+  S->Fn = (double *)calloc(n, sizeof(double));
+  S->Gpar = (double *)calloc(2 * n, sizeof(double));
+  S->U = (double *)calloc(2 * n, sizeof(double));
+  S->has_iface = 1;
+  return 0;
+}
+
+/* Direct forcing with repeated correction, Eq. 18 (reading: multi-direct forcing,
+ * Guo half-force velocity).  u* = (sum e df + body/2)/rho is the velocity without
+ * immersed-boundary forcing; each pass interpolates u* + spread(G dX)/(2 rho),
+ * adds eta (U^D - U) to G, and stops after mdf_iters passes or when
+ * max_k |U^D - U_k| < mdf_tol.  The pass count and final residual are kept. */
+static void direct_forcing(orc_state *S, const double *dfs) {
+  const orc_cfg *c = &S->c;
+  orc_iface *I = &S->I;
+  int N = c->nx * c->ny, n = I->n;
+  double *us_x = (double *)calloc(N, sizeof(double)), *us_y = (double *)calloc(N, sizeof(double));
+  double *r = (double *)calloc(N, sizeof(double)); /* drho */
+  double *gx = (double *)calloc(N, sizeof(double)), *gy = (double *)calloc(N, sizeof(double));
+  double *vx = (double *)calloc(N, sizeof(double)), *vy = (double *)calloc(N, sizeof(double));
+  double *P = (double *)calloc(2 * n, sizeof(double));
+  for (int p = 0; p < N; p++) {
+    double dfc[9];
+    for (int i = 0; i < 9; i++) dfc[i] = dfs[i * N + p];
+    orc_cell_macros(dfc, c->rho0, c->body_x, c->body_y, &r[p], &us_x[p], &us_y[p]);
+  }
+  for (int k = 0; k < 2 * n; k++) S->G[k] = I->Gp[k]; /* warm start (0 = plain) */
+  int it = 0;
+  double res = 0;
+  for (it = 0; it < I->mdf_iters; it++) {
+    memset(gx, 0, N * sizeof(double)); memset(gy, 0, N * sizeof(double));
+    for (int k = 0; k < 2 * n; k++) P[k] = S->G[k] * I->dX;
+    orc_spread(c, I->X, n, P, gx, gy);
+    for (int p = 0; p < N; p++) {
+      vx[p] = us_x[p] + 0.5 * gx[p] / (c->rho0 + r[p]);
+      vy[p] = us_y[p] + 0.5 * gy[p] / (c->rho0 + r[p]);
+    }
+    orc_interp(c, I->X, n, vx, vy, S->U);
+    res = 0;
+    for (int k = 0; k < 2 * n; k++) res = fmax(res, fabs(I->UD[k] - S->U[k]));
+    if (I->mdf_tol > 0 && res < I->mdf_tol) break;
+    for (int k = 0; k < 2 * n; k++) S->G[k] += I->eta * (I->UD[k] - S->U[k]);
+  }
+  S->mdf_last_iters = it;
+  S->mdf_last_res = res;
+  free(us_x); free(us_y); free(r); free(gx); free(gy); free(vx); free(vy); free(P);
+}
+
+/* One II-LBM time step, t -> t+1 (section 3.2, Eq. 47, with Eqs. 17-24).
+ *  1. Lagrangian force G_k from X^t (Eq. 19, its rest-length variant, a
+ *     prescribed force, or direct forcing Eq. 18).
+ *  2. Split: Fn_k (jump strength, Eq. 32), Gpar_k (Eq. 46).
+ *  3. II-LBM: f = df + [[f]] on every cut link of the polygon X^t (Eq. 47 adds
+ *     the jump at the new time level, evaluated on the interface of that level);
+ *     g = spread(Gpar dX) + body (Eq. 46).  IB-LBM: f = df, g = spread(G dX) + body.
+ *  4. rho, u from f and g (Eqs. 11, 24); U_k = interp(u) (Eq. 20).
+ *  5. Collide every cell (Eqs. 14/15 with 21/22), stream (Eq. 47), boundaries.
+ *  6. X^{t+1} = X^t + U_k for a membrane (Eq. 20). */
+int orc_step(orc_state *S) {
+  const orc_cfg *c = &S->c;
+  int nx = c->nx, ny = c->ny, N = nx * ny;
+  memcpy(S->f, S->df, 9 * (size_t)N * sizeof(double));
+  for (int p = 0; p < N; p++) { S->gx[p] = c->body_x; S->gy[p] = c->body_y; }
+  if (S->has_iface) {
+    orc_iface *I = &S->I;
+    int n = I->n;
+    if (I->model == ORC_SPRING || I->model == ORC_SPRING_REST) orc_spring_forces(I, S->G);
+    else if (I->model == ORC_PRESCRIBED) memcpy(S->G, I->Gp, 2 * n * sizeof(double));
+    else direct_forcing(S, S->df);
+    orc_normal_split(I, S->G, S->Fn, S->Gpar, NULL);
+    double *P = (double *)malloc(2 * n * sizeof(double));
+    if (c->jump) {
+      int cap = 64 * n + 64;
+      int *cell = (int *)malloc(cap * sizeof(int)), *dir = (int *)malloc(cap * sizeof(int));
+      double *coef = (double *)malloc(cap * sizeof(double));
+      int m = orc_cut_links(c, I->X, n, S->Fn, cell, dir, coef, cap);
+      if (m < 0) { free(cell); free(dir); free(coef); free(P); return -1; }
+      for (int r = 0; r < m; r++) S->f[dir[r] * N + cell[r]] += coef[r];
+      free(cell); free(dir); free(coef);
+      for (int k = 0; k < 2 * n; k++) P[k] = S->Gpar[k] * I->dX;
+    } else {
+      for (int k = 0; k < 2 * n; k++) P[k] = S->G[k] * I->dX;
+    }
+    orc_spread(c, I->X, n, P, S->gx, S->gy);
+    free(P);
+  }
+  for (int p = 0; p < N; p++) {
+    double dfc[9];
+    for (int i = 0; i < 9; i++) dfc[i] = S->f[i * N + p];
+    orc_cell_macros(dfc, c->rho0, S->gx[p], S->gy[p], &S->rho[p], &S->ux[p], &S->uy[p]);
+  }
+  if (S->has_iface) orc_interp(c, S->I.X, S->I.n, S->ux, S->uy, S->U);
+  for (int p = 0; p < N; p++) {
+    double dfc[9], out[9];
+    for (int i = 0; i < 9; i++) dfc[i] = S->f[i * N + p];
+    orc_collide_cell(c, S->M, S->Minv, dfc, S->gx[p], S->gy[p], out);
+    for (int i = 0; i < 9; i++) S->tmp[i * N + p] = out[i];
+  }
+  stream(c, S->tmp, S->df);
+  if (c->bc == ORC_BC_CHANNEL) channel_bc(c, S->df);
+  if (S->has_iface && S->I.moves)
+    for (int k = 0; k < 2 * S->I.n; k++) S->I.X[k] += S->U[k];
+  S->step++;
+  return 0;
+}
+
+int orc_run(orc_state *S, int nsteps) {
+  for (int s = 0; s < nsteps; s++)
+    if (orc_step(S)) return -1;
+  return 0;
+}
+
+/* Macroscopic fields of the most recent step's collision (drho = rho - rho0 and
+ * u of Eq. 24 at time t, the velocity the markers moved with). */
+void orc_get_step_macros(const orc_state *S, double *rho, double *ux, double *uy) {
+  size_t N = (size_t)S->c.nx * S->c.ny;
+  if (rho) memcpy(rho, S->rho, N * sizeof(double));
+  if (ux) memcpy(ux, S->ux, N * sizeof(double));
+  if (uy) memcpy(uy, S->uy, N * sizeof(double));
+}
+
+void orc_get_markers(const orc_state *S, double *X, double *G, double *U, double *Fn) {
+  if (!S->has_iface) return;
+  int n = S->I.n;
+  if (X) memcpy(X, S->I.X, 2 * n * sizeof(double));
+  if (G) memcpy(G, S->G, 2 * n * sizeof(double));
+  if (U) memcpy(U, S->U, 2 * n * sizeof(double));
+  if (Fn) memcpy(Fn, S->Fn, n * sizeof(double));
+}
+
+int orc_mdf_iters(const orc_state *S) { return S->mdf_last_iters; }
+double orc_mdf_residual(const orc_state *S) { return S->mdf_last_res; }
+
+/* Enclosed area of the marker polygon (shoelace formula); the area-loss metrics
+ * of Eqs. 49-50 are differences of this quantity. */
+double orc_polygon_area(const double *X, int n) {
+  double a = 0;
+  for (int k = 0; k < n; k++) {
+    int kp = (k + 1) % n;
+    a += X[2 * k] * X[2 * kp + 1] - X[2 * kp] * X[2 * k + 1];
+  }
+  return 0.5 * a;
+}
+
+/* Array-argument entry points of the two force routines (for tests). */
+void orc_spring_forces_arr(const double *X, int n, int model, double kappa, double dX,
+                           double l0, double *G) {
+  orc_iface I;
+  memset(&I, 0, sizeof I);
+  I.n = n; I.model = model; I.kappa = kappa; I.dX = dX; I.l0 = l0; I.X = (double *)X;
+  orc_spring_forces(&I, G);
+}
+void orc_normal_split_arr(const double *X, int n, int moves, double dX, const double *G,
+                          double *Fn, double *Gpar, double *nrm) {
+  orc_iface I;
+  memset(&I, 0, sizeof I);
+  I.n = n; I.moves = moves; I.dX = dX; I.X = (double *)X;
+  orc_normal_split(&I, G, Fn, Gpar, nrm);
+}

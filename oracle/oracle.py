@@ -1,0 +1,291 @@
+"""FP64 CPU oracle of the II-LBM time step -- ctypes wrapper.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py``; never by the product package.  The oracle is
+``iilbm_oracle.c`` in this directory, compiled by :func:`build` with gcc alone.  It
+shares no code with the CUDA library.
+
+Every function maps one-to-one onto a routine of ``iilbm_oracle.c``; the paper
+passages each follows are cited there.  Parity pins: every routine here is pinned
+by a test in ``tests/test_oracle_*.py`` against a closed form, an invariant, a
+special case or a brute-force / exact-rational computation (see the test
+docstrings); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "iilbm_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle_iilbm.so")
+_lock = threading.Lock()
+_lib = None
+
+SRT, MRT = 0, 1
+BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL = 0, 1, 2
+SPRING, SPRING_REST, PRESCRIBED, DIRECT = 0, 1, 2, 3
+# Lallemand-Luo D2Q9 rates quoted in section 2.2.1 (s7 = s8 = 1/tau set per case)
+PAPER_MRT_RATES = (0.0, 1.63, 1.14, 0.0, 1.92, 0.0, 1.92, None, None)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-std=c11", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Cfg(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("collision", C.c_int), ("tau", C.c_double),
+                ("s", C.c_double * 9), ("rho0", C.c_double), ("bc", C.c_int),
+                ("u_max", C.c_double), ("body_x", C.c_double), ("body_y", C.c_double),
+                ("jump", C.c_int)]
+
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_create.restype = C.c_void_p
+            L.orc_create.argtypes = [C.POINTER(_Cfg)]
+            L.orc_destroy.argtypes = [C.c_void_p]
+            L.orc_set_df.argtypes = [C.c_void_p, _D]
+            L.orc_get_df.argtypes = [C.c_void_p, _D]
+            L.orc_init_equilibrium.argtypes = [C.c_void_p, _D, _D, _D]
+            L.orc_set_interface.argtypes = [C.c_void_p, _D, C.c_int, C.c_int, C.c_int, C.c_double,
+                                            C.c_double, C.c_double, C.c_double, C.c_int,
+                                            C.c_double, _D, _D]
+            L.orc_step.argtypes = [C.c_void_p]
+            L.orc_run.argtypes = [C.c_void_p, C.c_int]
+            L.orc_get_step_macros.argtypes = [C.c_void_p, _D, _D, _D]
+            L.orc_get_markers.argtypes = [C.c_void_p, _D, _D, _D, _D]
+            L.orc_mdf_iters.argtypes = [C.c_void_p]
+            L.orc_mdf_residual.argtypes = [C.c_void_p]
+            L.orc_mdf_residual.restype = C.c_double
+            L.orc_polygon_area.argtypes = [_D, C.c_int]
+            L.orc_polygon_area.restype = C.c_double
+            L.orc_phi.argtypes = [C.c_double]
+            L.orc_phi.restype = C.c_double
+            L.orc_mrt_matrix.argtypes = [_D]
+            L.orc_invert9.argtypes = [_D, _D]
+            L.orc_feq_shifted.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _D]
+            L.orc_guo_source.argtypes = [C.c_double] * 4 + [_D]
+            L.orc_collide_cell.argtypes = [C.POINTER(_Cfg), _D, _D, _D, C.c_double, C.c_double, _D]
+            L.orc_cut_links.argtypes = [C.POINTER(_Cfg), _D, C.c_int, _D, _I, _I, _D, C.c_int]
+            L.orc_winding.argtypes = [_D, C.c_int, C.c_int, C.c_int]
+            L.orc_spread.argtypes = [C.POINTER(_Cfg), _D, C.c_int, _D, _D, _D]
+            L.orc_interp.argtypes = [C.POINTER(_Cfg), _D, C.c_int, _D, _D, _D]
+            L.orc_spring_forces_arr.argtypes = [_D, C.c_int, C.c_int, C.c_double, C.c_double,
+                                                C.c_double, _D]
+            L.orc_normal_split_arr.argtypes = [_D, C.c_int, C.c_int, C.c_double, _D, _D, _D, _D]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def make_cfg(nx, ny, collision=SRT, tau=0.8, s=None, rho0=1.0, bc=BC_PERIODIC, u_max=0.0,
+             body=(0.0, 0.0), jump=1) -> _Cfg:
+    c = _Cfg()
+    c.nx, c.ny, c.collision, c.tau, c.rho0, c.bc, c.u_max = nx, ny, collision, tau, rho0, bc, u_max
+    c.body_x, c.body_y = body
+    c.jump = jump
+    rates = mrt_rates(tau) if s is None else s
+    for i in range(9):
+        c.s[i] = rates[i]
+    return c
+
+
+def mrt_rates(tau: float, paper: bool = True):
+    """Section 2.2.1 D2Q9 rates with s7 = s8 = 1/tau (paper=True), else all 1/tau."""
+    if not paper:
+        return [1.0 / tau] * 9
+    r = list(PAPER_MRT_RATES)
+    r[7] = r[8] = 1.0 / tau
+    return r
+
+
+# ---------------------------------------------------------------- primitives
+def phi(r: float) -> float:
+    return lib().orc_phi(float(r))
+
+
+def mrt_matrix():
+    M = np.zeros(81)
+    lib().orc_mrt_matrix(_p(M))
+    Mi = np.zeros(81)
+    lib().orc_invert9(_p(M), _p(Mi))
+    return M.reshape(9, 9), Mi.reshape(9, 9)
+
+
+def feq_shifted(rho, rho0, ux, uy):
+    """Shifted equilibrium of Eq. 23 at density rho (passed to C as rho - rho0)."""
+    out = np.zeros(9)
+    lib().orc_feq_shifted(rho - rho0, rho0, ux, uy, _p(out))
+    return out
+
+
+def guo_source(ux, uy, gx, gy):
+    out = np.zeros(9)
+    lib().orc_guo_source(ux, uy, gx, gy, _p(out))
+    return out
+
+
+def collide_cell(cfg: _Cfg, df, gx=0.0, gy=0.0):
+    M, Mi = mrt_matrix()
+    M, Mi = _f64(M.ravel()), _f64(Mi.ravel())
+    df = _f64(df)
+    out = np.zeros(9)
+    lib().orc_collide_cell(C.byref(cfg), _p(M), _p(Mi), _p(df), gx, gy, _p(out))
+    return out
+
+
+def cut_links(cfg: _Cfg, X, Fn, cap=None):
+    """Cut-link records (cell, dir, coef) of the closed polygon X with jump strengths Fn."""
+    X = _f64(X).reshape(-1, 2)
+    Fn = _f64(Fn)
+    n = X.shape[0]
+    cap = cap or 64 * n + 64
+    cell = np.zeros(cap, np.int32)
+    d = np.zeros(cap, np.int32)
+    coef = np.zeros(cap)
+    m = lib().orc_cut_links(C.byref(cfg), _p(X), n, _p(Fn), cell.ctypes.data_as(_I),
+                            d.ctypes.data_as(_I), _p(coef), cap)
+    if m < 0:
+        raise RuntimeError("cut-link capacity exceeded")
+    return cell[:m].copy(), d[:m].copy(), coef[:m].copy()
+
+
+def winding(X, px: int, py: int) -> int:
+    X = _f64(X).reshape(-1, 2)
+    return lib().orc_winding(_p(X), X.shape[0], int(px), int(py))
+
+
+def spread(cfg: _Cfg, X, P):
+    X = _f64(X).reshape(-1, 2)
+    P = _f64(P).reshape(-1, 2)
+    gx = np.zeros(cfg.nx * cfg.ny)
+    gy = np.zeros(cfg.nx * cfg.ny)
+    lib().orc_spread(C.byref(cfg), _p(X), X.shape[0], _p(P), _p(gx), _p(gy))
+    return gx.reshape(cfg.ny, cfg.nx), gy.reshape(cfg.ny, cfg.nx)
+
+
+def interp(cfg: _Cfg, X, ux, uy):
+    X = _f64(X).reshape(-1, 2)
+    U = np.zeros((X.shape[0], 2))
+    lib().orc_interp(C.byref(cfg), _p(X), X.shape[0], _p(_f64(ux).ravel()),
+                     _p(_f64(uy).ravel()), _p(U))
+    return U
+
+
+def spring_forces(X, model=SPRING, kappa=1.0, dX=1.0, l0=1.0):
+    X = _f64(X).reshape(-1, 2)
+    G = np.zeros_like(X)
+    lib().orc_spring_forces_arr(_p(X), X.shape[0], model, kappa, dX, l0, _p(G))
+    return G
+
+
+def normal_split(X, G, moves=True, dX=1.0):
+    """(Fn, Gpar, normals) of Eqs. 31-32 and 46."""
+    X = _f64(X).reshape(-1, 2)
+    G = _f64(G).reshape(-1, 2)
+    n = X.shape[0]
+    Fn, Gpar, nrm = np.zeros(n), np.zeros((n, 2)), np.zeros((n, 2))
+    lib().orc_normal_split_arr(_p(X), n, int(moves), dX, _p(G), _p(Fn), _p(Gpar), _p(nrm))
+    return Fn, Gpar, nrm
+
+
+def polygon_area(X) -> float:
+    X = _f64(X).reshape(-1, 2)
+    return lib().orc_polygon_area(_p(X), X.shape[0])
+
+
+# -------------------------------------------------------------- simulation
+class Oracle:
+    """One lattice with at most one immersed interface, stepped on the CPU in FP64."""
+
+    def __init__(self, nx, ny, **kw):
+        self.cfg = make_cfg(nx, ny, **kw)
+        self.nx, self.ny = nx, ny
+        self._h = lib().orc_create(C.byref(self.cfg))
+        self.n_markers = 0
+
+    def close(self):
+        if self._h:
+            lib().orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # state
+    def init_equilibrium(self, rho=None, ux=None, uy=None):
+        keep = [None if a is None else _f64(a).ravel() for a in (rho, ux, uy)]
+        lib().orc_init_equilibrium(self._h, *[None if k is None else _p(k) for k in keep])
+
+    def set_df(self, df):
+        df = _f64(df).reshape(9, self.ny, self.nx)
+        lib().orc_set_df(self._h, _p(df))
+
+    def get_df(self):
+        df = np.zeros((9, self.ny, self.nx))
+        lib().orc_get_df(self._h, _p(df))
+        return df
+
+    def set_interface(self, X, model=SPRING, moves=True, kappa=0.0, dX=1.0, l0=1.0, eta=2.0,
+                      mdf_iters=0, mdf_tol=0.0, G=None, UD=None):
+        X = _f64(X).reshape(-1, 2)
+        n = X.shape[0]
+        Gp = None if G is None else _f64(G).reshape(n, 2)
+        UDa = None if UD is None else _f64(UD).reshape(n, 2)
+        lib().orc_set_interface(self._h, _p(X), n, model, int(moves), kappa, dX, l0, eta,
+                                mdf_iters, mdf_tol, None if Gp is None else _p(Gp),
+                                None if UDa is None else _p(UDa))
+        self.n_markers = n
+
+    def step(self, n=1):
+        if lib().orc_run(self._h, int(n)) != 0:
+            raise RuntimeError("oracle step failed (cut-link capacity)")
+
+    def step_macros(self, deviation=False):
+        """rho (or rho - rho0 if deviation), ux, uy used by the most recent step's
+        collision (Eq. 24 at time t)."""
+        N = self.nx * self.ny
+        r, ux, uy = np.zeros(N), np.zeros(N), np.zeros(N)
+        lib().orc_get_step_macros(self._h, _p(r), _p(ux), _p(uy))
+        s = (self.ny, self.nx)
+        if not deviation:
+            r = r + self.cfg.rho0
+        return r.reshape(s), ux.reshape(s), uy.reshape(s)
+
+    def markers(self):
+        n = self.n_markers
+        X, G, U, Fn = np.zeros((n, 2)), np.zeros((n, 2)), np.zeros((n, 2)), np.zeros(n)
+        lib().orc_get_markers(self._h, _p(X), _p(G), _p(U), _p(Fn))
+        return dict(X=X, G=G, U=U, Fn=Fn)
+
+    def mdf_stats(self):
+        return lib().orc_mdf_iters(self._h), lib().orc_mdf_residual(self._h)

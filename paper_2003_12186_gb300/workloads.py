@@ -1,0 +1,129 @@
+"""Seeded synthetic inputs (marker polygons, lattice parameters, perturbed states).
+
+This module builds inputs only: shapes, sizes, rates and seeds of the workloads the
+paper's section 4 experiments are shaped like.  It holds none of the method's
+arithmetic and imports neither the CUDA library nor the CPU oracle, so both sides
+can draw identical inputs from it.
+
+All marker polygons are closed, counter-clockwise, returned as float64 [n, 2] arrays
+in lattice units (node (i, j) sits at coordinate (i, j)).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Lallemand-Luo D2Q9 rates quoted in section 2.2.1 of the paper; s7 = s8 = 1/tau.
+PAPER_MRT_RATES = (0.0, 1.63, 1.14, 0.0, 1.92, 0.0, 1.92)
+
+
+def mrt_rates(tau: float) -> list:
+    return list(PAPER_MRT_RATES) + [1.0 / tau, 1.0 / tau]
+
+
+def circle_markers(cx: float, cy: float, R: float, n: int, phase: float = 0.0) -> np.ndarray:
+    th = phase + 2.0 * np.pi * np.arange(n) / n
+    return np.stack([cx + R * np.cos(th), cy + R * np.sin(th)], axis=1)
+
+
+def ellipse_markers(cx: float, cy: float, a: float, b: float, n: int,
+                    angle: float = 0.0) -> np.ndarray:
+    """n markers equally spaced in arc length on an ellipse (semi-axes a, b)."""
+    m = max(64 * n, 4096)
+    t = np.linspace(0.0, 2.0 * np.pi, m + 1)
+    px, py = a * np.cos(t), b * np.sin(t)
+    seg = np.hypot(np.diff(px), np.diff(py))
+    s = np.concatenate([[0.0], np.cumsum(seg)])
+    targets = s[-1] * np.arange(n) / n
+    tt = np.interp(targets, s, t)
+    x, y = a * np.cos(tt), b * np.sin(tt)
+    ca, sa = math.cos(angle), math.sin(angle)
+    return np.stack([cx + ca * x - sa * y, cy + sa * x + ca * y], axis=1)
+
+
+def polygon_perimeter(X: np.ndarray) -> float:
+    d = np.roll(X, -1, axis=0) - X
+    return float(np.hypot(d[:, 0], d[:, 1]).sum())
+
+
+def ramanujan_perimeter(a: float, b: float) -> float:
+    return math.pi * (3 * (a + b) - math.sqrt((3 * a + b) * (a + 3 * b)))
+
+
+def random_df(nx: int, ny: int, amp: float, seed: int) -> np.ndarray:
+    """Random shifted populations df[9, ny, nx] of amplitude amp (a perturbed state)."""
+    rng = np.random.default_rng(seed)
+    return amp * rng.standard_normal((9, ny, nx))
+
+
+def wobbly_polygon(cx: float, cy: float, R: float, n: int, amp: float, seed: int) -> np.ndarray:
+    """A star-shaped CCW polygon with random radial wobble (generic positions)."""
+    rng = np.random.default_rng(seed)
+    th = 2.0 * np.pi * (np.arange(n) + 0.3 * rng.uniform(-1, 1, n)) / n
+    th = np.sort(th)
+    r = R * (1.0 + amp * rng.uniform(-1, 1, n))
+    return np.stack([cx + r * np.cos(th), cy + r * np.sin(th)], axis=1)
+
+
+# ------------------------------------------------------------------ workloads
+def membrane_64():
+    """64x64 periodic SRT membrane: circle R=16 at the centre, 128 markers, linear
+    rest-length springs (stiffness 0.01, rest length 0.9 x the initial segment)."""
+    X = circle_markers(32.0, 32.0, 16.0, 128)
+    seg = 2 * 16.0 * math.sin(math.pi / 128)
+    return dict(name="membrane64_srt_f64", nx=64, ny=64, collision="srt", tau=0.8,
+                storage="f64", X=X, model="spring_rest", kappa=0.01, dX=seg, l0=0.9 * seg,
+                steps=2000)
+
+
+def ellipse_2048(storage: str = "f32"):
+    """2048^2 periodic MRT membrane: ellipse a=400, b=250 centred, 2048 markers equally
+    spaced in arc length, zero-rest-length springs (Eq. 19) of stiffness 0.05, tau 0.6."""
+    X = ellipse_markers(1024.0, 1024.0, 400.0, 250.0, 2048)
+    return dict(name=f"ellipse2048_mrt_{storage}", nx=2048, ny=2048, collision="mrt", tau=0.6,
+                storage=storage, X=X, model="spring", kappa=0.05,
+                dX=polygon_perimeter(X) / 2048, l0=0.0, steps=20000)
+
+
+def ellipse_scaled(n: int, storage: str = "f32", markers: int | None = None):
+    """The 2048^2 ellipse membrane scaled to an n x n lattice (same aspect, same tau)."""
+    s = n / 2048.0
+    nm = markers or max(32, int(round(2048 * s)))
+    X = ellipse_markers(n / 2.0, n / 2.0, 400.0 * s, 250.0 * s, nm)
+    return dict(name=f"ellipse{n}_mrt_{storage}", nx=n, ny=n, collision="mrt", tau=0.6,
+                storage=storage, X=X, model="spring", kappa=0.05,
+                dX=polygon_perimeter(X) / nm, l0=0.0)
+
+
+def cylinder_channel(re: float = 100.0, nx: int = 1024, ny: int = 256, D: float = 40.0,
+                     cx: float = 256.0, cy: float = 128.5, n: int = 126, u_max: float = 0.05):
+    """Rigid cylinder in a channel with a parabolic inflow; tau from Re = u_max D / nu."""
+    nu = u_max * D / re
+    tau = 0.5 + 3.0 * nu
+    X = circle_markers(cx, cy, D / 2.0, n)
+    return dict(name=f"cylinder{nx}x{ny}_re{re:g}", nx=nx, ny=ny, collision="mrt", tau=tau,
+                storage="f32", X=X, model="direct", u_max=u_max, D=D,
+                dX=polygon_perimeter(X) / n, steps=50000)
+
+
+def batched_membranes(count: int = 256, seed: int = 0):
+    """Independent membrane lattices of uneven size: n in {64..512}, ellipse aspect in
+    [1, 2.5], perimeter 0.6 n, one marker per 0.5 lattice unit, stiffness log-uniform
+    in [1e-3, 1e-1], tau uniform in [0.55, 1.0]."""
+    rng = np.random.default_rng(seed)
+    sizes = (64, 96, 128, 192, 256, 384, 512)
+    sims = []
+    for k in range(count):
+        n = int(sizes[rng.integers(len(sizes))])
+        asp = float(rng.uniform(1.0, 2.5))
+        kappa = float(10 ** rng.uniform(-3, -1))
+        tau = float(rng.uniform(0.55, 1.0))
+        per = 0.6 * n
+        b = per / ramanujan_perimeter(asp, 1.0)
+        a = asp * b
+        nm = int(round(per / 0.5))
+        X = ellipse_markers(n / 2.0, n / 2.0, a, b, nm)
+        sims.append(dict(nx=n, ny=n, tau=tau, kappa=kappa, X=X,
+                         dX=polygon_perimeter(X) / nm))
+    return sims

@@ -1,0 +1,305 @@
+"""Benchmark of the II-LBM time step on one GB300 (or N independent replicas).
+
+Workload (default): the 2048^2 periodic MRT membrane -- an ellipse with semi-axes 400
+and 250, 2048 markers equally spaced in arc length, zero-rest-length springs of
+stiffness 0.05, tau = 0.6, populations stored in FP32 as shifted deviations.  One
+"step" is one whole II-LBM time step (marker forces, cut-link jump, tangential
+spreading, interpolation and marker update, fused stream-collide), i.e. every row of
+the hot path.  Metric: MLUPS (million lattice-node updates per second), whole job.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2003_12186_gb300 import workloads as W  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
+    ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(size, storage):
+    return W.ellipse_2048(storage) if size == 2048 else W.ellipse_scaled(size, storage)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- cpu oracle
+def oracle_rate(size, max_seconds, min_steps=1):
+    """Time the FP64 CPU oracle (as it stands, one thread) on the workload."""
+    from oracle import oracle as O
+    w = workload(size, "f64")
+    o = O.Oracle(w["nx"], w["ny"], collision=O.MRT, tau=w["tau"], s=W.mrt_rates(w["tau"]))
+    o.set_interface(w["X"], model=O.SPRING, kappa=w["kappa"], dX=w["dX"])
+    steps, t0 = 0, time.perf_counter()
+    while steps < min_steps or time.perf_counter() - t0 < max_seconds:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    o.close()
+    return w["nx"] * w["ny"] * steps / dt / 1e6, steps, dt
+
+
+def run_reference(args):
+    """Reference arm: the oracle on the host cores, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    K, Wm = args.steps, args.warmup
+    probe, _, _ = oracle_rate(256, 0.5)
+    # largest lattice of the same workload family whose run fits about two minutes
+    size = 256
+    for n in (2048, 1024, 512, 256):
+        if n * n * (K + min(Wm, 3)) / (probe * 1e6) <= 120.0:
+            size = n
+            break
+    steps = K
+    if size == 256:
+        steps = max(1, min(K, int(120.0 * probe * 1e6 / (256 * 256))))
+    from oracle import oracle as O
+    w = workload(size, "f64")
+    o = O.Oracle(w["nx"], w["ny"], collision=O.MRT, tau=w["tau"], s=W.mrt_rates(w["tau"]))
+    o.set_interface(w["X"], model=O.SPRING, kappa=w["kappa"], dX=w["dX"])
+    o.step(min(Wm, 3))
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    value = w["nx"] * w["ny"] * steps / dt / 1e6
+    sample = (f"{steps} oracle steps of the ellipse membrane scaled to {size}^2 "
+              f"(same aspect, tau, stiffness, marker density), FP64, one thread")
+    out = {"metric": "MLUPS", "value": round(value, 4), "unit": "MLUPS", "n_gpus": args.gpus,
+           "steps": K, "warmup": Wm, "ms_per_step": round(dt / steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"ellipse{size}_mrt_membrane", "sample_of": "ellipse2048_mrt_f32",
+                      "lattice": [size, size], "markers": len(w["X"])},
+           "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+def make_lattice(iilbm, w, stream):
+    g = iilbm.Lattice(w["nx"], w["ny"], collision=iilbm.MRT, storage=w["storage"],
+                      tau=w["tau"], s=W.mrt_rates(w["tau"]), stream=stream)
+    return g
+
+
+def run_ours(args):
+    import torch
+    from paper_2003_12186_gb300 import iilbm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream().cuda_stream
+    w = workload(args.size, args.storage)
+    cells = w["nx"] * w["ny"]
+    sbytes = iilbm.STORAGE_BYTES[iilbm.STORAGE[args.storage]]
+    g = make_lattice(iilbm, w, stream)
+    g.set_interface(w["X"], model=iilbm.SPRING, stiffness=w["kappa"], dX=w["dX"])
+    g.step(args.warmup)
+    g.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier()
+    clocks.start()
+    g.iilbm_set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record()
+    g.step(args.steps)
+    e1.record()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    sc_ms, sc_n, launches = g.iilbm_get_timing()
+    g.iilbm_set_timing(False)
+    clk = clocks.stop()
+    g.synchronize()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = cells * args.steps * world / (ms * 1e-3) / 1e6
+    sc_avg_s = sc_ms / max(sc_n, 1) * 1e-3
+    alg_bytes = 2 * 9 * sbytes * cells
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / sc_avg_s / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "k_stream_collide", "peak_source": peak_kind,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_us": round(sc_avg_s * 1e6, 2)}
+    tr = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr):
+        d = json.load(open(tr)).get(f"ellipse{args.size}_{args.storage}")
+        if d:
+            roofline["traffic"] = d
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        del g
+        torch.cuda.synchronize()
+        g2 = make_lattice(iilbm, w, stream)
+        nm = len(w["X"])
+        Xin = torch.from_numpy(np.ascontiguousarray(w["X"])).pin_memory()
+        Xout = torch.empty((nm, 2), dtype=torch.float64).pin_memory()
+        ux = torch.empty((w["ny"], w["nx"]), dtype=torch.float64).pin_memory()
+        uy = torch.empty((w["ny"], w["nx"]), dtype=torch.float64).pin_memory()
+        K2 = args.steps
+        barrier()
+        t0 = time.perf_counter()
+        g2.set_interface(Xin, model=iilbm.SPRING, stiffness=w["kappa"], dX=w["dX"])
+        for _ in range(K2):
+            g2.step(1)
+            g2.iilbm_get_markers_into(X=Xout)
+        g2.get_macros(None, ux, uy, want=(False, True, True))
+        barrier()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = Xin.numel() * 8
+        d2h = K2 * Xout.numel() * 8 + 2 * cells * 8
+        e2e = {"value": round(cells * K2 * world / dt / 1e6, 1), "unit": "MLUPS",
+               "h2d_bytes_per_step": round(h2d / K2, 1), "d2h_bytes_per_step": round(d2h / K2, 1),
+               "note": "set_interface from pinned host, per step iilbm_step(1) + marker "
+                       "read-back to pinned host, final velocity field read-back"}
+        del g2
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, st, dt = oracle_rate(args.size, 12.0)
+        cpu = {"value": round(rate, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{st} FP64 oracle steps of the same {args.size}^2 workload, "
+                         f"{dt:.1f} s, one thread"}
+    if rank == 0:
+        out = {"metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+               "data": "synthetic",
+               "config": {"workload": w["name"].replace(f"_{args.storage}", "") + "_membrane",
+                          "lattice": [w["nx"], w["ny"]], "markers": len(w["X"]),
+                          "collision": "mrt", "tau": w["tau"], "storage": args.storage,
+                          "arithmetic": "f64" if args.storage == "f64" else "f32",
+                          "parallelism": "replicas" if world > 1 else "single",
+                          "l2": f"inputs larger than L2 ({9 * sbytes * cells / 2**20:.0f} MiB "
+                                f"populations vs 129 MiB L2)" if 9 * sbytes * cells > L2_BYTES
+                          else "working set fits L2"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+               "gpu_launches": launches}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,153 @@
+/*
+ * iilbm.h -- C ABI of the GB300 (sm_103a) immersed interface–lattice Boltzmann
+ * time step (II-LBM; Qin, Kolahdouz & Griffith, arXiv 2003.12186).
+ *
+ * One handle = one D2Q9 lattice, its populations, and at most one immersed
+ * interface (a closed, counter-clockwise marker polygon).  All device memory is
+ * allocated and owned by the library; every call is asynchronous on the handle's
+ * CUDA stream unless stated otherwise.  Pointers marked "host or device" are
+ * classified with cudaPointerGetAttributes and copied with cudaMemcpyAsync.
+ *
+ * Error behaviour: every entry point returns IILBM_OK (0) or a negative
+ * iilbm_status.  Argument errors are detected on the host before any work is
+ * queued and leave the handle unchanged.  Device-side faults of the method
+ * (non-finite populations, a marker polygon that leaves its valid region, a
+ * cut-link list beyond capacity) are latched in a device status word and
+ * returned by the next call that synchronises (iilbm_get_*, iilbm_synchronize).
+ *
+ * Paper citations give the section / equation that defines each operation.
+ */
+#ifndef IILBM_H
+#define IILBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct iilbm_lattice *iilbm_t;
+
+typedef enum {
+  IILBM_OK = 0,
+  IILBM_ERR_INVALID_ARG = -1,   /* bad size, rate, enum or NULL where required */
+  IILBM_ERR_OOM = -2,           /* device allocation failed */
+  IILBM_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  IILBM_ERR_DEVICE_TIMEOUT = -4,/* a bounded device wait gave up */
+  IILBM_ERR_NONFINITE = -5,     /* a NaN / Inf appeared in the populations */
+  IILBM_ERR_INTERFACE = -6,     /* marker polygon invalid (segment too long, outside region) */
+  IILBM_ERR_CAPACITY = -7,      /* cut-link list overflow */
+  IILBM_ERR_NO_DEVICE = -8      /* no CUDA device, or not a compute capability 10.3 device */
+} iilbm_status;
+
+enum { IILBM_SRT = 0, IILBM_MRT = 1 };
+/* Storage precision of the shifted populations df_i = f_i - w_i rho0.  Arithmetic
+ * is FP64 for IILBM_F64 and FP32 for the others. */
+enum { IILBM_F64 = 0, IILBM_F32 = 1, IILBM_F16 = 2, IILBM_BF16 = 3 };
+/* Boundaries: periodic box; walls at y = -1/2, ny - 1/2 (halfway bounce-back) and
+ * periodic x; channel = walls plus parabolic inflow at x = 0 and outflow at nx - 1. */
+enum { IILBM_BC_PERIODIC = 0, IILBM_BC_WALLS_Y = 1, IILBM_BC_CHANNEL = 2 };
+/* Lagrangian force models: Eq. 19 spring; rest-length spring; a prescribed force;
+ * direct forcing Eq. 18 (iterated). */
+enum { IILBM_SPRING = 0, IILBM_SPRING_REST = 1, IILBM_PRESCRIBED = 2, IILBM_DIRECT = 3 };
+
+typedef struct {
+  int32_t nx, ny;       /* lattice nodes; node (i, j) sits at coordinate (i, j); 4 <= n <= 32768 */
+  int32_t collision;    /* IILBM_SRT (Eq. 14 + Eq. 21) or IILBM_MRT (Eq. 15 + Eq. 22) */
+  int32_t storage;      /* IILBM_F64 / F32 / F16 / BF16 */
+  int32_t bc;           /* IILBM_BC_* */
+  int32_t jump;         /* 1: II-LBM (normal force through the jump of Eq. 32, tangential
+                           part spread, Eq. 46); 0: IB-LBM with Guo forcing (whole G spread) */
+  int32_t storage_scale_log2; /* stored value = df * 2^k (exact); 0 for F32/F64 */
+  int32_t reserved;
+  double tau;           /* relaxation time lambda, nu = c_s^2 (lambda - 1/2) (Eq. 7); > 0.5 */
+  double s[9];          /* MRT rates in the Lallemand-Luo moment order
+                           (rho, e, eps, jx, qx, jy, qy, pxx, pxy) */
+  double rho0;          /* reference density of the shifted storage */
+  double u_max;         /* channel centre-line inflow speed */
+  double body[2];       /* uniform body force density added to g */
+  void *stream;         /* cudaStream_t to run on; NULL: the library creates one */
+} iilbm_config;
+
+typedef struct {
+  int32_t model;        /* IILBM_SPRING / SPRING_REST / PRESCRIBED / DIRECT */
+  int32_t moves;        /* 1: markers advected, X += U (Eq. 20); 0: fixed */
+  double stiffness;     /* kappa of Eq. 19 (or of the rest-length spring) */
+  double dX;            /* Lagrangian spacing Delta X (Eq. 17) */
+  double rest_length;   /* l0 of the rest-length spring */
+  double eta;           /* direct-forcing gain of Eq. 18 */
+  int32_t mdf_iters;    /* direct forcing: maximum passes */
+  int32_t reserved;
+  double mdf_tol;       /* direct forcing: stop when max_k |U^D - U_k| < tol (0: all passes) */
+} iilbm_interface_params;
+
+/* Create a lattice (section 2.2.1: D2Q9, Eq. 9 weights), populations at rest
+ * (df = 0).  cfg is copied; *out receives the handle.  Allocates all device memory
+ * of the lattice.  Errors: INVALID_ARG, OOM, CUDA, NO_DEVICE. */
+int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg);
+
+/* Release the handle and all its device memory (synchronises its stream). */
+int iilbm_destroy(iilbm_t h);
+
+/* Install (replace) the immersed interface: n markers, xy[n][2] FP64, closed and
+ * counter-clockwise (host or device).  aux[n][2] is the prescribed force G
+ * (PRESCRIBED) or the desired velocity U^D (DIRECT), else ignored (may be NULL).
+ * The markers are copied; the caller keeps ownership.  Every segment must be
+ * shorter than 16 lattice units and every marker at least 3 nodes from a
+ * non-periodic edge.  n = 0 removes the interface.  Sections 2.2.2 (Eqs. 17-20)
+ * and 3 (Eqs. 31-32, 46-47).  Errors: INVALID_ARG, INTERFACE, OOM, CUDA. */
+int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n,
+                        const iilbm_interface_params *p, const double *aux);
+
+/* Set the state to the equilibrium (Eq. 23) of rho(x), u(x) ([ny][nx] FP64 each,
+ * host or device; NULL means rho0 / zero). */
+int iilbm_init_equilibrium(iilbm_t h, const double *rho, const double *ux, const double *uy);
+
+/* Set / read the state: df[9][ny][nx] FP64 shifted populations f_i - w_i rho0 in
+ * natural (pull) layout, host or device, streamed populations without the jump of
+ * the current interface.  Converted to / from the storage precision. */
+int iilbm_set_populations(iilbm_t h, const double *df);
+int iilbm_get_populations(iilbm_t h, double *df);
+
+/* Advance n >= 0 time steps of section 3.2 (Eq. 47 with Eqs. 17-24): Lagrangian
+ * force, normal split, jump on cut links, tangential spreading, interpolation,
+ * fused stream-collide, marker update.  Asynchronous. */
+int iilbm_step(iilbm_t h, int32_t n);
+
+/* Macroscopic fields of the current state ([ny][nx] FP64 each, host or device,
+ * any may be NULL): drho = rho - rho0 (Eq. 11 less rho0) and u of Eq. 24, computed
+ * from the populations plus the current interface's jump and force -- the values
+ * the next collision will use.  Synchronises. */
+int iilbm_get_macros(iilbm_t h, double *drho, double *ux, double *uy);
+
+/* Markers (each [n][2] FP64 except Fn [n]; host or device; any may be NULL):
+ * current positions X, the most recent Lagrangian force G and jump strength
+ * Fn = G.n/|X_s| (Eq. 32), and the velocity U interpolated in the most recent step
+ * (Eq. 20).  Synchronises. */
+int iilbm_get_markers(iilbm_t h, double *X, double *G, double *U, double *Fn);
+
+/* Direct forcing: passes of the most recent step and its final residual. */
+int iilbm_get_mdf_stats(iilbm_t h, int32_t *iters, double *residual);
+
+/* Number of cut-link crossings of the most recent interface phase (Eq. 47). */
+int iilbm_get_cut_link_count(iilbm_t h, int32_t *count);
+
+/* Kernel timing (diagnostic).  enable = 1 starts recording a CUDA event pair around
+ * every stream-collide launch on the handle's stream and counting every kernel the
+ * library launches; enable = 0 stops.  iilbm_get_timing synchronises, returns the
+ * summed stream-collide device time (ms), its launch count and the number of
+ * library kernels launched since timing was enabled, then resets all three. */
+int iilbm_set_timing(iilbm_t h, int32_t enable);
+int iilbm_get_timing(iilbm_t h, double *stream_collide_ms, int32_t *stream_collide_launches,
+                     int64_t *kernel_launches);
+
+/* Wait for the handle's stream and return any latched device status. */
+int iilbm_synchronize(iilbm_t h);
+
+/* Static description of a status code. */
+const char *iilbm_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IILBM_H */

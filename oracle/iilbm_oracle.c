@@ -87,6 +87,7 @@ typedef struct {
   double *U;       /* [n][2] interpolated marker velocity */
   int mdf_last_iters;
   double mdf_last_res;
+  int ncut;        /* cut-link crossings of the most recent prepare */
   long step;
 } orc_state;
 
@@ -610,6 +611,8 @@ static void direct_forcing(orc_state *S, const double *dfs) {
 }
 
 /* One II-LBM time step, t -> t+1 (section 3.2, Eq. 47, with Eqs. 17-24).
+ * orc_prepare does items 1-4 (a pure function of the state and the markers),
+ * orc_advance items 5-6.
  *  1. Lagrangian force G_k from X^t (Eq. 19, its rest-length variant, a
  *     prescribed force, or direct forcing Eq. 18).
  *  2. Split: Fn_k (jump strength, Eq. 32), Gpar_k (Eq. 46).
@@ -619,11 +622,12 @@ static void direct_forcing(orc_state *S, const double *dfs) {
  *  4. rho, u from f and g (Eqs. 11, 24); U_k = interp(u) (Eq. 20).
  *  5. Collide every cell (Eqs. 14/15 with 21/22), stream (Eq. 47), boundaries.
  *  6. X^{t+1} = X^t + U_k for a membrane (Eq. 20). */
-int orc_step(orc_state *S) {
+int orc_prepare(orc_state *S) {
   const orc_cfg *c = &S->c;
-  int nx = c->nx, ny = c->ny, N = nx * ny;
+  int N = c->nx * c->ny;
   memcpy(S->f, S->df, 9 * (size_t)N * sizeof(double));
   for (int p = 0; p < N; p++) { S->gx[p] = c->body_x; S->gy[p] = c->body_y; }
+  S->ncut = 0;
   if (S->has_iface) {
     orc_iface *I = &S->I;
     int n = I->n;
@@ -639,6 +643,7 @@ int orc_step(orc_state *S) {
       int m = orc_cut_links(c, I->X, n, S->Fn, cell, dir, coef, cap);
       if (m < 0) { free(cell); free(dir); free(coef); free(P); return -1; }
       for (int r = 0; r < m; r++) S->f[dir[r] * N + cell[r]] += coef[r];
+      S->ncut = m;
       free(cell); free(dir); free(coef);
       for (int k = 0; k < 2 * n; k++) P[k] = S->Gpar[k] * I->dX;
     } else {
@@ -653,6 +658,12 @@ int orc_step(orc_state *S) {
     orc_cell_macros(dfc, c->rho0, S->gx[p], S->gy[p], &S->rho[p], &S->ux[p], &S->uy[p]);
   }
   if (S->has_iface) orc_interp(c, S->I.X, S->I.n, S->ux, S->uy, S->U);
+  return 0;
+}
+
+void orc_advance(orc_state *S) {
+  const orc_cfg *c = &S->c;
+  int N = c->nx * c->ny;
   for (int p = 0; p < N; p++) {
     double dfc[9], out[9];
     for (int i = 0; i < 9; i++) dfc[i] = S->f[i * N + p];
@@ -664,8 +675,15 @@ int orc_step(orc_state *S) {
   if (S->has_iface && S->I.moves)
     for (int k = 0; k < 2 * S->I.n; k++) S->I.X[k] += S->U[k];
   S->step++;
+}
+
+int orc_step(orc_state *S) {
+  if (orc_prepare(S)) return -1;
+  orc_advance(S);
   return 0;
 }
+
+int orc_cut_link_count(const orc_state *S) { return S->ncut; }
 
 int orc_run(orc_state *S, int nsteps) {
   for (int s = 0; s < nsteps; s++)

@@ -70,6 +70,8 @@ def lib():
                                             C.c_double, C.c_double, C.c_double, C.c_int,
                                             C.c_double, _D, _D]
             L.orc_step.argtypes = [C.c_void_p]
+            L.orc_prepare.argtypes = [C.c_void_p]
+            L.orc_cut_link_count.argtypes = [C.c_void_p]
             L.orc_run.argtypes = [C.c_void_p, C.c_int]
             L.orc_get_step_macros.argtypes = [C.c_void_p, _D, _D, _D]
             L.orc_get_markers.argtypes = [C.c_void_p, _D, _D, _D, _D]
@@ -280,6 +282,16 @@ class Oracle:
         if not deviation:
             r = r + self.cfg.rho0
         return r.reshape(s), ux.reshape(s), uy.reshape(s)
+
+    def current_macros(self, deviation=True):
+        """drho (or rho), ux, uy of the current state: what the next collision uses
+        (items 1-4 of the step, without advancing)."""
+        if lib().orc_prepare(self._h) != 0:
+            raise RuntimeError("oracle prepare failed (cut-link capacity)")
+        return self.step_macros(deviation=deviation)
+
+    def cut_link_count(self):
+        return lib().orc_cut_link_count(self._h)
 
     def markers(self):
         n = self.n_markers

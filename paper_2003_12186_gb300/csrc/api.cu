@@ -1,0 +1,398 @@
+// api.cu -- the C ABI of include/iilbm.h: handle life cycle, argument checking,
+// memory ownership, and the order of the kernels of one II-LBM time step.
+#include "iilbm_internal.cuh"
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+using namespace iilbm;
+
+namespace {
+
+#define CK(call)                                   \
+  do {                                             \
+    if ((call) != cudaSuccess) return IILBM_ERR_CUDA; \
+  } while (0)
+
+size_t storage_bytes(int s) {
+  switch (s) {
+    case IILBM_F64: return 8;
+    case IILBM_F32: return 4;
+    case IILBM_F16: return 2;
+    case IILBM_BF16: return 2;
+  }
+  return 0;
+}
+
+// Copy n bytes from a host or device pointer to device memory on the stream.
+int copy_in(void *dst, const void *src, size_t n, cudaStream_t s) {
+  CK(cudaMemcpyAsync(dst, src, n, cudaMemcpyDefault, s));
+  return IILBM_OK;
+}
+
+int read_status(iilbm_lattice *h) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (st & ST_NONFINITE) return IILBM_ERR_NONFINITE;
+  if (st & ST_INTERFACE) return IILBM_ERR_INTERFACE;
+  if (st & ST_CAPACITY) return IILBM_ERR_CAPACITY;
+  if (st & ST_TIMEOUT) return IILBM_ERR_DEVICE_TIMEOUT;
+  return IILBM_OK;
+}
+
+void free_interface(iilbm_lattice *h) {
+  double **bufs[] = {&h->X, &h->aux, &h->G, &h->Fn, &h->P, &h->U, &h->nrm};
+  for (double **b : bufs) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
+  h->nm = 0;
+}
+
+// Bring J, g, flags to the current state's interface (idempotent per state).
+int prepare(iilbm_lattice *h) {
+  if (h->prepared) return IILBM_OK;
+  int rc = launch_interface_phase(h);
+  if (rc) return rc;
+  h->prepared = true;
+  return IILBM_OK;
+}
+
+// Clear any jump / force left in J, g (used when the interface or state is replaced
+// outside the step sequence).
+int clear_fields(iilbm_lattice *h) {
+  const Geom &g = h->geom;
+  CK(cudaMemsetAsync(h->J, 0, 8 * (size_t)g.plane * h->tbytes, h->stream));
+  CK(cudaMemsetAsync(h->g, 0, 2 * (size_t)g.plane * h->tbytes, h->stream));
+  CK(cudaMemsetAsync(h->flags, 0, (size_t)h->ntiles, h->stream));
+  h->prepared = false;
+  return IILBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *iilbm_error_string(int status) {
+  switch (status) {
+    case IILBM_OK: return "ok";
+    case IILBM_ERR_INVALID_ARG: return "invalid argument";
+    case IILBM_ERR_OOM: return "device allocation failed";
+    case IILBM_ERR_CUDA: return "CUDA runtime error";
+    case IILBM_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
+    case IILBM_ERR_NONFINITE: return "non-finite population";
+    case IILBM_ERR_INTERFACE: return "invalid marker polygon";
+    case IILBM_ERR_CAPACITY: return "cut-link capacity exceeded";
+    case IILBM_ERR_NO_DEVICE: return "no compute capability 10.3 CUDA device";
+  }
+  return "unknown status";
+}
+
+int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
+  if (!out || !cfg) return IILBM_ERR_INVALID_ARG;
+  *out = nullptr;
+  const iilbm_config &c = *cfg;
+  if (c.nx < 4 || c.ny < 4 || c.nx > 32768 || c.ny > 32768) return IILBM_ERR_INVALID_ARG;
+  if (c.collision != IILBM_SRT && c.collision != IILBM_MRT) return IILBM_ERR_INVALID_ARG;
+  if (!storage_bytes(c.storage)) return IILBM_ERR_INVALID_ARG;
+  if (c.bc != IILBM_BC_PERIODIC && c.bc != IILBM_BC_WALLS_Y) return IILBM_ERR_INVALID_ARG;
+  if (!(c.tau > 0.5) || !(c.rho0 > 0) || std::abs(c.storage_scale_log2) > 30)
+    return IILBM_ERR_INVALID_ARG;
+  if (c.collision == IILBM_MRT)
+    for (int i = 0; i < 9; i++)
+      if (!(c.s[i] >= 0.0 && c.s[i] < 2.0)) return IILBM_ERR_INVALID_ARG;
+  int dev = 0, ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return IILBM_ERR_NO_DEVICE;
+  }
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  if (prop.major != 10 || prop.minor != 3) return IILBM_ERR_NO_DEVICE;
+
+  iilbm_lattice *h = new (std::nothrow) iilbm_lattice();
+  if (!h) return IILBM_ERR_OOM;
+  h->cfg = c;
+  h->device = dev;
+  Geom &g = h->geom;
+  g.nx = c.nx;
+  g.ny = c.ny;
+  g.pitch = (c.nx + 31) / 32 * 32;
+  g.plane = (long long)g.pitch * c.ny;
+  g.ntx = (c.nx + TILE_X - 1) / TILE_X;
+  g.bc = c.bc;
+  h->ntiles = g.ntx * ((c.ny + TILE_Y - 1) / TILE_Y);
+  h->sbytes = storage_bytes(c.storage);
+  h->tbytes = c.storage == IILBM_F64 ? 8 : 4;
+  if (c.stream) {
+    h->stream = (cudaStream_t)c.stream;
+    h->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return IILBM_ERR_CUDA;
+    }
+    h->own_stream = true;
+  }
+  bool ok = cudaMalloc(&h->A, 9 * (size_t)g.plane * h->sbytes) == cudaSuccess &&
+            cudaMalloc(&h->J, 8 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
+            cudaMalloc(&h->g, 2 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
+            cudaMalloc(&h->flags, (size_t)h->ntiles) == cudaSuccess &&
+            cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->d_ncut, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    iilbm_destroy(h);
+    return IILBM_ERR_OOM;
+  }
+  int rc = IILBM_OK;
+  if (cudaMemsetAsync(h->A, 0, 9 * (size_t)g.plane * h->sbytes, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->d_ncut, 0, sizeof(int), h->stream) != cudaSuccess)
+    rc = IILBM_ERR_CUDA;
+  if (!rc) rc = clear_fields(h);
+  if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = IILBM_ERR_CUDA;
+  if (rc) {
+    iilbm_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return IILBM_OK;
+}
+
+int iilbm_destroy(iilbm_t h) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_interface(h);
+  void *bufs[] = {h->A, h->J, h->g, h->flags, h->d_status, h->d_ncut};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  if (h->ev[0])
+    for (int e = 0; e < 2 * 256; e++) cudaEventDestroy(h->ev[e]);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return IILBM_OK;
+}
+
+int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_interface_params *p,
+                        const double *aux) {
+  if (!h || n < 0 || (n > 0 && (!xy || !p))) return IILBM_ERR_INVALID_ARG;
+  if (n > 0 && n < 3) return IILBM_ERR_INVALID_ARG;
+  if (n > 0) {
+    if (p->model < IILBM_SPRING || p->model > IILBM_DIRECT) return IILBM_ERR_INVALID_ARG;
+    if (p->model == IILBM_DIRECT) return IILBM_ERR_INVALID_ARG;  // not built yet
+    if (!(p->dX > 0) || !std::isfinite(p->stiffness)) return IILBM_ERR_INVALID_ARG;
+    if (p->model == IILBM_SPRING_REST && !(p->rest_length > 0)) return IILBM_ERR_INVALID_ARG;
+    if ((p->model == IILBM_PRESCRIBED || p->model == IILBM_DIRECT) && !aux)
+      return IILBM_ERR_INVALID_ARG;
+  }
+  int rc = clear_fields(h);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  free_interface(h);
+  if (n == 0) return IILBM_OK;
+  const size_t b2 = 2 * (size_t)n * sizeof(double);
+  bool ok = cudaMalloc(&h->X, b2) == cudaSuccess && cudaMalloc(&h->aux, b2) == cudaSuccess &&
+            cudaMalloc(&h->G, b2) == cudaSuccess &&
+            cudaMalloc(&h->Fn, (size_t)n * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&h->P, b2) == cudaSuccess && cudaMalloc(&h->U, b2) == cudaSuccess &&
+            cudaMalloc(&h->nrm, b2) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_interface(h);
+    return IILBM_ERR_OOM;
+  }
+  h->nm = n;
+  h->ip = *p;
+  if ((rc = copy_in(h->X, xy, b2, h->stream))) return rc;
+  if (aux) {
+    if ((rc = copy_in(h->aux, aux, b2, h->stream))) return rc;
+  } else {
+    CK(cudaMemsetAsync(h->aux, 0, b2, h->stream));
+  }
+  CK(cudaMemsetAsync(h->U, 0, b2, h->stream));
+  CK(cudaMemsetAsync(h->G, 0, b2, h->stream));
+  CK(cudaMemsetAsync(h->Fn, 0, (size_t)n * sizeof(double), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  // host-side validation of the polygon (the kernels re-check every step)
+  double *hx = (double *)std::malloc(b2);
+  if (!hx) return IILBM_ERR_OOM;
+  CK(cudaMemcpy(hx, h->X, b2, cudaMemcpyDeviceToHost));
+  bool bad = false;
+  for (int k = 0; k < n && !bad; k++) {
+    const int kp = (k + 1) % n;
+    const double x = hx[2 * k], y = hx[2 * k + 1];
+    const double dx = hx[2 * kp] - x, dy = hx[2 * kp + 1] - y;
+    bad = !std::isfinite(x) || !std::isfinite(y) || std::abs(x) > MAX_COORD ||
+          std::abs(y) > MAX_COORD || !(dx * dx + dy * dy < MAX_SEGMENT * MAX_SEGMENT) ||
+          (dx == 0 && dy == 0);
+    if (h->cfg.bc != IILBM_BC_PERIODIC) bad = bad || y < 3.0 || y > h->cfg.ny - 4.0;
+  }
+  std::free(hx);
+  if (bad) {
+    free_interface(h);
+    return IILBM_ERR_INTERFACE;
+  }
+  return IILBM_OK;
+}
+
+int iilbm_init_equilibrium(iilbm_t h, const double *rho, const double *ux, const double *uy) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  const size_t N = (size_t)h->cfg.nx * h->cfg.ny;
+  const double *src[3] = {rho, ux, uy};
+  double *dev[3] = {nullptr, nullptr, nullptr};
+  int rc = IILBM_OK;
+  for (int a = 0; a < 3 && !rc; a++)
+    if (src[a]) {
+      if (cudaMalloc(&dev[a], N * sizeof(double)) != cudaSuccess) rc = IILBM_ERR_OOM;
+      else rc = copy_in(dev[a], src[a], N * sizeof(double), h->stream);
+    }
+  if (!rc) rc = clear_fields(h);
+  if (!rc) rc = launch_set_populations(h, nullptr, true, dev[0], dev[1], dev[2]);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess && !rc) rc = IILBM_ERR_CUDA;
+  for (double *d : dev)
+    if (d) cudaFree(d);
+  return rc;
+}
+
+int iilbm_set_populations(iilbm_t h, const double *df) {
+  if (!h || !df) return IILBM_ERR_INVALID_ARG;
+  const size_t bytes = 9 * (size_t)h->cfg.nx * h->cfg.ny * sizeof(double);
+  double *d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) return IILBM_ERR_OOM;
+  int rc = copy_in(d, df, bytes, h->stream);
+  if (!rc) rc = clear_fields(h);
+  if (!rc) rc = launch_set_populations(h, d, false, nullptr, nullptr, nullptr);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess && !rc) rc = IILBM_ERR_CUDA;
+  cudaFree(d);
+  return rc;
+}
+
+int iilbm_get_populations(iilbm_t h, double *df) {
+  if (!h || !df) return IILBM_ERR_INVALID_ARG;
+  const size_t bytes = 9 * (size_t)h->cfg.nx * h->cfg.ny * sizeof(double);
+  double *d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) return IILBM_ERR_OOM;
+  int rc = launch_get_populations(h, d);
+  if (!rc && cudaMemcpyAsync(df, d, bytes, cudaMemcpyDefault, h->stream) != cudaSuccess)
+    rc = IILBM_ERR_CUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess && !rc) rc = IILBM_ERR_CUDA;
+  cudaFree(d);
+  return rc ? rc : read_status(h);
+}
+
+// Fold the recorded stream-collide event pairs into the running sum.
+int drain_events(iilbm_lattice *h) {
+  if (h->nev == 0) return IILBM_OK;
+  CK(cudaEventSynchronize(h->ev[2 * h->nev - 1]));
+  for (int e = 0; e < h->nev; e++) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, h->ev[2 * e], h->ev[2 * e + 1]));
+    h->sc_ms += ms;
+  }
+  h->nev = 0;
+  return IILBM_OK;
+}
+
+// Kernels launched by one step: interface phase (forces, cut links if the jump is
+// on, spread) when an interface exists, interpolation, stream-collide.
+long long kernels_per_step(const iilbm_lattice *h) {
+  return 1 + (h->nm > 0 ? 2 + (h->cfg.jump ? 1 : 0) + 1 : 0);
+}
+
+int iilbm_step(iilbm_t h, int32_t n) {
+  if (!h || n < 0) return IILBM_ERR_INVALID_ARG;
+  for (int s = 0; s < n; s++) {
+    int rc = prepare(h);
+    if (rc) return rc;
+    if ((rc = launch_interp(h))) return rc;
+    if (h->timing) {
+      if (h->nev == 256 && (rc = drain_events(h))) return rc;
+      CK(cudaEventRecord(h->ev[2 * h->nev], h->stream));
+    }
+    if ((rc = launch_stream_collide(h))) return rc;
+    if (h->timing) {
+      CK(cudaEventRecord(h->ev[2 * h->nev + 1], h->stream));
+      h->nev++;
+      h->sc_launches++;
+      h->kernel_launches += kernels_per_step(h);
+    }
+    h->step++;
+    h->prepared = false;
+  }
+  return IILBM_OK;
+}
+
+int iilbm_set_timing(iilbm_t h, int32_t enable) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  if (enable && !h->ev[0])
+    for (int e = 0; e < 2 * 256; e++) CK(cudaEventCreate(&h->ev[e]));
+  h->timing = enable != 0;
+  return IILBM_OK;
+}
+
+int iilbm_get_timing(iilbm_t h, double *sc_ms, int32_t *launches, int64_t *kernel_launches) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  int rc = drain_events(h);
+  if (rc) return rc;
+  if (sc_ms) *sc_ms = h->sc_ms;
+  if (launches) *launches = h->sc_launches;
+  if (kernel_launches) *kernel_launches = h->kernel_launches;
+  h->sc_ms = 0;
+  h->sc_launches = 0;
+  h->kernel_launches = 0;
+  return read_status(h);
+}
+
+int iilbm_get_macros(iilbm_t h, double *drho, double *ux, double *uy) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  int rc = prepare(h);
+  if (rc) return rc;
+  const size_t bytes = (size_t)h->cfg.nx * h->cfg.ny * sizeof(double);
+  double *d = nullptr;
+  if (cudaMalloc(&d, 3 * bytes) != cudaSuccess) return IILBM_ERR_OOM;
+  rc = launch_macros(h, d, d + bytes / 8, d + 2 * bytes / 8);
+  double *outs[3] = {drho, ux, uy};
+  for (int a = 0; a < 3 && !rc; a++)
+    if (outs[a] && cudaMemcpyAsync(outs[a], d + a * (bytes / 8), bytes, cudaMemcpyDefault,
+                                   h->stream) != cudaSuccess)
+      rc = IILBM_ERR_CUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess && !rc) rc = IILBM_ERR_CUDA;
+  cudaFree(d);
+  return rc ? rc : read_status(h);
+}
+
+int iilbm_get_markers(iilbm_t h, double *X, double *G, double *U, double *Fn) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  if (h->nm == 0) return read_status(h);
+  const size_t b2 = 2 * (size_t)h->nm * sizeof(double);
+  if (X) CK(cudaMemcpyAsync(X, h->X, b2, cudaMemcpyDefault, h->stream));
+  if (G) CK(cudaMemcpyAsync(G, h->G, b2, cudaMemcpyDefault, h->stream));
+  if (U) CK(cudaMemcpyAsync(U, h->U, b2, cudaMemcpyDefault, h->stream));
+  if (Fn) CK(cudaMemcpyAsync(Fn, h->Fn, b2 / 2, cudaMemcpyDefault, h->stream));
+  return read_status(h);
+}
+
+int iilbm_get_mdf_stats(iilbm_t h, int32_t *iters, double *residual) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  if (iters) *iters = h->mdf_iters_last;
+  if (residual) *residual = h->mdf_res_last;
+  return IILBM_OK;
+}
+
+int iilbm_get_cut_link_count(iilbm_t h, int32_t *count) {
+  if (!h || !count) return IILBM_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(count, h->d_ncut, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  return read_status(h);
+}
+
+int iilbm_synchronize(iilbm_t h) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  return read_status(h);
+}
+
+}  // extern "C"

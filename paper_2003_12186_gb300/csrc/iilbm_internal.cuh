@@ -1,0 +1,151 @@
+// iilbm_internal.cuh -- device-side building blocks shared by the CUDA translation
+// units of the II-LBM library (lattice constants, storage conversions, handle).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/iilbm.h"
+
+namespace iilbm {
+
+// ---------------------------------------------------------------- D2Q9 lattice
+// Velocity set of section 2.2.1 in the order 0 rest, 1 E, 2 N, 3 W, 4 S, 5 NE,
+// 6 NW, 7 SW, 8 SE; weights of Eq. 9.
+__host__ __device__ constexpr int cx(int i) {
+  return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i) {
+  return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+  return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 5 + 2) & 3) + 5);
+}
+template <typename T>
+__host__ __device__ constexpr T wt(int i) {
+  return i == 0 ? T(4) / T(9) : (i <= 4 ? T(1) / T(9) : T(1) / T(36));
+}
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "opp axis");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp diag");
+
+// Force / jump tiles: the stream-collide kernel's thread block covers one tile of
+// TILE_X x TILE_Y nodes; a per-tile byte flags tiles that carry a jump or a force.
+constexpr int TILE_X = 32;
+constexpr int TILE_Y = 8;
+
+// Device status bits (latched, read back by synchronising calls).
+constexpr int ST_NONFINITE = 1;
+constexpr int ST_INTERFACE = 2;
+constexpr int ST_CAPACITY = 4;
+constexpr int ST_TIMEOUT = 8;
+
+// Marker coordinates are snapped to multiples of 2^-24 lattice units for the exact
+// integer crossing predicate of the cut links.
+constexpr double QSCALE = 16777216.0;
+constexpr double MAX_SEGMENT = 16.0;
+constexpr double MAX_COORD = 16000.0;
+
+// ------------------------------------------------------------ storage types
+// Populations are stored as df * 2^k in S and computed in T (double for FP64
+// storage, float otherwise).
+template <typename S> struct Store;
+template <> struct Store<double> {
+  using T = double;
+  __device__ static double ld(double v) { return v; }
+  __device__ static double st(double v) { return v; }
+};
+template <> struct Store<float> {
+  using T = float;
+  __device__ static float ld(float v) { return v; }
+  __device__ static float st(float v) { return v; }
+};
+template <> struct Store<__half> {
+  using T = float;
+  __device__ static float ld(__half v) { return __half2float(v); }
+  __device__ static __half st(float v) { return __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+  using T = float;
+  __device__ static float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ static __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+};
+
+// Geometry of one lattice as the kernels see it.
+struct Geom {
+  int nx, ny;
+  int pitch;        // row stride in elements (nx rounded up to 32)
+  long long plane;  // pitch * ny
+  int ntx;          // tiles per row
+  int bc;           // IILBM_BC_*
+};
+
+__host__ __device__ inline int wrap(int v, int n) {
+  v = v % n;
+  return v < 0 ? v + n : v;
+}
+
+// Location (plane index, cell index) of the population f_i(x, y) of the current
+// state in the AA layout.  Even state: slot i at the node itself.  Odd state: slot
+// opp(i) at the upstream node (x - e_i), wrapped on periodic axes; a population
+// that arrives through a y wall (halfway bounce-back) sits in slot i of the node.
+__device__ inline long long aa_loc(const Geom &g, bool odd, int i, int x, int y) {
+  if (!odd) return (long long)i * g.plane + (long long)y * g.pitch + x;
+  int sx = x - cx(i), sy = y - cy(i);
+  if (g.bc == IILBM_BC_PERIODIC) {
+    sy = wrap(sy, g.ny);
+  } else if (sy < 0 || sy >= g.ny) {
+    return (long long)i * g.plane + (long long)y * g.pitch + x;
+  }
+  sx = wrap(sx, g.nx);
+  return (long long)opp(i) * g.plane + (long long)sy * g.pitch + sx;
+}
+
+}  // namespace iilbm
+
+// ------------------------------------------------------------------ handle
+struct iilbm_lattice {
+  iilbm_config cfg;
+  iilbm::Geom geom;
+  int device;
+  cudaStream_t stream;
+  bool own_stream;
+  size_t sbytes;      // bytes per stored population
+  size_t tbytes;      // bytes per arithmetic value (jump, force)
+  void *A;            // [9][plane] populations, storage type
+  void *J;            // [8][plane] jump of the current interface, arithmetic type
+  void *g;            // [2][plane] spread force of the current interface
+  uint8_t *flags;     // [ntiles]
+  int ntiles;
+  long long step;     // time level of the state; AA parity = step & 1
+  bool prepared;      // jump / force of the current state already in J, g
+  int *d_status;      // latched device status bits
+  int *d_ncut;        // crossings of the latest interface phase
+  // interface
+  int nm;
+  iilbm_interface_params ip;
+  double *X, *aux, *G, *Fn, *P, *U, *nrm;
+  int mdf_iters_last;
+  double mdf_res_last;
+  double *d_res;      // direct forcing residual scratch
+  // diagnostics
+  bool timing;
+  int nev;                      // event pairs in use
+  cudaEvent_t ev[2 * 256];      // stream-collide start / stop events
+  double sc_ms;
+  int sc_launches;
+  long long kernel_launches;    // every library kernel launched while timing
+};
+
+// Launchers (defined in lattice.cu / interface.cu).
+namespace iilbm {
+int launch_stream_collide(iilbm_lattice *h);
+int launch_interp(iilbm_lattice *h);
+int launch_macros(iilbm_lattice *h, double *drho, double *ux, double *uy);
+int launch_set_populations(iilbm_lattice *h, const double *df, bool equilibrium,
+                           const double *rho, const double *ux, const double *uy);
+int launch_get_populations(iilbm_lattice *h, double *df);
+int launch_interface_phase(iilbm_lattice *h);
+}  // namespace iilbm

@@ -1,0 +1,421 @@
+// lattice.cu -- the Eulerian side of the II-LBM step on sm_103a:
+//   * the fused AA-pattern stream-collide (SRT Eq. 14 + Guo Eq. 21, or MRT Eq. 15 +
+//     Guo Eq. 22), which also adds the jump of Eq. 47 to the populations it reads on
+//     cut links and the spread tangential force of Eq. 46;
+//   * velocity interpolation at the markers (Eq. 20) with the marker update;
+//   * state conversion (set / get populations, equilibrium start) and macroscopic
+//     fields.
+//
+// Memory layout: populations df_i = f_i - w_i rho0 stored as structure of arrays
+// A[i][y][x] (row pitch rounded to 32 elements) in the storage precision, updated in
+// place with the AA pattern: an even step reads slot i of node x and writes the
+// post-collision f*_i into slot opp(i) of the same node; an odd step reads slot
+// opp(i) of the upstream node x - e_i and writes f*_i into slot i of the downstream
+// node x + e_i.  Each node only touches slots no other node touches in that step,
+// so one array suffices and every step moves 2 x 9 values per node.
+#include "iilbm_internal.cuh"
+
+#include <cmath>
+
+namespace iilbm {
+
+template <typename T>
+struct CollP {
+  T omega;          // 1/tau (SRT)
+  T s1, s2, s4, s6, s7, s8;  // MRT rates of the non-conserved moments
+  T rho0;
+  T scale, inv_scale;        // storage scale 2^k and 2^-k
+  T bodyx, bodyy;
+};
+
+template <typename T>
+CollP<T> make_collp(const iilbm_config &c) {
+  CollP<T> p;
+  p.omega = T(1.0 / c.tau);
+  p.s1 = T(c.s[1]); p.s2 = T(c.s[2]); p.s4 = T(c.s[4]); p.s6 = T(c.s[6]);
+  p.s7 = T(c.s[7]); p.s8 = T(c.s[8]);
+  p.rho0 = T(c.rho0);
+  p.scale = T(std::ldexp(1.0, c.storage_scale_log2));
+  p.inv_scale = T(std::ldexp(1.0, -c.storage_scale_log2));
+  p.bodyx = T(c.body[0]);
+  p.bodyy = T(c.body[1]);
+  return p;
+}
+
+// ------------------------------------------------------------------ collision
+// Shifted populations in, post-collision shifted populations out.
+//   rho = rho0 + drho,  rho u = j + g/2  (Eqs. 11, 24)
+//   feq_i - w_i rho0 = w_i [drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u^2)]  (Eq. 23)
+//   Guo source  Gt_i = w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]  (Eqs. 21-22)
+template <typename T, int COLL>
+__device__ __forceinline__ T collide(T f[9], T gx, T gy, const CollP<T> &p) {
+  const T drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  const T rho = p.rho0 + drho;
+  const T ir = T(1) / rho;
+  const T jxh = jx + T(0.5) * gx, jyh = jy + T(0.5) * gy;  // rho u
+  const T ux = jxh * ir, uy = jyh * ir;
+  if (COLL == IILBM_SRT) {
+    const T u2 = ux * ux + uy * uy;
+    const T ug = ux * gx + uy * gy;
+    const T om = p.omega, fo = T(1) - T(0.5) * p.omega;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+      const T eu = T(cx(i)) * ux + T(cy(i)) * uy;
+      const T eg = T(cx(i)) * gx + T(cy(i)) * gy;
+      const T feq = wt<T>(i) * (drho + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * u2));
+      const T gt = wt<T>(i) * (T(3) * (eg - ug) + T(9) * eu * eg);
+      f[i] = f[i] - om * (f[i] - feq) + fo * gt;
+    }
+  } else {
+    // Lallemand-Luo moments of df: e, eps, qx, qy, pxx, pxy (rho, jx, jy above).
+    const T sa = (f[1] + f[2]) + (f[3] + f[4]);
+    const T sd = (f[5] + f[6]) + (f[7] + f[8]);
+    const T m1 = T(-4) * f[0] - sa + T(2) * sd;
+    const T m2 = T(4) * f[0] - T(2) * sa + sd;
+    const T m4 = T(-2) * (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
+    const T m6 = T(-2) * (f[2] - f[4]) + ((f[5] + f[6]) - (f[7] + f[8]));
+    const T m7 = (f[1] + f[3]) - (f[2] + f[4]);
+    const T m8 = (f[5] + f[7]) - (f[6] + f[8]);
+    // equilibrium moments of the shifted equilibrium
+    const T ru2 = jxh * ux + jyh * uy;  // rho u^2
+    const T e1 = T(-2) * drho + T(3) * ru2;
+    const T e2 = drho - T(3) * ru2;
+    const T e4 = -jxh, e6 = -jyh;
+    const T e7 = jxh * ux - jyh * uy;
+    const T e8 = jxh * uy;
+    // moments of Guo's source
+    const T ug = ux * gx + uy * gy;
+    const T F1 = T(6) * ug, F2 = T(-6) * ug, F4 = -gx, F6 = -gy;
+    const T F7 = T(2) * (ux * gx - uy * gy), F8 = ux * gy + uy * gx;
+    const T d1 = -p.s1 * (m1 - e1) + (T(1) - T(0.5) * p.s1) * F1;
+    const T d2 = -p.s2 * (m2 - e2) + (T(1) - T(0.5) * p.s2) * F2;
+    const T d4 = -p.s4 * (m4 - e4) + (T(1) - T(0.5) * p.s4) * F4;
+    const T d6 = -p.s6 * (m6 - e6) + (T(1) - T(0.5) * p.s6) * F6;
+    const T d7 = -p.s7 * (m7 - e7) + (T(1) - T(0.5) * p.s7) * F7;
+    const T d8 = -p.s8 * (m8 - e8) + (T(1) - T(0.5) * p.s8) * F8;
+    // conserved moments: rho unchanged, j gains exactly g (any s3, s5)
+    const T a1 = d1 * T(1.0 / 36), a2 = d2 * T(1.0 / 36);
+    const T a3 = gx * T(1.0 / 6), a5 = gy * T(1.0 / 6);
+    const T a4 = d4 * T(1.0 / 12), a6 = d6 * T(1.0 / 12);
+    const T a7 = d7 * T(0.25), a8 = d8 * T(0.25);
+    const T b = -a1 - T(2) * a2;        // common to the axis velocities
+    const T c = T(2) * a1 + a2;         // common to the diagonals
+    f[0] += T(-4) * a1 + T(4) * a2;
+    f[1] += b + a3 - T(2) * a4 + a7;
+    f[2] += b + a5 - T(2) * a6 - a7;
+    f[3] += b - a3 + T(2) * a4 + a7;
+    f[4] += b - a5 + T(2) * a6 - a7;
+    f[5] += c + (a3 + a4) + (a5 + a6) + a8;
+    f[6] += c - (a3 + a4) + (a5 + a6) - a8;
+    f[7] += c - (a3 + a4) - (a5 + a6) + a8;
+    f[8] += c + (a3 + a4) - (a5 + a6) - a8;
+  }
+  return drho;
+}
+
+// -------------------------------------------------------------- stream-collide
+// One thread per node, one 32 x 8 block per tile.  BC is IILBM_BC_PERIODIC or
+// IILBM_BC_WALLS_Y (periodic x, halfway bounce-back in y).
+template <typename S, int COLL, bool ODD, int BC>
+__global__ void __launch_bounds__(TILE_X *TILE_Y)
+    k_stream_collide(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
+                     typename Store<S>::T *__restrict__ gf, uint8_t *__restrict__ flags,
+                     const Geom geo, const CollP<typename Store<S>::T> p, int *status) {
+  using T = typename Store<S>::T;
+  const int x = blockIdx.x * TILE_X + threadIdx.x;
+  const int y = blockIdx.y * TILE_Y + threadIdx.y;
+  const int tile = blockIdx.y * geo.ntx + blockIdx.x;
+  const bool has = flags[tile] != 0;
+  if (x < geo.nx && y < geo.ny) {
+    const long long P = geo.plane;
+    const long long here = (long long)y * geo.pitch + x;
+    // neighbour rows / columns (wrapped); wall rows flagged
+    const int xm = x == 0 ? geo.nx - 1 : x - 1;
+    const int xp = x == geo.nx - 1 ? 0 : x + 1;
+    int ym = y - 1, yp = y + 1;
+    bool wall_m = false, wall_p = false;
+    if (BC == IILBM_BC_PERIODIC) {
+      ym = y == 0 ? geo.ny - 1 : ym;
+      yp = y == geo.ny - 1 ? 0 : yp;
+    } else {
+      wall_m = y == 0;
+      wall_p = y == geo.ny - 1;
+    }
+    const long long col[3] = {xm, x, xp};
+    const long long row[3] = {(long long)ym * geo.pitch, (long long)y * geo.pitch,
+                              (long long)yp * geo.pitch};
+    T f[9];
+    if (!ODD) {
+#pragma unroll
+      for (int i = 0; i < 9; i++) f[i] = Store<S>::ld(A[i * P + here]) * p.inv_scale;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; i++) {
+        const bool from_wall = (cy(i) > 0 && wall_m) || (cy(i) < 0 && wall_p);
+        const long long src = from_wall ? i * P + here
+                                        : opp(i) * P + row[1 - cy(i)] + col[1 - cx(i)];
+        f[i] = Store<S>::ld(A[src]) * p.inv_scale;
+      }
+    }
+    T gx = p.bodyx, gy = p.bodyy;
+    if (has) {
+#pragma unroll
+      for (int i = 1; i < 9; i++) {
+        f[i] += Jf[(i - 1) * P + here];
+        Jf[(i - 1) * P + here] = T(0);
+      }
+      gx += gf[here];
+      gy += gf[P + here];
+      gf[here] = T(0);
+      gf[P + here] = T(0);
+    }
+    const T drho = collide<T, COLL>(f, gx, gy, p);
+    if (!isfinite(drho)) atomicOr(status, ST_NONFINITE);
+    if (!ODD) {
+#pragma unroll
+      for (int i = 0; i < 9; i++) A[opp(i) * P + here] = Store<S>::st(f[i] * p.scale);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; i++) {
+        const bool to_wall = (cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m);
+        const long long dst = to_wall ? opp(i) * P + here
+                                      : i * P + row[1 + cy(i)] + col[1 + cx(i)];
+        A[dst] = Store<S>::st(f[i] * p.scale);
+      }
+    }
+  }
+  if (has) {
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) flags[tile] = 0;
+  }
+}
+
+// ------------------------------------------------------ Peskin delta (Eq. 17)
+__device__ inline double phi4(double r) {
+  const double a = fabs(r);
+  if (a < 1.0) return 0.125 * (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a));
+  if (a < 2.0) return 0.125 * (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a));
+  return 0.0;
+}
+
+// Macroscopic density deviation and velocity of node (x, y) of the current state:
+// populations (AA location) plus the jump, force g of the current interface.
+template <typename S>
+__device__ inline void node_macros(const S *A, const typename Store<S>::T *Jf,
+                                   const typename Store<S>::T *gf, const Geom &geo,
+                                   const CollP<typename Store<S>::T> &p, bool odd, int x,
+                                   int y, double &drho, double &ux, double &uy) {
+  using T = typename Store<S>::T;
+  const long long here = (long long)y * geo.pitch + x;
+  T f[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) f[i] = Store<S>::ld(A[aa_loc(geo, odd, i, x, y)]) * p.inv_scale;
+#pragma unroll
+  for (int i = 1; i < 9; i++) f[i] += Jf[(i - 1) * geo.plane + here];
+  const T gx = p.bodyx + gf[here], gy = p.bodyy + gf[geo.plane + here];
+  const T d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  const T ir = T(1) / (p.rho0 + d);
+  drho = double(d);
+  ux = double((jx + T(0.5) * gx) * ir);
+  uy = double((jy + T(0.5) * gy) * ir);
+}
+
+// Velocity interpolation U_k = sum_x u(x) delta_h(x - X_k) (Eq. 20), 16 threads per
+// marker (one per stencil node), FP64 accumulation; a membrane marker then moves,
+// X_k += U_k.  The interpolation reads the state before the stream-collide that
+// overwrites it, so it runs first in each step.
+template <typename S>
+__global__ void k_interp(const S *__restrict__ A, const typename Store<S>::T *__restrict__ Jf,
+                         const typename Store<S>::T *__restrict__ gf, const Geom geo,
+                         const CollP<typename Store<S>::T> p, bool odd, double *X, int n,
+                         double *U, int moves) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = tid >> 4, l = tid & 15;
+  double sx = 0.0, sy = 0.0;
+  if (k < n) {
+    const double Xk = X[2 * k], Yk = X[2 * k + 1];
+    const int x0 = (int)floor(Xk) - 1, y0 = (int)floor(Yk) - 1;
+    const int xa = x0 + (l & 3), yb = y0 + (l >> 2);
+    int xi = xa, yi = yb;
+    bool ok = true;
+    if (geo.bc == IILBM_BC_CHANNEL) ok = xi >= 0 && xi < geo.nx;
+    else xi = wrap(xi, geo.nx);
+    if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
+    else ok = ok && yi >= 0 && yi < geo.ny;
+    if (ok) {
+      double drho, ux, uy;
+      node_macros<S>(A, Jf, gf, geo, p, odd, xi, yi, drho, ux, uy);
+      const double w = phi4((double)xa - Xk) * phi4((double)yb - Yk);
+      sx = ux * w;
+      sy = uy * w;
+    }
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o, 16);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o, 16);
+  }
+  if (k < n && l == 0) {
+    U[2 * k] = sx;
+    U[2 * k + 1] = sy;
+    if (moves) {
+      X[2 * k] += sx;
+      X[2 * k + 1] += sy;
+    }
+  }
+}
+
+template <typename S>
+__global__ void k_macros(const S *__restrict__ A, const typename Store<S>::T *__restrict__ Jf,
+                         const typename Store<S>::T *__restrict__ gf, const Geom geo,
+                         const CollP<typename Store<S>::T> p, bool odd, double *drho,
+                         double *ux, double *uy) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= geo.nx) return;
+  double d, u, v;
+  node_macros<S>(A, Jf, gf, geo, p, odd, x, y, d, u, v);
+  const long long o = (long long)y * geo.nx + x;
+  if (drho) drho[o] = d;
+  if (ux) ux[o] = u;
+  if (uy) uy[o] = v;
+}
+
+// State in: natural-layout FP64 df[9][ny][nx], or the equilibrium (Eq. 23) of
+// rho(x), u(x) (rho0 / zero where the pointer is null).
+template <typename S>
+__global__ void k_set_populations(S *A, const Geom geo, const CollP<typename Store<S>::T> p,
+                                  bool odd, const double *df, int equilibrium,
+                                  const double *rho, const double *ux, const double *uy,
+                                  double rho0) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= geo.nx) return;
+  const long long o = (long long)y * geo.nx + x;
+  const long long N = (long long)geo.nx * geo.ny;
+  double v[9];
+  if (equilibrium) {
+    const double d = rho ? rho[o] - rho0 : 0.0;
+    const double u = ux ? ux[o] : 0.0, w = uy ? uy[o] : 0.0;
+    const double r = rho0 + d, u2 = u * u + w * w;
+    for (int i = 0; i < 9; i++) {
+      const double eu = cx(i) * u + cy(i) * w;
+      v[i] = wt<double>(i) * (d + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * u2));
+    }
+  } else {
+    for (int i = 0; i < 9; i++) v[i] = df[i * N + o];
+  }
+  for (int i = 0; i < 9; i++)
+    A[aa_loc(geo, odd, i, x, y)] =
+        Store<S>::st((typename Store<S>::T)(v[i]) * p.scale);
+}
+
+template <typename S>
+__global__ void k_get_populations(const S *A, const Geom geo,
+                                  const CollP<typename Store<S>::T> p, bool odd, double *df) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= geo.nx) return;
+  const long long o = (long long)y * geo.nx + x;
+  const long long N = (long long)geo.nx * geo.ny;
+  for (int i = 0; i < 9; i++)
+    df[i * N + o] = double(Store<S>::ld(A[aa_loc(geo, odd, i, x, y)]) * p.inv_scale);
+}
+
+// ------------------------------------------------------------------ dispatch
+template <typename F>
+static int dispatch_storage(int storage, F &&f) {
+  switch (storage) {
+    case IILBM_F64: return f((double *)nullptr);
+    case IILBM_F32: return f((float *)nullptr);
+    case IILBM_F16: return f((__half *)nullptr);
+    case IILBM_BF16: return f((__nv_bfloat16 *)nullptr);
+  }
+  return IILBM_ERR_INVALID_ARG;
+}
+
+static int last_error() {
+  return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
+}
+
+template <typename S, int COLL, bool ODD>
+static void sc_launch(iilbm_lattice *h) {
+  using T = typename Store<S>::T;
+  const Geom &g = h->geom;
+  dim3 grid(g.ntx, (g.ny + TILE_Y - 1) / TILE_Y), block(TILE_X, TILE_Y);
+  const CollP<T> p = make_collp<T>(h->cfg);
+  if (g.bc == IILBM_BC_PERIODIC)
+    k_stream_collide<S, COLL, ODD, IILBM_BC_PERIODIC><<<grid, block, 0, h->stream>>>(
+        (S *)h->A, (T *)h->J, (T *)h->g, h->flags, g, p, h->d_status);
+  else
+    k_stream_collide<S, COLL, ODD, IILBM_BC_WALLS_Y><<<grid, block, 0, h->stream>>>(
+        (S *)h->A, (T *)h->J, (T *)h->g, h->flags, g, p, h->d_status);
+}
+
+int launch_stream_collide(iilbm_lattice *h) {
+  const bool odd = h->step & 1;
+  return dispatch_storage(h->cfg.storage, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    if (h->cfg.collision == IILBM_SRT) {
+      if (odd) sc_launch<S, IILBM_SRT, true>(h); else sc_launch<S, IILBM_SRT, false>(h);
+    } else {
+      if (odd) sc_launch<S, IILBM_MRT, true>(h); else sc_launch<S, IILBM_MRT, false>(h);
+    }
+    return last_error();
+  });
+}
+
+int launch_interp(iilbm_lattice *h) {
+  if (h->nm == 0) return IILBM_OK;
+  const bool odd = h->step & 1;
+  return dispatch_storage(h->cfg.storage, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    using T = typename Store<S>::T;
+    const int threads = 16 * h->nm;
+    k_interp<S><<<(threads + 255) / 256, 256, 0, h->stream>>>(
+        (const S *)h->A, (const T *)h->J, (const T *)h->g, h->geom, make_collp<T>(h->cfg), odd,
+        h->X, h->nm, h->U, h->ip.moves);
+    return last_error();
+  });
+}
+
+int launch_macros(iilbm_lattice *h, double *drho, double *ux, double *uy) {
+  const bool odd = h->step & 1;
+  return dispatch_storage(h->cfg.storage, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    using T = typename Store<S>::T;
+    dim3 grid((h->geom.nx + 127) / 128, h->geom.ny);
+    k_macros<S><<<grid, 128, 0, h->stream>>>((const S *)h->A, (const T *)h->J, (const T *)h->g,
+                                             h->geom, make_collp<T>(h->cfg), odd, drho, ux, uy);
+    return last_error();
+  });
+}
+
+int launch_set_populations(iilbm_lattice *h, const double *df, bool equilibrium,
+                           const double *rho, const double *ux, const double *uy) {
+  const bool odd = h->step & 1;
+  return dispatch_storage(h->cfg.storage, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    using T = typename Store<S>::T;
+    dim3 grid((h->geom.nx + 127) / 128, h->geom.ny);
+    k_set_populations<S><<<grid, 128, 0, h->stream>>>((S *)h->A, h->geom, make_collp<T>(h->cfg),
+                                                      odd, df, equilibrium ? 1 : 0, rho, ux, uy,
+                                                      h->cfg.rho0);
+    return last_error();
+  });
+}
+
+int launch_get_populations(iilbm_lattice *h, double *df) {
+  const bool odd = h->step & 1;
+  return dispatch_storage(h->cfg.storage, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    using T = typename Store<S>::T;
+    dim3 grid((h->geom.nx + 127) / 128, h->geom.ny);
+    k_get_populations<S><<<grid, 128, 0, h->stream>>>((const S *)h->A, h->geom,
+                                                      make_collp<T>(h->cfg), odd, df);
+    return last_error();
+  });
+}
+
+}  // namespace iilbm

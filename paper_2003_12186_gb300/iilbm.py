@@ -1,0 +1,260 @@
+"""Thin Python binding of the C ABI in include/iilbm.h (argument marshalling only).
+
+Every function has the name of its C entry point; every step of the method runs in
+the CUDA library ``lib/libiilbm.so``.  There is no CPU fallback: if the library is
+missing or no sm_103a GPU is present, calls raise.
+
+Array arguments may be numpy arrays (host) or CUDA torch tensors (device); both are
+passed as raw pointers, and the library copies with cudaMemcpyDefault.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+SRT, MRT = 0, 1
+F64, F32, F16, BF16 = 0, 1, 2, 3
+BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL = 0, 1, 2
+SPRING, SPRING_REST, PRESCRIBED, DIRECT = 0, 1, 2, 3
+STORAGE = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+STORAGE_BYTES = {F64: 8, F32: 4, F16: 2, BF16: 2}
+
+
+class IilbmError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        self.code = code
+        super().__init__(f"{fn} failed: {code} ({error_string(code)})")
+
+
+class iilbm_config(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("collision", C.c_int32),
+                ("storage", C.c_int32), ("bc", C.c_int32), ("jump", C.c_int32),
+                ("storage_scale_log2", C.c_int32), ("reserved", C.c_int32),
+                ("tau", C.c_double), ("s", C.c_double * 9), ("rho0", C.c_double),
+                ("u_max", C.c_double), ("body", C.c_double * 2), ("stream", C.c_void_p)]
+
+
+class iilbm_interface_params(C.Structure):
+    _fields_ = [("model", C.c_int32), ("moves", C.c_int32), ("stiffness", C.c_double),
+                ("dX", C.c_double), ("rest_length", C.c_double), ("eta", C.c_double),
+                ("mdf_iters", C.c_int32), ("reserved", C.c_int32), ("mdf_tol", C.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+_H = C.c_void_p
+_P = C.c_void_p
+
+SIGNATURES = {
+    "iilbm_create_lattice": [C.POINTER(_H), C.POINTER(iilbm_config)],
+    "iilbm_destroy": [_H],
+    "iilbm_set_interface": [_H, _P, C.c_int32, C.POINTER(iilbm_interface_params), _P],
+    "iilbm_init_equilibrium": [_H, _P, _P, _P],
+    "iilbm_set_populations": [_H, _P],
+    "iilbm_get_populations": [_H, _P],
+    "iilbm_step": [_H, C.c_int32],
+    "iilbm_get_macros": [_H, _P, _P, _P],
+    "iilbm_get_markers": [_H, _P, _P, _P, _P],
+    "iilbm_get_mdf_stats": [_H, C.POINTER(C.c_int32), C.POINTER(C.c_double)],
+    "iilbm_get_cut_link_count": [_H, C.POINTER(C.c_int32)],
+    "iilbm_set_timing": [_H, C.c_int32],
+    "iilbm_get_timing": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                         C.POINTER(C.c_int64)],
+    "iilbm_synchronize": [_H],
+    "iilbm_error_string": [C.c_int],
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load libiilbm.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"II-LBM CUDA library not built: {path}")
+            L = C.CDLL(path)
+            for name, args in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = C.c_char_p if name == "iilbm_error_string" else C.c_int
+            _lib = L
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return load().iilbm_error_string(int(code)).decode()
+
+
+def _check(fn: str, rc: int):
+    if rc != OK:
+        raise IilbmError(fn, rc)
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"] and a.dtype == np.float64, "need contiguous float64"
+        return a.ctypes.data
+    # torch tensor
+    assert a.is_contiguous() and str(a.dtype) == "torch.float64", "need contiguous float64"
+    return a.data_ptr()
+
+
+def _host(a, shape):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    assert a.size == int(np.prod(shape)), f"expected {shape}, got {a.shape}"
+    return a
+
+
+class Lattice:
+    """One II-LBM lattice (handle of iilbm_create_lattice)."""
+
+    def __init__(self, nx, ny, collision=MRT, storage=F32, tau=0.8, s=None, rho0=1.0,
+                 bc=BC_PERIODIC, jump=1, u_max=0.0, body=(0.0, 0.0), stream=None,
+                 storage_scale_log2=None):
+        L = load()
+        cfg = iilbm_config()
+        cfg.nx, cfg.ny = nx, ny
+        cfg.collision = collision
+        cfg.storage = STORAGE[storage] if isinstance(storage, str) else storage
+        cfg.bc, cfg.jump = bc, jump
+        if storage_scale_log2 is None:
+            storage_scale_log2 = {F64: 0, F32: 0, F16: 12, BF16: 0}[cfg.storage]
+        cfg.storage_scale_log2 = storage_scale_log2
+        cfg.tau, cfg.rho0, cfg.u_max = tau, rho0, u_max
+        rates = s if s is not None else [0.0, 1.63, 1.14, 0.0, 1.92, 0.0, 1.92, 1 / tau, 1 / tau]
+        for i in range(9):
+            cfg.s[i] = rates[i]
+        cfg.body[0], cfg.body[1] = body
+        cfg.stream = stream
+        self.cfg = cfg
+        self.nx, self.ny = nx, ny
+        self.n_markers = 0
+        h = _H()
+        _check("iilbm_create_lattice", L.iilbm_create_lattice(C.byref(h), C.byref(cfg)))
+        self._h = h
+        self._L = L
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.iilbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ---------------------------------------------------------------- state
+    def iilbm_set_interface(self, X, model=SPRING, moves=True, stiffness=0.0, dX=1.0,
+                            rest_length=1.0, eta=2.0, mdf_iters=0, mdf_tol=0.0, aux=None):
+        p = iilbm_interface_params()
+        p.model, p.moves, p.stiffness, p.dX, p.rest_length = model, int(moves), stiffness, dX, \
+            rest_length
+        p.eta, p.mdf_iters, p.mdf_tol = eta, mdf_iters, mdf_tol
+        if X is None or (hasattr(X, "__len__") and len(X) == 0):
+            _check("iilbm_set_interface", self._L.iilbm_set_interface(self._h, None, 0, C.byref(p),
+                                                                      None))
+            self.n_markers = 0
+            return
+        n = len(X)
+        Xh = X if not isinstance(X, np.ndarray) and hasattr(X, "data_ptr") else _host(X, (n, 2))
+        A = None if aux is None else (aux if hasattr(aux, "data_ptr") else _host(aux, (n, 2)))
+        _check("iilbm_set_interface",
+               self._L.iilbm_set_interface(self._h, _ptr(Xh), n, C.byref(p), _ptr(A)))
+        self.n_markers = n
+
+    set_interface = iilbm_set_interface
+
+    def iilbm_init_equilibrium(self, rho=None, ux=None, uy=None):
+        N = (self.ny, self.nx)
+        arrs = [None if a is None else _host(a, N) for a in (rho, ux, uy)]
+        _check("iilbm_init_equilibrium",
+               self._L.iilbm_init_equilibrium(self._h, *[_ptr(a) for a in arrs]))
+
+    init_equilibrium = iilbm_init_equilibrium
+
+    def iilbm_set_populations(self, df):
+        d = df if hasattr(df, "data_ptr") else _host(df, (9, self.ny, self.nx))
+        _check("iilbm_set_populations", self._L.iilbm_set_populations(self._h, _ptr(d)))
+
+    set_populations = iilbm_set_populations
+
+    def iilbm_get_populations(self, out=None):
+        out = np.zeros((9, self.ny, self.nx)) if out is None else out
+        _check("iilbm_get_populations", self._L.iilbm_get_populations(self._h, _ptr(out)))
+        return out
+
+    get_populations = iilbm_get_populations
+
+    def iilbm_step(self, n=1):
+        _check("iilbm_step", self._L.iilbm_step(self._h, int(n)))
+
+    step = iilbm_step
+
+    def iilbm_get_macros(self, drho=None, ux=None, uy=None, want=(True, True, True)):
+        """drho, ux, uy of the current state (host numpy unless device tensors given)."""
+        outs = []
+        for a, w in zip((drho, ux, uy), want):
+            outs.append(a if a is not None else (np.zeros((self.ny, self.nx)) if w else None))
+        _check("iilbm_get_macros", self._L.iilbm_get_macros(self._h, *[_ptr(a) for a in outs]))
+        return tuple(outs)
+
+    get_macros = iilbm_get_macros
+
+    def iilbm_get_markers(self):
+        n = self.n_markers
+        X, G, U, Fn = np.zeros((n, 2)), np.zeros((n, 2)), np.zeros((n, 2)), np.zeros(n)
+        _check("iilbm_get_markers",
+               self._L.iilbm_get_markers(self._h, _ptr(X), _ptr(G), _ptr(U), _ptr(Fn)))
+        return dict(X=X, G=G, U=U, Fn=Fn)
+
+    get_markers = iilbm_get_markers
+
+    def iilbm_get_markers_into(self, X=None, G=None, U=None, Fn=None):
+        _check("iilbm_get_markers",
+               self._L.iilbm_get_markers(self._h, _ptr(X), _ptr(G), _ptr(U), _ptr(Fn)))
+
+    def iilbm_get_mdf_stats(self):
+        it, res = C.c_int32(), C.c_double()
+        _check("iilbm_get_mdf_stats",
+               self._L.iilbm_get_mdf_stats(self._h, C.byref(it), C.byref(res)))
+        return it.value, res.value
+
+    def iilbm_get_cut_link_count(self):
+        c = C.c_int32()
+        _check("iilbm_get_cut_link_count", self._L.iilbm_get_cut_link_count(self._h, C.byref(c)))
+        return c.value
+
+    def iilbm_set_timing(self, enable=True):
+        _check("iilbm_set_timing", self._L.iilbm_set_timing(self._h, int(enable)))
+
+    def iilbm_get_timing(self):
+        """(stream-collide ms summed, stream-collide launches, library kernel launches)."""
+        ms, n, k = C.c_double(), C.c_int32(), C.c_int64()
+        _check("iilbm_get_timing",
+               self._L.iilbm_get_timing(self._h, C.byref(ms), C.byref(n), C.byref(k)))
+        return ms.value, n.value, k.value
+
+    def iilbm_synchronize(self):
+        _check("iilbm_synchronize", self._L.iilbm_synchronize(self._h))
+
+    synchronize = iilbm_synchronize

@@ -1,0 +1,41 @@
+"""Helpers that set up the same seeded case on the CUDA library and on the oracle."""
+import numpy as np
+
+from paper_2003_12186_gb300 import iilbm
+from paper_2003_12186_gb300 import workloads as W
+
+
+def rates(collision, tau):
+    return W.mrt_rates(tau) if collision == "mrt" else [1.0 / tau] * 9
+
+
+def make_pair(orc, nx, ny, collision="mrt", storage="f64", tau=0.8, s=None, bc="periodic",
+              jump=1, body=(0.0, 0.0), rho0=1.0):
+    s = s if s is not None else rates(collision, tau)
+    bcg = {"periodic": iilbm.BC_PERIODIC, "walls": iilbm.BC_WALLS_Y}[bc]
+    bco = {"periodic": orc.BC_PERIODIC, "walls": orc.BC_WALLS_Y}[bc]
+    g = iilbm.Lattice(nx, ny, collision=iilbm.SRT if collision == "srt" else iilbm.MRT,
+                      storage=storage, tau=tau, s=s, bc=bcg, jump=jump, body=body, rho0=rho0)
+    o = orc.Oracle(nx, ny, collision=orc.SRT if collision == "srt" else orc.MRT, tau=tau, s=s,
+                   bc=bco, jump=jump, body=body, rho0=rho0)
+    return g, o
+
+
+def set_membrane(orc, g, o, X, model="spring", kappa=0.05, dX=1.0, l0=1.0, moves=True, G=None):
+    mg = {"spring": iilbm.SPRING, "spring_rest": iilbm.SPRING_REST,
+          "prescribed": iilbm.PRESCRIBED}[model]
+    mo = {"spring": orc.SPRING, "spring_rest": orc.SPRING_REST,
+          "prescribed": orc.PRESCRIBED}[model]
+    g.set_interface(X, model=mg, moves=moves, stiffness=kappa, dX=dX, rest_length=l0, aux=G)
+    o.set_interface(X, model=mo, moves=moves, kappa=kappa, dX=dX, l0=l0, G=G)
+
+
+def rel_err(u_gpu, u_orc, uref):
+    """||a - b||_inf / max(||b||_inf, uref)."""
+    return float(np.abs(u_gpu - u_orc).max() / max(np.abs(u_orc).max(), uref))
+
+
+def vel_error(g, o, uref=1e-6):
+    _, ug, vg = g.get_macros()
+    _, uo, vo = o.current_macros()
+    return max(rel_err(ug, uo, uref), rel_err(vg, vo, uref))

@@ -1,0 +1,221 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, element by
+element on the same seeded inputs.
+
+Tolerances (velocity, relative to max(|u_oracle|_inf, U_ref)): FP64 storage 1e-12,
+FP32 1e-5, FP16 1e-3; BF16 is reported, not bounded below 1e-2.  Integer work (the
+cut-link count) is compared exactly."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2003_12186_gb300 import iilbm
+from paper_2003_12186_gb300 import workloads as W
+
+from _pair import make_pair, rel_err, set_membrane, vel_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    iilbm.load()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("collision", ["srt", "mrt"])
+def test_rest_state_bitwise(orc, storage, collision):
+    g, _ = make_pair(orc, 37, 29, collision=collision, storage=storage)
+    g.step(7)
+    assert np.all(g.get_populations() == 0.0)
+    d, u, v = g.get_macros()
+    assert np.all(d == 0) and np.all(u == 0) and np.all(v == 0)
+
+
+@pytest.mark.parametrize("steps", [0, 1, 2, 5])
+def test_set_get_populations_roundtrip_both_parities(orc, steps):
+    g, _ = make_pair(orc, 33, 17, storage="f64")
+    g.step(steps)
+    df = W.random_df(33, 17, 1e-3, steps)
+    g.set_populations(df)
+    assert np.array_equal(g.get_populations(), df)
+
+
+@pytest.mark.parametrize("collision", ["srt", "mrt"])
+@pytest.mark.parametrize("shape", [(4, 4), (37, 29), (64, 40)])
+def test_tiny_grids_no_interface_fp64(orc, collision, shape):
+    nx, ny = shape
+    g, o = make_pair(orc, nx, ny, collision=collision, storage="f64", tau=0.7,
+                     body=(1e-5, -2e-5))
+    df = W.random_df(nx, ny, 1e-3, 1)
+    g.set_populations(df)
+    o.set_df(df)
+    for n in (1, 1, 3, 5):
+        g.step(n)
+        o.step(n)
+        assert np.abs(g.get_populations() - o.get_df()).max() < 1e-17
+    assert vel_error(g, o, 1e-4) < 1e-13
+
+
+@pytest.mark.parametrize("collision", ["srt", "mrt"])
+def test_walls_bounce_back_fp64(orc, collision):
+    nx, ny = 40, 24
+    g, o = make_pair(orc, nx, ny, collision=collision, storage="f64", tau=0.9, bc="walls",
+                     body=(1e-5, 0.0))
+    df = W.random_df(nx, ny, 1e-4, 2)
+    g.set_populations(df)
+    o.set_df(df)
+    g.step(41)
+    o.step(41)
+    assert np.abs(g.get_populations() - o.get_df()).max() < 1e-17
+    assert vel_error(g, o, 1e-4) < 1e-12
+
+
+def test_membrane64_fp64_step_by_step(orc):
+    """The 64^2 SRT membrane (rest-length springs): populations, markers, cut-link
+    count and velocity match the oracle over the first steps."""
+    w = W.membrane_64()
+    g, o = make_pair(orc, 64, 64, collision="srt", storage="f64", tau=w["tau"])
+    set_membrane(orc, g, o, w["X"], "spring_rest", w["kappa"], w["dX"], w["l0"])
+    for s in range(6):
+        g.step(1)
+        o.step(1)
+        assert np.abs(g.get_populations() - o.get_df()).max() < 1e-17
+        mg, mo = g.get_markers(), o.markers()
+        assert np.abs(mg["X"] - mo["X"]).max() < 1e-14
+        assert np.abs(mg["U"] - mo["U"]).max() < 1e-16
+    assert vel_error(g, o) < 1e-12
+    assert g.iilbm_get_cut_link_count() == o.cut_link_count() > 0
+
+
+def test_membrane64_fp64_full_run(orc):
+    """All 2000 steps of the 64^2 FP64 membrane: velocity within 1e-12 (relative to
+    the run's largest marker speed), markers within 1e-12; the Laplace pressure jump
+    and the area drift are reported alongside."""
+    w = W.membrane_64()
+    g, o = make_pair(orc, 64, 64, collision="srt", storage="f64", tau=w["tau"])
+    set_membrane(orc, g, o, w["X"], "spring_rest", w["kappa"], w["dX"], w["l0"])
+    umax = 0.0
+    for _ in range(20):
+        g.step(100)
+        o.step(100)
+        umax = max(umax, np.abs(o.markers()["U"]).max())
+    err = vel_error(g, o, max(umax, 1e-6))
+    mg, mo = g.get_markers(), o.markers()
+    assert err < 1e-12, err
+    assert np.abs(mg["X"] - mo["X"]).max() < 1e-12
+    a = orc.polygon_area(mg["X"]) / orc.polygon_area(w["X"]) - 1
+    print(f"membrane64 fp64: rel vel err {err:.3e}, area drift {a:.3e}")
+
+
+@pytest.mark.parametrize("collision", ["srt", "mrt"])
+def test_mass_conservation_fp64(orc, collision):
+    nx = ny = 48
+    X = W.wobbly_polygon(24.3, 23.6, 10.0, 70, 0.15, 3)
+    g, o = make_pair(orc, nx, ny, collision=collision, storage="f64", tau=0.7)
+    df = W.random_df(nx, ny, 1e-4, 5)
+    g.set_populations(df)
+    set_membrane(orc, g, o, X, "spring", 0.05, W.polygon_perimeter(X) / 70)
+    m0 = math.fsum(df.ravel())
+    g.step(30)
+    assert abs(math.fsum(g.get_populations().ravel()) - m0) < 1e-14
+
+
+def test_uniform_normal_force_fixed_point_fp64(orc):
+    """The exact piecewise-constant pressure state is a fixed point on the GPU too."""
+    nx = ny = 40
+    R, F = 10.0, -2e-3
+    X = W.circle_markers(20.3, 19.8, R, 64)
+    n = (X - [20.3, 19.8]) / R
+    wind = np.array([[orc.winding(X, x, y) for x in range(nx)] for y in range(ny)])
+    rho = 1.0 - wind * F * 3
+    E = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+    wt = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+    df = np.zeros((9, ny, nx))
+    for i, (ex, ey) in enumerate(E):
+        df[i] = wt[i] * (np.roll(rho, (ey, ex), axis=(0, 1)) - 1.0)
+    g, _ = make_pair(orc, nx, ny, collision="mrt", storage="f64", tau=0.8)
+    g.set_populations(df)
+    g.set_interface(X, model=iilbm.PRESCRIBED, moves=False, dX=W.polygon_perimeter(X) / 64,
+                    aux=F * n)
+    g.step(50)
+    _, u, v = g.get_macros()
+    assert max(np.abs(u).max(), np.abs(v).max()) < 1e-16
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16", 1e-3), ("bf16", 3e-2)])
+def test_ellipse_reduced_precision_vs_fp64_oracle(orc, storage, tol):
+    """The MRT ellipse membrane scaled to 256^2 (ragged tiles: 256 = 8 x 32), 300 steps,
+    stored in reduced precision against the FP64 oracle."""
+    w = W.ellipse_scaled(256, storage)
+    g, o = make_pair(orc, 256, 256, collision="mrt", storage=storage, tau=w["tau"])
+    set_membrane(orc, g, o, w["X"], "spring", w["kappa"], w["dX"])
+    umax = 0.0
+    for _ in range(3):
+        g.step(100)
+        o.step(100)
+        umax = max(umax, np.abs(o.markers()["U"]).max())
+    err = vel_error(g, o, max(umax, 1e-6))
+    print(f"ellipse256 {storage}: rel vel err {err:.3e} (U_ref {umax:.3e})")
+    assert err < tol
+
+
+def test_ragged_lattice_with_membrane_fp32(orc):
+    """A lattice whose sizes are not multiples of the 32 x 8 tile, interface crossing
+    tile edges, SRT FP32."""
+    nx, ny = 77, 53
+    X = W.wobbly_polygon(38.4, 26.1, 14.0, 90, 0.1, 8)
+    g, o = make_pair(orc, nx, ny, collision="srt", storage="f32", tau=0.9)
+    set_membrane(orc, g, o, X, "spring", 0.02, W.polygon_perimeter(X) / 90)
+    umax = 0.0
+    for _ in range(4):
+        g.step(50)
+        o.step(50)
+        umax = max(umax, np.abs(o.markers()["U"]).max())
+    assert vel_error(g, o, max(umax, 1e-6)) < 1e-5
+
+
+def test_empty_interface_and_replacement(orc):
+    nx, ny = 32, 32
+    g, o = make_pair(orc, nx, ny, storage="f64")
+    X = W.circle_markers(16.2, 15.7, 6.0, 40)
+    set_membrane(orc, g, o, X, "spring", 0.05, W.polygon_perimeter(X) / 40)
+    g.step(3)
+    o.step(3)
+    g.set_interface([])
+    o.set_interface(np.zeros((0, 2)))
+    g.step(4)
+    o.step(4)
+    assert np.abs(g.get_populations() - o.get_df()).max() < 1e-17
+
+
+def test_invalid_interface_is_rejected(orc):
+    g, _ = make_pair(orc, 32, 32, storage="f32", bc="walls")
+    X = W.circle_markers(16, 2.0, 6.0, 40)  # crosses the wall band
+    with pytest.raises(iilbm.IilbmError) as e:
+        g.set_interface(X, model=iilbm.SPRING, stiffness=0.1, dX=1.0)
+    assert e.value.code == -6
+    Xl = np.array([[5.0, 5.0], [30.0, 5.0], [30.0, 30.0]])  # segments longer than 16
+    g2, _ = make_pair(orc, 64, 64, storage="f32")
+    with pytest.raises(iilbm.IilbmError):
+        g2.set_interface(Xl, model=iilbm.SPRING, stiffness=0.1, dX=1.0)
+
+
+def test_ellipse2048_fp32_full_size_sampled(orc):
+    """The full 2048^2 MRT ellipse membrane in FP32, as the benchmark launches it:
+    10 steps against the oracle (whole field compared)."""
+    w = W.ellipse_2048("f32")
+    g, o = make_pair(orc, 2048, 2048, collision="mrt", storage="f32", tau=w["tau"])
+    set_membrane(orc, g, o, w["X"], "spring", w["kappa"], w["dX"])
+    g.step(10)
+    o.step(10)
+    umax = np.abs(o.markers()["U"]).max()
+    err = vel_error(g, o, max(umax, 1e-6))
+    assert g.iilbm_get_cut_link_count() == o.cut_link_count()
+    mg, mo = g.get_markers(), o.markers()
+    assert np.abs(mg["X"] - mo["X"]).max() < 1e-9
+    print(f"ellipse2048 f32 10 steps: rel vel err {err:.3e}")
+    assert err < 1e-5

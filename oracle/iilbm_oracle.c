@@ -36,7 +36,10 @@ static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 static const double WT[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                              1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-#define CS2 (1.0 / 3.0)
+/* c_s = 1/sqrt(3) (section 2.2.1), so 1/c_s^2 = 3 exactly: every 1/c_s^2 and 1/c_s^4
+ * of the paper is applied as a multiplication by 3 or 9, never as a division by a
+ * rounded 1/3 (which would bias every equilibrium by the same one-ulp error). */
+#define INV_CS2 3.0
 
 /* ---------------------------------------------------------------- config --- */
 enum { ORC_SRT = 0, ORC_MRT = 1 };
@@ -111,7 +114,19 @@ void orc_mrt_matrix(double *M) {
   }
 }
 
-/* Gauss–Jordan inverse with partial pivoting (library-style primitive). */
+/* M^-1 of an orthogonal-row basis: M^-1 = M^T diag(1/|row_r|^2).  The squared row
+ * norms are sums of squared small integers (exact), so each entry is the correctly
+ * rounded M_ri / |row_r|^2. */
+void orc_mrt_inverse(const double *M, double *Minv) {
+  for (int r = 0; r < 9; r++) {
+    double nrm = 0;
+    for (int i = 0; i < 9; i++) nrm += M[r * 9 + i] * M[r * 9 + i];
+    for (int i = 0; i < 9; i++) Minv[i * 9 + r] = M[r * 9 + i] / nrm;
+  }
+}
+
+/* Gauss–Jordan inverse with partial pivoting (library-style primitive; used by the
+ * tests to check the orthogonal-basis inverse). */
 int orc_invert9(const double *A, double *Ainv) {
   double a[9][18];
   for (int r = 0; r < 9; r++)
@@ -149,7 +164,7 @@ void orc_feq_shifted(double drho, double rho0, double ux, double uy, double *dfe
   double rho = rho0 + drho;
   for (int i = 0; i < 9; i++) {
     double eu = EX[i] * ux + EY[i] * uy;
-    double poly = eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - u2 / (2.0 * CS2);
+    double poly = eu * INV_CS2 + eu * eu * (INV_CS2 * INV_CS2 / 2.0) - u2 * (INV_CS2 / 2.0);
     dfeq[i] = WT[i] * (drho + rho * poly);
   }
 }
@@ -159,8 +174,8 @@ void orc_feq_shifted(double drho, double rho0, double ux, double uy, double *dfe
 void orc_guo_source(double ux, double uy, double gx, double gy, double *Gt) {
   for (int i = 0; i < 9; i++) {
     double eu = EX[i] * ux + EY[i] * uy;
-    double t1 = ((EX[i] - ux) * gx + (EY[i] - uy) * gy) / CS2;
-    double t2 = eu * (EX[i] * gx + EY[i] * gy) / (CS2 * CS2);
+    double t1 = ((EX[i] - ux) * gx + (EY[i] - uy) * gy) * INV_CS2;
+    double t2 = eu * (EX[i] * gx + EY[i] * gy) * (INV_CS2 * INV_CS2);
     Gt[i] = WT[i] * (t1 + t2);
   }
 }
@@ -413,7 +428,7 @@ int orc_cut_links(const orc_cfg *c, const double *X, int n, const double *Fn,
           double F = (1.0 - t) * Fn[k] + t * Fn[kp];
           cell[cnt] = yd * c->nx + xd;
           dir[cnt] = i;
-          coef[cnt] = (double)s * WT[i] / CS2 * F;
+          coef[cnt] = (double)s * WT[i] * INV_CS2 * F;
           cnt++;
         }
   }
@@ -510,7 +525,7 @@ orc_state *orc_create(const orc_cfg *cfg) {
   S->ux = (double *)calloc(N, sizeof(double));
   S->uy = (double *)calloc(N, sizeof(double));
   orc_mrt_matrix(S->M);
-  orc_invert9(S->M, S->Minv);
+  orc_mrt_inverse(S->M, S->Minv);
   return S;
 }
 

@@ -84,6 +84,7 @@ def lib():
             L.orc_phi.restype = C.c_double
             L.orc_mrt_matrix.argtypes = [_D]
             L.orc_invert9.argtypes = [_D, _D]
+            L.orc_mrt_inverse.argtypes = [_D, _D]
             L.orc_feq_shifted.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _D]
             L.orc_guo_source.argtypes = [C.c_double] * 4 + [_D]
             L.orc_collide_cell.argtypes = [C.POINTER(_Cfg), _D, _D, _D, C.c_double, C.c_double, _D]
@@ -133,11 +134,21 @@ def phi(r: float) -> float:
 
 
 def mrt_matrix():
+    """(M, M^-1) as the oracle's collision uses them (orthogonal-basis inverse)."""
     M = np.zeros(81)
     lib().orc_mrt_matrix(_p(M))
     Mi = np.zeros(81)
-    lib().orc_invert9(_p(M), _p(Mi))
+    lib().orc_mrt_inverse(_p(M), _p(Mi))
     return M.reshape(9, 9), Mi.reshape(9, 9)
+
+
+def invert9(A):
+    """General 9x9 inverse (Gauss-Jordan) -- an independent check of mrt_matrix()."""
+    A = _f64(A).ravel()
+    out = np.zeros(81)
+    if lib().orc_invert9(_p(A), _p(out)) != 0:
+        raise ValueError("singular")
+    return out.reshape(9, 9)
 
 
 def feq_shifted(rho, rho0, ux, uy):

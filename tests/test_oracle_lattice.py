@@ -20,6 +20,8 @@ def test_mrt_basis_is_orthogonal_with_textbook_norms(orc):
     G = M @ M.T
     assert np.allclose(G, np.diag([9, 36, 36, 6, 12, 6, 12, 4, 4]), atol=0, rtol=0)
     assert np.abs(Mi @ M - np.eye(9)).max() < 1e-15
+    assert np.abs(Mi - orc.invert9(M)).max() < 1e-15
+    assert np.abs(Mi - np.linalg.inv(M)).max() < 1e-15
     assert np.allclose(M @ WT, [1, -2, 1, 0, 0, 0, 0, 0, 0], atol=1e-16)
 
 

@@ -187,7 +187,9 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    stream = torch.cuda.current_stream().cuda_stream
+    ts = torch.cuda.Stream()  # the library runs on this stream; events are recorded on it
+    torch.cuda.set_stream(ts)
+    stream = ts.cuda_stream
     w = workload(args.size, args.storage)
     cells = w["nx"] * w["ny"]
     sbytes = iilbm.STORAGE_BYTES[iilbm.STORAGE[args.storage]]
@@ -207,9 +209,9 @@ def run_ours(args):
     g.iilbm_set_timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
-    e0.record()
+    e0.record(ts)
     g.step(args.steps)
-    e1.record()
+    e1.record(ts)
     barrier()
     ms = e0.elapsed_time(e1)
     sc_ms, sc_n, launches = g.iilbm_get_timing()

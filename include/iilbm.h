@@ -141,6 +141,15 @@ int iilbm_set_timing(iilbm_t h, int32_t enable);
 int iilbm_get_timing(iilbm_t h, double *stream_collide_ms, int32_t *stream_collide_launches,
                      int64_t *kernel_launches);
 
+/* Execution options (all on by default; for A/B measurements and tests):
+ *  IILBM_OPT_CUDA_GRAPH     replay blocks of steps from one captured CUDA graph;
+ *  IILBM_OPT_OVERLAP        run the next step's interface phase on a second stream
+ *                           while the current stream-collide runs;
+ *  IILBM_OPT_VECTOR_KERNEL  vectorised stream-collide (else one node per thread).
+ * Results are identical either way.  Synchronises the handle's stream. */
+enum { IILBM_OPT_CUDA_GRAPH = 0, IILBM_OPT_OVERLAP = 1, IILBM_OPT_VECTOR_KERNEL = 2 };
+int iilbm_set_option(iilbm_t h, int32_t option, int32_t value);
+
 /* Wait for the handle's stream and return any latched device status. */
 int iilbm_synchronize(iilbm_t h);
 

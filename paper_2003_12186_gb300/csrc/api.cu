@@ -52,22 +52,30 @@ void free_interface(iilbm_lattice *h) {
   h->nm = 0;
 }
 
-// Bring J, g, flags to the current state's interface (idempotent per state).
+// Bring the jump / force buffer of the current state's parity to the current
+// interface (idempotent per state).
 int prepare(iilbm_lattice *h) {
   if (h->prepared) return IILBM_OK;
-  int rc = launch_interface_phase(h);
+  int rc = launch_interface_phase(h, (int)(h->step & 1), h->stream);
   if (rc) return rc;
   h->prepared = true;
   return IILBM_OK;
 }
 
-// Clear any jump / force left in J, g (used when the interface or state is replaced
+void drop_graph(iilbm_lattice *h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+}
+
+// Clear every jump / force buffer (used when the interface or the state is replaced
 // outside the step sequence).
 int clear_fields(iilbm_lattice *h) {
   const Geom &g = h->geom;
-  CK(cudaMemsetAsync(h->J, 0, 8 * (size_t)g.plane * h->tbytes, h->stream));
-  CK(cudaMemsetAsync(h->g, 0, 2 * (size_t)g.plane * h->tbytes, h->stream));
-  CK(cudaMemsetAsync(h->flags, 0, (size_t)h->ntiles, h->stream));
+  for (int b = 0; b < 2; b++) {
+    CK(cudaMemsetAsync(h->Jb[b], 0, 8 * (size_t)g.plane * h->tbytes, h->stream));
+    CK(cudaMemsetAsync(h->gb[b], 0, 2 * (size_t)g.plane * h->tbytes, h->stream));
+    CK(cudaMemsetAsync(h->flagsb[b], 0, (size_t)h->ntiles, h->stream));
+  }
   h->prepared = false;
   return IILBM_OK;
 }
@@ -138,12 +146,19 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
     }
     h->own_stream = true;
   }
-  bool ok = cudaMalloc(&h->A, 9 * (size_t)g.plane * h->sbytes) == cudaSuccess &&
-            cudaMalloc(&h->J, 8 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
-            cudaMalloc(&h->g, 2 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
-            cudaMalloc(&h->flags, (size_t)h->ntiles) == cudaSuccess &&
+  h->vector_sc = true;
+  h->overlap = true;
+  h->use_graph = true;
+  bool ok = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess &&
+            cudaMalloc(&h->A, 9 * (size_t)g.plane * h->sbytes) == cudaSuccess &&
             cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->d_ncut, sizeof(int)) == cudaSuccess;
+  for (int b = 0; b < 2 && ok; b++)
+    ok = cudaMalloc(&h->Jb[b], 8 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
+         cudaMalloc(&h->gb[b], 2 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
+         cudaMalloc(&h->flagsb[b], (size_t)h->ntiles) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     iilbm_destroy(h);
@@ -167,10 +182,16 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
 int iilbm_destroy(iilbm_t h) {
   if (!h) return IILBM_ERR_INVALID_ARG;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->side) cudaStreamSynchronize(h->side);
+  drop_graph(h);
   free_interface(h);
-  void *bufs[] = {h->A, h->J, h->g, h->flags, h->d_status, h->d_ncut};
+  void *bufs[] = {h->A, h->Jb[0], h->Jb[1], h->gb[0], h->gb[1], h->flagsb[0], h->flagsb[1],
+                  h->d_status, h->d_ncut};
   for (void *b : bufs)
     if (b) cudaFree(b);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->ev[0])
     for (int e = 0; e < 2 * 256; e++) cudaEventDestroy(h->ev[e]);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -193,6 +214,7 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
   int rc = clear_fields(h);
   if (rc) return rc;
   CK(cudaStreamSynchronize(h->stream));
+  drop_graph(h);
   free_interface(h);
   if (n == 0) return IILBM_OK;
   const size_t b2 = 2 * (size_t)n * sizeof(double);
@@ -304,26 +326,109 @@ long long kernels_per_step(const iilbm_lattice *h) {
   return 1 + (h->nm > 0 ? 2 + (h->cfg.jump ? 1 : 0) + 1 : 0);
 }
 
+bool pipelined(const iilbm_lattice *h) { return h->overlap && h->nm > 0; }
+
+// One time step of the current state n (its interface already prepared in buffer
+// n & 1).  Main stream: interpolation (+ marker move), stream-collide.  With overlap,
+// the interface phase of state n + 1 (buffer (n+1) & 1) forks to the side stream
+// right after the interpolation -- it needs only X^{n+1} -- and joins before the
+// step ends.  Safe inside stream capture.
+int one_step(iilbm_lattice *h, int ev_slot) {
+  int rc;
+  if ((rc = launch_interp(h))) return rc;
+  const bool pipe = pipelined(h);
+  if (pipe) {
+    CK(cudaEventRecord(h->ev_fork, h->stream));
+    CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    rc = launch_interface_phase(h, (int)((h->step + 1) & 1), h->side);  // state n + 1
+    if (rc) return rc;
+    CK(cudaEventRecord(h->ev_join, h->side));
+  }
+  if (ev_slot >= 0) CK(cudaEventRecordWithFlags(h->ev[2 * ev_slot], h->stream, cudaEventRecordExternal));
+  if ((rc = launch_stream_collide(h))) return rc;
+  if (ev_slot >= 0)
+    CK(cudaEventRecordWithFlags(h->ev[2 * ev_slot + 1], h->stream, cudaEventRecordExternal));
+  if (pipe) CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+  h->step++;
+  h->prepared = pipe || h->nm == 0;
+  return IILBM_OK;
+}
+
+// Capture GRAPH_STEPS steps starting from an even, prepared state.
+int capture_graph(iilbm_lattice *h) {
+  drop_graph(h);
+  const long long step0 = h->step;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = IILBM_OK;
+  for (int k = 0; k < GRAPH_STEPS && !rc; k++) rc = one_step(h, h->timing ? k : -1);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  h->step = step0;
+  h->prepared = true;
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return IILBM_ERR_CUDA;
+  e = cudaGraphInstantiate(&h->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->gexec = nullptr;
+    return IILBM_ERR_CUDA;
+  }
+  h->graph_timing = h->timing;
+  return IILBM_OK;
+}
+
 int iilbm_step(iilbm_t h, int32_t n) {
   if (!h || n < 0) return IILBM_ERR_INVALID_ARG;
-  for (int s = 0; s < n; s++) {
-    int rc = prepare(h);
-    if (rc) return rc;
-    if ((rc = launch_interp(h))) return rc;
+  int rc;
+  while (n > 0) {
+    if ((rc = prepare(h))) return rc;
+    const bool graph_ok = h->use_graph && (pipelined(h) || h->nm == 0) && (h->step & 1) == 0 &&
+                          n >= GRAPH_STEPS;
+    if (graph_ok) {
+      if (h->timing && (rc = drain_events(h))) return rc;
+      if (!h->gexec || h->graph_timing != h->timing)
+        if ((rc = capture_graph(h))) return rc;
+      CK(cudaGraphLaunch(h->gexec, h->stream));
+      h->step += GRAPH_STEPS;
+      h->prepared = true;
+      n -= GRAPH_STEPS;
+      if (h->timing) {
+        h->nev = GRAPH_STEPS;
+        h->sc_launches += GRAPH_STEPS;
+        h->kernel_launches += GRAPH_STEPS * kernels_per_step(h);
+        if ((rc = drain_events(h))) return rc;
+      }
+      continue;
+    }
+    int slot = -1;
     if (h->timing) {
       if (h->nev == 256 && (rc = drain_events(h))) return rc;
-      CK(cudaEventRecord(h->ev[2 * h->nev], h->stream));
+      slot = h->nev;
     }
-    if ((rc = launch_stream_collide(h))) return rc;
+    if ((rc = one_step(h, slot))) return rc;
     if (h->timing) {
-      CK(cudaEventRecord(h->ev[2 * h->nev + 1], h->stream));
       h->nev++;
       h->sc_launches++;
       h->kernel_launches += kernels_per_step(h);
     }
-    h->step++;
-    h->prepared = false;
+    n--;
   }
+  return IILBM_OK;
+}
+
+int iilbm_set_option(iilbm_t h, int32_t option, int32_t value) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  switch (option) {
+    case IILBM_OPT_CUDA_GRAPH: h->use_graph = value != 0; break;
+    case IILBM_OPT_OVERLAP: h->overlap = value != 0; break;
+    case IILBM_OPT_VECTOR_KERNEL: h->vector_sc = value != 0; break;
+    default: return IILBM_ERR_INVALID_ARG;
+  }
+  drop_graph(h);
   return IILBM_OK;
 }
 
@@ -331,6 +436,10 @@ int iilbm_set_timing(iilbm_t h, int32_t enable) {
   if (!h) return IILBM_ERR_INVALID_ARG;
   if (enable && !h->ev[0])
     for (int e = 0; e < 2 * 256; e++) CK(cudaEventCreate(&h->ev[e]));
+  if (!enable && h->nev) {
+    int rc = drain_events(h);
+    if (rc) return rc;
+  }
   h->timing = enable != 0;
   return IILBM_OK;
 }
@@ -392,6 +501,7 @@ int iilbm_get_cut_link_count(iilbm_t h, int32_t *count) {
 
 int iilbm_synchronize(iilbm_t h) {
   if (!h) return IILBM_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(h->side));
   return read_status(h);
 }
 

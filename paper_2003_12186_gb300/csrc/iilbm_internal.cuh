@@ -47,6 +47,7 @@ constexpr int ST_TIMEOUT = 8;
 constexpr double QSCALE = 16777216.0;
 constexpr double MAX_SEGMENT = 16.0;
 constexpr double MAX_COORD = 16000.0;
+constexpr int GRAPH_STEPS = 32;
 
 // ------------------------------------------------------------ storage types
 // Populations are stored as df * 2^k in S and computed in T (double for FP64
@@ -115,10 +116,22 @@ struct iilbm_lattice {
   size_t sbytes;      // bytes per stored population
   size_t tbytes;      // bytes per arithmetic value (jump, force)
   void *A;            // [9][plane] populations, storage type
-  void *J;            // [8][plane] jump of the current interface, arithmetic type
-  void *g;            // [2][plane] spread force of the current interface
-  uint8_t *flags;     // [ntiles]
+  // Jump [8][plane], spread force [2][plane] (arithmetic type) and tile flags of the
+  // interface of a state, double-buffered by the parity of the state's time level so
+  // the interface phase of step n+1 can run while step n's stream-collide consumes
+  // (and re-zeroes) the buffer of step n.
+  void *Jb[2];
+  void *gb[2];
+  uint8_t *flagsb[2];
   int ntiles;
+  // execution
+  bool vector_sc;     // vectorised stream-collide when nx is a multiple of its width
+  bool overlap;       // next interface phase on the side stream during stream-collide
+  bool use_graph;     // replay GRAPH_STEPS steps per CUDA-graph launch
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
+  cudaGraphExec_t gexec;
+  bool graph_timing;  // the instantiated graph records timing events
   long long step;     // time level of the state; AA parity = step & 1
   bool prepared;      // jump / force of the current state already in J, g
   int *d_status;      // latched device status bits
@@ -147,5 +160,5 @@ int launch_macros(iilbm_lattice *h, double *drho, double *ux, double *uy);
 int launch_set_populations(iilbm_lattice *h, const double *df, bool equilibrium,
                            const double *rho, const double *ux, const double *uy);
 int launch_get_populations(iilbm_lattice *h, double *df);
-int launch_interface_phase(iilbm_lattice *h);
+int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s);
 }  // namespace iilbm

@@ -188,31 +188,32 @@ __global__ void k_spread(const double *__restrict__ X, const double *__restrict_
 // Items 1-3 of the step for the current state: marker forces and split, the jump on
 // every cut link, spreading.  Leaves J, g, flags ready for interpolation and for the
 // stream-collide that consumes them.
-int launch_interface_phase(iilbm_lattice *h) {
+int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s) {
   if (h->nm == 0) return IILBM_OK;
   const int n = h->nm;
   if (h->ip.model == IILBM_DIRECT) return IILBM_ERR_INVALID_ARG;
-  k_marker_forces<<<(n + 127) / 128, 128, 0, h->stream>>>(h->X, h->aux, n, h->ip, h->cfg.jump,
-                                                          h->geom, h->G, h->Fn, h->P, h->nrm,
-                                                          h->d_status);
-  cudaMemsetAsync(h->d_ncut, 0, sizeof(int), h->stream);
+  uint8_t *flags = h->flagsb[buf];
+  if (cudaMemsetAsync(flags, 0, (size_t)h->ntiles, s) != cudaSuccess) return IILBM_ERR_CUDA;
+  if (cudaMemsetAsync(h->d_ncut, 0, sizeof(int), s) != cudaSuccess) return IILBM_ERR_CUDA;
+  k_marker_forces<<<(n + 127) / 128, 128, 0, s>>>(h->X, h->aux, n, h->ip, h->cfg.jump, h->geom,
+                                                  h->G, h->Fn, h->P, h->nrm, h->d_status);
   const bool dbl = h->cfg.storage == IILBM_F64;
   if (h->cfg.jump) {
     const int threads = 32 * n;
     if (dbl)
-      k_cut_links<double><<<(threads + 255) / 256, 256, 0, h->stream>>>(
-          h->X, h->Fn, n, h->geom, (double *)h->J, h->flags, h->d_ncut);
+      k_cut_links<double><<<(threads + 255) / 256, 256, 0, s>>>(
+          h->X, h->Fn, n, h->geom, (double *)h->Jb[buf], flags, h->d_ncut);
     else
-      k_cut_links<float><<<(threads + 255) / 256, 256, 0, h->stream>>>(
-          h->X, h->Fn, n, h->geom, (float *)h->J, h->flags, h->d_ncut);
+      k_cut_links<float><<<(threads + 255) / 256, 256, 0, s>>>(
+          h->X, h->Fn, n, h->geom, (float *)h->Jb[buf], flags, h->d_ncut);
   }
   const int threads = 16 * n;
   if (dbl)
-    k_spread<double><<<(threads + 255) / 256, 256, 0, h->stream>>>(h->X, h->P, n, h->geom,
-                                                                  (double *)h->g, h->flags);
+    k_spread<double><<<(threads + 255) / 256, 256, 0, s>>>(h->X, h->P, n, h->geom,
+                                                          (double *)h->gb[buf], flags);
   else
-    k_spread<float><<<(threads + 255) / 256, 256, 0, h->stream>>>(h->X, h->P, n, h->geom,
-                                                                 (float *)h->g, h->flags);
+    k_spread<float><<<(threads + 255) / 256, 256, 0, s>>>(h->X, h->P, n, h->geom,
+                                                         (float *)h->gb[buf], flags);
   return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
 }
 

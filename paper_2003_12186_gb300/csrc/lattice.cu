@@ -121,7 +121,7 @@ __device__ __forceinline__ T collide(T f[9], T gx, T gy, const CollP<T> &p) {
 template <typename S, int COLL, bool ODD, int BC>
 __global__ void __launch_bounds__(TILE_X *TILE_Y)
     k_stream_collide(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
-                     typename Store<S>::T *__restrict__ gf, uint8_t *__restrict__ flags,
+                     typename Store<S>::T *__restrict__ gf, const uint8_t *__restrict__ flags,
                      const Geom geo, const CollP<typename Store<S>::T> p, int *status) {
   using T = typename Store<S>::T;
   const int x = blockIdx.x * TILE_X + threadIdx.x;
@@ -186,9 +186,242 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y)
       }
     }
   }
+}
+
+// ------------------------------------------------- vectorised stream-collide
+// Each thread owns V consecutive nodes of one row (V = 4 for FP32 / FP16 / BF16
+// storage, 2 for FP64) and moves every population plane with one 16-byte (8-byte
+// for 16-bit storage) vector access per plane.  A warp covers 32 V consecutive nodes
+// of one row, a block of 8 warps 8 rows.  In the odd step the planes with e_x = +-1
+// are shifted by one node: the aligned vector is loaded (stored) and the one element
+// that crosses into the neighbouring lane travels by warp shuffle; lanes 0 and 31
+// (and the last active lane of a row) fetch / write that element with a scalar
+// access instead, wrapping around the periodic row.  Requires nx % V == 0.
+template <typename S> struct Vec;
+template <> struct Vec<float> {
+  static constexpr int V = 4;
+  __device__ static void ld(const float *p, float *o, float is) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    o[0] = t.x * is; o[1] = t.y * is; o[2] = t.z * is; o[3] = t.w * is;
+  }
+  __device__ static void st(float *p, const float *v, float sc) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0] * sc, v[1] * sc, v[2] * sc, v[3] * sc);
+  }
+};
+template <> struct Vec<double> {
+  static constexpr int V = 2;
+  __device__ static void ld(const double *p, double *o, double is) {
+    const double2 t = *reinterpret_cast<const double2 *>(p);
+    o[0] = t.x * is; o[1] = t.y * is;
+  }
+  __device__ static void st(double *p, const double *v, double sc) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0] * sc, v[1] * sc);
+  }
+};
+template <> struct Vec<__half> {
+  static constexpr int V = 4;
+  __device__ static void ld(const __half *p, float *o, float is) {
+    const uint2 t = *reinterpret_cast<const uint2 *>(p);
+    const __half2 a = *reinterpret_cast<const __half2 *>(&t.x);
+    const __half2 b = *reinterpret_cast<const __half2 *>(&t.y);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    o[0] = fa.x * is; o[1] = fa.y * is; o[2] = fb.x * is; o[3] = fb.y * is;
+  }
+  __device__ static void st(__half *p, const float *v, float sc) {
+    const __half2 a = __floats2half2_rn(v[0] * sc, v[1] * sc);
+    const __half2 b = __floats2half2_rn(v[2] * sc, v[3] * sc);
+    uint2 t;
+    t.x = *reinterpret_cast<const unsigned *>(&a);
+    t.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = t;
+  }
+};
+template <> struct Vec<__nv_bfloat16> {
+  static constexpr int V = 4;
+  __device__ static void ld(const __nv_bfloat16 *p, float *o, float is) {
+    const uint2 t = *reinterpret_cast<const uint2 *>(p);
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&t.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&t.y);
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    o[0] = fa.x * is; o[1] = fa.y * is; o[2] = fb.x * is; o[3] = fb.y * is;
+  }
+  __device__ static void st(__nv_bfloat16 *p, const float *v, float sc) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0] * sc, v[1] * sc);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2] * sc, v[3] * sc);
+    uint2 t;
+    t.x = *reinterpret_cast<const unsigned *>(&a);
+    t.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = t;
+  }
+};
+
+// V consecutive arithmetic values (jump / force fields): float4 or double2.
+template <typename T, int V>
+__device__ inline void ldT(const T *p, T *o) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+  } else {
+    const double2 t = *reinterpret_cast<const double2 *>(p);
+    o[0] = t.x; o[1] = t.y;
+  }
+}
+template <typename T, int V>
+__device__ inline void zeroT(T *p) {
+  if constexpr (sizeof(T) == 4) *reinterpret_cast<float4 *>(p) = make_float4(0.f, 0.f, 0.f, 0.f);
+  else *reinterpret_cast<double2 *>(p) = make_double2(0.0, 0.0);
+}
+
+constexpr int VEC_ROWS = 8;  // warps (rows) per block of the vectorised kernel
+
+template <typename S, int COLL, bool ODD, int BC>
+__global__ void __launch_bounds__(32 * VEC_ROWS)
+    k_stream_collide_vec(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
+                         typename Store<S>::T *__restrict__ gf, const uint8_t *__restrict__ flags,
+                         const Geom geo, const CollP<typename Store<S>::T> p, int *status) {
+  using T = typename Store<S>::T;
+  constexpr int V = Vec<S>::V;
+  const int lane = threadIdx.x & 31;
+  const int y = blockIdx.y * VEC_ROWS + (threadIdx.x >> 5);
+  if (y >= geo.ny) return;  // uniform per warp
+  const int x0 = (blockIdx.x * 32 + lane) * V;
+  const bool active = x0 < geo.nx;
+  const bool edge_r = active && (lane == 31 || x0 + V >= geo.nx);
+  const long long P = geo.plane;
+  int ym = y - 1, yp = y + 1;
+  bool wall_m = false, wall_p = false;
+  if (BC == IILBM_BC_PERIODIC) {
+    ym = y == 0 ? geo.ny - 1 : ym;
+    yp = y == geo.ny - 1 ? 0 : yp;
+  } else {
+    wall_m = y == 0;
+    wall_p = y == geo.ny - 1;
+  }
+  const long long row[3] = {(long long)ym * geo.pitch, (long long)y * geo.pitch,
+                            (long long)yp * geo.pitch};
+  const long long here = row[1] + x0;
+  const int xl = x0 == 0 ? geo.nx - 1 : x0 - 1;      // left neighbour of the chunk
+  const int xr = x0 + V >= geo.nx ? 0 : x0 + V;      // right neighbour of the chunk
+
+  T f[9][V];
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    if (!ODD) {
+      if (active) Vec<S>::ld(A + i * P + here, f[i], p.inv_scale);
+    } else {
+      const bool from_wall = (cy(i) > 0 && wall_m) || (cy(i) < 0 && wall_p);
+      if (from_wall) {
+        if (active) Vec<S>::ld(A + i * P + here, f[i], p.inv_scale);
+      } else {
+        const long long base = opp(i) * P + row[1 - cy(i)];
+        T c[V];
+#pragma unroll
+        for (int j = 0; j < V; j++) c[j] = T(0);
+        if (active) Vec<S>::ld(A + base + x0, c, p.inv_scale);
+        if (cx(i) == 0) {
+#pragma unroll
+          for (int j = 0; j < V; j++) f[i][j] = c[j];
+        } else if (cx(i) > 0) {  // source x - 1
+          T left = __shfl_up_sync(0xffffffffu, c[V - 1], 1);
+          if (active && lane == 0) left = Store<S>::ld(A[base + xl]) * p.inv_scale;
+          f[i][0] = left;
+#pragma unroll
+          for (int j = 1; j < V; j++) f[i][j] = c[j - 1];
+        } else {  // source x + 1
+          T right = __shfl_down_sync(0xffffffffu, c[0], 1);
+          if (edge_r) right = Store<S>::ld(A[base + xr]) * p.inv_scale;
+#pragma unroll
+          for (int j = 0; j < V - 1; j++) f[i][j] = c[j + 1];
+          f[i][V - 1] = right;
+        }
+      }
+    }
+  }
+  if (!active) {
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+#pragma unroll
+      for (int j = 0; j < V; j++) f[i][j] = T(0);
+  }
+  T gx[V], gy[V];
+#pragma unroll
+  for (int j = 0; j < V; j++) { gx[j] = p.bodyx; gy[j] = p.bodyy; }
+  const bool has = active && flags[(y / TILE_Y) * geo.ntx + x0 / TILE_X] != 0;
   if (has) {
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) flags[tile] = 0;
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+      T jv[V];
+      ldT<T, V>(Jf + (i - 1) * P + here, jv);
+      zeroT<T, V>(Jf + (i - 1) * P + here);
+#pragma unroll
+      for (int j = 0; j < V; j++) f[i][j] += jv[j];
+    }
+    T a[V], b[V];
+    ldT<T, V>(gf + here, a);
+    ldT<T, V>(gf + P + here, b);
+    zeroT<T, V>(gf + here);
+    zeroT<T, V>(gf + P + here);
+#pragma unroll
+    for (int j = 0; j < V; j++) { gx[j] += a[j]; gy[j] += b[j]; }
+  }
+  bool finite = true;
+#pragma unroll
+  for (int j = 0; j < V; j++) {
+    T fc[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) fc[i] = f[i][j];
+    const T drho = collide<T, COLL>(fc, gx[j], gy[j], p);
+    finite = finite && isfinite(drho);
+#pragma unroll
+    for (int i = 0; i < 9; i++) f[i][j] = fc[i];
+  }
+  if (active && !finite) atomicOr(status, ST_NONFINITE);
+
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    if (!ODD) {
+      if (active) Vec<S>::st(A + opp(i) * P + here, f[i], p.scale);
+    } else {
+      const bool to_wall = (cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m);
+      if (to_wall) {
+        if (active) Vec<S>::st(A + opp(i) * P + here, f[i], p.scale);
+      } else {
+        const long long base = i * P + row[1 + cy(i)];
+        if (cx(i) == 0) {
+          if (active) Vec<S>::st(A + base + x0, f[i], p.scale);
+        } else if (cx(i) > 0) {  // destination x + 1
+          const T in = __shfl_up_sync(0xffffffffu, f[i][V - 1], 1);
+          if (active) {
+            if (lane != 0) {
+              T v[V];
+              v[0] = in;
+#pragma unroll
+              for (int j = 1; j < V; j++) v[j] = f[i][j - 1];
+              Vec<S>::st(A + base + x0, v, p.scale);
+            } else {
+#pragma unroll
+              for (int j = 0; j < V - 1; j++) A[base + x0 + 1 + j] = Store<S>::st(f[i][j] * p.scale);
+            }
+            if (edge_r) A[base + xr] = Store<S>::st(f[i][V - 1] * p.scale);
+          }
+        } else {  // destination x - 1
+          const T in = __shfl_down_sync(0xffffffffu, f[i][0], 1);
+          if (active) {
+            if (!edge_r) {
+              T v[V];
+#pragma unroll
+              for (int j = 0; j < V - 1; j++) v[j] = f[i][j + 1];
+              v[V - 1] = in;
+              Vec<S>::st(A + base + x0, v, p.scale);
+            } else {
+#pragma unroll
+              for (int j = 1; j < V; j++) A[base + x0 + j - 1] = Store<S>::st(f[i][j] * p.scale);
+            }
+            if (lane == 0) A[base + xl] = Store<S>::st(f[i][0] * p.scale);
+          }
+        }
+      }
+    }
   }
 }
 
@@ -343,14 +576,28 @@ template <typename S, int COLL, bool ODD>
 static void sc_launch(iilbm_lattice *h) {
   using T = typename Store<S>::T;
   const Geom &g = h->geom;
-  dim3 grid(g.ntx, (g.ny + TILE_Y - 1) / TILE_Y), block(TILE_X, TILE_Y);
+  const int b = h->step & 1;
+  T *J = (T *)h->Jb[b], *gf = (T *)h->gb[b];
+  const uint8_t *fl = h->flagsb[b];
   const CollP<T> p = make_collp<T>(h->cfg);
+  constexpr int V = Vec<S>::V;
+  if (h->vector_sc && g.nx % V == 0) {
+    dim3 grid((g.nx + 32 * V - 1) / (32 * V), (g.ny + VEC_ROWS - 1) / VEC_ROWS);
+    if (g.bc == IILBM_BC_PERIODIC)
+      k_stream_collide_vec<S, COLL, ODD, IILBM_BC_PERIODIC><<<grid, 32 * VEC_ROWS, 0, h->stream>>>(
+          (S *)h->A, J, gf, fl, g, p, h->d_status);
+    else
+      k_stream_collide_vec<S, COLL, ODD, IILBM_BC_WALLS_Y><<<grid, 32 * VEC_ROWS, 0, h->stream>>>(
+          (S *)h->A, J, gf, fl, g, p, h->d_status);
+    return;
+  }
+  dim3 grid(g.ntx, (g.ny + TILE_Y - 1) / TILE_Y), block(TILE_X, TILE_Y);
   if (g.bc == IILBM_BC_PERIODIC)
     k_stream_collide<S, COLL, ODD, IILBM_BC_PERIODIC><<<grid, block, 0, h->stream>>>(
-        (S *)h->A, (T *)h->J, (T *)h->g, h->flags, g, p, h->d_status);
+        (S *)h->A, J, gf, fl, g, p, h->d_status);
   else
     k_stream_collide<S, COLL, ODD, IILBM_BC_WALLS_Y><<<grid, block, 0, h->stream>>>(
-        (S *)h->A, (T *)h->J, (T *)h->g, h->flags, g, p, h->d_status);
+        (S *)h->A, J, gf, fl, g, p, h->d_status);
 }
 
 int launch_stream_collide(iilbm_lattice *h) {
@@ -373,9 +620,10 @@ int launch_interp(iilbm_lattice *h) {
     using S = std::remove_pointer_t<decltype(tag)>;
     using T = typename Store<S>::T;
     const int threads = 16 * h->nm;
+    const int b = h->step & 1;
     k_interp<S><<<(threads + 255) / 256, 256, 0, h->stream>>>(
-        (const S *)h->A, (const T *)h->J, (const T *)h->g, h->geom, make_collp<T>(h->cfg), odd,
-        h->X, h->nm, h->U, h->ip.moves);
+        (const S *)h->A, (const T *)h->Jb[b], (const T *)h->gb[b], h->geom,
+        make_collp<T>(h->cfg), odd, h->X, h->nm, h->U, h->ip.moves);
     return last_error();
   });
 }
@@ -386,8 +634,10 @@ int launch_macros(iilbm_lattice *h, double *drho, double *ux, double *uy) {
     using S = std::remove_pointer_t<decltype(tag)>;
     using T = typename Store<S>::T;
     dim3 grid((h->geom.nx + 127) / 128, h->geom.ny);
-    k_macros<S><<<grid, 128, 0, h->stream>>>((const S *)h->A, (const T *)h->J, (const T *)h->g,
-                                             h->geom, make_collp<T>(h->cfg), odd, drho, ux, uy);
+    const int b = h->step & 1;
+    k_macros<S><<<grid, 128, 0, h->stream>>>((const S *)h->A, (const T *)h->Jb[b],
+                                             (const T *)h->gb[b], h->geom, make_collp<T>(h->cfg),
+                                             odd, drho, ux, uy);
     return last_error();
   });
 }

@@ -22,6 +22,7 @@ SRT, MRT = 0, 1
 F64, F32, F16, BF16 = 0, 1, 2, 3
 BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL = 0, 1, 2
 SPRING, SPRING_REST, PRESCRIBED, DIRECT = 0, 1, 2, 3
+OPT_CUDA_GRAPH, OPT_OVERLAP, OPT_VECTOR_KERNEL = 0, 1, 2
 STORAGE = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
 STORAGE_BYTES = {F64: 8, F32: 4, F16: 2, BF16: 2}
 
@@ -66,6 +67,7 @@ SIGNATURES = {
     "iilbm_set_timing": [_H, C.c_int32],
     "iilbm_get_timing": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int32),
                          C.POINTER(C.c_int64)],
+    "iilbm_set_option": [_H, C.c_int32, C.c_int32],
     "iilbm_synchronize": [_H],
     "iilbm_error_string": [C.c_int],
 }
@@ -253,6 +255,11 @@ class Lattice:
         _check("iilbm_get_timing",
                self._L.iilbm_get_timing(self._h, C.byref(ms), C.byref(n), C.byref(k)))
         return ms.value, n.value, k.value
+
+    def iilbm_set_option(self, option, value):
+        _check("iilbm_set_option", self._L.iilbm_set_option(self._h, int(option), int(value)))
+
+    set_option = iilbm_set_option
 
     def iilbm_synchronize(self):
         _check("iilbm_synchronize", self._L.iilbm_synchronize(self._h))

@@ -1,0 +1,92 @@
+"""Execution variants of the CUDA path give the same results: the vectorised and the
+one-node-per-thread stream-collide (bitwise), CUDA-graph replay and eager launches,
+the overlapped and the serial interface phase; kernel timing works in both modes."""
+import numpy as np
+import pytest
+
+from paper_2003_12186_gb300 import iilbm
+from paper_2003_12186_gb300 import workloads as W
+
+from _pair import make_pair, set_membrane, vel_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    iilbm.load()
+
+
+def _lat(nx, ny, storage, collision, bc, **kw):
+    return iilbm.Lattice(nx, ny, collision=iilbm.SRT if collision == "srt" else iilbm.MRT,
+                         storage=storage, tau=0.7, s=W.mrt_rates(0.7),
+                         bc=iilbm.BC_PERIODIC if bc == "periodic" else iilbm.BC_WALLS_Y,
+                         body=(1e-5, -3e-6), **kw)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64", "f16", "bf16"])
+@pytest.mark.parametrize("bc", ["periodic", "walls"])
+@pytest.mark.parametrize("shape", [(256, 24), (100, 13), (36, 9), (128, 40)])
+def test_vector_kernel_matches_scalar_bitwise(storage, bc, shape):
+    nx, ny = shape
+    df = W.random_df(nx, ny, 2e-3, nx + ny)
+    out = []
+    for vec in (0, 1):
+        g = _lat(nx, ny, storage, "mrt", bc)
+        g.set_option(iilbm.OPT_VECTOR_KERNEL, vec)
+        g.set_populations(df)
+        res = []
+        for n in (1, 1, 2, 3):  # both parities, several times
+            g.step(n)
+            res.append(g.get_populations())
+        out.append(res)
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_graph_and_overlap_match_eager(orc, storage):
+    """70 steps (two 32-step graph replays plus eager steps) of a moving membrane, in
+    every combination of graph / overlap, agree with each other and with the oracle."""
+    w = W.ellipse_scaled(256, storage)
+    ref = None
+    for graph, overlap in ((0, 0), (1, 0), (0, 1), (1, 1)):
+        g, o = make_pair(orc, 256, 256, collision="mrt", storage=storage, tau=w["tau"])
+        g.set_option(iilbm.OPT_CUDA_GRAPH, graph)
+        g.set_option(iilbm.OPT_OVERLAP, overlap)
+        set_membrane(orc, g, o, w["X"], "spring", w["kappa"], w["dX"])
+        g.step(3)
+        g.step(67)
+        d = g.get_populations()
+        X = g.get_markers()["X"]
+        if ref is None:
+            o.step(70)
+            umax = np.abs(o.markers()["U"]).max()
+            tol = 1e-12 if storage == "f64" else 1e-5
+            assert vel_error(g, o, max(umax, 1e-6)) < tol
+            assert np.abs(X - o.markers()["X"]).max() < (1e-12 if storage == "f64" else 1e-7)
+            ref = (d, X)
+        else:
+            scale = np.abs(ref[0]).max()
+            tol = 1e-13 if storage == "f64" else 1e-5
+            assert np.abs(d - ref[0]).max() < tol * scale
+            assert np.abs(X - ref[1]).max() < (1e-13 if storage == "f64" else 1e-7)
+
+
+def test_timing_counts_launches_in_graph_and_eager_modes():
+    w = W.ellipse_scaled(256, "f32")
+    g = iilbm.Lattice(256, 256, collision=iilbm.MRT, storage="f32", tau=w["tau"])
+    g.set_interface(w["X"], model=iilbm.SPRING, stiffness=w["kappa"], dX=w["dX"])
+    g.step(2)
+    g.iilbm_set_timing(True)
+    g.step(64 + 5)
+    ms, n, k = g.iilbm_get_timing()
+    assert n == 69 and k == 69 * 5 and 0 < ms < 69 * 10.0
+    g.iilbm_set_option(iilbm.OPT_CUDA_GRAPH, 0)
+    g.iilbm_set_timing(True)
+    g.step(7)
+    ms, n, k = g.iilbm_get_timing()
+    assert n == 7 and ms > 0

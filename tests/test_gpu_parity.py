@@ -92,23 +92,38 @@ def test_membrane64_fp64_step_by_step(orc):
 
 
 def test_membrane64_fp64_full_run(orc):
-    """All 2000 steps of the 64^2 FP64 membrane: velocity within 1e-12 (relative to
-    the run's largest marker speed), markers within 1e-12; the Laplace pressure jump
-    and the area drift are reported alongside."""
+    """All 2000 steps of the 64^2 FP64 membrane against the oracle.
+
+    Relative velocity error = |u_gpu - u_oracle|_inf / max(|u_oracle|_inf, U_ref), U_ref
+    the run's largest marker speed.  Bar: 1e-12 up to 100 steps.  Over 2000 steps the
+    problem itself amplifies rounding: two oracle runs whose markers differ by one ulp
+    drift apart by ~1.7e-12 (the spring tension is a small difference l/l0 - 1 and the
+    net marker force a small difference of tensions).  The GPU must stay within twice
+    that conditioning floor, measured here on the oracle."""
     w = W.membrane_64()
     g, o = make_pair(orc, 64, 64, collision="srt", storage="f64", tau=w["tau"])
     set_membrane(orc, g, o, w["X"], "spring_rest", w["kappa"], w["dX"], w["l0"])
+    o2 = orc.Oracle(64, 64, collision=orc.SRT, tau=w["tau"])
+    o2.set_interface(np.nextafter(w["X"], np.inf), model=orc.SPRING_REST, kappa=w["kappa"],
+                     dX=w["dX"], l0=w["l0"])
     umax = 0.0
-    for _ in range(20):
+    for k in range(20):
         g.step(100)
         o.step(100)
+        o2.step(100)
         umax = max(umax, np.abs(o.markers()["U"]).max())
+        if k == 0:
+            assert vel_error(g, o, max(umax, 1e-6)) < 1e-12
     err = vel_error(g, o, max(umax, 1e-6))
+    _, uo, vo = o.current_macros()
+    _, u2, v2 = o2.current_macros()
+    floor = max(np.abs(uo - u2).max(), np.abs(vo - v2).max()) / max(np.abs(uo).max(), umax)
     mg, mo = g.get_markers(), o.markers()
-    assert err < 1e-12, err
-    assert np.abs(mg["X"] - mo["X"]).max() < 1e-12
     a = orc.polygon_area(mg["X"]) / orc.polygon_area(w["X"]) - 1
-    print(f"membrane64 fp64: rel vel err {err:.3e}, area drift {a:.3e}")
+    print(f"membrane64 fp64 2000 steps: rel vel err {err:.3e}, one-ulp floor {floor:.3e}, "
+          f"area drift {a:.3e}")
+    assert err < 2 * floor + 1e-13, (err, floor)
+    assert np.abs(mg["X"] - mo["X"]).max() < 1e-12
 
 
 @pytest.mark.parametrize("collision", ["srt", "mrt"])

@@ -133,13 +133,15 @@ int iilbm_get_mdf_stats(iilbm_t h, int32_t *iters, double *residual);
 int iilbm_get_cut_link_count(iilbm_t h, int32_t *count);
 
 /* Kernel timing (diagnostic).  enable = 1 starts recording a CUDA event pair around
- * every stream-collide launch on the handle's stream and counting every kernel the
- * library launches; enable = 0 stops.  iilbm_get_timing synchronises, returns the
- * summed stream-collide device time (ms), its launch count and the number of
- * library kernels launched since timing was enabled, then resets all three. */
+ * every launch of the lean stream-collide (all tiles without a jump or force) on the
+ * handle's stream and counting every kernel the library launches; enable = 0 stops.
+ * iilbm_get_timing synchronises, returns the summed lean stream-collide device time
+ * (ms), its launch count, the number of library kernels launched, and the number of
+ * flagged tiles (128 x 8 nodes each, handed to the forced kernel instead) summed over
+ * the interface phases run since timing was enabled, then resets them. */
 int iilbm_set_timing(iilbm_t h, int32_t enable);
 int iilbm_get_timing(iilbm_t h, double *stream_collide_ms, int32_t *stream_collide_launches,
-                     int64_t *kernel_launches);
+                     int64_t *kernel_launches, int64_t *flagged_tiles);
 
 /* Execution options (all on by default; for A/B measurements and tests):
  *  IILBM_OPT_CUDA_GRAPH     replay blocks of steps from one captured CUDA graph;

@@ -2,6 +2,7 @@
 // memory ownership, and the order of the kernels of one II-LBM time step.
 #include "iilbm_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -11,9 +12,14 @@ using namespace iilbm;
 
 namespace {
 
-#define CK(call)                                   \
-  do {                                             \
-    if ((call) != cudaSuccess) return IILBM_ERR_CUDA; \
+// On failure, clear the runtime's last-error slot too, so a failed call never
+// surfaces again from a later, unrelated launch check.
+#define CK(call)                         \
+  do {                                   \
+    if ((call) != cudaSuccess) {         \
+      cudaGetLastError();                \
+      return IILBM_ERR_CUDA;             \
+    }                                    \
   } while (0)
 
 size_t storage_bytes(int s) {
@@ -75,6 +81,7 @@ int clear_fields(iilbm_lattice *h) {
     CK(cudaMemsetAsync(h->Jb[b], 0, 8 * (size_t)g.plane * h->tbytes, h->stream));
     CK(cudaMemsetAsync(h->gb[b], 0, 2 * (size_t)g.plane * h->tbytes, h->stream));
     CK(cudaMemsetAsync(h->flagsb[b], 0, (size_t)h->ntiles, h->stream));
+    CK(cudaMemsetAsync(h->tile_count[b], 0, sizeof(int), h->stream));
   }
   h->prepared = false;
   return IILBM_OK;
@@ -149,16 +156,24 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
   h->vector_sc = true;
   h->overlap = true;
   h->use_graph = true;
-  bool ok = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess &&
+  h->forced_grid = std::max(1, std::min(h->ntiles, 2 * prop.multiProcessorCount));
+  // The side stream (forced tiles, next interface phase) runs at the highest priority
+  // so its few blocks are dispatched ahead of the lean stream-collide's backlog.
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  bool ok = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
             cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess &&
             cudaMalloc(&h->A, 9 * (size_t)g.plane * h->sbytes) == cudaSuccess &&
             cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&h->d_ncut, sizeof(int)) == cudaSuccess;
+            cudaMalloc(&h->d_ncut, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->d_tiles_total, sizeof(unsigned long long)) == cudaSuccess;
   for (int b = 0; b < 2 && ok; b++)
     ok = cudaMalloc(&h->Jb[b], 8 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
          cudaMalloc(&h->gb[b], 2 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
-         cudaMalloc(&h->flagsb[b], (size_t)h->ntiles) == cudaSuccess;
+         cudaMalloc(&h->flagsb[b], (size_t)h->ntiles) == cudaSuccess &&
+         cudaMalloc(&h->tile_list[b], (size_t)h->ntiles * sizeof(int)) == cudaSuccess &&
+         cudaMalloc(&h->tile_count[b], sizeof(int)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     iilbm_destroy(h);
@@ -167,7 +182,8 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
   int rc = IILBM_OK;
   if (cudaMemsetAsync(h->A, 0, 9 * (size_t)g.plane * h->sbytes, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream) != cudaSuccess ||
-      cudaMemsetAsync(h->d_ncut, 0, sizeof(int), h->stream) != cudaSuccess)
+      cudaMemsetAsync(h->d_ncut, 0, sizeof(int), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->d_tiles_total, 0, sizeof(unsigned long long), h->stream) != cudaSuccess)
     rc = IILBM_ERR_CUDA;
   if (!rc) rc = clear_fields(h);
   if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = IILBM_ERR_CUDA;
@@ -186,7 +202,8 @@ int iilbm_destroy(iilbm_t h) {
   drop_graph(h);
   free_interface(h);
   void *bufs[] = {h->A, h->Jb[0], h->Jb[1], h->gb[0], h->gb[1], h->flagsb[0], h->flagsb[1],
-                  h->d_status, h->d_ncut};
+                  h->tile_list[0], h->tile_list[1], h->tile_count[0], h->tile_count[1],
+                  h->d_status, h->d_ncut, h->d_tiles_total};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -320,19 +337,22 @@ int drain_events(iilbm_lattice *h) {
   return IILBM_OK;
 }
 
-// Kernels launched by one step: interface phase (forces, cut links if the jump is
-// on, spread) when an interface exists, interpolation, stream-collide.
+// Kernels launched by one step: lean stream-collide; with an interface also the
+// interface phase (forces, cut links if the jump is on, spread, tile list), the
+// interpolation and the forced stream-collide.
 long long kernels_per_step(const iilbm_lattice *h) {
-  return 1 + (h->nm > 0 ? 2 + (h->cfg.jump ? 1 : 0) + 1 : 0);
+  return 1 + (h->nm > 0 ? 3 + (h->cfg.jump ? 1 : 0) + 1 + 1 : 0);
 }
 
 bool pipelined(const iilbm_lattice *h) { return h->overlap && h->nm > 0; }
 
 // One time step of the current state n (its interface already prepared in buffer
-// n & 1).  Main stream: interpolation (+ marker move), stream-collide.  With overlap,
-// the interface phase of state n + 1 (buffer (n+1) & 1) forks to the side stream
-// right after the interpolation -- it needs only X^{n+1} -- and joins before the
-// step ends.  Safe inside stream capture.
+// n & 1).  Main stream: interpolation (+ marker move), lean stream-collide.  With
+// overlap, the side stream (highest priority) forks right after the interpolation and
+// runs the forced stream-collide of the flagged tiles, then the interface phase of
+// state n + 1 (buffer (n+1) & 1) -- which needs only X^{n+1} -- and joins before the
+// step ends.  Without overlap everything runs in that order on the main stream.  Safe
+// inside stream capture.
 int one_step(iilbm_lattice *h, int ev_slot) {
   int rc;
   if ((rc = launch_interp(h))) return rc;
@@ -340,15 +360,19 @@ int one_step(iilbm_lattice *h, int ev_slot) {
   if (pipe) {
     CK(cudaEventRecord(h->ev_fork, h->stream));
     CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+  }
+  // Timing events: inside a stream capture they must become event-record nodes of the
+  // graph (cudaEventRecordExternal); outside a capture they are plain records.
+  const unsigned evflag = h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (ev_slot >= 0) CK(cudaEventRecordWithFlags(h->ev[2 * ev_slot], h->stream, evflag));
+  if ((rc = launch_stream_collide(h, pipe ? h->side : h->stream))) return rc;
+  if (ev_slot >= 0) CK(cudaEventRecordWithFlags(h->ev[2 * ev_slot + 1], h->stream, evflag));
+  if (pipe) {
     rc = launch_interface_phase(h, (int)((h->step + 1) & 1), h->side);  // state n + 1
     if (rc) return rc;
     CK(cudaEventRecord(h->ev_join, h->side));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   }
-  if (ev_slot >= 0) CK(cudaEventRecordWithFlags(h->ev[2 * ev_slot], h->stream, cudaEventRecordExternal));
-  if ((rc = launch_stream_collide(h))) return rc;
-  if (ev_slot >= 0)
-    CK(cudaEventRecordWithFlags(h->ev[2 * ev_slot + 1], h->stream, cudaEventRecordExternal));
-  if (pipe) CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   h->step++;
   h->prepared = pipe || h->nm == 0;
   return IILBM_OK;
@@ -361,8 +385,11 @@ int capture_graph(iilbm_lattice *h) {
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   int rc = IILBM_OK;
+  h->capturing = true;
   for (int k = 0; k < GRAPH_STEPS && !rc; k++) rc = one_step(h, h->timing ? k : -1);
+  h->capturing = false;
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  cudaGetLastError();
   h->step = step0;
   h->prepared = true;
   if (rc) {
@@ -370,7 +397,8 @@ int capture_graph(iilbm_lattice *h) {
     return rc;
   }
   if (e != cudaSuccess) return IILBM_ERR_CUDA;
-  e = cudaGraphInstantiate(&h->gexec, graph, 0);
+  // honour the side stream's priority inside the graph
+  e = cudaGraphInstantiateWithFlags(&h->gexec, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     h->gexec = nullptr;
@@ -434,6 +462,7 @@ int iilbm_set_option(iilbm_t h, int32_t option, int32_t value) {
 
 int iilbm_set_timing(iilbm_t h, int32_t enable) {
   if (!h) return IILBM_ERR_INVALID_ARG;
+  CK(cudaMemsetAsync(h->d_tiles_total, 0, sizeof(unsigned long long), h->stream));
   if (enable && !h->ev[0])
     for (int e = 0; e < 2 * 256; e++) CK(cudaEventCreate(&h->ev[e]));
   if (!enable && h->nev) {
@@ -444,17 +473,24 @@ int iilbm_set_timing(iilbm_t h, int32_t enable) {
   return IILBM_OK;
 }
 
-int iilbm_get_timing(iilbm_t h, double *sc_ms, int32_t *launches, int64_t *kernel_launches) {
+int iilbm_get_timing(iilbm_t h, double *sc_ms, int32_t *launches, int64_t *kernel_launches,
+                     int64_t *flagged_tiles) {
   if (!h) return IILBM_ERR_INVALID_ARG;
   int rc = drain_events(h);
   if (rc) return rc;
+  unsigned long long tiles = 0;
+  CK(cudaStreamSynchronize(h->side));
+  CK(cudaMemcpyAsync(&tiles, h->d_tiles_total, sizeof tiles, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemsetAsync(h->d_tiles_total, 0, sizeof tiles, h->stream));
+  if ((rc = read_status(h))) return rc;
   if (sc_ms) *sc_ms = h->sc_ms;
   if (launches) *launches = h->sc_launches;
   if (kernel_launches) *kernel_launches = h->kernel_launches;
+  if (flagged_tiles) *flagged_tiles = (int64_t)tiles;
   h->sc_ms = 0;
   h->sc_launches = 0;
   h->kernel_launches = 0;
-  return read_status(h);
+  return IILBM_OK;
 }
 
 int iilbm_get_macros(iilbm_t h, double *drho, double *ux, double *uy) {

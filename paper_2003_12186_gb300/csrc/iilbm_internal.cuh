@@ -31,9 +31,9 @@ __host__ __device__ constexpr T wt(int i) {
 static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "opp axis");
 static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp diag");
 
-// Force / jump tiles: the stream-collide kernel's thread block covers one tile of
-// TILE_X x TILE_Y nodes; a per-tile byte flags tiles that carry a jump or a force.
-constexpr int TILE_X = 32;
+// Force / jump tiles of TILE_X x TILE_Y nodes: a per-tile byte flags tiles that carry
+// a jump or a spread force; a tile is one block of the vectorised stream-collide.
+constexpr int TILE_X = 128;
 constexpr int TILE_Y = 8;
 
 // Device status bits (latched, read back by synchronising calls).
@@ -123,7 +123,11 @@ struct iilbm_lattice {
   void *Jb[2];
   void *gb[2];
   uint8_t *flagsb[2];
+  int *tile_list[2];  // flagged tiles of each buffer, compacted by the interface phase
+  int *tile_count[2];
+  unsigned long long *d_tiles_total;  // flagged tiles summed while timing
   int ntiles;
+  int forced_grid;    // blocks of the forced stream-collide (strides over the list)
   // execution
   bool vector_sc;     // vectorised stream-collide when nx is a multiple of its width
   bool overlap;       // next interface phase on the side stream during stream-collide
@@ -132,6 +136,7 @@ struct iilbm_lattice {
   cudaEvent_t ev_fork, ev_join;
   cudaGraphExec_t gexec;
   bool graph_timing;  // the instantiated graph records timing events
+  bool capturing;     // inside cudaStreamBeginCapture / EndCapture
   long long step;     // time level of the state; AA parity = step & 1
   bool prepared;      // jump / force of the current state already in J, g
   int *d_status;      // latched device status bits
@@ -154,7 +159,7 @@ struct iilbm_lattice {
 
 // Launchers (defined in lattice.cu / interface.cu).
 namespace iilbm {
-int launch_stream_collide(iilbm_lattice *h);
+int launch_stream_collide(iilbm_lattice *h, cudaStream_t forced_stream);
 int launch_interp(iilbm_lattice *h);
 int launch_macros(iilbm_lattice *h, double *drho, double *ux, double *uy);
 int launch_set_populations(iilbm_lattice *h, const double *df, bool equilibrium,

@@ -7,8 +7,9 @@
 //     Eq. 32 to the jump field of the destination node (Eq. 47);
 //   * spreading of the tangential force with Peskin's four-point kernel (Eq. 46),
 //     16 threads per marker, into the force field.
-// Both fields are dense [.][ny][pitch] arrays that only flagged 32 x 8 tiles touch;
-// the stream-collide kernel consumes and re-zeroes the flagged tiles.
+// Both fields are dense [.][ny][pitch] arrays that only flagged tiles touch; the
+// flagged tiles are listed for the forced stream-collide, which consumes and
+// re-zeroes them.
 #include "iilbm_internal.cuh"
 
 #include <cmath>
@@ -184,6 +185,22 @@ __global__ void k_spread(const double *__restrict__ X, const double *__restrict_
   flags[tile_of(geo, xi, yi)] = 1;
 }
 
+// ------------------------------------------------------------- tile list
+// Compact the flagged tiles into a list for the forced stream-collide.
+__global__ void k_tile_list(const uint8_t *__restrict__ flags, int ntiles, int *list, int *count,
+                            unsigned long long *total) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool f = t < ntiles && flags[t] != 0;
+  const unsigned m = __ballot_sync(0xffffffffu, f);
+  int base = 0;
+  if ((threadIdx.x & 31) == 0 && m) {
+    base = atomicAdd(count, __popc(m));
+    atomicAdd(total, (unsigned long long)__popc(m));
+  }
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (f) list[base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = t;
+}
+
 // ---------------------------------------------------------- interface phase
 // Items 1-3 of the step for the current state: marker forces and split, the jump on
 // every cut link, spreading.  Leaves J, g, flags ready for interpolation and for the
@@ -193,8 +210,12 @@ int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s) {
   const int n = h->nm;
   if (h->ip.model == IILBM_DIRECT) return IILBM_ERR_INVALID_ARG;
   uint8_t *flags = h->flagsb[buf];
-  if (cudaMemsetAsync(flags, 0, (size_t)h->ntiles, s) != cudaSuccess) return IILBM_ERR_CUDA;
-  if (cudaMemsetAsync(h->d_ncut, 0, sizeof(int), s) != cudaSuccess) return IILBM_ERR_CUDA;
+  if (cudaMemsetAsync(flags, 0, (size_t)h->ntiles, s) != cudaSuccess ||
+      cudaMemsetAsync(h->d_ncut, 0, sizeof(int), s) != cudaSuccess ||
+      cudaMemsetAsync(h->tile_count[buf], 0, sizeof(int), s) != cudaSuccess) {
+    cudaGetLastError();
+    return IILBM_ERR_CUDA;
+  }
   k_marker_forces<<<(n + 127) / 128, 128, 0, s>>>(h->X, h->aux, n, h->ip, h->cfg.jump, h->geom,
                                                   h->G, h->Fn, h->P, h->nrm, h->d_status);
   const bool dbl = h->cfg.storage == IILBM_F64;
@@ -214,6 +235,8 @@ int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s) {
   else
     k_spread<float><<<(threads + 255) / 256, 256, 0, s>>>(h->X, h->P, n, h->geom,
                                                          (float *)h->gb[buf], flags);
+  k_tile_list<<<(h->ntiles + 255) / 256, 256, 0, s>>>(flags, h->ntiles, h->tile_list[buf],
+                                                      h->tile_count[buf], h->d_tiles_total);
   return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
 }
 

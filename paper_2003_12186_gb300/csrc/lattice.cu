@@ -116,79 +116,15 @@ __device__ __forceinline__ T collide(T f[9], T gx, T gy, const CollP<T> &p) {
 }
 
 // -------------------------------------------------------------- stream-collide
-// One thread per node, one 32 x 8 block per tile.  BC is IILBM_BC_PERIODIC or
-// IILBM_BC_WALLS_Y (periodic x, halfway bounce-back in y).
-template <typename S, int COLL, bool ODD, int BC>
-__global__ void __launch_bounds__(TILE_X *TILE_Y)
-    k_stream_collide(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
-                     typename Store<S>::T *__restrict__ gf, const uint8_t *__restrict__ flags,
-                     const Geom geo, const CollP<typename Store<S>::T> p, int *status) {
-  using T = typename Store<S>::T;
-  const int x = blockIdx.x * TILE_X + threadIdx.x;
-  const int y = blockIdx.y * TILE_Y + threadIdx.y;
-  const int tile = blockIdx.y * geo.ntx + blockIdx.x;
-  const bool has = flags[tile] != 0;
-  if (x < geo.nx && y < geo.ny) {
-    const long long P = geo.plane;
-    const long long here = (long long)y * geo.pitch + x;
-    // neighbour rows / columns (wrapped); wall rows flagged
-    const int xm = x == 0 ? geo.nx - 1 : x - 1;
-    const int xp = x == geo.nx - 1 ? 0 : x + 1;
-    int ym = y - 1, yp = y + 1;
-    bool wall_m = false, wall_p = false;
-    if (BC == IILBM_BC_PERIODIC) {
-      ym = y == 0 ? geo.ny - 1 : ym;
-      yp = y == geo.ny - 1 ? 0 : yp;
-    } else {
-      wall_m = y == 0;
-      wall_p = y == geo.ny - 1;
-    }
-    const long long col[3] = {xm, x, xp};
-    const long long row[3] = {(long long)ym * geo.pitch, (long long)y * geo.pitch,
-                              (long long)yp * geo.pitch};
-    T f[9];
-    if (!ODD) {
-#pragma unroll
-      for (int i = 0; i < 9; i++) f[i] = Store<S>::ld(A[i * P + here]) * p.inv_scale;
-    } else {
-#pragma unroll
-      for (int i = 0; i < 9; i++) {
-        const bool from_wall = (cy(i) > 0 && wall_m) || (cy(i) < 0 && wall_p);
-        const long long src = from_wall ? i * P + here
-                                        : opp(i) * P + row[1 - cy(i)] + col[1 - cx(i)];
-        f[i] = Store<S>::ld(A[src]) * p.inv_scale;
-      }
-    }
-    T gx = p.bodyx, gy = p.bodyy;
-    if (has) {
-#pragma unroll
-      for (int i = 1; i < 9; i++) {
-        f[i] += Jf[(i - 1) * P + here];
-        Jf[(i - 1) * P + here] = T(0);
-      }
-      gx += gf[here];
-      gy += gf[P + here];
-      gf[here] = T(0);
-      gf[P + here] = T(0);
-    }
-    const T drho = collide<T, COLL>(f, gx, gy, p);
-    if (!isfinite(drho)) atomicOr(status, ST_NONFINITE);
-    if (!ODD) {
-#pragma unroll
-      for (int i = 0; i < 9; i++) A[opp(i) * P + here] = Store<S>::st(f[i] * p.scale);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 9; i++) {
-        const bool to_wall = (cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m);
-        const long long dst = to_wall ? opp(i) * P + here
-                                      : i * P + row[1 + cy(i)] + col[1 + cx(i)];
-        A[dst] = Store<S>::st(f[i] * p.scale);
-      }
-    }
-  }
-}
+// The stream-collide is split by tile.  Tiles (TILE_X x TILE_Y nodes) that carry no
+// jump and no spread force -- all but O(interface length) of them -- go through a
+// lean kernel with no jump / force code at all, which keeps its register count and
+// so its memory parallelism high.  The flagged tiles are listed by the interface phase
+// and processed by a "forced" kernel that adds the jump of Eq. 47 and the spread
+// force of Eq. 46 (and re-zeroes both fields).  Under the AA pattern every population
+// slot is read and written by one and the same node, so the two kernels touch
+// disjoint slots and may run in either order or concurrently.
 
-// ------------------------------------------------- vectorised stream-collide
 // Each thread owns V consecutive nodes of one row (V = 4 for FP32 / FP16 / BF16
 // storage, 2 for FP64) and moves every population plane with one 16-byte (8-byte
 // for 16-bit storage) vector access per plane.  A warp covers 32 V consecutive nodes
@@ -272,19 +208,91 @@ __device__ inline void zeroT(T *p) {
   else *reinterpret_cast<double2 *>(p) = make_double2(0.0, 0.0);
 }
 
-constexpr int VEC_ROWS = 8;  // warps (rows) per block of the vectorised kernel
 
-template <typename S, int COLL, bool ODD, int BC>
-__global__ void __launch_bounds__(32 * VEC_ROWS)
-    k_stream_collide_vec(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
-                         typename Store<S>::T *__restrict__ gf, const uint8_t *__restrict__ flags,
-                         const Geom geo, const CollP<typename Store<S>::T> p, int *status) {
+// One node per thread on a 32 x TILE_Y sub-block whose first node is (xb, yb).  BC is
+// IILBM_BC_PERIODIC or IILBM_BC_WALLS_Y (periodic x, halfway bounce-back in y).
+template <typename S, int COLL, bool ODD, int BC, bool FORCED>
+__device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
+                                                typename Store<S>::T *__restrict__ Jf,
+                                                typename Store<S>::T *__restrict__ gf,
+                                                const Geom &geo,
+                                                const CollP<typename Store<S>::T> &p, int *status,
+                                                int xb, int yb) {
+  using T = typename Store<S>::T;
+  const int x = xb + threadIdx.x, y = yb + threadIdx.y;
+  if (x >= geo.nx || y >= geo.ny) return;
+  const long long P = geo.plane;
+  const long long here = (long long)y * geo.pitch + x;
+  const int xm = x == 0 ? geo.nx - 1 : x - 1;
+  const int xp = x == geo.nx - 1 ? 0 : x + 1;
+  int ym = y - 1, yp = y + 1;
+  bool wall_m = false, wall_p = false;
+  if (BC == IILBM_BC_PERIODIC) {
+    ym = y == 0 ? geo.ny - 1 : ym;
+    yp = y == geo.ny - 1 ? 0 : yp;
+  } else {
+    wall_m = y == 0;
+    wall_p = y == geo.ny - 1;
+  }
+  const long long col[3] = {xm, x, xp};
+  const long long row[3] = {(long long)ym * geo.pitch, (long long)y * geo.pitch,
+                            (long long)yp * geo.pitch};
+  T f[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    long long src = i * P + here;
+    if (ODD) {
+      const bool from_wall = (cy(i) > 0 && wall_m) || (cy(i) < 0 && wall_p);
+      if (!from_wall) src = opp(i) * P + row[1 - cy(i)] + col[1 - cx(i)];
+    }
+    f[i] = Store<S>::ld(A[src]) * p.inv_scale;
+  }
+  T gx = p.bodyx, gy = p.bodyy;
+  if (FORCED) {
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+      f[i] += Jf[(i - 1) * P + here];
+      Jf[(i - 1) * P + here] = T(0);
+    }
+    gx += gf[here];
+    gy += gf[P + here];
+    gf[here] = T(0);
+    gf[P + here] = T(0);
+  }
+  const T drho = collide<T, COLL>(f, gx, gy, p);
+  if (!isfinite(drho)) atomicOr(status, ST_NONFINITE);
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    long long dst = opp(i) * P + here;
+    if (ODD) {
+      const bool to_wall = (cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m);
+      if (!to_wall) dst = i * P + row[1 + cy(i)] + col[1 + cx(i)];
+    }
+    A[dst] = Store<S>::st(f[i] * p.scale);
+  }
+}
+
+// Vectorised: each thread owns V consecutive nodes of one row (V = 4 for FP32 /
+// FP16 / BF16 storage, 2 for FP64) and moves every population plane with one 16-byte
+// (8-byte for 16-bit storage) access.  A warp covers 32 V nodes of row yb + warp, the
+// first at xb.  In the odd step the planes with e_x = +-1 are shifted by one node: the
+// aligned vector is loaded (stored) and the single element that crosses into the
+// neighbouring lane travels by warp shuffle; lane 0, lane 31 and the last active lane
+// of a row fetch / write that element with a scalar access instead, wrapping around
+// the periodic row.  Requires nx % V == 0.  Every lane of the warp must call this.
+template <typename S, int COLL, bool ODD, int BC, bool FORCED>
+__device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
+                                             typename Store<S>::T *__restrict__ Jf,
+                                             typename Store<S>::T *__restrict__ gf,
+                                             const Geom &geo,
+                                             const CollP<typename Store<S>::T> &p, int *status,
+                                             int xb, int yb) {
   using T = typename Store<S>::T;
   constexpr int V = Vec<S>::V;
   const int lane = threadIdx.x & 31;
-  const int y = blockIdx.y * VEC_ROWS + (threadIdx.x >> 5);
+  const int y = yb + (threadIdx.x >> 5);
   if (y >= geo.ny) return;  // uniform per warp
-  const int x0 = (blockIdx.x * 32 + lane) * V;
+  const int x0 = xb + lane * V;
   const bool active = x0 < geo.nx;
   const bool edge_r = active && (lane == 31 || x0 + V >= geo.nx);
   const long long P = geo.plane;
@@ -306,48 +314,39 @@ __global__ void __launch_bounds__(32 * VEC_ROWS)
   T f[9][V];
 #pragma unroll
   for (int i = 0; i < 9; i++) {
-    if (!ODD) {
+#pragma unroll
+    for (int j = 0; j < V; j++) f[i][j] = T(0);
+    const bool from_wall = ODD && ((cy(i) > 0 && wall_m) || (cy(i) < 0 && wall_p));
+    if (!ODD || from_wall) {
       if (active) Vec<S>::ld(A + i * P + here, f[i], p.inv_scale);
     } else {
-      const bool from_wall = (cy(i) > 0 && wall_m) || (cy(i) < 0 && wall_p);
-      if (from_wall) {
-        if (active) Vec<S>::ld(A + i * P + here, f[i], p.inv_scale);
-      } else {
-        const long long base = opp(i) * P + row[1 - cy(i)];
-        T c[V];
+      const long long base = opp(i) * P + row[1 - cy(i)];
+      T c[V];
 #pragma unroll
-        for (int j = 0; j < V; j++) c[j] = T(0);
-        if (active) Vec<S>::ld(A + base + x0, c, p.inv_scale);
-        if (cx(i) == 0) {
+      for (int j = 0; j < V; j++) c[j] = T(0);
+      if (active) Vec<S>::ld(A + base + x0, c, p.inv_scale);
+      if (cx(i) == 0) {
 #pragma unroll
-          for (int j = 0; j < V; j++) f[i][j] = c[j];
-        } else if (cx(i) > 0) {  // source x - 1
-          T left = __shfl_up_sync(0xffffffffu, c[V - 1], 1);
-          if (active && lane == 0) left = Store<S>::ld(A[base + xl]) * p.inv_scale;
-          f[i][0] = left;
+        for (int j = 0; j < V; j++) f[i][j] = c[j];
+      } else if (cx(i) > 0) {  // source x - 1
+        T left = __shfl_up_sync(0xffffffffu, c[V - 1], 1);
+        if (active && lane == 0) left = Store<S>::ld(A[base + xl]) * p.inv_scale;
+        f[i][0] = left;
 #pragma unroll
-          for (int j = 1; j < V; j++) f[i][j] = c[j - 1];
-        } else {  // source x + 1
-          T right = __shfl_down_sync(0xffffffffu, c[0], 1);
-          if (edge_r) right = Store<S>::ld(A[base + xr]) * p.inv_scale;
+        for (int j = 1; j < V; j++) f[i][j] = c[j - 1];
+      } else {  // source x + 1
+        T right = __shfl_down_sync(0xffffffffu, c[0], 1);
+        if (edge_r) right = Store<S>::ld(A[base + xr]) * p.inv_scale;
 #pragma unroll
-          for (int j = 0; j < V - 1; j++) f[i][j] = c[j + 1];
-          f[i][V - 1] = right;
-        }
+        for (int j = 0; j < V - 1; j++) f[i][j] = c[j + 1];
+        f[i][V - 1] = right;
       }
     }
-  }
-  if (!active) {
-#pragma unroll
-    for (int i = 0; i < 9; i++)
-#pragma unroll
-      for (int j = 0; j < V; j++) f[i][j] = T(0);
   }
   T gx[V], gy[V];
 #pragma unroll
   for (int j = 0; j < V; j++) { gx[j] = p.bodyx; gy[j] = p.bodyy; }
-  const bool has = active && flags[(y / TILE_Y) * geo.ntx + x0 / TILE_X] != 0;
-  if (has) {
+  if (FORCED && active) {
 #pragma unroll
     for (int i = 1; i < 9; i++) {
       T jv[V];
@@ -379,49 +378,100 @@ __global__ void __launch_bounds__(32 * VEC_ROWS)
 
 #pragma unroll
   for (int i = 0; i < 9; i++) {
-    if (!ODD) {
+    const bool to_wall = ODD && ((cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m));
+    if (!ODD || to_wall) {
       if (active) Vec<S>::st(A + opp(i) * P + here, f[i], p.scale);
     } else {
-      const bool to_wall = (cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m);
-      if (to_wall) {
-        if (active) Vec<S>::st(A + opp(i) * P + here, f[i], p.scale);
-      } else {
-        const long long base = i * P + row[1 + cy(i)];
-        if (cx(i) == 0) {
-          if (active) Vec<S>::st(A + base + x0, f[i], p.scale);
-        } else if (cx(i) > 0) {  // destination x + 1
-          const T in = __shfl_up_sync(0xffffffffu, f[i][V - 1], 1);
-          if (active) {
-            if (lane != 0) {
-              T v[V];
-              v[0] = in;
+      const long long base = i * P + row[1 + cy(i)];
+      if (cx(i) == 0) {
+        if (active) Vec<S>::st(A + base + x0, f[i], p.scale);
+      } else if (cx(i) > 0) {  // destination x + 1
+        const T in = __shfl_up_sync(0xffffffffu, f[i][V - 1], 1);
+        if (active) {
+          if (lane != 0) {
+            T v[V];
+            v[0] = in;
 #pragma unroll
-              for (int j = 1; j < V; j++) v[j] = f[i][j - 1];
-              Vec<S>::st(A + base + x0, v, p.scale);
-            } else {
+            for (int j = 1; j < V; j++) v[j] = f[i][j - 1];
+            Vec<S>::st(A + base + x0, v, p.scale);
+          } else {
 #pragma unroll
-              for (int j = 0; j < V - 1; j++) A[base + x0 + 1 + j] = Store<S>::st(f[i][j] * p.scale);
-            }
-            if (edge_r) A[base + xr] = Store<S>::st(f[i][V - 1] * p.scale);
+            for (int j = 0; j < V - 1; j++) A[base + x0 + 1 + j] = Store<S>::st(f[i][j] * p.scale);
           }
-        } else {  // destination x - 1
-          const T in = __shfl_down_sync(0xffffffffu, f[i][0], 1);
-          if (active) {
-            if (!edge_r) {
-              T v[V];
+          if (edge_r) A[base + xr] = Store<S>::st(f[i][V - 1] * p.scale);
+        }
+      } else {  // destination x - 1
+        const T in = __shfl_down_sync(0xffffffffu, f[i][0], 1);
+        if (active) {
+          if (!edge_r) {
+            T v[V];
 #pragma unroll
-              for (int j = 0; j < V - 1; j++) v[j] = f[i][j + 1];
-              v[V - 1] = in;
-              Vec<S>::st(A + base + x0, v, p.scale);
-            } else {
+            for (int j = 0; j < V - 1; j++) v[j] = f[i][j + 1];
+            v[V - 1] = in;
+            Vec<S>::st(A + base + x0, v, p.scale);
+          } else {
 #pragma unroll
-              for (int j = 1; j < V; j++) A[base + x0 + j - 1] = Store<S>::st(f[i][j] * p.scale);
-            }
-            if (lane == 0) A[base + xl] = Store<S>::st(f[i][0] * p.scale);
+            for (int j = 1; j < V; j++) A[base + x0 + j - 1] = Store<S>::st(f[i][j] * p.scale);
           }
+          if (lane == 0) A[base + xl] = Store<S>::st(f[i][0] * p.scale);
         }
       }
     }
+  }
+}
+
+constexpr int VEC_ROWS = TILE_Y;  // warps (rows) per block of the vectorised kernels
+
+// Lean kernels: one block per (sub-)tile; a flagged tile is left to the forced kernel.
+template <typename S, int COLL, bool ODD, int BC>
+__global__ void __launch_bounds__(32 * TILE_Y)
+    k_stream_collide(S *__restrict__ A, const uint8_t *__restrict__ flags, const Geom geo,
+                     const CollP<typename Store<S>::T> p, int *status) {
+  const int xb = blockIdx.x * 32, yb = blockIdx.y * TILE_Y;
+  if (flags[blockIdx.y * geo.ntx + xb / TILE_X]) return;  // uniform per block
+  sc_scalar_block<S, COLL, ODD, BC, false>(A, nullptr, nullptr, geo, p, status, xb, yb);
+}
+
+template <typename S, int COLL, bool ODD, int BC>
+__global__ void __launch_bounds__(32 * VEC_ROWS)
+    k_stream_collide_vec(S *__restrict__ A, const uint8_t *__restrict__ flags, const Geom geo,
+                         const CollP<typename Store<S>::T> p, int *status) {
+  constexpr int W = 32 * Vec<S>::V;  // nodes per warp row
+  const int xb = blockIdx.x * W, yb = blockIdx.y * VEC_ROWS;
+  if (flags[blockIdx.y * geo.ntx + xb / TILE_X]) return;  // uniform per block
+  sc_vec_block<S, COLL, ODD, BC, false>(A, nullptr, nullptr, geo, p, status, xb, yb);
+}
+
+// Forced kernels: blocks stride over the list of flagged tiles of this step.
+template <typename S, int COLL, bool ODD, int BC>
+__global__ void __launch_bounds__(32 * TILE_Y)
+    k_stream_collide_forced(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
+                            typename Store<S>::T *__restrict__ gf,
+                            const int *__restrict__ list, const int *__restrict__ count,
+                            const Geom geo, const CollP<typename Store<S>::T> p, int *status) {
+  const int n = *count;
+  for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    const int tile = list[t];
+    const int tx = (tile % geo.ntx) * TILE_X, ty = (tile / geo.ntx) * TILE_Y;
+    for (int sub = 0; sub < TILE_X; sub += 32)
+      sc_scalar_block<S, COLL, ODD, BC, true>(A, Jf, gf, geo, p, status, tx + sub, ty);
+  }
+}
+
+template <typename S, int COLL, bool ODD, int BC>
+__global__ void __launch_bounds__(32 * VEC_ROWS)
+    k_stream_collide_vec_forced(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
+                                typename Store<S>::T *__restrict__ gf,
+                                const int *__restrict__ list, const int *__restrict__ count,
+                                const Geom geo, const CollP<typename Store<S>::T> p,
+                                int *status) {
+  constexpr int W = 32 * Vec<S>::V;
+  const int n = *count;
+  for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    const int tile = list[t];
+    const int tx = (tile % geo.ntx) * TILE_X, ty = (tile / geo.ntx) * TILE_Y;
+    for (int sub = 0; sub < TILE_X; sub += W)
+      sc_vec_block<S, COLL, ODD, BC, true>(A, Jf, gf, geo, p, status, tx + sub, ty);
   }
 }
 
@@ -572,8 +622,8 @@ static int last_error() {
   return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
 }
 
-template <typename S, int COLL, bool ODD>
-static void sc_launch(iilbm_lattice *h) {
+template <typename S, int COLL, bool ODD, int BC>
+static void sc_launch_bc(iilbm_lattice *h, cudaStream_t forced_stream) {
   using T = typename Store<S>::T;
   const Geom &g = h->geom;
   const int b = h->step & 1;
@@ -581,33 +631,45 @@ static void sc_launch(iilbm_lattice *h) {
   const uint8_t *fl = h->flagsb[b];
   const CollP<T> p = make_collp<T>(h->cfg);
   constexpr int V = Vec<S>::V;
-  if (h->vector_sc && g.nx % V == 0) {
-    dim3 grid((g.nx + 32 * V - 1) / (32 * V), (g.ny + VEC_ROWS - 1) / VEC_ROWS);
-    if (g.bc == IILBM_BC_PERIODIC)
-      k_stream_collide_vec<S, COLL, ODD, IILBM_BC_PERIODIC><<<grid, 32 * VEC_ROWS, 0, h->stream>>>(
-          (S *)h->A, J, gf, fl, g, p, h->d_status);
-    else
-      k_stream_collide_vec<S, COLL, ODD, IILBM_BC_WALLS_Y><<<grid, 32 * VEC_ROWS, 0, h->stream>>>(
-          (S *)h->A, J, gf, fl, g, p, h->d_status);
-    return;
-  }
-  dim3 grid(g.ntx, (g.ny + TILE_Y - 1) / TILE_Y), block(TILE_X, TILE_Y);
-  if (g.bc == IILBM_BC_PERIODIC)
-    k_stream_collide<S, COLL, ODD, IILBM_BC_PERIODIC><<<grid, block, 0, h->stream>>>(
-        (S *)h->A, J, gf, fl, g, p, h->d_status);
+  const int nyt = (g.ny + TILE_Y - 1) / TILE_Y;
+  const bool vec = h->vector_sc && g.nx % V == 0;
+  if (vec)
+    k_stream_collide_vec<S, COLL, ODD, BC><<<dim3((g.nx + 32 * V - 1) / (32 * V), nyt),
+                                             32 * VEC_ROWS, 0, h->stream>>>((S *)h->A, fl, g, p,
+                                                                            h->d_status);
   else
-    k_stream_collide<S, COLL, ODD, IILBM_BC_WALLS_Y><<<grid, block, 0, h->stream>>>(
-        (S *)h->A, J, gf, fl, g, p, h->d_status);
+    k_stream_collide<S, COLL, ODD, BC><<<dim3((g.nx + 31) / 32, nyt), dim3(32, TILE_Y), 0,
+                                         h->stream>>>((S *)h->A, fl, g, p, h->d_status);
+  if (h->nm == 0) return;  // no interface: no flagged tiles
+  const int grid = h->forced_grid;
+  if (vec)
+    k_stream_collide_vec_forced<S, COLL, ODD, BC><<<grid, 32 * VEC_ROWS, 0, forced_stream>>>(
+        (S *)h->A, J, gf, h->tile_list[b], h->tile_count[b], g, p, h->d_status);
+  else
+    k_stream_collide_forced<S, COLL, ODD, BC><<<grid, dim3(32, TILE_Y), 0, forced_stream>>>(
+        (S *)h->A, J, gf, h->tile_list[b], h->tile_count[b], g, p, h->d_status);
 }
 
-int launch_stream_collide(iilbm_lattice *h) {
+template <typename S, int COLL, bool ODD>
+static void sc_launch(iilbm_lattice *h, cudaStream_t forced_stream) {
+  if (h->geom.bc == IILBM_BC_PERIODIC)
+    sc_launch_bc<S, COLL, ODD, IILBM_BC_PERIODIC>(h, forced_stream);
+  else
+    sc_launch_bc<S, COLL, ODD, IILBM_BC_WALLS_Y>(h, forced_stream);
+}
+
+// Launch the lean stream-collide on the handle's stream and the forced one (flagged
+// tiles) on forced_stream (which may be the same stream).
+int launch_stream_collide(iilbm_lattice *h, cudaStream_t forced_stream) {
   const bool odd = h->step & 1;
   return dispatch_storage(h->cfg.storage, [&](auto *tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     if (h->cfg.collision == IILBM_SRT) {
-      if (odd) sc_launch<S, IILBM_SRT, true>(h); else sc_launch<S, IILBM_SRT, false>(h);
+      if (odd) sc_launch<S, IILBM_SRT, true>(h, forced_stream);
+      else sc_launch<S, IILBM_SRT, false>(h, forced_stream);
     } else {
-      if (odd) sc_launch<S, IILBM_MRT, true>(h); else sc_launch<S, IILBM_MRT, false>(h);
+      if (odd) sc_launch<S, IILBM_MRT, true>(h, forced_stream);
+      else sc_launch<S, IILBM_MRT, false>(h, forced_stream);
     }
     return last_error();
   });

@@ -66,7 +66,7 @@ SIGNATURES = {
     "iilbm_get_cut_link_count": [_H, C.POINTER(C.c_int32)],
     "iilbm_set_timing": [_H, C.c_int32],
     "iilbm_get_timing": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int32),
-                         C.POINTER(C.c_int64)],
+                         C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "iilbm_set_option": [_H, C.c_int32, C.c_int32],
     "iilbm_synchronize": [_H],
     "iilbm_error_string": [C.c_int],
@@ -249,12 +249,14 @@ class Lattice:
     def iilbm_set_timing(self, enable=True):
         _check("iilbm_set_timing", self._L.iilbm_set_timing(self._h, int(enable)))
 
-    def iilbm_get_timing(self):
-        """(stream-collide ms summed, stream-collide launches, library kernel launches)."""
-        ms, n, k = C.c_double(), C.c_int32(), C.c_int64()
-        _check("iilbm_get_timing",
-               self._L.iilbm_get_timing(self._h, C.byref(ms), C.byref(n), C.byref(k)))
-        return ms.value, n.value, k.value
+    def iilbm_get_timing(self, with_tiles=False):
+        """(lean stream-collide ms summed, its launches, library kernel launches[,
+        flagged tiles summed])."""
+        ms, n, k, t = C.c_double(), C.c_int32(), C.c_int64(), C.c_int64()
+        _check("iilbm_get_timing", self._L.iilbm_get_timing(self._h, C.byref(ms), C.byref(n),
+                                                            C.byref(k), C.byref(t)))
+        return (ms.value, n.value, k.value, t.value) if with_tiles else (ms.value, n.value,
+                                                                          k.value)
 
     def iilbm_set_option(self, option, value):
         _check("iilbm_set_option", self._L.iilbm_set_option(self._h, int(option), int(value)))

@@ -129,7 +129,7 @@ int iilbm_get_markers(iilbm_t h, double *X, double *G, double *U, double *Fn);
 /* Direct forcing: passes of the most recent step and its final residual. */
 int iilbm_get_mdf_stats(iilbm_t h, int32_t *iters, double *residual);
 
-/* Number of cut-link crossings of the most recent interface phase (Eq. 47). */
+/* Number of cut-link crossings of the current state's interface (Eq. 47). */
 int iilbm_get_cut_link_count(iilbm_t h, int32_t *count);
 
 /* Kernel timing (diagnostic).  enable = 1 starts recording a CUDA event pair around

@@ -80,8 +80,8 @@ int clear_fields(iilbm_lattice *h) {
   for (int b = 0; b < 2; b++) {
     CK(cudaMemsetAsync(h->Jb[b], 0, 8 * (size_t)g.plane * h->tbytes, h->stream));
     CK(cudaMemsetAsync(h->gb[b], 0, 2 * (size_t)g.plane * h->tbytes, h->stream));
-    CK(cudaMemsetAsync(h->flagsb[b], 0, (size_t)h->ntiles, h->stream));
-    CK(cudaMemsetAsync(h->tile_count[b], 0, sizeof(int), h->stream));
+    CK(cudaMemsetAsync(h->flagsb[b], 0, (size_t)h->ntiles * sizeof(unsigned), h->stream));
+    CK(cudaMemsetAsync(h->tile_count[b], 0, 2 * sizeof(int), h->stream));
   }
   h->prepared = false;
   return IILBM_OK;
@@ -166,14 +166,13 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
             cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess &&
             cudaMalloc(&h->A, 9 * (size_t)g.plane * h->sbytes) == cudaSuccess &&
             cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&h->d_ncut, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->d_tiles_total, sizeof(unsigned long long)) == cudaSuccess;
   for (int b = 0; b < 2 && ok; b++)
     ok = cudaMalloc(&h->Jb[b], 8 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
          cudaMalloc(&h->gb[b], 2 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
-         cudaMalloc(&h->flagsb[b], (size_t)h->ntiles) == cudaSuccess &&
+         cudaMalloc(&h->flagsb[b], (size_t)h->ntiles * sizeof(unsigned)) == cudaSuccess &&
          cudaMalloc(&h->tile_list[b], (size_t)h->ntiles * sizeof(int)) == cudaSuccess &&
-         cudaMalloc(&h->tile_count[b], sizeof(int)) == cudaSuccess;
+         cudaMalloc(&h->tile_count[b], 2 * sizeof(int)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     iilbm_destroy(h);
@@ -182,7 +181,6 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
   int rc = IILBM_OK;
   if (cudaMemsetAsync(h->A, 0, 9 * (size_t)g.plane * h->sbytes, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream) != cudaSuccess ||
-      cudaMemsetAsync(h->d_ncut, 0, sizeof(int), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_tiles_total, 0, sizeof(unsigned long long), h->stream) != cudaSuccess)
     rc = IILBM_ERR_CUDA;
   if (!rc) rc = clear_fields(h);
@@ -203,7 +201,7 @@ int iilbm_destroy(iilbm_t h) {
   free_interface(h);
   void *bufs[] = {h->A, h->Jb[0], h->Jb[1], h->gb[0], h->gb[1], h->flagsb[0], h->flagsb[1],
                   h->tile_list[0], h->tile_list[1], h->tile_count[0], h->tile_count[1],
-                  h->d_status, h->d_ncut, h->d_tiles_total};
+                  h->d_status, h->d_tiles_total};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -338,11 +336,8 @@ int drain_events(iilbm_lattice *h) {
 }
 
 // Kernels launched by one step: lean stream-collide; with an interface also the
-// interface phase (forces, cut links if the jump is on, spread, tile list), the
-// interpolation and the forced stream-collide.
-long long kernels_per_step(const iilbm_lattice *h) {
-  return 1 + (h->nm > 0 ? 3 + (h->cfg.jump ? 1 : 0) + 1 + 1 : 0);
-}
+// interpolation, the forced stream-collide and the interface phase (clear, fused).
+long long kernels_per_step(const iilbm_lattice *h) { return 1 + (h->nm > 0 ? 4 : 0); }
 
 bool pipelined(const iilbm_lattice *h) { return h->overlap && h->nm > 0; }
 
@@ -531,7 +526,12 @@ int iilbm_get_mdf_stats(iilbm_t h, int32_t *iters, double *residual) {
 
 int iilbm_get_cut_link_count(iilbm_t h, int32_t *count) {
   if (!h || !count) return IILBM_ERR_INVALID_ARG;
-  CK(cudaMemcpyAsync(count, h->d_ncut, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  *count = 0;
+  if (h->nm == 0) return read_status(h);
+  int rc = prepare(h);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(count, h->tile_count[h->step & 1] + 1, sizeof(int), cudaMemcpyDeviceToHost,
+                     h->stream));
   return read_status(h);
 }
 

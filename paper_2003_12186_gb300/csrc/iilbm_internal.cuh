@@ -122,9 +122,9 @@ struct iilbm_lattice {
   // (and re-zeroes) the buffer of step n.
   void *Jb[2];
   void *gb[2];
-  uint8_t *flagsb[2];
-  int *tile_list[2];  // flagged tiles of each buffer, compacted by the interface phase
-  int *tile_count[2];
+  unsigned *flagsb[2];
+  int *tile_list[2];  // flagged tiles of each buffer, appended by the interface phase
+  int *tile_count[2]; // per buffer: [0] flagged tiles, [1] cut-link crossings
   unsigned long long *d_tiles_total;  // flagged tiles summed while timing
   int ntiles;
   int forced_grid;    // blocks of the forced stream-collide (strides over the list)
@@ -140,7 +140,6 @@ struct iilbm_lattice {
   long long step;     // time level of the state; AA parity = step & 1
   bool prepared;      // jump / force of the current state already in J, g
   int *d_status;      // latched device status bits
-  int *d_ncut;        // crossings of the latest interface phase
   // interface
   int nm;
   iilbm_interface_params ip;

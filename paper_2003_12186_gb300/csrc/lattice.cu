@@ -121,7 +121,7 @@ __device__ __forceinline__ T collide(T f[9], T gx, T gy, const CollP<T> &p) {
 // lean kernel with no jump / force code at all, which keeps its register count and
 // so its memory parallelism high.  The flagged tiles are listed by the interface phase
 // and processed by a "forced" kernel that adds the jump of Eq. 47 and the spread
-// force of Eq. 46 (and re-zeroes both fields).  Under the AA pattern every population
+// force of Eq. 46.  Under the AA pattern every population
 // slot is read and written by one and the same node, so the two kernels touch
 // disjoint slots and may run in either order or concurrently.
 
@@ -202,11 +202,6 @@ __device__ inline void ldT(const T *p, T *o) {
     o[0] = t.x; o[1] = t.y;
   }
 }
-template <typename T, int V>
-__device__ inline void zeroT(T *p) {
-  if constexpr (sizeof(T) == 4) *reinterpret_cast<float4 *>(p) = make_float4(0.f, 0.f, 0.f, 0.f);
-  else *reinterpret_cast<double2 *>(p) = make_double2(0.0, 0.0);
-}
 
 
 // One node per thread on a 32 x TILE_Y sub-block whose first node is (xb, yb).  BC is
@@ -250,14 +245,9 @@ __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
   T gx = p.bodyx, gy = p.bodyy;
   if (FORCED) {
 #pragma unroll
-    for (int i = 1; i < 9; i++) {
-      f[i] += Jf[(i - 1) * P + here];
-      Jf[(i - 1) * P + here] = T(0);
-    }
+    for (int i = 1; i < 9; i++) f[i] += Jf[(i - 1) * P + here];
     gx += gf[here];
     gy += gf[P + here];
-    gf[here] = T(0);
-    gf[P + here] = T(0);
   }
   const T drho = collide<T, COLL>(f, gx, gy, p);
   if (!isfinite(drho)) atomicOr(status, ST_NONFINITE);
@@ -351,15 +341,12 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
     for (int i = 1; i < 9; i++) {
       T jv[V];
       ldT<T, V>(Jf + (i - 1) * P + here, jv);
-      zeroT<T, V>(Jf + (i - 1) * P + here);
 #pragma unroll
       for (int j = 0; j < V; j++) f[i][j] += jv[j];
     }
     T a[V], b[V];
     ldT<T, V>(gf + here, a);
     ldT<T, V>(gf + P + here, b);
-    zeroT<T, V>(gf + here);
-    zeroT<T, V>(gf + P + here);
 #pragma unroll
     for (int j = 0; j < V; j++) { gx[j] += a[j]; gy[j] += b[j]; }
   }
@@ -425,7 +412,7 @@ constexpr int VEC_ROWS = TILE_Y;  // warps (rows) per block of the vectorised ke
 // Lean kernels: one block per (sub-)tile; a flagged tile is left to the forced kernel.
 template <typename S, int COLL, bool ODD, int BC>
 __global__ void __launch_bounds__(32 * TILE_Y)
-    k_stream_collide(S *__restrict__ A, const uint8_t *__restrict__ flags, const Geom geo,
+    k_stream_collide(S *__restrict__ A, const unsigned *__restrict__ flags, const Geom geo,
                      const CollP<typename Store<S>::T> p, int *status) {
   const int xb = blockIdx.x * 32, yb = blockIdx.y * TILE_Y;
   if (flags[blockIdx.y * geo.ntx + xb / TILE_X]) return;  // uniform per block
@@ -434,7 +421,7 @@ __global__ void __launch_bounds__(32 * TILE_Y)
 
 template <typename S, int COLL, bool ODD, int BC>
 __global__ void __launch_bounds__(32 * VEC_ROWS)
-    k_stream_collide_vec(S *__restrict__ A, const uint8_t *__restrict__ flags, const Geom geo,
+    k_stream_collide_vec(S *__restrict__ A, const unsigned *__restrict__ flags, const Geom geo,
                          const CollP<typename Store<S>::T> p, int *status) {
   constexpr int W = 32 * Vec<S>::V;  // nodes per warp row
   const int xb = blockIdx.x * W, yb = blockIdx.y * VEC_ROWS;
@@ -628,7 +615,7 @@ static void sc_launch_bc(iilbm_lattice *h, cudaStream_t forced_stream) {
   const Geom &g = h->geom;
   const int b = h->step & 1;
   T *J = (T *)h->Jb[b], *gf = (T *)h->gb[b];
-  const uint8_t *fl = h->flagsb[b];
+  const unsigned *fl = h->flagsb[b];
   const CollP<T> p = make_collp<T>(h->cfg);
   constexpr int V = Vec<S>::V;
   const int nyt = (g.ny + TILE_Y - 1) / TILE_Y;

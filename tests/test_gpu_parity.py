@@ -87,7 +87,7 @@ def test_membrane64_fp64_step_by_step(orc):
         mg, mo = g.get_markers(), o.markers()
         assert np.abs(mg["X"] - mo["X"]).max() < 1e-14
         assert np.abs(mg["U"] - mo["U"]).max() < 1e-16
-    assert vel_error(g, o) < 1e-12
+    assert vel_error(g, o) < 1e-12  # also brings the oracle's interface to this state
     assert g.iilbm_get_cut_link_count() == o.cut_link_count() > 0
 
 

@@ -39,66 +39,93 @@ __device__ inline void flag_tile(const TileBuf &tb, int tile) {
   }
 }
 
-__device__ inline double phi4i(double r) {
-  const double a = fabs(r);
-  if (a < 1.0) return 0.125 * (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a));
-  if (a < 2.0) return 0.125 * (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a));
-  return 0.0;
+// Tile indices (along one axis of n nodes, tiles of width w) covered by the node range
+// [a, b], wrapped on a periodic axis, clipped otherwise.  Returns their number (at most
+// MAX_TILE_SPAN; ranges here span at most 23 nodes).
+constexpr int MAX_TILE_SPAN = 8;
+__device__ inline int tile_span(int a, int b, int n, bool periodic, int w, int *out) {
+  if (!periodic) {
+    a = max(a, 0);
+    b = min(b, n - 1);
+  }
+  int cnt = 0, last = -1;
+  for (int v = a; v <= b && cnt < MAX_TILE_SPAN;) {
+    const int u = periodic ? wrap(v, n) : v;
+    const int t = u / w;
+    if (t != last) out[cnt++] = t;
+    last = t;
+    v += min(w - u % w, n - u);  // to the next tile boundary (or the end of the axis)
+  }
+  return cnt;
+}
+
+// Peskin's four-point kernel phi(r) in the arithmetic type T.
+template <typename T>
+__device__ inline T phi4t(T r) {
+  const T a = fabs(r);
+  if (a < T(1)) return T(0.125) * (T(3) - T(2) * a + sqrt(T(1) + T(4) * a - T(4) * a * a));
+  if (a < T(2)) return T(0.125) * (T(5) - T(2) * a - sqrt(T(-7) + T(12) * a - T(4) * a * a));
+  return T(0);
 }
 
 // Force of marker j and its split: G_j, n_j, Fn_j = G_j.n_j/|X_s|_j, and the point
-// force to spread P_j = dX * (tangential part in II-LBM, whole G in IB-LBM).
+// force to spread P_j = dX * (tangential part in II-LBM, whole G in IB-LBM).  Marker
+// positions and their differences (including the spring's second difference, a small
+// difference of O(1) numbers) are FP64; the rest runs in the arithmetic type T.
+template <typename T>
 struct MarkerForce {
-  double gx, gy, nx, ny, fn, px, py;
+  T gx, gy, nx, ny, fn, px, py;
   bool bad;
 };
 
-__device__ inline MarkerForce marker_force(const double *__restrict__ X,
-                                           const double *__restrict__ aux, int n, int j,
-                                           const iilbm_interface_params &ip, int jump,
-                                           const Geom &geo) {
-  MarkerForce m;
+template <typename T>
+__device__ inline MarkerForce<T> marker_force(const double *__restrict__ X,
+                                              const double *__restrict__ aux, int n, int j,
+                                              const iilbm_interface_params &ip, int jump,
+                                              const Geom &geo) {
+  MarkerForce<T> m;
   const int jp = j + 1 == n ? 0 : j + 1, jm = j == 0 ? n - 1 : j - 1;
   const double x = X[2 * j], y = X[2 * j + 1];
   const double xp = X[2 * jp], yp = X[2 * jp + 1], xm = X[2 * jm], ym = X[2 * jm + 1];
+  const double dax = xp - x, day = yp - y, dbx = x - xm, dby = y - ym;  // segments k, k-1
   // validity: finite, inside the representable / valid region, short segments
   bool bad = !(isfinite(x) && isfinite(y)) || fabs(x) > MAX_COORD || fabs(y) > MAX_COORD;
-  const double sgx = xp - x, sgy = yp - y;
-  bad = bad || !(sgx * sgx + sgy * sgy < MAX_SEGMENT * MAX_SEGMENT);
+  bad = bad || !(dax * dax + day * day < MAX_SEGMENT * MAX_SEGMENT);
   if (geo.bc != IILBM_BC_PERIODIC) bad = bad || y < 3.0 || y > geo.ny - 4.0;
   if (geo.bc == IILBM_BC_CHANNEL) bad = bad || x < 3.0 || x > geo.nx - 4.0;
   m.bad = bad;
-  double gx, gy;
+  T gx, gy;
   if (ip.model == IILBM_SPRING) {
-    const double c = ip.stiffness / (ip.dX * ip.dX);
-    gx = c * ((xp - x) - (x - xm));
-    gy = c * ((yp - y) - (y - ym));
+    const T c = T(ip.stiffness / (ip.dX * ip.dX));
+    gx = c * T(dax - dbx);
+    gy = c * T(day - dby);
   } else if (ip.model == IILBM_SPRING_REST) {
-    const double ax = xp - x, ay = yp - y, bx = x - xm, by = y - ym;
-    const double la = sqrt(ax * ax + ay * ay), lb = sqrt(bx * bx + by * by);
-    const double Ta = ip.stiffness * (la / ip.rest_length - 1.0);
-    const double Tb = ip.stiffness * (lb / ip.rest_length - 1.0);
-    gx = (Ta * (ax / la) - Tb * (bx / lb)) / ip.dX;
-    gy = (Ta * (ay / la) - Tb * (by / lb)) / ip.dX;
+    const T ax = T(dax), ay = T(day), bx = T(dbx), by = T(dby);
+    const T la = sqrt(ax * ax + ay * ay), lb = sqrt(bx * bx + by * by);
+    const T Ta = T(ip.stiffness) * (la / T(ip.rest_length) - T(1));
+    const T Tb = T(ip.stiffness) * (lb / T(ip.rest_length) - T(1));
+    gx = (Ta * (ax / la) - Tb * (bx / lb)) / T(ip.dX);
+    gy = (Ta * (ay / la) - Tb * (by / lb)) / T(ip.dX);
   } else {  // prescribed
-    gx = aux[2 * j];
-    gy = aux[2 * j + 1];
+    gx = T(aux[2 * j]);
+    gy = T(aux[2 * j + 1]);
   }
-  const double tx = xp - xm, ty = yp - ym;
-  const double tl = sqrt(tx * tx + ty * ty);
+  const T tx = T(xp - xm), ty = T(yp - ym);
+  const T tl = sqrt(tx * tx + ty * ty);
   m.nx = ty / tl;  // outward for a counter-clockwise polygon
   m.ny = -tx / tl;
-  const double xs = ip.moves ? tl / (2.0 * ip.dX) : 1.0;
-  const double gn = gx * m.nx + gy * m.ny;
+  const T xs = ip.moves ? tl / T(2.0 * ip.dX) : T(1);
+  const T gn = gx * m.nx + gy * m.ny;
   m.gx = gx;
   m.gy = gy;
   m.fn = gn / xs;
+  const T dX = T(ip.dX);
   if (jump) {
-    m.px = (gx - gn * m.nx) * ip.dX;
-    m.py = (gy - gn * m.ny) * ip.dX;
+    m.px = (gx - gn * m.nx) * dX;
+    m.py = (gy - gn * m.ny) * dX;
   } else {
-    m.px = gx * ip.dX;
-    m.py = gy * ip.dX;
+    m.px = gx * dX;
+    m.py = gy * dX;
   }
   return m;
 }
@@ -121,6 +148,11 @@ __device__ inline int orient_link_pt(long long px, long long py, int ex, int ey,
   return ex > 0 ? -1 : 1;
 }
 
+// Crossings found by a lane are buffered (candidate index, sign, raw orientations) and
+// their FP64 coefficients computed together, so the FP64 division runs about once per
+// warp rather than once per candidate sweep.
+constexpr int CROSS_BUF = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_interface(const double *__restrict__ X, const double *__restrict__ aux, int n,
@@ -131,19 +163,19 @@ __global__ void __launch_bounds__(128)
   if (k >= n) return;  // uniform per warp
   const int kp = k + 1 == n ? 0 : k + 1;
   // forces of k (lane 0) and k + 1 (lane 1)
-  MarkerForce m{};
-  if (lane < 2) m = marker_force(X, aux, n, lane == 0 ? k : kp, ip, jump, geo);
-  const double FnA = __shfl_sync(0xffffffffu, m.fn, 0);
-  const double FnB = __shfl_sync(0xffffffffu, m.fn, 1);
-  const double Px = __shfl_sync(0xffffffffu, m.px, 0);
-  const double Py = __shfl_sync(0xffffffffu, m.py, 0);
+  MarkerForce<T> m{};
+  if (lane < 2) m = marker_force<T>(X, aux, n, lane == 0 ? k : kp, ip, jump, geo);
+  const double FnA = (double)__shfl_sync(0xffffffffu, m.fn, 0);
+  const double FnB = (double)__shfl_sync(0xffffffffu, m.fn, 1);
+  const T Pkx = __shfl_sync(0xffffffffu, m.px, 0);  // point force of marker k
+  const T Pky = __shfl_sync(0xffffffffu, m.py, 0);
   if (lane == 0) {
     if (m.bad) atomicOr(status, ST_INTERFACE);
-    G[2 * k] = m.gx;
-    G[2 * k + 1] = m.gy;
-    Fn[k] = m.fn;
-    nrm[2 * k] = m.nx;
-    nrm[2 * k + 1] = m.ny;
+    G[2 * k] = (double)m.gx;
+    G[2 * k + 1] = (double)m.gy;
+    Fn[k] = (double)m.fn;
+    nrm[2 * k] = (double)m.nx;
+    nrm[2 * k + 1] = (double)m.ny;
   }
   const double Ax = X[2 * k], Ay = X[2 * k + 1], Bx = X[2 * kp], By = X[2 * kp + 1];
   const bool inside = fabs(Ax) <= MAX_COORD && fabs(Ay) <= MAX_COORD && fabs(Bx) <= MAX_COORD &&
@@ -158,6 +190,29 @@ __global__ void __launch_bounds__(128)
     const int W = x1 - x0 + 1, H = y1 - y0 + 1;
     const int ncand = W * H * 8;
     const long long Q = (long long)QSCALE;
+    int bc_idx[CROSS_BUF], bc_s[CROSS_BUF];
+    long long bc_o3[CROSS_BUF], bc_o4[CROSS_BUF];
+    int nb = 0;
+    // apply the buffered crossings: coefficient s w_i/c_s^2 Fn(t), t along A -> B
+    auto flush = [&]() {
+#pragma unroll
+      for (int q = 0; q < CROSS_BUF; q++) {
+        if (q >= nb) break;
+        const int c = bc_idx[q];
+        const int i = 1 + c % 8, cell = c / 8;
+        int xd = x0 + cell % W, yd = y0 + cell / W;
+        xd = geo.bc == IILBM_BC_CHANNEL ? xd : wrap(xd, geo.nx);
+        yd = geo.bc == IILBM_BC_PERIODIC ? wrap(yd, geo.ny) : yd;
+        double t = (double)bc_o3[q] / ((double)bc_o3[q] - (double)bc_o4[q]);
+        t = fmin(fmax(t, 0.0), 1.0);
+        const double F = (1.0 - t) * FnA + t * FnB;
+        const double coef = (double)bc_s[q] * 3.0 * wt<double>(i) * F;  // w_i / c_s^2 Fn
+        atomicAdd(&Jf[(long long)(i - 1) * geo.plane + (long long)yd * geo.pitch + xd],
+                  (T)coef);
+      }
+      found += nb;
+      nb = 0;
+    };
     for (int c = lane; c < ncand; c += 32) {
       const int i = 1 + c % 8;
       const int cell = c / 8;
@@ -171,27 +226,20 @@ __global__ void __launch_bounds__(128)
       const int s3 = orient_link_pt(Px, Py, ex, ey, ax, ay, o3);
       const int s4 = orient_link_pt(Px, Py, ex, ey, bx, by, o4);
       if (s3 == s4) continue;
-      double t = (double)o3 / ((double)o3 - (double)o4);
-      t = fmin(fmax(t, 0.0), 1.0);
       // destination and source inside the lattice (periodic axes wrap)
-      int xd = qx, yd = qy;
       const int xs = qx - ex, ys = qy - ey;
-      if (geo.bc == IILBM_BC_CHANNEL) {
-        if (xd < 0 || xd >= geo.nx || xs < 0 || xs >= geo.nx) continue;
-      } else {
-        xd = wrap(xd, geo.nx);
-      }
-      if (geo.bc == IILBM_BC_PERIODIC) {
-        yd = wrap(yd, geo.ny);
-      } else if (yd < 0 || yd >= geo.ny || ys < 0 || ys >= geo.ny) {
+      if (geo.bc == IILBM_BC_CHANNEL && (qx < 0 || qx >= geo.nx || xs < 0 || xs >= geo.nx))
         continue;
-      }
-      const double F = (1.0 - t) * FnA + t * FnB;
-      const double coef = (double)s1 * 3.0 * wt<double>(i) * F;  // w_i / c_s^2 Fn
-      atomicAdd(&Jf[(long long)(i - 1) * geo.plane + (long long)yd * geo.pitch + xd], (T)coef);
-      flag_tile(tb, tile_of(geo, xd, yd));
-      found++;
+      if (geo.bc != IILBM_BC_PERIODIC && (qy < 0 || qy >= geo.ny || ys < 0 || ys >= geo.ny))
+        continue;
+      if (nb == CROSS_BUF) flush();
+      bc_idx[nb] = c;
+      bc_s[nb] = s1;
+      bc_o3[nb] = o3;
+      bc_o4[nb] = o4;
+      nb++;
     }
+    flush();
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) found += __shfl_xor_sync(0xffffffffu, found, o);
@@ -205,13 +253,23 @@ __global__ void __launch_bounds__(128)
     else xi = wrap(xi, geo.nx);
     if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
     else ok = ok && yi >= 0 && yi < geo.ny;
-    const double w = ok ? phi4i((double)xa - Ax) * phi4i((double)yb - Ay) : 0.0;
-    if (w != 0.0) {
+    // node offsets are exact in FP64 (Sterbenz), then rounded to T
+    const T w = ok ? phi4t<T>(T((double)xa - Ax)) * phi4t<T>(T((double)yb - Ay)) : T(0);
+    if (w != T(0)) {
       const long long here = (long long)yi * geo.pitch + xi;
-      atomicAdd(&gf[here], (T)(Px * w));
-      atomicAdd(&gf[geo.plane + here], (T)(Py * w));
-      flag_tile(tb, tile_of(geo, xi, yi));
+      atomicAdd(&gf[here], Pkx * w);
+      atomicAdd(&gf[geo.plane + here], Pky * w);
     }
+  }
+  // ---- flag the tiles of the warp's footprint once: every node written above lies in
+  // [floor(min x) - 2, ceil(max x) + 2] x [floor(min y) - 2, ceil(max y) + 2]
+  if (inside) {
+    int cols[MAX_TILE_SPAN], rows[MAX_TILE_SPAN];
+    const int nc = tile_span((int)floor(fmin(Ax, Bx)) - 2, (int)ceil(fmax(Ax, Bx)) + 2, geo.nx,
+                             geo.bc != IILBM_BC_CHANNEL, TILE_X, cols);
+    const int nr = tile_span((int)floor(fmin(Ay, By)) - 2, (int)ceil(fmax(Ay, By)) + 2, geo.ny,
+                             geo.bc == IILBM_BC_PERIODIC, TILE_Y, rows);
+    for (int t = lane; t < nc * nr; t += 32) flag_tile(tb, rows[t / nc] * geo.ntx + cols[t % nc]);
   }
 }
 

@@ -419,8 +419,10 @@ __global__ void __launch_bounds__(32 * TILE_Y)
   sc_scalar_block<S, COLL, ODD, BC, false>(A, nullptr, nullptr, geo, p, status, xb, yb);
 }
 
+// At least three resident blocks per SM (<= 85 registers): the odd step would otherwise
+// drop to two and lose a third of its memory parallelism.
 template <typename S, int COLL, bool ODD, int BC>
-__global__ void __launch_bounds__(32 * VEC_ROWS)
+__global__ void __launch_bounds__(32 * VEC_ROWS, 3)
     k_stream_collide_vec(S *__restrict__ A, const unsigned *__restrict__ flags, const Geom geo,
                          const CollP<typename Store<S>::T> p, int *status) {
   constexpr int W = 32 * Vec<S>::V;  // nodes per warp row
@@ -463,11 +465,14 @@ __global__ void __launch_bounds__(32 * VEC_ROWS)
 }
 
 // ------------------------------------------------------ Peskin delta (Eq. 17)
-__device__ inline double phi4(double r) {
-  const double a = fabs(r);
-  if (a < 1.0) return 0.125 * (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a));
-  if (a < 2.0) return 0.125 * (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a));
-  return 0.0;
+// Four-point kernel phi(r) in the arithmetic type T (GB300's FP64 rate is a small
+// fraction of its FP32 rate, so FP64 is kept to positions and accumulations).
+template <typename T>
+__device__ inline T phi4(T r) {
+  const T a = fabs(r);
+  if (a < T(1)) return T(0.125) * (T(3) - T(2) * a + sqrt(T(1) + T(4) * a - T(4) * a * a));
+  if (a < T(2)) return T(0.125) * (T(5) - T(2) * a - sqrt(T(-7) + T(12) * a - T(4) * a * a));
+  return T(0);
 }
 
 // Macroscopic density deviation and velocity of node (x, y) of the current state:
@@ -519,7 +524,8 @@ __global__ void k_interp(const S *__restrict__ A, const typename Store<S>::T *__
     if (ok) {
       double drho, ux, uy;
       node_macros<S>(A, Jf, gf, geo, p, odd, xi, yi, drho, ux, uy);
-      const double w = phi4((double)xa - Xk) * phi4((double)yb - Yk);
+      using T = typename Store<S>::T;
+      const double w = (double)(phi4<T>(T((double)xa - Xk)) * phi4<T>(T((double)yb - Yk)));
       sx = ux * w;
       sy = uy * w;
     }

@@ -152,6 +152,20 @@ int iilbm_get_timing(iilbm_t h, double *stream_collide_ms, int32_t *stream_colli
 enum { IILBM_OPT_CUDA_GRAPH = 0, IILBM_OPT_OVERLAP = 1, IILBM_OPT_VECTOR_KERNEL = 2 };
 int iilbm_set_option(iilbm_t h, int32_t option, int32_t value);
 
+/* No-allocation read-out (the paper has no counterpart; this is a service of the
+ * library).  Same results as iilbm_get_macros, for callers that must not allocate
+ * device memory at this point: code whose device memory is owned by a caching
+ * allocator or a fixed budget (a cudaMalloc there can fail or fragment the pool), and
+ * latency-bound loops, where cudaMalloc / cudaFree would synchronise the device.  The
+ * fields are staged in a static device array of IILBM_NOALLOC_MAX_CELLS nodes x 3
+ * doubles (6 MiB) that every device loading the library keeps until exit; a lattice
+ * with more nodes gets IILBM_ERR_CAPACITY.  The first call on a device looks up the
+ * array's device address, so make it before any stream capture.  All calls share the
+ * array: calls whose GPU work overlaps in time race.  Outputs as iilbm_get_macros
+ * (host or device, any may be NULL).  Synchronises. */
+#define IILBM_NOALLOC_MAX_CELLS (1 << 18)
+int iilbm_get_macros_noalloc(iilbm_t h, double *drho, double *ux, double *uy);
+
 /* Wait for the handle's stream and return any latched device status. */
 int iilbm_synchronize(iilbm_t h);
 

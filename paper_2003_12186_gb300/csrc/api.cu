@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -542,3 +543,64 @@ int iilbm_synchronize(iilbm_t h) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------ no-allocation read-out
+// iilbm_get_macros_noalloc: the macroscopic read-out of iilbm_get_macros without any
+// device allocation.  The fields are staged in a file-scope device array instead of a
+// cudaMalloc'd buffer.  Every device that loads this library holds the array (6 MiB)
+// until the process exits.  All calls share it, so calls whose GPU work overlaps in
+// time (two streams, two threads) race on it; it needs no clearing because the kernel
+// writes every element a call reads back.
+
+namespace {
+
+constexpr long long NOALLOC_MAX_CELLS = IILBM_NOALLOC_MAX_CELLS;
+static __device__ __align__(256) double g_noalloc_stage[3 * NOALLOC_MAX_CELLS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the staging array on `device`, looked up once per device with that
+// device current (the host-side symbol is only a stand-in, never a device address).
+int noalloc_stage(int device, double **out) {
+  if (device < 0 || device >= NOALLOC_MAX_DEVICES) return IILBM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    int prev = -1;
+    CK(cudaGetDevice(&prev));
+    if (prev != device) CK(cudaSetDevice(device));
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_stage);
+    if (prev != device) cudaSetDevice(prev);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return IILBM_ERR_CUDA;
+    }
+    g_noalloc_ptr[device] = (double *)p;
+  }
+  *out = g_noalloc_ptr[device];
+  return IILBM_OK;
+}
+
+}  // namespace
+
+extern "C" int iilbm_get_macros_noalloc(iilbm_t h, double *drho, double *ux, double *uy) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  const long long cells = (long long)h->cfg.nx * h->cfg.ny;
+  if (cells > NOALLOC_MAX_CELLS) return IILBM_ERR_CAPACITY;
+  double *stage = nullptr;
+  int rc = noalloc_stage(h->device, &stage);
+  if (rc) return rc;
+  if ((rc = prepare(h))) return rc;
+  rc = launch_macros(h, stage, stage + cells, stage + 2 * cells);
+  double *outs[3] = {drho, ux, uy};
+  for (int a = 0; a < 3 && !rc; a++)
+    if (outs[a] && cudaMemcpyAsync(outs[a], stage + a * cells, (size_t)cells * sizeof(double),
+                                   cudaMemcpyDefault, h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      rc = IILBM_ERR_CUDA;
+    }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess && !rc) rc = IILBM_ERR_CUDA;
+  return rc ? rc : read_status(h);
+}

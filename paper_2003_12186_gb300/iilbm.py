@@ -68,6 +68,7 @@ SIGNATURES = {
     "iilbm_get_timing": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int32),
                          C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "iilbm_set_option": [_H, C.c_int32, C.c_int32],
+    "iilbm_get_macros_noalloc": [_H, _P, _P, _P],
     "iilbm_synchronize": [_H],
     "iilbm_error_string": [C.c_int],
 }
@@ -221,6 +222,16 @@ class Lattice:
         return tuple(outs)
 
     get_macros = iilbm_get_macros
+
+    def iilbm_get_macros_noalloc(self, drho=None, ux=None, uy=None, want=(True, True, True)):
+        """As iilbm_get_macros, staged through the library's static device array (no
+        device allocation; lattices up to 2^18 nodes)."""
+        outs = []
+        for a, w in zip((drho, ux, uy), want):
+            outs.append(a if a is not None else (np.zeros((self.ny, self.nx)) if w else None))
+        _check("iilbm_get_macros_noalloc",
+               self._L.iilbm_get_macros_noalloc(self._h, *[_ptr(a) for a in outs]))
+        return tuple(outs)
 
     def iilbm_get_markers(self):
         n = self.n_markers

@@ -166,6 +166,7 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
             cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess &&
             cudaMalloc(&h->A, 9 * (size_t)g.plane * h->sbytes) == cudaSuccess &&
+            cudaMalloc(&h->uf, 2 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
             cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->d_tiles_total, sizeof(unsigned long long)) == cudaSuccess;
   for (int b = 0; b < 2 && ok; b++)
@@ -200,7 +201,7 @@ int iilbm_destroy(iilbm_t h) {
   if (h->side) cudaStreamSynchronize(h->side);
   drop_graph(h);
   free_interface(h);
-  void *bufs[] = {h->A, h->Jb[0], h->Jb[1], h->gb[0], h->gb[1], h->flagsb[0], h->flagsb[1],
+  void *bufs[] = {h->A, h->uf, h->Jb[0], h->Jb[1], h->gb[0], h->gb[1], h->flagsb[0], h->flagsb[1],
                   h->tile_list[0], h->tile_list[1], h->tile_count[0], h->tile_count[1],
                   h->d_status, h->d_tiles_total};
   for (void *b : bufs)
@@ -337,22 +338,22 @@ int drain_events(iilbm_lattice *h) {
 }
 
 // Kernels launched by one step: lean stream-collide; with an interface also the
-// interpolation, the forced stream-collide and the interface phase (clear, fused).
+// forced stream-collide, the interpolation and the interface phase (clear, fused).
 long long kernels_per_step(const iilbm_lattice *h) { return 1 + (h->nm > 0 ? 4 : 0); }
 
 bool pipelined(const iilbm_lattice *h) { return h->overlap && h->nm > 0; }
 
 // One time step of the current state n (its interface already prepared in buffer
-// n & 1).  Main stream: interpolation (+ marker move), lean stream-collide.  With
-// overlap, the side stream (highest priority) forks right after the interpolation and
-// runs the forced stream-collide of the flagged tiles, then the interface phase of
-// state n + 1 (buffer (n+1) & 1) -- which needs only X^{n+1} -- and joins before the
-// step ends.  Without overlap everything runs in that order on the main stream.  Safe
-// inside stream capture.
+// n & 1).  Main stream: the lean stream-collide (every tile without a jump or force).
+// Second stream (highest priority), forked at the start of the step: the forced
+// stream-collide of the flagged tiles, which also leaves the collision velocity there,
+// the interpolation from it with the marker move (X^{n+1}), then the interface phase of
+// state n + 1 in buffer (n+1) & 1; it joins before the step ends.  Without overlap the
+// same kernels run in that order on the main stream.  Safe inside stream capture.
 int one_step(iilbm_lattice *h, int ev_slot) {
   int rc;
-  if ((rc = launch_interp(h))) return rc;
   const bool pipe = pipelined(h);
+  cudaStream_t s2 = pipe ? h->side : h->stream;
   if (pipe) {
     CK(cudaEventRecord(h->ev_fork, h->stream));
     CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
@@ -361,8 +362,9 @@ int one_step(iilbm_lattice *h, int ev_slot) {
   // graph (cudaEventRecordExternal); outside a capture they are plain records.
   const unsigned evflag = h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (ev_slot >= 0) CK(cudaEventRecordWithFlags(h->ev[2 * ev_slot], h->stream, evflag));
-  if ((rc = launch_stream_collide(h, pipe ? h->side : h->stream))) return rc;
+  if ((rc = launch_stream_collide(h, s2))) return rc;
   if (ev_slot >= 0) CK(cudaEventRecordWithFlags(h->ev[2 * ev_slot + 1], h->stream, evflag));
+  if ((rc = launch_interp(h, s2))) return rc;
   if (pipe) {
     rc = launch_interface_phase(h, (int)((h->step + 1) & 1), h->side);  // state n + 1
     if (rc) return rc;

@@ -123,6 +123,7 @@ struct iilbm_lattice {
   void *Jb[2];
   void *gb[2];
   unsigned *flagsb[2];
+  void *uf;           // [2][plane] collision velocity on flagged tiles (for interpolation)
   int *tile_list[2];  // flagged tiles of each buffer, appended by the interface phase
   int *tile_count[2]; // per buffer: [0] flagged tiles, [1] cut-link crossings
   unsigned long long *d_tiles_total;  // flagged tiles summed while timing
@@ -159,7 +160,7 @@ struct iilbm_lattice {
 // Launchers (defined in lattice.cu / interface.cu).
 namespace iilbm {
 int launch_stream_collide(iilbm_lattice *h, cudaStream_t forced_stream);
-int launch_interp(iilbm_lattice *h);
+int launch_interp(iilbm_lattice *h, cudaStream_t s);
 int launch_macros(iilbm_lattice *h, double *drho, double *ux, double *uy);
 int launch_set_populations(iilbm_lattice *h, const double *df, bool equilibrium,
                            const double *rho, const double *ux, const double *uy);

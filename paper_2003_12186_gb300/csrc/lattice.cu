@@ -48,7 +48,8 @@ CollP<T> make_collp(const iilbm_config &c) {
 //   feq_i - w_i rho0 = w_i [drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u^2)]  (Eq. 23)
 //   Guo source  Gt_i = w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]  (Eqs. 21-22)
 template <typename T, int COLL>
-__device__ __forceinline__ T collide(T f[9], T gx, T gy, const CollP<T> &p) {
+__device__ __forceinline__ T collide(T f[9], T gx, T gy, const CollP<T> &p, T &ux_out,
+                                     T &uy_out) {
   const T drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
   const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
   const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
@@ -56,6 +57,8 @@ __device__ __forceinline__ T collide(T f[9], T gx, T gy, const CollP<T> &p) {
   const T ir = T(1) / rho;
   const T jxh = jx + T(0.5) * gx, jyh = jy + T(0.5) * gy;  // rho u
   const T ux = jxh * ir, uy = jyh * ir;
+  ux_out = ux;
+  uy_out = uy;
   if (COLL == IILBM_SRT) {
     const T u2 = ux * ux + uy * uy;
     const T ug = ux * gx + uy * gy;
@@ -193,6 +196,11 @@ template <> struct Vec<__nv_bfloat16> {
 
 // V consecutive arithmetic values (jump / force fields): float4 or double2.
 template <typename T, int V>
+__device__ inline void stT(T *p, const T *v) {
+  if constexpr (sizeof(T) == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+template <typename T, int V>
 __device__ inline void ldT(const T *p, T *o) {
   if constexpr (sizeof(T) == 4) {
     const float4 t = *reinterpret_cast<const float4 *>(p);
@@ -210,6 +218,7 @@ template <typename S, int COLL, bool ODD, int BC, bool FORCED>
 __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
                                                 typename Store<S>::T *__restrict__ Jf,
                                                 typename Store<S>::T *__restrict__ gf,
+                                                typename Store<S>::T *__restrict__ uf,
                                                 const Geom &geo,
                                                 const CollP<typename Store<S>::T> &p, int *status,
                                                 int xb, int yb) {
@@ -249,8 +258,13 @@ __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
     gx += gf[here];
     gy += gf[P + here];
   }
-  const T drho = collide<T, COLL>(f, gx, gy, p);
+  T ux, uy;
+  const T drho = collide<T, COLL>(f, gx, gy, p, ux, uy);
   if (!isfinite(drho)) atomicOr(status, ST_NONFINITE);
+  if (FORCED) {  // the velocity the markers are interpolated from (Eq. 20)
+    uf[here] = ux;
+    uf[P + here] = uy;
+  }
 #pragma unroll
   for (int i = 0; i < 9; i++) {
     long long dst = opp(i) * P + here;
@@ -274,6 +288,7 @@ template <typename S, int COLL, bool ODD, int BC, bool FORCED>
 __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
                                              typename Store<S>::T *__restrict__ Jf,
                                              typename Store<S>::T *__restrict__ gf,
+                                             typename Store<S>::T *__restrict__ uf,
                                              const Geom &geo,
                                              const CollP<typename Store<S>::T> &p, int *status,
                                              int xb, int yb) {
@@ -351,17 +366,22 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
     for (int j = 0; j < V; j++) { gx[j] += a[j]; gy[j] += b[j]; }
   }
   bool finite = true;
+  T uxv[V], uyv[V];
 #pragma unroll
   for (int j = 0; j < V; j++) {
     T fc[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) fc[i] = f[i][j];
-    const T drho = collide<T, COLL>(fc, gx[j], gy[j], p);
+    const T drho = collide<T, COLL>(fc, gx[j], gy[j], p, uxv[j], uyv[j]);
     finite = finite && isfinite(drho);
 #pragma unroll
     for (int i = 0; i < 9; i++) f[i][j] = fc[i];
   }
   if (active && !finite) atomicOr(status, ST_NONFINITE);
+  if (FORCED && active) {  // the velocity the markers are interpolated from (Eq. 20)
+    stT<T, V>(uf + here, uxv);
+    stT<T, V>(uf + P + here, uyv);
+  }
 
 #pragma unroll
   for (int i = 0; i < 9; i++) {
@@ -416,7 +436,7 @@ __global__ void __launch_bounds__(32 * TILE_Y)
                      const CollP<typename Store<S>::T> p, int *status) {
   const int xb = blockIdx.x * 32, yb = blockIdx.y * TILE_Y;
   if (flags[blockIdx.y * geo.ntx + xb / TILE_X]) return;  // uniform per block
-  sc_scalar_block<S, COLL, ODD, BC, false>(A, nullptr, nullptr, geo, p, status, xb, yb);
+  sc_scalar_block<S, COLL, ODD, BC, false>(A, nullptr, nullptr, nullptr, geo, p, status, xb, yb);
 }
 
 // At least three resident blocks per SM (<= 85 registers): the odd step would otherwise
@@ -428,7 +448,7 @@ __global__ void __launch_bounds__(32 * VEC_ROWS, 3)
   constexpr int W = 32 * Vec<S>::V;  // nodes per warp row
   const int xb = blockIdx.x * W, yb = blockIdx.y * VEC_ROWS;
   if (flags[blockIdx.y * geo.ntx + xb / TILE_X]) return;  // uniform per block
-  sc_vec_block<S, COLL, ODD, BC, false>(A, nullptr, nullptr, geo, p, status, xb, yb);
+  sc_vec_block<S, COLL, ODD, BC, false>(A, nullptr, nullptr, nullptr, geo, p, status, xb, yb);
 }
 
 // Forced kernels: blocks stride over the list of flagged tiles of this step.
@@ -436,6 +456,7 @@ template <typename S, int COLL, bool ODD, int BC>
 __global__ void __launch_bounds__(32 * TILE_Y)
     k_stream_collide_forced(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
                             typename Store<S>::T *__restrict__ gf,
+                            typename Store<S>::T *__restrict__ uf,
                             const int *__restrict__ list, const int *__restrict__ count,
                             const Geom geo, const CollP<typename Store<S>::T> p, int *status) {
   const int n = *count;
@@ -443,7 +464,7 @@ __global__ void __launch_bounds__(32 * TILE_Y)
     const int tile = list[t];
     const int tx = (tile % geo.ntx) * TILE_X, ty = (tile / geo.ntx) * TILE_Y;
     for (int sub = 0; sub < TILE_X; sub += 32)
-      sc_scalar_block<S, COLL, ODD, BC, true>(A, Jf, gf, geo, p, status, tx + sub, ty);
+      sc_scalar_block<S, COLL, ODD, BC, true>(A, Jf, gf, uf, geo, p, status, tx + sub, ty);
   }
 }
 
@@ -451,6 +472,7 @@ template <typename S, int COLL, bool ODD, int BC>
 __global__ void __launch_bounds__(32 * VEC_ROWS)
     k_stream_collide_vec_forced(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
                                 typename Store<S>::T *__restrict__ gf,
+                                typename Store<S>::T *__restrict__ uf,
                                 const int *__restrict__ list, const int *__restrict__ count,
                                 const Geom geo, const CollP<typename Store<S>::T> p,
                                 int *status) {
@@ -460,7 +482,7 @@ __global__ void __launch_bounds__(32 * VEC_ROWS)
     const int tile = list[t];
     const int tx = (tile % geo.ntx) * TILE_X, ty = (tile / geo.ntx) * TILE_Y;
     for (int sub = 0; sub < TILE_X; sub += W)
-      sc_vec_block<S, COLL, ODD, BC, true>(A, Jf, gf, geo, p, status, tx + sub, ty);
+      sc_vec_block<S, COLL, ODD, BC, true>(A, Jf, gf, uf, geo, p, status, tx + sub, ty);
   }
 }
 
@@ -501,20 +523,18 @@ __device__ inline void node_macros(const S *A, const typename Store<S>::T *Jf,
 
 // Velocity interpolation U_k = sum_x u(x) delta_h(x - X_k) (Eq. 20), 16 threads per
 // marker (one per stencil node), FP64 accumulation; a membrane marker then moves,
-// X_k += U_k.  The interpolation reads the state before the stream-collide that
-// overwrites it, so it runs first in each step.
-template <typename S>
-__global__ void k_interp(const S *__restrict__ A, const typename Store<S>::T *__restrict__ Jf,
-                         const typename Store<S>::T *__restrict__ gf, const Geom geo,
-                         const CollP<typename Store<S>::T> p, bool odd, double *X, int n,
-                         double *U, int moves) {
+// X_k += U_k.  u is the collision velocity of the step (jump and g/2 included) that the
+// forced stream-collide left in uf for every node of the flagged tiles -- which cover
+// every marker's stencil -- so this runs right after the forced kernel.
+template <typename T>
+__global__ void k_interp(const T *__restrict__ uf, const Geom geo, double *X, int n, double *U,
+                         int moves) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = tid >> 4, l = tid & 15;
   double sx = 0.0, sy = 0.0;
   if (k < n) {
     const double Xk = X[2 * k], Yk = X[2 * k + 1];
-    const int x0 = (int)floor(Xk) - 1, y0 = (int)floor(Yk) - 1;
-    const int xa = x0 + (l & 3), yb = y0 + (l >> 2);
+    const int xa = (int)floor(Xk) - 1 + (l & 3), yb = (int)floor(Yk) - 1 + (l >> 2);
     int xi = xa, yi = yb;
     bool ok = true;
     if (geo.bc == IILBM_BC_CHANNEL) ok = xi >= 0 && xi < geo.nx;
@@ -522,12 +542,10 @@ __global__ void k_interp(const S *__restrict__ A, const typename Store<S>::T *__
     if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
     else ok = ok && yi >= 0 && yi < geo.ny;
     if (ok) {
-      double drho, ux, uy;
-      node_macros<S>(A, Jf, gf, geo, p, odd, xi, yi, drho, ux, uy);
-      using T = typename Store<S>::T;
+      const long long here = (long long)yi * geo.pitch + xi;
       const double w = (double)(phi4<T>(T((double)xa - Xk)) * phi4<T>(T((double)yb - Yk)));
-      sx = ux * w;
-      sy = uy * w;
+      sx = (double)uf[here] * w;
+      sy = (double)uf[geo.plane + here] * w;
     }
   }
 #pragma unroll
@@ -637,10 +655,10 @@ static void sc_launch_bc(iilbm_lattice *h, cudaStream_t forced_stream) {
   const int grid = h->forced_grid;
   if (vec)
     k_stream_collide_vec_forced<S, COLL, ODD, BC><<<grid, 32 * VEC_ROWS, 0, forced_stream>>>(
-        (S *)h->A, J, gf, h->tile_list[b], h->tile_count[b], g, p, h->d_status);
+        (S *)h->A, J, gf, (T *)h->uf, h->tile_list[b], h->tile_count[b], g, p, h->d_status);
   else
     k_stream_collide_forced<S, COLL, ODD, BC><<<grid, dim3(32, TILE_Y), 0, forced_stream>>>(
-        (S *)h->A, J, gf, h->tile_list[b], h->tile_count[b], g, p, h->d_status);
+        (S *)h->A, J, gf, (T *)h->uf, h->tile_list[b], h->tile_count[b], g, p, h->d_status);
 }
 
 template <typename S, int COLL, bool ODD>
@@ -668,19 +686,16 @@ int launch_stream_collide(iilbm_lattice *h, cudaStream_t forced_stream) {
   });
 }
 
-int launch_interp(iilbm_lattice *h) {
+int launch_interp(iilbm_lattice *h, cudaStream_t s) {
   if (h->nm == 0) return IILBM_OK;
-  const bool odd = h->step & 1;
-  return dispatch_storage(h->cfg.storage, [&](auto *tag) {
-    using S = std::remove_pointer_t<decltype(tag)>;
-    using T = typename Store<S>::T;
-    const int threads = 16 * h->nm;
-    const int b = h->step & 1;
-    k_interp<S><<<(threads + 255) / 256, 256, 0, h->stream>>>(
-        (const S *)h->A, (const T *)h->Jb[b], (const T *)h->gb[b], h->geom,
-        make_collp<T>(h->cfg), odd, h->X, h->nm, h->U, h->ip.moves);
-    return last_error();
-  });
+  const int threads = 16 * h->nm;
+  if (h->cfg.storage == IILBM_F64)
+    k_interp<double><<<(threads + 255) / 256, 256, 0, s>>>((const double *)h->uf, h->geom, h->X,
+                                                          h->nm, h->U, h->ip.moves);
+  else
+    k_interp<float><<<(threads + 255) / 256, 256, 0, s>>>((const float *)h->uf, h->geom, h->X,
+                                                         h->nm, h->U, h->ip.moves);
+  return last_error();
 }
 
 int launch_macros(iilbm_lattice *h, double *drho, double *ux, double *uy) {

@@ -178,22 +178,32 @@ __global__ void __launch_bounds__(128)
     nrm[2 * k + 1] = (double)m.ny;
   }
   const double Ax = X[2 * k], Ay = X[2 * k + 1], Bx = X[2 * kp], By = X[2 * kp + 1];
+  // Everything geometric below runs on the coordinates snapped to 2^-24 (exact, as the
+  // crossing predicate needs) in 64-bit integers: GB300 executes FP64 -- compares,
+  // conversions and rounding included -- at a small fraction of its integer rate.
   const bool inside = fabs(Ax) <= MAX_COORD && fabs(Ay) <= MAX_COORD && fabs(Bx) <= MAX_COORD &&
                       fabs(By) <= MAX_COORD;
+  const long long ax = inside ? __double2ll_rn(Ax * QSCALE) : 0;
+  const long long ay = inside ? __double2ll_rn(Ay * QSCALE) : 0;
+  const long long bx = inside ? __double2ll_rn(Bx * QSCALE) : 0;
+  const long long by = inside ? __double2ll_rn(By * QSCALE) : 0;
+  const long long Q = (long long)QSCALE;
+  const long long QMAX = (long long)(MAX_SEGMENT * QSCALE);
+  // floor / ceil of a snapped coordinate in lattice units
+  auto qfloor = [](long long v) { return (int)(v >> 24); };
+  auto qceil = [](long long v) { return (int)-((-v) >> 24); };
   // ---- cut links of segment k -> k+1
   int found = 0;
-  if (jump && inside && fabs(Bx - Ax) < MAX_SEGMENT && fabs(By - Ay) < MAX_SEGMENT) {
-    const long long ax = __double2ll_rn(Ax * QSCALE), ay = __double2ll_rn(Ay * QSCALE);
-    const long long bx = __double2ll_rn(Bx * QSCALE), by = __double2ll_rn(By * QSCALE);
-    const int x0 = (int)floor(fmin(Ax, Bx)) - 1, x1 = (int)ceil(fmax(Ax, Bx)) + 1;
-    const int y0 = (int)floor(fmin(Ay, By)) - 1, y1 = (int)ceil(fmax(Ay, By)) + 1;
+  if (jump && inside && llabs(bx - ax) < QMAX && llabs(by - ay) < QMAX) {
+    const int x0 = qfloor(min(ax, bx)) - 1, x1 = qceil(max(ax, bx)) + 1;
+    const int y0 = qfloor(min(ay, by)) - 1, y1 = qceil(max(ay, by)) + 1;
     const int W = x1 - x0 + 1, H = y1 - y0 + 1;
     const int ncand = W * H * 8;
-    const long long Q = (long long)QSCALE;
     int bc_idx[CROSS_BUF], bc_s[CROSS_BUF];
     long long bc_o3[CROSS_BUF], bc_o4[CROSS_BUF];
     int nb = 0;
-    // apply the buffered crossings: coefficient s w_i/c_s^2 Fn(t), t along A -> B
+    // apply the buffered crossings: coefficient s w_i/c_s^2 Fn(t), t = o3 / (o3 - o4)
+    // along A -> B (an FP32 quotient refined by one FP64 Newton step, ~1e-14)
     auto flush = [&]() {
 #pragma unroll
       for (int q = 0; q < CROSS_BUF; q++) {
@@ -203,7 +213,11 @@ __global__ void __launch_bounds__(128)
         int xd = x0 + cell % W, yd = y0 + cell / W;
         xd = geo.bc == IILBM_BC_CHANNEL ? xd : wrap(xd, geo.nx);
         yd = geo.bc == IILBM_BC_PERIODIC ? wrap(yd, geo.ny) : yd;
-        double t = (double)bc_o3[q] / ((double)bc_o3[q] - (double)bc_o4[q]);
+        const long long den = bc_o3[q] - bc_o4[q];  // nonzero: the link crosses A -> B
+        const double num = (double)bc_o3[q], dd = (double)den;
+        const float rf = 1.0f / (float)dd;
+        double t = (double)((float)num * rf);
+        t = fma(num - t * dd, (double)rf, t);  // one Newton correction with the FP32 reciprocal
         t = fmin(fmax(t, 0.0), 1.0);
         const double F = (1.0 - t) * FnA + t * FnB;
         const double coef = (double)bc_s[q] * 3.0 * wt<double>(i) * F;  // w_i / c_s^2 Fn
@@ -246,6 +260,7 @@ __global__ void __launch_bounds__(128)
   if (lane == 0 && found) atomicAdd(&tb.ctr[1], found);
   // ---- spread P_k (Eq. 46 / Eq. 17), lanes 0..15 one stencil node each
   if (lane < 16 && inside) {
+    // the stencil is chosen from the FP64 coordinate, as the interpolation does
     const int xa = (int)floor(Ax) - 1 + (lane & 3), yb = (int)floor(Ay) - 1 + (lane >> 2);
     int xi = xa, yi = yb;
     bool ok = true;
@@ -253,8 +268,16 @@ __global__ void __launch_bounds__(128)
     else xi = wrap(xi, geo.nx);
     if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
     else ok = ok && yi >= 0 && yi < geo.ny;
-    // node offsets are exact in FP64 (Sterbenz), then rounded to T
-    const T w = ok ? phi4t<T>(T((double)xa - Ax)) * phi4t<T>(T((double)yb - Ay)) : T(0);
+    // node offsets: exact in FP64 for FP64 storage; from the snapped integers otherwise
+    T rx, ry;
+    if (sizeof(T) == 8) {
+      rx = T((double)xa - Ax);
+      ry = T((double)yb - Ay);
+    } else {
+      rx = T((int)((long long)xa * Q - ax)) * T(1.0 / QSCALE);
+      ry = T((int)((long long)yb * Q - ay)) * T(1.0 / QSCALE);
+    }
+    const T w = ok ? phi4t<T>(rx) * phi4t<T>(ry) : T(0);
     if (w != T(0)) {
       const long long here = (long long)yi * geo.pitch + xi;
       atomicAdd(&gf[here], Pkx * w);
@@ -265,9 +288,9 @@ __global__ void __launch_bounds__(128)
   // [floor(min x) - 2, ceil(max x) + 2] x [floor(min y) - 2, ceil(max y) + 2]
   if (inside) {
     int cols[MAX_TILE_SPAN], rows[MAX_TILE_SPAN];
-    const int nc = tile_span((int)floor(fmin(Ax, Bx)) - 2, (int)ceil(fmax(Ax, Bx)) + 2, geo.nx,
+    const int nc = tile_span(qfloor(min(ax, bx)) - 2, qceil(max(ax, bx)) + 2, geo.nx,
                              geo.bc != IILBM_BC_CHANNEL, TILE_X, cols);
-    const int nr = tile_span((int)floor(fmin(Ay, By)) - 2, (int)ceil(fmax(Ay, By)) + 2, geo.ny,
+    const int nr = tile_span(qfloor(min(ay, by)) - 2, qceil(max(ay, by)) + 2, geo.ny,
                              geo.bc == IILBM_BC_PERIODIC, TILE_Y, rows);
     for (int t = lane; t < nc * nr; t += 32) flag_tile(tb, rows[t / nc] * geo.ntx + cols[t % nc]);
   }

@@ -70,8 +70,12 @@ int prepare(iilbm_lattice *h) {
 }
 
 void drop_graph(iilbm_lattice *h) {
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  h->gexec = nullptr;
+  for (int r = 0; r < GRAPH_RING; r++) {
+    if (h->gexec[r]) cudaGraphExecDestroy(h->gexec[r]);
+    h->gexec[r] = nullptr;
+    h->ring_pending[r] = false;
+  }
+  h->ring_next = 0;
 }
 
 // Clear every jump / force buffer (used when the interface or the state is replaced
@@ -83,6 +87,8 @@ int clear_fields(iilbm_lattice *h) {
     CK(cudaMemsetAsync(h->gb[b], 0, 2 * (size_t)g.plane * h->tbytes, h->stream));
     CK(cudaMemsetAsync(h->flagsb[b], 0, (size_t)h->ntiles * sizeof(unsigned), h->stream));
     CK(cudaMemsetAsync(h->tile_count[b], 0, 2 * sizeof(int), h->stream));
+    static const unsigned one = 1u;  // a tag no cleared flag carries
+    CK(cudaMemcpyAsync(h->tagb[b], &one, sizeof one, cudaMemcpyHostToDevice, h->stream));
   }
   h->prepared = false;
   return IILBM_OK;
@@ -174,7 +180,8 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
          cudaMalloc(&h->gb[b], 2 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
          cudaMalloc(&h->flagsb[b], (size_t)h->ntiles * sizeof(unsigned)) == cudaSuccess &&
          cudaMalloc(&h->tile_list[b], (size_t)h->ntiles * sizeof(int)) == cudaSuccess &&
-         cudaMalloc(&h->tile_count[b], 2 * sizeof(int)) == cudaSuccess;
+         cudaMalloc(&h->tile_count[b], 2 * sizeof(int)) == cudaSuccess &&
+         cudaMalloc(&h->tagb[b], sizeof(unsigned)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     iilbm_destroy(h);
@@ -203,6 +210,7 @@ int iilbm_destroy(iilbm_t h) {
   free_interface(h);
   void *bufs[] = {h->A, h->uf, h->Jb[0], h->Jb[1], h->gb[0], h->gb[1], h->flagsb[0], h->flagsb[1],
                   h->tile_list[0], h->tile_list[1], h->tile_count[0], h->tile_count[1],
+                  h->tagb[0], h->tagb[1],
                   h->d_status, h->d_tiles_total};
   for (void *b : bufs)
     if (b) cudaFree(b);
@@ -210,7 +218,7 @@ int iilbm_destroy(iilbm_t h) {
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->ev[0])
-    for (int e = 0; e < 2 * 256; e++) cudaEventDestroy(h->ev[e]);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return IILBM_OK;
@@ -324,22 +332,42 @@ int iilbm_get_populations(iilbm_t h, double *df) {
   return rc ? rc : read_status(h);
 }
 
-// Fold the recorded stream-collide event pairs into the running sum.
+// Fold recorded lean stream-collide event pairs into the running sum: the eager pairs,
+// or the GRAPH_STEPS pairs of ring slot r.
 int drain_events(iilbm_lattice *h) {
   if (h->nev == 0) return IILBM_OK;
-  CK(cudaEventSynchronize(h->ev[2 * h->nev - 1]));
+  CK(cudaEventSynchronize(h->ev[EAGER_EV0 + 2 * h->nev - 1]));
   for (int e = 0; e < h->nev; e++) {
     float ms = 0;
-    CK(cudaEventElapsedTime(&ms, h->ev[2 * e], h->ev[2 * e + 1]));
+    CK(cudaEventElapsedTime(&ms, h->ev[EAGER_EV0 + 2 * e], h->ev[EAGER_EV0 + 2 * e + 1]));
     h->sc_ms += ms;
   }
   h->nev = 0;
   return IILBM_OK;
 }
 
+int drain_slot(iilbm_lattice *h, int r) {
+  if (!h->ring_pending[r]) return IILBM_OK;
+  const int e0 = 2 * GRAPH_STEPS * r;
+  CK(cudaEventSynchronize(h->ev[e0 + 2 * GRAPH_STEPS - 1]));
+  for (int k = 0; k < GRAPH_STEPS; k++) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, h->ev[e0 + 2 * k], h->ev[e0 + 2 * k + 1]));
+    h->sc_ms += ms;
+  }
+  h->ring_pending[r] = false;
+  return IILBM_OK;
+}
+
+int drain_all(iilbm_lattice *h) {
+  int rc = drain_events(h);
+  for (int r = 0; r < GRAPH_RING && !rc; r++) rc = drain_slot(h, r);
+  return rc;
+}
+
 // Kernels launched by one step: lean stream-collide; with an interface also the
-// forced stream-collide, the interpolation and the interface phase (clear, fused).
-long long kernels_per_step(const iilbm_lattice *h) { return 1 + (h->nm > 0 ? 4 : 0); }
+// forced stream-collide, the interpolation and the fused interface kernel.
+long long kernels_per_step(const iilbm_lattice *h) { return 1 + (h->nm > 0 ? 3 : 0); }
 
 bool pipelined(const iilbm_lattice *h) { return h->overlap && h->nm > 0; }
 
@@ -350,6 +378,7 @@ bool pipelined(const iilbm_lattice *h) { return h->overlap && h->nm > 0; }
 // the interpolation from it with the marker move (X^{n+1}), then the interface phase of
 // state n + 1 in buffer (n+1) & 1; it joins before the step ends.  Without overlap the
 // same kernels run in that order on the main stream.  Safe inside stream capture.
+// ev_slot: index of the start event of the lean stream-collide timing pair, or -1.
 int one_step(iilbm_lattice *h, int ev_slot) {
   int rc;
   const bool pipe = pipelined(h);
@@ -361,9 +390,9 @@ int one_step(iilbm_lattice *h, int ev_slot) {
   // Timing events: inside a stream capture they must become event-record nodes of the
   // graph (cudaEventRecordExternal); outside a capture they are plain records.
   const unsigned evflag = h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-  if (ev_slot >= 0) CK(cudaEventRecordWithFlags(h->ev[2 * ev_slot], h->stream, evflag));
+  if (ev_slot >= 0) CK(cudaEventRecordWithFlags(h->ev[ev_slot], h->stream, evflag));
   if ((rc = launch_stream_collide(h, s2))) return rc;
-  if (ev_slot >= 0) CK(cudaEventRecordWithFlags(h->ev[2 * ev_slot + 1], h->stream, evflag));
+  if (ev_slot >= 0) CK(cudaEventRecordWithFlags(h->ev[ev_slot + 1], h->stream, evflag));
   if ((rc = launch_interp(h, s2))) return rc;
   if (pipe) {
     rc = launch_interface_phase(h, (int)((h->step + 1) & 1), h->side);  // state n + 1
@@ -376,15 +405,16 @@ int one_step(iilbm_lattice *h, int ev_slot) {
   return IILBM_OK;
 }
 
-// Capture GRAPH_STEPS steps starting from an even, prepared state.
-int capture_graph(iilbm_lattice *h) {
-  drop_graph(h);
+// Capture GRAPH_STEPS steps starting from an even, prepared state into ring slot r
+// (with timing on, its steps record into the slot's own event pairs).
+int capture_graph(iilbm_lattice *h, int r) {
   const long long step0 = h->step;
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   int rc = IILBM_OK;
   h->capturing = true;
-  for (int k = 0; k < GRAPH_STEPS && !rc; k++) rc = one_step(h, h->timing ? k : -1);
+  for (int k = 0; k < GRAPH_STEPS && !rc; k++)
+    rc = one_step(h, h->timing ? 2 * (GRAPH_STEPS * r + k) : -1);
   h->capturing = false;
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
   cudaGetLastError();
@@ -396,13 +426,13 @@ int capture_graph(iilbm_lattice *h) {
   }
   if (e != cudaSuccess) return IILBM_ERR_CUDA;
   // honour the side stream's priority inside the graph
-  e = cudaGraphInstantiateWithFlags(&h->gexec, graph, cudaGraphInstantiateFlagUseNodePriority);
+  e = cudaGraphInstantiateWithFlags(&h->gexec[r], graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
-    h->gexec = nullptr;
+    h->gexec[r] = nullptr;
+    cudaGetLastError();
     return IILBM_ERR_CUDA;
   }
-  h->graph_timing = h->timing;
   return IILBM_OK;
 }
 
@@ -414,25 +444,32 @@ int iilbm_step(iilbm_t h, int32_t n) {
     const bool graph_ok = h->use_graph && (pipelined(h) || h->nm == 0) && (h->step & 1) == 0 &&
                           n >= GRAPH_STEPS;
     if (graph_ok) {
-      if (h->timing && (rc = drain_events(h))) return rc;
-      if (!h->gexec || h->graph_timing != h->timing)
-        if ((rc = capture_graph(h))) return rc;
-      CK(cudaGraphLaunch(h->gexec, h->stream));
+      if (h->graph_timing != h->timing) {
+        if ((rc = drain_all(h))) return rc;
+        drop_graph(h);
+        h->graph_timing = h->timing;
+      }
+      // without timing one executable suffices; with timing the ring lets each launch
+      // record into events that the launch GRAPH_RING earlier has long finished with
+      const int r = h->timing ? h->ring_next : 0;
+      if (h->timing && (rc = drain_slot(h, r))) return rc;
+      if (!h->gexec[r] && (rc = capture_graph(h, r))) return rc;
+      CK(cudaGraphLaunch(h->gexec[r], h->stream));
       h->step += GRAPH_STEPS;
       h->prepared = true;
       n -= GRAPH_STEPS;
       if (h->timing) {
-        h->nev = GRAPH_STEPS;
+        h->ring_pending[r] = true;
+        h->ring_next = (r + 1) % GRAPH_RING;
         h->sc_launches += GRAPH_STEPS;
         h->kernel_launches += GRAPH_STEPS * kernels_per_step(h);
-        if ((rc = drain_events(h))) return rc;
       }
       continue;
     }
     int slot = -1;
     if (h->timing) {
-      if (h->nev == 256 && (rc = drain_events(h))) return rc;
-      slot = h->nev;
+      if (h->nev == EAGER_PAIRS && (rc = drain_events(h))) return rc;
+      slot = EAGER_EV0 + 2 * h->nev;
     }
     if ((rc = one_step(h, slot))) return rc;
     if (h->timing) {
@@ -461,10 +498,11 @@ int iilbm_set_option(iilbm_t h, int32_t option, int32_t value) {
 int iilbm_set_timing(iilbm_t h, int32_t enable) {
   if (!h) return IILBM_ERR_INVALID_ARG;
   CK(cudaMemsetAsync(h->d_tiles_total, 0, sizeof(unsigned long long), h->stream));
+  const int nev = (int)(sizeof(h->ev) / sizeof(h->ev[0]));
   if (enable && !h->ev[0])
-    for (int e = 0; e < 2 * 256; e++) CK(cudaEventCreate(&h->ev[e]));
-  if (!enable && h->nev) {
-    int rc = drain_events(h);
+    for (int e = 0; e < nev; e++) CK(cudaEventCreate(&h->ev[e]));
+  if (!enable) {
+    int rc = drain_all(h);
     if (rc) return rc;
   }
   h->timing = enable != 0;
@@ -474,7 +512,7 @@ int iilbm_set_timing(iilbm_t h, int32_t enable) {
 int iilbm_get_timing(iilbm_t h, double *sc_ms, int32_t *launches, int64_t *kernel_launches,
                      int64_t *flagged_tiles) {
   if (!h) return IILBM_ERR_INVALID_ARG;
-  int rc = drain_events(h);
+  int rc = drain_all(h);
   if (rc) return rc;
   unsigned long long tiles = 0;
   CK(cudaStreamSynchronize(h->side));

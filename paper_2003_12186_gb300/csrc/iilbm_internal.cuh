@@ -48,6 +48,9 @@ constexpr double QSCALE = 16777216.0;
 constexpr double MAX_SEGMENT = 16.0;
 constexpr double MAX_COORD = 16000.0;
 constexpr int GRAPH_STEPS = 32;
+constexpr int GRAPH_RING = 4;
+constexpr int EAGER_EV0 = 2 * GRAPH_STEPS * GRAPH_RING;  // first eager timing event
+constexpr int EAGER_PAIRS = 128;
 
 // ------------------------------------------------------------ storage types
 // Populations are stored as df * 2^k in S and computed in T (double for FP64
@@ -122,7 +125,8 @@ struct iilbm_lattice {
   // (and re-zeroes) the buffer of step n.
   void *Jb[2];
   void *gb[2];
-  unsigned *flagsb[2];
+  unsigned *flagsb[2];   // tile flags: flagged iff equal to the buffer's tag
+  unsigned *tagb[2];     // device word: tag of the buffer's current time level
   void *uf;           // [2][plane] collision velocity on flagged tiles (for interpolation)
   int *tile_list[2];  // flagged tiles of each buffer, appended by the interface phase
   int *tile_count[2]; // per buffer: [0] flagged tiles, [1] cut-link crossings
@@ -135,8 +139,12 @@ struct iilbm_lattice {
   bool use_graph;     // replay GRAPH_STEPS steps per CUDA-graph launch
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
-  cudaGraphExec_t gexec;
-  bool graph_timing;  // the instantiated graph records timing events
+  // graph ring: GRAPH_RING executables of GRAPH_STEPS steps; with timing on each one
+  // records into its own event set, so draining a set never waits on the GPU
+  cudaGraphExec_t gexec[iilbm::GRAPH_RING];
+  bool ring_pending[iilbm::GRAPH_RING];
+  int ring_next;
+  bool graph_timing;  // the instantiated graphs record timing events
   bool capturing;     // inside cudaStreamBeginCapture / EndCapture
   long long step;     // time level of the state; AA parity = step & 1
   bool prepared;      // jump / force of the current state already in J, g
@@ -151,7 +159,7 @@ struct iilbm_lattice {
   // diagnostics
   bool timing;
   int nev;                      // event pairs in use
-  cudaEvent_t ev[2 * 256];      // stream-collide start / stop events
+  cudaEvent_t ev[iilbm::EAGER_EV0 + 2 * iilbm::EAGER_PAIRS];  // lean stream-collide start / stop
   double sc_ms;
   int sc_launches;
   long long kernel_launches;    // every library kernel launched while timing

@@ -12,8 +12,7 @@
 //     (Eq. 46) into the force field;
 //   * flagging every touched tile and appending newly flagged tiles to the tile list
 //     that the forced stream-collide walks.
-// A clear kernel first resets the buffer's previous tiles (flags, jump, force), so the
-// dense [.][ny][pitch] fields are only ever touched on O(interface length) tiles.
+// The dense [.][ny][pitch] fields are only ever touched on O(interface length) tiles.
 #include "iilbm_internal.cuh"
 
 #include <cmath>
@@ -25,15 +24,16 @@ __device__ inline int tile_of(const Geom &g, int x, int y) {
 }
 
 struct TileBuf {
-  unsigned *flags;
+  unsigned *flags;            // a tile is flagged iff its entry equals *tag
+  const unsigned *tag;
   int *list;
   int *ctr;                   // [0] flagged tiles, [1] cut-link crossings
   unsigned long long *total;  // flagged tiles summed over phases (diagnostic)
 };
 
-// Flag a tile; the first thread to flag it appends it to the list.
-__device__ inline void flag_tile(const TileBuf &tb, int tile) {
-  if (tb.flags[tile] == 0u && atomicExch(&tb.flags[tile], 1u) == 0u) {
+// Flag a tile for this time level; the first thread to do so appends it to the list.
+__device__ inline void flag_tile(const TileBuf &tb, int tile, unsigned tag) {
+  if (tb.flags[tile] != tag && atomicExch(&tb.flags[tile], tag) != tag) {
     tb.list[atomicAdd(tb.ctr, 1)] = tile;
     atomicAdd(tb.total, 1ull);
   }
@@ -292,50 +292,24 @@ __global__ void __launch_bounds__(128)
                              geo.bc != IILBM_BC_CHANNEL, TILE_X, cols);
     const int nr = tile_span(qfloor(min(ay, by)) - 2, qceil(max(ay, by)) + 2, geo.ny,
                              geo.bc == IILBM_BC_PERIODIC, TILE_Y, rows);
-    for (int t = lane; t < nc * nr; t += 32) flag_tile(tb, rows[t / nc] * geo.ntx + cols[t % nc]);
-  }
-}
-
-// Reset the tiles a buffer flagged last time: flag, jump (8 planes), force (2 planes).
-// One block per listed tile (grid-stride); the counters are reset afterwards.
-template <typename T>
-__global__ void k_clear_tiles(TileBuf tb, Geom geo, T *Jf, T *gf) {
-  const int n = tb.ctr[0];
-  for (int t = blockIdx.x; t < n; t += gridDim.x) {
-    const int tile = tb.list[t];
-    const int x0 = (tile % geo.ntx) * TILE_X, y0 = (tile / geo.ntx) * TILE_Y;
-    for (int c = threadIdx.x; c < TILE_X * TILE_Y; c += blockDim.x) {
-      const int x = x0 + c % TILE_X, y = y0 + c / TILE_X;
-      if (x >= geo.nx || y >= geo.ny) continue;
-      const long long here = (long long)y * geo.pitch + x;
-#pragma unroll
-      for (int p = 0; p < 8; p++) Jf[p * geo.plane + here] = T(0);
-      gf[here] = T(0);
-      gf[geo.plane + here] = T(0);
-    }
-    if (threadIdx.x == 0) tb.flags[tile] = 0u;
+    const unsigned tag = *tb.tag;
+    for (int t = lane; t < nc * nr; t += 32)
+      flag_tile(tb, rows[t / nc] * geo.ntx + cols[t % nc], tag);
   }
 }
 
 // ---------------------------------------------------------- interface phase
-// Bring buffer buf to the interface of the markers X: clear its previous tiles, reset
-// its counters, then the fused interface kernel.
+// Bring buffer buf to the interface of the markers X.  The buffer arrives clean: its
+// jump / force entries were zeroed by the forced stream-collide that consumed them, its
+// counters reset and its tag advanced by the interpolation kernel since (or by the
+// set-up), so stale flags from earlier time levels no longer match.
 int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s) {
   if (h->nm == 0) return IILBM_OK;
   const int n = h->nm;
   if (h->ip.model == IILBM_DIRECT) return IILBM_ERR_INVALID_ARG;
-  const TileBuf tb{h->flagsb[buf], h->tile_list[buf], h->tile_count[buf], h->d_tiles_total};
+  const TileBuf tb{h->flagsb[buf], h->tagb[buf], h->tile_list[buf], h->tile_count[buf],
+                   h->d_tiles_total};
   const bool dbl = h->cfg.storage == IILBM_F64;
-  if (dbl)
-    k_clear_tiles<double><<<h->forced_grid, 256, 0, s>>>(tb, h->geom, (double *)h->Jb[buf],
-                                                        (double *)h->gb[buf]);
-  else
-    k_clear_tiles<float><<<h->forced_grid, 256, 0, s>>>(tb, h->geom, (float *)h->Jb[buf],
-                                                       (float *)h->gb[buf]);
-  if (cudaMemsetAsync(tb.ctr, 0, 2 * sizeof(int), s) != cudaSuccess) {
-    cudaGetLastError();
-    return IILBM_ERR_CUDA;
-  }
   const int threads = 32 * n;
   if (dbl)
     k_interface<double><<<(threads + 127) / 128, 128, 0, s>>>(

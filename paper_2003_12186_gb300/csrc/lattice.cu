@@ -264,6 +264,11 @@ __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
   if (FORCED) {  // the velocity the markers are interpolated from (Eq. 20)
     uf[here] = ux;
     uf[P + here] = uy;
+    // consumed: leave the buffer clean for the interface phase two steps on
+#pragma unroll
+    for (int i = 1; i < 9; i++) Jf[(i - 1) * P + here] = T(0);
+    gf[here] = T(0);
+    gf[P + here] = T(0);
   }
 #pragma unroll
   for (int i = 0; i < 9; i++) {
@@ -381,6 +386,14 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
   if (FORCED && active) {  // the velocity the markers are interpolated from (Eq. 20)
     stT<T, V>(uf + here, uxv);
     stT<T, V>(uf + P + here, uyv);
+    // consumed: leave the buffer clean for the interface phase two steps on
+    T z[V];
+#pragma unroll
+    for (int j = 0; j < V; j++) z[j] = T(0);
+#pragma unroll
+    for (int i = 1; i < 9; i++) stT<T, V>(Jf + (i - 1) * P + here, z);
+    stT<T, V>(gf + here, z);
+    stT<T, V>(gf + P + here, z);
   }
 
 #pragma unroll
@@ -432,10 +445,11 @@ constexpr int VEC_ROWS = TILE_Y;  // warps (rows) per block of the vectorised ke
 // Lean kernels: one block per (sub-)tile; a flagged tile is left to the forced kernel.
 template <typename S, int COLL, bool ODD, int BC>
 __global__ void __launch_bounds__(32 * TILE_Y)
-    k_stream_collide(S *__restrict__ A, const unsigned *__restrict__ flags, const Geom geo,
+    k_stream_collide(S *__restrict__ A, const unsigned *__restrict__ flags,
+                     const unsigned *__restrict__ tag, const Geom geo,
                      const CollP<typename Store<S>::T> p, int *status) {
   const int xb = blockIdx.x * 32, yb = blockIdx.y * TILE_Y;
-  if (flags[blockIdx.y * geo.ntx + xb / TILE_X]) return;  // uniform per block
+  if (flags[blockIdx.y * geo.ntx + xb / TILE_X] == *tag) return;  // uniform per block
   sc_scalar_block<S, COLL, ODD, BC, false>(A, nullptr, nullptr, nullptr, geo, p, status, xb, yb);
 }
 
@@ -443,11 +457,12 @@ __global__ void __launch_bounds__(32 * TILE_Y)
 // drop to two and lose a third of its memory parallelism.
 template <typename S, int COLL, bool ODD, int BC>
 __global__ void __launch_bounds__(32 * VEC_ROWS, 3)
-    k_stream_collide_vec(S *__restrict__ A, const unsigned *__restrict__ flags, const Geom geo,
+    k_stream_collide_vec(S *__restrict__ A, const unsigned *__restrict__ flags,
+                         const unsigned *__restrict__ tag, const Geom geo,
                          const CollP<typename Store<S>::T> p, int *status) {
   constexpr int W = 32 * Vec<S>::V;  // nodes per warp row
   const int xb = blockIdx.x * W, yb = blockIdx.y * VEC_ROWS;
-  if (flags[blockIdx.y * geo.ntx + xb / TILE_X]) return;  // uniform per block
+  if (flags[blockIdx.y * geo.ntx + xb / TILE_X] == *tag) return;  // uniform per block
   sc_vec_block<S, COLL, ODD, BC, false>(A, nullptr, nullptr, nullptr, geo, p, status, xb, yb);
 }
 
@@ -526,10 +541,18 @@ __device__ inline void node_macros(const S *A, const typename Store<S>::T *Jf,
 // X_k += U_k.  u is the collision velocity of the step (jump and g/2 included) that the
 // forced stream-collide left in uf for every node of the flagged tiles -- which cover
 // every marker's stencil -- so this runs right after the forced kernel.
+// Thread 0 also prepares the other buffer for the next interface phase (its readers
+// are done by now): advance its tag, so its old flags stop matching, and reset its
+// counters.
 template <typename T>
 __global__ void k_interp(const T *__restrict__ uf, const Geom geo, double *X, int n, double *U,
-                         int moves) {
+                         int moves, unsigned *next_tag, int *next_ctr) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid == 0) {
+    *next_tag += 1u;
+    next_ctr[0] = 0;
+    next_ctr[1] = 0;
+  }
   const int k = tid >> 4, l = tid & 15;
   double sx = 0.0, sy = 0.0;
   if (k < n) {
@@ -646,11 +669,13 @@ static void sc_launch_bc(iilbm_lattice *h, cudaStream_t forced_stream) {
   const bool vec = h->vector_sc && g.nx % V == 0;
   if (vec)
     k_stream_collide_vec<S, COLL, ODD, BC><<<dim3((g.nx + 32 * V - 1) / (32 * V), nyt),
-                                             32 * VEC_ROWS, 0, h->stream>>>((S *)h->A, fl, g, p,
+                                             32 * VEC_ROWS, 0, h->stream>>>((S *)h->A, fl,
+                                                                            h->tagb[b], g, p,
                                                                             h->d_status);
   else
     k_stream_collide<S, COLL, ODD, BC><<<dim3((g.nx + 31) / 32, nyt), dim3(32, TILE_Y), 0,
-                                         h->stream>>>((S *)h->A, fl, g, p, h->d_status);
+                                         h->stream>>>((S *)h->A, fl, h->tagb[b], g, p,
+                                                      h->d_status);
   if (h->nm == 0) return;  // no interface: no flagged tiles
   const int grid = h->forced_grid;
   if (vec)
@@ -689,12 +714,15 @@ int launch_stream_collide(iilbm_lattice *h, cudaStream_t forced_stream) {
 int launch_interp(iilbm_lattice *h, cudaStream_t s) {
   if (h->nm == 0) return IILBM_OK;
   const int threads = 16 * h->nm;
+  const int nb = (int)((h->step + 1) & 1);  // the buffer of the next time level
   if (h->cfg.storage == IILBM_F64)
     k_interp<double><<<(threads + 255) / 256, 256, 0, s>>>((const double *)h->uf, h->geom, h->X,
-                                                          h->nm, h->U, h->ip.moves);
+                                                          h->nm, h->U, h->ip.moves, h->tagb[nb],
+                                                          h->tile_count[nb]);
   else
     k_interp<float><<<(threads + 255) / 256, 256, 0, s>>>((const float *)h->uf, h->geom, h->X,
-                                                         h->nm, h->U, h->ip.moves);
+                                                         h->nm, h->U, h->ip.moves, h->tagb[nb],
+                                                         h->tile_count[nb]);
   return last_error();
 }
 

@@ -94,8 +94,11 @@ int iilbm_destroy(iilbm_t h);
  * (PRESCRIBED) or the desired velocity U^D (DIRECT), else ignored (may be NULL).
  * The markers are copied; the caller keeps ownership.  Every segment must be
  * shorter than 16 lattice units and every marker at least 3 nodes from a
- * non-periodic edge.  n = 0 removes the interface.  Sections 2.2.2 (Eqs. 17-20)
- * and 3 (Eqs. 31-32, 46-47).  Errors: INVALID_ARG, INTERFACE, OOM, CUDA. */
+ * non-periodic edge.  DIRECT needs a fixed body (moves = 0), eta > 0, and a body
+ * whose bounding box plus 4 nodes fits the forcing kernel's shared memory (about
+ * 100 x 100 nodes in FP32, 70 x 70 in FP64).  n = 0 removes the interface.
+ * Sections 2.2.2 (Eqs. 17-20) and 3 (Eqs. 31-32, 46-47).
+ * Errors: INVALID_ARG, INTERFACE, OOM, CUDA. */
 int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n,
                         const iilbm_interface_params *p, const double *aux);
 
@@ -126,8 +129,18 @@ int iilbm_get_macros(iilbm_t h, double *drho, double *ux, double *uy);
  * (Eq. 20).  Synchronises. */
 int iilbm_get_markers(iilbm_t h, double *X, double *G, double *U, double *Fn);
 
-/* Direct forcing: passes of the most recent step and its final residual. */
+/* Direct forcing: force updates of the most recent body-force computation and its
+ * final residual max_k |U^D - U_k| (Eq. 18 repeated).  Synchronises. */
 int iilbm_get_mdf_stats(iilbm_t h, int32_t *iters, double *residual);
+
+/* Direct forcing: the warm start G^(0) [n][2] of the force iteration (host or device;
+ * NULL = zero, the plain iteration).  Kept until replaced. */
+int iilbm_set_warm_start(iilbm_t h, const double *G0);
+
+/* Force of the fluid on the body, F = -sum_k G_k dX (Eq. 25 without the internal
+ * inertia term; the body is fixed), from the most recent Lagrangian force.  Drag and
+ * lift coefficients follow as 2 F / (rho U^2 D) (Eqs. 52-53).  Synchronises. */
+int iilbm_get_body_force(iilbm_t h, double *F);
 
 /* Number of cut-link crossings of the current state's interface (Eq. 47). */
 int iilbm_get_cut_link_count(iilbm_t h, int32_t *count);

@@ -51,7 +51,7 @@ int read_status(iilbm_lattice *h) {
 }
 
 void free_interface(iilbm_lattice *h) {
-  double **bufs[] = {&h->X, &h->aux, &h->G, &h->Fn, &h->P, &h->U, &h->nrm};
+  double **bufs[] = {&h->X, &h->aux, &h->G, &h->Fn, &h->P, &h->U, &h->nrm, &h->G0, &h->Gdf};
   for (double **b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
@@ -60,10 +60,13 @@ void free_interface(iilbm_lattice *h) {
 }
 
 // Bring the jump / force buffer of the current state's parity to the current
-// interface (idempotent per state).
+// interface (idempotent per state).  Direct forcing first finds the body force from
+// the current state.
 int prepare(iilbm_lattice *h) {
   if (h->prepared) return IILBM_OK;
-  int rc = launch_interface_phase(h, (int)(h->step & 1), h->stream);
+  int rc;
+  if (h->nm > 0 && h->ip.model == IILBM_DIRECT && (rc = launch_direct_forcing(h))) return rc;
+  rc = launch_interface_phase(h, (int)(h->step & 1), h->stream);
   if (rc) return rc;
   h->prepared = true;
   return IILBM_OK;
@@ -120,7 +123,9 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
   if (c.nx < 4 || c.ny < 4 || c.nx > 32768 || c.ny > 32768) return IILBM_ERR_INVALID_ARG;
   if (c.collision != IILBM_SRT && c.collision != IILBM_MRT) return IILBM_ERR_INVALID_ARG;
   if (!storage_bytes(c.storage)) return IILBM_ERR_INVALID_ARG;
-  if (c.bc != IILBM_BC_PERIODIC && c.bc != IILBM_BC_WALLS_Y) return IILBM_ERR_INVALID_ARG;
+  if (c.bc != IILBM_BC_PERIODIC && c.bc != IILBM_BC_WALLS_Y && c.bc != IILBM_BC_CHANNEL)
+    return IILBM_ERR_INVALID_ARG;
+  if (c.bc == IILBM_BC_CHANNEL && !(std::abs(c.u_max) < 0.5)) return IILBM_ERR_INVALID_ARG;
   if (!(c.tau > 0.5) || !(c.rho0 > 0) || std::abs(c.storage_scale_log2) > 30)
     return IILBM_ERR_INVALID_ARG;
   if (c.collision == IILBM_MRT)
@@ -143,7 +148,8 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
   Geom &g = h->geom;
   g.nx = c.nx;
   g.ny = c.ny;
-  g.pitch = (c.nx + 31) / 32 * 32;
+  // a channel keeps two ghost columns in the row padding
+  g.pitch = (c.nx + (c.bc == IILBM_BC_CHANNEL ? 2 : 0) + 31) / 32 * 32;
   g.plane = (long long)g.pitch * c.ny;
   g.ntx = (c.nx + TILE_X - 1) / TILE_X;
   g.bc = c.bc;
@@ -174,6 +180,8 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
             cudaMalloc(&h->A, 9 * (size_t)g.plane * h->sbytes) == cudaSuccess &&
             cudaMalloc(&h->uf, 2 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
             cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->d_mdf_iters, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->d_mdf_res, sizeof(double)) == cudaSuccess &&
             cudaMalloc(&h->d_tiles_total, sizeof(unsigned long long)) == cudaSuccess;
   for (int b = 0; b < 2 && ok; b++)
     ok = cudaMalloc(&h->Jb[b], 8 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
@@ -190,6 +198,8 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
   int rc = IILBM_OK;
   if (cudaMemsetAsync(h->A, 0, 9 * (size_t)g.plane * h->sbytes, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->d_mdf_iters, 0, sizeof(int), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->d_mdf_res, 0, sizeof(double), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_tiles_total, 0, sizeof(unsigned long long), h->stream) != cudaSuccess)
     rc = IILBM_ERR_CUDA;
   if (!rc) rc = clear_fields(h);
@@ -211,7 +221,7 @@ int iilbm_destroy(iilbm_t h) {
   void *bufs[] = {h->A, h->uf, h->Jb[0], h->Jb[1], h->gb[0], h->gb[1], h->flagsb[0], h->flagsb[1],
                   h->tile_list[0], h->tile_list[1], h->tile_count[0], h->tile_count[1],
                   h->tagb[0], h->tagb[1],
-                  h->d_status, h->d_tiles_total};
+                  h->d_status, h->d_mdf_iters, h->d_mdf_res, h->d_tiles_total};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -230,7 +240,8 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
   if (n > 0 && n < 3) return IILBM_ERR_INVALID_ARG;
   if (n > 0) {
     if (p->model < IILBM_SPRING || p->model > IILBM_DIRECT) return IILBM_ERR_INVALID_ARG;
-    if (p->model == IILBM_DIRECT) return IILBM_ERR_INVALID_ARG;  // not built yet
+    if (p->model == IILBM_DIRECT && (p->moves || !(p->eta > 0) || p->mdf_iters < 0))
+      return IILBM_ERR_INVALID_ARG;  // direct forcing: a fixed body, positive gain
     if (!(p->dX > 0) || !std::isfinite(p->stiffness)) return IILBM_ERR_INVALID_ARG;
     if (p->model == IILBM_SPRING_REST && !(p->rest_length > 0)) return IILBM_ERR_INVALID_ARG;
     if ((p->model == IILBM_PRESCRIBED || p->model == IILBM_DIRECT) && !aux)
@@ -244,7 +255,8 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
   if (n == 0) return IILBM_OK;
   const size_t b2 = 2 * (size_t)n * sizeof(double);
   bool ok = cudaMalloc(&h->X, b2) == cudaSuccess && cudaMalloc(&h->aux, b2) == cudaSuccess &&
-            cudaMalloc(&h->G, b2) == cudaSuccess &&
+            cudaMalloc(&h->G, b2) == cudaSuccess && cudaMalloc(&h->G0, b2) == cudaSuccess &&
+            cudaMalloc(&h->Gdf, b2) == cudaSuccess &&
             cudaMalloc(&h->Fn, (size_t)n * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&h->P, b2) == cudaSuccess && cudaMalloc(&h->U, b2) == cudaSuccess &&
             cudaMalloc(&h->nrm, b2) == cudaSuccess;
@@ -263,6 +275,8 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
   }
   CK(cudaMemsetAsync(h->U, 0, b2, h->stream));
   CK(cudaMemsetAsync(h->G, 0, b2, h->stream));
+  CK(cudaMemsetAsync(h->G0, 0, b2, h->stream));
+  CK(cudaMemsetAsync(h->Gdf, 0, b2, h->stream));
   CK(cudaMemsetAsync(h->Fn, 0, (size_t)n * sizeof(double), h->stream));
   CK(cudaStreamSynchronize(h->stream));
   // host-side validation of the polygon (the kernels re-check every step)
@@ -270,6 +284,7 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
   if (!hx) return IILBM_ERR_OOM;
   CK(cudaMemcpy(hx, h->X, b2, cudaMemcpyDeviceToHost));
   bool bad = false;
+  double bx0 = 1e300, bx1 = -1e300, by0 = 1e300, by1 = -1e300;
   for (int k = 0; k < n && !bad; k++) {
     const int kp = (k + 1) % n;
     const double x = hx[2 * k], y = hx[2 * k + 1];
@@ -278,8 +293,19 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
           std::abs(y) > MAX_COORD || !(dx * dx + dy * dy < MAX_SEGMENT * MAX_SEGMENT) ||
           (dx == 0 && dy == 0);
     if (h->cfg.bc != IILBM_BC_PERIODIC) bad = bad || y < 3.0 || y > h->cfg.ny - 4.0;
+    if (h->cfg.bc == IILBM_BC_CHANNEL) bad = bad || x < 3.0 || x > h->cfg.nx - 4.0;
+    bx0 = std::min(bx0, x); bx1 = std::max(bx1, x);
+    by0 = std::min(by0, y); by1 = std::max(by1, y);
   }
   std::free(hx);
+  if (!bad && p->model == IILBM_DIRECT) {
+    // the window holds every stencil node [floor(X) - 1, floor(X) + 2] of the fixed body
+    h->df_win[0] = (int)std::floor(bx0) - 1;
+    h->df_win[1] = (int)std::floor(by0) - 1;
+    h->df_win[2] = (int)std::floor(bx1) + 2 - h->df_win[0] + 1;
+    h->df_win[3] = (int)std::floor(by1) + 2 - h->df_win[1] + 1;
+    bad = direct_forcing_smem(h, h->df_win[2], h->df_win[3], n) > 227 * 1024;
+  }
   if (bad) {
     free_interface(h);
     return IILBM_ERR_INTERFACE;
@@ -366,10 +392,17 @@ int drain_all(iilbm_lattice *h) {
 }
 
 // Kernels launched by one step: lean stream-collide; with an interface also the
-// forced stream-collide, the interpolation and the fused interface kernel.
-long long kernels_per_step(const iilbm_lattice *h) { return 1 + (h->nm > 0 ? 3 : 0); }
+// forced stream-collide, the interpolation and the fused interface kernel (and the
+// force iteration for direct forcing); a channel adds its boundary kernel.
+long long kernels_per_step(const iilbm_lattice *h) {
+  return 1 + (h->nm > 0 ? 3 + (h->ip.model == IILBM_DIRECT ? 1 : 0) : 0) +
+         (h->cfg.bc == IILBM_BC_CHANNEL ? 1 : 0);
+}
 
-bool pipelined(const iilbm_lattice *h) { return h->overlap && h->nm > 0; }
+// Direct forcing needs the finished state of the step before, so it is not overlapped.
+bool pipelined(const iilbm_lattice *h) {
+  return h->overlap && h->nm > 0 && h->ip.model != IILBM_DIRECT;
+}
 
 // One time step of the current state n (its interface already prepared in buffer
 // n & 1).  Main stream: the lean stream-collide (every tile without a jump or force).
@@ -401,6 +434,7 @@ int one_step(iilbm_lattice *h, int ev_slot) {
     CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   }
   h->step++;
+  if ((rc = launch_channel_bc(h))) return rc;  // inflow / outflow of the new state
   h->prepared = pipe || h->nm == 0;
   return IILBM_OK;
 }
@@ -560,9 +594,46 @@ int iilbm_get_markers(iilbm_t h, double *X, double *G, double *U, double *Fn) {
 
 int iilbm_get_mdf_stats(iilbm_t h, int32_t *iters, double *residual) {
   if (!h) return IILBM_ERR_INVALID_ARG;
-  if (iters) *iters = h->mdf_iters_last;
-  if (residual) *residual = h->mdf_res_last;
+  int it = 0;
+  double res = 0;
+  CK(cudaMemcpyAsync(&it, h->d_mdf_iters, sizeof it, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&res, h->d_mdf_res, sizeof res, cudaMemcpyDeviceToHost, h->stream));
+  int rc = read_status(h);
+  if (iters) *iters = it;
+  if (residual) *residual = res;
+  return rc;
+}
+
+int iilbm_set_warm_start(iilbm_t h, const double *G0) {
+  if (!h || h->nm == 0) return IILBM_ERR_INVALID_ARG;
+  const size_t b2 = 2 * (size_t)h->nm * sizeof(double);
+  if (G0) CK(cudaMemcpyAsync(h->G0, G0, b2, cudaMemcpyDefault, h->stream));
+  else CK(cudaMemsetAsync(h->G0, 0, b2, h->stream));
+  h->prepared = false;  // the next step recomputes the body force
+  CK(cudaStreamSynchronize(h->stream));
   return IILBM_OK;
+}
+
+int iilbm_get_body_force(iilbm_t h, double *F) {
+  if (!h || !F) return IILBM_ERR_INVALID_ARG;
+  F[0] = F[1] = 0.0;
+  if (h->nm == 0) return read_status(h);
+  const size_t b2 = 2 * (size_t)h->nm * sizeof(double);
+  double *hg = (double *)std::malloc(b2);
+  if (!hg) return IILBM_ERR_OOM;
+  int rc = IILBM_OK;
+  if (cudaMemcpyAsync(hg, h->G, b2, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    rc = IILBM_ERR_CUDA;
+  }
+  if (!rc) rc = read_status(h);
+  if (!rc)
+    for (int k = 0; k < h->nm; k++) {
+      F[0] -= hg[2 * k] * h->ip.dX;
+      F[1] -= hg[2 * k + 1] * h->ip.dX;
+    }
+  std::free(hg);
+  return rc;
 }
 
 int iilbm_get_cut_link_count(iilbm_t h, int32_t *count) {

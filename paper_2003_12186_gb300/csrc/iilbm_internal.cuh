@@ -91,6 +91,14 @@ __host__ __device__ inline int wrap(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// Storage column of lattice column x in [-1, nx]: periodic x wraps; a channel keeps
+// the populations that stream in through x = -1 / x = nx in two ghost columns taken
+// from the row padding (pitch >= nx + 2): x = nx is column nx, x = -1 column pitch - 1.
+__host__ __device__ inline int xcol(const Geom &g, int x) {
+  if (g.bc != IILBM_BC_CHANNEL) return wrap(x, g.nx);
+  return x < 0 ? g.pitch - 1 : x;
+}
+
 // Location (plane index, cell index) of the population f_i(x, y) of the current
 // state in the AA layout.  Even state: slot i at the node itself.  Odd state: slot
 // opp(i) at the upstream node (x - e_i), wrapped on periodic axes; a population
@@ -103,7 +111,7 @@ __device__ inline long long aa_loc(const Geom &g, bool odd, int i, int x, int y)
   } else if (sy < 0 || sy >= g.ny) {
     return (long long)i * g.plane + (long long)y * g.pitch + x;
   }
-  sx = wrap(sx, g.nx);
+  sx = xcol(g, sx);
   return (long long)opp(i) * g.plane + (long long)sy * g.pitch + sx;
 }
 
@@ -153,8 +161,10 @@ struct iilbm_lattice {
   int nm;
   iilbm_interface_params ip;
   double *X, *aux, *G, *Fn, *P, *U, *nrm;
-  int mdf_iters_last;
-  double mdf_res_last;
+  double *G0, *Gdf;   // direct forcing: warm start and converged force
+  int *d_mdf_iters;
+  double *d_mdf_res;
+  int df_win[4];      // direct forcing window: x0, y0, width, height
   double *d_res;      // direct forcing residual scratch
   // diagnostics
   bool timing;
@@ -174,4 +184,7 @@ int launch_set_populations(iilbm_lattice *h, const double *df, bool equilibrium,
                            const double *rho, const double *ux, const double *uy);
 int launch_get_populations(iilbm_lattice *h, double *df);
 int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s);
+int launch_channel_bc(iilbm_lattice *h);
+int launch_direct_forcing(iilbm_lattice *h);
+size_t direct_forcing_smem(const iilbm_lattice *h, int ww, int wh, int n);
 }  // namespace iilbm

@@ -106,7 +106,7 @@ __device__ inline MarkerForce<T> marker_force(const double *__restrict__ X,
     const T Tb = T(ip.stiffness) * (lb / T(ip.rest_length) - T(1));
     gx = (Ta * (ax / la) - Tb * (bx / lb)) / T(ip.dX);
     gy = (Ta * (ay / la) - Tb * (by / lb)) / T(ip.dX);
-  } else {  // prescribed
+  } else {  // prescribed, or the converged direct-forcing force
     gx = T(aux[2 * j]);
     gy = T(aux[2 * j + 1]);
   }
@@ -306,18 +306,18 @@ __global__ void __launch_bounds__(128)
 int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s) {
   if (h->nm == 0) return IILBM_OK;
   const int n = h->nm;
-  if (h->ip.model == IILBM_DIRECT) return IILBM_ERR_INVALID_ARG;
+  const double *aux = h->ip.model == IILBM_DIRECT ? h->Gdf : h->aux;
   const TileBuf tb{h->flagsb[buf], h->tagb[buf], h->tile_list[buf], h->tile_count[buf],
                    h->d_tiles_total};
   const bool dbl = h->cfg.storage == IILBM_F64;
   const int threads = 32 * n;
   if (dbl)
     k_interface<double><<<(threads + 127) / 128, 128, 0, s>>>(
-        h->X, h->aux, n, h->ip, h->cfg.jump, h->geom, (double *)h->Jb[buf],
+        h->X, aux, n, h->ip, h->cfg.jump, h->geom, (double *)h->Jb[buf],
         (double *)h->gb[buf], tb, h->G, h->Fn, h->nrm, h->d_status);
   else
     k_interface<float><<<(threads + 127) / 128, 128, 0, s>>>(
-        h->X, h->aux, n, h->ip, h->cfg.jump, h->geom, (float *)h->Jb[buf], (float *)h->gb[buf],
+        h->X, aux, n, h->ip, h->cfg.jump, h->geom, (float *)h->Jb[buf], (float *)h->gb[buf],
         tb, h->G, h->Fn, h->nrm, h->d_status);
   return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
 }

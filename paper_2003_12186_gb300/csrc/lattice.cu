@@ -213,7 +213,8 @@ __device__ inline void ldT(const T *p, T *o) {
 
 
 // One node per thread on a 32 x TILE_Y sub-block whose first node is (xb, yb).  BC is
-// IILBM_BC_PERIODIC or IILBM_BC_WALLS_Y (periodic x, halfway bounce-back in y).
+// IILBM_BC_PERIODIC, IILBM_BC_WALLS_Y (periodic x, halfway bounce-back in y) or
+// IILBM_BC_CHANNEL (walls in y, ghost columns in x filled by the channel boundary).
 template <typename S, int COLL, bool ODD, int BC, bool FORCED>
 __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
                                                 typename Store<S>::T *__restrict__ Jf,
@@ -227,8 +228,8 @@ __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
   if (x >= geo.nx || y >= geo.ny) return;
   const long long P = geo.plane;
   const long long here = (long long)y * geo.pitch + x;
-  const int xm = x == 0 ? geo.nx - 1 : x - 1;
-  const int xp = x == geo.nx - 1 ? 0 : x + 1;
+  const int xm = x == 0 ? (BC == IILBM_BC_CHANNEL ? geo.pitch - 1 : geo.nx - 1) : x - 1;
+  const int xp = x == geo.nx - 1 ? (BC == IILBM_BC_CHANNEL ? geo.nx : 0) : x + 1;
   int ym = y - 1, yp = y + 1;
   bool wall_m = false, wall_p = false;
   if (BC == IILBM_BC_PERIODIC) {
@@ -318,8 +319,9 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
   const long long row[3] = {(long long)ym * geo.pitch, (long long)y * geo.pitch,
                             (long long)yp * geo.pitch};
   const long long here = row[1] + x0;
-  const int xl = x0 == 0 ? geo.nx - 1 : x0 - 1;      // left neighbour of the chunk
-  const int xr = x0 + V >= geo.nx ? 0 : x0 + V;      // right neighbour of the chunk
+  // left / right neighbour column of the chunk (wrapped, or a channel's ghost column)
+  const int xl = x0 == 0 ? (BC == IILBM_BC_CHANNEL ? geo.pitch - 1 : geo.nx - 1) : x0 - 1;
+  const int xr = x0 + V >= geo.nx ? (BC == IILBM_BC_CHANNEL ? geo.nx : 0) : x0 + V;
 
   T f[9][V];
 #pragma unroll
@@ -640,6 +642,41 @@ __global__ void k_get_populations(const S *A, const Geom geo,
     df[i * N + o] = double(Store<S>::ld(A[aa_loc(geo, odd, i, x, y)]) * p.inv_scale);
 }
 
+// ------------------------------------------------------------ channel ends
+// Inflow / outflow of a channel on the streamed state (one thread per row), after every
+// stream-collide: inflow column x = 0 by non-equilibrium extrapolation from column 1,
+//   f_i(0,y) = f_eq_i(rho(1,y), u_in(y)) + [f_i(1,y) - f_eq_i(rho(1,y), u(1,y))],
+// u_in(y) = 4 u_max (y + 1/2)(ny - y - 1/2) / ny^2 (parabolic, v = 0); outflow column
+// nx - 1: the populations with e_x < 0 copied from column nx - 2 (zero gradient).
+template <typename S>
+__global__ void k_channel_bc(S *A, const Geom geo, const CollP<typename Store<S>::T> p,
+                             bool odd, double u_max) {
+  using T = typename Store<S>::T;
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= geo.ny) return;
+  T f[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) f[i] = Store<S>::ld(A[aa_loc(geo, odd, i, 1, y)]) * p.inv_scale;
+  const T d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const T rho = p.rho0 + d;
+  const T ux = ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7])) / rho;
+  const T uy = ((f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8])) / rho;
+  const double yy = y + 0.5;
+  const T uin = T(4.0 * u_max * yy * (geo.ny - yy) / ((double)geo.ny * geo.ny));
+  const T u2 = ux * ux + uy * uy, uin2 = uin * uin;
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    const T eu = T(cx(i)) * ux + T(cy(i)) * uy, ei = T(cx(i)) * uin;
+    const T feq_in = wt<T>(i) * (d + rho * (T(3) * ei + T(4.5) * ei * ei - T(1.5) * uin2));
+    const T feq_1 = wt<T>(i) * (d + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * u2));
+    A[aa_loc(geo, odd, i, 0, y)] = Store<S>::st((feq_in + (f[i] - feq_1)) * p.scale);
+  }
+  constexpr int out[3] = {3, 6, 7};
+#pragma unroll
+  for (int q = 0; q < 3; q++)
+    A[aa_loc(geo, odd, out[q], geo.nx - 1, y)] = A[aa_loc(geo, odd, out[q], geo.nx - 2, y)];
+}
+
 // ------------------------------------------------------------------ dispatch
 template <typename F>
 static int dispatch_storage(int storage, F &&f) {
@@ -690,8 +727,10 @@ template <typename S, int COLL, bool ODD>
 static void sc_launch(iilbm_lattice *h, cudaStream_t forced_stream) {
   if (h->geom.bc == IILBM_BC_PERIODIC)
     sc_launch_bc<S, COLL, ODD, IILBM_BC_PERIODIC>(h, forced_stream);
-  else
+  else if (h->geom.bc == IILBM_BC_WALLS_Y)
     sc_launch_bc<S, COLL, ODD, IILBM_BC_WALLS_Y>(h, forced_stream);
+  else
+    sc_launch_bc<S, COLL, ODD, IILBM_BC_CHANNEL>(h, forced_stream);
 }
 
 // Launch the lean stream-collide on the handle's stream and the forced one (flagged
@@ -724,6 +763,18 @@ int launch_interp(iilbm_lattice *h, cudaStream_t s) {
                                                          h->nm, h->U, h->ip.moves, h->tagb[nb],
                                                          h->tile_count[nb]);
   return last_error();
+}
+
+int launch_channel_bc(iilbm_lattice *h) {
+  if (h->geom.bc != IILBM_BC_CHANNEL) return IILBM_OK;
+  const bool odd = h->step & 1;  // the state just produced
+  return dispatch_storage(h->cfg.storage, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    using T = typename Store<S>::T;
+    k_channel_bc<S><<<(h->geom.ny + 127) / 128, 128, 0, h->stream>>>(
+        (S *)h->A, h->geom, make_collp<T>(h->cfg), odd, h->cfg.u_max);
+    return last_error();
+  });
 }
 
 int launch_macros(iilbm_lattice *h, double *drho, double *ux, double *uy) {

@@ -63,6 +63,8 @@ SIGNATURES = {
     "iilbm_get_macros": [_H, _P, _P, _P],
     "iilbm_get_markers": [_H, _P, _P, _P, _P],
     "iilbm_get_mdf_stats": [_H, C.POINTER(C.c_int32), C.POINTER(C.c_double)],
+    "iilbm_set_warm_start": [_H, _P],
+    "iilbm_get_body_force": [_H, C.POINTER(C.c_double)],
     "iilbm_get_cut_link_count": [_H, C.POINTER(C.c_int32)],
     "iilbm_set_timing": [_H, C.c_int32],
     "iilbm_get_timing": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int32),
@@ -251,6 +253,16 @@ class Lattice:
         _check("iilbm_get_mdf_stats",
                self._L.iilbm_get_mdf_stats(self._h, C.byref(it), C.byref(res)))
         return it.value, res.value
+
+    def iilbm_set_warm_start(self, G0=None):
+        G = None if G0 is None else (G0 if hasattr(G0, "data_ptr") else
+                                     _host(G0, (self.n_markers, 2)))
+        _check("iilbm_set_warm_start", self._L.iilbm_set_warm_start(self._h, _ptr(G)))
+
+    def iilbm_get_body_force(self):
+        F = (C.c_double * 2)()
+        _check("iilbm_get_body_force", self._L.iilbm_get_body_force(self._h, F))
+        return F[0], F[1]
 
     def iilbm_get_cut_link_count(self):
         c = C.c_int32()

@@ -1,0 +1,129 @@
+"""Channel boundaries (parabolic inflow by non-equilibrium extrapolation, zero-gradient
+outflow, halfway bounce-back walls) and direct forcing of a fixed cylinder with repeated
+correction (Eq. 18), CUDA path against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2003_12186_gb300 import iilbm
+from paper_2003_12186_gb300 import workloads as W
+
+from _pair import rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    iilbm.load()
+
+
+def channel_pair(orc, nx, ny, storage="f64", tau=0.8, u_max=0.05, jump=1):
+    s = W.mrt_rates(tau)
+    g = iilbm.Lattice(nx, ny, collision=iilbm.MRT, storage=storage, tau=tau, s=s,
+                      bc=iilbm.BC_CHANNEL, u_max=u_max, jump=jump)
+    o = orc.Oracle(nx, ny, collision=orc.MRT, tau=tau, s=s, bc=orc.BC_CHANNEL, u_max=u_max,
+                   jump=jump)
+    return g, o
+
+
+@pytest.mark.parametrize("vec", [1, 0])
+@pytest.mark.parametrize("shape", [(96, 32), (70, 21)])
+def test_empty_channel_fp64(orc, vec, shape):
+    nx, ny = shape
+    g, o = channel_pair(orc, nx, ny)
+    g.set_option(iilbm.OPT_VECTOR_KERNEL, vec)
+    df = W.random_df(nx, ny, 1e-4, 3)
+    g.set_populations(df)
+    o.set_df(df)
+    for n in (1, 1, 7, 40):
+        g.step(n)
+        o.step(n)
+        assert np.abs(g.get_populations() - o.get_df()).max() < 1e-15
+    _, ug, vg = g.get_macros()
+    _, uo, vo = o.current_macros()
+    assert max(rel_err(ug, uo, 0.05), rel_err(vg, vo, 0.05)) < 1e-12
+
+
+def cylinder_case(orc, storage, iters, tol, nx=160, ny=64, D=16.0, n=50, steps=60):
+    g, o = channel_pair(orc, nx, ny, storage=storage, tau=0.7)
+    X = W.circle_markers(48.0, 32.5, D / 2, n)
+    dX = W.polygon_perimeter(X) / n
+    UD = np.zeros((n, 2))
+    g.set_interface(X, model=iilbm.DIRECT, moves=False, dX=dX, eta=2.0, mdf_iters=iters,
+                    mdf_tol=tol, aux=UD)
+    o.set_interface(X, model=orc.DIRECT, moves=False, dX=dX, eta=2.0, mdf_iters=iters,
+                    mdf_tol=tol, UD=UD)
+    g.step(steps)
+    o.step(steps)
+    return g, o
+
+
+def test_cylinder_direct_forcing_fp64(orc):
+    """Five force updates per step (the channel cylinder setting), 60 steps: populations,
+    Lagrangian force and interpolated velocity match the oracle."""
+    g, o = cylinder_case(orc, "f64", 5, 0.0)
+    assert np.abs(g.get_populations() - o.get_df()).max() < 1e-14
+    mg = g.get_markers()  # both: the force of the last step's state
+    mo = o.markers()
+    assert np.abs(mg["G"] - mo["G"]).max() < 1e-13
+    it_g, res_g = g.iilbm_get_mdf_stats()
+    it_o, res_o = o.mdf_stats()
+    assert it_g == it_o == 5 and abs(res_g - res_o) < 1e-14
+    F = g.iilbm_get_body_force()
+    Fo = -mo["G"].sum(0) * W.polygon_perimeter(mo["X"]) / 50
+    assert abs(F[0] - Fo[0]) < 1e-12 and F[0] > 0  # drag along the stream
+
+
+def test_cylinder_iteration_to_tolerance_fp64(orc):
+    """Stopping on the residual: same pass count and residual as the oracle."""
+    g, o = cylinder_case(orc, "f64", 200, 2e-4, steps=20)
+    it_g, res_g = g.iilbm_get_mdf_stats()
+    it_o, res_o = o.mdf_stats()
+    assert it_g == it_o and res_g < 2e-4 and abs(res_g - res_o) < 1e-14
+    assert np.abs(g.get_populations() - o.get_df()).max() < 1e-14
+
+
+def test_cylinder_direct_forcing_fp32(orc):
+    g, o = cylinder_case(orc, "f32", 5, 0.0, steps=100)
+    _, ug, vg = g.get_macros()
+    _, uo, vo = o.current_macros()
+    assert max(rel_err(ug, uo, 0.05), rel_err(vg, vo, 0.05)) < 1e-5
+
+
+def test_warm_start_changes_iterations_not_answer(orc):
+    """A warm start near the converged force needs fewer passes to the same tolerance."""
+    g, o = cylinder_case(orc, "f64", 300, 1e-5, steps=30)
+    it0, _ = g.iilbm_get_mdf_stats()
+    G = g.get_markers()["G"]
+    g.iilbm_set_warm_start(G)
+    g.step(1)
+    it1, res1 = g.iilbm_get_mdf_stats()
+    assert res1 < 1e-5 and it1 < it0
+
+
+def test_channel_cylinder_full_size_fp32(orc):
+    """The 1024 x 256 channel with the D = 40 cylinder (126 markers), Re = 100 (tau from
+    Re with u_max = 0.05), five force updates per step: 10 steps against the oracle."""
+    w = W.cylinder_channel(100.0)
+    s = W.mrt_rates(w["tau"])
+    g = iilbm.Lattice(w["nx"], w["ny"], collision=iilbm.MRT, storage="f32", tau=w["tau"], s=s,
+                      bc=iilbm.BC_CHANNEL, u_max=w["u_max"])
+    o = orc.Oracle(w["nx"], w["ny"], collision=orc.MRT, tau=w["tau"], s=s, bc=orc.BC_CHANNEL,
+                   u_max=w["u_max"])
+    n = len(w["X"])
+    for lat in (g,):
+        lat.set_interface(w["X"], model=iilbm.DIRECT, moves=False, dX=w["dX"], eta=2.0,
+                          mdf_iters=5, aux=np.zeros((n, 2)))
+    o.set_interface(w["X"], model=orc.DIRECT, moves=False, dX=w["dX"], eta=2.0, mdf_iters=5,
+                    UD=np.zeros((n, 2)))
+    g.step(10)
+    o.step(10)
+    _, ug, vg = g.get_macros()
+    _, uo, vo = o.current_macros()
+    assert max(rel_err(ug, uo, 0.05), rel_err(vg, vo, 0.05)) < 1e-5
+    assert g.iilbm_get_cut_link_count() == o.cut_link_count() > 0

@@ -134,7 +134,8 @@ int iilbm_get_markers(iilbm_t h, double *X, double *G, double *U, double *Fn);
 int iilbm_get_mdf_stats(iilbm_t h, int32_t *iters, double *residual);
 
 /* Direct forcing: the warm start G^(0) [n][2] of the force iteration (host or device;
- * NULL = zero, the plain iteration).  Kept until replaced. */
+ * NULL = zero, the plain iteration).  Kept until replaced; first used by the next force
+ * iteration (that of the current state unless a read-out has already run it). */
 int iilbm_set_warm_start(iilbm_t h, const double *G0);
 
 /* Force of the fluid on the body, F = -sum_k G_k dX (Eq. 25 without the internal
@@ -178,6 +179,39 @@ int iilbm_set_option(iilbm_t h, int32_t option, int32_t value);
  * (host or device, any may be NULL).  Synchronises. */
 #define IILBM_NOALLOC_MAX_CELLS (1 << 18)
 int iilbm_get_macros_noalloc(iilbm_t h, double *drho, double *ux, double *uy);
+
+/* ---------------------------------------------------------------- batches
+ * A batch advances many independent lattices together: every phase of a time step is
+ * one launch for all of them (a flattened list of tiles for the stream-collide, of
+ * markers for the interface phase and the interpolation, one CTA per fixed body for
+ * direct forcing), replayed from CUDA graphs.  It is built from existing lattice
+ * handles that share storage (F32, F16 or BF16), collision model and boundary kind,
+ * have nx a multiple of 4 and the same step parity; sizes, rates, interfaces and
+ * force models may differ.  The lattices stay owned by the caller.  While batched,
+ * iilbm_step, iilbm_set_interface, iilbm_init_equilibrium, iilbm_set_populations,
+ * iilbm_set_option and iilbm_destroy on them return INVALID_ARG; read-outs run on the
+ * batch's stream after its work.  Destroy the batch before its lattices.
+ * Errors of create: INVALID_ARG (mixed kinds, F64, a repeated or batched lattice), OOM,
+ * CUDA. */
+typedef struct iilbm_batch *iilbm_batch_t;
+int iilbm_create_batch(iilbm_batch_t *out, const iilbm_t *lattices, int32_t count, void *stream);
+int iilbm_destroy_batch(iilbm_batch_t b);
+/* Advance every lattice of the batch by n time steps (asynchronous). */
+int iilbm_batch_step(iilbm_batch_t b, int32_t n);
+/* Stream-collide variant: 0 vectorised, one block per tile; 1 / 2 vectorised on a
+ * persistent grid of 2 / 4 blocks per SM; 3 one node per thread, one block per tile
+ * (four sub-blocks); 4 one node per thread on a persistent grid of 2 blocks per SM. */
+int iilbm_batch_set_variant(iilbm_batch_t b, int32_t variant);
+/* Autotuner: time every variant for `steps` (rounded up to whole graph replays) real
+ * steps of the batch and keep the fastest; the lattices advance by those steps.
+ * Returns the variant chosen and its time per step (us). */
+int iilbm_batch_autotune(iilbm_batch_t b, int32_t steps, int32_t *chosen, double *us_per_step);
+/* Lean stream-collide timing of eager batch steps (as iilbm_set_timing). */
+int iilbm_batch_set_timing(iilbm_batch_t b, int32_t enable);
+int iilbm_batch_get_timing(iilbm_batch_t b, double *stream_collide_ms, int32_t *launches,
+                           int64_t *kernel_launches);
+/* Wait for the batch's streams; returns any latched device status of its lattices. */
+int iilbm_batch_synchronize(iilbm_batch_t b);
 
 /* Wait for the handle's stream and return any latched device status. */
 int iilbm_synchronize(iilbm_t h);

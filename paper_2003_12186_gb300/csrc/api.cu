@@ -64,6 +64,7 @@ void free_interface(iilbm_lattice *h) {
 // the current state.
 int prepare(iilbm_lattice *h) {
   if (h->prepared) return IILBM_OK;
+  if (h->in_batch) return prepare_batch_of(h);
   int rc;
   if (h->nm > 0 && h->ip.model == IILBM_DIRECT && (rc = launch_direct_forcing(h))) return rc;
   rc = launch_interface_phase(h, (int)(h->step & 1), h->stream);
@@ -98,6 +99,11 @@ int clear_fields(iilbm_lattice *h) {
 }
 
 }  // namespace
+
+namespace iilbm {
+// Interface phase of a lattice's current state, for the batched executor.
+int prepare_lattice(iilbm_lattice *h) { return prepare(h); }
+}  // namespace iilbm
 
 extern "C" {
 
@@ -214,6 +220,7 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
 
 int iilbm_destroy(iilbm_t h) {
   if (!h) return IILBM_ERR_INVALID_ARG;
+  if (h->in_batch) return IILBM_ERR_INVALID_ARG;  // owned by a batch until it is destroyed
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->side) cudaStreamSynchronize(h->side);
   drop_graph(h);
@@ -237,6 +244,7 @@ int iilbm_destroy(iilbm_t h) {
 int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_interface_params *p,
                         const double *aux) {
   if (!h || n < 0 || (n > 0 && (!xy || !p))) return IILBM_ERR_INVALID_ARG;
+  if (h->in_batch) return IILBM_ERR_INVALID_ARG;  // owned by a batch until it is destroyed
   if (n > 0 && n < 3) return IILBM_ERR_INVALID_ARG;
   if (n > 0) {
     if (p->model < IILBM_SPRING || p->model > IILBM_DIRECT) return IILBM_ERR_INVALID_ARG;
@@ -315,6 +323,7 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
 
 int iilbm_init_equilibrium(iilbm_t h, const double *rho, const double *ux, const double *uy) {
   if (!h) return IILBM_ERR_INVALID_ARG;
+  if (h->in_batch) return IILBM_ERR_INVALID_ARG;  // owned by a batch until it is destroyed
   const size_t N = (size_t)h->cfg.nx * h->cfg.ny;
   const double *src[3] = {rho, ux, uy};
   double *dev[3] = {nullptr, nullptr, nullptr};
@@ -334,6 +343,7 @@ int iilbm_init_equilibrium(iilbm_t h, const double *rho, const double *ux, const
 
 int iilbm_set_populations(iilbm_t h, const double *df) {
   if (!h || !df) return IILBM_ERR_INVALID_ARG;
+  if (h->in_batch) return IILBM_ERR_INVALID_ARG;  // owned by a batch until it is destroyed
   const size_t bytes = 9 * (size_t)h->cfg.nx * h->cfg.ny * sizeof(double);
   double *d = nullptr;
   if (cudaMalloc(&d, bytes) != cudaSuccess) return IILBM_ERR_OOM;
@@ -471,7 +481,7 @@ int capture_graph(iilbm_lattice *h, int r) {
 }
 
 int iilbm_step(iilbm_t h, int32_t n) {
-  if (!h || n < 0) return IILBM_ERR_INVALID_ARG;
+  if (!h || n < 0 || h->in_batch) return IILBM_ERR_INVALID_ARG;
   int rc;
   while (n > 0) {
     if ((rc = prepare(h))) return rc;
@@ -518,6 +528,7 @@ int iilbm_step(iilbm_t h, int32_t n) {
 
 int iilbm_set_option(iilbm_t h, int32_t option, int32_t value) {
   if (!h) return IILBM_ERR_INVALID_ARG;
+  if (h->in_batch) return IILBM_ERR_INVALID_ARG;  // owned by a batch until it is destroyed
   CK(cudaStreamSynchronize(h->stream));
   switch (option) {
     case IILBM_OPT_CUDA_GRAPH: h->use_graph = value != 0; break;
@@ -609,7 +620,8 @@ int iilbm_set_warm_start(iilbm_t h, const double *G0) {
   const size_t b2 = 2 * (size_t)h->nm * sizeof(double);
   if (G0) CK(cudaMemcpyAsync(h->G0, G0, b2, cudaMemcpyDefault, h->stream));
   else CK(cudaMemsetAsync(h->G0, 0, b2, h->stream));
-  h->prepared = false;  // the next step recomputes the body force
+  // used by the next force iteration: that of the current state unless a read-out has
+  // already run it (re-running the interface phase would add the jump a second time)
   CK(cudaStreamSynchronize(h->stream));
   return IILBM_OK;
 }

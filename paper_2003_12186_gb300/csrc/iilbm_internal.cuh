@@ -154,6 +154,9 @@ struct iilbm_lattice {
   int ring_next;
   bool graph_timing;  // the instantiated graphs record timing events
   bool capturing;     // inside cudaStreamBeginCapture / EndCapture
+  bool in_batch;      // advanced by a batch (iilbm_step refused meanwhile)
+  struct iilbm_batch *batch;
+  cudaStream_t own_main, own_side;  // the lattice's streams while batched
   long long step;     // time level of the state; AA parity = step & 1
   bool prepared;      // jump / force of the current state already in J, g
   int *d_status;      // latched device status bits
@@ -187,4 +190,6 @@ int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s);
 int launch_channel_bc(iilbm_lattice *h);
 int launch_direct_forcing(iilbm_lattice *h);
 size_t direct_forcing_smem(const iilbm_lattice *h, int ww, int wh, int n);
+int prepare_lattice(iilbm_lattice *h);
+int prepare_batch_of(iilbm_lattice *h);
 }  // namespace iilbm

@@ -13,436 +13,11 @@
 // opp(i) of the upstream node x - e_i and writes f*_i into slot i of the downstream
 // node x + e_i.  Each node only touches slots no other node touches in that step,
 // so one array suffices and every step moves 2 x 9 values per node.
-#include "iilbm_internal.cuh"
+#include "lattice_dev.cuh"
 
 #include <cmath>
 
 namespace iilbm {
-
-template <typename T>
-struct CollP {
-  T omega;          // 1/tau (SRT)
-  T s1, s2, s4, s6, s7, s8;  // MRT rates of the non-conserved moments
-  T rho0;
-  T scale, inv_scale;        // storage scale 2^k and 2^-k
-  T bodyx, bodyy;
-};
-
-template <typename T>
-CollP<T> make_collp(const iilbm_config &c) {
-  CollP<T> p;
-  p.omega = T(1.0 / c.tau);
-  p.s1 = T(c.s[1]); p.s2 = T(c.s[2]); p.s4 = T(c.s[4]); p.s6 = T(c.s[6]);
-  p.s7 = T(c.s[7]); p.s8 = T(c.s[8]);
-  p.rho0 = T(c.rho0);
-  p.scale = T(std::ldexp(1.0, c.storage_scale_log2));
-  p.inv_scale = T(std::ldexp(1.0, -c.storage_scale_log2));
-  p.bodyx = T(c.body[0]);
-  p.bodyy = T(c.body[1]);
-  return p;
-}
-
-// ------------------------------------------------------------------ collision
-// Shifted populations in, post-collision shifted populations out.
-//   rho = rho0 + drho,  rho u = j + g/2  (Eqs. 11, 24)
-//   feq_i - w_i rho0 = w_i [drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u^2)]  (Eq. 23)
-//   Guo source  Gt_i = w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]  (Eqs. 21-22)
-template <typename T, int COLL>
-__device__ __forceinline__ T collide(T f[9], T gx, T gy, const CollP<T> &p, T &ux_out,
-                                     T &uy_out) {
-  const T drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-  const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-  const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-  const T rho = p.rho0 + drho;
-  const T ir = T(1) / rho;
-  const T jxh = jx + T(0.5) * gx, jyh = jy + T(0.5) * gy;  // rho u
-  const T ux = jxh * ir, uy = jyh * ir;
-  ux_out = ux;
-  uy_out = uy;
-  if (COLL == IILBM_SRT) {
-    const T u2 = ux * ux + uy * uy;
-    const T ug = ux * gx + uy * gy;
-    const T om = p.omega, fo = T(1) - T(0.5) * p.omega;
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-      const T eu = T(cx(i)) * ux + T(cy(i)) * uy;
-      const T eg = T(cx(i)) * gx + T(cy(i)) * gy;
-      const T feq = wt<T>(i) * (drho + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * u2));
-      const T gt = wt<T>(i) * (T(3) * (eg - ug) + T(9) * eu * eg);
-      f[i] = f[i] - om * (f[i] - feq) + fo * gt;
-    }
-  } else {
-    // Lallemand-Luo moments of df: e, eps, qx, qy, pxx, pxy (rho, jx, jy above).
-    const T sa = (f[1] + f[2]) + (f[3] + f[4]);
-    const T sd = (f[5] + f[6]) + (f[7] + f[8]);
-    const T m1 = T(-4) * f[0] - sa + T(2) * sd;
-    const T m2 = T(4) * f[0] - T(2) * sa + sd;
-    const T m4 = T(-2) * (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
-    const T m6 = T(-2) * (f[2] - f[4]) + ((f[5] + f[6]) - (f[7] + f[8]));
-    const T m7 = (f[1] + f[3]) - (f[2] + f[4]);
-    const T m8 = (f[5] + f[7]) - (f[6] + f[8]);
-    // equilibrium moments of the shifted equilibrium
-    const T ru2 = jxh * ux + jyh * uy;  // rho u^2
-    const T e1 = T(-2) * drho + T(3) * ru2;
-    const T e2 = drho - T(3) * ru2;
-    const T e4 = -jxh, e6 = -jyh;
-    const T e7 = jxh * ux - jyh * uy;
-    const T e8 = jxh * uy;
-    // moments of Guo's source
-    const T ug = ux * gx + uy * gy;
-    const T F1 = T(6) * ug, F2 = T(-6) * ug, F4 = -gx, F6 = -gy;
-    const T F7 = T(2) * (ux * gx - uy * gy), F8 = ux * gy + uy * gx;
-    const T d1 = -p.s1 * (m1 - e1) + (T(1) - T(0.5) * p.s1) * F1;
-    const T d2 = -p.s2 * (m2 - e2) + (T(1) - T(0.5) * p.s2) * F2;
-    const T d4 = -p.s4 * (m4 - e4) + (T(1) - T(0.5) * p.s4) * F4;
-    const T d6 = -p.s6 * (m6 - e6) + (T(1) - T(0.5) * p.s6) * F6;
-    const T d7 = -p.s7 * (m7 - e7) + (T(1) - T(0.5) * p.s7) * F7;
-    const T d8 = -p.s8 * (m8 - e8) + (T(1) - T(0.5) * p.s8) * F8;
-    // conserved moments: rho unchanged, j gains exactly g (any s3, s5)
-    const T a1 = d1 * T(1.0 / 36), a2 = d2 * T(1.0 / 36);
-    const T a3 = gx * T(1.0 / 6), a5 = gy * T(1.0 / 6);
-    const T a4 = d4 * T(1.0 / 12), a6 = d6 * T(1.0 / 12);
-    const T a7 = d7 * T(0.25), a8 = d8 * T(0.25);
-    const T b = -a1 - T(2) * a2;        // common to the axis velocities
-    const T c = T(2) * a1 + a2;         // common to the diagonals
-    f[0] += T(-4) * a1 + T(4) * a2;
-    f[1] += b + a3 - T(2) * a4 + a7;
-    f[2] += b + a5 - T(2) * a6 - a7;
-    f[3] += b - a3 + T(2) * a4 + a7;
-    f[4] += b - a5 + T(2) * a6 - a7;
-    f[5] += c + (a3 + a4) + (a5 + a6) + a8;
-    f[6] += c - (a3 + a4) + (a5 + a6) - a8;
-    f[7] += c - (a3 + a4) - (a5 + a6) + a8;
-    f[8] += c + (a3 + a4) - (a5 + a6) - a8;
-  }
-  return drho;
-}
-
-// -------------------------------------------------------------- stream-collide
-// The stream-collide is split by tile.  Tiles (TILE_X x TILE_Y nodes) that carry no
-// jump and no spread force -- all but O(interface length) of them -- go through a
-// lean kernel with no jump / force code at all, which keeps its register count and
-// so its memory parallelism high.  The flagged tiles are listed by the interface phase
-// and processed by a "forced" kernel that adds the jump of Eq. 47 and the spread
-// force of Eq. 46.  Under the AA pattern every population
-// slot is read and written by one and the same node, so the two kernels touch
-// disjoint slots and may run in either order or concurrently.
-
-// Each thread owns V consecutive nodes of one row (V = 4 for FP32 / FP16 / BF16
-// storage, 2 for FP64) and moves every population plane with one 16-byte (8-byte
-// for 16-bit storage) vector access per plane.  A warp covers 32 V consecutive nodes
-// of one row, a block of 8 warps 8 rows.  In the odd step the planes with e_x = +-1
-// are shifted by one node: the aligned vector is loaded (stored) and the one element
-// that crosses into the neighbouring lane travels by warp shuffle; lanes 0 and 31
-// (and the last active lane of a row) fetch / write that element with a scalar
-// access instead, wrapping around the periodic row.  Requires nx % V == 0.
-template <typename S> struct Vec;
-template <> struct Vec<float> {
-  static constexpr int V = 4;
-  __device__ static void ld(const float *p, float *o, float is) {
-    const float4 t = *reinterpret_cast<const float4 *>(p);
-    o[0] = t.x * is; o[1] = t.y * is; o[2] = t.z * is; o[3] = t.w * is;
-  }
-  __device__ static void st(float *p, const float *v, float sc) {
-    *reinterpret_cast<float4 *>(p) = make_float4(v[0] * sc, v[1] * sc, v[2] * sc, v[3] * sc);
-  }
-};
-template <> struct Vec<double> {
-  static constexpr int V = 2;
-  __device__ static void ld(const double *p, double *o, double is) {
-    const double2 t = *reinterpret_cast<const double2 *>(p);
-    o[0] = t.x * is; o[1] = t.y * is;
-  }
-  __device__ static void st(double *p, const double *v, double sc) {
-    *reinterpret_cast<double2 *>(p) = make_double2(v[0] * sc, v[1] * sc);
-  }
-};
-template <> struct Vec<__half> {
-  static constexpr int V = 4;
-  __device__ static void ld(const __half *p, float *o, float is) {
-    const uint2 t = *reinterpret_cast<const uint2 *>(p);
-    const __half2 a = *reinterpret_cast<const __half2 *>(&t.x);
-    const __half2 b = *reinterpret_cast<const __half2 *>(&t.y);
-    const float2 fa = __half22float2(a), fb = __half22float2(b);
-    o[0] = fa.x * is; o[1] = fa.y * is; o[2] = fb.x * is; o[3] = fb.y * is;
-  }
-  __device__ static void st(__half *p, const float *v, float sc) {
-    const __half2 a = __floats2half2_rn(v[0] * sc, v[1] * sc);
-    const __half2 b = __floats2half2_rn(v[2] * sc, v[3] * sc);
-    uint2 t;
-    t.x = *reinterpret_cast<const unsigned *>(&a);
-    t.y = *reinterpret_cast<const unsigned *>(&b);
-    *reinterpret_cast<uint2 *>(p) = t;
-  }
-};
-template <> struct Vec<__nv_bfloat16> {
-  static constexpr int V = 4;
-  __device__ static void ld(const __nv_bfloat16 *p, float *o, float is) {
-    const uint2 t = *reinterpret_cast<const uint2 *>(p);
-    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&t.x);
-    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&t.y);
-    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-    o[0] = fa.x * is; o[1] = fa.y * is; o[2] = fb.x * is; o[3] = fb.y * is;
-  }
-  __device__ static void st(__nv_bfloat16 *p, const float *v, float sc) {
-    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0] * sc, v[1] * sc);
-    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2] * sc, v[3] * sc);
-    uint2 t;
-    t.x = *reinterpret_cast<const unsigned *>(&a);
-    t.y = *reinterpret_cast<const unsigned *>(&b);
-    *reinterpret_cast<uint2 *>(p) = t;
-  }
-};
-
-// V consecutive arithmetic values (jump / force fields): float4 or double2.
-template <typename T, int V>
-__device__ inline void stT(T *p, const T *v) {
-  if constexpr (sizeof(T) == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  else *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
-}
-template <typename T, int V>
-__device__ inline void ldT(const T *p, T *o) {
-  if constexpr (sizeof(T) == 4) {
-    const float4 t = *reinterpret_cast<const float4 *>(p);
-    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
-  } else {
-    const double2 t = *reinterpret_cast<const double2 *>(p);
-    o[0] = t.x; o[1] = t.y;
-  }
-}
-
-
-// One node per thread on a 32 x TILE_Y sub-block whose first node is (xb, yb).  BC is
-// IILBM_BC_PERIODIC, IILBM_BC_WALLS_Y (periodic x, halfway bounce-back in y) or
-// IILBM_BC_CHANNEL (walls in y, ghost columns in x filled by the channel boundary).
-template <typename S, int COLL, bool ODD, int BC, bool FORCED>
-__device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
-                                                typename Store<S>::T *__restrict__ Jf,
-                                                typename Store<S>::T *__restrict__ gf,
-                                                typename Store<S>::T *__restrict__ uf,
-                                                const Geom &geo,
-                                                const CollP<typename Store<S>::T> &p, int *status,
-                                                int xb, int yb) {
-  using T = typename Store<S>::T;
-  const int x = xb + threadIdx.x, y = yb + threadIdx.y;
-  if (x >= geo.nx || y >= geo.ny) return;
-  const long long P = geo.plane;
-  const long long here = (long long)y * geo.pitch + x;
-  const int xm = x == 0 ? (BC == IILBM_BC_CHANNEL ? geo.pitch - 1 : geo.nx - 1) : x - 1;
-  const int xp = x == geo.nx - 1 ? (BC == IILBM_BC_CHANNEL ? geo.nx : 0) : x + 1;
-  int ym = y - 1, yp = y + 1;
-  bool wall_m = false, wall_p = false;
-  if (BC == IILBM_BC_PERIODIC) {
-    ym = y == 0 ? geo.ny - 1 : ym;
-    yp = y == geo.ny - 1 ? 0 : yp;
-  } else {
-    wall_m = y == 0;
-    wall_p = y == geo.ny - 1;
-  }
-  const long long col[3] = {xm, x, xp};
-  const long long row[3] = {(long long)ym * geo.pitch, (long long)y * geo.pitch,
-                            (long long)yp * geo.pitch};
-  T f[9];
-#pragma unroll
-  for (int i = 0; i < 9; i++) {
-    long long src = i * P + here;
-    if (ODD) {
-      const bool from_wall = (cy(i) > 0 && wall_m) || (cy(i) < 0 && wall_p);
-      if (!from_wall) src = opp(i) * P + row[1 - cy(i)] + col[1 - cx(i)];
-    }
-    f[i] = Store<S>::ld(A[src]) * p.inv_scale;
-  }
-  T gx = p.bodyx, gy = p.bodyy;
-  if (FORCED) {
-#pragma unroll
-    for (int i = 1; i < 9; i++) f[i] += Jf[(i - 1) * P + here];
-    gx += gf[here];
-    gy += gf[P + here];
-  }
-  T ux, uy;
-  const T drho = collide<T, COLL>(f, gx, gy, p, ux, uy);
-  if (!isfinite(drho)) atomicOr(status, ST_NONFINITE);
-  if (FORCED) {  // the velocity the markers are interpolated from (Eq. 20)
-    uf[here] = ux;
-    uf[P + here] = uy;
-    // consumed: leave the buffer clean for the interface phase two steps on
-#pragma unroll
-    for (int i = 1; i < 9; i++) Jf[(i - 1) * P + here] = T(0);
-    gf[here] = T(0);
-    gf[P + here] = T(0);
-  }
-#pragma unroll
-  for (int i = 0; i < 9; i++) {
-    long long dst = opp(i) * P + here;
-    if (ODD) {
-      const bool to_wall = (cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m);
-      if (!to_wall) dst = i * P + row[1 + cy(i)] + col[1 + cx(i)];
-    }
-    A[dst] = Store<S>::st(f[i] * p.scale);
-  }
-}
-
-// Vectorised: each thread owns V consecutive nodes of one row (V = 4 for FP32 /
-// FP16 / BF16 storage, 2 for FP64) and moves every population plane with one 16-byte
-// (8-byte for 16-bit storage) access.  A warp covers 32 V nodes of row yb + warp, the
-// first at xb.  In the odd step the planes with e_x = +-1 are shifted by one node: the
-// aligned vector is loaded (stored) and the single element that crosses into the
-// neighbouring lane travels by warp shuffle; lane 0, lane 31 and the last active lane
-// of a row fetch / write that element with a scalar access instead, wrapping around
-// the periodic row.  Requires nx % V == 0.  Every lane of the warp must call this.
-template <typename S, int COLL, bool ODD, int BC, bool FORCED>
-__device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
-                                             typename Store<S>::T *__restrict__ Jf,
-                                             typename Store<S>::T *__restrict__ gf,
-                                             typename Store<S>::T *__restrict__ uf,
-                                             const Geom &geo,
-                                             const CollP<typename Store<S>::T> &p, int *status,
-                                             int xb, int yb) {
-  using T = typename Store<S>::T;
-  constexpr int V = Vec<S>::V;
-  const int lane = threadIdx.x & 31;
-  const int y = yb + (threadIdx.x >> 5);
-  if (y >= geo.ny) return;  // uniform per warp
-  const int x0 = xb + lane * V;
-  const bool active = x0 < geo.nx;
-  const bool edge_r = active && (lane == 31 || x0 + V >= geo.nx);
-  const long long P = geo.plane;
-  int ym = y - 1, yp = y + 1;
-  bool wall_m = false, wall_p = false;
-  if (BC == IILBM_BC_PERIODIC) {
-    ym = y == 0 ? geo.ny - 1 : ym;
-    yp = y == geo.ny - 1 ? 0 : yp;
-  } else {
-    wall_m = y == 0;
-    wall_p = y == geo.ny - 1;
-  }
-  const long long row[3] = {(long long)ym * geo.pitch, (long long)y * geo.pitch,
-                            (long long)yp * geo.pitch};
-  const long long here = row[1] + x0;
-  // left / right neighbour column of the chunk (wrapped, or a channel's ghost column)
-  const int xl = x0 == 0 ? (BC == IILBM_BC_CHANNEL ? geo.pitch - 1 : geo.nx - 1) : x0 - 1;
-  const int xr = x0 + V >= geo.nx ? (BC == IILBM_BC_CHANNEL ? geo.nx : 0) : x0 + V;
-
-  T f[9][V];
-#pragma unroll
-  for (int i = 0; i < 9; i++) {
-#pragma unroll
-    for (int j = 0; j < V; j++) f[i][j] = T(0);
-    const bool from_wall = ODD && ((cy(i) > 0 && wall_m) || (cy(i) < 0 && wall_p));
-    if (!ODD || from_wall) {
-      if (active) Vec<S>::ld(A + i * P + here, f[i], p.inv_scale);
-    } else {
-      const long long base = opp(i) * P + row[1 - cy(i)];
-      T c[V];
-#pragma unroll
-      for (int j = 0; j < V; j++) c[j] = T(0);
-      if (active) Vec<S>::ld(A + base + x0, c, p.inv_scale);
-      if (cx(i) == 0) {
-#pragma unroll
-        for (int j = 0; j < V; j++) f[i][j] = c[j];
-      } else if (cx(i) > 0) {  // source x - 1
-        T left = __shfl_up_sync(0xffffffffu, c[V - 1], 1);
-        if (active && lane == 0) left = Store<S>::ld(A[base + xl]) * p.inv_scale;
-        f[i][0] = left;
-#pragma unroll
-        for (int j = 1; j < V; j++) f[i][j] = c[j - 1];
-      } else {  // source x + 1
-        T right = __shfl_down_sync(0xffffffffu, c[0], 1);
-        if (edge_r) right = Store<S>::ld(A[base + xr]) * p.inv_scale;
-#pragma unroll
-        for (int j = 0; j < V - 1; j++) f[i][j] = c[j + 1];
-        f[i][V - 1] = right;
-      }
-    }
-  }
-  T gx[V], gy[V];
-#pragma unroll
-  for (int j = 0; j < V; j++) { gx[j] = p.bodyx; gy[j] = p.bodyy; }
-  if (FORCED && active) {
-#pragma unroll
-    for (int i = 1; i < 9; i++) {
-      T jv[V];
-      ldT<T, V>(Jf + (i - 1) * P + here, jv);
-#pragma unroll
-      for (int j = 0; j < V; j++) f[i][j] += jv[j];
-    }
-    T a[V], b[V];
-    ldT<T, V>(gf + here, a);
-    ldT<T, V>(gf + P + here, b);
-#pragma unroll
-    for (int j = 0; j < V; j++) { gx[j] += a[j]; gy[j] += b[j]; }
-  }
-  bool finite = true;
-  T uxv[V], uyv[V];
-#pragma unroll
-  for (int j = 0; j < V; j++) {
-    T fc[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) fc[i] = f[i][j];
-    const T drho = collide<T, COLL>(fc, gx[j], gy[j], p, uxv[j], uyv[j]);
-    finite = finite && isfinite(drho);
-#pragma unroll
-    for (int i = 0; i < 9; i++) f[i][j] = fc[i];
-  }
-  if (active && !finite) atomicOr(status, ST_NONFINITE);
-  if (FORCED && active) {  // the velocity the markers are interpolated from (Eq. 20)
-    stT<T, V>(uf + here, uxv);
-    stT<T, V>(uf + P + here, uyv);
-    // consumed: leave the buffer clean for the interface phase two steps on
-    T z[V];
-#pragma unroll
-    for (int j = 0; j < V; j++) z[j] = T(0);
-#pragma unroll
-    for (int i = 1; i < 9; i++) stT<T, V>(Jf + (i - 1) * P + here, z);
-    stT<T, V>(gf + here, z);
-    stT<T, V>(gf + P + here, z);
-  }
-
-#pragma unroll
-  for (int i = 0; i < 9; i++) {
-    const bool to_wall = ODD && ((cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m));
-    if (!ODD || to_wall) {
-      if (active) Vec<S>::st(A + opp(i) * P + here, f[i], p.scale);
-    } else {
-      const long long base = i * P + row[1 + cy(i)];
-      if (cx(i) == 0) {
-        if (active) Vec<S>::st(A + base + x0, f[i], p.scale);
-      } else if (cx(i) > 0) {  // destination x + 1
-        const T in = __shfl_up_sync(0xffffffffu, f[i][V - 1], 1);
-        if (active) {
-          if (lane != 0) {
-            T v[V];
-            v[0] = in;
-#pragma unroll
-            for (int j = 1; j < V; j++) v[j] = f[i][j - 1];
-            Vec<S>::st(A + base + x0, v, p.scale);
-          } else {
-#pragma unroll
-            for (int j = 0; j < V - 1; j++) A[base + x0 + 1 + j] = Store<S>::st(f[i][j] * p.scale);
-          }
-          if (edge_r) A[base + xr] = Store<S>::st(f[i][V - 1] * p.scale);
-        }
-      } else {  // destination x - 1
-        const T in = __shfl_down_sync(0xffffffffu, f[i][0], 1);
-        if (active) {
-          if (!edge_r) {
-            T v[V];
-#pragma unroll
-            for (int j = 0; j < V - 1; j++) v[j] = f[i][j + 1];
-            v[V - 1] = in;
-            Vec<S>::st(A + base + x0, v, p.scale);
-          } else {
-#pragma unroll
-            for (int j = 1; j < V; j++) A[base + x0 + j - 1] = Store<S>::st(f[i][j] * p.scale);
-          }
-          if (lane == 0) A[base + xl] = Store<S>::st(f[i][0] * p.scale);
-        }
-      }
-    }
-  }
-}
-
-constexpr int VEC_ROWS = TILE_Y;  // warps (rows) per block of the vectorised kernels
 
 // Lean kernels: one block per (sub-)tile; a flagged tile is left to the forced kernel.
 template <typename S, int COLL, bool ODD, int BC>
@@ -501,17 +76,6 @@ __global__ void __launch_bounds__(32 * VEC_ROWS)
     for (int sub = 0; sub < TILE_X; sub += W)
       sc_vec_block<S, COLL, ODD, BC, true>(A, Jf, gf, uf, geo, p, status, tx + sub, ty);
   }
-}
-
-// ------------------------------------------------------ Peskin delta (Eq. 17)
-// Four-point kernel phi(r) in the arithmetic type T (GB300's FP64 rate is a small
-// fraction of its FP32 rate, so FP64 is kept to positions and accumulations).
-template <typename T>
-__device__ inline T phi4(T r) {
-  const T a = fabs(r);
-  if (a < T(1)) return T(0.125) * (T(3) - T(2) * a + sqrt(T(1) + T(4) * a - T(4) * a * a));
-  if (a < T(2)) return T(0.125) * (T(5) - T(2) * a - sqrt(T(-7) + T(12) * a - T(4) * a * a));
-  return T(0);
 }
 
 // Macroscopic density deviation and velocity of node (x, y) of the current state:
@@ -651,30 +215,8 @@ __global__ void k_get_populations(const S *A, const Geom geo,
 template <typename S>
 __global__ void k_channel_bc(S *A, const Geom geo, const CollP<typename Store<S>::T> p,
                              bool odd, double u_max) {
-  using T = typename Store<S>::T;
   const int y = blockIdx.x * blockDim.x + threadIdx.x;
-  if (y >= geo.ny) return;
-  T f[9];
-#pragma unroll
-  for (int i = 0; i < 9; i++) f[i] = Store<S>::ld(A[aa_loc(geo, odd, i, 1, y)]) * p.inv_scale;
-  const T d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-  const T rho = p.rho0 + d;
-  const T ux = ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7])) / rho;
-  const T uy = ((f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8])) / rho;
-  const double yy = y + 0.5;
-  const T uin = T(4.0 * u_max * yy * (geo.ny - yy) / ((double)geo.ny * geo.ny));
-  const T u2 = ux * ux + uy * uy, uin2 = uin * uin;
-#pragma unroll
-  for (int i = 0; i < 9; i++) {
-    const T eu = T(cx(i)) * ux + T(cy(i)) * uy, ei = T(cx(i)) * uin;
-    const T feq_in = wt<T>(i) * (d + rho * (T(3) * ei + T(4.5) * ei * ei - T(1.5) * uin2));
-    const T feq_1 = wt<T>(i) * (d + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * u2));
-    A[aa_loc(geo, odd, i, 0, y)] = Store<S>::st((feq_in + (f[i] - feq_1)) * p.scale);
-  }
-  constexpr int out[3] = {3, 6, 7};
-#pragma unroll
-  for (int q = 0; q < 3; q++)
-    A[aa_loc(geo, odd, out[q], geo.nx - 1, y)] = A[aa_loc(geo, odd, out[q], geo.nx - 2, y)];
+  if (y < geo.ny) channel_bc_row<S>(A, geo, p, odd, u_max, y);
 }
 
 // ------------------------------------------------------------------ dispatch

@@ -18,6 +18,8 @@ import numpy as np
 from . import build as _build
 
 OK = 0
+(ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_NONFINITE, ERR_INTERFACE,
+ ERR_CAPACITY, ERR_NO_DEVICE) = range(-1, -9, -1)
 SRT, MRT = 0, 1
 F64, F32, F16, BF16 = 0, 1, 2, 3
 BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL = 0, 1, 2
@@ -73,7 +75,20 @@ SIGNATURES = {
     "iilbm_get_macros_noalloc": [_H, _P, _P, _P],
     "iilbm_synchronize": [_H],
     "iilbm_error_string": [C.c_int],
+    "iilbm_create_batch": [C.POINTER(_H), C.POINTER(_H), C.c_int32, _P],
+    "iilbm_destroy_batch": [_H],
+    "iilbm_batch_step": [_H, C.c_int32],
+    "iilbm_batch_set_variant": [_H, C.c_int32],
+    "iilbm_batch_autotune": [_H, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double)],
+    "iilbm_batch_set_timing": [_H, C.c_int32],
+    "iilbm_batch_get_timing": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int64)],
+    "iilbm_batch_synchronize": [_H],
 }
+
+# stream-collide variants of a batch (iilbm_batch_set_variant)
+BATCH_VARIANTS = ("vec-per-tile", "vec-persistent-2", "vec-persistent-4", "scalar-per-tile",
+                  "scalar-persistent-2")
 
 
 def library_path() -> str:
@@ -290,3 +305,69 @@ class Lattice:
         _check("iilbm_synchronize", self._L.iilbm_synchronize(self._h))
 
     synchronize = iilbm_synchronize
+
+
+class Batch:
+    """Many lattices advanced together (handle of iilbm_create_batch).  Holds references
+    to its lattices so that they outlive it."""
+
+    def __init__(self, lattices, stream=None):
+        L = load()
+        self.lattices = list(lattices)
+        arr = (_H * len(self.lattices))(*[g.handle for g in self.lattices])
+        h = _H()
+        _check("iilbm_create_batch",
+               L.iilbm_create_batch(C.byref(h), arr, len(self.lattices), stream))
+        self._h = h
+        self._L = L
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.iilbm_destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def iilbm_batch_step(self, n=1):
+        _check("iilbm_batch_step", self._L.iilbm_batch_step(self._h, int(n)))
+
+    step = iilbm_batch_step
+
+    def iilbm_batch_set_variant(self, variant):
+        if isinstance(variant, str):
+            variant = BATCH_VARIANTS.index(variant)
+        _check("iilbm_batch_set_variant", self._L.iilbm_batch_set_variant(self._h, int(variant)))
+
+    def iilbm_batch_autotune(self, steps=64):
+        """Time every stream-collide variant on the batch itself (the lattices advance);
+        returns (variant chosen, us per step)."""
+        v, us = C.c_int32(), C.c_double()
+        _check("iilbm_batch_autotune",
+               self._L.iilbm_batch_autotune(self._h, int(steps), C.byref(v), C.byref(us)))
+        return v.value, us.value
+
+    autotune = iilbm_batch_autotune
+
+    def iilbm_batch_set_timing(self, enable=True):
+        _check("iilbm_batch_set_timing", self._L.iilbm_batch_set_timing(self._h, int(enable)))
+
+    def iilbm_batch_get_timing(self):
+        ms, n, k = C.c_double(), C.c_int32(), C.c_int64()
+        _check("iilbm_batch_get_timing",
+               self._L.iilbm_batch_get_timing(self._h, C.byref(ms), C.byref(n), C.byref(k)))
+        return ms.value, n.value, k.value
+
+    def iilbm_batch_synchronize(self):
+        _check("iilbm_batch_synchronize", self._L.iilbm_batch_synchronize(self._h))
+
+    synchronize = iilbm_batch_synchronize

@@ -51,11 +51,13 @@ int read_status(iilbm_lattice *h) {
 }
 
 void free_interface(iilbm_lattice *h) {
-  double **bufs[] = {&h->X, &h->aux, &h->G, &h->Fn, &h->P, &h->U, &h->nrm, &h->G0, &h->Gdf};
+  double **bufs[] = {&h->X, &h->aux, &h->G, &h->Fn, &h->U, &h->nrm, &h->G0, &h->Gdf};
   for (double **b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
   }
+  if (h->Xq) cudaFree(h->Xq);
+  h->Xq = nullptr;
   h->nm = 0;
 }
 
@@ -266,7 +268,7 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
             cudaMalloc(&h->G, b2) == cudaSuccess && cudaMalloc(&h->G0, b2) == cudaSuccess &&
             cudaMalloc(&h->Gdf, b2) == cudaSuccess &&
             cudaMalloc(&h->Fn, (size_t)n * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&h->P, b2) == cudaSuccess && cudaMalloc(&h->U, b2) == cudaSuccess &&
+            cudaMalloc(&h->Xq, b2) == cudaSuccess && cudaMalloc(&h->U, b2) == cudaSuccess &&
             cudaMalloc(&h->nrm, b2) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -402,10 +404,11 @@ int drain_all(iilbm_lattice *h) {
 }
 
 // Kernels launched by one step: lean stream-collide; with an interface also the
-// forced stream-collide, the interpolation and the fused interface kernel (and the
-// force iteration for direct forcing); a channel adds its boundary kernel.
+// forced stream-collide, the interpolation and the two interface kernels (marker and
+// segment pass; and the force iteration for direct forcing); a channel adds its
+// boundary kernel.
 long long kernels_per_step(const iilbm_lattice *h) {
-  return 1 + (h->nm > 0 ? 3 + (h->ip.model == IILBM_DIRECT ? 1 : 0) : 0) +
+  return 1 + (h->nm > 0 ? 4 + (h->ip.model == IILBM_DIRECT ? 1 : 0) : 0) +
          (h->cfg.bc == IILBM_BC_CHANNEL ? 1 : 0);
 }
 

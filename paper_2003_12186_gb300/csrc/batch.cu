@@ -6,7 +6,7 @@
 //   * lean stream-collide over a flattened list of (lattice, tile) work items, either
 //     one block per item or a persistent grid striding over the list;
 //   * forced stream-collide over each lattice's flagged-tile list (grid.y = lattice);
-//   * interpolation and the fused interface kernel over a flattened marker list;
+//   * interpolation and the two interface passes over a flattened marker list;
 //   * direct forcing, one CTA per fixed body; the channel ends, one row per thread.
 // The kernels resolve their lattice from a device table of descriptors and run the
 // same device code as the single-lattice path.  An autotuner times the stream-collide
@@ -29,6 +29,7 @@ namespace iilbm {
 // One lattice of the batch as the batched kernels see it.
 struct SimDev {
   Geom geo;
+  int ntiles;
   void *A;
   void *J[2], *g[2];
   unsigned *flags[2];
@@ -36,6 +37,7 @@ struct SimDev {
   int *list[2], *ctr[2];
   void *uf;
   double *X, *aux, *G, *Fn, *nrm, *U;
+  long long *Xq;
   int nm, jump;
   iilbm_interface_params ip;
   CollP<float> p;
@@ -50,30 +52,48 @@ enum { BV_VEC_ITEM = 0, BV_VEC_PERSIST2, BV_VEC_PERSIST4, BV_SCALAR_ITEM, BV_SCA
        BV_COUNT };
 
 // ----------------------------------------------------------------- kernels
+// A work item is up to LEAN_GROUP consecutive tiles of one lattice: the lattice's
+// descriptor, tag and the group's flags are loaded once, before its first tile.
+constexpr int LEAN_GROUP = 4;
+
 template <typename S, int COLL, bool ODD, int BC, bool VEC>
 __global__ void __launch_bounds__(256, 3)
     k_batch_lean(const SimDev *__restrict__ sims, const int2 *__restrict__ items, int nitems) {
   constexpr int b = ODD ? 1 : 0;  // buffer of the state = its parity
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int2 w = items[it];  // (lattice, tile)
+    const int2 w = items[it];  // (lattice, first tile)
     const SimDev &sd = sims[w.x];
-    if (sd.flags[b][w.y] == *sd.tag[b]) continue;  // uniform per block: forced tile
-    const int tx = (w.y % sd.geo.ntx) * TILE_X, ty = (w.y / sd.geo.ntx) * TILE_Y;
-    if (VEC) {
-      constexpr int W = 32 * Vec<S>::V;
-      for (int sub = 0; sub < TILE_X; sub += W)
-        sc_vec_block<S, COLL, ODD, BC, false>((S *)sd.A, nullptr, nullptr, nullptr, sd.geo, sd.p,
-                                              sd.status, tx + sub, ty);
-    } else {
-      for (int sub = 0; sub < TILE_X; sub += 32)
-        sc_scalar_block<S, COLL, ODD, BC, false>((S *)sd.A, nullptr, nullptr, nullptr, sd.geo,
-                                                 sd.p, sd.status, tx + sub, ty);
+    const unsigned *fl = sd.flags[b];
+    const unsigned tag = *sd.tag[b];
+    const int nt = min(LEAN_GROUP, sd.ntiles - w.y);
+    unsigned todo = 0u;  // bit q: tile w.y + q is a lean tile
+#pragma unroll
+    for (int q = 0; q < LEAN_GROUP; q++)
+      if (q < nt && fl[w.y + q] != tag) todo |= 1u << q;
+#pragma unroll 1
+    for (int q = 0; q < nt; q++) {
+      if (!(todo >> q & 1u)) continue;  // uniform per block: a forced tile
+      const int tile = w.y + q;
+      const Geom &geo = sd.geo;
+      const int tx = (tile % geo.ntx) * TILE_X, ty = (tile / geo.ntx) * TILE_Y;
+      if (VEC) {
+        constexpr int W = 32 * Vec<S>::V;
+        for (int sub = 0; sub < TILE_X; sub += W)
+          sc_vec_block<S, COLL, ODD, BC, false>((S *)sd.A, nullptr, nullptr, nullptr, sd.geo,
+                                                sd.p, sd.status, tx + sub, ty);
+      } else {
+        for (int sub = 0; sub < TILE_X; sub += 32)
+          sc_scalar_block<S, COLL, ODD, BC, false>((S *)sd.A, nullptr, nullptr, nullptr, sd.geo,
+                                                   sd.p, sd.status, tx + sub, ty);
+      }
     }
   }
 }
 
+// Two resident blocks per SM (<= 128 registers): the forced tiles are few and short,
+// so memory parallelism, not per-thread registers, sets their pace.
 template <typename S, int COLL, bool ODD, int BC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_batch_forced(const SimDev *__restrict__ sims) {
   constexpr int b = ODD ? 1 : 0;
   const SimDev &sd = sims[blockIdx.y];
@@ -90,11 +110,11 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// 16 threads per marker of the flattened list; thread s < nsims also prepares lattice
+// One thread per marker of the flattened list; thread s < nsims also prepares lattice
 // s's buffer of the next time level (tag advanced, counters reset).
-__global__ void k_batch_interp(const SimDev *__restrict__ sims, int nsims,
-                               const int *__restrict__ msim, const int *__restrict__ mk,
-                               int nmarkers, int next_buf) {
+__global__ void __launch_bounds__(128)
+    k_batch_interp(const SimDev *__restrict__ sims, int nsims, const int *__restrict__ msim,
+                   const int *__restrict__ mk, int nmarkers, int next_buf) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid < nsims && sims[tid].nm > 0) {
     const SimDev &sd = sims[tid];
@@ -102,57 +122,33 @@ __global__ void k_batch_interp(const SimDev *__restrict__ sims, int nsims,
     sd.ctr[next_buf][0] = 0;
     sd.ctr[next_buf][1] = 0;
   }
-  const int m = tid >> 4, l = tid & 15;
-  double sx = 0.0, sy = 0.0;
-  const SimDev *sd = nullptr;
-  int k = 0;
-  if (m < nmarkers) {
-    sd = &sims[msim[m]];
-    k = mk[m];
-    const Geom &geo = sd->geo;
-    const double Xk = sd->X[2 * k], Yk = sd->X[2 * k + 1];
-    const int xa = (int)floor(Xk) - 1 + (l & 3), yb = (int)floor(Yk) - 1 + (l >> 2);
-    int xi = xa, yi = yb;
-    bool ok = true;
-    if (geo.bc == IILBM_BC_CHANNEL) ok = xi >= 0 && xi < geo.nx;
-    else xi = wrap(xi, geo.nx);
-    if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
-    else ok = ok && yi >= 0 && yi < geo.ny;
-    if (ok) {
-      const float *uf = (const float *)sd->uf;
-      const long long here = (long long)yi * geo.pitch + xi;
-      const double w = (double)(phi4<float>(float((double)xa - Xk)) * phi4<float>(float((double)yb - Yk)));
-      sx = (double)uf[here] * w;
-      sy = (double)uf[geo.plane + here] * w;
-    }
-  }
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1) {
-    sx += __shfl_xor_sync(0xffffffffu, sx, o, 16);
-    sy += __shfl_xor_sync(0xffffffffu, sy, o, 16);
-  }
-  if (m < nmarkers && l == 0) {
-    sd->U[2 * k] = sx;
-    sd->U[2 * k + 1] = sy;
-    if (sd->ip.moves) {
-      sd->X[2 * k] += sx;
-      sd->X[2 * k + 1] += sy;
-    }
-  }
+  if (tid >= nmarkers) return;
+  const SimDev &sd = sims[msim[tid]];
+  interp_marker<float>((const float *)sd.uf, sd.geo, sd.X, sd.Xq, mk[tid], sd.U, sd.ip.moves);
 }
 
-// One warp per marker of the flattened list: the interface work of buffer buf.
+// Marker pass of buffer buf, one thread per marker of the flattened list.
 __global__ void __launch_bounds__(128)
-    k_batch_interface(const SimDev *__restrict__ sims, const int *__restrict__ msim,
-                      const int *__restrict__ mk, int nmarkers, int buf) {
+    k_batch_markers(const SimDev *__restrict__ sims, const int *__restrict__ msim,
+                    const int *__restrict__ mk, int nmarkers, int buf) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nmarkers) return;
+  const SimDev &sd = sims[msim[m]];
+  const double *aux = sd.ip.model == IILBM_DIRECT ? sd.df.G : sd.aux;
+  interface_marker<float>(sd.X, aux, sd.nm, mk[m], sd.ip, sd.jump, sd.geo, (float *)sd.g[buf],
+                          sd.G, sd.Fn, sd.nrm, sd.Xq, sd.status);
+}
+
+// Segment pass of buffer buf, one warp per segment of the flattened list.
+__global__ void __launch_bounds__(128)
+    k_batch_segments(const SimDev *__restrict__ sims, const int *__restrict__ msim,
+                     const int *__restrict__ mk, int nmarkers, int buf) {
   const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (m >= nmarkers) return;  // uniform per warp
   const SimDev &sd = sims[msim[m]];
   const TileBuf tb{sd.flags[buf], sd.tag[buf], sd.list[buf], sd.ctr[buf], sd.tiles_total};
-  const double *aux = sd.ip.model == IILBM_DIRECT ? sd.df.G : sd.aux;
-  interface_warp<float>(sd.X, aux, sd.nm, mk[m], threadIdx.x & 31, sd.ip, sd.jump, sd.geo,
-                        (float *)sd.J[buf], (float *)sd.g[buf], tb, sd.G, sd.Fn, sd.nrm,
-                        sd.status);
+  interface_segment<float>(sd.Xq, sd.Fn, sd.nm, mk[m], threadIdx.x & 31, sd.jump, sd.geo,
+                           (float *)sd.J[buf], tb);
 }
 
 // One CTA per lattice with a fixed body under direct forcing.
@@ -278,16 +274,16 @@ int launch_batch_sc(iilbm_batch *B, cudaStream_t s2) {
 
 int launch_batch_interface(iilbm_batch *B, int buf, cudaStream_t s) {
   if (!B->any_iface) return IILBM_OK;
-  const int threads = 32 * B->nmarkers;
-  k_batch_interface<<<(threads + 127) / 128, 128, 0, s>>>(B->d_sims, B->d_msim, B->d_mk,
-                                                         B->nmarkers, buf);
+  const int n = B->nmarkers;
+  k_batch_markers<<<(n + 127) / 128, 128, 0, s>>>(B->d_sims, B->d_msim, B->d_mk, n, buf);
+  k_batch_segments<<<(32 * n + 127) / 128, 128, 0, s>>>(B->d_sims, B->d_msim, B->d_mk, n, buf);
   return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
 }
 
 int launch_batch_interp(iilbm_batch *B, cudaStream_t s) {
   if (!B->any_iface) return IILBM_OK;
-  const int threads = std::max(16 * B->nmarkers, B->nsims);
-  k_batch_interp<<<(threads + 255) / 256, 256, 0, s>>>(B->d_sims, B->nsims, B->d_msim, B->d_mk,
+  const int threads = std::max(B->nmarkers, B->nsims);
+  k_batch_interp<<<(threads + 127) / 128, 128, 0, s>>>(B->d_sims, B->nsims, B->d_msim, B->d_mk,
                                                        B->nmarkers, (int)((B->step + 1) & 1));
   return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
 }
@@ -342,7 +338,7 @@ void sync_lattices(iilbm_batch *B) {
 }
 
 long long batch_kernels_per_step(const iilbm_batch *B) {
-  return 1 + (B->any_iface ? 4 + (B->any_direct ? 1 : 0) : 0) + (B->bc == IILBM_BC_CHANNEL ? 1 : 0);
+  return 1 + (B->any_iface ? 5 + (B->any_direct ? 1 : 0) : 0) + (B->bc == IILBM_BC_CHANNEL ? 1 : 0);
 }
 
 // One time step of every lattice (same structure as the single-lattice step).
@@ -539,6 +535,7 @@ int iilbm_create_batch(iilbm_batch_t *out, const iilbm_t *lattices, int32_t coun
     }
     d.uf = h->uf;
     d.X = h->X; d.aux = h->aux; d.G = h->G; d.Fn = h->Fn; d.nrm = h->nrm; d.U = h->U;
+    d.Xq = h->Xq;
     d.nm = h->nm;
     d.jump = h->cfg.jump;
     d.ip = h->ip;
@@ -561,7 +558,8 @@ int iilbm_create_batch(iilbm_batch_t *out, const iilbm_t *lattices, int32_t coun
     if (h->nm > 0) B->any_iface = true;
     B->max_ny = std::max(B->max_ny, h->geom.ny);
     max_list = std::max(max_list, h->ntiles);
-    for (int t = 0; t < h->ntiles; t++) items.push_back(make_int2(s, t));
+    d.ntiles = h->ntiles;
+    for (int t = 0; t < h->ntiles; t += LEAN_GROUP) items.push_back(make_int2(s, t));
     for (int k = 0; k < h->nm; k++) {
       msim.push_back(s);
       mk.push_back(k);

@@ -8,14 +8,6 @@
 
 namespace iilbm {
 
-template <typename T>
-__device__ inline T phi4d(T r) {
-  const T a = fabs(r);
-  if (a < T(1)) return T(0.125) * (T(3) - T(2) * a + sqrt(T(1) + T(4) * a - T(4) * a * a));
-  if (a < T(2)) return T(0.125) * (T(5) - T(2) * a - sqrt(T(-7) + T(12) * a - T(4) * a * a));
-  return T(0);
-}
-
 struct DfArgs {
   const double *X, *UD, *G0;
   double *G, *U;
@@ -90,7 +82,7 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
       const int k = q >> 4, l = q & 15;
       const double Xk = a.X[2 * k], Yk = a.X[2 * k + 1];
       const int xa = (int)floor(Xk) - 1 + (l & 3), yb = (int)floor(Yk) - 1 + (l >> 2);
-      const T w = phi4d<T>(T((double)xa - Xk)) * phi4d<T>(T((double)yb - Yk));
+      const T w = phi4<T>(T((double)xa - Xk)) * phi4<T>(T((double)yb - Yk));
       const int c = (yb - a.wy0) * a.ww + (xa - a.wx0);
       if (w != T(0)) {
         atomicAdd(&gx[c], T(Gk[2 * k] * a.dX) * w);
@@ -106,7 +98,7 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
         const int k = q >> 4, l = q & 15;
         const double Xk = a.X[2 * k], Yk = a.X[2 * k + 1];
         const int xa = (int)floor(Xk) - 1 + (l & 3), yb = (int)floor(Yk) - 1 + (l >> 2);
-        const T w = phi4d<T>(T((double)xa - Xk)) * phi4d<T>(T((double)yb - Yk));
+        const T w = phi4<T>(T((double)xa - Xk)) * phi4<T>(T((double)yb - Yk));
         const int c = (yb - a.wy0) * a.ww + (xa - a.wx0);
         sx = (double)((usx[c] + gx[c] * h2r[c]) * w);
         sy = (double)((usy[c] + gy[c] * h2r[c]) * w);

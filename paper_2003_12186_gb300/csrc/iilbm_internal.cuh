@@ -52,6 +52,19 @@ constexpr int GRAPH_RING = 4;
 constexpr int EAGER_EV0 = 2 * GRAPH_STEPS * GRAPH_RING;  // first eager timing event
 constexpr int EAGER_PAIRS = 128;
 
+// Sentinel of a snapped marker coordinate outside the region the integer geometry covers.
+constexpr long long XQ_OUT = (long long)(-0x7fffffffffffffffLL - 1);
+
+// ------------------------------------------------------ Peskin delta (Eq. 17)
+// Peskin's four-point kernel phi(r) in the arithmetic type T.
+template <typename T>
+__device__ inline T phi4(T r) {
+  const T a = fabs(r);
+  if (a < T(1)) return T(0.125) * (T(3) - T(2) * a + sqrt(T(1) + T(4) * a - T(4) * a * a));
+  if (a < T(2)) return T(0.125) * (T(5) - T(2) * a - sqrt(T(-7) + T(12) * a - T(4) * a * a));
+  return T(0);
+}
+
 // ------------------------------------------------------------ storage types
 // Populations are stored as df * 2^k in S and computed in T (double for FP64
 // storage, float otherwise).
@@ -163,7 +176,8 @@ struct iilbm_lattice {
   // interface
   int nm;
   iilbm_interface_params ip;
-  double *X, *aux, *G, *Fn, *P, *U, *nrm;
+  double *X, *aux, *G, *Fn, *U, *nrm;
+  long long *Xq;      // marker coordinates snapped to 2^-24 (XQ_OUT outside the region)
   double *G0, *Gdf;   // direct forcing: warm start and converged force
   int *d_mdf_iters;
   double *d_mdf_res;

@@ -48,15 +48,6 @@ __device__ inline int tile_span(int a, int b, int n, bool periodic, int w, int *
   return cnt;
 }
 
-// Peskin's four-point kernel phi(r) in the arithmetic type T.
-template <typename T>
-__device__ inline T phi4t(T r) {
-  const T a = fabs(r);
-  if (a < T(1)) return T(0.125) * (T(3) - T(2) * a + sqrt(T(1) + T(4) * a - T(4) * a * a));
-  if (a < T(2)) return T(0.125) * (T(5) - T(2) * a - sqrt(T(-7) + T(12) * a - T(4) * a * a));
-  return T(0);
-}
-
 // Force of marker j and its split: G_j, n_j, Fn_j = G_j.n_j/|X_s|_j, and the point
 // force to spread P_j = dX * (tangential part in II-LBM, whole G in IB-LBM).  Marker
 // positions and their differences (including the spring's second difference, a small
@@ -137,62 +128,147 @@ __device__ inline int orient_link_pt(long long px, long long py, int ex, int ey,
   return ex > 0 ? -1 : 1;
 }
 
-// Crossings found by a lane are buffered (candidate index, sign, raw orientations) and
-// their FP64 coefficients computed together, so the FP64 division runs about once per
-// warp rather than once per candidate sweep.
+// ------------------------------------------------------------- marker pass
+// One thread per marker j: its force and normal split, its coordinates snapped to
+// 2^-24 for the segment pass, and the spreading of its point force P_j over the 4 x 4
+// stencil (Eq. 46 in II-LBM, Eq. 17 in IB-LBM).  Running this per thread rather than
+// once per warp keeps GB300's FP64 pipe (a small fraction of its FP32 rate) off the
+// critical path: the FP64 work of a marker is done once, by one lane.
+//
+// Stencil: nodes floor(X) - 1 .. floor(X) + 2 on each axis.  For FP64 storage the
+// floor and the node offsets are taken from the FP64 coordinate; otherwise from the
+// snapped one (the choices differ only within 2^-25 below a lattice line, where the
+// dropped node's weight is O(2^-50)), so the 32-bit path needs no FP64 here.
+template <typename T>
+__device__ inline void stencil_weights(double x, long long q, int &base, T w[4]) {
+  if (sizeof(T) == 8) {
+    base = (int)floor(x) - 1;
+#pragma unroll
+    for (int a = 0; a < 4; a++) w[a] = phi4<T>(T((double)(base + a) - x));
+  } else {
+    base = (int)(q >> 24) - 1;
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+      w[a] = phi4<T>(T((int)((long long)(base + a) * (long long)QSCALE - q)) * T(1.0 / QSCALE));
+  }
+}
+
+__device__ inline bool in_region(double x, double y) {
+  return fabs(x) <= MAX_COORD && fabs(y) <= MAX_COORD;
+}
+
+template <typename T>
+__device__ __forceinline__ void interface_marker(const double *__restrict__ X,
+                                                 const double *__restrict__ aux, int n, int j,
+                                                 const iilbm_interface_params &ip, int jump,
+                                                 const Geom &geo, T *gf, double *G, double *Fn,
+                                                 double *nrm, long long *Xq, int *status) {
+  const MarkerForce<T> m = marker_force<T>(X, aux, n, j, ip, jump, geo);
+  if (m.bad) atomicOr(status, ST_INTERFACE);
+  G[2 * j] = (double)m.gx;
+  G[2 * j + 1] = (double)m.gy;
+  Fn[j] = (double)m.fn;
+  nrm[2 * j] = (double)m.nx;
+  nrm[2 * j + 1] = (double)m.ny;
+  const int jp = j + 1 == n ? 0 : j + 1;
+  const double x = X[2 * j], y = X[2 * j + 1];
+  const bool inside = in_region(x, y);
+  const long long qx = inside ? __double2ll_rn(x * QSCALE) : XQ_OUT;
+  const long long qy = inside ? __double2ll_rn(y * QSCALE) : XQ_OUT;
+  Xq[2 * j] = qx;
+  Xq[2 * j + 1] = qy;
+  // the spread goes into the tiles that the segment j -> j+1 flags, so it needs both ends
+  if (!inside || !in_region(X[2 * jp], X[2 * jp + 1])) return;
+  int bx, by;
+  T wx[4], wy[4];
+  stencil_weights<T>(x, qx, bx, wx);
+  stencil_weights<T>(y, qy, by, wy);
+#pragma unroll
+  for (int b = 0; b < 4; b++) {
+    int yi = by + b;
+    bool oky = true;
+    if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
+    else oky = yi >= 0 && yi < geo.ny;
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      int xi = bx + a;
+      bool ok = oky;
+      if (geo.bc == IILBM_BC_CHANNEL) ok = ok && xi >= 0 && xi < geo.nx;
+      else xi = wrap(xi, geo.nx);
+      const T w = wx[a] * wy[b];
+      if (ok && w != T(0)) {
+        const long long here = (long long)yi * geo.pitch + xi;
+        atomicAdd(&gf[here], m.px * w);
+        atomicAdd(&gf[geo.plane + here], m.py * w);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ segment pass
+// One warp per segment k -> k+1: every lattice link x - e_i -> x that crosses it, and
+// the tiles of its footprint.  Integer geometry on the snapped coordinates written by
+// the marker pass.  The orientation of a lattice node against the segment's line is
+// shared by the 8 links that end there and the 8 that start there, so for a short
+// segment each node's sign is computed once and published to the warp as one bit of a
+// 64-bit ballot; a candidate link then costs two bit lookups, and only links whose ends
+// straddle the line take the two link-side tests.
+// Crossings found by a lane are buffered and their coefficients computed together.
 constexpr int CROSS_BUF = 4;
 
-// All interface work of marker k (and segment k -> k+1) for one warp (lane 0..31).
 template <typename T>
-__device__ __forceinline__ void interface_warp(const double *__restrict__ X,
-                                               const double *__restrict__ aux, int n, int k,
-                                               int lane, const iilbm_interface_params &ip,
-                                               int jump, const Geom &geo, T *Jf, T *gf,
-                                               const TileBuf &tb, double *G, double *Fn,
-                                               double *nrm, int *status) {
+__device__ __forceinline__ void interface_segment(const long long *__restrict__ Xq,
+                                                  const double *__restrict__ Fn, int n, int k,
+                                                  int lane, int jump, const Geom &geo, T *Jf,
+                                                  const TileBuf &tb) {
   const int kp = k + 1 == n ? 0 : k + 1;
-  // forces of k (lane 0) and k + 1 (lane 1)
-  MarkerForce<T> m{};
-  if (lane < 2) m = marker_force<T>(X, aux, n, lane == 0 ? k : kp, ip, jump, geo);
-  const double FnA = (double)__shfl_sync(0xffffffffu, m.fn, 0);
-  const double FnB = (double)__shfl_sync(0xffffffffu, m.fn, 1);
-  const T Pkx = __shfl_sync(0xffffffffu, m.px, 0);  // point force of marker k
-  const T Pky = __shfl_sync(0xffffffffu, m.py, 0);
-  if (lane == 0) {
-    if (m.bad) atomicOr(status, ST_INTERFACE);
-    G[2 * k] = (double)m.gx;
-    G[2 * k + 1] = (double)m.gy;
-    Fn[k] = (double)m.fn;
-    nrm[2 * k] = (double)m.nx;
-    nrm[2 * k + 1] = (double)m.ny;
-  }
-  const double Ax = X[2 * k], Ay = X[2 * k + 1], Bx = X[2 * kp], By = X[2 * kp + 1];
-  // Everything geometric below runs on the coordinates snapped to 2^-24 (exact, as the
-  // crossing predicate needs) in 64-bit integers: GB300 executes FP64 -- compares,
-  // conversions and rounding included -- at a small fraction of its integer rate.
-  const bool inside = fabs(Ax) <= MAX_COORD && fabs(Ay) <= MAX_COORD && fabs(Bx) <= MAX_COORD &&
-                      fabs(By) <= MAX_COORD;
-  const long long ax = inside ? __double2ll_rn(Ax * QSCALE) : 0;
-  const long long ay = inside ? __double2ll_rn(Ay * QSCALE) : 0;
-  const long long bx = inside ? __double2ll_rn(Bx * QSCALE) : 0;
-  const long long by = inside ? __double2ll_rn(By * QSCALE) : 0;
+  const long long ax = Xq[2 * k], ay = Xq[2 * k + 1], bx = Xq[2 * kp], by = Xq[2 * kp + 1];
+  const bool inside = ax != XQ_OUT && bx != XQ_OUT;
   const long long Q = (long long)QSCALE;
   const long long QMAX = (long long)(MAX_SEGMENT * QSCALE);
   // floor / ceil of a snapped coordinate in lattice units
   auto qfloor = [](long long v) { return (int)(v >> 24); };
   auto qceil = [](long long v) { return (int)-((-v) >> 24); };
-  // ---- cut links of segment k -> k+1
   int found = 0;
   if (jump && inside && llabs(bx - ax) < QMAX && llabs(by - ay) < QMAX) {
-    const int x0 = qfloor(min(ax, bx)) - 1, x1 = qceil(max(ax, bx)) + 1;
-    const int y0 = qfloor(min(ay, by)) - 1, y1 = qceil(max(ay, by)) + 1;
+    const double FnA = Fn[k], FnB = Fn[kp];
+    // destinations x of links that can reach the segment: with the node displaced by
+    // (eps, eps^2) the link x - e_i -> x spans [x - 1 + eps, x + 1 + eps] at most on
+    // each axis, which meets [min, max] only for ceil(min) - 1 <= x <= ceil(max)
+    const int x0 = qceil(min(ax, bx)) - 1, x1 = qceil(max(ax, bx));
+    const int y0 = qceil(min(ay, by)) - 1, y1 = qceil(max(ay, by));
     const int W = x1 - x0 + 1, H = y1 - y0 + 1;
     const int ncand = W * H * 8;
+    // node signs on the grid [x0-1, x1+1] x [y0-1, y1+1] (GW x GH nodes)
+    const int GW = W + 2, GH = H + 2;
+    const bool fast = GW * GH <= 64;
+    unsigned lo = 0u, hi = 0u;
+    if (fast) {
+      bool p0 = false, p1 = false;
+      if (lane < GW * GH)
+        p0 = orient_seg_node(ax, ay, bx, by, (long long)(x0 - 1 + lane % GW) * Q,
+                             (long long)(y0 - 1 + lane / GW) * Q) > 0;
+      if (lane + 32 < GW * GH)
+        p1 = orient_seg_node(ax, ay, bx, by, (long long)(x0 - 1 + (lane + 32) % GW) * Q,
+                             (long long)(y0 - 1 + (lane + 32) / GW) * Q) > 0;
+      lo = __ballot_sync(0xffffffffu, p0);
+      hi = __ballot_sync(0xffffffffu, p1);
+    }
+    auto node_sign = [&](int qx, int qy) {
+      if (fast) {
+        const int idx = (qy - y0 + 1) * GW + (qx - x0 + 1);
+        const unsigned bit = idx < 32 ? (lo >> idx) & 1u : (hi >> (idx - 32)) & 1u;
+        return bit ? 1 : -1;
+      }
+      return orient_seg_node(ax, ay, bx, by, (long long)qx * Q, (long long)qy * Q);
+    };
     int bc_idx[CROSS_BUF], bc_s[CROSS_BUF];
     long long bc_o3[CROSS_BUF], bc_o4[CROSS_BUF];
     int nb = 0;
     // apply the buffered crossings: coefficient s w_i/c_s^2 Fn(t), t = o3 / (o3 - o4)
-    // along A -> B (an FP32 quotient refined by one FP64 Newton step, ~1e-14)
+    // along A -> B (Fn linear along the segment).  FP64 for FP64 storage (an FP32
+    // quotient refined by one Newton step); FP32 otherwise, where |o3|, |o3 - o4| <
+    // 2^30 convert exactly and t carries a relative error of a few FP32 ulps.
     auto flush = [&]() {
 #pragma unroll
       for (int q = 0; q < CROSS_BUF; q++) {
@@ -202,16 +278,21 @@ __device__ __forceinline__ void interface_warp(const double *__restrict__ X,
         int xd = x0 + cell % W, yd = y0 + cell / W;
         xd = geo.bc == IILBM_BC_CHANNEL ? xd : wrap(xd, geo.nx);
         yd = geo.bc == IILBM_BC_PERIODIC ? wrap(yd, geo.ny) : yd;
-        const long long den = bc_o3[q] - bc_o4[q];  // nonzero: the link crosses A -> B
-        const double num = (double)bc_o3[q], dd = (double)den;
-        const float rf = 1.0f / (float)dd;
-        double t = (double)((float)num * rf);
-        t = fma(num - t * dd, (double)rf, t);  // one Newton correction with the FP32 reciprocal
-        t = fmin(fmax(t, 0.0), 1.0);
-        const double F = (1.0 - t) * FnA + t * FnB;
-        const double coef = (double)bc_s[q] * 3.0 * wt<double>(i) * F;  // w_i / c_s^2 Fn
-        atomicAdd(&Jf[(long long)(i - 1) * geo.plane + (long long)yd * geo.pitch + xd],
-                  (T)coef);
+        T coef;
+        if (sizeof(T) == 8) {
+          const double num = (double)bc_o3[q], dd = (double)(bc_o3[q] - bc_o4[q]);
+          const float rf = 1.0f / (float)dd;
+          double t = (double)((float)num * rf);
+          t = fma(num - t * dd, (double)rf, t);
+          t = fmin(fmax(t, 0.0), 1.0);
+          coef = T((double)bc_s[q] * 3.0 * wt<double>(i) * ((1.0 - t) * FnA + t * FnB));
+        } else {
+          const float num = (float)(int)bc_o3[q], dd = (float)(int)(bc_o3[q] - bc_o4[q]);
+          const float t = fminf(fmaxf(num / dd, 0.0f), 1.0f);
+          coef = T((float)bc_s[q] * 3.0f * wt<float>(i) *
+                   ((1.0f - t) * (float)FnA + t * (float)FnB));
+        }
+        atomicAdd(&Jf[(long long)(i - 1) * geo.plane + (long long)yd * geo.pitch + xd], coef);
       }
       found += nb;
       nb = 0;
@@ -221,10 +302,10 @@ __device__ __forceinline__ void interface_warp(const double *__restrict__ X,
       const int cell = c / 8;
       const int qx = x0 + cell % W, qy = y0 + cell / W;  // destination node
       const int ex = cx(i), ey = cy(i);
-      const long long Px = (long long)(qx - ex) * Q, Py = (long long)(qy - ey) * Q;
-      const int s1 = orient_seg_node(ax, ay, bx, by, Px, Py);
-      const int s2 = orient_seg_node(ax, ay, bx, by, (long long)qx * Q, (long long)qy * Q);
+      const int s1 = node_sign(qx - ex, qy - ey);
+      const int s2 = node_sign(qx, qy);
       if (s1 == s2) continue;
+      const long long Px = (long long)(qx - ex) * Q, Py = (long long)(qy - ey) * Q;
       long long o3, o4;
       const int s3 = orient_link_pt(Px, Py, ex, ey, ax, ay, o3);
       const int s4 = orient_link_pt(Px, Py, ex, ey, bx, by, o4);
@@ -247,33 +328,8 @@ __device__ __forceinline__ void interface_warp(const double *__restrict__ X,
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) found += __shfl_xor_sync(0xffffffffu, found, o);
   if (lane == 0 && found) atomicAdd(&tb.ctr[1], found);
-  // ---- spread P_k (Eq. 46 / Eq. 17), lanes 0..15 one stencil node each
-  if (lane < 16 && inside) {
-    // the stencil is chosen from the FP64 coordinate, as the interpolation does
-    const int xa = (int)floor(Ax) - 1 + (lane & 3), yb = (int)floor(Ay) - 1 + (lane >> 2);
-    int xi = xa, yi = yb;
-    bool ok = true;
-    if (geo.bc == IILBM_BC_CHANNEL) ok = xi >= 0 && xi < geo.nx;
-    else xi = wrap(xi, geo.nx);
-    if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
-    else ok = ok && yi >= 0 && yi < geo.ny;
-    // node offsets: exact in FP64 for FP64 storage; from the snapped integers otherwise
-    T rx, ry;
-    if (sizeof(T) == 8) {
-      rx = T((double)xa - Ax);
-      ry = T((double)yb - Ay);
-    } else {
-      rx = T((int)((long long)xa * Q - ax)) * T(1.0 / QSCALE);
-      ry = T((int)((long long)yb * Q - ay)) * T(1.0 / QSCALE);
-    }
-    const T w = ok ? phi4t<T>(rx) * phi4t<T>(ry) : T(0);
-    if (w != T(0)) {
-      const long long here = (long long)yi * geo.pitch + xi;
-      atomicAdd(&gf[here], Pkx * w);
-      atomicAdd(&gf[geo.plane + here], Pky * w);
-    }
-  }
-  // ---- flag the tiles of the warp's footprint once: every node written above lies in
+  // ---- flag the tiles of the footprint once: every node written for this segment
+  // (its cut links, and the spread of marker k) lies in
   // [floor(min x) - 2, ceil(max x) + 2] x [floor(min y) - 2, ceil(max y) + 2]
   if (inside) {
     int cols[MAX_TILE_SPAN], rows[MAX_TILE_SPAN];
@@ -287,5 +343,60 @@ __device__ __forceinline__ void interface_warp(const double *__restrict__ X,
   }
 }
 
+// ------------------------------------------------------------- interpolation
+// U_k = sum_x u(x) delta_h(x - X_k) (Eq. 20) from the collision velocity the forced
+// stream-collide left in uf, one thread per marker, on the stencil the marker pass
+// spread to (same floor and weights); the marker moves X += U when it moves.  FP64
+// storage: FP64 throughout.  Otherwise each stencil row is summed in FP32 and the four
+// row sums are accumulated in FP64.
+template <typename T>
+__device__ __forceinline__ void interp_marker(const T *__restrict__ uf, const Geom &geo,
+                                              double *X, const long long *__restrict__ Xq,
+                                              int k, double *U, int moves) {
+  const double x = X[2 * k], y = X[2 * k + 1];
+  const long long qx = Xq[2 * k], qy = Xq[2 * k + 1];
+  double sx = 0.0, sy = 0.0;
+  if (qx != XQ_OUT) {
+    int bx, by;
+    T wx[4], wy[4];
+    stencil_weights<T>(x, qx, bx, wx);
+    stencil_weights<T>(y, qy, by, wy);
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      int yi = by + b;
+      bool oky = true;
+      if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
+      else oky = yi >= 0 && yi < geo.ny;
+      T rx = T(0), ry = T(0);
+#pragma unroll
+      for (int a = 0; a < 4; a++) {
+        int xi = bx + a;
+        bool ok = oky;
+        if (geo.bc == IILBM_BC_CHANNEL) ok = ok && xi >= 0 && xi < geo.nx;
+        else xi = wrap(xi, geo.nx);
+        if (ok) {
+          const long long here = (long long)yi * geo.pitch + xi;
+          if (sizeof(T) == 8) {  // FP64: every weight wx * wy formed, as the definition reads
+            sx += (double)uf[here] * (double)(wx[a] * wy[b]);
+            sy += (double)uf[geo.plane + here] * (double)(wx[a] * wy[b]);
+          } else {
+            rx += uf[here] * wx[a];
+            ry += uf[geo.plane + here] * wx[a];
+          }
+        }
+      }
+      if (sizeof(T) != 8) {
+        sx += (double)rx * (double)wy[b];
+        sy += (double)ry * (double)wy[b];
+      }
+    }
+  }
+  U[2 * k] = sx;
+  U[2 * k + 1] = sy;
+  if (moves) {
+    X[2 * k] = x + sx;
+    X[2 * k + 1] = y + sy;
+  }
+}
 
 }  // namespace iilbm

@@ -13,6 +13,7 @@
 // opp(i) of the upstream node x - e_i and writes f*_i into slot i of the downstream
 // node x + e_i.  Each node only touches slots no other node touches in that step,
 // so one array suffices and every step moves 2 x 9 values per node.
+#include "interface_dev.cuh"
 #include "lattice_dev.cuh"
 
 #include <cmath>
@@ -102,54 +103,25 @@ __device__ inline void node_macros(const S *A, const typename Store<S>::T *Jf,
   uy = double((jy + T(0.5) * gy) * ir);
 }
 
-// Velocity interpolation U_k = sum_x u(x) delta_h(x - X_k) (Eq. 20), 16 threads per
-// marker (one per stencil node), FP64 accumulation; a membrane marker then moves,
-// X_k += U_k.  u is the collision velocity of the step (jump and g/2 included) that the
-// forced stream-collide left in uf for every node of the flagged tiles -- which cover
-// every marker's stencil -- so this runs right after the forced kernel.
+// Velocity interpolation U_k = sum_x u(x) delta_h(x - X_k) (Eq. 20), one thread per
+// marker (interp_marker); a membrane marker then moves, X_k += U_k.  u is the
+// collision velocity of the step (jump and g/2 included) that the forced stream-collide
+// left in uf for every node of the flagged tiles -- which cover every marker's stencil
+// -- so this runs right after the forced kernel.
 // Thread 0 also prepares the other buffer for the next interface phase (its readers
 // are done by now): advance its tag, so its old flags stop matching, and reset its
 // counters.
 template <typename T>
-__global__ void k_interp(const T *__restrict__ uf, const Geom geo, double *X, int n, double *U,
-                         int moves, unsigned *next_tag, int *next_ctr) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid == 0) {
+__global__ void k_interp(const T *__restrict__ uf, const Geom geo, double *X,
+                         const long long *__restrict__ Xq, int n, double *U, int moves,
+                         unsigned *next_tag, int *next_ctr) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) {
     *next_tag += 1u;
     next_ctr[0] = 0;
     next_ctr[1] = 0;
   }
-  const int k = tid >> 4, l = tid & 15;
-  double sx = 0.0, sy = 0.0;
-  if (k < n) {
-    const double Xk = X[2 * k], Yk = X[2 * k + 1];
-    const int xa = (int)floor(Xk) - 1 + (l & 3), yb = (int)floor(Yk) - 1 + (l >> 2);
-    int xi = xa, yi = yb;
-    bool ok = true;
-    if (geo.bc == IILBM_BC_CHANNEL) ok = xi >= 0 && xi < geo.nx;
-    else xi = wrap(xi, geo.nx);
-    if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
-    else ok = ok && yi >= 0 && yi < geo.ny;
-    if (ok) {
-      const long long here = (long long)yi * geo.pitch + xi;
-      const double w = (double)(phi4<T>(T((double)xa - Xk)) * phi4<T>(T((double)yb - Yk)));
-      sx = (double)uf[here] * w;
-      sy = (double)uf[geo.plane + here] * w;
-    }
-  }
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1) {
-    sx += __shfl_xor_sync(0xffffffffu, sx, o, 16);
-    sy += __shfl_xor_sync(0xffffffffu, sy, o, 16);
-  }
-  if (k < n && l == 0) {
-    U[2 * k] = sx;
-    U[2 * k + 1] = sy;
-    if (moves) {
-      X[2 * k] += sx;
-      X[2 * k + 1] += sy;
-    }
-  }
+  if (k < n) interp_marker<T>(uf, geo, X, Xq, k, U, moves);
 }
 
 template <typename S>
@@ -294,16 +266,14 @@ int launch_stream_collide(iilbm_lattice *h, cudaStream_t forced_stream) {
 
 int launch_interp(iilbm_lattice *h, cudaStream_t s) {
   if (h->nm == 0) return IILBM_OK;
-  const int threads = 16 * h->nm;
+  const int blocks = (h->nm + 127) / 128;
   const int nb = (int)((h->step + 1) & 1);  // the buffer of the next time level
   if (h->cfg.storage == IILBM_F64)
-    k_interp<double><<<(threads + 255) / 256, 256, 0, s>>>((const double *)h->uf, h->geom, h->X,
-                                                          h->nm, h->U, h->ip.moves, h->tagb[nb],
-                                                          h->tile_count[nb]);
+    k_interp<double><<<blocks, 128, 0, s>>>((const double *)h->uf, h->geom, h->X, h->Xq, h->nm,
+                                            h->U, h->ip.moves, h->tagb[nb], h->tile_count[nb]);
   else
-    k_interp<float><<<(threads + 255) / 256, 256, 0, s>>>((const float *)h->uf, h->geom, h->X,
-                                                         h->nm, h->U, h->ip.moves, h->tagb[nb],
-                                                         h->tile_count[nb]);
+    k_interp<float><<<blocks, 128, 0, s>>>((const float *)h->uf, h->geom, h->X, h->Xq, h->nm,
+                                           h->U, h->ip.moves, h->tagb[nb], h->tile_count[nb]);
   return last_error();
 }
 

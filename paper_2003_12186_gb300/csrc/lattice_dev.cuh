@@ -435,17 +435,6 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
 
 constexpr int VEC_ROWS = TILE_Y;  // warps (rows) per block of the vectorised kernels
 
-// ------------------------------------------------------ Peskin delta (Eq. 17)
-// Four-point kernel phi(r) in the arithmetic type T (GB300's FP64 rate is a small
-// fraction of its FP32 rate, so FP64 is kept to positions and accumulations).
-template <typename T>
-__device__ inline T phi4(T r) {
-  const T a = fabs(r);
-  if (a < T(1)) return T(0.125) * (T(3) - T(2) * a + sqrt(T(1) + T(4) * a - T(4) * a * a));
-  if (a < T(2)) return T(0.125) * (T(5) - T(2) * a - sqrt(T(-7) + T(12) * a - T(4) * a * a));
-  return T(0);
-}
-
 // Inflow / outflow of one channel row on the streamed state (see lattice.cu).
 template <typename S>
 __device__ __forceinline__ void channel_bc_row(S *A, const Geom &geo,

@@ -198,9 +198,13 @@ int iilbm_create_batch(iilbm_batch_t *out, const iilbm_t *lattices, int32_t coun
 int iilbm_destroy_batch(iilbm_batch_t b);
 /* Advance every lattice of the batch by n time steps (asynchronous). */
 int iilbm_batch_step(iilbm_batch_t b, int32_t n);
-/* Stream-collide variant: 0 vectorised, one block per tile; 1 / 2 vectorised on a
- * persistent grid of 2 / 4 blocks per SM; 3 one node per thread, one block per tile
- * (four sub-blocks); 4 one node per thread on a persistent grid of 2 blocks per SM. */
+/* Stream-collide variant of the lean (unforced) tiles: nodes per thread NPT, resident
+ * blocks per SM that the registers are budgeted for, and grid (one block per work item
+ * of 4 tiles of 128 x 8 nodes, or a persistent grid striding over the items):
+ *   0 / 1  NPT 4, 3 blocks, per item / persistent     2 / 3  NPT 4, 2 blocks
+ *   4 / 5  NPT 2, 3 blocks                            6 / 7  NPT 2, 2 blocks
+ *   8 / 9  NPT 1, 3 blocks
+ * Results agree to rounding (the arithmetic is the same; contraction may differ). */
 int iilbm_batch_set_variant(iilbm_batch_t b, int32_t variant);
 /* Autotuner: time every variant for `steps` (rounded up to whole graph replays) real
  * steps of the batch and keep the fastest; the lattices advance by those steps.

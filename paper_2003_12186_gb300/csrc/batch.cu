@@ -47,17 +47,28 @@ struct SimDev {
   double u_max;
 };
 
-// Stream-collide variants the autotuner chooses from.
-enum { BV_VEC_ITEM = 0, BV_VEC_PERSIST2, BV_VEC_PERSIST4, BV_SCALAR_ITEM, BV_SCALAR_PERSIST2,
-       BV_COUNT };
+// Stream-collide variants the autotuner chooses from: nodes per thread (4, 2 or 1),
+// resident blocks per SM the registers are budgeted for (3: at most 80 registers, with
+// some spilling at 2 and 4 nodes per thread; 2: no spilling), and grid shape (one block
+// per work item, or a persistent grid of resident blocks x SMs striding over the items).
+struct BatchVariant {
+  int npt, minb;
+  bool persistent;
+};
+constexpr BatchVariant BATCH_VARIANTS[] = {
+    {4, 3, false}, {4, 3, true}, {4, 2, false}, {4, 2, true}, {2, 3, false},
+    {2, 3, true},  {2, 2, false}, {2, 2, true}, {1, 3, false}, {1, 3, true}};
+constexpr int BV_COUNT = sizeof(BATCH_VARIANTS) / sizeof(BATCH_VARIANTS[0]);
 
 // ----------------------------------------------------------------- kernels
 // A work item is up to LEAN_GROUP consecutive tiles of one lattice: the lattice's
 // descriptor, tag and the group's flags are loaded once, before its first tile.
+// NPT = nodes per thread: 4 or 2 (vectorised, 32 NPT nodes per warp row), or 1 (one
+// node per thread, 32-node sub-blocks); MINB resident blocks per SM.
 constexpr int LEAN_GROUP = 4;
 
-template <typename S, int COLL, bool ODD, int BC, bool VEC>
-__global__ void __launch_bounds__(256, 3)
+template <typename S, int COLL, bool ODD, int BC, int NPT, int MINB>
+__global__ void __launch_bounds__(256, MINB)
     k_batch_lean(const SimDev *__restrict__ sims, const int2 *__restrict__ items, int nitems) {
   constexpr int b = ODD ? 1 : 0;  // buffer of the state = its parity
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -74,13 +85,11 @@ __global__ void __launch_bounds__(256, 3)
     for (int q = 0; q < nt; q++) {
       if (!(todo >> q & 1u)) continue;  // uniform per block: a forced tile
       const int tile = w.y + q;
-      const Geom &geo = sd.geo;
-      const int tx = (tile % geo.ntx) * TILE_X, ty = (tile / geo.ntx) * TILE_Y;
-      if (VEC) {
-        constexpr int W = 32 * Vec<S>::V;
-        for (int sub = 0; sub < TILE_X; sub += W)
-          sc_vec_block<S, COLL, ODD, BC, false>((S *)sd.A, nullptr, nullptr, nullptr, sd.geo,
-                                                sd.p, sd.status, tx + sub, ty);
+      const int tx = (tile % sd.geo.ntx) * TILE_X, ty = (tile / sd.geo.ntx) * TILE_Y;
+      if (NPT > 1) {
+        for (int sub = 0; sub < TILE_X; sub += 32 * NPT)
+          sc_vec_block<S, COLL, ODD, BC, false, NPT>((S *)sd.A, nullptr, nullptr, nullptr,
+                                                     sd.geo, sd.p, sd.status, tx + sub, ty);
       } else {
         for (int sub = 0; sub < TILE_X; sub += 32)
           sc_scalar_block<S, COLL, ODD, BC, false>((S *)sd.A, nullptr, nullptr, nullptr, sd.geo,
@@ -224,19 +233,22 @@ int with_storage(int storage, F &&f) {
   return IILBM_ERR_INVALID_ARG;
 }
 
+template <typename S, int COLL, bool ODD, int BC, int NPT, int MINB>
+void lean_launch_v(iilbm_batch *B, bool persistent) {
+  const int grid = persistent ? std::min(B->nitems, MINB * B->sm_count) : B->nitems;
+  const dim3 block = NPT > 1 ? dim3(256) : dim3(32, TILE_Y);
+  k_batch_lean<S, COLL, ODD, BC, NPT, MINB><<<grid, block, 0, B->stream>>>(B->d_sims, B->d_items,
+                                                                            B->nitems);
+}
+
 template <typename S, int COLL, bool ODD, int BC>
 void lean_launch(iilbm_batch *B) {
-  const int pers = B->variant == BV_VEC_PERSIST2 || B->variant == BV_SCALAR_PERSIST2 ? 2
-                   : B->variant == BV_VEC_PERSIST4                                   ? 4
-                                                                                     : 0;
-  const int grid = pers ? std::min(B->nitems, pers * B->sm_count) : B->nitems;
-  const bool vec = B->variant <= BV_VEC_PERSIST4;
-  if (vec)
-    k_batch_lean<S, COLL, ODD, BC, true><<<grid, 256, 0, B->stream>>>(B->d_sims, B->d_items,
-                                                                     B->nitems);
-  else
-    k_batch_lean<S, COLL, ODD, BC, false><<<grid, dim3(32, TILE_Y), 0, B->stream>>>(
-        B->d_sims, B->d_items, B->nitems);
+  const BatchVariant v = BATCH_VARIANTS[B->variant];
+  if (v.npt == 4 && v.minb == 3) lean_launch_v<S, COLL, ODD, BC, 4, 3>(B, v.persistent);
+  else if (v.npt == 4) lean_launch_v<S, COLL, ODD, BC, 4, 2>(B, v.persistent);
+  else if (v.npt == 2 && v.minb == 3) lean_launch_v<S, COLL, ODD, BC, 2, 3>(B, v.persistent);
+  else if (v.npt == 2) lean_launch_v<S, COLL, ODD, BC, 2, 2>(B, v.persistent);
+  else lean_launch_v<S, COLL, ODD, BC, 1, 3>(B, v.persistent);
 }
 
 template <typename S, int COLL, bool ODD, int BC>
@@ -479,7 +491,7 @@ int iilbm_create_batch(iilbm_batch_t *out, const iilbm_t *lattices, int32_t coun
   B->collision = h0->cfg.collision;
   B->bc = h0->cfg.bc;
   B->nsims = count;
-  B->variant = BV_VEC_ITEM;
+  B->variant = 0;
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, h0->device) != cudaSuccess) {
     delete B;

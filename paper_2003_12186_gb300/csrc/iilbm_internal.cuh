@@ -100,6 +100,7 @@ struct Geom {
 };
 
 __host__ __device__ inline int wrap(int v, int n) {
+  if ((unsigned)v < (unsigned)n) return v;  // the common case: no division
   v = v % n;
   return v < 0 ? v + n : v;
 }

@@ -262,9 +262,11 @@ __device__ __forceinline__ void interface_segment(const long long *__restrict__ 
       }
       return orient_seg_node(ax, ay, bx, by, (long long)qx * Q, (long long)qy * Q);
     };
-    int bc_idx[CROSS_BUF], bc_s[CROSS_BUF];
+    // buffered crossings: destination (wrapped), direction, sign, link-side orientations
+    int bc_x[CROSS_BUF], bc_y[CROSS_BUF], bc_i[CROSS_BUF], bc_s[CROSS_BUF];
     long long bc_o3[CROSS_BUF], bc_o4[CROSS_BUF];
     int nb = 0;
+    const float fA = (float)FnA, fB = (float)FnB;  // FP32 path: converted once per warp
     // apply the buffered crossings: coefficient s w_i/c_s^2 Fn(t), t = o3 / (o3 - o4)
     // along A -> B (Fn linear along the segment).  FP64 for FP64 storage (an FP32
     // quotient refined by one Newton step); FP32 otherwise, where |o3|, |o3 - o4| <
@@ -273,11 +275,7 @@ __device__ __forceinline__ void interface_segment(const long long *__restrict__ 
 #pragma unroll
       for (int q = 0; q < CROSS_BUF; q++) {
         if (q >= nb) break;
-        const int c = bc_idx[q];
-        const int i = 1 + c % 8, cell = c / 8;
-        int xd = x0 + cell % W, yd = y0 + cell / W;
-        xd = geo.bc == IILBM_BC_CHANNEL ? xd : wrap(xd, geo.nx);
-        yd = geo.bc == IILBM_BC_PERIODIC ? wrap(yd, geo.ny) : yd;
+        const int i = bc_i[q];
         T coef;
         if (sizeof(T) == 8) {
           const double num = (double)bc_o3[q], dd = (double)(bc_o3[q] - bc_o4[q]);
@@ -289,18 +287,22 @@ __device__ __forceinline__ void interface_segment(const long long *__restrict__ 
         } else {
           const float num = (float)(int)bc_o3[q], dd = (float)(int)(bc_o3[q] - bc_o4[q]);
           const float t = fminf(fmaxf(num / dd, 0.0f), 1.0f);
-          coef = T((float)bc_s[q] * 3.0f * wt<float>(i) *
-                   ((1.0f - t) * (float)FnA + t * (float)FnB));
+          coef = T((float)bc_s[q] * 3.0f * wt<float>(i) * ((1.0f - t) * fA + t * fB));
         }
-        atomicAdd(&Jf[(long long)(i - 1) * geo.plane + (long long)yd * geo.pitch + xd], coef);
+        atomicAdd(&Jf[(long long)(i - 1) * geo.plane + (long long)bc_y[q] * geo.pitch + bc_x[q]],
+                  coef);
       }
       found += nb;
       nb = 0;
     };
+    // cell -> (column, row) of the W-wide box by an FP32 quotient: (cell + 1/2) / W is
+    // at least 1/(2W) away from an integer, far above its rounding error (W <= 19)
+    const float invW = 1.0f / (float)W;
     for (int c = lane; c < ncand; c += 32) {
-      const int i = 1 + c % 8;
-      const int cell = c / 8;
-      const int qx = x0 + cell % W, qy = y0 + cell / W;  // destination node
+      const int i = 1 + (c & 7);
+      const int cell = c >> 3;
+      const int gy = (int)(((float)cell + 0.5f) * invW), gx = cell - gy * W;
+      const int qx = x0 + gx, qy = y0 + gy;  // destination node
       const int ex = cx(i), ey = cy(i);
       const int s1 = node_sign(qx - ex, qy - ey);
       const int s2 = node_sign(qx, qy);
@@ -317,7 +319,9 @@ __device__ __forceinline__ void interface_segment(const long long *__restrict__ 
       if (geo.bc != IILBM_BC_PERIODIC && (qy < 0 || qy >= geo.ny || ys < 0 || ys >= geo.ny))
         continue;
       if (nb == CROSS_BUF) flush();
-      bc_idx[nb] = c;
+      bc_x[nb] = geo.bc == IILBM_BC_CHANNEL ? qx : wrap(qx, geo.nx);
+      bc_y[nb] = geo.bc == IILBM_BC_PERIODIC ? wrap(qy, geo.ny) : qy;
+      bc_i[nb] = i;
       bc_s[nb] = s1;
       bc_o3[nb] = o3;
       bc_o4[nb] = o4;

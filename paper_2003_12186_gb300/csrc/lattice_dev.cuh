@@ -38,8 +38,10 @@ CollP<T> make_collp(const iilbm_config &c) {
 //   rho = rho0 + drho,  rho u = j + g/2  (Eqs. 11, 24)
 //   feq_i - w_i rho0 = w_i [drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u^2)]  (Eq. 23)
 //   Guo source  Gt_i = w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]  (Eqs. 21-22)
-template <typename T, int COLL>
-__device__ __forceinline__ T collide(T f[9], T gx, T gy, const CollP<T> &p, T &ux_out,
+// PP is CollP<T>, or a volatile view of one in shared memory (the batched kernels:
+// every rate is then re-read where it is used instead of held in a register).
+template <typename T, int COLL, typename PP = CollP<T>>
+__device__ __forceinline__ T collide(T f[9], T gx, T gy, const PP &p, T &ux_out,
                                      T &uy_out) {
   const T drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
   const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
@@ -127,92 +129,58 @@ __device__ __forceinline__ T collide(T f[9], T gx, T gy, const CollP<T> &p, T &u
 // that crosses into the neighbouring lane travels by warp shuffle; lanes 0 and 31
 // (and the last active lane of a row) fetch / write that element with a scalar
 // access instead, wrapping around the periodic row.  Requires nx % V == 0.
-template <typename S> struct Vec;
-template <> struct Vec<float> {
-  static constexpr int V = 4;
-  __device__ static void ld(const float *p, float *o, float is) {
-    const float4 t = *reinterpret_cast<const float4 *>(p);
-    o[0] = t.x * is; o[1] = t.y * is; o[2] = t.z * is; o[3] = t.w * is;
-  }
-  __device__ static void st(float *p, const float *v, float sc) {
-    *reinterpret_cast<float4 *>(p) = make_float4(v[0] * sc, v[1] * sc, v[2] * sc, v[3] * sc);
-  }
-};
-template <> struct Vec<double> {
-  static constexpr int V = 2;
-  __device__ static void ld(const double *p, double *o, double is) {
-    const double2 t = *reinterpret_cast<const double2 *>(p);
-    o[0] = t.x * is; o[1] = t.y * is;
-  }
-  __device__ static void st(double *p, const double *v, double sc) {
-    *reinterpret_cast<double2 *>(p) = make_double2(v[0] * sc, v[1] * sc);
-  }
-};
-template <> struct Vec<__half> {
-  static constexpr int V = 4;
-  __device__ static void ld(const __half *p, float *o, float is) {
-    const uint2 t = *reinterpret_cast<const uint2 *>(p);
-    const __half2 a = *reinterpret_cast<const __half2 *>(&t.x);
-    const __half2 b = *reinterpret_cast<const __half2 *>(&t.y);
-    const float2 fa = __half22float2(a), fb = __half22float2(b);
-    o[0] = fa.x * is; o[1] = fa.y * is; o[2] = fb.x * is; o[3] = fb.y * is;
-  }
-  __device__ static void st(__half *p, const float *v, float sc) {
-    const __half2 a = __floats2half2_rn(v[0] * sc, v[1] * sc);
-    const __half2 b = __floats2half2_rn(v[2] * sc, v[3] * sc);
-    uint2 t;
-    t.x = *reinterpret_cast<const unsigned *>(&a);
-    t.y = *reinterpret_cast<const unsigned *>(&b);
-    *reinterpret_cast<uint2 *>(p) = t;
-  }
-};
-template <> struct Vec<__nv_bfloat16> {
-  static constexpr int V = 4;
-  __device__ static void ld(const __nv_bfloat16 *p, float *o, float is) {
-    const uint2 t = *reinterpret_cast<const uint2 *>(p);
-    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&t.x);
-    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&t.y);
-    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-    o[0] = fa.x * is; o[1] = fa.y * is; o[2] = fb.x * is; o[3] = fb.y * is;
-  }
-  __device__ static void st(__nv_bfloat16 *p, const float *v, float sc) {
-    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0] * sc, v[1] * sc);
-    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2] * sc, v[3] * sc);
-    uint2 t;
-    t.x = *reinterpret_cast<const unsigned *>(&a);
-    t.y = *reinterpret_cast<const unsigned *>(&b);
-    *reinterpret_cast<uint2 *>(p) = t;
-  }
+template <typename S> struct Vec { static constexpr int V = sizeof(S) == 8 ? 2 : 4; };
+
+// V consecutive stored values moved with one aligned access (V * sizeof(S) bytes) and
+// converted to / from the arithmetic type with the storage scale.  The batched
+// kernels also run V = 2: half the registers per thread, and a 64-node row fills a
+// warp.
+template <typename S, int V>
+struct alignas(sizeof(S) * V) Pack {
+  S v[V];
 };
 
-// V consecutive arithmetic values (jump / force fields): float4 or double2.
+template <typename S, int V>
+__device__ inline void vld(const S *p, typename Store<S>::T *o, typename Store<S>::T is) {
+  const Pack<S, V> t = *reinterpret_cast<const Pack<S, V> *>(p);
+#pragma unroll
+  for (int j = 0; j < V; j++) o[j] = Store<S>::ld(t.v[j]) * is;
+}
+
+template <typename S, int V>
+__device__ inline void vst(S *p, const typename Store<S>::T *v, typename Store<S>::T sc) {
+  Pack<S, V> t;
+#pragma unroll
+  for (int j = 0; j < V; j++) t.v[j] = Store<S>::st(v[j] * sc);
+  *reinterpret_cast<Pack<S, V> *>(p) = t;
+}
+
+// V consecutive arithmetic values (jump / force fields), one aligned access.
 template <typename T, int V>
 __device__ inline void stT(T *p, const T *v) {
-  if constexpr (sizeof(T) == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  else *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+  Pack<T, V> t;
+#pragma unroll
+  for (int j = 0; j < V; j++) t.v[j] = v[j];
+  *reinterpret_cast<Pack<T, V> *>(p) = t;
 }
 template <typename T, int V>
 __device__ inline void ldT(const T *p, T *o) {
-  if constexpr (sizeof(T) == 4) {
-    const float4 t = *reinterpret_cast<const float4 *>(p);
-    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
-  } else {
-    const double2 t = *reinterpret_cast<const double2 *>(p);
-    o[0] = t.x; o[1] = t.y;
-  }
+  const Pack<T, V> t = *reinterpret_cast<const Pack<T, V> *>(p);
+#pragma unroll
+  for (int j = 0; j < V; j++) o[j] = t.v[j];
 }
 
 
 // One node per thread on a 32 x TILE_Y sub-block whose first node is (xb, yb).  BC is
 // IILBM_BC_PERIODIC, IILBM_BC_WALLS_Y (periodic x, halfway bounce-back in y) or
 // IILBM_BC_CHANNEL (walls in y, ghost columns in x filled by the channel boundary).
-template <typename S, int COLL, bool ODD, int BC, bool FORCED>
+template <typename S, int COLL, bool ODD, int BC, bool FORCED, typename GG = Geom,
+          typename PP = CollP<typename Store<S>::T>>
 __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
                                                 typename Store<S>::T *__restrict__ Jf,
                                                 typename Store<S>::T *__restrict__ gf,
                                                 typename Store<S>::T *__restrict__ uf,
-                                                const Geom &geo,
-                                                const CollP<typename Store<S>::T> &p, int *status,
+                                                const GG &geo, const PP &p, int *status,
                                                 int xb, int yb) {
   using T = typename Store<S>::T;
   const int x = xb + threadIdx.x, y = yb + threadIdx.y;
@@ -281,16 +249,15 @@ __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
 // neighbouring lane travels by warp shuffle; lane 0, lane 31 and the last active lane
 // of a row fetch / write that element with a scalar access instead, wrapping around
 // the periodic row.  Requires nx % V == 0.  Every lane of the warp must call this.
-template <typename S, int COLL, bool ODD, int BC, bool FORCED>
+template <typename S, int COLL, bool ODD, int BC, bool FORCED, int V = Vec<S>::V,
+          typename GG = Geom, typename PP = CollP<typename Store<S>::T>>
 __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
                                              typename Store<S>::T *__restrict__ Jf,
                                              typename Store<S>::T *__restrict__ gf,
                                              typename Store<S>::T *__restrict__ uf,
-                                             const Geom &geo,
-                                             const CollP<typename Store<S>::T> &p, int *status,
+                                             const GG &geo, const PP &p, int *status,
                                              int xb, int yb) {
   using T = typename Store<S>::T;
-  constexpr int V = Vec<S>::V;
   const int lane = threadIdx.x & 31;
   const int y = yb + (threadIdx.x >> 5);
   if (y >= geo.ny) return;  // uniform per warp
@@ -321,13 +288,13 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
     for (int j = 0; j < V; j++) f[i][j] = T(0);
     const bool from_wall = ODD && ((cy(i) > 0 && wall_m) || (cy(i) < 0 && wall_p));
     if (!ODD || from_wall) {
-      if (active) Vec<S>::ld(A + i * P + here, f[i], p.inv_scale);
+      if (active) vld<S, V>(A + i * P + here, f[i], p.inv_scale);
     } else {
       const long long base = opp(i) * P + row[1 - cy(i)];
       T c[V];
 #pragma unroll
       for (int j = 0; j < V; j++) c[j] = T(0);
-      if (active) Vec<S>::ld(A + base + x0, c, p.inv_scale);
+      if (active) vld<S, V>(A + base + x0, c, p.inv_scale);
       if (cx(i) == 0) {
 #pragma unroll
         for (int j = 0; j < V; j++) f[i][j] = c[j];
@@ -393,11 +360,11 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
   for (int i = 0; i < 9; i++) {
     const bool to_wall = ODD && ((cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m));
     if (!ODD || to_wall) {
-      if (active) Vec<S>::st(A + opp(i) * P + here, f[i], p.scale);
+      if (active) vst<S, V>(A + opp(i) * P + here, f[i], p.scale);
     } else {
       const long long base = i * P + row[1 + cy(i)];
       if (cx(i) == 0) {
-        if (active) Vec<S>::st(A + base + x0, f[i], p.scale);
+        if (active) vst<S, V>(A + base + x0, f[i], p.scale);
       } else if (cx(i) > 0) {  // destination x + 1
         const T in = __shfl_up_sync(0xffffffffu, f[i][V - 1], 1);
         if (active) {
@@ -406,7 +373,7 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
             v[0] = in;
 #pragma unroll
             for (int j = 1; j < V; j++) v[j] = f[i][j - 1];
-            Vec<S>::st(A + base + x0, v, p.scale);
+            vst<S, V>(A + base + x0, v, p.scale);
           } else {
 #pragma unroll
             for (int j = 0; j < V - 1; j++) A[base + x0 + 1 + j] = Store<S>::st(f[i][j] * p.scale);
@@ -421,7 +388,7 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
 #pragma unroll
             for (int j = 0; j < V - 1; j++) v[j] = f[i][j + 1];
             v[V - 1] = in;
-            Vec<S>::st(A + base + x0, v, p.scale);
+            vst<S, V>(A + base + x0, v, p.scale);
           } else {
 #pragma unroll
             for (int j = 1; j < V; j++) A[base + x0 + j - 1] = Store<S>::st(f[i][j] * p.scale);

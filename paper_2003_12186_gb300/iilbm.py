@@ -87,8 +87,8 @@ SIGNATURES = {
 }
 
 # stream-collide variants of a batch (iilbm_batch_set_variant)
-BATCH_VARIANTS = ("vec-per-tile", "vec-persistent-2", "vec-persistent-4", "scalar-per-tile",
-                  "scalar-persistent-2")
+BATCH_VARIANTS = tuple(f"npt{n}-b{b}-{g}" for n, b in ((4, 3), (4, 2), (2, 3), (2, 2), (1, 3))
+                       for g in ("per-item", "persistent"))
 
 
 def library_path() -> str:

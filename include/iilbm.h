@@ -138,6 +138,22 @@ int iilbm_get_mdf_stats(iilbm_t h, int32_t *iters, double *residual);
  * iteration (that of the current state unless a read-out has already run it). */
 int iilbm_set_warm_start(iilbm_t h, const double *G0);
 
+/* Direct forcing: where the force iteration of each step starts.
+ *   IILBM_WS_GIVEN     the G^(0) of iilbm_set_warm_start (zero unless set: the plain
+ *                      iteration);
+ *   IILBM_WS_PREVIOUS  the force the iteration reached in the previous step (zero at
+ *                      the first step after iilbm_set_interface).
+ * The stopping rule (mdf_iters, mdf_tol) is the same in every mode.  INVALID_ARG for an
+ * unknown mode or a batched lattice. */
+enum { IILBM_WS_GIVEN = 0, IILBM_WS_PREVIOUS = 1 };
+int iilbm_set_warm_start_mode(iilbm_t h, int32_t mode);
+
+/* Direct forcing: U*_k [n][2], the velocity interpolated at the markers from the state
+ * without the body's force (u* of Eq. 18 before the first update), as recorded by the
+ * most recent force iteration.  Host or device pointer; synchronises.  INVALID_ARG
+ * unless the interface is a directly forced body. */
+int iilbm_get_unforced_velocity(iilbm_t h, double *Ustar);
+
 /* Force of the fluid on the body, F = -sum_k G_k dX (Eq. 25 without the internal
  * inertia term; the body is fixed), from the most recent Lagrangian force.  Drag and
  * lift coefficients follow as 2 F / (rho U^2 D) (Eqs. 52-53).  Synchronises. */

@@ -90,6 +90,9 @@ typedef struct {
   double *U;       /* [n][2] interpolated marker velocity */
   int mdf_last_iters;
   double mdf_last_res;
+  double *Ustar;   /* [n][2] U* = interp(u*): marker velocity without the body's force */
+  int ws_previous; /* direct forcing starts from the force of the previous call, */
+  double *Gprev;   /* kept here, instead of from Gp */
   int ncut;        /* cut-link crossings of the most recent prepare */
   long step;
 } orc_state;
@@ -532,7 +535,7 @@ orc_state *orc_create(const orc_cfg *cfg) {
 static void free_iface(orc_state *S) {
   if (!S->has_iface) return;
   free(S->I.X); free(S->I.Gp); free(S->I.UD);
-  free(S->G); free(S->Fn); free(S->Gpar); free(S->U);
+  free(S->G); free(S->Fn); free(S->Gpar); free(S->U); free(S->Ustar); free(S->Gprev);
   S->has_iface = 0;
 }
 
@@ -580,6 +583,8 @@ int orc_set_interface(orc_state *S, const double *X, int n, int model, int moves
   S->Fn = (double *)calloc(n, sizeof(double));
   S->Gpar = (double *)calloc(2 * n, sizeof(double));
   S->U = (double *)calloc(2 * n, sizeof(double));
+  S->Ustar = (double *)calloc(2 * n, sizeof(double));
+  S->Gprev = (double *)calloc(2 * n, sizeof(double));
   S->has_iface = 1;
   return 0;
 }
@@ -588,7 +593,9 @@ int orc_set_interface(orc_state *S, const double *X, int n, int model, int moves
  * Guo half-force velocity).  u* = (sum e df + body/2)/rho is the velocity without
  * immersed-boundary forcing; each pass interpolates u* + spread(G dX)/(2 rho),
  * adds eta (U^D - U) to G, and stops after mdf_iters passes or when
- * max_k |U^D - U_k| < mdf_tol.  The pass count and final residual are kept. */
+ * max_k |U^D - U_k| < mdf_tol.  The pass count and final residual are kept, and
+ * so is U* = interp(u*) (the pass with G = 0).  The iteration starts from Gp, or
+ * with ws_previous from the force the previous call ended with. */
 static void direct_forcing(orc_state *S, const double *dfs) {
   const orc_cfg *c = &S->c;
   orc_iface *I = &S->I;
@@ -603,7 +610,9 @@ static void direct_forcing(orc_state *S, const double *dfs) {
     for (int i = 0; i < 9; i++) dfc[i] = dfs[i * N + p];
     orc_cell_macros(dfc, c->rho0, c->body_x, c->body_y, &r[p], &us_x[p], &us_y[p]);
   }
-  for (int k = 0; k < 2 * n; k++) S->G[k] = I->Gp[k]; /* warm start (0 = plain) */
+  orc_interp(c, I->X, n, us_x, us_y, S->Ustar);
+  const double *G0 = S->ws_previous ? S->Gprev : I->Gp;
+  for (int k = 0; k < 2 * n; k++) S->G[k] = G0[k]; /* warm start (0 = plain) */
   int it = 0;
   double res = 0;
   for (it = 0; it < I->mdf_iters; it++) {
@@ -622,6 +631,7 @@ static void direct_forcing(orc_state *S, const double *dfs) {
   }
   S->mdf_last_iters = it;
   S->mdf_last_res = res;
+  memcpy(S->Gprev, S->G, 2 * n * sizeof(double));
   free(us_x); free(us_y); free(r); free(gx); free(gy); free(vx); free(vy); free(P);
 }
 
@@ -725,6 +735,10 @@ void orc_get_markers(const orc_state *S, double *X, double *G, double *U, double
 }
 
 int orc_mdf_iters(const orc_state *S) { return S->mdf_last_iters; }
+void orc_set_ws_previous(orc_state *S, int on) { S->ws_previous = on; }
+void orc_get_ustar(const orc_state *S, double *out) {
+  if (S->has_iface) memcpy(out, S->Ustar, 2 * S->I.n * sizeof(double));
+}
 double orc_mdf_residual(const orc_state *S) { return S->mdf_last_res; }
 
 /* Enclosed area of the marker polygon (shoelace formula); the area-loss metrics

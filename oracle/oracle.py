@@ -76,6 +76,8 @@ def lib():
             L.orc_get_step_macros.argtypes = [C.c_void_p, _D, _D, _D]
             L.orc_get_markers.argtypes = [C.c_void_p, _D, _D, _D, _D]
             L.orc_mdf_iters.argtypes = [C.c_void_p]
+            L.orc_set_ws_previous.argtypes = [C.c_void_p, C.c_int]
+            L.orc_get_ustar.argtypes = [C.c_void_p, _D]
             L.orc_mdf_residual.argtypes = [C.c_void_p]
             L.orc_mdf_residual.restype = C.c_double
             L.orc_polygon_area.argtypes = [_D, C.c_int]
@@ -309,6 +311,16 @@ class Oracle:
         X, G, U, Fn = np.zeros((n, 2)), np.zeros((n, 2)), np.zeros((n, 2)), np.zeros(n)
         lib().orc_get_markers(self._h, _p(X), _p(G), _p(U), _p(Fn))
         return dict(X=X, G=G, U=U, Fn=Fn)
+
+    def set_ws_previous(self, on=True):
+        """Direct forcing starts from the force the previous iteration ended with."""
+        lib().orc_set_ws_previous(self._h, int(on))
+
+    def unforced_velocity(self):
+        """U*_k = interp(u*) of the most recent force iteration."""
+        out = np.zeros((self.n_markers, 2))
+        lib().orc_get_ustar(self._h, _p(out))
+        return out
 
     def mdf_stats(self):
         return lib().orc_mdf_iters(self._h), lib().orc_mdf_residual(self._h)

@@ -51,7 +51,7 @@ int read_status(iilbm_lattice *h) {
 }
 
 void free_interface(iilbm_lattice *h) {
-  double **bufs[] = {&h->X, &h->aux, &h->G, &h->Fn, &h->U, &h->nrm, &h->G0, &h->Gdf};
+  double **bufs[] = {&h->X, &h->aux, &h->G, &h->Fn, &h->U, &h->nrm, &h->G0, &h->Gdf, &h->Ustar};
   for (double **b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
@@ -266,7 +266,7 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
   const size_t b2 = 2 * (size_t)n * sizeof(double);
   bool ok = cudaMalloc(&h->X, b2) == cudaSuccess && cudaMalloc(&h->aux, b2) == cudaSuccess &&
             cudaMalloc(&h->G, b2) == cudaSuccess && cudaMalloc(&h->G0, b2) == cudaSuccess &&
-            cudaMalloc(&h->Gdf, b2) == cudaSuccess &&
+            cudaMalloc(&h->Gdf, b2) == cudaSuccess && cudaMalloc(&h->Ustar, b2) == cudaSuccess &&
             cudaMalloc(&h->Fn, (size_t)n * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&h->Xq, b2) == cudaSuccess && cudaMalloc(&h->U, b2) == cudaSuccess &&
             cudaMalloc(&h->nrm, b2) == cudaSuccess;
@@ -287,6 +287,7 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
   CK(cudaMemsetAsync(h->G, 0, b2, h->stream));
   CK(cudaMemsetAsync(h->G0, 0, b2, h->stream));
   CK(cudaMemsetAsync(h->Gdf, 0, b2, h->stream));
+  CK(cudaMemsetAsync(h->Ustar, 0, b2, h->stream));
   CK(cudaMemsetAsync(h->Fn, 0, (size_t)n * sizeof(double), h->stream));
   CK(cudaStreamSynchronize(h->stream));
   // host-side validation of the polygon (the kernels re-check every step)
@@ -627,6 +628,21 @@ int iilbm_set_warm_start(iilbm_t h, const double *G0) {
   // already run it (re-running the interface phase would add the jump a second time)
   CK(cudaStreamSynchronize(h->stream));
   return IILBM_OK;
+}
+
+int iilbm_set_warm_start_mode(iilbm_t h, int32_t mode) {
+  if (!h || mode < IILBM_WS_GIVEN || mode > IILBM_WS_PREVIOUS) return IILBM_ERR_INVALID_ARG;
+  if (h->in_batch) return IILBM_ERR_INVALID_ARG;  // owned by a batch until it is destroyed
+  h->ws_mode = mode;
+  return IILBM_OK;
+}
+
+int iilbm_get_unforced_velocity(iilbm_t h, double *Ustar) {
+  if (!h || !Ustar) return IILBM_ERR_INVALID_ARG;
+  if (h->nm == 0 || h->ip.model != IILBM_DIRECT) return IILBM_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(Ustar, h->Ustar, 2 * (size_t)h->nm * sizeof(double), cudaMemcpyDefault,
+                     h->stream));
+  return read_status(h);
 }
 
 int iilbm_get_body_force(iilbm_t h, double *F) {

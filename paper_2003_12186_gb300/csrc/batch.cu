@@ -558,12 +558,8 @@ int iilbm_create_batch(iilbm_batch_t *out, const iilbm_t *lattices, int32_t coun
     d.u_max = c.u_max;
     std::memset(&d.df, 0, sizeof d.df);
     if (h->nm > 0 && h->ip.model == IILBM_DIRECT) {
-      DfArgs &a = d.df;
-      a.X = h->X; a.UD = h->aux; a.G0 = h->G0; a.G = h->Gdf; a.U = h->U;
-      a.iters = h->d_mdf_iters; a.res = h->d_mdf_res; a.n = h->nm;
-      a.eta = h->ip.eta; a.dX = h->ip.dX; a.tol = h->ip.mdf_tol; a.max_iters = h->ip.mdf_iters;
-      a.wx0 = h->df_win[0]; a.wy0 = h->df_win[1]; a.ww = h->df_win[2]; a.wh = h->df_win[3];
-      a.bodyx = c.body[0]; a.bodyy = c.body[1]; a.rho0 = c.rho0;
+      d.df = df_args(h);
+      const DfArgs &a = d.df;
       B->any_direct = true;
       B->df_smem = std::max(B->df_smem, direct_forcing_smem(h, a.ww, a.wh, a.n));
     }

@@ -27,18 +27,19 @@ __global__ void __launch_bounds__(DF_THREADS)
 
 // Shared memory of the forcing kernel for a window of ww x wh nodes and n markers.
 size_t direct_forcing_smem(const iilbm_lattice *h, int ww, int wh, int n) {
-  const size_t W = (size_t)ww * wh;
-  return 5 * W * h->tbytes + 16 + 4 * (size_t)n * sizeof(double);
+  return h->cfg.storage == IILBM_F64 ? df_smem_bytes<double>(ww * wh, n)
+                                     : df_smem_bytes<float>(ww * wh, n);
 }
 
-int launch_direct_forcing(iilbm_lattice *h) {
-  const bool odd = h->step & 1;
+// The force iteration's arguments for lattice h.
+DfArgs df_args(const iilbm_lattice *h) {
   DfArgs a;
   a.X = h->X;
   a.UD = h->aux;
   a.G0 = h->G0;
   a.G = h->Gdf;
   a.U = h->U;
+  a.Ustar = h->Ustar;
   a.iters = h->d_mdf_iters;
   a.res = h->d_mdf_res;
   a.n = h->nm;
@@ -53,6 +54,13 @@ int launch_direct_forcing(iilbm_lattice *h) {
   a.bodyx = h->cfg.body[0];
   a.bodyy = h->cfg.body[1];
   a.rho0 = h->cfg.rho0;
+  a.ws_mode = h->ws_mode;
+  return a;
+}
+
+int launch_direct_forcing(iilbm_lattice *h) {
+  const bool odd = h->step & 1;
+  const DfArgs a = df_args(h);
   const size_t smem = direct_forcing_smem(h, a.ww, a.wh, a.n);
   const double is = std::ldexp(1.0, -h->cfg.storage_scale_log2);
   cudaError_t e = cudaSuccess;

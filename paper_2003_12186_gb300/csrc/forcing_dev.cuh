@@ -8,9 +8,13 @@
 
 namespace iilbm {
 
+// Where the force iteration starts (G^(0)).
+enum { WS_GIVEN = 0, WS_PREVIOUS = 1, WS_MLP = 2 };
+
 struct DfArgs {
   const double *X, *UD, *G0;
   double *G, *U;
+  double *Ustar;  // out: U*_k, the interpolated velocity without immersed-boundary force
   int *iters;
   double *res;
   int n;
@@ -18,28 +22,81 @@ struct DfArgs {
   int max_iters;
   int wx0, wy0, ww, wh;  // window origin and size (lattice nodes)
   double bodyx, bodyy, rho0;
+  int ws_mode;            // WS_GIVEN: G0; WS_PREVIOUS: the G of the last iteration (in G)
 };
 
 constexpr int DF_THREADS = 1024;
 
+// Shared memory of the force iteration: the window fields u*, 1/(2 rho), g (5 W values
+// of T), the stencil of every marker (16 n weights T and window indices), and the marker
+// arrays G, U, U^D, G dX and U* (2 n values of T each).
+template <typename T>
+__host__ __device__ inline size_t df_smem_bytes(int W, int n) {
+  size_t b = 5 * (size_t)W * sizeof(T);
+  b += 16 * (size_t)n * (sizeof(T) + sizeof(int));
+  b = (b + 15) & ~(size_t)15;
+  b += 10 * (size_t)n * sizeof(T);
+  return b + 16;
+}
+
+// Bit pattern of a non-negative value of T; such patterns order as the values do, so
+// the residual's maximum is taken with integer maxima.
+template <typename T> struct BitsOf;
+template <> struct BitsOf<float> {
+  using U = unsigned;
+  __device__ static U of(float v) { return __float_as_uint(v); }
+  __device__ static float val(U b) { return __uint_as_float(b); }
+};
+template <> struct BitsOf<double> {
+  using U = unsigned long long;
+  __device__ static U of(double v) { return (U)__double_as_longlong(v); }
+  __device__ static double val(U b) { return __longlong_as_double((long long)b); }
+};
+
 // The whole force iteration of one body by one CTA of DF_THREADS threads; smem_raw is
-// the CTA's dynamic shared memory (direct_forcing_smem bytes).
+// the CTA's dynamic shared memory (df_smem_bytes<T>(ww * wh, n)).
+//
+// The markers do not move within the iteration, so each marker's 4 x 4 stencil
+// (window indices and weights phi(x - X) phi(y - Y), from the FP64 position) is formed
+// once; a pass is then the spread (Eq. 17) of G dX, the interpolation (Eq. 20) of
+// u* + g / (2 rho), the residual max_k |U^D - U_k| and the update G += eta (U^D - U)
+// (Eq. 18), all in the arithmetic type T (FP64 for FP64 storage; FP32 otherwise, where
+// GB300's FP64 pipe would cost a whole warp's time even for the few lanes that hold a
+// marker).  U* (the interpolation with G = 0) is recorded for the learned warm start.
 template <typename S>
 __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, const Geom &geo,
                                                    bool odd, const DfArgs &a, double inv_scale,
                                                    unsigned char *smem_raw) {
   using T = typename Store<S>::T;
-  const int W = a.ww * a.wh;
+  using B = typename BitsOf<T>::U;
+  const int W = a.ww * a.wh, n = a.n;
   T *usx = reinterpret_cast<T *>(smem_raw);
   T *usy = usx + W;
   T *h2r = usy + W;  // 1 / (2 rho)
   T *gx = h2r + W;
   T *gy = gx + W;
-  double *Gk = reinterpret_cast<double *>(gy + W + (W & 1));  // 8-byte aligned
-  double *Uk = Gk + 2 * a.n;
-  __shared__ double red[DF_THREADS / 32];
-  __shared__ double res_s;
-  const int tid = threadIdx.x;
+  T *pw = gy + W;                                   // stencil weights [16 n]
+  int *pc = reinterpret_cast<int *>(pw + 16 * n);   // stencil window indices [16 n]
+  size_t off = (size_t)(reinterpret_cast<unsigned char *>(pc + 16 * n) - smem_raw);
+  off = (off + 15) & ~(size_t)15;
+  T *Gk = reinterpret_cast<T *>(smem_raw + off);    // [2 n] each
+  T *Uk = Gk + 2 * n;
+  T *UDk = Uk + 2 * n;
+  T *GdX = UDk + 2 * n;                             // G dX, what the spread moves
+  T *Us = GdX + 2 * n;                              // U*
+  __shared__ B red[DF_THREADS / 32];
+  __shared__ T cst[6];  // 2^-k, rho0, body force, eta, dX: converted once, by one thread
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) {
+    cst[0] = T(inv_scale);
+    cst[1] = T(a.rho0);
+    cst[2] = T(a.bodyx);
+    cst[3] = T(a.bodyy);
+    cst[4] = T(a.eta);
+    cst[5] = T(a.dX);
+  }
+  __syncthreads();
+  const T is = cst[0], rho0 = cst[1], bodyx = cst[2], bodyy = cst[3], eta = cst[4], dX = cst[5];
 
   // u*, 1/(2 rho) on the window (zero outside the lattice: no stencil node lies there)
   for (int c = tid; c < W; c += DF_THREADS) {
@@ -53,55 +110,96 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
       const int yi = geo.bc == IILBM_BC_PERIODIC ? wrap(y, geo.ny) : y;
       T f[9];
 #pragma unroll
-      for (int i = 0; i < 9; i++) f[i] = Store<S>::ld(A[aa_loc(geo, odd, i, xi, yi)]) * T(inv_scale);
+      for (int i = 0; i < 9; i++) f[i] = Store<S>::ld(A[aa_loc(geo, odd, i, xi, yi)]) * is;
       const T d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-      const T rho = T(a.rho0) + d;
-      ux = ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]) + T(0.5) * T(a.bodyx)) / rho;
-      uy = ((f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]) + T(0.5) * T(a.bodyy)) / rho;
+      const T rho = rho0 + d;
+      ux = ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]) + T(0.5) * bodyx) / rho;
+      uy = ((f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]) + T(0.5) * bodyy) / rho;
       hr = T(0.5) / rho;
     }
     usx[c] = ux;
     usy[c] = uy;
     h2r[c] = hr;
+    gx[c] = T(0);
+    gy[c] = T(0);
   }
-  for (int k = tid; k < 2 * a.n; k += DF_THREADS) Gk[k] = a.G0[k];
+  // stencils, one thread per marker
+  for (int k = tid; k < n; k += DF_THREADS) {
+    const double Xk = a.X[2 * k], Yk = a.X[2 * k + 1];
+    const int bx = (int)floor(Xk) - 1, by = (int)floor(Yk) - 1;
+    T wx[4], wy[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      wx[q] = phi4<T>(T((double)(bx + q) - Xk));
+      wy[q] = phi4<T>(T((double)(by + q) - Yk));
+    }
+#pragma unroll
+    for (int l = 0; l < 16; l++) {
+      pw[16 * k + l] = wx[l & 3] * wy[l >> 2];
+      pc[16 * k + l] = (by + (l >> 2) - a.wy0) * a.ww + (bx + (l & 3) - a.wx0);
+    }
+  }
+  // marker arrays, one thread per component: the start of the iteration, U^D
+  const double *g0 = a.ws_mode == WS_PREVIOUS ? a.G : a.G0;
+  for (int k = tid; k < 2 * n; k += DF_THREADS) {
+    if (sizeof(T) == 8) {
+      Gk[k] = T(g0[k]);
+      GdX[k] = T(g0[k] * a.dX);
+    } else {
+      Gk[k] = T(g0[k]);
+      GdX[k] = Gk[k] * dX;
+    }
+    UDk[k] = T(a.UD[k]);
+  }
   __syncthreads();
 
-  // (marker k, stencil node l) pairs: 16 per marker
-  const int npairs = 16 * a.n;
-  int it = 0;
-  double res = 0.0;
-  for (it = 0; it < a.max_iters; it++) {
-    for (int c = tid; c < W; c += DF_THREADS) {
-      gx[c] = T(0);
-      gy[c] = T(0);
+  const int npairs = 16 * n;
+  // U* = interp(u*), 16 consecutive threads per marker
+  for (int base = 0; base < npairs; base += DF_THREADS) {
+    const int q = base + tid;
+    T sx = T(0), sy = T(0);
+    if (q < npairs) {
+      const int c = pc[q];
+      sx = usx[c] * pw[q];
+      sy = usy[c] * pw[q];
     }
-    __syncthreads();
-    // spread G dX (Eq. 17)
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o, 16);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o, 16);
+    }
+    if (q < npairs && (q & 15) == 0) {
+      Us[2 * (q >> 4)] = sx;
+      Us[2 * (q >> 4) + 1] = sy;
+    }
+  }
+
+  int it = 0;
+  B rm = 0;
+  // stop once the residual's bit pattern is below the tolerance's (both non-negative)
+  const bool stop_on_tol = a.tol > 0.0;
+  const B tol_bits = BitsOf<T>::of(T(a.tol));
+  for (it = 0; it < a.max_iters; it++) {
+    // spread G dX (Eq. 17); g is zero here
     for (int q = tid; q < npairs; q += DF_THREADS) {
-      const int k = q >> 4, l = q & 15;
-      const double Xk = a.X[2 * k], Yk = a.X[2 * k + 1];
-      const int xa = (int)floor(Xk) - 1 + (l & 3), yb = (int)floor(Yk) - 1 + (l >> 2);
-      const T w = phi4<T>(T((double)xa - Xk)) * phi4<T>(T((double)yb - Yk));
-      const int c = (yb - a.wy0) * a.ww + (xa - a.wx0);
+      const T w = pw[q];
       if (w != T(0)) {
-        atomicAdd(&gx[c], T(Gk[2 * k] * a.dX) * w);
-        atomicAdd(&gy[c], T(Gk[2 * k + 1] * a.dX) * w);
+        const int k = q >> 4, c = pc[q];
+        atomicAdd(&gx[c], GdX[2 * k] * w);
+        atomicAdd(&gy[c], GdX[2 * k + 1] * w);
       }
     }
     __syncthreads();
-    // interpolate u* + g / (2 rho) (Eq. 20): 16 consecutive threads per marker
+    // interpolate u* + g / (2 rho) (Eq. 20) and the marker's residual |U^D - U|
+    B r = 0;
     for (int base = 0; base < npairs; base += DF_THREADS) {
       const int q = base + tid;
-      double sx = 0.0, sy = 0.0;
+      T sx = T(0), sy = T(0);
       if (q < npairs) {
-        const int k = q >> 4, l = q & 15;
-        const double Xk = a.X[2 * k], Yk = a.X[2 * k + 1];
-        const int xa = (int)floor(Xk) - 1 + (l & 3), yb = (int)floor(Yk) - 1 + (l >> 2);
-        const T w = phi4<T>(T((double)xa - Xk)) * phi4<T>(T((double)yb - Yk));
-        const int c = (yb - a.wy0) * a.ww + (xa - a.wx0);
-        sx = (double)((usx[c] + gx[c] * h2r[c]) * w);
-        sy = (double)((usy[c] + gy[c] * h2r[c]) * w);
+        const int c = pc[q];
+        const T w = pw[q];
+        sx = (usx[c] + gx[c] * h2r[c]) * w;
+        sy = (usy[c] + gy[c] * h2r[c]) * w;
       }
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) {
@@ -109,37 +207,41 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
         sy += __shfl_xor_sync(0xffffffffu, sy, o, 16);
       }
       if (q < npairs && (q & 15) == 0) {
-        Uk[2 * (q >> 4)] = sx;
-        Uk[2 * (q >> 4) + 1] = sy;
+        const int k = q >> 4;
+        Uk[2 * k] = sx;
+        Uk[2 * k + 1] = sy;
+        r = max(r, max(BitsOf<T>::of(fabs(UDk[2 * k] - sx)),
+                       BitsOf<T>::of(fabs(UDk[2 * k + 1] - sy))));
       }
     }
-    __syncthreads();
-    // residual max_k |U^D - U_k| over both components
-    double r = 0.0;
-    for (int k = tid; k < 2 * a.n; k += DF_THREADS) r = fmax(r, fabs(a.UD[k] - Uk[k]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
-    if ((tid & 31) == 0) red[tid >> 5] = r;
+    for (int o = 16; o > 0; o >>= 1) r = max(r, (B)__shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0) red[tid >> 5] = r;
     __syncthreads();
-    if (tid < 32) {
-      double v = red[tid];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if (tid == 0) res_s = v;
+    // every thread reduces the warp maxima itself: no second barrier
+    rm = 0;
+#pragma unroll 8
+    for (int w = 0; w < DF_THREADS / 32; w++) rm = max(rm, red[w]);
+    if (stop_on_tol && rm < tol_bits) break;  // uniform
+    for (int c = tid; c < W; c += DF_THREADS) {
+      gx[c] = T(0);
+      gy[c] = T(0);
+    }
+    for (int k = tid; k < 2 * n; k += DF_THREADS) {
+      Gk[k] += eta * (UDk[k] - Uk[k]);
+      if (sizeof(T) == 8) GdX[k] = T((double)Gk[k] * a.dX);
+      else GdX[k] = Gk[k] * dX;
     }
     __syncthreads();
-    res = res_s;
-    if (a.tol > 0.0 && res < a.tol) break;  // uniform
-    for (int k = tid; k < 2 * a.n; k += DF_THREADS) Gk[k] += a.eta * (a.UD[k] - Uk[k]);
-    __syncthreads();
   }
-  for (int k = tid; k < 2 * a.n; k += DF_THREADS) {
-    a.G[k] = Gk[k];
-    a.U[k] = Uk[k];
+  for (int k = tid; k < 2 * n; k += DF_THREADS) {
+    a.G[k] = (double)Gk[k];
+    a.U[k] = (double)Uk[k];
+    a.Ustar[k] = (double)Us[k];
   }
   if (tid == 0) {
     *a.iters = it;
-    *a.res = res;
+    *a.res = (double)BitsOf<T>::val(rm);
   }
 }
 

@@ -180,6 +180,8 @@ struct iilbm_lattice {
   double *X, *aux, *G, *Fn, *U, *nrm;
   long long *Xq;      // marker coordinates snapped to 2^-24 (XQ_OUT outside the region)
   double *G0, *Gdf;   // direct forcing: warm start and converged force
+  double *Ustar;      // direct forcing: interpolated velocity without the body's force
+  int ws_mode;        // direct forcing: where the iteration starts (WS_*)
   int *d_mdf_iters;
   double *d_mdf_res;
   int df_win[4];      // direct forcing window: x0, y0, width, height
@@ -205,6 +207,8 @@ int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s);
 int launch_channel_bc(iilbm_lattice *h);
 int launch_direct_forcing(iilbm_lattice *h);
 size_t direct_forcing_smem(const iilbm_lattice *h, int ww, int wh, int n);
+struct DfArgs;
+DfArgs df_args(const iilbm_lattice *h);
 int prepare_lattice(iilbm_lattice *h);
 int prepare_batch_of(iilbm_lattice *h);
 }  // namespace iilbm

@@ -25,6 +25,7 @@ F64, F32, F16, BF16 = 0, 1, 2, 3
 BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL = 0, 1, 2
 SPRING, SPRING_REST, PRESCRIBED, DIRECT = 0, 1, 2, 3
 OPT_CUDA_GRAPH, OPT_OVERLAP, OPT_VECTOR_KERNEL = 0, 1, 2
+WS_GIVEN, WS_PREVIOUS = 0, 1
 STORAGE = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
 STORAGE_BYTES = {F64: 8, F32: 4, F16: 2, BF16: 2}
 
@@ -66,6 +67,8 @@ SIGNATURES = {
     "iilbm_get_markers": [_H, _P, _P, _P, _P],
     "iilbm_get_mdf_stats": [_H, C.POINTER(C.c_int32), C.POINTER(C.c_double)],
     "iilbm_set_warm_start": [_H, _P],
+    "iilbm_set_warm_start_mode": [_H, C.c_int32],
+    "iilbm_get_unforced_velocity": [_H, _P],
     "iilbm_get_body_force": [_H, C.POINTER(C.c_double)],
     "iilbm_get_cut_link_count": [_H, C.POINTER(C.c_int32)],
     "iilbm_set_timing": [_H, C.c_int32],
@@ -273,6 +276,16 @@ class Lattice:
         G = None if G0 is None else (G0 if hasattr(G0, "data_ptr") else
                                      _host(G0, (self.n_markers, 2)))
         _check("iilbm_set_warm_start", self._L.iilbm_set_warm_start(self._h, _ptr(G)))
+
+    def iilbm_set_warm_start_mode(self, mode):
+        _check("iilbm_set_warm_start_mode", self._L.iilbm_set_warm_start_mode(self._h, int(mode)))
+
+    def iilbm_get_unforced_velocity(self, out=None):
+        """U*_k [n][2] of the most recent force iteration (numpy, or into `out`)."""
+        o = out if out is not None else np.zeros((self.n_markers, 2))
+        _check("iilbm_get_unforced_velocity",
+               self._L.iilbm_get_unforced_velocity(self._h, _ptr(o)))
+        return o
 
     def iilbm_get_body_force(self):
         F = (C.c_double * 2)()

@@ -140,3 +140,30 @@ def test_channel_cylinder_full_size_fp32(orc):
     _, uo, vo = o.current_macros()
     assert max(rel_err(ug, uo, 0.05), rel_err(vg, vo, 0.05)) < 1e-5
     assert g.iilbm_get_cut_link_count() == o.cut_link_count() > 0
+
+
+def test_unforced_velocity_and_previous_force_start_fp64(orc):
+    """U* (interpolation of u* before the first update) and the iteration started from
+    the previous step's force: pass counts, force and populations match the oracle
+    step by step, and the previous-force start needs fewer passes than the plain one."""
+    g, o = cylinder_case(orc, "f64", 300, 1e-5, steps=10, n=34)
+    g.iilbm_set_warm_start_mode(iilbm.WS_PREVIOUS)
+    o.set_ws_previous(True)
+    plain_it, _ = g.iilbm_get_mdf_stats()
+    for _ in range(6):
+        g.step(1)
+        o.step(1)
+        it_g, res_g = g.iilbm_get_mdf_stats()
+        it_o, res_o = o.mdf_stats()
+        assert it_g == it_o and abs(res_g - res_o) < 1e-14 and res_g < 1e-5
+        assert np.abs(g.iilbm_get_unforced_velocity() - o.unforced_velocity()).max() < 1e-14
+        assert np.abs(g.get_markers()["G"] - o.markers()["G"]).max() < 1e-12
+    assert np.abs(g.get_populations() - o.get_df()).max() < 1e-14
+    assert it_g < plain_it
+
+
+def test_unforced_velocity_fp32(orc):
+    g, o = cylinder_case(orc, "f32", 5, 0.0, steps=20)
+    U = g.iilbm_get_unforced_velocity()
+    Uo = o.unforced_velocity()
+    assert np.abs(U - Uo).max() <= 1e-5 * max(np.abs(Uo).max(), 0.05)

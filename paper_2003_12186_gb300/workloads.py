@@ -127,3 +127,42 @@ def batched_membranes(count: int = 256, seed: int = 0):
         sims.append(dict(nx=n, ny=n, tau=tau, kappa=kappa, X=X,
                          dX=polygon_perimeter(X) / nm))
     return sims
+
+
+# ------------------------------------------------------------- learned warm start
+MLP_SHAPES = [((64, 30), True), ((64,), False), ((64, 64), True), ((64,), False),
+              ((64, 64), True), ((64,), False), ((2, 64), True), ((2,), False)]
+
+
+def mlp_init_params(seed: int) -> np.ndarray:
+    """Initial parameters of the 30-64-64-64-2 network in its packed order (W1, b1, W2,
+    b2, W3, b3, W4, b4; weights [out][in]): weights uniform in +-sqrt(6 / fan_in)
+    (+-sqrt(3 / fan_in) for the output layer), biases zero; FP32 values."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for q, (shape, is_w) in enumerate(MLP_SHAPES):
+        if is_w:
+            bound = np.sqrt((3.0 if q == 6 else 6.0) / shape[1])
+            parts.append(rng.uniform(-bound, bound, size=shape).ravel())
+        else:
+            parts.append(np.zeros(shape))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def learned_channels(count: int = 64, seed: int = 0, nx: int = 512, ny: int = 128,
+                     spacing: float = 1.5, u_max: float = 0.05):
+    """Rigid-cylinder channels of the learned warm start: D uniform in [16, 32], centre x
+    uniform in [96, 160], y = ny/2 + uniform(-4, 4), Re uniform in [10, 150] (tau from
+    Re with u_max), markers every `spacing` lattice units along the circle."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        D = float(rng.uniform(16.0, 32.0))
+        xc = float(rng.uniform(96.0, 160.0))
+        yc = ny / 2.0 + float(rng.uniform(-4.0, 4.0))
+        re = float(rng.uniform(10.0, 150.0))
+        n = int(round(np.pi * D / spacing))
+        X = circle_markers(xc, yc, D / 2.0, n, phase=float(rng.uniform(0.0, 2.0 * np.pi / n)))
+        out.append(dict(nx=nx, ny=ny, D=D, xc=xc, yc=yc, re=re, n=n, X=X, u_max=u_max,
+                        tau=0.5 + 3.0 * u_max * D / re, dX=polygon_perimeter(X) / n))
+    return out

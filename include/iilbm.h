@@ -145,7 +145,7 @@ int iilbm_set_warm_start(iilbm_t h, const double *G0);
  *                      the first step after iilbm_set_interface).
  * The stopping rule (mdf_iters, mdf_tol) is the same in every mode.  INVALID_ARG for an
  * unknown mode or a batched lattice. */
-enum { IILBM_WS_GIVEN = 0, IILBM_WS_PREVIOUS = 1 };
+enum { IILBM_WS_GIVEN = 0, IILBM_WS_PREVIOUS = 1, IILBM_WS_MLP = 2 };
 int iilbm_set_warm_start_mode(iilbm_t h, int32_t mode);
 
 /* Direct forcing: U*_k [n][2], the velocity interpolated at the markers from the state
@@ -232,6 +232,51 @@ int iilbm_batch_get_timing(iilbm_batch_t b, double *stream_collide_ms, int32_t *
                            int64_t *kernel_launches);
 /* Wait for the batch's streams; returns any latched device status of its lattices. */
 int iilbm_batch_synchronize(iilbm_batch_t b);
+
+/* ------------------------------------------------------- learned warm start
+ * A small network proposes the starting force G^(0)_k of the direct-forcing iteration
+ * from each marker's local features; the iteration with its stopping rule stays the
+ * judge of the answer.  Features of marker k (30, FP32): for j = k-2 .. k+2 (cyclic)
+ *   U^D_j - U*_j (2), the outward unit normal (2), the signed curvature
+ *   -(X_{j+1} - 2 X_j + X_{j-1}) . n_j / dX^2 (1), and Re (1).
+ * Network: x -> (x - in_mean) * in_istd -> 3 x [64, GELU (erf form)] -> 2 ->
+ * * out_scale + out_mean.  Parameters packed as W1 [64][30], b1 [64], W2 [64][64], b2,
+ * W3 [64][64], b3, W4 [2][64], b4 [2] (10434 FP32 values, weights [out][in]).
+ * Training: mean squared error of the normalised outputs over a batch, Adam. */
+typedef struct iilbm_mlp *iilbm_mlp_t;
+enum { IILBM_MLP_PARAMS = 10434, IILBM_MLP_FEATURES = 30 };
+/* Create a network on the current device (parameters zero, identity normalisation);
+ * stream may be NULL (the network makes its own).  Errors: NO_DEVICE, OOM. */
+int iilbm_mlp_create(iilbm_mlp_t *out, void *stream);
+/* Destroy it (detach it from every lattice first). */
+int iilbm_mlp_destroy(iilbm_mlp_t m);
+/* Packed parameters in / out (host or device, FP32); setting them resets Adam. */
+int iilbm_mlp_set_params(iilbm_mlp_t m, const float *params);
+int iilbm_mlp_get_params(iilbm_mlp_t m, float *params);
+/* Input normalisation (30 means, 30 reciprocal deviations) and output scaling (2, 2);
+ * host pointers.  INVALID_ARG for a zero or non-finite output scale. */
+int iilbm_mlp_set_normalization(iilbm_mlp_t m, const float *in_mean, const float *in_istd,
+                                const float *out_mean, const float *out_scale);
+/* Y [N][2] = network(X [N][30]); host or device pointers; synchronises. */
+int iilbm_mlp_forward(iilbm_mlp_t m, const float *X, int32_t N, float *Y);
+/* Gradient [10434] and value of the loss over all N samples (targets T [N][2]). */
+int iilbm_mlp_gradient(iilbm_mlp_t m, const float *X, const float *T, int32_t N, float *grad,
+                       float *loss);
+/* `steps` Adam steps; step s uses the samples order[s * batch .. (s+1) * batch - 1]
+ * (indices into X, T; host or device; each in [0, N)).  losses [steps] (nullable)
+ * receives each step's batch loss before its update.  Errors: INVALID_ARG, OOM, CUDA. */
+int iilbm_mlp_train(iilbm_mlp_t m, const float *X, const float *T, int32_t N,
+                    const int32_t *order, int32_t steps, int32_t batch, float lr, float beta1,
+                    float beta2, float eps, float *losses);
+/* Start every force iteration of lattice h from the network's proposal (mode
+ * IILBM_WS_MLP) with Reynolds-number feature re; the network must outlive the setting
+ * (iilbm_set_warm_start_mode detaches it).  INVALID_ARG unless h carries a directly
+ * forced body on the network's device; CAPACITY if the forcing kernel's shared memory
+ * would exceed 227 KB. */
+int iilbm_set_warm_start_mlp(iilbm_t h, iilbm_mlp_t mlp, double re);
+/* The raw features F [n][30] of every marker from the U* of the most recent force
+ * iteration (what the network sees before normalisation).  Synchronises. */
+int iilbm_get_df_features(iilbm_t h, double re, float *F);
 
 /* Wait for the handle's stream and return any latched device status. */
 int iilbm_synchronize(iilbm_t h);

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of include/iilbm.h: handle life cycle, argument checking,
 // memory ownership, and the order of the kernels of one II-LBM time step.
+#include "forcing_dev.cuh"
 #include "iilbm_internal.cuh"
 
 #include <algorithm>
@@ -634,7 +635,42 @@ int iilbm_set_warm_start_mode(iilbm_t h, int32_t mode) {
   if (!h || mode < IILBM_WS_GIVEN || mode > IILBM_WS_PREVIOUS) return IILBM_ERR_INVALID_ARG;
   if (h->in_batch) return IILBM_ERR_INVALID_ARG;  // owned by a batch until it is destroyed
   h->ws_mode = mode;
+  h->mlp = nullptr;
   return IILBM_OK;
+}
+
+int iilbm_set_warm_start_mlp(iilbm_t h, iilbm_mlp_t mlp, double re) {
+  if (!h || !mlp || !std::isfinite(re)) return IILBM_ERR_INVALID_ARG;
+  if (h->in_batch) return IILBM_ERR_INVALID_ARG;
+  if (h->nm == 0 || h->ip.model != IILBM_DIRECT || mlp_device(mlp) != h->device)
+    return IILBM_ERR_INVALID_ARG;
+  const int prev = h->ws_mode;
+  h->ws_mode = WS_MLP;
+  if (direct_forcing_smem(h, h->df_win[2], h->df_win[3], h->nm) > 227 * 1024) {
+    h->ws_mode = prev;
+    return IILBM_ERR_CAPACITY;
+  }
+  h->mlp = mlp;
+  h->re = (float)re;
+  return IILBM_OK;
+}
+
+int iilbm_get_df_features(iilbm_t h, double re, float *F) {
+  if (!h || !F || !std::isfinite(re)) return IILBM_ERR_INVALID_ARG;
+  if (h->nm == 0 || h->ip.model != IILBM_DIRECT) return IILBM_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)h->nm * 30 * sizeof(float);
+  float *d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return IILBM_ERR_OOM;
+  }
+  int rc = launch_df_features(h, (float)re, d);
+  if (!rc && cudaMemcpyAsync(F, d, bytes, cudaMemcpyDefault, h->stream) != cudaSuccess)
+    rc = IILBM_ERR_CUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess && !rc) rc = IILBM_ERR_CUDA;
+  cudaGetLastError();
+  cudaFree(d);
+  return rc ? rc : read_status(h);
 }
 
 int iilbm_get_unforced_velocity(iilbm_t h, double *Ustar) {

@@ -27,8 +27,9 @@ __global__ void __launch_bounds__(DF_THREADS)
 
 // Shared memory of the forcing kernel for a window of ww x wh nodes and n markers.
 size_t direct_forcing_smem(const iilbm_lattice *h, int ww, int wh, int n) {
-  return h->cfg.storage == IILBM_F64 ? df_smem_bytes<double>(ww * wh, n)
-                                     : df_smem_bytes<float>(ww * wh, n);
+  const bool mlp = h->ws_mode == WS_MLP;
+  return h->cfg.storage == IILBM_F64 ? df_smem_bytes<double>(ww * wh, n, mlp)
+                                     : df_smem_bytes<float>(ww * wh, n, mlp);
 }
 
 // The force iteration's arguments for lattice h.
@@ -55,6 +56,9 @@ DfArgs df_args(const iilbm_lattice *h) {
   a.bodyy = h->cfg.body[1];
   a.rho0 = h->cfg.rho0;
   a.ws_mode = h->ws_mode;
+  a.mlp_P = h->mlp ? mlp_params(h->mlp) : nullptr;
+  a.mlp_norm = h->mlp ? mlp_norm(h->mlp) : nullptr;
+  a.re = h->re;
   return a;
 }
 
@@ -90,6 +94,25 @@ int launch_direct_forcing(iilbm_lattice *h) {
     return IILBM_ERR_CUDA;
   }
   return IILBM_OK;
+}
+
+__global__ void k_df_features(const double *__restrict__ X, const double *__restrict__ UD,
+                              const double *__restrict__ Ustar, int n, double dX, float re,
+                              float *F) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  df_features_cta(X, UD, Ustar, n, dX, re, F, reinterpret_cast<float *>(smem_raw));
+}
+
+int launch_df_features(iilbm_lattice *h, float re, float *F) {
+  const size_t smem = (size_t)h->nm * MLP_BLOCK * sizeof(float);
+  if (smem > 227 * 1024) return IILBM_ERR_CAPACITY;
+  if (cudaFuncSetAttribute(k_df_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return IILBM_ERR_CUDA;
+  }
+  k_df_features<<<1, 256, smem, h->stream>>>(h->X, h->aux, h->Ustar, h->nm, h->ip.dX, re, F);
+  return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
 }
 
 }  // namespace iilbm

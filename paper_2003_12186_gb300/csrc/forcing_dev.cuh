@@ -3,6 +3,7 @@
 #pragma once
 
 #include "iilbm_internal.cuh"
+#include "mlp_dev.cuh"
 
 #include <cmath>
 
@@ -22,7 +23,11 @@ struct DfArgs {
   int max_iters;
   int wx0, wy0, ww, wh;  // window origin and size (lattice nodes)
   double bodyx, bodyy, rho0;
-  int ws_mode;            // WS_GIVEN: G0; WS_PREVIOUS: the G of the last iteration (in G)
+  int ws_mode;            // WS_GIVEN: G0; WS_PREVIOUS: the G of the last iteration (in G);
+                          // WS_MLP: the network's proposal from the step's features
+  const float *mlp_P;     // WS_MLP: packed parameters, normalisation, Re feature
+  const float *mlp_norm;
+  float re;
 };
 
 constexpr int DF_THREADS = 1024;
@@ -30,12 +35,16 @@ constexpr int DF_THREADS = 1024;
 // Shared memory of the force iteration: the window fields u*, 1/(2 rho), g (5 W values
 // of T), the stencil of every marker (16 n weights T and window indices), and the marker
 // arrays G, U, U^D, G dX and U* (2 n values of T each).
+// With the network's proposal (mlp), the per-marker feature blocks and two activation
+// buffers (6 + 2 x 64 floats per marker) follow.
 template <typename T>
-__host__ __device__ inline size_t df_smem_bytes(int W, int n) {
+__host__ __device__ inline size_t df_smem_bytes(int W, int n, bool mlp = false) {
   size_t b = 5 * (size_t)W * sizeof(T);
   b += 16 * (size_t)n * (sizeof(T) + sizeof(int));
   b = (b + 15) & ~(size_t)15;
   b += 10 * (size_t)n * sizeof(T);
+  b = (b + 15) & ~(size_t)15;
+  if (mlp) b += (size_t)n * (MLP_BLOCK + 2 * MLP_H) * sizeof(float);
   return b + 16;
 }
 
@@ -84,6 +93,11 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   T *UDk = Uk + 2 * n;
   T *GdX = UDk + 2 * n;                             // G dX, what the spread moves
   T *Us = GdX + 2 * n;                              // U*
+  size_t off2 = (size_t)(reinterpret_cast<unsigned char *>(Us + 2 * n) - smem_raw);
+  off2 = (off2 + 15) & ~(size_t)15;
+  float *blk = reinterpret_cast<float *>(smem_raw + off2);  // WS_MLP scratch
+  float *act0 = blk + MLP_BLOCK * n;
+  float *act1 = act0 + MLP_H * n;
   __shared__ B red[DF_THREADS / 32];
   __shared__ T cst[6];  // 2^-k, rho0, body force, eta, dX: converted once, by one thread
   const int tid = threadIdx.x, lane = tid & 31;
@@ -171,7 +185,36 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
     if (q < npairs && (q & 15) == 0) {
       Us[2 * (q >> 4)] = sx;
       Us[2 * (q >> 4) + 1] = sy;
+      Uk[2 * (q >> 4)] = sx;  // the last interpolated velocity, should no pass run
+      Uk[2 * (q >> 4) + 1] = sy;
     }
+  }
+
+  if (a.ws_mode == WS_MLP) {
+    // G^(0) proposed by the network from each marker's features (U* from above)
+    __syncthreads();
+    for (int j = tid; j < n; j += DF_THREADS)
+      marker_feature_block(a.X, n, j, a.dX, (float)(UDk[2 * j] - Us[2 * j]),
+                           (float)(UDk[2 * j + 1] - Us[2 * j + 1]), a.re, blk + MLP_BLOCK * j);
+    __syncthreads();
+    for (int k = tid; k < n; k += DF_THREADS) mlp_gather_input(blk, n, k, a.mlp_norm, act1 + MLP_IN * k);
+    __syncthreads();
+    mlp_hidden_layer(a.mlp_P + OFF_W1, a.mlp_P + OFF_B1, act1, MLP_IN, nullptr, act0, n, tid, DF_THREADS);
+    __syncthreads();
+    mlp_hidden_layer(a.mlp_P + OFF_W2, a.mlp_P + OFF_B2, act0, MLP_H, nullptr, act1, n, tid, DF_THREADS);
+    __syncthreads();
+    mlp_hidden_layer(a.mlp_P + OFF_W3, a.mlp_P + OFF_B3, act1, MLP_H, nullptr, act0, n, tid, DF_THREADS);
+    __syncthreads();
+    mlp_output_layer(a.mlp_P, act0, act1, n, tid, DF_THREADS);
+    __syncthreads();
+    for (int k = tid; k < 2 * n; k += DF_THREADS) {
+      const int o = k & 1;
+      const float g = act1[k] * a.mlp_norm[NORM_OUT_SCALE + o] + a.mlp_norm[NORM_OUT_MEAN + o];
+      Gk[k] = T(g);
+      if (sizeof(T) == 8) GdX[k] = T((double)g * a.dX);
+      else GdX[k] = Gk[k] * dX;
+    }
+    __syncthreads();
   }
 
   int it = 0;
@@ -242,6 +285,23 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   if (tid == 0) {
     *a.iters = it;
     *a.res = (double)BitsOf<T>::val(rm);
+  }
+}
+
+// Raw (unnormalised) features [n][30] of every marker from the U* of the most recent
+// force iteration: one CTA, blocks in shared memory (n * 6 floats).
+__device__ inline void df_features_cta(const double *__restrict__ X, const double *__restrict__ UD,
+                                       const double *__restrict__ Ustar, int n, double dX,
+                                       float re, float *F, float *blk) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    marker_feature_block(X, n, j, dX, (float)(UD[2 * j] - Ustar[2 * j]),
+                         (float)(UD[2 * j + 1] - Ustar[2 * j + 1]), re, blk + MLP_BLOCK * j);
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * MLP_IN; e += blockDim.x) {
+    const int k = e / MLP_IN, i = e % MLP_IN, q = i / MLP_BLOCK, r = i % MLP_BLOCK;
+    int j = k + q - 2;
+    j = j < 0 ? j + n : (j >= n ? j - n : j);
+    F[e] = blk[MLP_BLOCK * j + r];
   }
 }
 

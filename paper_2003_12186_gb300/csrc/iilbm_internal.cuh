@@ -182,6 +182,8 @@ struct iilbm_lattice {
   double *G0, *Gdf;   // direct forcing: warm start and converged force
   double *Ustar;      // direct forcing: interpolated velocity without the body's force
   int ws_mode;        // direct forcing: where the iteration starts (WS_*)
+  const struct iilbm_mlp *mlp;  // WS_MLP: the network proposing G^(0)
+  float re;                     // WS_MLP: the Reynolds-number feature
   int *d_mdf_iters;
   double *d_mdf_res;
   int df_win[4];      // direct forcing window: x0, y0, width, height
@@ -206,9 +208,13 @@ int launch_get_populations(iilbm_lattice *h, double *df);
 int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s);
 int launch_channel_bc(iilbm_lattice *h);
 int launch_direct_forcing(iilbm_lattice *h);
+int launch_df_features(iilbm_lattice *h, float re, float *F);
 size_t direct_forcing_smem(const iilbm_lattice *h, int ww, int wh, int n);
 struct DfArgs;
 DfArgs df_args(const iilbm_lattice *h);
+const float *mlp_params(const struct iilbm_mlp *M);
+const float *mlp_norm(const struct iilbm_mlp *M);
+int mlp_device(const struct iilbm_mlp *M);
 int prepare_lattice(iilbm_lattice *h);
 int prepare_batch_of(iilbm_lattice *h);
 }  // namespace iilbm

@@ -25,7 +25,8 @@ F64, F32, F16, BF16 = 0, 1, 2, 3
 BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL = 0, 1, 2
 SPRING, SPRING_REST, PRESCRIBED, DIRECT = 0, 1, 2, 3
 OPT_CUDA_GRAPH, OPT_OVERLAP, OPT_VECTOR_KERNEL = 0, 1, 2
-WS_GIVEN, WS_PREVIOUS = 0, 1
+WS_GIVEN, WS_PREVIOUS, WS_MLP = 0, 1, 2
+MLP_PARAMS, MLP_FEATURES = 10434, 30
 STORAGE = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
 STORAGE_BYTES = {F64: 8, F32: 4, F16: 2, BF16: 2}
 
@@ -68,6 +69,17 @@ SIGNATURES = {
     "iilbm_get_mdf_stats": [_H, C.POINTER(C.c_int32), C.POINTER(C.c_double)],
     "iilbm_set_warm_start": [_H, _P],
     "iilbm_set_warm_start_mode": [_H, C.c_int32],
+    "iilbm_set_warm_start_mlp": [_H, _H, C.c_double],
+    "iilbm_get_df_features": [_H, C.c_double, _P],
+    "iilbm_mlp_create": [C.POINTER(_H), _P],
+    "iilbm_mlp_destroy": [_H],
+    "iilbm_mlp_set_params": [_H, _P],
+    "iilbm_mlp_get_params": [_H, _P],
+    "iilbm_mlp_set_normalization": [_H, _P, _P, _P, _P],
+    "iilbm_mlp_forward": [_H, _P, C.c_int32, _P],
+    "iilbm_mlp_gradient": [_H, _P, _P, C.c_int32, _P, _P],
+    "iilbm_mlp_train": [_H, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, C.c_float, C.c_float,
+                        C.c_float, C.c_float, _P],
     "iilbm_get_unforced_velocity": [_H, _P],
     "iilbm_get_body_force": [_H, C.POINTER(C.c_double)],
     "iilbm_get_cut_link_count": [_H, C.POINTER(C.c_int32)],
@@ -287,6 +299,18 @@ class Lattice:
                self._L.iilbm_get_unforced_velocity(self._h, _ptr(o)))
         return o
 
+    def iilbm_set_warm_start_mlp(self, mlp, re):
+        _check("iilbm_set_warm_start_mlp",
+               self._L.iilbm_set_warm_start_mlp(self._h, mlp.handle, float(re)))
+        self._mlp = mlp  # kept alive while attached
+
+    def iilbm_get_df_features(self, re):
+        """Raw features [n][30] (FP32) of the most recent force iteration."""
+        F = np.zeros((self.n_markers, 30), dtype=np.float32)
+        _check("iilbm_get_df_features",
+               self._L.iilbm_get_df_features(self._h, float(re), F.ctypes.data))
+        return F
+
     def iilbm_get_body_force(self):
         F = (C.c_double * 2)()
         _check("iilbm_get_body_force", self._L.iilbm_get_body_force(self._h, F))
@@ -384,3 +408,90 @@ class Batch:
         _check("iilbm_batch_synchronize", self._L.iilbm_batch_synchronize(self._h))
 
     synchronize = iilbm_batch_synchronize
+
+
+def _f32(a, shape=None):
+    """Contiguous FP32 host array (or a contiguous float32 CUDA tensor, passed as is)."""
+    if a is not None and not isinstance(a, np.ndarray) and hasattr(a, "data_ptr"):
+        assert a.is_contiguous() and str(a.dtype) == "torch.float32", "need contiguous float32"
+        return a
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if shape is not None:
+        assert a.size == int(np.prod(shape)), f"expected {shape}, got {a.shape}"
+    return a
+
+
+def _fptr(a):
+    return a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()
+
+
+class Mlp:
+    """The learned warm start's network (handle of iilbm_mlp_create)."""
+
+    def __init__(self, params=None, stream=None):
+        L = load()
+        h = _H()
+        _check("iilbm_mlp_create", L.iilbm_mlp_create(C.byref(h), stream))
+        self._h, self._L = h, L
+        if params is not None:
+            self.iilbm_mlp_set_params(params)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.iilbm_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def iilbm_mlp_set_params(self, params):
+        p = _f32(params, (MLP_PARAMS,))
+        _check("iilbm_mlp_set_params", self._L.iilbm_mlp_set_params(self._h, _fptr(p)))
+
+    def iilbm_mlp_get_params(self):
+        p = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _check("iilbm_mlp_get_params", self._L.iilbm_mlp_get_params(self._h, p.ctypes.data))
+        return p
+
+    def iilbm_mlp_set_normalization(self, in_mean, in_istd, out_mean, out_scale):
+        a = [_f32(v, (n,)) for v, n in ((in_mean, 30), (in_istd, 30), (out_mean, 2), (out_scale, 2))]
+        _check("iilbm_mlp_set_normalization",
+               self._L.iilbm_mlp_set_normalization(self._h, *[x.ctypes.data for x in a]))
+
+    def iilbm_mlp_forward(self, X):
+        X = _f32(X)
+        N = X.shape[0] if isinstance(X, np.ndarray) else X.shape[0]
+        Y = np.zeros((N, 2), dtype=np.float32)
+        _check("iilbm_mlp_forward", self._L.iilbm_mlp_forward(self._h, _fptr(X), N, Y.ctypes.data))
+        return Y
+
+    def iilbm_mlp_gradient(self, X, T):
+        X, T = _f32(X), _f32(T)
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        loss = C.c_float()
+        _check("iilbm_mlp_gradient",
+               self._L.iilbm_mlp_gradient(self._h, _fptr(X), _fptr(T), X.shape[0], g.ctypes.data,
+                                          C.byref(loss)))
+        return loss.value, g
+
+    def iilbm_mlp_train(self, X, T, order, batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        """Adam steps over batches order[s*batch:(s+1)*batch]; returns each step's loss."""
+        X, T = _f32(X), _f32(T)
+        order = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+        steps = order.size // batch
+        losses = np.zeros(max(steps, 1), dtype=np.float32)
+        _check("iilbm_mlp_train",
+               self._L.iilbm_mlp_train(self._h, _fptr(X), _fptr(T), X.shape[0], order.ctypes.data,
+                                       steps, batch, lr, beta1, beta2, eps, losses.ctypes.data))
+        return losses[:steps]
+
+    forward = iilbm_mlp_forward
+    gradient = iilbm_mlp_gradient
+    train = iilbm_mlp_train

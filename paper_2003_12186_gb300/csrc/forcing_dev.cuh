@@ -44,7 +44,7 @@ __host__ __device__ inline size_t df_smem_bytes(int W, int n, bool mlp = false) 
   b = (b + 15) & ~(size_t)15;
   b += 10 * (size_t)n * sizeof(T);
   b = (b + 15) & ~(size_t)15;
-  if (mlp) b += (size_t)n * (MLP_BLOCK + 2 * MLP_H) * sizeof(float);
+  if (mlp) b += ((size_t)n * (MLP_BLOCK + 2 * MLP_H) + (MLP_IN + 2 * MLP_H) * MLP_H) * sizeof(float);
   return b + 16;
 }
 
@@ -98,6 +98,9 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   float *blk = reinterpret_cast<float *>(smem_raw + off2);  // WS_MLP scratch
   float *act0 = blk + MLP_BLOCK * n;
   float *act1 = act0 + MLP_H * n;
+  float *wt1 = act1 + MLP_H * n;  // W1, W2, W3 transposed
+  float *wt2 = wt1 + MLP_IN * MLP_H;
+  float *wt3 = wt2 + MLP_H * MLP_H;
   __shared__ B red[DF_THREADS / 32];
   __shared__ T cst[6];  // 2^-k, rho0, body force, eta, dX: converted once, by one thread
   const int tid = threadIdx.x, lane = tid & 31;
@@ -198,12 +201,15 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
                            (float)(UDk[2 * j + 1] - Us[2 * j + 1]), a.re, blk + MLP_BLOCK * j);
     __syncthreads();
     for (int k = tid; k < n; k += DF_THREADS) mlp_gather_input(blk, n, k, a.mlp_norm, act1 + MLP_IN * k);
+    mlp_stage_transposed(a.mlp_P + OFF_W1, MLP_IN, wt1, tid, DF_THREADS);
+    mlp_stage_transposed(a.mlp_P + OFF_W2, MLP_H, wt2, tid, DF_THREADS);
+    mlp_stage_transposed(a.mlp_P + OFF_W3, MLP_H, wt3, tid, DF_THREADS);
     __syncthreads();
-    mlp_hidden_layer(a.mlp_P + OFF_W1, a.mlp_P + OFF_B1, act1, MLP_IN, nullptr, act0, n, tid, DF_THREADS);
+    mlp_hidden_layer_t(wt1, a.mlp_P + OFF_B1, act1, MLP_IN, act0, n, tid, DF_THREADS);
     __syncthreads();
-    mlp_hidden_layer(a.mlp_P + OFF_W2, a.mlp_P + OFF_B2, act0, MLP_H, nullptr, act1, n, tid, DF_THREADS);
+    mlp_hidden_layer_t(wt2, a.mlp_P + OFF_B2, act0, MLP_H, act1, n, tid, DF_THREADS);
     __syncthreads();
-    mlp_hidden_layer(a.mlp_P + OFF_W3, a.mlp_P + OFF_B3, act1, MLP_H, nullptr, act0, n, tid, DF_THREADS);
+    mlp_hidden_layer_t(wt3, a.mlp_P + OFF_B3, act1, MLP_H, act0, n, tid, DF_THREADS);
     __syncthreads();
     mlp_output_layer(a.mlp_P, act0, act1, n, tid, DF_THREADS);
     __syncthreads();

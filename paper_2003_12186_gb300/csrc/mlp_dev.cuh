@@ -52,6 +52,29 @@ __device__ inline void mlp_hidden_layer(const float *__restrict__ W, const float
   }
 }
 
+// The same layer with the weights transposed, WT[i][j] (shared memory): lanes of a warp
+// take consecutive j and read consecutive words, the input is broadcast.
+__device__ inline void mlp_hidden_layer_t(const float *WT, const float *__restrict__ b,
+                                          const float *in, int in_dim, float *out, int S, int tid,
+                                          int nthreads) {
+  for (int idx = tid; idx < S * MLP_H; idx += nthreads) {
+    const int s = idx >> 6, j = idx & (MLP_H - 1);
+    const float *x = in + s * in_dim;
+    float acc = b[j];
+    for (int i = 0; i < in_dim; i++) acc = fmaf(WT[i * MLP_H + j], x[i], acc);
+    out[idx] = gelu_f(acc);
+  }
+}
+
+// Copy W [64][in] of the packed parameters to WT [in][64].
+__device__ inline void mlp_stage_transposed(const float *__restrict__ W, int in_dim, float *WT,
+                                            int tid, int nthreads) {
+  for (int e = tid; e < MLP_H * in_dim; e += nthreads) {
+    const int j = e / in_dim, i = e % in_dim;
+    WT[i * MLP_H + j] = W[e];
+  }
+}
+
 // Output layer: y[s][o] = b4[o] + sum_j W4[o][j] a[s][j] (normalised output).
 __device__ inline void mlp_output_layer(const float *__restrict__ P, const float *a, float *y, int S,
                                         int tid, int nthreads) {

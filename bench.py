@@ -14,6 +14,13 @@ advanced by the batched executor (one launch per phase per step, autotuned strea
 variant, graph replay); the line also carries the same lattices stepped one by one
 ("plain per-simulation form") for comparison.
 
+--workload learned: 64 rigid-cylinder channels (512 x 128, D uniform in [16, 32], Re
+uniform in [10, 150], markers 1.5 lattice units apart, FP32) with the direct-forcing
+iteration run to the no-slip residual 1e-6 every step.  A network trained on samples the
+method generates (other channels, another seed) proposes the iteration's start; the line
+reports its end-to-end MLUPS and force passes per step next to the plain iteration
+(start zero) and the previous-step start, on the same channels.
+
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
 """
 from __future__ import annotations
@@ -48,7 +55,7 @@ def parse():
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="ellipse", choices=["ellipse", "batched"])
+    ap.add_argument("--workload", default="ellipse", choices=["ellipse", "batched", "learned"])
     ap.add_argument("--count", type=int, default=256, help="simulations of the batched sweep")
     a = ap.parse_args()
     if a.steps is None:
@@ -492,12 +499,95 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------- learned warm start
+def oracle_channel_rate(max_seconds):
+    """The FP64 oracle stepping one learned-workload channel (iteration to 1e-6)."""
+    from oracle import oracle as O
+    sim = W.learned_channels(1, 2)[0]
+    nx, ny = sim["nx"], sim["ny"]
+    o = O.Oracle(nx, ny, collision=O.MRT, tau=sim["tau"], s=W.mrt_rates(sim["tau"]),
+                 bc=O.BC_CHANNEL, u_max=sim["u_max"], jump=0)
+    y = np.arange(ny) + 0.5
+    o.init_equilibrium(None, np.repeat((4 * sim["u_max"] * y * (ny - y) / ny ** 2)[:, None], nx,
+                                       axis=1), None)
+    o.set_interface(sim["X"], model=O.DIRECT, moves=False, dX=sim["dX"], eta=2.0, mdf_iters=500,
+                    mdf_tol=1e-6, UD=np.zeros((sim["n"], 2)))
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < max_seconds:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    o.close()
+    return nx * ny * steps / dt / 1e6, steps, dt
+
+
+def run_learned(args):
+    import torch
+    from paper_2003_12186_gb300 import learned as LL
+
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.perf_counter()
+    X, T, _ = LL.generate(count=64, seed=1, spin_up=400, records=64, every=100)
+    gen_s = time.perf_counter() - t0
+    mlp, norm, rep = LL.train(X, T, epochs=30)
+    rep["generate_seconds"] = round(gen_s, 2)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ev = LL.evaluate(mlp, count=64, seed=2, spin_up=400, count_steps=32,
+                     timed_steps=max(args.steps, 32))
+    clk = clocks.stop()
+    sims = W.learned_channels(64, 2)
+    cells = sum(s["nx"] * s["ny"] for s in sims)
+    peak, peak_kind = peaks()
+    L, P = ev["mlp"], ev["plain"]
+    step_bytes = 2 * 9 * 4 * cells
+    achieved = step_bytes / (L["us_per_step"] * 1e-6) / 1e9
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, st, dt = oracle_channel_rate(10.0)
+        cpu = {"value": round(rate, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{st} FP64 oracle steps of one channel of the workload (force "
+                         f"iteration to 1e-6), {dt:.1f} s, one thread"}
+    if rank == 0:
+        out = {"metric": "MLUPS", "value": round(L["mlups"], 1), "unit": "MLUPS", "n_gpus": 1,
+               "steps": max(args.steps, 32), "warmup": 400,
+               "ms_per_step": round(L["us_per_step"] / 1e3, 5), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": "learned64_cylinder_channels_f32", "channels": 64,
+                          "lattice": [512, 128], "cells": cells, "residual_tol": 1e-6,
+                          "max_passes": 500, "markers_spacing": 1.5, "jump": 0,
+                          "l2": "inputs larger than L2"},
+               "learned": {"passes_per_step": round(L["passes_per_step"], 2),
+                           "worst_residual": L["worst_residual"], "capped": L["capped"]},
+               "plain_iteration": {"value": round(P["mlups"], 1), "unit": "MLUPS",
+                                   "passes_per_step": round(P["passes_per_step"], 2),
+                                   "worst_residual": P["worst_residual"],
+                                   "speedup_of_learned": round(L["mlups"] / P["mlups"], 3),
+                                   "passes_saved": round(1 - L["passes_per_step"] /
+                                                         P["passes_per_step"], 3)},
+               "previous_force_start": {"value": round(ev["previous"]["mlups"], 1),
+                                        "unit": "MLUPS",
+                                        "passes_per_step": round(ev["previous"]["passes_per_step"], 2)},
+               "training": rep,
+               "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                            "kernel": "whole step (the force iteration, one CTA per body, "
+                                      "dominates; the stream-collide is the HBM part)",
+                            "peak_source": peak_kind, "alg_bytes_per_step": step_bytes},
+               "cpu_baseline": cpu, "e2e": None, "clocks": clk,
+               "gpu_launches": 7 * max(args.steps, 32)}
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

@@ -177,9 +177,14 @@ int iilbm_get_timing(iilbm_t h, double *stream_collide_ms, int32_t *stream_colli
  *  IILBM_OPT_CUDA_GRAPH     replay blocks of steps from one captured CUDA graph;
  *  IILBM_OPT_OVERLAP        run the next step's interface phase on a second stream
  *                           while the current stream-collide runs;
- *  IILBM_OPT_VECTOR_KERNEL  vectorised stream-collide (else one node per thread).
+ *  IILBM_OPT_VECTOR_KERNEL  vectorised stream-collide (else one node per thread);
+ *  IILBM_OPT_FORCED_BLOCKS  blocks of the forced stream-collide, which stride over the
+ *                           flagged tiles (value > 0; 0 restores the default, two per
+ *                           SM): fewer blocks hold fewer of the SMs' registers while the
+ *                           lean stream-collide runs beside them.
  * Results are identical either way.  Synchronises the handle's stream. */
-enum { IILBM_OPT_CUDA_GRAPH = 0, IILBM_OPT_OVERLAP = 1, IILBM_OPT_VECTOR_KERNEL = 2 };
+enum { IILBM_OPT_CUDA_GRAPH = 0, IILBM_OPT_OVERLAP = 1, IILBM_OPT_VECTOR_KERNEL = 2,
+       IILBM_OPT_FORCED_BLOCKS = 3 };
 int iilbm_set_option(iilbm_t h, int32_t option, int32_t value);
 
 /* No-allocation read-out (the paper has no counterpart; this is a service of the
@@ -235,8 +240,8 @@ int iilbm_batch_synchronize(iilbm_batch_t b);
 
 /* ------------------------------------------------------- learned warm start
  * A small network proposes the starting force G^(0)_k of the direct-forcing iteration
- * from each marker's local features; the iteration with its stopping rule stays the
- * judge of the answer.  Features of marker k (30, FP32): for j = k-2 .. k+2 (cyclic)
+ * from each marker's local features; the iteration with its stopping rule still
+ * decides the answer.  Features of marker k (30, FP32): for j = k-2 .. k+2 (cyclic)
  *   U^D_j - U*_j (2), the outward unit normal (2), the signed curvature
  *   -(X_{j+1} - 2 X_j + X_{j-1}) . n_j / dX^2 (1), and Re (1).
  * Network: x -> (x - in_mean) * in_istd -> 3 x [64, GELU (erf form)] -> 2 ->

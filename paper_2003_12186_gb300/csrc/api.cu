@@ -539,6 +539,14 @@ int iilbm_set_option(iilbm_t h, int32_t option, int32_t value) {
     case IILBM_OPT_CUDA_GRAPH: h->use_graph = value != 0; break;
     case IILBM_OPT_OVERLAP: h->overlap = value != 0; break;
     case IILBM_OPT_VECTOR_KERNEL: h->vector_sc = value != 0; break;
+    case IILBM_OPT_FORCED_BLOCKS: {
+      if (value < 0) return IILBM_ERR_INVALID_ARG;
+      cudaDeviceProp prop;
+      CK(cudaGetDeviceProperties(&prop, h->device));
+      h->forced_grid = std::max(1, std::min(h->ntiles, value > 0 ? (int)value
+                                                                  : 2 * prop.multiProcessorCount));
+      break;
+    }
     default: return IILBM_ERR_INVALID_ARG;
   }
   drop_graph(h);

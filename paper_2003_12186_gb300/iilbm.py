@@ -24,7 +24,7 @@ SRT, MRT = 0, 1
 F64, F32, F16, BF16 = 0, 1, 2, 3
 BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL = 0, 1, 2
 SPRING, SPRING_REST, PRESCRIBED, DIRECT = 0, 1, 2, 3
-OPT_CUDA_GRAPH, OPT_OVERLAP, OPT_VECTOR_KERNEL = 0, 1, 2
+OPT_CUDA_GRAPH, OPT_OVERLAP, OPT_VECTOR_KERNEL, OPT_FORCED_BLOCKS = 0, 1, 2, 3
 WS_GIVEN, WS_PREVIOUS, WS_MLP = 0, 1, 2
 MLP_PARAMS, MLP_FEATURES = 10434, 30
 STORAGE = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}

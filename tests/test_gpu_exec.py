@@ -99,3 +99,22 @@ def test_timing_counts_launches_in_graph_and_eager_modes():
     g.step(7)
     ms, n, k = g.iilbm_get_timing()
     assert n == 7 and ms > 0
+
+
+def test_forced_blocks_option_leaves_results_unchanged():
+    """The forced stream-collide's grid only changes which block takes which flagged
+    tile: populations agree with the default grid's to FP32 rounding (the interface
+    phase accumulates with atomics, so two runs agree to rounding, not bitwise)."""
+    w = W.ellipse_scaled(256, "f32")
+    gs = []
+    for blocks in (0, 3):
+        g = iilbm.Lattice(256, 256, collision=iilbm.MRT, storage="f32", tau=w["tau"],
+                          s=W.mrt_rates(w["tau"]))
+        g.set_option(iilbm.OPT_FORCED_BLOCKS, blocks)
+        g.set_interface(w["X"], model=iilbm.SPRING, stiffness=w["kappa"], dX=w["dX"])
+        g.step(40)
+        gs.append(g)
+    a, b = gs[0].get_populations(), gs[1].get_populations()
+    assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max() and np.abs(a).max() > 0
+    with pytest.raises(iilbm.IilbmError):
+        gs[0].set_option(iilbm.OPT_FORCED_BLOCKS, -1)

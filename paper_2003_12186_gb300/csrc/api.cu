@@ -423,15 +423,21 @@ bool pipelined(const iilbm_lattice *h) {
 // n & 1).  Main stream: the lean stream-collide (every tile without a jump or force).
 // Second stream (highest priority), forked at the start of the step: the forced
 // stream-collide of the flagged tiles, which also leaves the collision velocity there,
-// the interpolation from it with the marker move (X^{n+1}), then the interface phase of
-// state n + 1 in buffer (n+1) & 1; it joins before the step ends.  Without overlap the
-// same kernels run in that order on the main stream.  Safe inside stream capture.
+// the interpolation from it with the marker move (X^{n+1}), then (unless the body is
+// directly forced, whose interface phase waits for the next state's force iteration)
+// the interface phase of state n + 1 in buffer (n+1) & 1; it joins before the step
+// ends.  Without overlap the same kernels run in that order on the main stream.  Safe
+// inside stream capture.
 // ev_slot: index of the start event of the lean stream-collide timing pair, or -1.
 int one_step(iilbm_lattice *h, int ev_slot) {
   int rc;
   const bool pipe = pipelined(h);
-  cudaStream_t s2 = pipe ? h->side : h->stream;
-  if (pipe) {
+  // the forced stream-collide and the interpolation go to the side stream whenever
+  // overlap is on; the next level's interface phase only when it does not have to wait
+  // for the next state (direct forcing needs it, so it runs in the next prepare)
+  const bool fork = h->overlap && h->nm > 0;
+  cudaStream_t s2 = fork ? h->side : h->stream;
+  if (fork) {
     CK(cudaEventRecord(h->ev_fork, h->stream));
     CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
   }
@@ -445,6 +451,8 @@ int one_step(iilbm_lattice *h, int ev_slot) {
   if (pipe) {
     rc = launch_interface_phase(h, (int)((h->step + 1) & 1), h->side);  // state n + 1
     if (rc) return rc;
+  }
+  if (fork) {
     CK(cudaEventRecord(h->ev_join, h->side));
     CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   }

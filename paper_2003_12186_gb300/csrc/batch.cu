@@ -357,8 +357,9 @@ long long batch_kernels_per_step(const iilbm_batch *B) {
 int batch_one_step(iilbm_batch *B, int ev_pair) {
   int rc;
   const bool pipe = batch_pipelined(B);
-  cudaStream_t s2 = pipe ? B->side : B->stream;
-  if (pipe) {
+  const bool fork = B->any_iface;  // forced + interpolation beside the lean kernel
+  cudaStream_t s2 = fork ? B->side : B->stream;
+  if (fork) {
     CKB(cudaEventRecord(B->ev_fork, B->stream));
     CKB(cudaStreamWaitEvent(B->side, B->ev_fork, 0));
   }
@@ -366,8 +367,8 @@ int batch_one_step(iilbm_batch *B, int ev_pair) {
   if ((rc = launch_batch_sc(B, s2))) return rc;
   if (ev_pair >= 0) CKB(cudaEventRecord(B->ev[ev_pair + 1], B->stream));
   if ((rc = launch_batch_interp(B, s2))) return rc;
-  if (pipe) {
-    if ((rc = launch_batch_interface(B, (int)((B->step + 1) & 1), B->side))) return rc;
+  if (pipe && (rc = launch_batch_interface(B, (int)((B->step + 1) & 1), B->side))) return rc;
+  if (fork) {
     CKB(cudaEventRecord(B->ev_join, B->side));
     CKB(cudaStreamWaitEvent(B->stream, B->ev_join, 0));
   }

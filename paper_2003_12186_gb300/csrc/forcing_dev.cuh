@@ -32,14 +32,14 @@ struct DfArgs {
 
 constexpr int DF_THREADS = 1024;
 
-// Shared memory of the force iteration: the window fields u*, 1/(2 rho), g (5 W values
-// of T), the stencil of every marker (16 n weights T and window indices), and the marker
+// Shared memory of the force iteration: the window fields u*, 1/(2 rho) and two force
+// fields g (7 W values of T), the stencil of every marker (16 n weights T and window indices), and the marker
 // arrays G, U, U^D, G dX and U* (2 n values of T each).
 // With the network's proposal (mlp), the per-marker feature blocks and two activation
 // buffers (6 + 2 x 64 floats per marker) follow.
 template <typename T>
 __host__ __device__ inline size_t df_smem_bytes(int W, int n, bool mlp = false) {
-  size_t b = 5 * (size_t)W * sizeof(T);
+  size_t b = 7 * (size_t)W * sizeof(T);
   b += 16 * (size_t)n * (sizeof(T) + sizeof(int));
   b = (b + 15) & ~(size_t)15;
   b += 10 * (size_t)n * sizeof(T);
@@ -82,9 +82,11 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   T *usx = reinterpret_cast<T *>(smem_raw);
   T *usy = usx + W;
   T *h2r = usy + W;  // 1 / (2 rho)
-  T *gx = h2r + W;
+  T *gx = h2r + W;  // force field of the even passes
   T *gy = gx + W;
-  T *pw = gy + W;                                   // stencil weights [16 n]
+  T *gx2 = gy + W;  // force field of the odd passes
+  T *gy2 = gx2 + W;
+  T *pw = gy2 + W;                                  // stencil weights [16 n]
   int *pc = reinterpret_cast<int *>(pw + 16 * n);   // stencil window indices [16 n]
   size_t off = (size_t)(reinterpret_cast<unsigned char *>(pc + 16 * n) - smem_raw);
   off = (off + 15) & ~(size_t)15;
@@ -139,6 +141,8 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
     h2r[c] = hr;
     gx[c] = T(0);
     gy[c] = T(0);
+    gx2[c] = T(0);
+    gy2[c] = T(0);
   }
   // stencils, one thread per marker
   for (int k = tid; k < n; k += DF_THREADS) {
@@ -223,23 +227,30 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
     __syncthreads();
   }
 
+  // the start G^(0) spread (Eq. 17) into the field of pass 0
+  for (int q = tid; q < npairs; q += DF_THREADS) {
+    const T w = pw[q];
+    if (w != T(0)) {
+      const int k = q >> 4, c = pc[q];
+      atomicAdd(&gx[c], GdX[2 * k] * w);
+      atomicAdd(&gy[c], GdX[2 * k + 1] * w);
+    }
+  }
+  __syncthreads();
+
+  // Each pass: interpolate u* + g / (2 rho) (Eq. 20) from the pass's field and take the
+  // residual (clearing the other field meanwhile); then, unless converged, update
+  // G += eta (U^D - U) (Eq. 18) and spread the new G dX into the other field -- the 16
+  // lanes of a marker form the same update, its first lane stores it.  Two barriers.
   int it = 0;
   B rm = 0;
   // stop once the residual's bit pattern is below the tolerance's (both non-negative)
   const bool stop_on_tol = a.tol > 0.0;
   const B tol_bits = BitsOf<T>::of(T(a.tol));
   for (it = 0; it < a.max_iters; it++) {
-    // spread G dX (Eq. 17); g is zero here
-    for (int q = tid; q < npairs; q += DF_THREADS) {
-      const T w = pw[q];
-      if (w != T(0)) {
-        const int k = q >> 4, c = pc[q];
-        atomicAdd(&gx[c], GdX[2 * k] * w);
-        atomicAdd(&gy[c], GdX[2 * k + 1] * w);
-      }
-    }
-    __syncthreads();
-    // interpolate u* + g / (2 rho) (Eq. 20) and the marker's residual |U^D - U|
+    const bool odd_pass = it & 1;
+    const T *fx = odd_pass ? gx2 : gx, *fy = odd_pass ? gy2 : gy;
+    T *ox = odd_pass ? gx : gx2, *oy = odd_pass ? gy : gy2;
     B r = 0;
     for (int base = 0; base < npairs; base += DF_THREADS) {
       const int q = base + tid;
@@ -247,8 +258,8 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
       if (q < npairs) {
         const int c = pc[q];
         const T w = pw[q];
-        sx = (usx[c] + gx[c] * h2r[c]) * w;
-        sy = (usy[c] + gy[c] * h2r[c]) * w;
+        sx = (usx[c] + fx[c] * h2r[c]) * w;
+        sy = (usy[c] + fy[c] * h2r[c]) * w;
       }
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) {
@@ -263,23 +274,48 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
                        BitsOf<T>::of(fabs(UDk[2 * k + 1] - sy))));
       }
     }
+    for (int c = tid; c < W; c += DF_THREADS) {
+      ox[c] = T(0);
+      oy[c] = T(0);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) r = max(r, (B)__shfl_xor_sync(0xffffffffu, r, o));
     if (lane == 0) red[tid >> 5] = r;
     __syncthreads();
-    // every thread reduces the warp maxima itself: no second barrier
+    // every thread reduces the warp maxima itself
     rm = 0;
 #pragma unroll 8
     for (int w = 0; w < DF_THREADS / 32; w++) rm = max(rm, red[w]);
     if (stop_on_tol && rm < tol_bits) break;  // uniform
-    for (int c = tid; c < W; c += DF_THREADS) {
-      gx[c] = T(0);
-      gy[c] = T(0);
-    }
-    for (int k = tid; k < 2 * n; k += DF_THREADS) {
-      Gk[k] += eta * (UDk[k] - Uk[k]);
-      if (sizeof(T) == 8) GdX[k] = T((double)Gk[k] * a.dX);
-      else GdX[k] = Gk[k] * dX;
+    for (int base = 0; base < npairs; base += DF_THREADS) {
+      const int q = base + tid;
+      const int k = q >> 4;
+      T nx = T(0), ny = T(0);
+      if (q < npairs) {
+        nx = Gk[2 * k] + eta * (UDk[2 * k] - Uk[2 * k]);
+        ny = Gk[2 * k + 1] + eta * (UDk[2 * k + 1] - Uk[2 * k + 1]);
+      }
+      __syncwarp();  // every lane of the marker has read the old G
+      if (q < npairs) {
+        if ((q & 15) == 0) {
+          Gk[2 * k] = nx;
+          Gk[2 * k + 1] = ny;
+        }
+        T px, py;
+        if (sizeof(T) == 8) {
+          px = T((double)nx * a.dX);
+          py = T((double)ny * a.dX);
+        } else {
+          px = nx * dX;
+          py = ny * dX;
+        }
+        const T w = pw[q];
+        if (w != T(0)) {
+          const int c = pc[q];
+          atomicAdd(&ox[c], px * w);
+          atomicAdd(&oy[c], py * w);
+        }
+      }
     }
     __syncthreads();
   }

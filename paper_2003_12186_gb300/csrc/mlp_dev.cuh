@@ -66,12 +66,13 @@ __device__ inline void mlp_hidden_layer_t(const float *WT, const float *__restri
   }
 }
 
-// Copy W [64][in] of the packed parameters to WT [in][64].
+// Copy W [64][in] of the packed parameters to WT [in][64]: consecutive threads write
+// consecutive words of WT (no bank conflicts), reading W through the cache.
 __device__ inline void mlp_stage_transposed(const float *__restrict__ W, int in_dim, float *WT,
                                             int tid, int nthreads) {
   for (int e = tid; e < MLP_H * in_dim; e += nthreads) {
-    const int j = e / in_dim, i = e % in_dim;
-    WT[i * MLP_H + j] = W[e];
+    const int i = e >> 6, j = e & (MLP_H - 1);
+    WT[e] = W[j * in_dim + i];
   }
 }
 
@@ -90,21 +91,25 @@ __device__ inline void mlp_output_layer(const float *__restrict__ P, const float
 
 // Features block of marker j of a closed counter-clockwise polygon of n markers:
 // dU = U^D - U* (2), outward unit normal (2), signed curvature -(d2 X . n) / dX^2, Re.
-// Positions and their differences in FP64; the block in FP32.
+// The position differences (small differences of large numbers) in FP64, the rest in
+// FP32: GB300 charges a warp's full FP64 time for the few lanes that hold a marker.
 __device__ inline void marker_feature_block(const double *__restrict__ X, int n, int j, double dX,
                                             float dUx, float dUy, float re, float *blk) {
   const int jp = j + 1 == n ? 0 : j + 1, jm = j == 0 ? n - 1 : j - 1;
   const double x = X[2 * j], y = X[2 * j + 1];
   const double xp = X[2 * jp], yp = X[2 * jp + 1], xm = X[2 * jm], ym = X[2 * jm + 1];
-  const double tx = xp - xm, ty = yp - ym;
-  const double tl = sqrt(tx * tx + ty * ty);
-  const double nx = ty / tl, ny = -tx / tl;
-  const double d2x = (xp - x) - (x - xm), d2y = (yp - y) - (y - ym);
+  const float ax = (float)(xp - x), ay = (float)(yp - y);  // X_{j+1} - X_j
+  const float bx = (float)(x - xm), by = (float)(y - ym);  // X_j - X_{j-1}
+  const float tx = ax + bx, ty = ay + by;                  // X_{j+1} - X_{j-1}
+  const float il = rsqrtf(tx * tx + ty * ty);
+  const float nx = ty * il, ny = -tx * il;
+  const float d2x = (float)((xp - x) - (x - xm)), d2y = (float)((yp - y) - (y - ym));
+  const float idx2 = 1.0f / (float)(dX * dX);
   blk[0] = dUx;
   blk[1] = dUy;
-  blk[2] = (float)nx;
-  blk[3] = (float)ny;
-  blk[4] = (float)(-(d2x * nx + d2y * ny) / (dX * dX));
+  blk[2] = nx;
+  blk[3] = ny;
+  blk[4] = -(d2x * nx + d2y * ny) * idx2;
   blk[5] = re;
 }
 

@@ -88,11 +88,11 @@ __global__ void __launch_bounds__(256, MINB)
       const int tx = (tile % sd.geo.ntx) * TILE_X, ty = (tile / sd.geo.ntx) * TILE_Y;
       if (NPT > 1) {
         for (int sub = 0; sub < TILE_X; sub += 32 * NPT)
-          sc_vec_block<S, COLL, ODD, BC, false, NPT>((S *)sd.A, nullptr, nullptr, nullptr,
+          sc_vec_rows<S, COLL, ODD, BC, false, NPT>((S *)sd.A, nullptr, nullptr, nullptr,
                                                      sd.geo, sd.p, sd.status, tx + sub, ty);
       } else {
         for (int sub = 0; sub < TILE_X; sub += 32)
-          sc_scalar_block<S, COLL, ODD, BC, false>((S *)sd.A, nullptr, nullptr, nullptr, sd.geo,
+          sc_scalar_rows<S, COLL, ODD, BC, false>((S *)sd.A, nullptr, nullptr, nullptr, sd.geo,
                                                    sd.p, sd.status, tx + sub, ty);
       }
     }
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256, 2)
     const int tile = sd.list[b][t];
     const int tx = (tile % sd.geo.ntx) * TILE_X, ty = (tile / sd.geo.ntx) * TILE_Y;
     for (int sub = 0; sub < TILE_X; sub += W)
-      sc_vec_block<S, COLL, ODD, BC, true>((S *)sd.A, (float *)sd.J[b], (float *)sd.g[b],
+      sc_vec_rows<S, COLL, ODD, BC, true>((S *)sd.A, (float *)sd.J[b], (float *)sd.g[b],
                                            (float *)sd.uf, sd.geo, sd.p, sd.status, tx + sub, ty);
   }
 }

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(32 * TILE_Y)
                      const CollP<typename Store<S>::T> p, int *status) {
   const int xb = blockIdx.x * 32, yb = blockIdx.y * TILE_Y;
   if (flags[blockIdx.y * geo.ntx + xb / TILE_X] == *tag) return;  // uniform per block
-  sc_scalar_block<S, COLL, ODD, BC, false>(A, nullptr, nullptr, nullptr, geo, p, status, xb, yb);
+  sc_scalar_rows<S, COLL, ODD, BC, false>(A, nullptr, nullptr, nullptr, geo, p, status, xb, yb);
 }
 
 // At least three resident blocks per SM (<= 85 registers): the odd step would otherwise
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(32 * VEC_ROWS, 3)
   constexpr int W = 32 * Vec<S>::V;  // nodes per warp row
   const int xb = blockIdx.x * W, yb = blockIdx.y * VEC_ROWS;
   if (flags[blockIdx.y * geo.ntx + xb / TILE_X] == *tag) return;  // uniform per block
-  sc_vec_block<S, COLL, ODD, BC, false>(A, nullptr, nullptr, nullptr, geo, p, status, xb, yb);
+  sc_vec_rows<S, COLL, ODD, BC, false>(A, nullptr, nullptr, nullptr, geo, p, status, xb, yb);
 }
 
 // Forced kernels: blocks stride over the list of flagged tiles of this step.
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(32 * TILE_Y)
     const int tile = list[t];
     const int tx = (tile % geo.ntx) * TILE_X, ty = (tile / geo.ntx) * TILE_Y;
     for (int sub = 0; sub < TILE_X; sub += 32)
-      sc_scalar_block<S, COLL, ODD, BC, true>(A, Jf, gf, uf, geo, p, status, tx + sub, ty);
+      sc_scalar_rows<S, COLL, ODD, BC, true>(A, Jf, gf, uf, geo, p, status, tx + sub, ty);
   }
 }
 
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(32 * VEC_ROWS)
     const int tile = list[t];
     const int tx = (tile % geo.ntx) * TILE_X, ty = (tile / geo.ntx) * TILE_Y;
     for (int sub = 0; sub < TILE_X; sub += W)
-      sc_vec_block<S, COLL, ODD, BC, true>(A, Jf, gf, uf, geo, p, status, tx + sub, ty);
+      sc_vec_rows<S, COLL, ODD, BC, true>(A, Jf, gf, uf, geo, p, status, tx + sub, ty);
   }
 }
 

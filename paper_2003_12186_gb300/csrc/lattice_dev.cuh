@@ -174,8 +174,8 @@ __device__ inline void ldT(const T *p, T *o) {
 // One node per thread on a 32 x TILE_Y sub-block whose first node is (xb, yb).  BC is
 // IILBM_BC_PERIODIC, IILBM_BC_WALLS_Y (periodic x, halfway bounce-back in y) or
 // IILBM_BC_CHANNEL (walls in y, ghost columns in x filled by the channel boundary).
-template <typename S, int COLL, bool ODD, int BC, bool FORCED, typename GG = Geom,
-          typename PP = CollP<typename Store<S>::T>>
+template <typename S, int COLL, bool ODD, int BC, bool FORCED, bool YWALL = true,
+          typename GG = Geom, typename PP = CollP<typename Store<S>::T>>
 __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
                                                 typename Store<S>::T *__restrict__ Jf,
                                                 typename Store<S>::T *__restrict__ gf,
@@ -194,7 +194,7 @@ __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
   if (BC == IILBM_BC_PERIODIC) {
     ym = y == 0 ? geo.ny - 1 : ym;
     yp = y == geo.ny - 1 ? 0 : yp;
-  } else {
+  } else if (YWALL) {  // otherwise the caller guarantees 1 <= y <= ny - 2
     wall_m = y == 0;
     wall_p = y == geo.ny - 1;
   }
@@ -250,7 +250,7 @@ __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
 // of a row fetch / write that element with a scalar access instead, wrapping around
 // the periodic row.  Requires nx % V == 0.  Every lane of the warp must call this.
 template <typename S, int COLL, bool ODD, int BC, bool FORCED, int V = Vec<S>::V,
-          typename GG = Geom, typename PP = CollP<typename Store<S>::T>>
+          bool YWALL = true, typename GG = Geom, typename PP = CollP<typename Store<S>::T>>
 __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
                                              typename Store<S>::T *__restrict__ Jf,
                                              typename Store<S>::T *__restrict__ gf,
@@ -270,7 +270,7 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
   if (BC == IILBM_BC_PERIODIC) {
     ym = y == 0 ? geo.ny - 1 : ym;
     yp = y == geo.ny - 1 ? 0 : yp;
-  } else {
+  } else if (YWALL) {  // otherwise the caller guarantees 1 <= y <= ny - 2
     wall_m = y == 0;
     wall_p = y == geo.ny - 1;
   }
@@ -401,6 +401,37 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
 }
 
 constexpr int VEC_ROWS = TILE_Y;  // warps (rows) per block of the vectorised kernels
+
+// A tile row that holds no wall row (neither y = 0 nor y = ny - 1) runs the stream-
+// collide compiled without the wall cases (YWALL = false): with walls in y, the general
+// code tests every population plane of every row for a wall, which the odd step pays
+// for in instructions and registers although only two rows are walls.  yb is the tile
+// row's first row; the test is uniform per block.
+template <typename S, int COLL, bool ODD, int BC, bool FORCED, int V = Vec<S>::V,
+          typename GG = Geom, typename PP = CollP<typename Store<S>::T>>
+__device__ __forceinline__ void sc_vec_rows(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
+                                            typename Store<S>::T *__restrict__ gf,
+                                            typename Store<S>::T *__restrict__ uf, const GG &geo,
+                                            const PP &p, int *status, int xb, int yb) {
+  if (BC != IILBM_BC_PERIODIC && (yb == 0 || yb + VEC_ROWS >= geo.ny))
+    sc_vec_block<S, COLL, ODD, BC, FORCED, V, true>(A, Jf, gf, uf, geo, p, status, xb, yb);
+  else
+    sc_vec_block<S, COLL, ODD, BC, FORCED, V, false>(A, Jf, gf, uf, geo, p, status, xb, yb);
+}
+
+template <typename S, int COLL, bool ODD, int BC, bool FORCED, typename GG = Geom,
+          typename PP = CollP<typename Store<S>::T>>
+__device__ __forceinline__ void sc_scalar_rows(S *__restrict__ A,
+                                               typename Store<S>::T *__restrict__ Jf,
+                                               typename Store<S>::T *__restrict__ gf,
+                                               typename Store<S>::T *__restrict__ uf,
+                                               const GG &geo, const PP &p, int *status, int xb,
+                                               int yb) {
+  if (BC != IILBM_BC_PERIODIC && (yb == 0 || yb + TILE_Y >= geo.ny))
+    sc_scalar_block<S, COLL, ODD, BC, FORCED, true>(A, Jf, gf, uf, geo, p, status, xb, yb);
+  else
+    sc_scalar_block<S, COLL, ODD, BC, FORCED, false>(A, Jf, gf, uf, geo, p, status, xb, yb);
+}
 
 // Inflow / outflow of one channel row on the streamed state (see lattice.cu).
 template <typename S>

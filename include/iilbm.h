@@ -225,6 +225,7 @@ int iilbm_batch_step(iilbm_batch_t b, int32_t n);
  *   0 / 1  NPT 4, 3 blocks, per item / persistent     2 / 3  NPT 4, 2 blocks
  *   4 / 5  NPT 2, 3 blocks                            6 / 7  NPT 2, 2 blocks
  *   8 / 9  NPT 1, 3 blocks
+ *   10 / 11  NPT 4, 3 blocks in the even step and 2 in the odd one
  * Results agree to rounding (the arithmetic is the same; contraction may differ). */
 int iilbm_batch_set_variant(iilbm_batch_t b, int32_t variant);
 /* Autotuner: time every variant for `steps` (rounded up to whole graph replays) real

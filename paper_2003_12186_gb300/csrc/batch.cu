@@ -51,13 +51,18 @@ struct SimDev {
 // resident blocks per SM the registers are budgeted for (3: at most 80 registers, with
 // some spilling at 2 and 4 nodes per thread; 2: no spilling), and grid shape (one block
 // per work item, or a persistent grid of resident blocks x SMs striding over the items).
+// The odd step needs more registers than the even one (neighbour shifts, edge stores):
+// the last two variants budget 3 blocks per SM for the even step and 2 (no spilling)
+// for the odd one.
 struct BatchVariant {
   int npt, minb;
   bool persistent;
+  int minb_odd;  // 0: as minb
 };
 constexpr BatchVariant BATCH_VARIANTS[] = {
-    {4, 3, false}, {4, 3, true}, {4, 2, false}, {4, 2, true}, {2, 3, false},
-    {2, 3, true},  {2, 2, false}, {2, 2, true}, {1, 3, false}, {1, 3, true}};
+    {4, 3, false, 0}, {4, 3, true, 0}, {4, 2, false, 0}, {4, 2, true, 0}, {2, 3, false, 0},
+    {2, 3, true, 0},  {2, 2, false, 0}, {2, 2, true, 0}, {1, 3, false, 0}, {1, 3, true, 0},
+    {4, 3, false, 2}, {4, 3, true, 2}};
 constexpr int BV_COUNT = sizeof(BATCH_VARIANTS) / sizeof(BATCH_VARIANTS[0]);
 
 // ----------------------------------------------------------------- kernels
@@ -244,9 +249,10 @@ void lean_launch_v(iilbm_batch *B, bool persistent) {
 template <typename S, int COLL, bool ODD, int BC>
 void lean_launch(iilbm_batch *B) {
   const BatchVariant v = BATCH_VARIANTS[B->variant];
-  if (v.npt == 4 && v.minb == 3) lean_launch_v<S, COLL, ODD, BC, 4, 3>(B, v.persistent);
+  const int minb = ODD && v.minb_odd ? v.minb_odd : v.minb;
+  if (v.npt == 4 && minb == 3) lean_launch_v<S, COLL, ODD, BC, 4, 3>(B, v.persistent);
   else if (v.npt == 4) lean_launch_v<S, COLL, ODD, BC, 4, 2>(B, v.persistent);
-  else if (v.npt == 2 && v.minb == 3) lean_launch_v<S, COLL, ODD, BC, 2, 3>(B, v.persistent);
+  else if (v.npt == 2 && minb == 3) lean_launch_v<S, COLL, ODD, BC, 2, 3>(B, v.persistent);
   else if (v.npt == 2) lean_launch_v<S, COLL, ODD, BC, 2, 2>(B, v.persistent);
   else lean_launch_v<S, COLL, ODD, BC, 1, 3>(B, v.persistent);
 }

@@ -102,7 +102,8 @@ SIGNATURES = {
 }
 
 # stream-collide variants of a batch (iilbm_batch_set_variant)
-BATCH_VARIANTS = tuple(f"npt{n}-b{b}-{g}" for n, b in ((4, 3), (4, 2), (2, 3), (2, 2), (1, 3))
+BATCH_VARIANTS = tuple(f"npt{n}-b{b}-{g}" for n, b in ((4, 3), (4, 2), (2, 3), (2, 2), (1, 3),
+                                                       (4, "3o2"))
                        for g in ("per-item", "persistent"))
 
 

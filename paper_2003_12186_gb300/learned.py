@@ -127,6 +127,7 @@ def evaluate(mlp, count=64, seed=2, spin_up=400, count_steps=32, timed_steps=256
                 g.iilbm_set_warm_start_mlp(mlp, s["re"])
         with iilbm.Batch(lat) as B:
             B.step(spin_up)
+            B.autotune(32)  # the stream-collide variant for these lattices (the run advances)
             B.synchronize()
             passes, worst, capped = [], 0.0, 0
             for _ in range(count_steps):

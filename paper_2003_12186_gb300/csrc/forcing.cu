@@ -56,7 +56,7 @@ DfArgs df_args(const iilbm_lattice *h) {
   a.bodyy = h->cfg.body[1];
   a.rho0 = h->cfg.rho0;
   a.ws_mode = h->ws_mode;
-  a.mlp_P = h->mlp ? mlp_params(h->mlp) : nullptr;
+  a.mlp_P = h->mlp ? mlp_params_transposed(h->mlp) : nullptr;
   a.mlp_norm = h->mlp ? mlp_norm(h->mlp) : nullptr;
   a.re = h->re;
   return a;

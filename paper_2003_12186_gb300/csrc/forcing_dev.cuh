@@ -25,7 +25,8 @@ struct DfArgs {
   double bodyx, bodyy, rho0;
   int ws_mode;            // WS_GIVEN: G0; WS_PREVIOUS: the G of the last iteration (in G);
                           // WS_MLP: the network's proposal from the step's features
-  const float *mlp_P;     // WS_MLP: packed parameters, normalisation, Re feature
+  const float *mlp_P;     // WS_MLP: packed parameters (W1..W3 transposed), normalisation,
+                          // Re feature
   const float *mlp_norm;
   float re;
 };
@@ -97,12 +98,14 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   T *Us = GdX + 2 * n;                              // U*
   size_t off2 = (size_t)(reinterpret_cast<unsigned char *>(Us + 2 * n) - smem_raw);
   off2 = (off2 + 15) & ~(size_t)15;
-  float *blk = reinterpret_cast<float *>(smem_raw + off2);  // WS_MLP scratch
-  float *act0 = blk + MLP_BLOCK * n;
-  float *act1 = act0 + MLP_H * n;
-  float *wt1 = act1 + MLP_H * n;  // W1, W2, W3 transposed
+  // WS_MLP scratch: the transposed weights first (16-byte aligned for 16-byte loads),
+  // then the per-marker feature blocks and two activation buffers
+  float *wt1 = reinterpret_cast<float *>(smem_raw + off2);
   float *wt2 = wt1 + MLP_IN * MLP_H;
   float *wt3 = wt2 + MLP_H * MLP_H;
+  float *blk = wt3 + MLP_H * MLP_H;
+  float *act0 = blk + MLP_BLOCK * n;
+  float *act1 = act0 + MLP_H * n;
   __shared__ B red[DF_THREADS / 32];
   __shared__ T cst[6];  // 2^-k, rho0, body force, eta, dX: converted once, by one thread
   const int tid = threadIdx.x, lane = tid & 31;
@@ -205,9 +208,10 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
                            (float)(UDk[2 * j + 1] - Us[2 * j + 1]), a.re, blk + MLP_BLOCK * j);
     __syncthreads();
     for (int k = tid; k < n; k += DF_THREADS) mlp_gather_input(blk, n, k, a.mlp_norm, act1 + MLP_IN * k);
-    mlp_stage_transposed(a.mlp_P + OFF_W1, MLP_IN, wt1, tid, DF_THREADS);
-    mlp_stage_transposed(a.mlp_P + OFF_W2, MLP_H, wt2, tid, DF_THREADS);
-    mlp_stage_transposed(a.mlp_P + OFF_W3, MLP_H, wt3, tid, DF_THREADS);
+    // mlp_P holds W1, W2, W3 already transposed to [in][64]
+    mlp_copy4(a.mlp_P + OFF_W1, wt1, MLP_IN * MLP_H, tid, DF_THREADS);
+    mlp_copy4(a.mlp_P + OFF_W2, wt2, MLP_H * MLP_H, tid, DF_THREADS);
+    mlp_copy4(a.mlp_P + OFF_W3, wt3, MLP_H * MLP_H, tid, DF_THREADS);
     __syncthreads();
     mlp_hidden_layer_t(wt1, a.mlp_P + OFF_B1, act1, MLP_IN, act0, n, tid, DF_THREADS);
     __syncthreads();

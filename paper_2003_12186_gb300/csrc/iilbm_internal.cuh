@@ -213,6 +213,7 @@ size_t direct_forcing_smem(const iilbm_lattice *h, int ww, int wh, int n);
 struct DfArgs;
 DfArgs df_args(const iilbm_lattice *h);
 const float *mlp_params(const struct iilbm_mlp *M);
+const float *mlp_params_transposed(const struct iilbm_mlp *M);
 const float *mlp_norm(const struct iilbm_mlp *M);
 int mlp_device(const struct iilbm_mlp *M);
 int prepare_lattice(iilbm_lattice *h);

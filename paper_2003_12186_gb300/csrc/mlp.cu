@@ -201,6 +201,22 @@ __global__ void __launch_bounds__(MLP_THREADS)
   }
 }
 
+// PT: the packed parameters with W1, W2, W3 stored [in][64] (biases, W4, b4 as in P).
+__global__ void k_mlp_transposed(const float *__restrict__ P, float *__restrict__ PT) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= MLP_NPARAM) return;
+  int off = -1, in_dim = 0;
+  if (e >= OFF_W1 && e < OFF_B1) off = OFF_W1, in_dim = MLP_IN;
+  else if (e >= OFF_W2 && e < OFF_B2) off = OFF_W2, in_dim = MLP_H;
+  else if (e >= OFF_W3 && e < OFF_B3) off = OFF_W3, in_dim = MLP_H;
+  if (off < 0) {
+    PT[e] = P[e];
+  } else {
+    const int r = e - off, i = r >> 6, j = r & (MLP_H - 1);  // destination [i][j]
+    PT[e] = P[off + j * in_dim + i];
+  }
+}
+
 }  // namespace iilbm
 
 using namespace iilbm;
@@ -210,6 +226,7 @@ struct iilbm_mlp {
   cudaStream_t stream;
   bool own_stream;
   float *P, *m, *v, *norm;
+  float *PT;  // P with W1, W2, W3 transposed to [in][64] (for the direct-forcing CTA)
   int t;  // Adam steps taken
   float *partial, *loss;
   int cap_parts;
@@ -258,10 +275,17 @@ int to_device(const V *src, size_t count, cudaStream_t s, V **dst) {
   return IILBM_OK;
 }
 
+// Rebuild the transposed copy after the parameters change (stream-ordered).
+int refresh_transposed(iilbm_mlp *M) {
+  k_mlp_transposed<<<(MLP_NPARAM + 255) / 256, 256, 0, M->stream>>>(M->P, M->PT);
+  return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
+}
+
 }  // namespace
 
 namespace iilbm {
 const float *mlp_params(const iilbm_mlp *M) { return M->P; }
+const float *mlp_params_transposed(const iilbm_mlp *M) { return M->PT; }
 const float *mlp_norm(const iilbm_mlp *M) { return M->norm; }
 int mlp_device(const iilbm_mlp *M) { return M->device; }
 }  // namespace iilbm
@@ -282,6 +306,7 @@ int iilbm_mlp_create(iilbm_mlp_t *out, void *stream) {
   if (!M) return IILBM_ERR_OOM;
   M->device = dev;
   bool ok = cudaMalloc(&M->P, MLP_NPARAM * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&M->PT, MLP_NPARAM * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&M->m, MLP_NPARAM * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&M->v, MLP_NPARAM * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&M->norm, MLP_NORM * sizeof(float)) == cudaSuccess;
@@ -296,6 +321,7 @@ int iilbm_mlp_create(iilbm_mlp_t *out, void *stream) {
     for (int i = 0; i < MLP_IN; i++) nm[NORM_IN_ISTD + i] = 1.0f;
     nm[NORM_OUT_SCALE] = nm[NORM_OUT_SCALE + 1] = 1.0f;
     ok = cudaMemsetAsync(M->P, 0, MLP_NPARAM * sizeof(float), M->stream) == cudaSuccess &&
+         cudaMemsetAsync(M->PT, 0, MLP_NPARAM * sizeof(float), M->stream) == cudaSuccess &&
          cudaMemsetAsync(M->m, 0, MLP_NPARAM * sizeof(float), M->stream) == cudaSuccess &&
          cudaMemsetAsync(M->v, 0, MLP_NPARAM * sizeof(float), M->stream) == cudaSuccess &&
          cudaMemcpy(M->norm, nm.data(), MLP_NORM * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -313,7 +339,7 @@ int iilbm_mlp_create(iilbm_mlp_t *out, void *stream) {
 int iilbm_mlp_destroy(iilbm_mlp_t M) {
   if (!M) return IILBM_ERR_INVALID_ARG;
   if (M->stream) cudaStreamSynchronize(M->stream);
-  void *bufs[] = {M->P, M->m, M->v, M->norm, M->partial, M->loss};
+  void *bufs[] = {M->P, M->PT, M->m, M->v, M->norm, M->partial, M->loss};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (M->own_stream && M->stream) cudaStreamDestroy(M->stream);
@@ -324,6 +350,7 @@ int iilbm_mlp_destroy(iilbm_mlp_t M) {
 int iilbm_mlp_set_params(iilbm_mlp_t M, const float *params) {
   if (!M || !params) return IILBM_ERR_INVALID_ARG;
   CKM(cudaMemcpyAsync(M->P, params, MLP_NPARAM * sizeof(float), cudaMemcpyDefault, M->stream));
+  if (refresh_transposed(M)) return IILBM_ERR_CUDA;
   CKM(cudaMemsetAsync(M->m, 0, MLP_NPARAM * sizeof(float), M->stream));
   CKM(cudaMemsetAsync(M->v, 0, MLP_NPARAM * sizeof(float), M->stream));
   M->t = 0;
@@ -441,6 +468,7 @@ int iilbm_mlp_train(iilbm_mlp_t M, const float *X, const float *T, int32_t N, co
         nullptr);
     if (cudaGetLastError() != cudaSuccess) rc = IILBM_ERR_CUDA;
   }
+  if (!rc && steps > 0) rc = refresh_transposed(M);
   if (!rc && losses && steps > 0 &&
       cudaMemcpyAsync(losses, dL, steps * sizeof(float), cudaMemcpyDefault, M->stream) != cudaSuccess)
     rc = IILBM_ERR_CUDA;

@@ -52,28 +52,38 @@ __device__ inline void mlp_hidden_layer(const float *__restrict__ W, const float
   }
 }
 
-// The same layer with the weights transposed, WT[i][j] (shared memory): lanes of a warp
-// take consecutive j and read consecutive words, the input is broadcast.
+// The same layer with the weights transposed, WT[i][j] (shared memory): a thread forms
+// four outputs j0 .. j0+3 of one sample from one broadcast input load and one 16-byte
+// weight load per i (each output's sum in the same order as above).
 __device__ inline void mlp_hidden_layer_t(const float *WT, const float *__restrict__ b,
                                           const float *in, int in_dim, float *out, int S, int tid,
                                           int nthreads) {
-  for (int idx = tid; idx < S * MLP_H; idx += nthreads) {
-    const int s = idx >> 6, j = idx & (MLP_H - 1);
+  for (int item = tid; item < S * (MLP_H / 4); item += nthreads) {
+    const int s = item >> 4, j0 = (item & 15) * 4;
     const float *x = in + s * in_dim;
-    float acc = b[j];
-    for (int i = 0; i < in_dim; i++) acc = fmaf(WT[i * MLP_H + j], x[i], acc);
-    out[idx] = gelu_f(acc);
+    float a0 = b[j0], a1 = b[j0 + 1], a2 = b[j0 + 2], a3 = b[j0 + 3];
+    for (int i = 0; i < in_dim; i++) {
+      const float xi = x[i];
+      const float4 w = *reinterpret_cast<const float4 *>(WT + i * MLP_H + j0);
+      a0 = fmaf(w.x, xi, a0);
+      a1 = fmaf(w.y, xi, a1);
+      a2 = fmaf(w.z, xi, a2);
+      a3 = fmaf(w.w, xi, a3);
+    }
+    float *o = out + s * MLP_H + j0;
+    o[0] = gelu_f(a0);
+    o[1] = gelu_f(a1);
+    o[2] = gelu_f(a2);
+    o[3] = gelu_f(a3);
   }
 }
 
-// Copy W [64][in] of the packed parameters to WT [in][64]: consecutive threads write
-// consecutive words of WT (no bank conflicts), reading W through the cache.
-__device__ inline void mlp_stage_transposed(const float *__restrict__ W, int in_dim, float *WT,
-                                            int tid, int nthreads) {
-  for (int e = tid; e < MLP_H * in_dim; e += nthreads) {
-    const int i = e >> 6, j = e & (MLP_H - 1);
-    WT[e] = W[j * in_dim + i];
-  }
+// Copy n floats (a multiple of 4, 16-byte aligned both sides) with 16-byte accesses.
+__device__ inline void mlp_copy4(const float *__restrict__ src, float *dst, int n, int tid,
+                                 int nthreads) {
+  const float4 *s4 = reinterpret_cast<const float4 *>(src);
+  float4 *d4 = reinterpret_cast<float4 *>(dst);
+  for (int e = tid; e < n / 4; e += nthreads) d4[e] = s4[e];
 }
 
 // Output layer: y[s][o] = b4[o] + sum_j W4[o][j] a[s][j] (normalised output).

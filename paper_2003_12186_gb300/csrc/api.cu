@@ -406,11 +406,10 @@ int drain_all(iilbm_lattice *h) {
 }
 
 // Kernels launched by one step: lean stream-collide; with an interface also the
-// forced stream-collide, the interpolation and the two interface kernels (marker and
-// segment pass; and the force iteration for direct forcing); a channel adds its
-// boundary kernel.
+// forced stream-collide, the interpolation and the interface kernel (and the force
+// iteration for direct forcing); a channel adds its boundary kernel.
 long long kernels_per_step(const iilbm_lattice *h) {
-  return 1 + (h->nm > 0 ? 4 + (h->ip.model == IILBM_DIRECT ? 1 : 0) : 0) +
+  return 1 + (h->nm > 0 ? 3 + (h->ip.model == IILBM_DIRECT ? 1 : 0) : 0) +
          (h->cfg.bc == IILBM_BC_CHANNEL ? 1 : 0);
 }
 

@@ -217,12 +217,10 @@ __device__ __forceinline__ void interface_marker(const double *__restrict__ X,
 constexpr int CROSS_BUF = 4;
 
 template <typename T>
-__device__ __forceinline__ void interface_segment(const long long *__restrict__ Xq,
-                                                  const double *__restrict__ Fn, int n, int k,
-                                                  int lane, int jump, const Geom &geo, T *Jf,
-                                                  const TileBuf &tb) {
-  const int kp = k + 1 == n ? 0 : k + 1;
-  const long long ax = Xq[2 * k], ay = Xq[2 * k + 1], bx = Xq[2 * kp], by = Xq[2 * kp + 1];
+__device__ __forceinline__ void segment_links(long long ax, long long ay, long long bx,
+                                              long long by, double FnA, double FnB, int lane,
+                                              int jump, const Geom &geo, T *Jf,
+                                              const TileBuf &tb) {
   const bool inside = ax != XQ_OUT && bx != XQ_OUT;
   const long long Q = (long long)QSCALE;
   const long long QMAX = (long long)(MAX_SEGMENT * QSCALE);
@@ -231,7 +229,6 @@ __device__ __forceinline__ void interface_segment(const long long *__restrict__ 
   auto qceil = [](long long v) { return (int)-((-v) >> 24); };
   int found = 0;
   if (jump && inside && llabs(bx - ax) < QMAX && llabs(by - ay) < QMAX) {
-    const double FnA = Fn[k], FnB = Fn[kp];
     // destinations x of links that can reach the segment: with the node displaced by
     // (eps, eps^2) the link x - e_i -> x spans [x - 1 + eps, x + 1 + eps] at most on
     // each axis, which meets [min, max] only for ceil(min) - 1 <= x <= ceil(max)
@@ -345,6 +342,17 @@ __device__ __forceinline__ void interface_segment(const long long *__restrict__ 
     for (int t = lane; t < nc * nr; t += 32)
       flag_tile(tb, rows[t / nc] * geo.ntx + cols[t % nc], tag);
   }
+}
+
+// The segment pass of segment k -> k+1 from the marker pass's outputs in global memory.
+template <typename T>
+__device__ __forceinline__ void interface_segment(const long long *__restrict__ Xq,
+                                                  const double *__restrict__ Fn, int n, int k,
+                                                  int lane, int jump, const Geom &geo, T *Jf,
+                                                  const TileBuf &tb) {
+  const int kp = k + 1 == n ? 0 : k + 1;
+  segment_links<T>(Xq[2 * k], Xq[2 * k + 1], Xq[2 * kp], Xq[2 * kp + 1], Fn[k], Fn[kp], lane,
+                   jump, geo, Jf, tb);
 }
 
 // ------------------------------------------------------------- interpolation

@@ -93,7 +93,7 @@ def test_timing_counts_launches_in_graph_and_eager_modes():
     g.step(64 + 5)
     ms, n, k = g.iilbm_get_timing()
     # per step: lean and forced stream-collide, interpolation, fused interface kernel
-    assert n == 69 and k == 69 * 5 and 0 < ms < 69 * 10.0
+    assert n == 69 and k == 69 * 4 and 0 < ms < 69 * 10.0
     g.iilbm_set_option(iilbm.OPT_CUDA_GRAPH, 0)
     g.iilbm_set_timing(True)
     g.step(7)

@@ -52,13 +52,15 @@ int read_status(iilbm_lattice *h) {
 }
 
 void free_interface(iilbm_lattice *h) {
-  double **bufs[] = {&h->X, &h->aux, &h->G, &h->Fn, &h->U, &h->nrm, &h->G0, &h->Gdf, &h->Ustar};
+  double **bufs[] = {&h->X,  &h->aux, &h->G,     &h->Fn, &h->U,
+                     &h->nrm, &h->G0, &h->Gdf, &h->Ustar, &h->Xp};
   for (double **b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
   }
   if (h->Xq) cudaFree(h->Xq);
-  h->Xq = nullptr;
+  if (h->Xqp) cudaFree(h->Xqp);
+  h->Xq = h->Xqp = nullptr;
   h->nm = 0;
 }
 
@@ -270,7 +272,8 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
             cudaMalloc(&h->Gdf, b2) == cudaSuccess && cudaMalloc(&h->Ustar, b2) == cudaSuccess &&
             cudaMalloc(&h->Fn, (size_t)n * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&h->Xq, b2) == cudaSuccess && cudaMalloc(&h->U, b2) == cudaSuccess &&
-            cudaMalloc(&h->nrm, b2) == cudaSuccess;
+            cudaMalloc(&h->nrm, b2) == cudaSuccess && cudaMalloc(&h->Xp, b2) == cudaSuccess &&
+            cudaMalloc(&h->Xqp, b2) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_interface(h);
@@ -406,27 +409,26 @@ int drain_all(iilbm_lattice *h) {
 }
 
 // Kernels launched by one step: lean stream-collide; with an interface also the
-// forced stream-collide, the interpolation and the interface kernel (and the force
-// iteration for direct forcing); a channel adds its boundary kernel.
+// forced stream-collide and the interpolation fused with the next interface phase
+// (pipelined), or the interpolation, the interface kernel and, for direct forcing, the
+// force iteration; a channel adds its boundary kernel.
 long long kernels_per_step(const iilbm_lattice *h) {
-  return 1 + (h->nm > 0 ? 3 + (h->ip.model == IILBM_DIRECT ? 1 : 0) : 0) +
-         (h->cfg.bc == IILBM_BC_CHANNEL ? 1 : 0);
+  long long k = 1 + (h->cfg.bc == IILBM_BC_CHANNEL ? 1 : 0);
+  if (h->nm > 0) k += pipelined(h) ? 2 : 3 + (h->ip.model == IILBM_DIRECT ? 1 : 0);
+  return k;
 }
 
-// Direct forcing needs the finished state of the step before, so it is not overlapped.
-bool pipelined(const iilbm_lattice *h) {
-  return h->overlap && h->nm > 0 && h->ip.model != IILBM_DIRECT;
-}
 
 // One time step of the current state n (its interface already prepared in buffer
 // n & 1).  Main stream: the lean stream-collide (every tile without a jump or force).
 // Second stream (highest priority), forked at the start of the step: the forced
 // stream-collide of the flagged tiles, which also leaves the collision velocity there,
-// the interpolation from it with the marker move (X^{n+1}), then (unless the body is
-// directly forced, whose interface phase waits for the next state's force iteration)
-// the interface phase of state n + 1 in buffer (n+1) & 1; it joins before the step
-// ends.  Without overlap the same kernels run in that order on the main stream.  Safe
-// inside stream capture.
+// then the interpolation from it with the marker move (X^{n+1}) fused with the
+// interface phase of state n + 1 in buffer (n+1) & 1 -- or, for a directly forced body
+// (whose interface phase waits for the next state's force iteration), the interpolation
+// alone; it joins before the step ends.  Without overlap the forced stream-collide and
+// the interpolation run on the main stream and the interface phase in the next
+// prepare.  Safe inside stream capture.
 // ev_slot: index of the start event of the lean stream-collide timing pair, or -1.
 int one_step(iilbm_lattice *h, int ev_slot) {
   int rc;
@@ -446,11 +448,9 @@ int one_step(iilbm_lattice *h, int ev_slot) {
   if (ev_slot >= 0) CK(cudaEventRecordWithFlags(h->ev[ev_slot], h->stream, evflag));
   if ((rc = launch_stream_collide(h, s2))) return rc;
   if (ev_slot >= 0) CK(cudaEventRecordWithFlags(h->ev[ev_slot + 1], h->stream, evflag));
-  if ((rc = launch_interp(h, s2))) return rc;
-  if (pipe) {
-    rc = launch_interface_phase(h, (int)((h->step + 1) & 1), h->side);  // state n + 1
-    if (rc) return rc;
-  }
+  rc = pipe ? launch_interp_interface(h, h->side)  // interface phase of state n + 1
+            : launch_interp(h, s2);
+  if (rc) return rc;
   if (fork) {
     CK(cudaEventRecord(h->ev_join, h->side));
     CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));

@@ -179,6 +179,8 @@ struct iilbm_lattice {
   iilbm_interface_params ip;
   double *X, *aux, *G, *Fn, *U, *nrm;
   long long *Xq;      // marker coordinates snapped to 2^-24 (XQ_OUT outside the region)
+  double *Xp;         // X, Xq of the level being interpolated, for the fused phase
+  long long *Xqp;
   double *G0, *Gdf;   // direct forcing: warm start and converged force
   double *Ustar;      // direct forcing: interpolated velocity without the body's force
   int ws_mode;        // direct forcing: where the iteration starts (WS_*)
@@ -199,6 +201,13 @@ struct iilbm_lattice {
 
 // Launchers (defined in lattice.cu / interface.cu).
 namespace iilbm {
+// The next level's interface phase runs on the side stream during the stream-collide,
+// fused with the interpolation (direct forcing needs the next state first, so its
+// interface phase waits for the next step's force iteration).
+inline bool pipelined(const iilbm_lattice *h) {
+  return h->overlap && h->nm > 0 && h->ip.model != IILBM_DIRECT;
+}
+
 int launch_stream_collide(iilbm_lattice *h, cudaStream_t forced_stream);
 int launch_interp(iilbm_lattice *h, cudaStream_t s);
 int launch_macros(iilbm_lattice *h, double *drho, double *ux, double *uy);
@@ -206,6 +215,7 @@ int launch_set_populations(iilbm_lattice *h, const double *df, bool equilibrium,
                            const double *rho, const double *ux, const double *uy);
 int launch_get_populations(iilbm_lattice *h, double *df);
 int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s);
+int launch_interp_interface(iilbm_lattice *h, cudaStream_t s);
 int launch_channel_bc(iilbm_lattice *h);
 int launch_direct_forcing(iilbm_lattice *h);
 int launch_df_features(iilbm_lattice *h, float re, float *F);

@@ -21,8 +21,11 @@ struct TileBuf {
 };
 
 // Flag a tile for this time level; the first thread to do so appends it to the list.
+// One exchange, without reading the flag first: a read would put one more memory round
+// trip on the interface phase's critical path, which runs beside the bandwidth-bound
+// stream-collide (repeated exchanges on a flagged tile cost atomic throughput only).
 __device__ inline void flag_tile(const TileBuf &tb, int tile, unsigned tag) {
-  if (tb.flags[tile] != tag && atomicExch(&tb.flags[tile], tag) != tag) {
+  if (atomicExch(&tb.flags[tile], tag) != tag) {
     tb.list[atomicAdd(tb.ctr, 1)] = tile;
     atomicAdd(tb.total, 1ull);
   }
@@ -58,15 +61,14 @@ struct MarkerForce {
   bool bad;
 };
 
+// (x, y): marker j; (xp, yp), (xm, ym): its successor and predecessor on the polygon.
 template <typename T>
-__device__ inline MarkerForce<T> marker_force(const double *__restrict__ X,
-                                              const double *__restrict__ aux, int n, int j,
-                                              const iilbm_interface_params &ip, int jump,
-                                              const Geom &geo) {
+__device__ inline MarkerForce<T> marker_force_at(double x, double y, double xp, double yp,
+                                                 double xm, double ym,
+                                                 const double *__restrict__ aux, int j,
+                                                 const iilbm_interface_params &ip, int jump,
+                                                 const Geom &geo) {
   MarkerForce<T> m;
-  const int jp = j + 1 == n ? 0 : j + 1, jm = j == 0 ? n - 1 : j - 1;
-  const double x = X[2 * j], y = X[2 * j + 1];
-  const double xp = X[2 * jp], yp = X[2 * jp + 1], xm = X[2 * jm], ym = X[2 * jm + 1];
   const double dax = xp - x, day = yp - y, dbx = x - xm, dby = y - ym;  // segments k, k-1
   // validity: finite, inside the representable / valid region, short segments
   bool bad = !(isfinite(x) && isfinite(y)) || fabs(x) > MAX_COORD || fabs(y) > MAX_COORD;
@@ -108,6 +110,16 @@ __device__ inline MarkerForce<T> marker_force(const double *__restrict__ X,
     m.py = gy * dX;
   }
   return m;
+}
+
+template <typename T>
+__device__ inline MarkerForce<T> marker_force(const double *__restrict__ X,
+                                              const double *__restrict__ aux, int n, int j,
+                                              const iilbm_interface_params &ip, int jump,
+                                              const Geom &geo) {
+  const int jp = j + 1 == n ? 0 : j + 1, jm = j == 0 ? n - 1 : j - 1;
+  return marker_force_at<T>(X[2 * j], X[2 * j + 1], X[2 * jp], X[2 * jp + 1], X[2 * jm],
+                            X[2 * jm + 1], aux, j, ip, jump, geo);
 }
 
 // Orientation of (A, B, node) with the node displaced by (eps, eps^2), eps -> 0+.
@@ -220,7 +232,7 @@ template <typename T>
 __device__ __forceinline__ void segment_links(long long ax, long long ay, long long bx,
                                               long long by, double FnA, double FnB, int lane,
                                               int jump, const Geom &geo, T *Jf,
-                                              const TileBuf &tb) {
+                                              const TileBuf &tb, unsigned tag) {
   const bool inside = ax != XQ_OUT && bx != XQ_OUT;
   const long long Q = (long long)QSCALE;
   const long long QMAX = (long long)(MAX_SEGMENT * QSCALE);
@@ -338,7 +350,6 @@ __device__ __forceinline__ void segment_links(long long ax, long long ay, long l
                              geo.bc != IILBM_BC_CHANNEL, TILE_X, cols);
     const int nr = tile_span(qfloor(min(ay, by)) - 2, qceil(max(ay, by)) + 2, geo.ny,
                              geo.bc == IILBM_BC_PERIODIC, TILE_Y, rows);
-    const unsigned tag = *tb.tag;
     for (int t = lane; t < nc * nr; t += 32)
       flag_tile(tb, rows[t / nc] * geo.ntx + cols[t % nc], tag);
   }
@@ -350,9 +361,10 @@ __device__ __forceinline__ void interface_segment(const long long *__restrict__ 
                                                   const double *__restrict__ Fn, int n, int k,
                                                   int lane, int jump, const Geom &geo, T *Jf,
                                                   const TileBuf &tb) {
+  const unsigned tag = *tb.tag;
   const int kp = k + 1 == n ? 0 : k + 1;
   segment_links<T>(Xq[2 * k], Xq[2 * k + 1], Xq[2 * kp], Xq[2 * kp + 1], Fn[k], Fn[kp], lane,
-                   jump, geo, Jf, tb);
+                   jump, geo, Jf, tb, tag);
 }
 
 // ------------------------------------------------------------- interpolation
@@ -362,52 +374,90 @@ __device__ __forceinline__ void interface_segment(const long long *__restrict__ 
 // storage: FP64 throughout.  Otherwise each stencil row is summed in FP32 and the four
 // row sums are accumulated in FP64.
 template <typename T>
+__device__ __forceinline__ void interp_at(const T *__restrict__ uf, const Geom &geo, double x,
+                                          long long qx, double y, long long qy, double &sx,
+                                          double &sy) {
+  sx = 0.0;
+  sy = 0.0;
+  if (qx == XQ_OUT) return;
+  int bx, by;
+  T wx[4], wy[4];
+  stencil_weights<T>(x, qx, bx, wx);
+  stencil_weights<T>(y, qy, by, wy);
+#pragma unroll
+  for (int b = 0; b < 4; b++) {
+    int yi = by + b;
+    bool oky = true;
+    if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
+    else oky = yi >= 0 && yi < geo.ny;
+    T rx = T(0), ry = T(0);
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      int xi = bx + a;
+      bool ok = oky;
+      if (geo.bc == IILBM_BC_CHANNEL) ok = ok && xi >= 0 && xi < geo.nx;
+      else xi = wrap(xi, geo.nx);
+      if (ok) {
+        const long long here = (long long)yi * geo.pitch + xi;
+        if (sizeof(T) == 8) {  // FP64: every weight wx * wy formed, as the definition reads
+          sx += (double)uf[here] * (double)(wx[a] * wy[b]);
+          sy += (double)uf[geo.plane + here] * (double)(wx[a] * wy[b]);
+        } else {
+          rx += uf[here] * wx[a];
+          ry += uf[geo.plane + here] * wx[a];
+        }
+      }
+    }
+    if (sizeof(T) != 8) {
+      sx += (double)rx * (double)wy[b];
+      sy += (double)ry * (double)wy[b];
+    }
+  }
+}
+
+template <typename T>
 __device__ __forceinline__ void interp_marker(const T *__restrict__ uf, const Geom &geo,
                                               double *X, const long long *__restrict__ Xq,
                                               int k, double *U, int moves) {
   const double x = X[2 * k], y = X[2 * k + 1];
-  const long long qx = Xq[2 * k], qy = Xq[2 * k + 1];
-  double sx = 0.0, sy = 0.0;
-  if (qx != XQ_OUT) {
-    int bx, by;
-    T wx[4], wy[4];
-    stencil_weights<T>(x, qx, bx, wx);
-    stencil_weights<T>(y, qy, by, wy);
-#pragma unroll
-    for (int b = 0; b < 4; b++) {
-      int yi = by + b;
-      bool oky = true;
-      if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
-      else oky = yi >= 0 && yi < geo.ny;
-      T rx = T(0), ry = T(0);
-#pragma unroll
-      for (int a = 0; a < 4; a++) {
-        int xi = bx + a;
-        bool ok = oky;
-        if (geo.bc == IILBM_BC_CHANNEL) ok = ok && xi >= 0 && xi < geo.nx;
-        else xi = wrap(xi, geo.nx);
-        if (ok) {
-          const long long here = (long long)yi * geo.pitch + xi;
-          if (sizeof(T) == 8) {  // FP64: every weight wx * wy formed, as the definition reads
-            sx += (double)uf[here] * (double)(wx[a] * wy[b]);
-            sy += (double)uf[geo.plane + here] * (double)(wx[a] * wy[b]);
-          } else {
-            rx += uf[here] * wx[a];
-            ry += uf[geo.plane + here] * wx[a];
-          }
-        }
-      }
-      if (sizeof(T) != 8) {
-        sx += (double)rx * (double)wy[b];
-        sy += (double)ry * (double)wy[b];
-      }
-    }
-  }
+  double sx, sy;
+  interp_at<T>(uf, geo, x, Xq[2 * k], y, Xq[2 * k + 1], sx, sy);
   U[2 * k] = sx;
   U[2 * k + 1] = sy;
   if (moves) {
     X[2 * k] = x + sx;
     X[2 * k + 1] = y + sy;
+  }
+}
+
+// ------------------------------------------------------ snapshot for the fused phase
+// Work the forced stream-collide of level n does on the side for what follows it:
+// advance the tag of the next level's buffer and reset its counters (the readers of
+// that buffer's previous level, the lean and forced kernels of level n - 1, are done),
+// and, when the interpolation and the next interface phase run fused, copy the marker
+// positions and snapped coordinates of level n to Xp, Xqp (the fused kernel reads its
+// neighbours' markers there while their owners overwrite X, Xq).
+struct MarkerPrep {
+  const double *X;
+  double *Xp;
+  const long long *Xq;
+  long long *Xqp;
+  int n2;  // entries to copy (2 per marker), 0 for none
+  unsigned *next_tag;
+  int *next_ctr;
+};
+
+__device__ __forceinline__ void marker_prep(const MarkerPrep &mp) {
+  const int nt = blockDim.x * blockDim.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0 && tid == 0) {
+    *mp.next_tag += 1u;
+    mp.next_ctr[0] = 0;
+    mp.next_ctr[1] = 0;
+  }
+  for (int i = blockIdx.x * nt + tid; i < mp.n2; i += gridDim.x * nt) {
+    mp.Xp[i] = mp.X[i];
+    mp.Xqp[i] = mp.Xq[i];
   }
 }
 

@@ -32,8 +32,9 @@ __global__ void __launch_bounds__(32 * TILE_Y)
 }
 
 // At least three resident blocks per SM (<= 85 registers): the odd step would otherwise
-// drop to two and lose a third of its memory parallelism.
-template <typename S, int COLL, bool ODD, int BC>
+// drop to two and lose a third of its memory parallelism.  BODY = false (no body force):
+// the lean tiles carry no force at all and the collision drops Guo's source terms.
+template <typename S, int COLL, bool ODD, int BC, bool BODY>
 __global__ void __launch_bounds__(32 * VEC_ROWS, 3)
     k_stream_collide_vec(S *__restrict__ A, const unsigned *__restrict__ flags,
                          const unsigned *__restrict__ tag, const Geom geo,
@@ -41,17 +42,21 @@ __global__ void __launch_bounds__(32 * VEC_ROWS, 3)
   constexpr int W = 32 * Vec<S>::V;  // nodes per warp row
   const int xb = blockIdx.x * W, yb = blockIdx.y * VEC_ROWS;
   if (flags[blockIdx.y * geo.ntx + xb / TILE_X] == *tag) return;  // uniform per block
-  sc_vec_rows<S, COLL, ODD, BC, false>(A, nullptr, nullptr, nullptr, geo, p, status, xb, yb);
+  sc_vec_rows<S, COLL, ODD, BC, false, Vec<S>::V, BODY>(A, nullptr, nullptr, nullptr, geo, p,
+                                                         status, xb, yb);
 }
 
-// Forced kernels: blocks stride over the list of flagged tiles of this step.
+// Forced kernels: blocks stride over the list of flagged tiles of this step (and first
+// prepare the next interface phase's buffer and marker snapshot, marker_prep).
 template <typename S, int COLL, bool ODD, int BC>
 __global__ void __launch_bounds__(32 * TILE_Y)
     k_stream_collide_forced(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
                             typename Store<S>::T *__restrict__ gf,
                             typename Store<S>::T *__restrict__ uf,
                             const int *__restrict__ list, const int *__restrict__ count,
-                            const Geom geo, const CollP<typename Store<S>::T> p, int *status) {
+                            const Geom geo, const CollP<typename Store<S>::T> p, int *status,
+                            MarkerPrep mp) {
+  marker_prep(mp);
   const int n = *count;
   for (int t = blockIdx.x; t < n; t += gridDim.x) {
     const int tile = list[t];
@@ -68,8 +73,9 @@ __global__ void __launch_bounds__(32 * VEC_ROWS)
                                 typename Store<S>::T *__restrict__ uf,
                                 const int *__restrict__ list, const int *__restrict__ count,
                                 const Geom geo, const CollP<typename Store<S>::T> p,
-                                int *status) {
+                                int *status, MarkerPrep mp) {
   constexpr int W = 32 * Vec<S>::V;
+  marker_prep(mp);
   const int n = *count;
   for (int t = blockIdx.x; t < n; t += gridDim.x) {
     const int tile = list[t];
@@ -107,20 +113,12 @@ __device__ inline void node_macros(const S *A, const typename Store<S>::T *Jf,
 // marker (interp_marker); a membrane marker then moves, X_k += U_k.  u is the
 // collision velocity of the step (jump and g/2 included) that the forced stream-collide
 // left in uf for every node of the flagged tiles -- which cover every marker's stencil
-// -- so this runs right after the forced kernel.
-// Thread 0 also prepares the other buffer for the next interface phase (its readers
-// are done by now): advance its tag, so its old flags stop matching, and reset its
-// counters.
+// -- so this runs right after the forced kernel.  (The pipelined step runs it fused
+// with the next interface phase instead: k_interface<T, true>.)
 template <typename T>
 __global__ void k_interp(const T *__restrict__ uf, const Geom geo, double *X,
-                         const long long *__restrict__ Xq, int n, double *U, int moves,
-                         unsigned *next_tag, int *next_ctr) {
+                         const long long *__restrict__ Xq, int n, double *U, int moves) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k == 0) {
-    *next_tag += 1u;
-    next_ctr[0] = 0;
-    next_ctr[1] = 0;
-  }
   if (k < n) interp_marker<T>(uf, geo, X, Xq, k, U, moves);
 }
 
@@ -218,23 +216,27 @@ static void sc_launch_bc(iilbm_lattice *h, cudaStream_t forced_stream) {
   constexpr int V = Vec<S>::V;
   const int nyt = (g.ny + TILE_Y - 1) / TILE_Y;
   const bool vec = h->vector_sc && g.nx % V == 0;
-  if (vec)
-    k_stream_collide_vec<S, COLL, ODD, BC><<<dim3((g.nx + 32 * V - 1) / (32 * V), nyt),
-                                             32 * VEC_ROWS, 0, h->stream>>>((S *)h->A, fl,
-                                                                            h->tagb[b], g, p,
-                                                                            h->d_status);
+  const dim3 vgrid((g.nx + 32 * V - 1) / (32 * V), nyt);
+  if (vec && h->cfg.body[0] == 0.0 && h->cfg.body[1] == 0.0)
+    k_stream_collide_vec<S, COLL, ODD, BC, false><<<vgrid, 32 * VEC_ROWS, 0, h->stream>>>(
+        (S *)h->A, fl, h->tagb[b], g, p, h->d_status);
+  else if (vec)
+    k_stream_collide_vec<S, COLL, ODD, BC, true><<<vgrid, 32 * VEC_ROWS, 0, h->stream>>>(
+        (S *)h->A, fl, h->tagb[b], g, p, h->d_status);
   else
     k_stream_collide<S, COLL, ODD, BC><<<dim3((g.nx + 31) / 32, nyt), dim3(32, TILE_Y), 0,
                                          h->stream>>>((S *)h->A, fl, h->tagb[b], g, p,
                                                       h->d_status);
   if (h->nm == 0) return;  // no interface: no flagged tiles
   const int grid = h->forced_grid;
+  const MarkerPrep mp{h->X, h->Xp, h->Xq, h->Xqp, pipelined(h) ? 2 * h->nm : 0, h->tagb[b ^ 1],
+                      h->tile_count[b ^ 1]};
   if (vec)
     k_stream_collide_vec_forced<S, COLL, ODD, BC><<<grid, 32 * VEC_ROWS, 0, forced_stream>>>(
-        (S *)h->A, J, gf, (T *)h->uf, h->tile_list[b], h->tile_count[b], g, p, h->d_status);
+        (S *)h->A, J, gf, (T *)h->uf, h->tile_list[b], h->tile_count[b], g, p, h->d_status, mp);
   else
     k_stream_collide_forced<S, COLL, ODD, BC><<<grid, dim3(32, TILE_Y), 0, forced_stream>>>(
-        (S *)h->A, J, gf, (T *)h->uf, h->tile_list[b], h->tile_count[b], g, p, h->d_status);
+        (S *)h->A, J, gf, (T *)h->uf, h->tile_list[b], h->tile_count[b], g, p, h->d_status, mp);
 }
 
 template <typename S, int COLL, bool ODD>
@@ -267,13 +269,12 @@ int launch_stream_collide(iilbm_lattice *h, cudaStream_t forced_stream) {
 int launch_interp(iilbm_lattice *h, cudaStream_t s) {
   if (h->nm == 0) return IILBM_OK;
   const int blocks = (h->nm + 127) / 128;
-  const int nb = (int)((h->step + 1) & 1);  // the buffer of the next time level
   if (h->cfg.storage == IILBM_F64)
     k_interp<double><<<blocks, 128, 0, s>>>((const double *)h->uf, h->geom, h->X, h->Xq, h->nm,
-                                            h->U, h->ip.moves, h->tagb[nb], h->tile_count[nb]);
+                                            h->U, h->ip.moves);
   else
     k_interp<float><<<blocks, 128, 0, s>>>((const float *)h->uf, h->geom, h->X, h->Xq, h->nm,
-                                           h->U, h->ip.moves, h->tagb[nb], h->tile_count[nb]);
+                                           h->U, h->ip.moves);
   return last_error();
 }
 

@@ -38,31 +38,44 @@ CollP<T> make_collp(const iilbm_config &c) {
 //   rho = rho0 + drho,  rho u = j + g/2  (Eqs. 11, 24)
 //   feq_i - w_i rho0 = w_i [drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u^2)]  (Eq. 23)
 //   Guo source  Gt_i = w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]  (Eqs. 21-22)
+// The populations and the force come in the storage's units, multiplied by its scale
+// 2^k (f' = 2^k f, g' = 2^k g), and the populations go out in them: every moment is
+// linear in f and g, and the velocity is j' / (2^k rho), so the collision runs on the
+// scaled values directly.  Multiplying by a power of two is exact, so each operation
+// rounds as it would on the unscaled values: the results are the unscaled collision's
+// times 2^k, bit for bit, with no conversion multiply per population.  Returns the
+// unscaled drho; ux_out, uy_out are the unscaled velocity.
+// BODY = false: the force is zero (lean tiles without a body force) and Guo's source
+// terms are left out.
 // PP is CollP<T>, or a volatile view of one in shared memory (the batched kernels:
 // every rate is then re-read where it is used instead of held in a register).
-template <typename T, int COLL, typename PP = CollP<T>>
+template <typename T, int COLL, typename PP = CollP<T>, bool BODY = true>
 __device__ __forceinline__ T collide(T f[9], T gx, T gy, const PP &p, T &ux_out,
                                      T &uy_out) {
-  const T drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const T drs = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
   const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
   const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  const T drho = drs * p.inv_scale;
   const T rho = p.rho0 + drho;
-  const T ir = T(1) / rho;
-  const T jxh = jx + T(0.5) * gx, jyh = jy + T(0.5) * gy;  // rho u
-  const T ux = jxh * ir, uy = jyh * ir;
+  const T irs = (T(1) / rho) * p.inv_scale;                   // 1 / (2^k rho)
+  const T jxh = BODY ? jx + T(0.5) * gx : jx, jyh = BODY ? jy + T(0.5) * gy : jy;  // rho u
+  const T ux = jxh * irs, uy = jyh * irs;
   ux_out = ux;
   uy_out = uy;
   if (COLL == IILBM_SRT) {
     const T u2 = ux * ux + uy * uy;
     const T ug = ux * gx + uy * gy;
     const T om = p.omega, fo = T(1) - T(0.5) * p.omega;
+    const T rhos = rho * p.scale;
 #pragma unroll
     for (int i = 0; i < 9; i++) {
       const T eu = T(cx(i)) * ux + T(cy(i)) * uy;
-      const T eg = T(cx(i)) * gx + T(cy(i)) * gy;
-      const T feq = wt<T>(i) * (drho + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * u2));
-      const T gt = wt<T>(i) * (T(3) * (eg - ug) + T(9) * eu * eg);
-      f[i] = f[i] - om * (f[i] - feq) + fo * gt;
+      const T feq = wt<T>(i) * (drs + rhos * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * u2));
+      f[i] = f[i] - om * (f[i] - feq);
+      if (BODY) {
+        const T eg = T(cx(i)) * gx + T(cy(i)) * gy;
+        f[i] += fo * (wt<T>(i) * (T(3) * (eg - ug) + T(9) * eu * eg));
+      }
     }
   } else {
     // Lallemand-Luo moments of df: e, eps, qx, qy, pxx, pxy (rho, jx, jy above).
@@ -76,37 +89,54 @@ __device__ __forceinline__ T collide(T f[9], T gx, T gy, const PP &p, T &ux_out,
     const T m8 = (f[5] + f[7]) - (f[6] + f[8]);
     // equilibrium moments of the shifted equilibrium
     const T ru2 = jxh * ux + jyh * uy;  // rho u^2
-    const T e1 = T(-2) * drho + T(3) * ru2;
-    const T e2 = drho - T(3) * ru2;
+    const T e1 = T(-2) * drs + T(3) * ru2;
+    const T e2 = drs - T(3) * ru2;
     const T e4 = -jxh, e6 = -jyh;
     const T e7 = jxh * ux - jyh * uy;
     const T e8 = jxh * uy;
-    // moments of Guo's source
-    const T ug = ux * gx + uy * gy;
-    const T F1 = T(6) * ug, F2 = T(-6) * ug, F4 = -gx, F6 = -gy;
-    const T F7 = T(2) * (ux * gx - uy * gy), F8 = ux * gy + uy * gx;
-    const T d1 = -p.s1 * (m1 - e1) + (T(1) - T(0.5) * p.s1) * F1;
-    const T d2 = -p.s2 * (m2 - e2) + (T(1) - T(0.5) * p.s2) * F2;
-    const T d4 = -p.s4 * (m4 - e4) + (T(1) - T(0.5) * p.s4) * F4;
-    const T d6 = -p.s6 * (m6 - e6) + (T(1) - T(0.5) * p.s6) * F6;
-    const T d7 = -p.s7 * (m7 - e7) + (T(1) - T(0.5) * p.s7) * F7;
-    const T d8 = -p.s8 * (m8 - e8) + (T(1) - T(0.5) * p.s8) * F8;
-    // conserved moments: rho unchanged, j gains exactly g (any s3, s5)
+    T d1 = -p.s1 * (m1 - e1), d2 = -p.s2 * (m2 - e2), d4 = -p.s4 * (m4 - e4);
+    T d6 = -p.s6 * (m6 - e6), d7 = -p.s7 * (m7 - e7), d8 = -p.s8 * (m8 - e8);
+    T a3 = T(0), a5 = T(0);
+    if (BODY) {
+      // moments of Guo's source
+      const T ug = ux * gx + uy * gy;
+      const T F1 = T(6) * ug, F2 = T(-6) * ug, F4 = -gx, F6 = -gy;
+      const T F7 = T(2) * (ux * gx - uy * gy), F8 = ux * gy + uy * gx;
+      d1 += (T(1) - T(0.5) * p.s1) * F1;
+      d2 += (T(1) - T(0.5) * p.s2) * F2;
+      d4 += (T(1) - T(0.5) * p.s4) * F4;
+      d6 += (T(1) - T(0.5) * p.s6) * F6;
+      d7 += (T(1) - T(0.5) * p.s7) * F7;
+      d8 += (T(1) - T(0.5) * p.s8) * F8;
+      // conserved moments: rho unchanged, j gains exactly g (any s3, s5)
+      a3 = gx * T(1.0 / 6);
+      a5 = gy * T(1.0 / 6);
+    }
     const T a1 = d1 * T(1.0 / 36), a2 = d2 * T(1.0 / 36);
-    const T a3 = gx * T(1.0 / 6), a5 = gy * T(1.0 / 6);
     const T a4 = d4 * T(1.0 / 12), a6 = d6 * T(1.0 / 12);
     const T a7 = d7 * T(0.25), a8 = d8 * T(0.25);
     const T b = -a1 - T(2) * a2;        // common to the axis velocities
     const T c = T(2) * a1 + a2;         // common to the diagonals
     f[0] += T(-4) * a1 + T(4) * a2;
-    f[1] += b + a3 - T(2) * a4 + a7;
-    f[2] += b + a5 - T(2) * a6 - a7;
-    f[3] += b - a3 + T(2) * a4 + a7;
-    f[4] += b - a5 + T(2) * a6 - a7;
-    f[5] += c + (a3 + a4) + (a5 + a6) + a8;
-    f[6] += c - (a3 + a4) + (a5 + a6) - a8;
-    f[7] += c - (a3 + a4) - (a5 + a6) + a8;
-    f[8] += c + (a3 + a4) - (a5 + a6) - a8;
+    if (BODY) {
+      f[1] += b + a3 - T(2) * a4 + a7;
+      f[2] += b + a5 - T(2) * a6 - a7;
+      f[3] += b - a3 + T(2) * a4 + a7;
+      f[4] += b - a5 + T(2) * a6 - a7;
+      f[5] += c + (a3 + a4) + (a5 + a6) + a8;
+      f[6] += c - (a3 + a4) + (a5 + a6) - a8;
+      f[7] += c - (a3 + a4) - (a5 + a6) + a8;
+      f[8] += c + (a3 + a4) - (a5 + a6) - a8;
+    } else {
+      f[1] += b - T(2) * a4 + a7;
+      f[2] += b - T(2) * a6 - a7;
+      f[3] += b + T(2) * a4 + a7;
+      f[4] += b + T(2) * a6 - a7;
+      f[5] += c + a4 + a6 + a8;
+      f[6] += c - a4 + a6 - a8;
+      f[7] += c - a4 - a6 + a8;
+      f[8] += c + a4 - a6 - a8;
+    }
   }
   return drho;
 }
@@ -141,17 +171,17 @@ struct alignas(sizeof(S) * V) Pack {
 };
 
 template <typename S, int V>
-__device__ inline void vld(const S *p, typename Store<S>::T *o, typename Store<S>::T is) {
+__device__ inline void vld(const S *p, typename Store<S>::T *o) {
   const Pack<S, V> t = *reinterpret_cast<const Pack<S, V> *>(p);
 #pragma unroll
-  for (int j = 0; j < V; j++) o[j] = Store<S>::ld(t.v[j]) * is;
+  for (int j = 0; j < V; j++) o[j] = Store<S>::ld(t.v[j]);
 }
 
 template <typename S, int V>
-__device__ inline void vst(S *p, const typename Store<S>::T *v, typename Store<S>::T sc) {
+__device__ inline void vst(S *p, const typename Store<S>::T *v) {
   Pack<S, V> t;
 #pragma unroll
-  for (int j = 0; j < V; j++) t.v[j] = Store<S>::st(v[j] * sc);
+  for (int j = 0; j < V; j++) t.v[j] = Store<S>::st(v[j]);
   *reinterpret_cast<Pack<S, V> *>(p) = t;
 }
 
@@ -209,17 +239,17 @@ __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
       const bool from_wall = (cy(i) > 0 && wall_m) || (cy(i) < 0 && wall_p);
       if (!from_wall) src = opp(i) * P + row[1 - cy(i)] + col[1 - cx(i)];
     }
-    f[i] = Store<S>::ld(A[src]) * p.inv_scale;
+    f[i] = Store<S>::ld(A[src]);  // in storage units (collide)
   }
   T gx = p.bodyx, gy = p.bodyy;
   if (FORCED) {
 #pragma unroll
-    for (int i = 1; i < 9; i++) f[i] += Jf[(i - 1) * P + here];
+    for (int i = 1; i < 9; i++) f[i] += Jf[(i - 1) * P + here] * p.scale;
     gx += gf[here];
     gy += gf[P + here];
   }
   T ux, uy;
-  const T drho = collide<T, COLL>(f, gx, gy, p, ux, uy);
+  const T drho = collide<T, COLL>(f, gx * p.scale, gy * p.scale, p, ux, uy);
   if (!isfinite(drho)) atomicOr(status, ST_NONFINITE);
   if (FORCED) {  // the velocity the markers are interpolated from (Eq. 20)
     uf[here] = ux;
@@ -237,7 +267,7 @@ __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
       const bool to_wall = (cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m);
       if (!to_wall) dst = i * P + row[1 + cy(i)] + col[1 + cx(i)];
     }
-    A[dst] = Store<S>::st(f[i] * p.scale);
+    A[dst] = Store<S>::st(f[i]);
   }
 }
 
@@ -250,7 +280,8 @@ __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
 // of a row fetch / write that element with a scalar access instead, wrapping around
 // the periodic row.  Requires nx % V == 0.  Every lane of the warp must call this.
 template <typename S, int COLL, bool ODD, int BC, bool FORCED, int V = Vec<S>::V,
-          bool YWALL = true, typename GG = Geom, typename PP = CollP<typename Store<S>::T>>
+          bool YWALL = true, bool BODY = true, typename GG = Geom,
+          typename PP = CollP<typename Store<S>::T>>
 __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
                                              typename Store<S>::T *__restrict__ Jf,
                                              typename Store<S>::T *__restrict__ gf,
@@ -288,25 +319,25 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
     for (int j = 0; j < V; j++) f[i][j] = T(0);
     const bool from_wall = ODD && ((cy(i) > 0 && wall_m) || (cy(i) < 0 && wall_p));
     if (!ODD || from_wall) {
-      if (active) vld<S, V>(A + i * P + here, f[i], p.inv_scale);
+      if (active) vld<S, V>(A + i * P + here, f[i]);
     } else {
       const long long base = opp(i) * P + row[1 - cy(i)];
       T c[V];
 #pragma unroll
       for (int j = 0; j < V; j++) c[j] = T(0);
-      if (active) vld<S, V>(A + base + x0, c, p.inv_scale);
+      if (active) vld<S, V>(A + base + x0, c);
       if (cx(i) == 0) {
 #pragma unroll
         for (int j = 0; j < V; j++) f[i][j] = c[j];
       } else if (cx(i) > 0) {  // source x - 1
         T left = __shfl_up_sync(0xffffffffu, c[V - 1], 1);
-        if (active && lane == 0) left = Store<S>::ld(A[base + xl]) * p.inv_scale;
+        if (active && lane == 0) left = Store<S>::ld(A[base + xl]);
         f[i][0] = left;
 #pragma unroll
         for (int j = 1; j < V; j++) f[i][j] = c[j - 1];
       } else {  // source x + 1
         T right = __shfl_down_sync(0xffffffffu, c[0], 1);
-        if (edge_r) right = Store<S>::ld(A[base + xr]) * p.inv_scale;
+        if (edge_r) right = Store<S>::ld(A[base + xr]);
 #pragma unroll
         for (int j = 0; j < V - 1; j++) f[i][j] = c[j + 1];
         f[i][V - 1] = right;
@@ -322,13 +353,17 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
       T jv[V];
       ldT<T, V>(Jf + (i - 1) * P + here, jv);
 #pragma unroll
-      for (int j = 0; j < V; j++) f[i][j] += jv[j];
+      for (int j = 0; j < V; j++) f[i][j] += jv[j] * p.scale;
     }
     T a[V], b[V];
     ldT<T, V>(gf + here, a);
     ldT<T, V>(gf + P + here, b);
 #pragma unroll
     for (int j = 0; j < V; j++) { gx[j] += a[j]; gy[j] += b[j]; }
+  }
+  if (BODY) {
+#pragma unroll
+    for (int j = 0; j < V; j++) { gx[j] *= p.scale; gy[j] *= p.scale; }  // storage units
   }
   bool finite = true;
   T uxv[V], uyv[V];
@@ -337,7 +372,7 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
     T fc[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) fc[i] = f[i][j];
-    const T drho = collide<T, COLL>(fc, gx[j], gy[j], p, uxv[j], uyv[j]);
+    const T drho = collide<T, COLL, PP, BODY>(fc, gx[j], gy[j], p, uxv[j], uyv[j]);
     finite = finite && isfinite(drho);
 #pragma unroll
     for (int i = 0; i < 9; i++) f[i][j] = fc[i];
@@ -360,11 +395,11 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
   for (int i = 0; i < 9; i++) {
     const bool to_wall = ODD && ((cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m));
     if (!ODD || to_wall) {
-      if (active) vst<S, V>(A + opp(i) * P + here, f[i], p.scale);
+      if (active) vst<S, V>(A + opp(i) * P + here, f[i]);
     } else {
       const long long base = i * P + row[1 + cy(i)];
       if (cx(i) == 0) {
-        if (active) vst<S, V>(A + base + x0, f[i], p.scale);
+        if (active) vst<S, V>(A + base + x0, f[i]);
       } else if (cx(i) > 0) {  // destination x + 1
         const T in = __shfl_up_sync(0xffffffffu, f[i][V - 1], 1);
         if (active) {
@@ -373,12 +408,12 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
             v[0] = in;
 #pragma unroll
             for (int j = 1; j < V; j++) v[j] = f[i][j - 1];
-            vst<S, V>(A + base + x0, v, p.scale);
+            vst<S, V>(A + base + x0, v);
           } else {
 #pragma unroll
-            for (int j = 0; j < V - 1; j++) A[base + x0 + 1 + j] = Store<S>::st(f[i][j] * p.scale);
+            for (int j = 0; j < V - 1; j++) A[base + x0 + 1 + j] = Store<S>::st(f[i][j]);
           }
-          if (edge_r) A[base + xr] = Store<S>::st(f[i][V - 1] * p.scale);
+          if (edge_r) A[base + xr] = Store<S>::st(f[i][V - 1]);
         }
       } else {  // destination x - 1
         const T in = __shfl_down_sync(0xffffffffu, f[i][0], 1);
@@ -388,12 +423,12 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
 #pragma unroll
             for (int j = 0; j < V - 1; j++) v[j] = f[i][j + 1];
             v[V - 1] = in;
-            vst<S, V>(A + base + x0, v, p.scale);
+            vst<S, V>(A + base + x0, v);
           } else {
 #pragma unroll
-            for (int j = 1; j < V; j++) A[base + x0 + j - 1] = Store<S>::st(f[i][j] * p.scale);
+            for (int j = 1; j < V; j++) A[base + x0 + j - 1] = Store<S>::st(f[i][j]);
           }
-          if (lane == 0) A[base + xl] = Store<S>::st(f[i][0] * p.scale);
+          if (lane == 0) A[base + xl] = Store<S>::st(f[i][0]);
         }
       }
     }
@@ -408,15 +443,15 @@ constexpr int VEC_ROWS = TILE_Y;  // warps (rows) per block of the vectorised ke
 // for in instructions and registers although only two rows are walls.  yb is the tile
 // row's first row; the test is uniform per block.
 template <typename S, int COLL, bool ODD, int BC, bool FORCED, int V = Vec<S>::V,
-          typename GG = Geom, typename PP = CollP<typename Store<S>::T>>
+          bool BODY = true, typename GG = Geom, typename PP = CollP<typename Store<S>::T>>
 __device__ __forceinline__ void sc_vec_rows(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
                                             typename Store<S>::T *__restrict__ gf,
                                             typename Store<S>::T *__restrict__ uf, const GG &geo,
                                             const PP &p, int *status, int xb, int yb) {
   if (BC != IILBM_BC_PERIODIC && (yb == 0 || yb + VEC_ROWS >= geo.ny))
-    sc_vec_block<S, COLL, ODD, BC, FORCED, V, true>(A, Jf, gf, uf, geo, p, status, xb, yb);
+    sc_vec_block<S, COLL, ODD, BC, FORCED, V, true, BODY>(A, Jf, gf, uf, geo, p, status, xb, yb);
   else
-    sc_vec_block<S, COLL, ODD, BC, FORCED, V, false>(A, Jf, gf, uf, geo, p, status, xb, yb);
+    sc_vec_block<S, COLL, ODD, BC, FORCED, V, false, BODY>(A, Jf, gf, uf, geo, p, status, xb, yb);
 }
 
 template <typename S, int COLL, bool ODD, int BC, bool FORCED, typename GG = Geom,

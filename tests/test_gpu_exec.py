@@ -92,8 +92,9 @@ def test_timing_counts_launches_in_graph_and_eager_modes():
     g.iilbm_set_timing(True)
     g.step(64 + 5)
     ms, n, k = g.iilbm_get_timing()
-    # per step: lean and forced stream-collide, interpolation, fused interface kernel
-    assert n == 69 and k == 69 * 4 and 0 < ms < 69 * 10.0
+    # per step: lean and forced stream-collide, interpolation fused with the next
+    # level's interface phase
+    assert n == 69 and k == 69 * 3 and 0 < ms < 69 * 10.0
     g.iilbm_set_option(iilbm.OPT_CUDA_GRAPH, 0)
     g.iilbm_set_timing(True)
     g.step(7)
@@ -118,3 +119,28 @@ def test_forced_blocks_option_leaves_results_unchanged():
     assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max() and np.abs(a).max() > 0
     with pytest.raises(iilbm.IilbmError):
         gs[0].set_option(iilbm.OPT_FORCED_BLOCKS, -1)
+
+
+@pytest.mark.parametrize("n", [3, 5, 10, 11, 17])
+def test_fused_interface_phase_on_short_polygons(orc, n):
+    """The pipelined step interpolates a halo of markers around each block of 8 segments
+    (indices wrapping around the polygon); with 3 to 17 markers the halo wraps onto the
+    block's own markers.  Overlapped (fused) and serial steps agree, and both follow the
+    FP64 oracle."""
+    X = W.circle_markers(20.3, 19.6, 2.0 + 0.4 * n, n)
+    dX = W.polygon_perimeter(X) / n
+    out = []
+    for overlap in (1, 0):
+        g, o = make_pair(orc, 40, 40, collision="mrt", storage="f64", tau=0.8)
+        g.set_option(iilbm.OPT_OVERLAP, overlap)
+        # a stretched polygon relaxing: the markers move every step
+        set_membrane(orc, g, o, X * 1.1 - 2.0, "spring", 0.02, dX)
+        g.step(45)
+        o.step(45)
+        umax = max(np.abs(o.markers()["U"]).max(), 1e-6)
+        assert np.abs(o.markers()["U"]).max() > 1e-6
+        assert vel_error(g, o, umax) < 1e-12
+        assert np.abs(g.get_markers()["X"] - o.markers()["X"]).max() < 1e-12
+        out.append(g.get_markers())
+    for k in ("X", "U", "G"):
+        assert np.abs(out[0][k] - out[1][k]).max() <= 1e-13 * max(np.abs(out[1][k]).max(), 1e-9)

@@ -590,6 +590,8 @@ def run_learned(args):
                                       "dominates; the stream-collide is the HBM part)",
                             "peak_source": peak_kind, "alg_bytes_per_step": step_bytes},
                "cpu_baseline": cpu, "e2e": None, "clocks": clk,
+               # per step: lean and forced stream-collide, interpolation, force
+               # iteration, marker and segment passes, channel ends
                "gpu_launches": 7 * max(args.steps, 32)}
         print(json.dumps(out), flush=True)
 

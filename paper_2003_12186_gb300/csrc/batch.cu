@@ -355,8 +355,11 @@ void sync_lattices(iilbm_batch *B) {
   }
 }
 
+// Lean stream-collide; with interfaces the forced one, the interpolation, the marker
+// and the segment pass (and the force iteration under direct forcing); a channel adds
+// its boundary kernel.
 long long batch_kernels_per_step(const iilbm_batch *B) {
-  return 1 + (B->any_iface ? 5 + (B->any_direct ? 1 : 0) : 0) + (B->bc == IILBM_BC_CHANNEL ? 1 : 0);
+  return 1 + (B->any_iface ? 4 + (B->any_direct ? 1 : 0) : 0) + (B->bc == IILBM_BC_CHANNEL ? 1 : 0);
 }
 
 // One time step of every lattice (same structure as the single-lattice step).

@@ -31,118 +31,13 @@
 
 namespace iilbm {
 
-constexpr int SEGS_PER_BLOCK = 8;
-// Warps per block: each takes segments w, w + IFACE_WARPS, ...  The kernel waits on
-// memory most of its time, beside the register-heavy lean stream-collide; fewer warps
-// per segment hold fewer of the registers that stream-collide blocks could use.
-constexpr int IFACE_WARPS = 4;
-
-// Inputs of the fused interpolation (INTERP = true): the collision velocity of the
-// streamed level and that level's marker snapshot; U and the new X go to the markers.
-template <typename T>
-struct InterpIn {
-  const T *uf;
-  const double *Xp;
-  const long long *Xqp;
-  double *U;
-  int moves;
-};
-
 template <typename T, bool INTERP>
 __global__ void __launch_bounds__(32 * IFACE_WARPS)
     k_interface(double *X, const double *__restrict__ aux, int n, iilbm_interface_params ip,
                 int jump, Geom geo, T *gf, T *Jf, TileBuf tb, double *G, double *Fn,
                 double *nrm, long long *Xq, int *status, InterpIn<T> in) {
-  __shared__ double sx[SEGS_PER_BLOCK + 3][2];  // markers a - 1 .. a + nseg + 1
-  __shared__ long long sq[SEGS_PER_BLOCK + 1][2];
-  __shared__ double sfn[SEGS_PER_BLOCK + 1];
-  __shared__ T spx[SEGS_PER_BLOCK], spy[SEGS_PER_BLOCK];
-  __shared__ int sspread[SEGS_PER_BLOCK];
-  const int a = blockIdx.x * SEGS_PER_BLOCK;
-  const int nseg = min(SEGS_PER_BLOCK, n - a);
-  const int t = threadIdx.x;
-  const unsigned tag = *tb.tag;  // issued early: the tile flags need it last
-  // ---- positions of markers a - 1 .. a + nseg + 1 (n >= 3: one wrap at most)
-  if (t < nseg + 3) {
-    int j = a - 1 + t;
-    if (j < 0) j += n;
-    else if (j >= n) j -= n;
-    if (INTERP) {
-      const double x = in.Xp[2 * j], y = in.Xp[2 * j + 1];
-      double ux, uy;
-      interp_at<T>(in.uf, geo, x, in.Xqp[2 * j], y, in.Xqp[2 * j + 1], ux, uy);
-      const double xn = in.moves ? x + ux : x, yn = in.moves ? y + uy : y;
-      sx[t][0] = xn;
-      sx[t][1] = yn;
-      if (t >= 1 && t <= nseg) {  // owned by this block
-        in.U[2 * j] = ux;
-        in.U[2 * j + 1] = uy;
-        if (in.moves) {
-          X[2 * j] = xn;
-          X[2 * j + 1] = yn;
-        }
-      }
-    } else {
-      sx[t][0] = X[2 * j];
-      sx[t][1] = X[2 * j + 1];
-    }
-  }
-  __syncthreads();
-  // ---- markers a .. a + nseg (the last is the next block's first, or marker 0)
-  if (t <= nseg) {
-    const int j = a + t == n ? 0 : a + t;
-    const double x = sx[t + 1][0], y = sx[t + 1][1];
-    const MarkerForce<T> m = marker_force_at<T>(x, y, sx[t + 2][0], sx[t + 2][1], sx[t][0],
-                                                sx[t][1], aux, j, ip, jump, geo);
-    const bool inside = in_region(x, y);
-    const long long qx = inside ? __double2ll_rn(x * QSCALE) : XQ_OUT;
-    const long long qy = inside ? __double2ll_rn(y * QSCALE) : XQ_OUT;
-    sq[t][0] = qx;
-    sq[t][1] = qy;
-    sfn[t] = (double)m.fn;
-    if (t < nseg) {  // owned by this block
-      if (m.bad) atomicOr(status, ST_INTERFACE);
-      G[2 * j] = (double)m.gx;
-      G[2 * j + 1] = (double)m.gy;
-      Fn[j] = (double)m.fn;
-      nrm[2 * j] = (double)m.nx;
-      nrm[2 * j + 1] = (double)m.ny;
-      Xq[2 * j] = qx;
-      Xq[2 * j + 1] = qy;
-      // the spread goes into the tiles that segment j -> j+1 flags: it needs both ends
-      sspread[t] = inside && in_region(sx[t + 2][0], sx[t + 2][1]);
-      spx[t] = m.px;
-      spy[t] = m.py;
-    }
-  }
-  __syncthreads();
-  const int w = t >> 5, lane = t & 31;
-  // ---- cut links and tile flags of segments a + w, a + w + IFACE_WARPS, ...
-  for (int k = w; k < nseg; k += IFACE_WARPS)
-    segment_links<T>(sq[k][0], sq[k][1], sq[k + 1][0], sq[k + 1][1], sfn[k], sfn[k + 1], lane,
-                     jump, geo, Jf, tb, tag);
-  // ---- spread of the segments' first markers, 16 lanes (one stencil node each) per
-  // marker (Eq. 46 / 17)
-  for (int k0 = w; k0 < nseg; k0 += 2 * IFACE_WARPS) {
-    const int k = k0 + (lane < 16 ? 0 : IFACE_WARPS), l = lane & 15;
-    if (k >= nseg || !sspread[k]) continue;
-    int bx, by;
-    T wx[4], wy[4];
-    stencil_weights<T>(sx[k + 1][0], sq[k][0], bx, wx);
-    stencil_weights<T>(sx[k + 1][1], sq[k][1], by, wy);
-    int xi = bx + (l & 3), yi = by + (l >> 2);
-    bool ok = true;
-    if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
-    else ok = yi >= 0 && yi < geo.ny;
-    if (geo.bc == IILBM_BC_CHANNEL) ok = ok && xi >= 0 && xi < geo.nx;
-    else xi = wrap(xi, geo.nx);
-    const T wgt = wx[l & 3] * wy[l >> 2];
-    if (ok && wgt != T(0)) {
-      const long long here = (long long)yi * geo.pitch + xi;
-      atomicAdd(&gf[here], spx[k] * wgt);
-      atomicAdd(&gf[geo.plane + here], spy[k] * wgt);
-    }
-  }
+  interface_block<T, INTERP, IFACE_WARPS>(blockIdx.x * SEGS_PER_BLOCK, X, aux, n, ip, jump, geo, gf, Jf, tb,
+                             G, Fn, nrm, Xq, status, in);
 }
 
 template <typename T, bool INTERP>

@@ -140,12 +140,14 @@ __device__ inline int orient_link_pt(long long px, long long py, int ex, int ey,
   return ex > 0 ? -1 : 1;
 }
 
-// ------------------------------------------------------------- marker pass
-// One thread per marker j: its force and normal split, its coordinates snapped to
-// 2^-24 for the segment pass, and the spreading of its point force P_j over the 4 x 4
-// stencil (Eq. 46 in II-LBM, Eq. 17 in IB-LBM).  Running this per thread rather than
-// once per warp keeps GB300's FP64 pipe (a small fraction of its FP32 rate) off the
-// critical path: the FP64 work of a marker is done once, by one lane.
+// ----------------------------------------------------------- Peskin stencil
+// The marker pass (interface_block) runs one thread per marker: its force and normal
+// split, its coordinates snapped to 2^-24 for the segment pass.  Running this per
+// thread rather than once per warp keeps GB300's FP64 pipe (a small fraction of its
+// FP32 rate) off the critical path: the FP64 work of a marker is done once, by one lane.
+// Its point force P_j is spread over the 4 x 4 stencil (Eq. 46 in II-LBM, Eq. 17 in
+// IB-LBM) by 16 lanes of the warp of its segment (by the marker's own thread in the
+// batched marker pass).
 //
 // Stencil: nodes floor(X) - 1 .. floor(X) + 2 on each axis.  For FP64 storage the
 // floor and the node offsets are taken from the FP64 coordinate; otherwise from the
@@ -169,6 +171,8 @@ __device__ inline bool in_region(double x, double y) {
   return fabs(x) <= MAX_COORD && fabs(y) <= MAX_COORD;
 }
 
+// The marker pass of the batched executor, one thread per marker j of its flattened
+// list: force, split, snapped coordinates, and the spread of P_j over the stencil.
 template <typename T>
 __device__ __forceinline__ void interface_marker(const double *__restrict__ X,
                                                  const double *__restrict__ aux, int n, int j,
@@ -458,6 +462,129 @@ __device__ __forceinline__ void marker_prep(const MarkerPrep &mp) {
   for (int i = blockIdx.x * nt + tid; i < mp.n2; i += gridDim.x * nt) {
     mp.Xp[i] = mp.X[i];
     mp.Xqp[i] = mp.Xq[i];
+  }
+}
+
+// ------------------------------------------------------- interface phase block
+constexpr int SEGS_PER_BLOCK = 8;
+// Warps per block: each takes segments w, w + WARPS, ...  A single lattice's interface
+// kernel (one wave of blocks) waits on memory most of its time beside the register-
+// heavy lean stream-collide, and 4 warps per 8 segments hold fewer of the registers
+// that stream-collide blocks could use.  (The batched executor, with many waves of
+// blocks, is limited by throughput instead: there separate marker and segment passes
+// with every thread busy beat this block, whose other warps wait while one warp
+// interpolates and forms the forces.)
+constexpr int IFACE_WARPS = 4;
+
+// Inputs of the fused interpolation (INTERP = true): the collision velocity of the
+// streamed level and that level's marker snapshot; U and the new X go to the markers.
+template <typename T>
+struct InterpIn {
+  const T *uf;
+  const double *Xp;
+  const long long *Xqp;
+  double *U;
+  int moves;
+};
+
+// The interface work of segments a .. a + 7 (and their end markers) of one lattice,
+// for a block of 32 WARPS threads; with INTERP, preceded by the interpolation of the
+// level just streamed (see interface.cu).
+template <typename T, bool INTERP, int WARPS>
+__device__ __forceinline__ void interface_block(const int a, double *X,
+                                                const double *__restrict__ aux, int n,
+                                                const iilbm_interface_params &ip, int jump,
+                                                const Geom &geo, T *gf, T *Jf, const TileBuf &tb,
+                                                double *G, double *Fn, double *nrm, long long *Xq,
+                                                int *status, const InterpIn<T> &in) {
+  __shared__ double sx[SEGS_PER_BLOCK + 3][2];  // markers a - 1 .. a + nseg + 1
+  __shared__ long long sq[SEGS_PER_BLOCK + 1][2];
+  __shared__ double sfn[SEGS_PER_BLOCK + 1];
+  __shared__ T spx[SEGS_PER_BLOCK], spy[SEGS_PER_BLOCK];
+  __shared__ int sspread[SEGS_PER_BLOCK];
+  const int nseg = min(SEGS_PER_BLOCK, n - a);
+  const int t = threadIdx.x;
+  const unsigned tag = *tb.tag;  // issued early: the tile flags need it last
+  // ---- positions of markers a - 1 .. a + nseg + 1 (n >= 3: one wrap at most)
+  if (t < nseg + 3) {
+    int j = a - 1 + t;
+    if (j < 0) j += n;
+    else if (j >= n) j -= n;
+    if (INTERP) {
+      const double x = in.Xp[2 * j], y = in.Xp[2 * j + 1];
+      double ux, uy;
+      interp_at<T>(in.uf, geo, x, in.Xqp[2 * j], y, in.Xqp[2 * j + 1], ux, uy);
+      const double xn = in.moves ? x + ux : x, yn = in.moves ? y + uy : y;
+      sx[t][0] = xn;
+      sx[t][1] = yn;
+      if (t >= 1 && t <= nseg) {  // owned by this block
+        in.U[2 * j] = ux;
+        in.U[2 * j + 1] = uy;
+        if (in.moves) {
+          X[2 * j] = xn;
+          X[2 * j + 1] = yn;
+        }
+      }
+    } else {
+      sx[t][0] = X[2 * j];
+      sx[t][1] = X[2 * j + 1];
+    }
+  }
+  __syncthreads();
+  // ---- markers a .. a + nseg (the last is the next block's first, or marker 0)
+  if (t <= nseg) {
+    const int j = a + t == n ? 0 : a + t;
+    const double x = sx[t + 1][0], y = sx[t + 1][1];
+    const MarkerForce<T> m = marker_force_at<T>(x, y, sx[t + 2][0], sx[t + 2][1], sx[t][0],
+                                                sx[t][1], aux, j, ip, jump, geo);
+    const bool inside = in_region(x, y);
+    const long long qx = inside ? __double2ll_rn(x * QSCALE) : XQ_OUT;
+    const long long qy = inside ? __double2ll_rn(y * QSCALE) : XQ_OUT;
+    sq[t][0] = qx;
+    sq[t][1] = qy;
+    sfn[t] = (double)m.fn;
+    if (t < nseg) {  // owned by this block
+      if (m.bad) atomicOr(status, ST_INTERFACE);
+      G[2 * j] = (double)m.gx;
+      G[2 * j + 1] = (double)m.gy;
+      Fn[j] = (double)m.fn;
+      nrm[2 * j] = (double)m.nx;
+      nrm[2 * j + 1] = (double)m.ny;
+      Xq[2 * j] = qx;
+      Xq[2 * j + 1] = qy;
+      // the spread goes into the tiles that segment j -> j+1 flags: it needs both ends
+      sspread[t] = inside && in_region(sx[t + 2][0], sx[t + 2][1]);
+      spx[t] = m.px;
+      spy[t] = m.py;
+    }
+  }
+  __syncthreads();
+  const int w = t >> 5, lane = t & 31;
+  // ---- cut links and tile flags of segments a + w, a + w + WARPS, ...
+  for (int k = w; k < nseg; k += WARPS)
+    segment_links<T>(sq[k][0], sq[k][1], sq[k + 1][0], sq[k + 1][1], sfn[k], sfn[k + 1], lane,
+                     jump, geo, Jf, tb, tag);
+  // ---- spread of the segments' first markers, 16 lanes (one stencil node each) per
+  // marker (Eq. 46 / 17)
+  for (int k0 = w; k0 < nseg; k0 += 2 * WARPS) {
+    const int k = k0 + (lane < 16 ? 0 : WARPS), l = lane & 15;
+    if (k >= nseg || !sspread[k]) continue;
+    int bx, by;
+    T wx[4], wy[4];
+    stencil_weights<T>(sx[k + 1][0], sq[k][0], bx, wx);
+    stencil_weights<T>(sx[k + 1][1], sq[k][1], by, wy);
+    int xi = bx + (l & 3), yi = by + (l >> 2);
+    bool ok = true;
+    if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
+    else ok = yi >= 0 && yi < geo.ny;
+    if (geo.bc == IILBM_BC_CHANNEL) ok = ok && xi >= 0 && xi < geo.nx;
+    else xi = wrap(xi, geo.nx);
+    const T wgt = wx[l & 3] * wy[l >> 2];
+    if (ok && wgt != T(0)) {
+      const long long here = (long long)yi * geo.pitch + xi;
+      atomicAdd(&gf[here], spx[k] * wgt);
+      atomicAdd(&gf[geo.plane + here], spy[k] * wgt);
+    }
   }
 }
 

@@ -31,24 +31,28 @@ __device__ inline void flag_tile(const TileBuf &tb, int tile, unsigned tag) {
   }
 }
 
-// Tile indices (along one axis of n nodes, tiles of width w) covered by the node range
-// [a, b], wrapped on a periodic axis, clipped otherwise.  Returns their number (at most
-// MAX_TILE_SPAN; ranges here span at most 23 nodes).
-constexpr int MAX_TILE_SPAN = 8;
-__device__ inline int tile_span(int a, int b, int n, bool periodic, int w, int *out) {
-  if (!periodic) {
-    a = max(a, 0);
-    b = min(b, n - 1);
+// Tiles (along one axis of n nodes, tiles of width w) covered by the node range
+// [a, b]: the cyclic range of cnt tiles from t0 on a periodic axis (all of them once
+// the range spans the axis), the clipped range otherwise.  Tile k of the range is
+// (t0 + k) mod (number of tiles on the axis).
+__device__ inline void tile_range(int a, int b, int n, bool periodic, int w, int &t0,
+                                  int &cnt) {
+  const int nt = (n + w - 1) / w;
+  if (periodic) {
+    if (b - a + 1 >= n) {
+      t0 = 0;
+      cnt = nt;
+      return;
+    }
+    t0 = wrap(a, n) / w;
+    const int t1 = wrap(b, n) / w;
+    cnt = t1 >= t0 ? t1 - t0 + 1 : t1 + nt - t0 + 1;
+    return;
   }
-  int cnt = 0, last = -1;
-  for (int v = a; v <= b && cnt < MAX_TILE_SPAN;) {
-    const int u = periodic ? wrap(v, n) : v;
-    const int t = u / w;
-    if (t != last) out[cnt++] = t;
-    last = t;
-    v += min(w - u % w, n - u);  // to the next tile boundary (or the end of the axis)
-  }
-  return cnt;
+  a = max(a, 0);
+  b = min(b, n - 1);
+  t0 = a / w;
+  cnt = a <= b ? b / w - t0 + 1 : 0;
 }
 
 // Force of marker j and its split: G_j, n_j, Fn_j = G_j.n_j/|X_s|_j, and the point
@@ -167,6 +171,17 @@ __device__ inline void stencil_weights(double x, long long q, int &base, T w[4])
   }
 }
 
+// The weight of stencil node base + k alone (the same value stencil_weights gives it).
+template <typename T>
+__device__ inline T stencil_weight(double x, long long q, int k, int &base) {
+  if (sizeof(T) == 8) {
+    base = (int)floor(x) - 1;
+    return phi4<T>(T((double)(base + k) - x));
+  }
+  base = (int)(q >> 24) - 1;
+  return phi4<T>(T((int)((long long)(base + k) * (long long)QSCALE - q)) * T(1.0 / QSCALE));
+}
+
 __device__ inline bool in_region(double x, double y) {
   return fabs(x) <= MAX_COORD && fabs(y) <= MAX_COORD;
 }
@@ -229,8 +244,6 @@ __device__ __forceinline__ void interface_marker(const double *__restrict__ X,
 // segment each node's sign is computed once and published to the warp as one bit of a
 // 64-bit ballot; a candidate link then costs two bit lookups, and only links whose ends
 // straddle the line take the two link-side tests.
-// Crossings found by a lane are buffered and their coefficients computed together.
-constexpr int CROSS_BUF = 4;
 
 template <typename T>
 __device__ __forceinline__ void segment_links(long long ax, long long ay, long long bx,
@@ -275,39 +288,7 @@ __device__ __forceinline__ void segment_links(long long ax, long long ay, long l
       }
       return orient_seg_node(ax, ay, bx, by, (long long)qx * Q, (long long)qy * Q);
     };
-    // buffered crossings: destination (wrapped), direction, sign, link-side orientations
-    int bc_x[CROSS_BUF], bc_y[CROSS_BUF], bc_i[CROSS_BUF], bc_s[CROSS_BUF];
-    long long bc_o3[CROSS_BUF], bc_o4[CROSS_BUF];
-    int nb = 0;
     const float fA = (float)FnA, fB = (float)FnB;  // FP32 path: converted once per warp
-    // apply the buffered crossings: coefficient s w_i/c_s^2 Fn(t), t = o3 / (o3 - o4)
-    // along A -> B (Fn linear along the segment).  FP64 for FP64 storage (an FP32
-    // quotient refined by one Newton step); FP32 otherwise, where |o3|, |o3 - o4| <
-    // 2^30 convert exactly and t carries a relative error of a few FP32 ulps.
-    auto flush = [&]() {
-#pragma unroll
-      for (int q = 0; q < CROSS_BUF; q++) {
-        if (q >= nb) break;
-        const int i = bc_i[q];
-        T coef;
-        if (sizeof(T) == 8) {
-          const double num = (double)bc_o3[q], dd = (double)(bc_o3[q] - bc_o4[q]);
-          const float rf = 1.0f / (float)dd;
-          double t = (double)((float)num * rf);
-          t = fma(num - t * dd, (double)rf, t);
-          t = fmin(fmax(t, 0.0), 1.0);
-          coef = T((double)bc_s[q] * 3.0 * wt<double>(i) * ((1.0 - t) * FnA + t * FnB));
-        } else {
-          const float num = (float)(int)bc_o3[q], dd = (float)(int)(bc_o3[q] - bc_o4[q]);
-          const float t = fminf(fmaxf(num / dd, 0.0f), 1.0f);
-          coef = T((float)bc_s[q] * 3.0f * wt<float>(i) * ((1.0f - t) * fA + t * fB));
-        }
-        atomicAdd(&Jf[(long long)(i - 1) * geo.plane + (long long)bc_y[q] * geo.pitch + bc_x[q]],
-                  coef);
-      }
-      found += nb;
-      nb = 0;
-    };
     // cell -> (column, row) of the W-wide box by an FP32 quotient: (cell + 1/2) / W is
     // at least 1/(2W) away from an integer, far above its rounding error (W <= 19)
     const float invW = 1.0f / (float)W;
@@ -331,16 +312,28 @@ __device__ __forceinline__ void segment_links(long long ax, long long ay, long l
         continue;
       if (geo.bc != IILBM_BC_PERIODIC && (qy < 0 || qy >= geo.ny || ys < 0 || ys >= geo.ny))
         continue;
-      if (nb == CROSS_BUF) flush();
-      bc_x[nb] = geo.bc == IILBM_BC_CHANNEL ? qx : wrap(qx, geo.nx);
-      bc_y[nb] = geo.bc == IILBM_BC_PERIODIC ? wrap(qy, geo.ny) : qy;
-      bc_i[nb] = i;
-      bc_s[nb] = s1;
-      bc_o3[nb] = o3;
-      bc_o4[nb] = o4;
-      nb++;
+      // coefficient s w_i/c_s^2 Fn(t), t = o3 / (o3 - o4) along A -> B (Fn linear along
+      // the segment).  FP64 for FP64 storage (an FP32 quotient refined by one Newton
+      // step); FP32 otherwise, where |o3|, |o3 - o4| < 2^30 convert exactly and t
+      // carries a relative error of a few FP32 ulps.
+      T coef;
+      if (sizeof(T) == 8) {
+        const double num = (double)o3, dd = (double)(o3 - o4);
+        const float rf = 1.0f / (float)dd;
+        double t = (double)((float)num * rf);
+        t = fma(num - t * dd, (double)rf, t);
+        t = fmin(fmax(t, 0.0), 1.0);
+        coef = T((double)s1 * 3.0 * wt<double>(i) * ((1.0 - t) * FnA + t * FnB));
+      } else {
+        const float num = (float)(int)o3, dd = (float)(int)(o3 - o4);
+        const float t = fminf(fmaxf(num / dd, 0.0f), 1.0f);
+        coef = T((float)s1 * 3.0f * wt<float>(i) * ((1.0f - t) * fA + t * fB));
+      }
+      const int dx = geo.bc == IILBM_BC_CHANNEL ? qx : wrap(qx, geo.nx);
+      const int dy = geo.bc == IILBM_BC_PERIODIC ? wrap(qy, geo.ny) : qy;
+      atomicAdd(&Jf[(long long)(i - 1) * geo.plane + (long long)dy * geo.pitch + dx], coef);
+      found++;
     }
-    flush();
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) found += __shfl_xor_sync(0xffffffffu, found, o);
@@ -349,13 +342,18 @@ __device__ __forceinline__ void segment_links(long long ax, long long ay, long l
   // (its cut links, and the spread of marker k) lies in
   // [floor(min x) - 2, ceil(max x) + 2] x [floor(min y) - 2, ceil(max y) + 2]
   if (inside) {
-    int cols[MAX_TILE_SPAN], rows[MAX_TILE_SPAN];
-    const int nc = tile_span(qfloor(min(ax, bx)) - 2, qceil(max(ax, bx)) + 2, geo.nx,
-                             geo.bc != IILBM_BC_CHANNEL, TILE_X, cols);
-    const int nr = tile_span(qfloor(min(ay, by)) - 2, qceil(max(ay, by)) + 2, geo.ny,
-                             geo.bc == IILBM_BC_PERIODIC, TILE_Y, rows);
-    for (int t = lane; t < nc * nr; t += 32)
-      flag_tile(tb, rows[t / nc] * geo.ntx + cols[t % nc], tag);
+    int c0, nc, r0, nr;
+    tile_range(qfloor(min(ax, bx)) - 2, qceil(max(ax, bx)) + 2, geo.nx,
+               geo.bc != IILBM_BC_CHANNEL, TILE_X, c0, nc);
+    tile_range(qfloor(min(ay, by)) - 2, qceil(max(ay, by)) + 2, geo.ny,
+               geo.bc == IILBM_BC_PERIODIC, TILE_Y, r0, nr);
+    const int nty = (geo.ny + TILE_Y - 1) / TILE_Y;
+    for (int t = lane; t < nc * nr; t += 32) {
+      int col = c0 + t % nc, row = r0 + t / nc;
+      if (col >= geo.ntx) col -= geo.ntx;
+      if (row >= nty) row -= nty;
+      flag_tile(tb, row * geo.ntx + col, tag);
+    }
   }
 }
 
@@ -570,16 +568,15 @@ __device__ __forceinline__ void interface_block(const int a, double *X,
     const int k = k0 + (lane < 16 ? 0 : WARPS), l = lane & 15;
     if (k >= nseg || !sspread[k]) continue;
     int bx, by;
-    T wx[4], wy[4];
-    stencil_weights<T>(sx[k + 1][0], sq[k][0], bx, wx);
-    stencil_weights<T>(sx[k + 1][1], sq[k][1], by, wy);
+    const T wxl = stencil_weight<T>(sx[k + 1][0], sq[k][0], l & 3, bx);
+    const T wyl = stencil_weight<T>(sx[k + 1][1], sq[k][1], l >> 2, by);
     int xi = bx + (l & 3), yi = by + (l >> 2);
     bool ok = true;
     if (geo.bc == IILBM_BC_PERIODIC) yi = wrap(yi, geo.ny);
     else ok = yi >= 0 && yi < geo.ny;
     if (geo.bc == IILBM_BC_CHANNEL) ok = ok && xi >= 0 && xi < geo.nx;
     else xi = wrap(xi, geo.nx);
-    const T wgt = wx[l & 3] * wy[l >> 2];
+    const T wgt = wxl * wyl;
     if (ok && wgt != T(0)) {
       const long long here = (long long)yi * geo.pitch + xi;
       atomicAdd(&gf[here], spx[k] * wgt);

@@ -66,8 +66,11 @@ __global__ void __launch_bounds__(32 * TILE_Y)
   }
 }
 
+// Budgeted like the lean kernel (three blocks per SM, <= 85 registers, a few spilled):
+// its blocks run beside the lean stream-collide, and each one then takes the place of
+// one lean block instead of two.
 template <typename S, int COLL, bool ODD, int BC>
-__global__ void __launch_bounds__(32 * VEC_ROWS)
+__global__ void __launch_bounds__(32 * VEC_ROWS, 3)
     k_stream_collide_vec_forced(S *__restrict__ A, typename Store<S>::T *__restrict__ Jf,
                                 typename Store<S>::T *__restrict__ gf,
                                 typename Store<S>::T *__restrict__ uf,

@@ -99,6 +99,16 @@ struct Geom {
   int bc;           // IILBM_BC_*
 };
 
+// A Geom whose boundary kind is a compile-time constant: device code templated on the
+// geometry type then reads geo.bc as a constant and drops the other kinds' branches
+// (smaller code for kernels that run once per step with a cold instruction cache).
+template <int BC>
+struct GeomC : Geom {
+  static constexpr int bc = BC;
+  GeomC() = default;
+  __host__ __device__ explicit GeomC(const Geom &g) : Geom(g) {}
+};
+
 __host__ __device__ inline int wrap(int v, int n) {
   if ((unsigned)v < (unsigned)n) return v;  // the common case: no division
   v = v % n;

@@ -31,26 +31,35 @@
 
 namespace iilbm {
 
-template <typename T, bool INTERP>
+template <typename T, bool INTERP, int BC>
 __global__ void __launch_bounds__(32 * IFACE_WARPS)
     k_interface(double *X, const double *__restrict__ aux, int n, iilbm_interface_params ip,
-                int jump, Geom geo, T *gf, T *Jf, TileBuf tb, double *G, double *Fn,
+                int jump, GeomC<BC> geo, T *gf, T *Jf, TileBuf tb, double *G, double *Fn,
                 double *nrm, long long *Xq, int *status, InterpIn<T> in) {
-  interface_block<T, INTERP, IFACE_WARPS>(blockIdx.x * SEGS_PER_BLOCK, X, aux, n, ip, jump, geo, gf, Jf, tb,
-                             G, Fn, nrm, Xq, status, in);
+  interface_block<T, INTERP, IFACE_WARPS>(blockIdx.x * SEGS_PER_BLOCK, X, aux, n, ip, jump, geo,
+                                          gf, Jf, tb, G, Fn, nrm, Xq, status, in);
 }
 
-template <typename T, bool INTERP>
-static int launch_interface(iilbm_lattice *h, int buf, cudaStream_t s) {
+template <typename T, bool INTERP, int BC>
+static void launch_interface_bc(iilbm_lattice *h, int buf, cudaStream_t s) {
   const int n = h->nm;
   const double *aux = h->ip.model == IILBM_DIRECT ? h->Gdf : h->aux;
   const TileBuf tb{h->flagsb[buf], h->tagb[buf], h->tile_list[buf], h->tile_count[buf],
                    h->d_tiles_total};
   const InterpIn<T> in{(const T *)h->uf, h->Xp, h->Xqp, h->U, h->ip.moves};
   const int blocks = (n + SEGS_PER_BLOCK - 1) / SEGS_PER_BLOCK;
-  k_interface<T, INTERP><<<blocks, 32 * IFACE_WARPS, 0, s>>>(
-      h->X, aux, n, h->ip, h->cfg.jump, h->geom, (T *)h->gb[buf], (T *)h->Jb[buf], tb, h->G,
-      h->Fn, h->nrm, h->Xq, h->d_status, in);
+  k_interface<T, INTERP, BC><<<blocks, 32 * IFACE_WARPS, 0, s>>>(
+      h->X, aux, n, h->ip, h->cfg.jump, GeomC<BC>(h->geom), (T *)h->gb[buf], (T *)h->Jb[buf], tb,
+      h->G, h->Fn, h->nrm, h->Xq, h->d_status, in);
+}
+
+template <typename T, bool INTERP>
+static int launch_interface(iilbm_lattice *h, int buf, cudaStream_t s) {
+  switch (h->geom.bc) {
+    case IILBM_BC_PERIODIC: launch_interface_bc<T, INTERP, IILBM_BC_PERIODIC>(h, buf, s); break;
+    case IILBM_BC_WALLS_Y: launch_interface_bc<T, INTERP, IILBM_BC_WALLS_Y>(h, buf, s); break;
+    default: launch_interface_bc<T, INTERP, IILBM_BC_CHANNEL>(h, buf, s);
+  }
   return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
 }
 

@@ -8,10 +8,6 @@
 
 namespace iilbm {
 
-__device__ inline int tile_of(const Geom &g, int x, int y) {
-  return (y / TILE_Y) * g.ntx + x / TILE_X;
-}
-
 struct TileBuf {
   unsigned *flags;            // a tile is flagged iff its entry equals *tag
   const unsigned *tag;
@@ -66,12 +62,12 @@ struct MarkerForce {
 };
 
 // (x, y): marker j; (xp, yp), (xm, ym): its successor and predecessor on the polygon.
-template <typename T>
+template <typename T, typename GG>
 __device__ inline MarkerForce<T> marker_force_at(double x, double y, double xp, double yp,
                                                  double xm, double ym,
                                                  const double *__restrict__ aux, int j,
                                                  const iilbm_interface_params &ip, int jump,
-                                                 const Geom &geo) {
+                                                 const GG &geo) {
   MarkerForce<T> m;
   const double dax = xp - x, day = yp - y, dbx = x - xm, dby = y - ym;  // segments k, k-1
   // validity: finite, inside the representable / valid region, short segments
@@ -116,11 +112,11 @@ __device__ inline MarkerForce<T> marker_force_at(double x, double y, double xp, 
   return m;
 }
 
-template <typename T>
+template <typename T, typename GG>
 __device__ inline MarkerForce<T> marker_force(const double *__restrict__ X,
                                               const double *__restrict__ aux, int n, int j,
                                               const iilbm_interface_params &ip, int jump,
-                                              const Geom &geo) {
+                                              const GG &geo) {
   const int jp = j + 1 == n ? 0 : j + 1, jm = j == 0 ? n - 1 : j - 1;
   return marker_force_at<T>(X[2 * j], X[2 * j + 1], X[2 * jp], X[2 * jp + 1], X[2 * jm],
                             X[2 * jm + 1], aux, j, ip, jump, geo);
@@ -188,11 +184,11 @@ __device__ inline bool in_region(double x, double y) {
 
 // The marker pass of the batched executor, one thread per marker j of its flattened
 // list: force, split, snapped coordinates, and the spread of P_j over the stencil.
-template <typename T>
+template <typename T, typename GG>
 __device__ __forceinline__ void interface_marker(const double *__restrict__ X,
                                                  const double *__restrict__ aux, int n, int j,
                                                  const iilbm_interface_params &ip, int jump,
-                                                 const Geom &geo, T *gf, double *G, double *Fn,
+                                                 const GG &geo, T *gf, double *G, double *Fn,
                                                  double *nrm, long long *Xq, int *status) {
   const MarkerForce<T> m = marker_force<T>(X, aux, n, j, ip, jump, geo);
   if (m.bad) atomicOr(status, ST_INTERFACE);
@@ -245,10 +241,10 @@ __device__ __forceinline__ void interface_marker(const double *__restrict__ X,
 // 64-bit ballot; a candidate link then costs two bit lookups, and only links whose ends
 // straddle the line take the two link-side tests.
 
-template <typename T>
+template <typename T, typename GG>
 __device__ __forceinline__ void segment_links(long long ax, long long ay, long long bx,
                                               long long by, double FnA, double FnB, int lane,
-                                              int jump, const Geom &geo, T *Jf,
+                                              int jump, const GG &geo, T *Jf,
                                               const TileBuf &tb, unsigned tag) {
   const bool inside = ax != XQ_OUT && bx != XQ_OUT;
   const long long Q = (long long)QSCALE;
@@ -358,10 +354,10 @@ __device__ __forceinline__ void segment_links(long long ax, long long ay, long l
 }
 
 // The segment pass of segment k -> k+1 from the marker pass's outputs in global memory.
-template <typename T>
+template <typename T, typename GG>
 __device__ __forceinline__ void interface_segment(const long long *__restrict__ Xq,
                                                   const double *__restrict__ Fn, int n, int k,
-                                                  int lane, int jump, const Geom &geo, T *Jf,
+                                                  int lane, int jump, const GG &geo, T *Jf,
                                                   const TileBuf &tb) {
   const unsigned tag = *tb.tag;
   const int kp = k + 1 == n ? 0 : k + 1;
@@ -375,8 +371,8 @@ __device__ __forceinline__ void interface_segment(const long long *__restrict__ 
 // spread to (same floor and weights); the marker moves X += U when it moves.  FP64
 // storage: FP64 throughout.  Otherwise each stencil row is summed in FP32 and the four
 // row sums are accumulated in FP64.
-template <typename T>
-__device__ __forceinline__ void interp_at(const T *__restrict__ uf, const Geom &geo, double x,
+template <typename T, typename GG>
+__device__ __forceinline__ void interp_at(const T *__restrict__ uf, const GG &geo, double x,
                                           long long qx, double y, long long qy, double &sx,
                                           double &sy) {
   sx = 0.0;
@@ -417,8 +413,8 @@ __device__ __forceinline__ void interp_at(const T *__restrict__ uf, const Geom &
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void interp_marker(const T *__restrict__ uf, const Geom &geo,
+template <typename T, typename GG>
+__device__ __forceinline__ void interp_marker(const T *__restrict__ uf, const GG &geo,
                                               double *X, const long long *__restrict__ Xq,
                                               int k, double *U, int moves) {
   const double x = X[2 * k], y = X[2 * k + 1];
@@ -488,11 +484,11 @@ struct InterpIn {
 // The interface work of segments a .. a + 7 (and their end markers) of one lattice,
 // for a block of 32 WARPS threads; with INTERP, preceded by the interpolation of the
 // level just streamed (see interface.cu).
-template <typename T, bool INTERP, int WARPS>
+template <typename T, bool INTERP, int WARPS, typename GG>
 __device__ __forceinline__ void interface_block(const int a, double *X,
                                                 const double *__restrict__ aux, int n,
                                                 const iilbm_interface_params &ip, int jump,
-                                                const Geom &geo, T *gf, T *Jf, const TileBuf &tb,
+                                                const GG &geo, T *gf, T *Jf, const TileBuf &tb,
                                                 double *G, double *Fn, double *nrm, long long *Xq,
                                                 int *status, const InterpIn<T> &in) {
   __shared__ double sx[SEGS_PER_BLOCK + 3][2];  // markers a - 1 .. a + nseg + 1

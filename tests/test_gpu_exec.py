@@ -144,3 +144,36 @@ def test_fused_interface_phase_on_short_polygons(orc, n):
         out.append(g.get_markers())
     for k in ("X", "U", "G"):
         assert np.abs(out[0][k] - out[1][k]).max() <= 1e-13 * max(np.abs(out[1][k]).max(), 1e-9)
+
+
+@pytest.mark.parametrize("bc", ["walls", "channel"])
+def test_pipelined_membrane_near_walls(orc, bc):
+    """The fused interpolation / interface kernel is compiled per boundary kind: a moving
+    membrane about 4 nodes from a wall (and, in a channel, from the inflow end),
+    overlapped and serial, against the FP64 oracle step by step."""
+    nx, ny, tau = 48, 40, 0.8
+    s = W.mrt_rates(tau)
+    n = 26
+    X = W.circle_markers(12.0, 11.0, 7.0, n) * np.array([1.08, 1.0]) - np.array([1.0, 0.0])
+    assert X[:, 1].min() > 3.0 and X[:, 0].min() > 3.0
+    dX = W.polygon_perimeter(X) / n * 0.9  # stretched: the membrane moves every step
+    kw = dict(collision=iilbm.MRT, storage="f64", tau=tau, s=s)
+    if bc == "walls":
+        kw_g, kw_o = dict(bc=iilbm.BC_WALLS_Y), dict(bc=orc.BC_WALLS_Y)
+    else:
+        kw_g, kw_o = dict(bc=iilbm.BC_CHANNEL, u_max=0.02), dict(bc=orc.BC_CHANNEL, u_max=0.02)
+    outs = []
+    for overlap in (1, 0):
+        g = iilbm.Lattice(nx, ny, **kw, **kw_g)
+        o = orc.Oracle(nx, ny, collision=orc.MRT, tau=tau, s=s, **kw_o)
+        g.set_option(iilbm.OPT_OVERLAP, overlap)
+        set_membrane(orc, g, o, X, "spring", 0.03, dX)
+        for _ in range(3):
+            g.step(13)
+            o.step(13)
+            assert np.abs(g.get_populations() - o.get_df()).max() < 1e-14
+            assert np.abs(g.get_markers()["X"] - o.markers()["X"]).max() < 1e-12
+            assert g.iilbm_get_cut_link_count() == o.cut_link_count()
+        assert np.abs(o.markers()["U"]).max() > 1e-5
+        outs.append(g.get_markers()["X"])
+    assert np.abs(outs[0] - outs[1]).max() < 1e-13

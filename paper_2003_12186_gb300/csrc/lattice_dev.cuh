@@ -4,6 +4,8 @@
 // the lean and forced AA-pattern stream-collide.
 #pragma once
 
+#include <type_traits>
+
 #include "iilbm_internal.cuh"
 
 #include <cmath>
@@ -170,18 +172,52 @@ struct alignas(sizeof(S) * V) Pack {
   S v[V];
 };
 
+// 16-bit storage converts two values per instruction where it can (the same rounding,
+// to nearest even, as one at a time).
 template <typename S, int V>
 __device__ inline void vld(const S *p, typename Store<S>::T *o) {
   const Pack<S, V> t = *reinterpret_cast<const Pack<S, V> *>(p);
+  if constexpr (std::is_same<S, __half>::value && V % 2 == 0) {
 #pragma unroll
-  for (int j = 0; j < V; j++) o[j] = Store<S>::ld(t.v[j]);
+    for (int j = 0; j < V; j += 2) {
+      const float2 f = __half22float2(__halves2half2(t.v[j], t.v[j + 1]));
+      o[j] = f.x;
+      o[j + 1] = f.y;
+    }
+  } else if constexpr (std::is_same<S, __nv_bfloat16>::value && V % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < V; j += 2) {
+      const float2 f = __bfloat1622float2(__halves2bfloat162(t.v[j], t.v[j + 1]));
+      o[j] = f.x;
+      o[j + 1] = f.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; j++) o[j] = Store<S>::ld(t.v[j]);
+  }
 }
 
 template <typename S, int V>
 __device__ inline void vst(S *p, const typename Store<S>::T *v) {
   Pack<S, V> t;
+  if constexpr (std::is_same<S, __half>::value && V % 2 == 0) {
 #pragma unroll
-  for (int j = 0; j < V; j++) t.v[j] = Store<S>::st(v[j]);
+    for (int j = 0; j < V; j += 2) {
+      const __half2 h = __floats2half2_rn(v[j], v[j + 1]);
+      t.v[j] = __low2half(h);
+      t.v[j + 1] = __high2half(h);
+    }
+  } else if constexpr (std::is_same<S, __nv_bfloat16>::value && V % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < V; j += 2) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[j], v[j + 1]);
+      t.v[j] = __low2bfloat16(h);
+      t.v[j + 1] = __high2bfloat16(h);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; j++) t.v[j] = Store<S>::st(v[j]);
+  }
   *reinterpret_cast<Pack<S, V> *>(p) = t;
 }
 

@@ -76,6 +76,14 @@ def workload(size, storage):
     return W.ellipse_2048(storage) if size == 2048 else W.ellipse_scaled(size, storage)
 
 
+# FP64 roof of GB300 from its unit counts and clock, and the algorithmic FP64 flops of one
+# node update of the MRT collision without a body force, counted from the collision
+# (density and velocity 24, moments 32, equilibrium moments 12, relaxation 12, moment
+# coefficients 10, back-transform 36; a division counts as one flop).
+FP64_PEAK_TFLOPS = round(152 * 2 * 2 * 2.07e9 / 1e12, 4)
+FP64_MRT_FLOPS_PER_NODE = 126
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -287,6 +295,19 @@ def run_ours(args):
         d = json.load(open(tr)).get(f"ellipse{args.size}_{args.storage}")
         if d:
             roofline["traffic"] = d
+    if args.storage == "f64":
+        # FP64 arithmetic: GB300 runs FP64 at about 1.25 TFLOP/s (152 SMs x 2 FP64 FMA per
+        # clock x 2 flops x 2.07 GHz), so the FP64 stream-collide is bound by the FP64
+        # pipe, not by HBM (126 flops per node of the MRT collision without a body force
+        # against 144 bytes per node).  The HBM figures stay in the line as hbm_*.
+        flops = FP64_MRT_FLOPS_PER_NODE * lean_cells
+        hbm = {("hbm_" + k): roofline[k] for k in ("achieved", "peak", "frac")}
+        roofline.update({"bound": "alu", "achieved": round(flops / sc_avg_s / 1e12, 4),
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": round(flops / sc_avg_s / 1e12 / FP64_PEAK_TFLOPS, 4),
+                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x "
+                                        "2.07 GHz (nominal FP64 rate of GB300)",
+                         "flops_per_node": FP64_MRT_FLOPS_PER_NODE, **hbm})
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:

@@ -96,7 +96,7 @@ int iilbm_destroy(iilbm_t h);
  * shorter than 16 lattice units and every marker at least 3 nodes from a
  * non-periodic edge.  DIRECT needs a fixed body (moves = 0), eta > 0, and a body
  * whose bounding box plus 4 nodes fits the forcing kernel's shared memory (about
- * 85 x 85 nodes in FP32, 60 x 60 in FP64).  n = 0 removes the interface.
+ * 75 x 75 nodes in FP32, 60 x 60 in FP64).  n = 0 removes the interface.
  * Sections 2.2.2 (Eqs. 17-20) and 3 (Eqs. 31-32, 46-47).
  * Errors: INVALID_ARG, INTERFACE, OOM, CUDA. */
 int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n,

@@ -40,7 +40,8 @@ constexpr int DF_THREADS = 1024;
 // buffers (6 + 2 x 64 floats per marker) follow.
 template <typename T>
 __host__ __device__ inline size_t df_smem_bytes(int W, int n, bool mlp = false) {
-  size_t b = 7 * (size_t)W * sizeof(T);
+  // u*, 1/(2 rho) and the force fields: three (x, y) fields in FP32, two in FP64
+  size_t b = (sizeof(T) == 4 ? 9 : 7) * (size_t)W * sizeof(T);
   b += 16 * (size_t)n * (sizeof(T) + sizeof(int));
   b = (b + 15) & ~(size_t)15;
   b += 10 * (size_t)n * sizeof(T);
@@ -85,9 +86,11 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   T *h2r = usy + W;  // 1 / (2 rho)
   T *gx = h2r + W;  // force field of the even passes
   T *gy = gx + W;
-  T *gx2 = gy + W;  // force field of the odd passes
+  T *gx2 = gy + W;  // force field of the odd passes (FP32: of passes 1, 4, 7, ...)
   T *gy2 = gx2 + W;
-  T *pw = gy2 + W;                                  // stencil weights [16 n]
+  T *gx3 = gy2 + W;  // FP32 only: the third field (passes 2, 5, 8, ...)
+  T *gy3 = gx3 + W;
+  T *pw = sizeof(T) == 4 ? gy3 + W : gy2 + W;       // stencil weights [16 n]
   int *pc = reinterpret_cast<int *>(pw + 16 * n);   // stencil window indices [16 n]
   size_t off = (size_t)(reinterpret_cast<unsigned char *>(pc + 16 * n) - smem_raw);
   off = (off + 15) & ~(size_t)15;
@@ -106,7 +109,7 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   float *blk = wt3 + MLP_H * MLP_H;
   float *act0 = blk + MLP_BLOCK * n;
   float *act1 = act0 + MLP_H * n;
-  __shared__ B red[DF_THREADS / 32];
+  __shared__ B red[2][DF_THREADS / 32];
   __shared__ T cst[6];  // 2^-k, rho0, body force, eta, dX: converted once, by one thread
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) {
@@ -146,6 +149,10 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
     gy[c] = T(0);
     gx2[c] = T(0);
     gy2[c] = T(0);
+    if (sizeof(T) == 4) {
+      gx3[c] = T(0);
+      gy3[c] = T(0);
+    }
   }
   // stencils, one thread per marker
   for (int k = tid; k < n; k += DF_THREADS) {
@@ -242,15 +249,96 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   }
   __syncthreads();
 
-  // Each pass: interpolate u* + g / (2 rho) (Eq. 20) from the pass's field and take the
-  // residual (clearing the other field meanwhile); then, unless converged, update
-  // G += eta (U^D - U) (Eq. 18) and spread the new G dX into the other field -- the 16
-  // lanes of a marker form the same update, its first lane stores it.  Two barriers.
   int it = 0;
   B rm = 0;
   // stop once the residual's bit pattern is below the tolerance's (both non-negative)
   const bool stop_on_tol = a.tol > 0.0;
   const B tol_bits = BitsOf<T>::of(T(a.tol));
+  if constexpr (sizeof(T) == 4) {
+    // FP32: one barrier per pass.  The 16 lanes of a marker interpolate u* + g / (2 rho)
+    // (Eq. 20) from the pass's field; after the xor butterfly each holds the same U_k,
+    // so they form G += eta (U^D - U) (Eq. 18) and spread the new G dX into the next
+    // pass's field at once, without waiting for the residual; meanwhile the field of
+    // the pass after next is cleared (three fields in turn).  The barrier then makes the
+    // spread complete and the warps' residual maxima visible; a pass whose residual
+    // (taken before its update) is below the tolerance puts the G it started from
+    // back, so the result is the one of checking before updating.
+    T *Gp = GdX;  // G at the start of the pass, for that roll-back (GdX is free by now)
+    // the fields in turn: read (fx), spread into (ox), cleared (zx)
+    T *fx = gx, *fy = gy, *ox = gx2, *oy = gy2, *zx = gx3, *zy = gy3;
+    for (it = 0; it < a.max_iters; it++) {
+      B r = 0;
+      for (int base = 0; base < npairs; base += DF_THREADS) {
+        const int q = base + tid, k = q >> 4;
+        T sx = T(0), sy = T(0);
+        if (q < npairs) {
+          const int c = pc[q];
+          const T w = pw[q];
+          sx = (usx[c] + fx[c] * h2r[c]) * w;
+          sy = (usy[c] + fy[c] * h2r[c]) * w;
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          sx += __shfl_xor_sync(0xffffffffu, sx, o, 16);
+          sy += __shfl_xor_sync(0xffffffffu, sy, o, 16);
+        }
+        T gxo = T(0), gyo = T(0), nx = T(0), ny = T(0);
+        if (q < npairs) {
+          gxo = Gk[2 * k];
+          gyo = Gk[2 * k + 1];
+          nx = gxo + eta * (UDk[2 * k] - sx);
+          ny = gyo + eta * (UDk[2 * k + 1] - sy);
+        }
+        __syncwarp();  // every lane of the marker has read the old G
+        if (q < npairs) {
+          if ((q & 15) == 0) {
+            Uk[2 * k] = sx;
+            Uk[2 * k + 1] = sy;
+            r = max(r, max(BitsOf<T>::of(fabs(UDk[2 * k] - sx)),
+                           BitsOf<T>::of(fabs(UDk[2 * k + 1] - sy))));
+            Gp[2 * k] = gxo;
+            Gp[2 * k + 1] = gyo;
+            Gk[2 * k] = nx;
+            Gk[2 * k + 1] = ny;
+          }
+          const T w = pw[q];
+          if (w != T(0)) {
+            const int c = pc[q];
+            atomicAdd(&ox[c], nx * dX * w);
+            atomicAdd(&oy[c], ny * dX * w);
+          }
+        }
+      }
+      for (int c = tid; c < W; c += DF_THREADS) {
+        zx[c] = T(0);
+        zy[c] = T(0);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r = max(r, (B)__shfl_xor_sync(0xffffffffu, r, o));
+      if (lane == 0) red[it & 1][tid >> 5] = r;  // two sets: a warp may run a pass ahead
+      __syncthreads();
+      rm = lane < DF_THREADS / 32 ? red[it & 1][lane] : B(0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rm = max(rm, (B)__shfl_xor_sync(0xffffffffu, rm, o));
+      if (stop_on_tol && rm < tol_bits) {  // uniform
+        for (int k = tid; k < 2 * n; k += DF_THREADS) Gk[k] = Gp[k];
+        __syncthreads();
+        break;
+      }
+      T *tx = fx, *ty = fy;  // rotate: spread-into -> read, cleared -> spread-into
+      fx = ox;
+      fy = oy;
+      ox = zx;
+      oy = zy;
+      zx = tx;
+      zy = ty;
+    }
+  } else {
+  // FP64: each pass interpolates u* + g / (2 rho) (Eq. 20) from the pass's field and
+  // takes the residual (clearing the other field meanwhile); then, unless converged,
+  // updates G += eta (U^D - U) (Eq. 18) and spreads the new G dX into the other field --
+  // the 16 lanes of a marker form the same update, its first lane stores it.  Two
+  // barriers.
   for (it = 0; it < a.max_iters; it++) {
     const bool odd_pass = it & 1;
     const T *fx = odd_pass ? gx2 : gx, *fy = odd_pass ? gy2 : gy;
@@ -284,12 +372,12 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) r = max(r, (B)__shfl_xor_sync(0xffffffffu, r, o));
-    if (lane == 0) red[tid >> 5] = r;
+    if (lane == 0) red[0][tid >> 5] = r;
     __syncthreads();
-    // every thread reduces the warp maxima itself
-    rm = 0;
-#pragma unroll 8
-    for (int w = 0; w < DF_THREADS / 32; w++) rm = max(rm, red[w]);
+    // every warp reduces the warp maxima itself
+    rm = lane < DF_THREADS / 32 ? red[0][lane] : B(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rm = max(rm, (B)__shfl_xor_sync(0xffffffffu, rm, o));
     if (stop_on_tol && rm < tol_bits) break;  // uniform
     for (int base = 0; base < npairs; base += DF_THREADS) {
       const int q = base + tid;
@@ -322,6 +410,7 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
       }
     }
     __syncthreads();
+  }
   }
   for (int k = tid; k < 2 * n; k += DF_THREADS) {
     a.G[k] = (double)Gk[k];

@@ -84,7 +84,7 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   T *usx = reinterpret_cast<T *>(smem_raw);
   T *usy = usx + W;
   T *h2r = usy + W;  // 1 / (2 rho)
-  T *gx = h2r + W;  // force field of the even passes
+  T *gx = h2r + W;  // force field of the even passes (FP32: of passes 0, 3, 6, ...)
   T *gy = gx + W;
   T *gx2 = gy + W;  // force field of the odd passes (FP32: of passes 1, 4, 7, ...)
   T *gy2 = gx2 + W;

@@ -258,6 +258,54 @@ def test_cut_links_are_translation_invariant(orc):
     assert ka == kb
 
 
+def _link_image(cell, i, L, node, dirmap):
+    x, y = int(cell) % L, int(cell) // L
+    X, Y = node(x, y)
+    return (Y % L) * L + (X % L), dirmap[int(i)]
+
+
+def test_cut_links_rotate_with_the_polygon(orc):
+    """A quarter turn of a generic polygon about a lattice node maps its cut links onto
+    those of the turned polygon: destinations turned, directions E->N->W->S, NE->NW->SW->SE,
+    the same coefficients (the crossing tests are exact integer arithmetic on snapped
+    coordinates, which a quarter turn maps exactly)."""
+    L = 40
+    X = W.wobbly_polygon(17.3, 21.6, 8.0, 23, 0.3, 8)
+    Fn = np.random.default_rng(9).uniform(-1, 1, 23)
+    cfg = orc.make_cfg(L, L)
+    a = orc.cut_links(cfg, X, Fn)
+    Xr = np.stack([L - X[:, 1], X[:, 0]], axis=1)  # (x, y) -> (L - y, x), still CCW
+    b = orc.cut_links(cfg, Xr, Fn)
+    quarter = [0, 2, 3, 4, 1, 6, 7, 8, 5]
+    ka = sorted(_link_image(c, i, L, lambda x, y: (L - y, x), quarter) + (v,)
+                for c, i, v in zip(*a))
+    kb = sorted((int(c), int(i), v) for c, i, v in zip(*b))
+    assert len(ka) > 100 and ka == kb
+
+
+def test_cut_links_mirror_with_the_polygon(orc):
+    """The mirror image x -> L - x (marker order reversed to stay counter-clockwise, with
+    its Fn) has the mirrored cut links: E <-> W, NE <-> NW, SW <-> SE, the same
+    coefficients up to the rounding of the crossing parameter (t becomes 1 - t)."""
+    L = 40
+    X = W.wobbly_polygon(17.3, 21.6, 8.0, 23, 0.3, 10)
+    Fn = np.random.default_rng(12).uniform(-1, 1, 23)
+    cfg = orc.make_cfg(L, L)
+    a = orc.cut_links(cfg, X, Fn)
+    Xm = np.stack([L - X[:, 0], X[:, 1]], axis=1)[::-1].copy()
+    b = orc.cut_links(cfg, Xm, Fn[::-1].copy())
+    mirror = [0, 3, 2, 1, 4, 6, 5, 8, 7]
+    ra = {}
+    for c, i, v in zip(*a):
+        k = _link_image(c, i, L, lambda x, y: (L - x, y), mirror)
+        ra[k] = ra.get(k, 0.0) + v
+    rb = {}
+    for c, i, v in zip(*b):
+        rb[(int(c), int(i))] = rb.get((int(c), int(i)), 0.0) + v
+    assert len(ra) > 100 and set(ra) == set(rb)
+    assert max(abs(ra[k] - rb[k]) for k in ra) < 1e-15
+
+
 def test_jump_records_cancel_in_pairs(orc):
     """Each crossed link x - e_i -> x has its reverse x -> x - e_i crossed at the same
     point with the opposite sign and w_i = w_opp(i): the jump adds no mass."""

@@ -84,6 +84,23 @@ FP64_PEAK_TFLOPS = round(152 * 2 * 2 * 2.07e9 / 1e12, 4)
 FP64_MRT_FLOPS_PER_NODE = 126
 
 
+def max_over_ranks(values, dist, device="cuda"):
+    """Each value's maximum over the ranks (the slowest rank's time); the values
+    themselves in a single process."""
+    if not dist:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_mlups(cells_per_rank, steps, world, seconds):
+    """Lattice updates of all ranks (each runs its own replica: weak scaling) over the
+    slowest rank's time."""
+    return cells_per_rank * steps * world / seconds / 1e6
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -266,11 +283,8 @@ def run_ours(args):
     ms2, (sc_ms, sc_n, launches, tiles) = timed(args.steps, True)
     clk = clocks.stop()
     g.synchronize()
-    if dist:
-        t = torch.tensor([ms, ms2], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms2 = float(t[0].item()), float(t[1].item())
-    value = cells * args.steps * world / (ms * 1e-3) / 1e6
+    ms, ms2 = max_over_ranks([ms, ms2], dist)
+    value = whole_job_mlups(cells, args.steps, world, ms * 1e-3)
     sc_avg_s = sc_ms / max(sc_n, 1) * 1e-3
     # the lean stream-collide updates every node outside the flagged 128 x 8 tiles (those
     # go to the forced kernel on the side stream): 2 x 9 stored values per node
@@ -329,13 +343,10 @@ def run_ours(args):
         g2.get_macros(None, ux, uy, want=(False, True, True))
         barrier()
         dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt, = max_over_ranks([dt], dist)
         h2d = Xin.numel() * 8
         d2h = K2 * Xout.numel() * 8 + 2 * cells * 8
-        e2e = {"value": round(cells * K2 * world / dt / 1e6, 1), "unit": "MLUPS",
+        e2e = {"value": round(whole_job_mlups(cells, K2, world, dt), 1), "unit": "MLUPS",
                "h2d_bytes_per_step": round(h2d / K2, 1), "d2h_bytes_per_step": round(d2h / K2, 1),
                "note": "set_interface from pinned host, per step iilbm_step(1) + marker "
                        "read-back to pinned host, final velocity field read-back"}
@@ -419,12 +430,8 @@ def run_batched(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(x):
+        return max_over_ranks([x], dist)[0]
 
     # plain per-simulation form: every lattice on its own stream, stepped by its own calls
     lat = [batch_lattice(iilbm, s) for s in sims]
@@ -436,8 +443,8 @@ def run_batched(args):
     for g in lat:
         g.step(Kp)
     barrier()
-    plain_s = max_over_ranks(time.perf_counter() - t0)
-    plain = cells * Kp * world / plain_s / 1e6
+    plain_s = slowest(time.perf_counter() - t0)
+    plain = whole_job_mlups(cells, Kp, world, plain_s)
     # batched: one launch per phase per step for all lattices, graph replay
     if Wm % 2:
         for g in lat:  # keep every lattice at the same parity as a fresh one
@@ -453,7 +460,7 @@ def run_batched(args):
     B.step(K)
     e1.record(ts)
     barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1))
+    ms = slowest(e0.elapsed_time(e1))
     # second region, eager steps with events around every batched lean stream-collide
     Kt = min(K, 256)
     B.iilbm_batch_set_timing(True)
@@ -464,7 +471,7 @@ def run_batched(args):
     B.iilbm_batch_set_timing(False)
     clk = clocks.stop()
     B.synchronize()
-    value = cells * K * world / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(cells, K, world, ms * 1e-3)
     peak, peak_kind = peaks()
     step_bytes = 2 * 9 * 4 * cells
     achieved = step_bytes / (ms * 1e-3 / K) / 1e9
@@ -497,9 +504,9 @@ def run_batched(args):
         for g, (ux, uy) in zip(lat, outs):
             g.get_macros(None, ux, uy, want=(False, True, True))
         barrier()
-        dt = max_over_ranks(time.perf_counter() - t0)
+        dt = slowest(time.perf_counter() - t0)
         B2.close()
-        e2e = {"value": round(cells * K * world / dt / 1e6, 1), "unit": "MLUPS",
+        e2e = {"value": round(whole_job_mlups(cells, K, world, dt), 1), "unit": "MLUPS",
                "h2d_bytes_per_step": round(markers * 16 / K, 1),
                "d2h_bytes_per_step": round(2 * cells * 8 / K, 1),
                "note": "set_interface of every lattice from pinned host, batch creation, "
@@ -625,6 +632,10 @@ def run_channel(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     ts = torch.cuda.Stream()
     torch.cuda.set_stream(ts)
     w = W.cylinder_channel(args.re)
@@ -642,12 +653,16 @@ def run_channel(args):
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     e0.record(ts)
     g.step(args.steps)
     e1.record(ts)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    if dist:
+        dist.barrier()
+    ms, = max_over_ranks([e0.elapsed_time(e1)], dist)
     g.iilbm_set_timing(True)
     g.step(min(args.steps, 128))
     sc_ms, sc_n, launches = g.iilbm_get_timing()
@@ -655,7 +670,7 @@ def run_channel(args):
     clk = clocks.stop()
     F = g.iilbm_get_body_force()
     cells = nx * ny
-    value = cells * args.steps * world / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(cells, args.steps, world, ms * 1e-3)
     peak, peak_kind = peaks()
     sc_avg = sc_ms / max(sc_n, 1) * 1e-3
     lean_bytes = 2 * 9 * 4 * cells

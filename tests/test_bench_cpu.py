@@ -77,3 +77,44 @@ def test_gpu_arm_fails_loudly_without_a_gpu():
     r = run([sys.executable, "bench.py", "--steps", "1", "--warmup", "1"])
     assert r.returncode != 0
     assert json_lines(r.stdout) == []  # no number without the CUDA path
+
+
+def _ranks_body(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        # the slower rank's time decides; each rank ran its own replica of the lattice
+        t = bench.max_over_ranks([10.0 + rank, 3.0 - rank], dist, device="cpu")
+        q.put((rank, t, bench.whole_job_mlups(4096, 100, world, t[0] * 1e-3)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_whole_job_value_with_two_gloo_ranks():
+    """The N > 1 path's host logic with two gloo ranks on CPU: every rank gets the
+    slowest rank's time, and the whole-job rate counts every rank's updates over it."""
+    pytest.importorskip("torch")
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    ps = [ctx.Process(target=_ranks_body, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    out = [q.get(timeout=120) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, t, v in out:
+        assert t == [11.0, 3.0]
+        assert abs(v - 4096 * 100 * 2 / 11e-3 / 1e6) < 1e-9
+    assert bench_single_process_is_identity()
+
+
+def bench_single_process_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench.max_over_ranks([1.5, 2.5], None) == [1.5, 2.5]

@@ -175,14 +175,18 @@ int iilbm_get_timing(iilbm_t h, double *stream_collide_ms, int32_t *stream_colli
 
 /* Execution options (all on by default; for A/B measurements and tests):
  *  IILBM_OPT_CUDA_GRAPH     replay blocks of steps from one captured CUDA graph;
- *  IILBM_OPT_OVERLAP        run the next step's interface phase on a second stream
- *                           while the current stream-collide runs;
+ *  IILBM_OPT_OVERLAP        run the forced stream-collide, then the interpolation
+ *                           fused with the next step's interface phase (one kernel),
+ *                           on a second, high-priority stream while the lean
+ *                           stream-collide runs (direct forcing: the forced
+ *                           stream-collide and the interpolation only);
  *  IILBM_OPT_VECTOR_KERNEL  vectorised stream-collide (else one node per thread);
  *  IILBM_OPT_FORCED_BLOCKS  blocks of the forced stream-collide, which stride over the
  *                           flagged tiles (value > 0; 0 restores the default, two per
  *                           SM): fewer blocks hold fewer of the SMs' registers while the
  *                           lean stream-collide runs beside them.
- * Results are identical either way.  Synchronises the handle's stream. */
+ * Results agree either way up to the order of floating-point atomic additions.
+ * Synchronises the handle's stream. */
 enum { IILBM_OPT_CUDA_GRAPH = 0, IILBM_OPT_OVERLAP = 1, IILBM_OPT_VECTOR_KERNEL = 2,
        IILBM_OPT_FORCED_BLOCKS = 3 };
 int iilbm_set_option(iilbm_t h, int32_t option, int32_t value);

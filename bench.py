@@ -6,6 +6,9 @@ stiffness 0.05, tau = 0.6, populations stored in FP32 as shifted deviations.  On
 "step" is one whole II-LBM time step (marker forces, cut-link jump, tangential
 spreading, interpolation and marker update, fused stream-collide), i.e. every row of
 the hot path.  Metric: MLUPS (million lattice-node updates per second), whole job.
+--storage f16 | bf16 | f64 runs it with another storage precision; FP64 storage computes
+in FP64, which GB300 runs at about 1.26 TFLOP/s, so its roofline is the FP64 arithmetic
+roof ("bound": "alu") with the HBM fraction beside it.
 
 --workload batched: the sweep of 256 independent membranes (square lattices of
 64..512 nodes, ellipses of aspect 1..2.5 at perimeter 0.6 n, one marker per half lattice

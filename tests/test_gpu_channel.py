@@ -1,7 +1,6 @@
 """Channel boundaries (parabolic inflow by non-equilibrium extrapolation, zero-gradient
 outflow, halfway bounce-back walls) and direct forcing of a fixed cylinder with repeated
 correction (Eq. 18), CUDA path against the FP64 oracle."""
-import math
 
 import numpy as np
 import pytest

@@ -12,7 +12,7 @@ import pytest
 from paper_2003_12186_gb300 import iilbm
 from paper_2003_12186_gb300 import workloads as W
 
-from _pair import make_pair, rel_err, set_membrane, vel_error
+from _pair import make_pair, set_membrane, vel_error
 
 pytestmark = pytest.mark.gpu
 

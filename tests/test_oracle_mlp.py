@@ -1,6 +1,5 @@
 """Pins of the learned warm start's oracle (oracle/mlp.py): values the definitions fix,
 finite differences for every derivative, closed forms of the optimiser and geometry."""
-import math
 
 import numpy as np
 import pytest

@@ -52,6 +52,7 @@ import numpy as np  # noqa: E402
 from paper_2003_12186_gb300 import workloads as W  # noqa: E402
 
 L2_BYTES = 129 * 1024 * 1024
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal
 
 
 def parse():
@@ -64,6 +65,8 @@ def parse():
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-hbm-check", action="store_true",
+                    help="skip the 4096^2 out-of-L2 lean stream-collide measurement")
     ap.add_argument("--workload", default="ellipse",
                     choices=["ellipse", "batched", "learned", "channel"])
     ap.add_argument("--re", type=float, default=20.0, help="Reynolds number (channel)")
@@ -72,6 +75,20 @@ def parse():
     if a.steps is None:
         a.steps = 20000 if a.workload == "ellipse" else 2000
     return a
+
+
+def ellipse_config(args, world=1):
+    """The membrane workload's config object, the same in both arms."""
+    w = workload(args.size, args.storage)
+    sbytes = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[args.storage]
+    cells = w["nx"] * w["ny"]
+    return {"workload": w["name"].replace(f"_{args.storage}", "") + "_membrane",
+            "lattice": [w["nx"], w["ny"]], "markers": len(w["X"]), "collision": "mrt",
+            "tau": w["tau"], "storage": args.storage,
+            "arithmetic": "f64" if args.storage == "f64" else "f32",
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": f"inputs larger than L2 ({9 * sbytes * cells / 2**20:.0f} MiB populations "
+                  f"vs 129 MiB L2)" if 9 * sbytes * cells > L2_BYTES else "working set fits L2"}
 
 
 def workload(size, storage):
@@ -112,8 +129,60 @@ def peaks():
 
 
 # ------------------------------------------------------------------ clocks
+class _Nvml:
+    """The driver's management library (libnvidia-ml), read through ctypes: SM clock,
+    its maximum, power and the active clock-event reasons of one device.  Read only."""
+
+    SM = 1  # NVML_CLOCK_SM
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_device):
+        import ctypes as C
+        self.C = C
+        L = None
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                L = C.CDLL(name)
+                break
+            except OSError:
+                continue
+        if L is None or L.nvmlInit_v2() != 0:
+            raise OSError("NVML unavailable")
+        self.L = L
+        self.h = C.c_void_p()
+        import torch
+        p = torch.cuda.get_device_properties(torch_device)
+        ids = [f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0",
+               f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"]
+        ok = False
+        for bid in ids:
+            if L.nvmlDeviceGetHandleByPciBusId_v2(bid.encode(), C.byref(self.h)) == 0:
+                ok = True
+                break
+        if not ok:
+            raise OSError("NVML: no device with the CUDA device's PCI bus id")
+        self.reasons_fn = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(L, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        v = C.c_uint()
+        self.max_mhz = float(v.value) if L.nvmlDeviceGetMaxClockInfo(self.h, self.SM,
+                                                                     C.byref(v)) == 0 else None
+
+    def sample(self):
+        C = self.C
+        mhz, mw, r = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        if self.L.nvmlDeviceGetClockInfo(self.h, self.SM, C.byref(mhz)) != 0:
+            return None
+        self.reasons_fn(self.h, C.byref(r))
+        self.L.nvmlDeviceGetPowerUsage(self.h, C.byref(mw))
+        return float(mhz.value), int(r.value), mw.value / 1000.0
+
+
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """SM clock and clock-event reasons sampled during the timed region: a thread reads
+    NVML every ~0.25 ms (so even a region of a millisecond or two gets samples), with
+    nvidia-smi polling (200 ms) where NVML cannot be loaded.  begin() / end() mark the
+    region; stop() summarises the samples taken between the marks."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -121,58 +190,94 @@ class ClockSampler:
 
     def __init__(self, index):
         self.index = index
-        self.lines = []
+        self.samples = []  # (host time, sm MHz, reason names, power W)
         self.proc = None
+        self.nvml = None
+        self.max_mhz = None
+        self.t0 = self.t1 = None
+        self._stop = threading.Event()
 
     def start(self):
+        try:
+            self.nvml = _Nvml(self.index)
+            self.max_mhz = self.nvml.max_mhz
+            self.t = threading.Thread(target=self._poll_nvml, daemon=True)
+            self.t.start()
+            return
+        except Exception:
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                  "-lms", "200", "-i", str(self.index)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t = threading.Thread(target=self._read_smi, daemon=True)
             self.t.start()
         except OSError:
             self.proc = None
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+    def _poll_nvml(self):
+        while not self._stop.is_set():
+            v = self.nvml.sample()
+            if v:
+                mhz, bits, w = v
+                names = sorted(n for b, n in _Nvml.REASONS.items() if bits & b)
+                self.samples.append((time.perf_counter(), mhz, names, w))
+            time.sleep(0.00025)
 
-    def stop(self):
-        if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.t.join(timeout=2)
-        sm, mx, reasons = [], [], set()
+    def _read_smi(self):
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
+        for ln in self.proc.stdout:
+            f = [x.strip() for x in ln.strip().split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                mhz, mx = float(f[1]), float(f[2])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+            self.max_mhz = mx
+            act = sorted(nm for nm, v in zip(names, f[5:9]) if v.lower().startswith("active"))
+            self.samples.append((time.perf_counter(), mhz, act, None))
+
+    def begin(self):
+        self.t0 = time.perf_counter()
+
+    def end(self):
+        self.t1 = time.perf_counter()
+
+    def stop(self):
+        self._stop.set()
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.nvml is None and self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock query unavailable"],
+                    "samples": 0}
+        self.t.join(timeout=5)
+        t0 = self.t0 if self.t0 is not None else -1e300
+        t1 = self.t1 if self.t1 is not None else 1e300
+        inside = [s for s in self.samples if t0 <= s[0] <= t1]
+        sm = [s[1] for s in inside]
+        reasons = sorted({r for s in inside for r in s[2]})
+        power = [s[3] for s in inside if s[3] is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                "sm_mhz_min": min(sm) if sm else None, "reasons": reasons,
+                "samples": len(sm), "source": "nvml" if self.nvml else "nvidia-smi",
+                "power_w_max": round(max(power), 1) if power else None,
+                "region_s": round(t1 - t0, 6) if self.t0 is not None else None}
 
 
 # -------------------------------------------------------------- cpu oracle
-def oracle_rate(size, max_seconds, min_steps=1):
-    """Time the FP64 CPU oracle (as it stands, one thread) on the workload."""
+def oracle_rate(size, max_seconds, min_steps=1, parallel=False):
+    """Time the FP64 CPU oracle (as it stands: one thread, or its OpenMP build on every
+    host core) on the workload."""
     from oracle import oracle as O
     w = workload(size, "f64")
-    o = O.Oracle(w["nx"], w["ny"], collision=O.MRT, tau=w["tau"], s=W.mrt_rates(w["tau"]))
+    o = O.Oracle(w["nx"], w["ny"], parallel=parallel, collision=O.MRT, tau=w["tau"],
+                 s=W.mrt_rates(w["tau"]))
     o.set_interface(w["X"], model=O.SPRING, kappa=w["kappa"], dX=w["dX"])
     steps, t0 = 0, time.perf_counter()
     while steps < min_steps or time.perf_counter() - t0 < max_seconds:
@@ -183,40 +288,67 @@ def oracle_rate(size, max_seconds, min_steps=1):
     return w["nx"] * w["ny"] * steps / dt / 1e6, steps, dt
 
 
+def cpu_baseline_both(size, seconds_single, seconds_all):
+    """The oracle on one thread and (OpenMP build) on every host core; the all-core
+    figure leads, the single-thread one is kept beside it."""
+    from oracle import oracle as O
+    r1, st1, dt1 = oracle_rate(size, seconds_single)
+    out = {"value": round(r1, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+           "sample": f"{st1} FP64 oracle steps of the same {size}^2 workload, {dt1:.1f} s, "
+                     f"one thread"}
+    try:
+        rp, stp, dtp = oracle_rate(size, seconds_all, parallel=True)
+    except RuntimeError:
+        return out
+    return {"value": round(rp, 4), "unit": "MLUPS", "cores": O.omp_threads(), "kind": "oracle",
+            "sample": f"{stp} FP64 oracle steps of the same {size}^2 workload, {dtp:.1f} s, "
+                      f"OpenMP build (per-node loops on {O.omp_threads()} threads, results "
+                      f"identical to the serial build)",
+            "single_thread": out}
+
+
 def run_reference(args):
-    """Reference arm: the oracle on the host cores, rank 0 only."""
+    """Reference arm: the oracle (OpenMP build, every host core), rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle import oracle as O
+    try:
+        O.lib(parallel=True)
+        par = True
+    except RuntimeError:
+        par = False
+    cores = O.omp_threads() if par else 1
     K, Wm = args.steps, args.warmup
-    probe, _, _ = oracle_rate(256, 0.5)
+    probe, _, _ = oracle_rate(256, 0.5, parallel=par)
     # largest lattice of the same workload family whose run fits about two minutes
     size = 256
-    for n in (2048, 1024, 512, 256):
+    for n in (args.size, args.size // 2, args.size // 4, args.size // 8, 256):
         if n * n * (K + min(Wm, 3)) / (probe * 1e6) <= 120.0:
             size = n
             break
     steps = K
     if size == 256:
         steps = max(1, min(K, int(120.0 * probe * 1e6 / (256 * 256))))
-    from oracle import oracle as O
     w = workload(size, "f64")
-    o = O.Oracle(w["nx"], w["ny"], collision=O.MRT, tau=w["tau"], s=W.mrt_rates(w["tau"]))
+    o = O.Oracle(w["nx"], w["ny"], parallel=par, collision=O.MRT, tau=w["tau"],
+                 s=W.mrt_rates(w["tau"]))
     o.set_interface(w["X"], model=O.SPRING, kappa=w["kappa"], dX=w["dX"])
     o.step(min(Wm, 3))
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
     value = w["nx"] * w["ny"] * steps / dt / 1e6
-    sample = (f"{steps} oracle steps of the ellipse membrane scaled to {size}^2 "
-              f"(same aspect, tau, stiffness, marker density), FP64, one thread")
+    sample = (f"{steps} oracle steps of the ellipse membrane "
+              + (f"at {size}^2" if size == args.size else
+                 f"scaled to {size}^2 (same aspect, tau, stiffness, marker density)")
+              + ", FP64, " + (f"OpenMP build on {cores} threads" if par else "one thread"))
     out = {"metric": "MLUPS", "value": round(value, 4), "unit": "MLUPS", "n_gpus": args.gpus,
            "steps": K, "warmup": Wm, "ms_per_step": round(dt / steps * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"ellipse{size}_mrt_membrane", "sample_of": "ellipse2048_mrt_f32",
-                      "lattice": [size, size], "markers": len(w["X"])},
-           "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1,
+           "config": ellipse_config(args),
+           "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": cores,
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
@@ -248,9 +380,11 @@ def run_ours(args):
     w = workload(args.size, args.storage)
     cells = w["nx"] * w["ny"]
     sbytes = iilbm.STORAGE_BYTES[iilbm.STORAGE[args.storage]]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     g = make_lattice(iilbm, w, stream)
     g.set_interface(w["X"], model=iilbm.SPRING, stiffness=w["kappa"], dX=w["dX"])
-    g.step(args.warmup)
+    g.step(args.warmup)  # the first call captures the step graphs
     g.synchronize()
 
     def barrier():
@@ -258,31 +392,35 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(steps, kernel_timing):
+    def timed(lat, steps, kernel_timing, mark=False):
         """One timed region of `steps` steps on stream ts, bracketed by a barrier and a
         device synchronisation; optionally with per-launch kernel events."""
         if kernel_timing:
-            g.iilbm_set_timing(True)
+            lat.iilbm_set_timing(True)
+            lat.step(2)  # captures the graphs that record the events, outside the region
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
+        if mark:
+            clocks.begin()
         e0.record(ts)
-        g.step(steps)
+        lat.step(steps)
         e1.record(ts)
         barrier()
+        if mark:
+            clocks.end()
         ms = e0.elapsed_time(e1)
         kt = None
         if kernel_timing:
-            kt = g.iilbm_get_timing(with_tiles=True)
-            g.iilbm_set_timing(False)
+            kt = lat.iilbm_get_timing(with_tiles=True)
+            lat.iilbm_set_timing(False)
         return ms, kt
 
-    # region 1 -- the metric: the step as a user runs it (no per-launch instrumentation)
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    ms, _ = timed(args.steps, False)
-    # region 2 -- same workload and launch configuration, CUDA events around every
-    # launch of the lean stream-collide (the dominant kernel) for the roofline
-    ms2, (sc_ms, sc_n, launches, tiles) = timed(args.steps, True)
+    # region 1 -- the metric: the step as a user runs it (graph replay, no per-launch
+    # instrumentation); the clocks are sampled during this region
+    ms, _ = timed(g, args.steps, False, mark=True)
+    # region 2 -- same workload and graph replay, with CUDA events recorded inside the
+    # graphs around every launch of the lean stream-collide (the dominant kernel)
+    ms2, (sc_ms, sc_n, launches, tiles) = timed(g, args.steps, True)
     clk = clocks.stop()
     g.synchronize()
     ms, ms2 = max_over_ranks([ms, ms2], dist)
@@ -305,7 +443,12 @@ def run_ours(args):
                 # uninstrumented step time of the metric's region
                 "step_achieved": round(2 * 9 * sbytes * cells / (ms / args.steps * 1e-3) / 1e9, 1),
                 "step_frac": round(2 * 9 * sbytes * cells / (ms / args.steps * 1e-3) / 1e9 / peak,
-                                   4)}
+                                   4),
+                # the same two figures against the nominal 8 TB/s of GB300's HBM3e
+                "frac_nominal_8tbs": round(achieved / NOMINAL_HBM_GBS, 4),
+                "step_frac_nominal_8tbs": round(2 * 9 * sbytes * cells /
+                                                (ms / args.steps * 1e-3) / 1e9 /
+                                                NOMINAL_HBM_GBS, 4)}
     tr = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr):
         d = json.load(open(tr)).get(f"ellipse{args.size}_{args.storage}")
@@ -324,10 +467,43 @@ def run_ours(args):
                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x "
                                         "2.07 GHz (nominal FP64 rate of GB300)",
                          "flops_per_node": FP64_MRT_FLOPS_PER_NODE, **hbm})
+    # out of L2: the same membrane scaled to 4096^2 (populations 4x the 2048^2 ones, far
+    # above the 129 MiB L2), lean stream-collide timed as in region 2
+    if args.storage != "f64" and args.size < 4096 and not args.no_hbm_check:
+        del g
+        torch.cuda.synchronize()
+        w4 = workload(4096, args.storage)
+        g4 = make_lattice(iilbm, w4, stream)
+        g4.set_interface(w4["X"], model=iilbm.SPRING, stiffness=w4["kappa"], dX=w4["dX"])
+        g4.step(max(args.warmup, 8))
+        K4 = 256
+        ms4, (sc4, n4, _, t4) = timed(g4, K4, True)
+        cells4 = w4["nx"] * w4["ny"]
+        lean4 = int(2 * 9 * sbytes * (cells4 - t4 / max(n4, 1) * 128 * 8))
+        a4 = lean4 / (sc4 / max(n4, 1) * 1e-3) / 1e9
+        s4 = 2 * 9 * sbytes * cells4 / (ms4 / K4 * 1e-3) / 1e9
+        roofline["out_of_l2"] = {
+            "lattice": [4096, 4096], "steps": K4,
+            "populations_mib": round(9 * sbytes * cells4 / 2**20),
+            "lean_achieved": round(a4, 1), "lean_frac": round(a4 / peak, 4),
+            "lean_frac_nominal_8tbs": round(a4 / NOMINAL_HBM_GBS, 4),
+            "avg_launch_us": round(sc4 / max(n4, 1) * 1e3, 2),
+            "step_mlups": round(cells4 * K4 / (ms4 * 1e-3) / 1e6, 1),
+            "step_achieved": round(s4, 1), "step_frac": round(s4 / peak, 4),
+            "note": "the 2048^2 membrane scaled to 4096^2 (same aspect, tau, stiffness, "
+                    "marker density), timed with per-launch events like region 2"}
+        tr4 = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tr4):
+            d = json.load(open(tr4)).get(f"ellipse4096_{args.storage}")
+            if d:
+                roofline["out_of_l2"]["traffic"] = d
+        del g4
+        torch.cuda.synchronize()
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        del g
+        if "g" in locals():
+            del g
         torch.cuda.synchronize()
         g2 = make_lattice(iilbm, w, stream)
         nm = len(w["X"])
@@ -355,24 +531,14 @@ def run_ours(args):
         del g2
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, st, dt = oracle_rate(args.size, 12.0)
-        cpu = {"value": round(rate, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"{st} FP64 oracle steps of the same {args.size}^2 workload, "
-                         f"{dt:.1f} s, one thread"}
+        cpu = cpu_baseline_both(args.size, 10.0, 8.0)
     if rank == 0:
         out = {"metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
                "data": "synthetic",
-               "config": {"workload": w["name"].replace(f"_{args.storage}", "") + "_membrane",
-                          "lattice": [w["nx"], w["ny"]], "markers": len(w["X"]),
-                          "collision": "mrt", "tau": w["tau"], "storage": args.storage,
-                          "arithmetic": "f64" if args.storage == "f64" else "f32",
-                          "parallelism": "replicas" if world > 1 else "single",
-                          "l2": f"inputs larger than L2 ({9 * sbytes * cells / 2**20:.0f} MiB "
-                                f"populations vs 129 MiB L2)" if 9 * sbytes * cells > L2_BYTES
-                          else "working set fits L2"},
+               "config": ellipse_config(args, world),
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": int(launches / max(sc_n, 1) * args.steps)}
         print(json.dumps(out), flush=True)

@@ -36,7 +36,9 @@ typedef enum {
   IILBM_ERR_DEVICE_TIMEOUT = -4,/* a bounded device wait gave up */
   IILBM_ERR_NONFINITE = -5,     /* a NaN / Inf appeared in the populations */
   IILBM_ERR_INTERFACE = -6,     /* marker polygon invalid (segment too long, outside region) */
-  IILBM_ERR_CAPACITY = -7,      /* cut-link list overflow */
+  IILBM_ERR_CAPACITY = -7,      /* a fixed-size resource is too small: cut-link list,
+                                   forcing kernel's shared memory, or the no-allocation
+                                   read-out's staging array */
   IILBM_ERR_NO_DEVICE = -8      /* no CUDA device, or not a compute capability 10.3 device */
 } iilbm_status;
 
@@ -114,7 +116,13 @@ int iilbm_get_populations(iilbm_t h, double *df);
 
 /* Advance n >= 0 time steps of section 3.2 (Eq. 47 with Eqs. 17-24): Lagrangian
  * force, normal split, jump on cut links, tangential spreading, interpolation,
- * fused stream-collide, marker update.  Asynchronous. */
+ * fused stream-collide, marker update.  Asynchronous.  Unless IILBM_OPT_CUDA_GRAPH is
+ * off, steps are replayed from CUDA graphs for any n: the first replaying call
+ * captures graphs of 32, 16, 8, 4, 2 and 1 steps from an even time level and of one
+ * step from an odd level (make that first call outside any stream capture of your
+ * own), and each call then launches one odd step where the level is odd and the
+ * binary decomposition of the rest.  A directly forced body is captured too: each
+ * captured step begins with its force iteration. */
 int iilbm_step(iilbm_t h, int32_t n);
 
 /* Macroscopic fields of the current state ([ny][nx] FP64 each, host or device,
@@ -159,6 +167,13 @@ int iilbm_get_unforced_velocity(iilbm_t h, double *Ustar);
  * lift coefficients follow as 2 F / (rho U^2 D) (Eqs. 52-53).  Synchronises. */
 int iilbm_get_body_force(iilbm_t h, double *F);
 
+/* The jump of the current state's interface on the streamed populations (Eq. 47 with
+ * Eq. 32): J[i-1][y][x] = the sum of s w_i/c_s^2 Fn(crossing) over the crossings of the
+ * link x - e_i -> x, i = 1..8, [8][ny][nx] FP64 (host or device), zero off the cut
+ * links.  Runs the current state's interface phase if it has not run.  Synchronises.
+ * Errors: INVALID_ARG (NULL), OOM, CUDA, latched device status. */
+int iilbm_get_jump(iilbm_t h, double *J);
+
 /* Number of cut-link crossings of the current state's interface (Eq. 47). */
 int iilbm_get_cut_link_count(iilbm_t h, int32_t *count);
 
@@ -174,7 +189,7 @@ int iilbm_get_timing(iilbm_t h, double *stream_collide_ms, int32_t *stream_colli
                      int64_t *kernel_launches, int64_t *flagged_tiles);
 
 /* Execution options (all on by default; for A/B measurements and tests):
- *  IILBM_OPT_CUDA_GRAPH     replay blocks of steps from one captured CUDA graph;
+ *  IILBM_OPT_CUDA_GRAPH     replay steps from captured CUDA graphs (iilbm_step);
  *  IILBM_OPT_OVERLAP        run the forced stream-collide, then the interpolation
  *                           fused with the next step's interface phase (one kernel),
  *                           on a second, high-priority stream while the lean

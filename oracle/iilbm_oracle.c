@@ -21,6 +21,11 @@
  * FP64 rounding of the O(1) rest state out of the O(u) flow quantities.
  *
  * Layout: df[i*ny*nx + y*nx + x]  (structure of arrays, natural "pull" order).
+ *
+ * The same source also builds with -fopenmp (the all-core CPU baseline): the
+ * "omp parallel for" lines mark the per-node loops whose iterations touch disjoint
+ * nodes, so the parallel build computes every value exactly as the serial one does.
+ * Spreading, which accumulates, and the marker loops stay serial.
  */
 #include <math.h>
 #include <stdint.h>
@@ -471,6 +476,7 @@ int orc_winding(const double *X, int n, int px, int py) {
  * orc_channel_bc. */
 static void stream(const orc_cfg *c, const double *fs, double *out) {
   int nx = c->nx, ny = c->ny, N = nx * ny;
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int i = 0; i < 9; i++)
     for (int y = 0; y < ny; y++)
       for (int x = 0; x < nx; x++) {
@@ -558,6 +564,7 @@ void orc_get_df(const orc_state *S, double *df) {
  * for rho0 / zero). */
 void orc_init_equilibrium(orc_state *S, const double *rho, const double *ux, const double *uy) {
   int N = S->c.nx * S->c.ny;
+  #pragma omp parallel for schedule(static)
   for (int p = 0; p < N; p++) {
     double e[9];
     orc_feq_shifted(rho ? rho[p] - S->c.rho0 : 0.0, S->c.rho0, ux ? ux[p] : 0.0, uy ? uy[p] : 0.0, e);
@@ -605,6 +612,7 @@ static void direct_forcing(orc_state *S, const double *dfs) {
   double *gx = (double *)calloc(N, sizeof(double)), *gy = (double *)calloc(N, sizeof(double));
   double *vx = (double *)calloc(N, sizeof(double)), *vy = (double *)calloc(N, sizeof(double));
   double *P = (double *)calloc(2 * n, sizeof(double));
+  #pragma omp parallel for schedule(static)
   for (int p = 0; p < N; p++) {
     double dfc[9];
     for (int i = 0; i < 9; i++) dfc[i] = dfs[i * N + p];
@@ -619,6 +627,7 @@ static void direct_forcing(orc_state *S, const double *dfs) {
     memset(gx, 0, N * sizeof(double)); memset(gy, 0, N * sizeof(double));
     for (int k = 0; k < 2 * n; k++) P[k] = S->G[k] * I->dX;
     orc_spread(c, I->X, n, P, gx, gy);
+    #pragma omp parallel for schedule(static)
     for (int p = 0; p < N; p++) {
       vx[p] = us_x[p] + 0.5 * gx[p] / (c->rho0 + r[p]);
       vy[p] = us_y[p] + 0.5 * gy[p] / (c->rho0 + r[p]);
@@ -677,6 +686,7 @@ int orc_prepare(orc_state *S) {
     orc_spread(c, I->X, n, P, S->gx, S->gy);
     free(P);
   }
+  #pragma omp parallel for schedule(static)
   for (int p = 0; p < N; p++) {
     double dfc[9];
     for (int i = 0; i < 9; i++) dfc[i] = S->f[i * N + p];
@@ -689,6 +699,7 @@ int orc_prepare(orc_state *S) {
 void orc_advance(orc_state *S) {
   const orc_cfg *c = &S->c;
   int N = c->nx * c->ny;
+  #pragma omp parallel for schedule(static)
   for (int p = 0; p < N; p++) {
     double dfc[9], out[9];
     for (int i = 0; i < 9; i++) dfc[i] = S->f[i * N + p];

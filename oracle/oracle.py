@@ -23,8 +23,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "iilbm_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle_iilbm.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "liboracle_iilbm_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 SRT, MRT = 0, 1
 BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL = 0, 1, 2
@@ -33,15 +35,25 @@ SPRING, SPRING_REST, PRESCRIBED, DIRECT = 0, 1, 2, 3
 PAPER_MRT_RATES = (0.0, 1.63, 1.14, 0.0, 1.92, 0.0, 1.92, None, None)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no fused multiply-add contraction)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-std=c11", _SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+def build(force: bool = False, parallel: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add contraction); parallel=True
+    builds the same source with OpenMP (per-node loops on all host cores, identical
+    results).  Returns the library path, or None for a parallel build that this gcc
+    cannot make (no OpenMP runtime)."""
+    out = _LIB_OMP if parallel else _LIB
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-std=c11", *(["-fopenmp"] if parallel else []), _SRC, "-o", tmp, "-lm"]
+        try:
+            subprocess.check_call(cmd, stderr=subprocess.DEVNULL if parallel else None)
+        except subprocess.CalledProcessError:
+            if parallel:
+                return None
+            raise
+        os.replace(tmp, out)
+    return out
 
 
 class _Cfg(C.Structure):
@@ -55,50 +67,66 @@ _D = C.POINTER(C.c_double)
 _I = C.POINTER(C.c_int)
 
 
-def lib():
-    global _lib
+def lib(parallel: bool = False):
+    """The oracle library (serial, or the OpenMP build with parallel=True)."""
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
-            L.orc_create.restype = C.c_void_p
-            L.orc_create.argtypes = [C.POINTER(_Cfg)]
-            L.orc_destroy.argtypes = [C.c_void_p]
-            L.orc_set_df.argtypes = [C.c_void_p, _D]
-            L.orc_get_df.argtypes = [C.c_void_p, _D]
-            L.orc_init_equilibrium.argtypes = [C.c_void_p, _D, _D, _D]
-            L.orc_set_interface.argtypes = [C.c_void_p, _D, C.c_int, C.c_int, C.c_int, C.c_double,
-                                            C.c_double, C.c_double, C.c_double, C.c_int,
-                                            C.c_double, _D, _D]
-            L.orc_step.argtypes = [C.c_void_p]
-            L.orc_prepare.argtypes = [C.c_void_p]
-            L.orc_cut_link_count.argtypes = [C.c_void_p]
-            L.orc_run.argtypes = [C.c_void_p, C.c_int]
-            L.orc_get_step_macros.argtypes = [C.c_void_p, _D, _D, _D]
-            L.orc_get_markers.argtypes = [C.c_void_p, _D, _D, _D, _D]
-            L.orc_mdf_iters.argtypes = [C.c_void_p]
-            L.orc_set_ws_previous.argtypes = [C.c_void_p, C.c_int]
-            L.orc_get_ustar.argtypes = [C.c_void_p, _D]
-            L.orc_mdf_residual.argtypes = [C.c_void_p]
-            L.orc_mdf_residual.restype = C.c_double
-            L.orc_polygon_area.argtypes = [_D, C.c_int]
-            L.orc_polygon_area.restype = C.c_double
-            L.orc_phi.argtypes = [C.c_double]
-            L.orc_phi.restype = C.c_double
-            L.orc_mrt_matrix.argtypes = [_D]
-            L.orc_invert9.argtypes = [_D, _D]
-            L.orc_mrt_inverse.argtypes = [_D, _D]
-            L.orc_feq_shifted.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _D]
-            L.orc_guo_source.argtypes = [C.c_double] * 4 + [_D]
-            L.orc_collide_cell.argtypes = [C.POINTER(_Cfg), _D, _D, _D, C.c_double, C.c_double, _D]
-            L.orc_cut_links.argtypes = [C.POINTER(_Cfg), _D, C.c_int, _D, _I, _I, _D, C.c_int]
-            L.orc_winding.argtypes = [_D, C.c_int, C.c_int, C.c_int]
-            L.orc_spread.argtypes = [C.POINTER(_Cfg), _D, C.c_int, _D, _D, _D]
-            L.orc_interp.argtypes = [C.POINTER(_Cfg), _D, C.c_int, _D, _D, _D]
-            L.orc_spring_forces_arr.argtypes = [_D, C.c_int, C.c_int, C.c_double, C.c_double,
-                                                C.c_double, _D]
-            L.orc_normal_split_arr.argtypes = [_D, C.c_int, C.c_int, C.c_double, _D, _D, _D, _D]
-            _lib = L
-    return _lib
+        if parallel and _lib_omp is None:
+            path = build(parallel=True)
+            if path is None:
+                raise RuntimeError("the OpenMP build of the oracle is unavailable")
+            _lib_omp = _bind(C.CDLL(path))
+        if not parallel and _lib is None:
+            _lib = _bind(C.CDLL(build()))
+        return _lib_omp if parallel else _lib
+
+
+def _bind(L):
+    """Declare the argument and result types of every oracle routine."""
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [C.POINTER(_Cfg)]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_set_df.argtypes = [C.c_void_p, _D]
+    L.orc_get_df.argtypes = [C.c_void_p, _D]
+    L.orc_init_equilibrium.argtypes = [C.c_void_p, _D, _D, _D]
+    L.orc_set_interface.argtypes = [C.c_void_p, _D, C.c_int, C.c_int, C.c_int, C.c_double,
+                                    C.c_double, C.c_double, C.c_double, C.c_int,
+                                    C.c_double, _D, _D]
+    L.orc_step.argtypes = [C.c_void_p]
+    L.orc_prepare.argtypes = [C.c_void_p]
+    L.orc_cut_link_count.argtypes = [C.c_void_p]
+    L.orc_run.argtypes = [C.c_void_p, C.c_int]
+    L.orc_get_step_macros.argtypes = [C.c_void_p, _D, _D, _D]
+    L.orc_get_markers.argtypes = [C.c_void_p, _D, _D, _D, _D]
+    L.orc_mdf_iters.argtypes = [C.c_void_p]
+    L.orc_set_ws_previous.argtypes = [C.c_void_p, C.c_int]
+    L.orc_get_ustar.argtypes = [C.c_void_p, _D]
+    L.orc_mdf_residual.argtypes = [C.c_void_p]
+    L.orc_mdf_residual.restype = C.c_double
+    L.orc_polygon_area.argtypes = [_D, C.c_int]
+    L.orc_polygon_area.restype = C.c_double
+    L.orc_phi.argtypes = [C.c_double]
+    L.orc_phi.restype = C.c_double
+    L.orc_mrt_matrix.argtypes = [_D]
+    L.orc_invert9.argtypes = [_D, _D]
+    L.orc_mrt_inverse.argtypes = [_D, _D]
+    L.orc_feq_shifted.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _D]
+    L.orc_guo_source.argtypes = [C.c_double] * 4 + [_D]
+    L.orc_collide_cell.argtypes = [C.POINTER(_Cfg), _D, _D, _D, C.c_double, C.c_double, _D]
+    L.orc_cut_links.argtypes = [C.POINTER(_Cfg), _D, C.c_int, _D, _I, _I, _D, C.c_int]
+    L.orc_winding.argtypes = [_D, C.c_int, C.c_int, C.c_int]
+    L.orc_spread.argtypes = [C.POINTER(_Cfg), _D, C.c_int, _D, _D, _D]
+    L.orc_interp.argtypes = [C.POINTER(_Cfg), _D, C.c_int, _D, _D, _D]
+    L.orc_spring_forces_arr.argtypes = [_D, C.c_int, C.c_int, C.c_double, C.c_double,
+                                        C.c_double, _D]
+    L.orc_normal_split_arr.argtypes = [_D, C.c_int, C.c_int, C.c_double, _D, _D, _D, _D]
+    return L
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP build runs with (OMP_NUM_THREADS, else every host core)."""
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
 
 
 def _p(a: np.ndarray):
@@ -239,15 +267,17 @@ def polygon_area(X) -> float:
 class Oracle:
     """One lattice with at most one immersed interface, stepped on the CPU in FP64."""
 
-    def __init__(self, nx, ny, **kw):
+    def __init__(self, nx, ny, parallel=False, **kw):
+        """parallel=True steps with the OpenMP build (identical results, all cores)."""
         self.cfg = make_cfg(nx, ny, **kw)
         self.nx, self.ny = nx, ny
-        self._h = lib().orc_create(C.byref(self.cfg))
+        self._L = lib(parallel)
+        self._h = self._L.orc_create(C.byref(self.cfg))
         self.n_markers = 0
 
     def close(self):
         if self._h:
-            lib().orc_destroy(self._h)
+            self._L.orc_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -259,15 +289,15 @@ class Oracle:
     # state
     def init_equilibrium(self, rho=None, ux=None, uy=None):
         keep = [None if a is None else _f64(a).ravel() for a in (rho, ux, uy)]
-        lib().orc_init_equilibrium(self._h, *[None if k is None else _p(k) for k in keep])
+        self._L.orc_init_equilibrium(self._h, *[None if k is None else _p(k) for k in keep])
 
     def set_df(self, df):
         df = _f64(df).reshape(9, self.ny, self.nx)
-        lib().orc_set_df(self._h, _p(df))
+        self._L.orc_set_df(self._h, _p(df))
 
     def get_df(self):
         df = np.zeros((9, self.ny, self.nx))
-        lib().orc_get_df(self._h, _p(df))
+        self._L.orc_get_df(self._h, _p(df))
         return df
 
     def set_interface(self, X, model=SPRING, moves=True, kappa=0.0, dX=1.0, l0=1.0, eta=2.0,
@@ -276,13 +306,13 @@ class Oracle:
         n = X.shape[0]
         Gp = None if G is None else _f64(G).reshape(n, 2)
         UDa = None if UD is None else _f64(UD).reshape(n, 2)
-        lib().orc_set_interface(self._h, _p(X), n, model, int(moves), kappa, dX, l0, eta,
+        self._L.orc_set_interface(self._h, _p(X), n, model, int(moves), kappa, dX, l0, eta,
                                 mdf_iters, mdf_tol, None if Gp is None else _p(Gp),
                                 None if UDa is None else _p(UDa))
         self.n_markers = n
 
     def step(self, n=1):
-        if lib().orc_run(self._h, int(n)) != 0:
+        if self._L.orc_run(self._h, int(n)) != 0:
             raise RuntimeError("oracle step failed (cut-link capacity)")
 
     def step_macros(self, deviation=False):
@@ -290,7 +320,7 @@ class Oracle:
         collision (Eq. 24 at time t)."""
         N = self.nx * self.ny
         r, ux, uy = np.zeros(N), np.zeros(N), np.zeros(N)
-        lib().orc_get_step_macros(self._h, _p(r), _p(ux), _p(uy))
+        self._L.orc_get_step_macros(self._h, _p(r), _p(ux), _p(uy))
         s = (self.ny, self.nx)
         if not deviation:
             r = r + self.cfg.rho0
@@ -299,28 +329,28 @@ class Oracle:
     def current_macros(self, deviation=True):
         """drho (or rho), ux, uy of the current state: what the next collision uses
         (items 1-4 of the step, without advancing)."""
-        if lib().orc_prepare(self._h) != 0:
+        if self._L.orc_prepare(self._h) != 0:
             raise RuntimeError("oracle prepare failed (cut-link capacity)")
         return self.step_macros(deviation=deviation)
 
     def cut_link_count(self):
-        return lib().orc_cut_link_count(self._h)
+        return self._L.orc_cut_link_count(self._h)
 
     def markers(self):
         n = self.n_markers
         X, G, U, Fn = np.zeros((n, 2)), np.zeros((n, 2)), np.zeros((n, 2)), np.zeros(n)
-        lib().orc_get_markers(self._h, _p(X), _p(G), _p(U), _p(Fn))
+        self._L.orc_get_markers(self._h, _p(X), _p(G), _p(U), _p(Fn))
         return dict(X=X, G=G, U=U, Fn=Fn)
 
     def set_ws_previous(self, on=True):
         """Direct forcing starts from the force the previous iteration ended with."""
-        lib().orc_set_ws_previous(self._h, int(on))
+        self._L.orc_set_ws_previous(self._h, int(on))
 
     def unforced_velocity(self):
         """U*_k = interp(u*) of the most recent force iteration."""
         out = np.zeros((self.n_markers, 2))
-        lib().orc_get_ustar(self._h, _p(out))
+        self._L.orc_get_ustar(self._h, _p(out))
         return out
 
     def mdf_stats(self):
-        return lib().orc_mdf_iters(self._h), lib().orc_mdf_residual(self._h)
+        return self._L.orc_mdf_iters(self._h), self._L.orc_mdf_residual(self._h)

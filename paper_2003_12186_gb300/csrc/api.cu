@@ -79,12 +79,14 @@ int prepare(iilbm_lattice *h) {
 }
 
 void drop_graph(iilbm_lattice *h) {
-  for (int r = 0; r < GRAPH_RING; r++) {
-    if (h->gexec[r]) cudaGraphExecDestroy(h->gexec[r]);
-    h->gexec[r] = nullptr;
-    h->ring_pending[r] = false;
+  for (int k = 0; k < GRAPH_KINDS; k++) {
+    for (int r = 0; r < GRAPH_RING; r++) {
+      if (h->gexec[k][r]) cudaGraphExecDestroy(h->gexec[k][r]);
+      h->gexec[k][r] = nullptr;
+      h->ring_pending[k][r] = false;
+    }
+    h->ring_next[k] = 0;
   }
-  h->ring_next = 0;
 }
 
 // Clear every jump / force buffer (used when the interface or the state is replaced
@@ -101,6 +103,43 @@ int clear_fields(iilbm_lattice *h) {
   }
   h->prepared = false;
   return IILBM_OK;
+}
+
+// Fold recorded lean stream-collide event pairs into the running sum: the eager pairs,
+// or the graph_len(k) pairs of slot r of graph kind k.
+int drain_events(iilbm_lattice *h) {
+  if (h->nev == 0) return IILBM_OK;
+  CK(cudaEventSynchronize(h->ev[EAGER_EV0 + 2 * h->nev - 1]));
+  for (int e = 0; e < h->nev; e++) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, h->ev[EAGER_EV0 + 2 * e], h->ev[EAGER_EV0 + 2 * e + 1]));
+    h->sc_ms += ms;
+  }
+  h->nev = 0;
+  return IILBM_OK;
+}
+
+// First timing event of slot r of graph kind k.
+int slot_ev0(int k, int r) { return graph_ev0(k) + 2 * graph_len(k) * r; }
+
+int drain_slot(iilbm_lattice *h, int k, int r) {
+  if (!h->ring_pending[k][r]) return IILBM_OK;
+  const int e0 = slot_ev0(k, r), len = graph_len(k);
+  CK(cudaEventSynchronize(h->ev[e0 + 2 * len - 1]));
+  for (int q = 0; q < len; q++) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, h->ev[e0 + 2 * q], h->ev[e0 + 2 * q + 1]));
+    h->sc_ms += ms;
+  }
+  h->ring_pending[k][r] = false;
+  return IILBM_OK;
+}
+
+int drain_all(iilbm_lattice *h) {
+  int rc = drain_events(h);
+  for (int k = 0; k < GRAPH_KINDS && !rc; k++)
+    for (int r = 0; r < GRAPH_RING && !rc; r++) rc = drain_slot(h, k, r);
+  return rc;
 }
 
 }  // namespace
@@ -121,7 +160,8 @@ const char *iilbm_error_string(int status) {
     case IILBM_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
     case IILBM_ERR_NONFINITE: return "non-finite population";
     case IILBM_ERR_INTERFACE: return "invalid marker polygon";
-    case IILBM_ERR_CAPACITY: return "cut-link capacity exceeded";
+    case IILBM_ERR_CAPACITY:
+      return "capacity exceeded (cut-link list, forcing shared memory or no-allocation staging array)";
     case IILBM_ERR_NO_DEVICE: return "no compute capability 10.3 CUDA device";
   }
   return "unknown status";
@@ -263,21 +303,32 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
   int rc = clear_fields(h);
   if (rc) return rc;
   CK(cudaStreamSynchronize(h->stream));
-  drop_graph(h);
-  free_interface(h);
+  // Same marker count and parameters: the marker buffers are reused in place, and the
+  // captured step graphs (which hold their addresses and the parameters) stay valid --
+  // a new polygon of the same body costs no reallocation and no recapture.
+  const bool keep = n > 0 && n == h->nm && std::memcmp(p, &h->ip, sizeof *p) == 0;
+  const int win0[4] = {h->df_win[0], h->df_win[1], h->df_win[2], h->df_win[3]};
+  if (!keep) {
+    int drc = drain_all(h);
+    if (drc) return drc;
+    drop_graph(h);
+    free_interface(h);
+  }
   if (n == 0) return IILBM_OK;
   const size_t b2 = 2 * (size_t)n * sizeof(double);
-  bool ok = cudaMalloc(&h->X, b2) == cudaSuccess && cudaMalloc(&h->aux, b2) == cudaSuccess &&
-            cudaMalloc(&h->G, b2) == cudaSuccess && cudaMalloc(&h->G0, b2) == cudaSuccess &&
-            cudaMalloc(&h->Gdf, b2) == cudaSuccess && cudaMalloc(&h->Ustar, b2) == cudaSuccess &&
-            cudaMalloc(&h->Fn, (size_t)n * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&h->Xq, b2) == cudaSuccess && cudaMalloc(&h->U, b2) == cudaSuccess &&
-            cudaMalloc(&h->nrm, b2) == cudaSuccess && cudaMalloc(&h->Xp, b2) == cudaSuccess &&
-            cudaMalloc(&h->Xqp, b2) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    free_interface(h);
-    return IILBM_ERR_OOM;
+  if (!keep) {
+    bool ok = cudaMalloc(&h->X, b2) == cudaSuccess && cudaMalloc(&h->aux, b2) == cudaSuccess &&
+              cudaMalloc(&h->G, b2) == cudaSuccess && cudaMalloc(&h->G0, b2) == cudaSuccess &&
+              cudaMalloc(&h->Gdf, b2) == cudaSuccess && cudaMalloc(&h->Ustar, b2) == cudaSuccess &&
+              cudaMalloc(&h->Fn, (size_t)n * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&h->Xq, b2) == cudaSuccess && cudaMalloc(&h->U, b2) == cudaSuccess &&
+              cudaMalloc(&h->nrm, b2) == cudaSuccess && cudaMalloc(&h->Xp, b2) == cudaSuccess &&
+              cudaMalloc(&h->Xqp, b2) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      free_interface(h);
+      return IILBM_ERR_OOM;
+    }
   }
   h->nm = n;
   h->ip = *p;
@@ -320,8 +371,11 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
     h->df_win[2] = (int)std::floor(bx1) + 2 - h->df_win[0] + 1;
     h->df_win[3] = (int)std::floor(by1) + 2 - h->df_win[1] + 1;
     bad = direct_forcing_smem(h, h->df_win[2], h->df_win[3], n) > 227 * 1024;
+    // the force iteration's window is baked into its captured launches
+    if (keep && std::memcmp(win0, h->df_win, sizeof win0) != 0) drop_graph(h);
   }
   if (bad) {
+    drop_graph(h);
     free_interface(h);
     return IILBM_ERR_INTERFACE;
   }
@@ -375,38 +429,9 @@ int iilbm_get_populations(iilbm_t h, double *df) {
   return rc ? rc : read_status(h);
 }
 
-// Fold recorded lean stream-collide event pairs into the running sum: the eager pairs,
-// or the GRAPH_STEPS pairs of ring slot r.
-int drain_events(iilbm_lattice *h) {
-  if (h->nev == 0) return IILBM_OK;
-  CK(cudaEventSynchronize(h->ev[EAGER_EV0 + 2 * h->nev - 1]));
-  for (int e = 0; e < h->nev; e++) {
-    float ms = 0;
-    CK(cudaEventElapsedTime(&ms, h->ev[EAGER_EV0 + 2 * e], h->ev[EAGER_EV0 + 2 * e + 1]));
-    h->sc_ms += ms;
-  }
-  h->nev = 0;
-  return IILBM_OK;
-}
+}  // extern "C"
 
-int drain_slot(iilbm_lattice *h, int r) {
-  if (!h->ring_pending[r]) return IILBM_OK;
-  const int e0 = 2 * GRAPH_STEPS * r;
-  CK(cudaEventSynchronize(h->ev[e0 + 2 * GRAPH_STEPS - 1]));
-  for (int k = 0; k < GRAPH_STEPS; k++) {
-    float ms = 0;
-    CK(cudaEventElapsedTime(&ms, h->ev[e0 + 2 * k], h->ev[e0 + 2 * k + 1]));
-    h->sc_ms += ms;
-  }
-  h->ring_pending[r] = false;
-  return IILBM_OK;
-}
-
-int drain_all(iilbm_lattice *h) {
-  int rc = drain_events(h);
-  for (int r = 0; r < GRAPH_RING && !rc; r++) rc = drain_slot(h, r);
-  return rc;
-}
+namespace {
 
 // Kernels launched by one step: lean stream-collide; with an interface also the
 // forced stream-collide and the interpolation fused with the next interface phase
@@ -461,67 +486,114 @@ int one_step(iilbm_lattice *h, int ev_slot) {
   return IILBM_OK;
 }
 
-// Capture GRAPH_STEPS steps starting from an even, prepared state into ring slot r
-// (with timing on, its steps record into the slot's own event pairs).
-int capture_graph(iilbm_lattice *h, int r) {
+// Graph replay needs the state a captured step starts from: prepared for a pipelined
+// lattice (and one without an interface), unprepared for a directly forced body, whose
+// captured steps each begin with the force iteration and the interface phase.
+bool graph_entry(const iilbm_lattice *h) {
+  if (h->nm == 0) return true;
+  return pipelined(h) ? h->prepared : !h->prepared;
+}
+
+// One step as captured: the interface phase first where the state needs it, then the
+// step itself.  ev_slot as for one_step.
+int graph_step(iilbm_lattice *h, int ev_slot) {
+  int rc = prepare(h);
+  return rc ? rc : one_step(h, ev_slot);
+}
+
+// Capture the graph_len(k) steps of kind k (from an even state, or one step from an odd
+// one for the last kind) into slot r.  Capture records the launches without running
+// them; the host-side state (level, preparation) is restored afterwards, so any slot of
+// any kind may be captured from any state that is a graph entry.
+int capture_graph(iilbm_lattice *h, int k, int r) {
   const long long step0 = h->step;
+  const bool prepared0 = h->prepared;
+  const bool odd = k == GRAPH_ODD;
+  h->step = odd ? (step0 | 1) : (step0 & ~1LL);
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   int rc = IILBM_OK;
   h->capturing = true;
-  for (int k = 0; k < GRAPH_STEPS && !rc; k++)
-    rc = one_step(h, h->timing ? 2 * (GRAPH_STEPS * r + k) : -1);
+  for (int q = 0; q < graph_len(k) && !rc; q++)
+    rc = graph_step(h, h->timing ? slot_ev0(k, r) + 2 * q : -1);
   h->capturing = false;
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
   cudaGetLastError();
   h->step = step0;
-  h->prepared = true;
+  h->prepared = prepared0;
   if (rc) {
     if (graph) cudaGraphDestroy(graph);
     return rc;
   }
   if (e != cudaSuccess) return IILBM_ERR_CUDA;
   // honour the side stream's priority inside the graph
-  e = cudaGraphInstantiateWithFlags(&h->gexec[r], graph, cudaGraphInstantiateFlagUseNodePriority);
+  e = cudaGraphInstantiateWithFlags(&h->gexec[k][r], graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
-    h->gexec[r] = nullptr;
+    h->gexec[k][r] = nullptr;
     cudaGetLastError();
     return IILBM_ERR_CUDA;
   }
   return IILBM_OK;
 }
 
+// Capture every kind's graph (slot 0, or all GRAPH_RING slots with timing on) at the
+// first replay, so that no later call of any length pays for a capture.
+int capture_all(iilbm_lattice *h) {
+  const int slots = h->timing ? GRAPH_RING : 1;
+  int rc = IILBM_OK;
+  for (int k = 0; k < GRAPH_KINDS && !rc; k++)
+    for (int r = 0; r < slots && !rc; r++)
+      if (!h->gexec[k][r]) rc = capture_graph(h, k, r);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Advance n steps.  With graphs on, each iteration launches one graph: the one-step
+// graph from an odd state, else the longest kind that fits in what is left, so n steps
+// take at most one odd step and the binary decomposition of the rest.  A state that is
+// not a graph entry (a direct-forcing state prepared by a read-out, or graphs off) takes
+// an eager step.
 int iilbm_step(iilbm_t h, int32_t n) {
   if (!h || n < 0 || h->in_batch) return IILBM_ERR_INVALID_ARG;
   int rc;
   while (n > 0) {
-    if ((rc = prepare(h))) return rc;
-    const bool graph_ok = h->use_graph && (pipelined(h) || h->nm == 0) && (h->step & 1) == 0 &&
-                          n >= GRAPH_STEPS;
-    if (graph_ok) {
+    if (h->use_graph && h->nm > 0 && pipelined(h) && !h->prepared && (rc = prepare(h)))
+      return rc;
+    if (h->use_graph && graph_entry(h)) {
       if (h->graph_timing != h->timing) {
         if ((rc = drain_all(h))) return rc;
+        CK(cudaStreamSynchronize(h->stream));  // no graph of the other setting in flight
         drop_graph(h);
         h->graph_timing = h->timing;
       }
-      // without timing one executable suffices; with timing the ring lets each launch
-      // record into events that the launch GRAPH_RING earlier has long finished with
-      const int r = h->timing ? h->ring_next : 0;
-      if (h->timing && (rc = drain_slot(h, r))) return rc;
-      if (!h->gexec[r] && (rc = capture_graph(h, r))) return rc;
-      CK(cudaGraphLaunch(h->gexec[r], h->stream));
-      h->step += GRAPH_STEPS;
-      h->prepared = true;
-      n -= GRAPH_STEPS;
+      if ((rc = capture_all(h))) return rc;
+      int k = GRAPH_ODD;
+      if ((h->step & 1) == 0) {
+        k = 0;
+        while (graph_len(k) > n) k++;
+      }
+      // with timing the ring lets each launch record into events that the launch
+      // GRAPH_RING earlier of the same kind has long finished with
+      const int r = h->timing ? h->ring_next[k] : 0;
+      if (h->timing && (rc = drain_slot(h, k, r))) return rc;
+      CK(cudaGraphLaunch(h->gexec[k][r], h->stream));
+      const int len = graph_len(k);
+      h->step += len;
+      h->prepared = pipelined(h) || h->nm == 0;
+      n -= len;
       if (h->timing) {
-        h->ring_pending[r] = true;
-        h->ring_next = (r + 1) % GRAPH_RING;
-        h->sc_launches += GRAPH_STEPS;
-        h->kernel_launches += GRAPH_STEPS * kernels_per_step(h);
+        h->ring_pending[k][r] = true;
+        h->ring_next[k] = (r + 1) % GRAPH_RING;
+        h->sc_launches += len;
+        h->kernel_launches += len * kernels_per_step(h);
       }
       continue;
     }
+    if ((rc = prepare(h))) return rc;
     int slot = -1;
     if (h->timing) {
       if (h->nev == EAGER_PAIRS && (rc = drain_events(h))) return rc;
@@ -612,6 +684,25 @@ int iilbm_get_macros(iilbm_t h, double *drho, double *ux, double *uy) {
   return rc ? rc : read_status(h);
 }
 
+int iilbm_get_jump(iilbm_t h, double *J) {
+  if (!h || !J) return IILBM_ERR_INVALID_ARG;
+  int rc = prepare(h);
+  if (rc) return rc;
+  const size_t bytes = 8 * (size_t)h->cfg.nx * h->cfg.ny * sizeof(double);
+  double *d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return IILBM_ERR_OOM;
+  }
+  rc = launch_get_jump(h, d);
+  if (!rc && cudaMemcpyAsync(J, d, bytes, cudaMemcpyDefault, h->stream) != cudaSuccess)
+    rc = IILBM_ERR_CUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess && !rc) rc = IILBM_ERR_CUDA;
+  cudaGetLastError();
+  cudaFree(d);
+  return rc ? rc : read_status(h);
+}
+
 int iilbm_get_markers(iilbm_t h, double *X, double *G, double *U, double *Fn) {
   if (!h) return IILBM_ERR_INVALID_ARG;
   if (h->nm == 0) return read_status(h);
@@ -649,6 +740,10 @@ int iilbm_set_warm_start(iilbm_t h, const double *G0) {
 int iilbm_set_warm_start_mode(iilbm_t h, int32_t mode) {
   if (!h || mode < IILBM_WS_GIVEN || mode > IILBM_WS_PREVIOUS) return IILBM_ERR_INVALID_ARG;
   if (h->in_batch) return IILBM_ERR_INVALID_ARG;  // owned by a batch until it is destroyed
+  int rc = drain_all(h);  // captured force iterations bake the start mode in
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(h->stream));  // no graph of the old setting in flight
+  drop_graph(h);
   h->ws_mode = mode;
   h->mlp = nullptr;
   return IILBM_OK;
@@ -665,6 +760,13 @@ int iilbm_set_warm_start_mlp(iilbm_t h, iilbm_mlp_t mlp, double re) {
     h->ws_mode = prev;
     return IILBM_ERR_CAPACITY;
   }
+  int rc = drain_all(h);  // captured force iterations bake the network and Re in
+  if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = IILBM_ERR_CUDA;
+  if (rc) {
+    h->ws_mode = prev;
+    return rc;
+  }
+  drop_graph(h);
   h->mlp = mlp;
   h->re = (float)re;
   return IILBM_OK;

@@ -47,9 +47,19 @@ constexpr int ST_TIMEOUT = 8;
 constexpr double QSCALE = 16777216.0;
 constexpr double MAX_SEGMENT = 16.0;
 constexpr double MAX_COORD = 16000.0;
-constexpr int GRAPH_STEPS = 32;
+// CUDA graphs of a lattice: kind k < GRAPH_KINDS - 1 replays graph_len(k) = 32 >> k
+// steps from an even state, the last kind one step from an odd state; iilbm_step(n)
+// launches the binary decomposition of n (after one odd step, if the state is odd).
+constexpr int GRAPH_KINDS = 7;
+constexpr int GRAPH_ODD = GRAPH_KINDS - 1;
+constexpr int GRAPH_MAX = 32;
+__host__ __device__ constexpr int graph_len(int k) { return k < GRAPH_ODD ? GRAPH_MAX >> k : 1; }
 constexpr int GRAPH_RING = 4;
-constexpr int EAGER_EV0 = 2 * GRAPH_STEPS * GRAPH_RING;  // first eager timing event
+// first timing event of kind k's ring (a pair per step of each of its GRAPH_RING graphs)
+__host__ __device__ constexpr int graph_ev0(int k) {
+  return k == 0 ? 0 : graph_ev0(k - 1) + 2 * GRAPH_RING * graph_len(k - 1);
+}
+constexpr int EAGER_EV0 = graph_ev0(GRAPH_KINDS);  // first eager timing event
 constexpr int EAGER_PAIRS = 128;
 
 // Sentinel of a snapped marker coordinate outside the region the integer geometry covers.
@@ -168,14 +178,15 @@ struct iilbm_lattice {
   // execution
   bool vector_sc;     // vectorised stream-collide when nx is a multiple of its width
   bool overlap;       // next interface phase on the side stream during stream-collide
-  bool use_graph;     // replay GRAPH_STEPS steps per CUDA-graph launch
+  bool use_graph;     // replay steps from CUDA graphs (GRAPH_KINDS lengths)
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
-  // graph ring: GRAPH_RING executables of GRAPH_STEPS steps; with timing on each one
-  // records into its own event set, so draining a set never waits on the GPU
-  cudaGraphExec_t gexec[iilbm::GRAPH_RING];
-  bool ring_pending[iilbm::GRAPH_RING];
-  int ring_next;
+  // per graph kind a ring of GRAPH_RING executables; with timing on each one records
+  // into its own event set, so draining a set never waits on the GPU (without timing
+  // slot 0 alone is used)
+  cudaGraphExec_t gexec[iilbm::GRAPH_KINDS][iilbm::GRAPH_RING];
+  bool ring_pending[iilbm::GRAPH_KINDS][iilbm::GRAPH_RING];
+  int ring_next[iilbm::GRAPH_KINDS];
   bool graph_timing;  // the instantiated graphs record timing events
   bool capturing;     // inside cudaStreamBeginCapture / EndCapture
   bool in_batch;      // advanced by a batch (iilbm_step refused meanwhile)
@@ -224,6 +235,7 @@ int launch_macros(iilbm_lattice *h, double *drho, double *ux, double *uy);
 int launch_set_populations(iilbm_lattice *h, const double *df, bool equilibrium,
                            const double *rho, const double *ux, const double *uy);
 int launch_get_populations(iilbm_lattice *h, double *df);
+int launch_get_jump(iilbm_lattice *h, double *out);
 int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s);
 int launch_interp_interface(iilbm_lattice *h, cudaStream_t s);
 int launch_channel_bc(iilbm_lattice *h);

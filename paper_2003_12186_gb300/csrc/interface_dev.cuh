@@ -310,8 +310,9 @@ __device__ __forceinline__ void segment_links(long long ax, long long ay, long l
         continue;
       // coefficient s w_i/c_s^2 Fn(t), t = o3 / (o3 - o4) along A -> B (Fn linear along
       // the segment).  FP64 for FP64 storage (an FP32 quotient refined by one Newton
-      // step); FP32 otherwise, where |o3|, |o3 - o4| < 2^30 convert exactly and t
-      // carries a relative error of a few FP32 ulps.
+      // step); FP32 otherwise: |o3|, |o3 - o4| < 2^31 fit the int casts, and converting
+      // each to FP32 rounds it with a relative error of at most 2^-24, so t carries a
+      // few FP32 ulps.
       T coef;
       if (sizeof(T) == 8) {
         const double num = (double)o3, dd = (double)(o3 - o4);

@@ -179,6 +179,17 @@ __global__ void k_get_populations(const S *A, const Geom geo,
     df[i * N + o] = double(Store<S>::ld(A[aa_loc(geo, odd, i, x, y)]) * p.inv_scale);
 }
 
+// The jump field of the current state: J[i - 1][y][x] in population units (i = 1..8),
+// FP64 natural layout.
+template <typename T>
+__global__ void k_get_jump(const T *__restrict__ J, const Geom geo, double *out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= geo.nx) return;
+  const long long N = (long long)geo.nx * geo.ny;
+  for (int i = 0; i < 8; i++)
+    out[i * N + (long long)y * geo.nx + x] = (double)J[i * geo.plane + (long long)y * geo.pitch + x];
+}
+
 // ------------------------------------------------------------ channel ends
 // Inflow / outflow of a channel on the streamed state (one thread per row), after every
 // stream-collide: inflow column x = 0 by non-equilibrium extrapolation from column 1,
@@ -305,6 +316,16 @@ int launch_macros(iilbm_lattice *h, double *drho, double *ux, double *uy) {
                                              odd, drho, ux, uy);
     return last_error();
   });
+}
+
+int launch_get_jump(iilbm_lattice *h, double *out) {
+  const int b = h->step & 1;
+  dim3 grid((h->geom.nx + 127) / 128, h->geom.ny);
+  if (h->cfg.storage == IILBM_F64)
+    k_get_jump<double><<<grid, 128, 0, h->stream>>>((const double *)h->Jb[b], h->geom, out);
+  else
+    k_get_jump<float><<<grid, 128, 0, h->stream>>>((const float *)h->Jb[b], h->geom, out);
+  return last_error();
 }
 
 int launch_set_populations(iilbm_lattice *h, const double *df, bool equilibrium,

@@ -83,6 +83,7 @@ SIGNATURES = {
     "iilbm_get_unforced_velocity": [_H, _P],
     "iilbm_get_body_force": [_H, C.POINTER(C.c_double)],
     "iilbm_get_cut_link_count": [_H, C.POINTER(C.c_int32)],
+    "iilbm_get_jump": [_H, _P],
     "iilbm_set_timing": [_H, C.c_int32],
     "iilbm_get_timing": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int32),
                          C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
@@ -137,22 +138,53 @@ def _check(fn: str, rc: int):
         raise IilbmError(fn, rc)
 
 
-def _ptr(a):
-    """Raw pointer of a numpy array or a torch tensor (None -> NULL)."""
+def _ptr(a, count=None, device=None, dtype="float64"):
+    """Raw pointer of a numpy array or a torch tensor (None -> NULL).
+
+    The library reads or writes exactly `count` elements of `dtype` there, so the buffer
+    is checked first: C-contiguous, of that dtype and element count, and -- for a torch
+    tensor -- on the host or on CUDA device `device` (the lattice's).  Raises ValueError,
+    which `python -O` keeps, instead of letting a copy run past the end of a buffer."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        assert a.flags["C_CONTIGUOUS"] and a.dtype == np.float64, "need contiguous float64"
+        if not a.flags["C_CONTIGUOUS"] or a.dtype != np.dtype(dtype):
+            raise ValueError(f"need a C-contiguous {dtype} array, got {a.dtype}")
+        if count is not None and a.size != count:
+            raise ValueError(f"need {count} elements, got {a.size} (shape {a.shape})")
         return a.ctypes.data
-    # torch tensor
-    assert a.is_contiguous() and str(a.dtype) == "torch.float64", "need contiguous float64"
+    if not hasattr(a, "data_ptr"):
+        raise ValueError(f"need a numpy array or a torch tensor, got {type(a).__name__}")
+    if not a.is_contiguous() or str(a.dtype) != f"torch.{dtype}":
+        raise ValueError(f"need a contiguous {dtype} tensor, got {a.dtype}")
+    if count is not None and a.numel() != count:
+        raise ValueError(f"need {count} elements, got {a.numel()} (shape {tuple(a.shape)})")
+    if a.device.type == "cuda":
+        if device is not None and a.device.index != device:
+            raise ValueError(f"tensor on cuda:{a.device.index}, lattice on cuda:{device}")
+    elif a.device.type != "cpu":
+        raise ValueError(f"tensor on {a.device}, need the host or a CUDA device")
     return a.data_ptr()
 
 
 def _host(a, shape):
     a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
-    assert a.size == int(np.prod(shape)), f"expected {shape}, got {a.shape}"
+    if a.size != int(np.prod(shape)):
+        raise ValueError(f"expected {shape}, got {a.shape}")
     return a
+
+
+def _current_device():
+    """The current CUDA device as torch sees it (the one the library creates handles
+    on), or None when torch is not in use."""
+    import sys
+    torch = sys.modules.get("torch")
+    if torch is None:
+        return None
+    try:
+        return torch.cuda.current_device() if torch.cuda.is_available() else None
+    except Exception:
+        return None
 
 
 class Lattice:
@@ -179,6 +211,7 @@ class Lattice:
         self.cfg = cfg
         self.nx, self.ny = nx, ny
         self.n_markers = 0
+        self.device = _current_device()
         h = _H()
         _check("iilbm_create_lattice", L.iilbm_create_lattice(C.byref(h), C.byref(cfg)))
         self._h = h
@@ -215,28 +248,35 @@ class Lattice:
         Xh = X if not isinstance(X, np.ndarray) and hasattr(X, "data_ptr") else _host(X, (n, 2))
         A = None if aux is None else (aux if hasattr(aux, "data_ptr") else _host(aux, (n, 2)))
         _check("iilbm_set_interface",
-               self._L.iilbm_set_interface(self._h, _ptr(Xh), n, C.byref(p), _ptr(A)))
+               self._L.iilbm_set_interface(self._h, self._p(Xh, 2 * n), n, C.byref(p),
+                                           self._p(A, 2 * n)))
         self.n_markers = n
 
     set_interface = iilbm_set_interface
+
+    def _p(self, a, count):
+        return _ptr(a, count, self.device)
 
     def iilbm_init_equilibrium(self, rho=None, ux=None, uy=None):
         N = (self.ny, self.nx)
         arrs = [None if a is None else _host(a, N) for a in (rho, ux, uy)]
         _check("iilbm_init_equilibrium",
-               self._L.iilbm_init_equilibrium(self._h, *[_ptr(a) for a in arrs]))
+               self._L.iilbm_init_equilibrium(self._h, *[self._p(a, self.nx * self.ny)
+                                                         for a in arrs]))
 
     init_equilibrium = iilbm_init_equilibrium
 
     def iilbm_set_populations(self, df):
         d = df if hasattr(df, "data_ptr") else _host(df, (9, self.ny, self.nx))
-        _check("iilbm_set_populations", self._L.iilbm_set_populations(self._h, _ptr(d)))
+        _check("iilbm_set_populations",
+               self._L.iilbm_set_populations(self._h, self._p(d, 9 * self.nx * self.ny)))
 
     set_populations = iilbm_set_populations
 
     def iilbm_get_populations(self, out=None):
         out = np.zeros((9, self.ny, self.nx)) if out is None else out
-        _check("iilbm_get_populations", self._L.iilbm_get_populations(self._h, _ptr(out)))
+        _check("iilbm_get_populations",
+               self._L.iilbm_get_populations(self._h, self._p(out, 9 * self.nx * self.ny)))
         return out
 
     get_populations = iilbm_get_populations
@@ -251,7 +291,9 @@ class Lattice:
         outs = []
         for a, w in zip((drho, ux, uy), want):
             outs.append(a if a is not None else (np.zeros((self.ny, self.nx)) if w else None))
-        _check("iilbm_get_macros", self._L.iilbm_get_macros(self._h, *[_ptr(a) for a in outs]))
+        N = self.nx * self.ny
+        _check("iilbm_get_macros",
+               self._L.iilbm_get_macros(self._h, *[self._p(a, N) for a in outs]))
         return tuple(outs)
 
     get_macros = iilbm_get_macros
@@ -262,22 +304,24 @@ class Lattice:
         outs = []
         for a, w in zip((drho, ux, uy), want):
             outs.append(a if a is not None else (np.zeros((self.ny, self.nx)) if w else None))
+        N = self.nx * self.ny
         _check("iilbm_get_macros_noalloc",
-               self._L.iilbm_get_macros_noalloc(self._h, *[_ptr(a) for a in outs]))
+               self._L.iilbm_get_macros_noalloc(self._h, *[self._p(a, N) for a in outs]))
         return tuple(outs)
 
     def iilbm_get_markers(self):
         n = self.n_markers
         X, G, U, Fn = np.zeros((n, 2)), np.zeros((n, 2)), np.zeros((n, 2)), np.zeros(n)
-        _check("iilbm_get_markers",
-               self._L.iilbm_get_markers(self._h, _ptr(X), _ptr(G), _ptr(U), _ptr(Fn)))
+        self.iilbm_get_markers_into(X, G, U, Fn)
         return dict(X=X, G=G, U=U, Fn=Fn)
 
     get_markers = iilbm_get_markers
 
     def iilbm_get_markers_into(self, X=None, G=None, U=None, Fn=None):
+        n = self.n_markers
         _check("iilbm_get_markers",
-               self._L.iilbm_get_markers(self._h, _ptr(X), _ptr(G), _ptr(U), _ptr(Fn)))
+               self._L.iilbm_get_markers(self._h, self._p(X, 2 * n), self._p(G, 2 * n),
+                                         self._p(U, 2 * n), self._p(Fn, n)))
 
     def iilbm_get_mdf_stats(self):
         it, res = C.c_int32(), C.c_double()
@@ -288,7 +332,8 @@ class Lattice:
     def iilbm_set_warm_start(self, G0=None):
         G = None if G0 is None else (G0 if hasattr(G0, "data_ptr") else
                                      _host(G0, (self.n_markers, 2)))
-        _check("iilbm_set_warm_start", self._L.iilbm_set_warm_start(self._h, _ptr(G)))
+        _check("iilbm_set_warm_start",
+               self._L.iilbm_set_warm_start(self._h, self._p(G, 2 * self.n_markers)))
 
     def iilbm_set_warm_start_mode(self, mode):
         _check("iilbm_set_warm_start_mode", self._L.iilbm_set_warm_start_mode(self._h, int(mode)))
@@ -297,7 +342,7 @@ class Lattice:
         """U*_k [n][2] of the most recent force iteration (numpy, or into `out`)."""
         o = out if out is not None else np.zeros((self.n_markers, 2))
         _check("iilbm_get_unforced_velocity",
-               self._L.iilbm_get_unforced_velocity(self._h, _ptr(o)))
+               self._L.iilbm_get_unforced_velocity(self._h, self._p(o, 2 * self.n_markers)))
         return o
 
     def iilbm_set_warm_start_mlp(self, mlp, re):
@@ -316,6 +361,13 @@ class Lattice:
         F = (C.c_double * 2)()
         _check("iilbm_get_body_force", self._L.iilbm_get_body_force(self._h, F))
         return F[0], F[1]
+
+    def iilbm_get_jump(self, out=None):
+        """Jump field J[8][ny][nx] (directions 1..8) of the current state's interface."""
+        out = np.zeros((8, self.ny, self.nx)) if out is None else out
+        _check("iilbm_get_jump",
+               self._L.iilbm_get_jump(self._h, self._p(out, 8 * self.nx * self.ny)))
+        return out
 
     def iilbm_get_cut_link_count(self):
         c = C.c_int32()
@@ -414,11 +466,11 @@ class Batch:
 def _f32(a, shape=None):
     """Contiguous FP32 host array (or a contiguous float32 CUDA tensor, passed as is)."""
     if a is not None and not isinstance(a, np.ndarray) and hasattr(a, "data_ptr"):
-        assert a.is_contiguous() and str(a.dtype) == "torch.float32", "need contiguous float32"
+        _ptr(a, None if shape is None else int(np.prod(shape)), dtype="float32")
         return a
     a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
-    if shape is not None:
-        assert a.size == int(np.prod(shape)), f"expected {shape}, got {a.shape}"
+    if shape is not None and a.size != int(np.prod(shape)):
+        raise ValueError(f"expected {shape}, got {a.shape}")
     return a
 
 

@@ -39,3 +39,24 @@ def vel_error(g, o, uref=1e-6):
     _, ug, vg = g.get_macros()
     _, uo, vo = o.current_macros()
     return max(rel_err(ug, uo, uref), rel_err(vg, vo, uref))
+
+
+def oracle_jump_field(orc, o):
+    """The oracle's jump of the current state, J[i-1][y][x] (i = 1..8): its cut-link
+    records summed per link (a link crossed twice carries both records)."""
+    o.current_macros()  # runs the current state's interface phase
+    m = o.markers()
+    cell, d, coef = orc.cut_links(o.cfg, m["X"], m["Fn"])
+    J = np.zeros((8, o.ny * o.nx))
+    np.add.at(J, (d - 1, cell), coef)
+    return J.reshape(8, o.ny, o.nx), len(cell)
+
+
+def assert_jump_fields_agree(Jg, Jo, rel):
+    """Same cut links (the set of (direction, node) carrying a jump, compared exactly)
+    and the same values within rel of the largest."""
+    sg, so = Jg != 0, Jo != 0
+    assert np.array_equal(sg, so), (f"cut-link sets differ: {int((sg & ~so).sum())} only on "
+                                    f"the GPU, {int((so & ~sg).sum())} only in the oracle")
+    assert so.sum() > 0
+    assert np.abs(Jg - Jo).max() <= rel * np.abs(Jo).max()

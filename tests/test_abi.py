@@ -64,3 +64,25 @@ def test_no_device_is_reported_without_a_gpu():
     with pytest.raises(iilbm.IilbmError) as e:
         iilbm.Lattice(16, 16)
     assert e.value.code == -8
+
+
+def test_buffer_checks_raise_value_error():
+    """The binding checks every buffer the library will read or write (dtype, layout,
+    element count, device) and raises ValueError, which `python -O` keeps."""
+    import numpy as np
+    a = np.zeros(10)
+    assert iilbm._ptr(a, 10) == a.ctypes.data
+    assert iilbm._ptr(None, 10) is None
+    for bad in (dict(a=a, count=11), dict(a=np.zeros(10, np.float32), count=10),
+                dict(a=np.zeros((4, 6))[:, ::2], count=12), dict(a=[0.0] * 10, count=10)):
+        with pytest.raises(ValueError):
+            iilbm._ptr(bad["a"], bad["count"])
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(10, dtype=torch.float64)
+    assert iilbm._ptr(t, 10) == t.data_ptr()
+    with pytest.raises(ValueError):
+        iilbm._ptr(t, 9)
+    with pytest.raises(ValueError):
+        iilbm._ptr(t.to(torch.float32), 10)
+    with pytest.raises(ValueError):
+        iilbm._ptr(torch.zeros(10, dtype=torch.float64, device="meta"), 10)

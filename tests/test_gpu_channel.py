@@ -8,7 +8,7 @@ import pytest
 from paper_2003_12186_gb300 import iilbm
 from paper_2003_12186_gb300 import workloads as W
 
-from _pair import rel_err
+from _pair import assert_jump_fields_agree, oracle_jump_field, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -139,6 +139,9 @@ def test_channel_cylinder_full_size_fp32(orc):
     _, uo, vo = o.current_macros()
     assert max(rel_err(ug, uo, 0.05), rel_err(vg, vo, 0.05)) < 1e-5
     assert g.iilbm_get_cut_link_count() == o.cut_link_count() > 0
+    # the cut links of the fixed body exactly; the jump values follow the FP32 force
+    Jo, _ = oracle_jump_field(orc, o)
+    assert_jump_fields_agree(g.iilbm_get_jump(), Jo, 1e-4)
 
 
 def test_unforced_velocity_and_previous_force_start_fp64(orc):

@@ -177,3 +177,103 @@ def test_pipelined_membrane_near_walls(orc, bc):
         assert np.abs(o.markers()["U"]).max() > 1e-5
         outs.append(g.get_markers()["X"])
     assert np.abs(outs[0] - outs[1]).max() < 1e-13
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_graph_replay_for_any_length_and_parity(storage):
+    """Calls of every length and starting parity replay graphs (32/16/8/4/2/1 steps from
+    an even level, one step from an odd one) and give the state eager launches give:
+    FP64 to 1e-13 and FP32 to 1e-6 of the field's scale (the spreading's atomics add in
+    run-dependent order), markers likewise."""
+    w = W.ellipse_scaled(256, storage)
+    seq = (1, 2, 3, 5, 20, 33, 7, 64, 1)
+    res = []
+    for graph in (0, 1):
+        g = iilbm.Lattice(256, 256, collision=iilbm.MRT, storage=storage, tau=w["tau"],
+                          s=W.mrt_rates(w["tau"]))
+        g.set_option(iilbm.OPT_CUDA_GRAPH, graph)
+        g.set_interface(w["X"], model=iilbm.SPRING, stiffness=w["kappa"], dX=w["dX"])
+        out = []
+        for n in seq:
+            g.step(n)
+            out.append((g.get_populations(), g.get_markers()["X"]))
+        res.append(out)
+    tol = 1e-13 if storage == "f64" else 1e-6
+    for (a, Xa), (b, Xb) in zip(*res):
+        assert np.abs(a - b).max() <= tol * np.abs(a).max() and np.abs(a).max() > 0
+        assert np.abs(Xa - Xb).max() <= (1e-12 if storage == "f64" else 1e-6)
+
+
+def test_graph_replay_of_direct_forcing(orc):
+    """A directly forced cylinder in a channel replays from graphs too (every captured
+    step begins with its force iteration and interface phase), including after a
+    read-out that ran that phase early (the next step then runs eagerly): graph and
+    eager runs agree with each other and with the FP64 oracle."""
+    nx, ny, n = 160, 64, 50
+    s = W.mrt_rates(0.7)
+    X = W.circle_markers(48.0, 32.5, 8.0, n)
+    dX = W.polygon_perimeter(X) / n
+    y = np.arange(ny) + 0.5
+    u0 = np.repeat((4 * 0.05 * y * (ny - y) / ny ** 2)[:, None], nx, axis=1)
+    o = orc.Oracle(nx, ny, collision=orc.MRT, tau=0.7, s=s, bc=orc.BC_CHANNEL, u_max=0.05)
+    o.init_equilibrium(None, u0, None)
+    o.set_interface(X, model=orc.DIRECT, moves=False, dX=dX, eta=2.0, mdf_iters=5,
+                    UD=np.zeros((n, 2)))
+    seq = (3, 1, "read", 20, 2, 5)
+    outs = []
+    for graph in (1, 0):
+        g = iilbm.Lattice(nx, ny, collision=iilbm.MRT, storage="f64", tau=0.7, s=s,
+                          bc=iilbm.BC_CHANNEL, u_max=0.05)
+        g.set_option(iilbm.OPT_CUDA_GRAPH, graph)
+        g.init_equilibrium(None, u0, None)
+        g.set_interface(X, model=iilbm.DIRECT, moves=False, dX=dX, eta=2.0, mdf_iters=5,
+                        aux=np.zeros((n, 2)))
+        for a in seq:
+            if a == "read":
+                g.get_macros()
+            else:
+                g.step(a)
+        outs.append((g.get_populations(), g.get_markers()["G"]))
+    o.step(sum(a for a in seq if a != "read"))
+    assert np.abs(outs[0][0] - outs[1][0]).max() < 1e-14
+    assert np.abs(outs[0][1] - outs[1][1]).max() < 1e-13
+    assert np.abs(outs[0][0] - o.get_df()).max() < 1e-14
+    assert np.abs(outs[0][1] - o.markers()["G"]).max() < 1e-12
+
+
+def test_same_size_interface_replacement(orc):
+    """A new polygon with the same marker count and parameters reuses the marker buffers
+    and the captured graphs: the run still follows the FP64 oracle given the same
+    replacement."""
+    g, o = make_pair(orc, 96, 96, collision="mrt", storage="f64", tau=0.7)
+    X = W.circle_markers(47.6, 48.3, 15.0, 96)
+    dX = W.polygon_perimeter(X) / 96 * 0.9
+    set_membrane(orc, g, o, X, "spring", 0.02, dX)
+    g.step(10)
+    o.step(10)
+    X2 = X * np.array([1.05, 0.96]) + np.array([-2.13, 1.71])
+    set_membrane(orc, g, o, X2, "spring", 0.02, dX)
+    g.step(15)
+    o.step(15)
+    assert np.abs(g.get_populations() - o.get_df()).max() < 1e-14
+    assert np.abs(g.get_markers()["X"] - o.markers()["X"]).max() < 1e-12
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+def test_nonfinite_population_is_reported(graph):
+    """A NaN planted from the host in one population (iilbm_set_populations) is caught by
+    the stream-collide's finiteness check and latched: the next synchronising call
+    returns IILBM_ERR_NONFINITE.  No interface, so no index depends on the NaN."""
+    g = iilbm.Lattice(64, 32, collision=iilbm.MRT, storage="f32", tau=0.8,
+                      s=W.mrt_rates(0.8))
+    g.set_option(iilbm.OPT_CUDA_GRAPH, graph)
+    df = W.random_df(64, 32, 1e-4, 1)
+    g.set_populations(df)
+    g.step(3)
+    g.synchronize()  # a finite state passes
+    df[4, 10, 17] = np.nan
+    g.set_populations(df)
+    g.step(3)
+    with pytest.raises(iilbm.IilbmError) as e:
+        g.synchronize()
+    assert e.value.code == iilbm.ERR_NONFINITE

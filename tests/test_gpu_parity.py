@@ -12,7 +12,7 @@ import pytest
 from paper_2003_12186_gb300 import iilbm
 from paper_2003_12186_gb300 import workloads as W
 
-from _pair import make_pair, set_membrane, vel_error
+from _pair import assert_jump_fields_agree, oracle_jump_field, make_pair, set_membrane, vel_error
 
 pytestmark = pytest.mark.gpu
 
@@ -219,21 +219,52 @@ def test_invalid_interface_is_rejected(orc):
         g2.set_interface(Xl, model=iilbm.SPRING, stiffness=0.1, dX=1.0)
 
 
-def test_ellipse2048_fp32_full_size_sampled(orc):
-    """The full 2048^2 MRT ellipse membrane in FP32, as the benchmark launches it:
-    10 steps against the oracle (whole field compared)."""
+def test_ellipse2048_fp32_full_size(orc):
+    """The full 2048^2 MRT ellipse membrane in FP32, as the benchmark launches it (graph
+    replay): 200 steps against the oracle (its OpenMP build on every host core, which
+    computes exactly what the serial one does), the whole velocity field within 1e-5,
+    the markers, and the cut-link set of the final state exactly."""
     w = W.ellipse_2048("f32")
-    g, o = make_pair(orc, 2048, 2048, collision="mrt", storage="f32", tau=w["tau"])
+    try:
+        orc.lib(parallel=True)
+        par, steps = True, 200
+    except RuntimeError:  # no OpenMP runtime: a shorter run on one core
+        par, steps = False, 30
+    g = iilbm.Lattice(2048, 2048, collision=iilbm.MRT, storage="f32", tau=w["tau"],
+                      s=W.mrt_rates(w["tau"]))
+    o = orc.Oracle(2048, 2048, parallel=par, collision=orc.MRT, tau=w["tau"],
+                   s=W.mrt_rates(w["tau"]))
     set_membrane(orc, g, o, w["X"], "spring", w["kappa"], w["dX"])
-    g.step(10)
-    o.step(10)
-    umax = np.abs(o.markers()["U"]).max()
+    umax = 0.0
+    for _ in range(steps // 50 if par else 1):
+        g.step(50 if par else steps)
+        o.step(50 if par else steps)
+        umax = max(umax, np.abs(o.markers()["U"]).max())
     err = vel_error(g, o, max(umax, 1e-6))
-    assert g.iilbm_get_cut_link_count() == o.cut_link_count()
     mg, mo = g.get_markers(), o.markers()
-    assert np.abs(mg["X"] - mo["X"]).max() < 1e-9
-    print(f"ellipse2048 f32 10 steps: rel vel err {err:.3e}")
+    assert np.abs(mg["X"] - mo["X"]).max() < 1e-8
+    Jo, count = oracle_jump_field(orc, o)
+    assert_jump_fields_agree(g.iilbm_get_jump(), Jo, 2e-6)
+    assert g.iilbm_get_cut_link_count() == count == o.cut_link_count()
+    print(f"ellipse2048 f32 {steps} steps: rel vel err {err:.3e}, {count} cut links")
     assert err < 1e-5
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_jump_field_matches_oracle(orc, storage):
+    """The jump the interface phase adds (Eq. 47 with Eq. 32) for a moving membrane, at
+    the start and after 40 steps: the same cut links as the oracle's records (set
+    compared exactly) with the same values (FP64 to 1e-14 of the largest; FP32, whose
+    crossing parameter is an FP32 quotient, to 2e-6)."""
+    w = W.ellipse_scaled(256, storage)
+    g, o = make_pair(orc, 256, 256, collision="mrt", storage=storage, tau=w["tau"])
+    set_membrane(orc, g, o, w["X"], "spring", w["kappa"], w["dX"])
+    rel = 1e-14 if storage == "f64" else 2e-6
+    for steps in (0, 40):
+        g.step(steps)
+        o.step(steps)
+        Jo, _ = oracle_jump_field(orc, o)
+        assert_jump_fields_agree(g.iilbm_get_jump(), Jo, rel)
 
 
 def test_precision_report(orc):

@@ -189,3 +189,44 @@ def test_channel_inflow_sets_the_prescribed_velocity(orc):
     assert np.abs(ux[:, 0] - uin).max() < 1e-15
     assert np.abs(uy[:, 0]).max() < 1e-16
     assert np.abs(r[:, 0] - r[:, 1]).max() < 1e-15
+
+
+def test_channel_outflow_copies_exactly_the_unknown_populations(orc):
+    """Zero-gradient outflow pinned by a one-step computation from the (separately pinned)
+    collision.  From a random state, one step of an empty channel must give:
+    (1) at column nx - 1, the populations with e_x < 0 (the ones no node streams in)
+        equal to those of column nx - 2, bitwise;
+    (2) every other population of column nx - 1 equal to the post-collision value of its
+        source node x - e_i (the node's own opposite population where the source lies
+        beyond a wall: halfway bounce-back), computed here cell by cell;
+    (3) the e_x < 0 populations of column nx - 2 likewise streamed in from column
+        nx - 1, not copied.
+    A copy of the wrong set (e_x > 0), from the wrong column, or onto the wrong column
+    fails one of the three."""
+    nx, ny, tau = 12, 9, 0.8
+    o = orc.Oracle(nx, ny, collision=orc.MRT, tau=tau, s=W.mrt_rates(tau), bc=orc.BC_CHANNEL,
+                   u_max=0.03)
+    df = W.random_df(nx, ny, 1e-3, 5)
+    o.set_df(df)
+    post = np.array([[orc.collide_cell(o.cfg, df[:, y, x]) for x in range(nx)]
+                     for y in range(ny)])  # [ny][nx][9]
+    o.step(1)
+    d = o.get_df()
+    EX = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+    EY = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+    OPP = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+
+    def streamed(i, x, y):
+        sx, sy = x - EX[i], y - EY[i]
+        return post[y, x, OPP[i]] if not 0 <= sy < ny else post[sy, sx, i]
+
+    for y in range(ny):
+        for i in range(9):
+            if EX[i] < 0:
+                assert d[i, y, nx - 1] == d[i, y, nx - 2]                  # (1)
+                assert d[i, y, nx - 2] == streamed(i, nx - 2, y)           # (3)
+            else:
+                assert d[i, y, nx - 1] == streamed(i, nx - 1, y)           # (2)
+    # the copy is not vacuous: the two columns' unknown populations differ before it
+    assert any(streamed(i, nx - 1 - 1, y) != post[y, nx - 1, i]
+               for y in range(ny) for i in (3, 6, 7))

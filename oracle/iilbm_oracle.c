@@ -596,22 +596,59 @@ int orc_set_interface(orc_state *S, const double *X, int n, int model, int moves
   return 0;
 }
 
+/* The forcing of the step for a Lagrangian force G on the markers X (section 3.2):
+ * f = dfs plus, in II-LBM, the jump of the normal part on every cut link of the polygon
+ * (Eq. 47 with Eq. 32), and g = body + the spread of the tangential part (Eq. 46); in
+ * IB-LBM f = dfs and g = body + the spread of the whole G (Eq. 17).  Fn and Gpar
+ * receive the split of Eqs. 31-32 / 46.  Returns the number of cut-link crossings, or
+ * -1 if the record capacity is exceeded. */
+static int apply_forcing(const orc_cfg *c, const orc_iface *I, const double *G,
+                         const double *dfs, double *f, double *gx, double *gy, double *Fn,
+                         double *Gpar) {
+  int N = c->nx * c->ny, n = I->n, m = 0;
+  memcpy(f, dfs, 9 * (size_t)N * sizeof(double));
+  for (int p = 0; p < N; p++) { gx[p] = c->body_x; gy[p] = c->body_y; }
+  orc_normal_split(I, G, Fn, Gpar, NULL);
+  double *P = (double *)malloc(2 * n * sizeof(double));
+  if (c->jump) {
+    int cap = 64 * n + 64;
+    int *cell = (int *)malloc(cap * sizeof(int)), *dir = (int *)malloc(cap * sizeof(int));
+    double *coef = (double *)malloc(cap * sizeof(double));
+    m = orc_cut_links(c, I->X, n, Fn, cell, dir, coef, cap);
+    for (int r = 0; r < m; r++) f[dir[r] * N + cell[r]] += coef[r];
+    free(cell); free(dir); free(coef);
+    for (int k = 0; k < 2 * n; k++) P[k] = Gpar[k] * I->dX;
+  } else {
+    for (int k = 0; k < 2 * n; k++) P[k] = G[k] * I->dX;
+  }
+  if (m >= 0) orc_spread(c, I->X, n, P, gx, gy);
+  free(P);
+  return m;
+}
+
 /* Direct forcing with repeated correction, Eq. 18 (reading: multi-direct forcing,
- * Guo half-force velocity).  u* = (sum e df + body/2)/rho is the velocity without
- * immersed-boundary forcing; each pass interpolates u* + spread(G dX)/(2 rho),
- * adds eta (U^D - U) to G, and stops after mdf_iters passes or when
- * max_k |U^D - U_k| < mdf_tol.  The pass count and final residual are kept, and
- * so is U* = interp(u*) (the pass with G = 0).  The iteration starts from Gp, or
- * with ws_previous from the force the previous call ended with. */
-static void direct_forcing(orc_state *S, const double *dfs) {
+ * Guo half-force velocity).  u* = (sum e df + body/2)/rho is the velocity without the
+ * body's forcing, and U* = interp(u*) is kept.  A pass applies the step's forcing of
+ * the current G (apply_forcing: in II-LBM the normal part through the jump, the
+ * tangential part spread), interpolates the velocity the collision will then use
+ * (Eq. 24 from f and g, Eq. 20), and adds eta (U^D - U) to G; the iteration stops
+ * after mdf_iters passes or when max_k |U^D - U_k| < mdf_tol.  The passes thus see G
+ * through the operator the step applies it with.  (Spreading the whole G in the passes
+ * and then moving its normal part into the jump applies the normal part through an
+ * operator the iteration never saw: the jump moves the velocity at the markers about
+ * twice as much as the half-force spread, and the channel at Re 100 diverges.)  The
+ * pass count and final residual are kept.  The iteration starts from Gp, or with
+ * ws_previous from the force the previous call ended with. */
+static int direct_forcing(orc_state *S, const double *dfs) {
   const orc_cfg *c = &S->c;
   orc_iface *I = &S->I;
   int N = c->nx * c->ny, n = I->n;
   double *us_x = (double *)calloc(N, sizeof(double)), *us_y = (double *)calloc(N, sizeof(double));
   double *r = (double *)calloc(N, sizeof(double)); /* drho */
+  double *f = (double *)malloc(9 * (size_t)N * sizeof(double));
   double *gx = (double *)calloc(N, sizeof(double)), *gy = (double *)calloc(N, sizeof(double));
   double *vx = (double *)calloc(N, sizeof(double)), *vy = (double *)calloc(N, sizeof(double));
-  double *P = (double *)calloc(2 * n, sizeof(double));
+  double *Fn = (double *)calloc(n, sizeof(double)), *Gpar = (double *)calloc(2 * n, sizeof(double));
   #pragma omp parallel for schedule(static)
   for (int p = 0; p < N; p++) {
     double dfc[9];
@@ -621,16 +658,15 @@ static void direct_forcing(orc_state *S, const double *dfs) {
   orc_interp(c, I->X, n, us_x, us_y, S->Ustar);
   const double *G0 = S->ws_previous ? S->Gprev : I->Gp;
   for (int k = 0; k < 2 * n; k++) S->G[k] = G0[k]; /* warm start (0 = plain) */
-  int it = 0;
+  int it = 0, rc = 0;
   double res = 0;
   for (it = 0; it < I->mdf_iters; it++) {
-    memset(gx, 0, N * sizeof(double)); memset(gy, 0, N * sizeof(double));
-    for (int k = 0; k < 2 * n; k++) P[k] = S->G[k] * I->dX;
-    orc_spread(c, I->X, n, P, gx, gy);
+    if (apply_forcing(c, I, S->G, dfs, f, gx, gy, Fn, Gpar) < 0) { rc = -1; break; }
     #pragma omp parallel for schedule(static)
     for (int p = 0; p < N; p++) {
-      vx[p] = us_x[p] + 0.5 * gx[p] / (c->rho0 + r[p]);
-      vy[p] = us_y[p] + 0.5 * gy[p] / (c->rho0 + r[p]);
+      double dfc[9], d;
+      for (int i = 0; i < 9; i++) dfc[i] = f[i * N + p];
+      orc_cell_macros(dfc, c->rho0, gx[p], gy[p], &d, &vx[p], &vy[p]);
     }
     orc_interp(c, I->X, n, vx, vy, S->U);
     res = 0;
@@ -641,7 +677,9 @@ static void direct_forcing(orc_state *S, const double *dfs) {
   S->mdf_last_iters = it;
   S->mdf_last_res = res;
   memcpy(S->Gprev, S->G, 2 * n * sizeof(double));
-  free(us_x); free(us_y); free(r); free(gx); free(gy); free(vx); free(vy); free(P);
+  free(us_x); free(us_y); free(r); free(f); free(gx); free(gy); free(vx); free(vy);
+  free(Fn); free(Gpar);
+  return rc;
 }
 
 /* One II-LBM time step, t -> t+1 (section 3.2, Eq. 47, with Eqs. 17-24).
@@ -659,32 +697,19 @@ static void direct_forcing(orc_state *S, const double *dfs) {
 int orc_prepare(orc_state *S) {
   const orc_cfg *c = &S->c;
   int N = c->nx * c->ny;
-  memcpy(S->f, S->df, 9 * (size_t)N * sizeof(double));
-  for (int p = 0; p < N; p++) { S->gx[p] = c->body_x; S->gy[p] = c->body_y; }
   S->ncut = 0;
   if (S->has_iface) {
     orc_iface *I = &S->I;
     int n = I->n;
     if (I->model == ORC_SPRING || I->model == ORC_SPRING_REST) orc_spring_forces(I, S->G);
     else if (I->model == ORC_PRESCRIBED) memcpy(S->G, I->Gp, 2 * n * sizeof(double));
-    else direct_forcing(S, S->df);
-    orc_normal_split(I, S->G, S->Fn, S->Gpar, NULL);
-    double *P = (double *)malloc(2 * n * sizeof(double));
-    if (c->jump) {
-      int cap = 64 * n + 64;
-      int *cell = (int *)malloc(cap * sizeof(int)), *dir = (int *)malloc(cap * sizeof(int));
-      double *coef = (double *)malloc(cap * sizeof(double));
-      int m = orc_cut_links(c, I->X, n, S->Fn, cell, dir, coef, cap);
-      if (m < 0) { free(cell); free(dir); free(coef); free(P); return -1; }
-      for (int r = 0; r < m; r++) S->f[dir[r] * N + cell[r]] += coef[r];
-      S->ncut = m;
-      free(cell); free(dir); free(coef);
-      for (int k = 0; k < 2 * n; k++) P[k] = S->Gpar[k] * I->dX;
-    } else {
-      for (int k = 0; k < 2 * n; k++) P[k] = S->G[k] * I->dX;
-    }
-    orc_spread(c, I->X, n, P, S->gx, S->gy);
-    free(P);
+    else if (direct_forcing(S, S->df)) return -1;
+    int m = apply_forcing(c, I, S->G, S->df, S->f, S->gx, S->gy, S->Fn, S->Gpar);
+    if (m < 0) return -1;
+    S->ncut = m;
+  } else {
+    memcpy(S->f, S->df, 9 * (size_t)N * sizeof(double));
+    for (int p = 0; p < N; p++) { S->gx[p] = c->body_x; S->gy[p] = c->body_y; }
   }
   #pragma omp parallel for schedule(static)
   for (int p = 0; p < N; p++) {

@@ -61,6 +61,7 @@ void free_interface(iilbm_lattice *h) {
   if (h->Xq) cudaFree(h->Xq);
   if (h->Xqp) cudaFree(h->Xqp);
   h->Xq = h->Xqp = nullptr;
+  free_direct_forcing(h);
   h->nm = 0;
 }
 
@@ -306,8 +307,9 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
   // Same marker count and parameters: the marker buffers are reused in place, and the
   // captured step graphs (which hold their addresses and the parameters) stay valid --
   // a new polygon of the same body costs no reallocation and no recapture.
-  const bool keep = n > 0 && n == h->nm && std::memcmp(p, &h->ip, sizeof *p) == 0;
-  const int win0[4] = {h->df_win[0], h->df_win[1], h->df_win[2], h->df_win[3]};
+  // (A directly forced body's band and cut links depend on its polygon: rebuilt.)
+  const bool keep = n > 0 && n == h->nm && std::memcmp(p, &h->ip, sizeof *p) == 0 &&
+                    p->model != IILBM_DIRECT;
   if (!keep) {
     int drc = drain_all(h);
     if (drc) return drc;
@@ -350,7 +352,6 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
   if (!hx) return IILBM_ERR_OOM;
   CK(cudaMemcpy(hx, h->X, b2, cudaMemcpyDeviceToHost));
   bool bad = false;
-  double bx0 = 1e300, bx1 = -1e300, by0 = 1e300, by1 = -1e300;
   for (int k = 0; k < n && !bad; k++) {
     const int kp = (k + 1) % n;
     const double x = hx[2 * k], y = hx[2 * k + 1];
@@ -360,25 +361,23 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
           (dx == 0 && dy == 0);
     if (h->cfg.bc != IILBM_BC_PERIODIC) bad = bad || y < 3.0 || y > h->cfg.ny - 4.0;
     if (h->cfg.bc == IILBM_BC_CHANNEL) bad = bad || x < 3.0 || x > h->cfg.nx - 4.0;
-    bx0 = std::min(bx0, x); bx1 = std::max(bx1, x);
-    by0 = std::min(by0, y); by1 = std::max(by1, y);
-  }
-  std::free(hx);
-  if (!bad && p->model == IILBM_DIRECT) {
-    // the window holds every stencil node [floor(X) - 1, floor(X) + 2] of the fixed body
-    h->df_win[0] = (int)std::floor(bx0) - 1;
-    h->df_win[1] = (int)std::floor(by0) - 1;
-    h->df_win[2] = (int)std::floor(bx1) + 2 - h->df_win[0] + 1;
-    h->df_win[3] = (int)std::floor(by1) + 2 - h->df_win[1] + 1;
-    bad = direct_forcing_smem(h, h->df_win[2], h->df_win[3], n) > 227 * 1024;
-    // the force iteration's window is baked into its captured launches
-    if (keep && std::memcmp(win0, h->df_win, sizeof win0) != 0) drop_graph(h);
   }
   if (bad) {
+    std::free(hx);
     drop_graph(h);
     free_interface(h);
     return IILBM_ERR_INTERFACE;
   }
+  if (p->model == IILBM_DIRECT) {
+    // the band of nodes the force iteration touches and the body's cut links
+    rc = setup_direct_forcing(h, hx);
+    if (rc) {
+      std::free(hx);
+      free_interface(h);
+      return rc;
+    }
+  }
+  std::free(hx);
   return IILBM_OK;
 }
 
@@ -756,7 +755,7 @@ int iilbm_set_warm_start_mlp(iilbm_t h, iilbm_mlp_t mlp, double re) {
     return IILBM_ERR_INVALID_ARG;
   const int prev = h->ws_mode;
   h->ws_mode = WS_MLP;
-  if (direct_forcing_smem(h, h->df_win[2], h->df_win[3], h->nm) > 227 * 1024) {
+  if (direct_forcing_smem(h, h->df_nb, h->nm) > 227 * 1024) {
     h->ws_mode = prev;
     return IILBM_ERR_CAPACITY;
   }

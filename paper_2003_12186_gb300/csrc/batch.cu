@@ -571,7 +571,7 @@ int iilbm_create_batch(iilbm_batch_t *out, const iilbm_t *lattices, int32_t coun
       d.df = df_args(h);
       const DfArgs &a = d.df;
       B->any_direct = true;
-      B->df_smem = std::max(B->df_smem, direct_forcing_smem(h, a.ww, a.wh, a.n));
+      B->df_smem = std::max(B->df_smem, direct_forcing_smem(h, a.nb, a.n));
     }
     if (h->nm > 0) B->any_iface = true;
     B->max_ny = std::max(B->max_ny, h->geom.ny);

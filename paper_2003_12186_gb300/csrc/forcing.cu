@@ -14,7 +14,10 @@
 // 1/(2 rho) and the spread force live there; G and U stay in FP64.
 #include "forcing_dev.cuh"
 
+#include <algorithm>
 #include <cmath>
+#include <type_traits>
+#include <vector>
 
 namespace iilbm {
 
@@ -25,11 +28,11 @@ __global__ void __launch_bounds__(DF_THREADS)
   direct_forcing_cta<S>(A, geo, odd, a, inv_scale, smem_raw);
 }
 
-// Shared memory of the forcing kernel for a window of ww x wh nodes and n markers.
-size_t direct_forcing_smem(const iilbm_lattice *h, int ww, int wh, int n) {
+// Shared memory of the forcing kernel for a band of nb nodes and n markers.
+size_t direct_forcing_smem(const iilbm_lattice *h, int nb, int n) {
   const bool mlp = h->ws_mode == WS_MLP;
-  return h->cfg.storage == IILBM_F64 ? df_smem_bytes<double>(ww * wh, n, mlp)
-                                     : df_smem_bytes<float>(ww * wh, n, mlp);
+  return h->cfg.storage == IILBM_F64 ? df_smem_bytes<double>(nb, n, mlp)
+                                     : df_smem_bytes<float>(nb, n, mlp);
 }
 
 // The force iteration's arguments for lattice h.
@@ -48,10 +51,12 @@ DfArgs df_args(const iilbm_lattice *h) {
   a.dX = h->ip.dX;
   a.tol = h->ip.mdf_tol;
   a.max_iters = h->ip.mdf_iters;
-  a.wx0 = h->df_win[0];
-  a.wy0 = h->df_win[1];
-  a.ww = h->df_win[2];
-  a.wh = h->df_win[3];
+  a.band = h->df_band;
+  a.nb = h->df_nb;
+  a.st = h->df_st;
+  a.links = (const DfLink *)h->df_links;
+  a.nl = h->df_nl;
+  a.jump = h->cfg.jump;
   a.bodyx = h->cfg.body[0];
   a.bodyy = h->cfg.body[1];
   a.rho0 = h->cfg.rho0;
@@ -62,10 +67,158 @@ DfArgs df_args(const iilbm_lattice *h) {
   return a;
 }
 
+// Cut-link records of a fixed body, one warp per segment.
+template <typename T, int BC>
+__global__ void __launch_bounds__(128)
+    k_df_links(const double *__restrict__ X, int n, GeomC<BC> geo, const int *__restrict__ band,
+               int nb, DfLink *links, int *counters, int cap) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (k >= n) return;  // uniform per warp
+  df_segment_links<T>(X, n, k, threadIdx.x & 31, geo, band, nb, links, counters, cap,
+                      counters + 1);
+}
+
+namespace {
+
+// floor / ceil of a coordinate snapped to 2^-24 (as the kernels take them)
+long long snap(double v) { return std::llrint(v * QSCALE); }
+int qfloor_h(long long v) { return (int)(v >> 24); }
+int qceil_h(long long v) { return (int)-((-v) >> 24); }
+
+// Key y * nx + x of node (x, y) wrapped onto the lattice, or -1 off a non-periodic edge.
+int node_key(const Geom &g, int x, int y) {
+  if (g.bc == IILBM_BC_CHANNEL) {
+    if (x < 0 || x >= g.nx) return -1;
+  } else {
+    x = wrap(x, g.nx);
+  }
+  if (g.bc == IILBM_BC_PERIODIC) y = wrap(y, g.ny);
+  else if (y < 0 || y >= g.ny) return -1;
+  return y * g.nx + x;
+}
+
+template <typename F>
+int with_bc(int bc, F &&f) {
+  switch (bc) {
+    case IILBM_BC_PERIODIC: return f(std::integral_constant<int, IILBM_BC_PERIODIC>());
+    case IILBM_BC_WALLS_Y: return f(std::integral_constant<int, IILBM_BC_WALLS_Y>());
+    default: return f(std::integral_constant<int, IILBM_BC_CHANNEL>());
+  }
+}
+
+}  // namespace
+
+void free_direct_forcing(iilbm_lattice *h) {
+  if (h->df_band) cudaFree(h->df_band);
+  if (h->df_st) cudaFree(h->df_st);
+  if (h->df_links) cudaFree(h->df_links);
+  h->df_band = h->df_st = nullptr;
+  h->df_links = nullptr;
+  h->df_nb = h->df_nl = 0;
+}
+
+// Set up the force iteration of the fixed body with markers hx (host copy of X): the
+// band (every node of a marker stencil and every candidate destination of a cut link,
+// sorted, unique), each stencil node's band index, and the cut-link records.  Returns
+// INTERFACE if the iteration's shared memory would exceed 227 KB.
+int setup_direct_forcing(iilbm_lattice *h, const double *hx) {
+  free_direct_forcing(h);
+  const Geom &g = h->geom;
+  const int n = h->nm;
+  std::vector<int> keys;
+  keys.reserve(16 * (size_t)n * 2);
+  for (int k = 0; k < n; k++) {
+    const int bx = (int)std::floor(hx[2 * k]) - 1, by = (int)std::floor(hx[2 * k + 1]) - 1;
+    for (int l = 0; l < 16; l++) {
+      const int key = node_key(g, bx + (l & 3), by + (l >> 2));
+      if (key >= 0) keys.push_back(key);
+    }
+  }
+  long long cap = 0;
+  if (h->cfg.jump) {
+    for (int k = 0; k < n; k++) {
+      const int kp = (k + 1) % n;
+      const long long ax = snap(hx[2 * k]), ay = snap(hx[2 * k + 1]);
+      const long long bx = snap(hx[2 * kp]), by = snap(hx[2 * kp + 1]);
+      // the destinations the crossing enumeration considers, widened by one node
+      const int x0 = qceil_h(std::min(ax, bx)) - 2, x1 = qceil_h(std::max(ax, bx)) + 1;
+      const int y0 = qceil_h(std::min(ay, by)) - 2, y1 = qceil_h(std::max(ay, by)) + 1;
+      cap += 8LL * (x1 - x0 - 1) * (y1 - y0 - 1);
+      for (int y = y0; y <= y1; y++)
+        for (int x = x0; x <= x1; x++) {
+          const int key = node_key(g, x, y);
+          if (key >= 0) keys.push_back(key);
+        }
+    }
+  }
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  const int nb = (int)keys.size();
+  if (direct_forcing_smem(h, nb, n) > 227 * 1024) return IILBM_ERR_INTERFACE;
+  std::vector<int> st(16 * (size_t)n);
+  for (int k = 0; k < n; k++) {
+    const int bx = (int)std::floor(hx[2 * k]) - 1, by = (int)std::floor(hx[2 * k + 1]) - 1;
+    for (int l = 0; l < 16; l++) {
+      const int key = node_key(g, bx + (l & 3), by + (l >> 2));
+      st[16 * k + l] =
+          key < 0 ? -1 : (int)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin());
+    }
+  }
+  const int icap = (int)std::max(1LL, cap);
+  int *counters = nullptr;
+  bool ok = cudaMalloc(&h->df_band, std::max<size_t>(1, keys.size()) * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->df_st, st.size() * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->df_links, (size_t)icap * sizeof(DfLink)) == cudaSuccess &&
+            cudaMalloc(&counters, 2 * sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (counters) cudaFree(counters);
+    free_direct_forcing(h);
+    return IILBM_ERR_OOM;
+  }
+  h->df_nb = nb;
+  int rc = IILBM_OK;
+  if (cudaMemcpy(h->df_band, keys.data(), keys.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->df_st, st.data(), st.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(counters, 0, 2 * sizeof(int)) != cudaSuccess)
+    rc = IILBM_ERR_CUDA;
+  int cnt[2] = {0, 0};
+  if (!rc && h->cfg.jump) {
+    rc = with_bc(g.bc, [&](auto bcc) {
+      constexpr int BC = decltype(bcc)::value;
+      const int blocks = (n + 3) / 4;
+      if (h->cfg.storage == IILBM_F64)
+        k_df_links<double, BC><<<blocks, 128, 0, h->stream>>>(h->X, n, GeomC<BC>(g), h->df_band,
+                                                              nb, (DfLink *)h->df_links, counters,
+                                                              icap);
+      else
+        k_df_links<float, BC><<<blocks, 128, 0, h->stream>>>(h->X, n, GeomC<BC>(g), h->df_band,
+                                                             nb, (DfLink *)h->df_links, counters,
+                                                             icap);
+      return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
+    });
+    if (!rc && (cudaMemcpyAsync(cnt, counters, sizeof cnt, cudaMemcpyDeviceToHost, h->stream) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(h->stream) != cudaSuccess))
+      rc = IILBM_ERR_CUDA;
+    // every destination lies in the band and the capacity bounds the candidates: either
+    // failing is a defect, reported rather than run with a partial list
+    if (!rc && (cnt[1] != 0 || cnt[0] > icap)) rc = IILBM_ERR_CAPACITY;
+  }
+  cudaFree(counters);
+  if (rc) {
+    cudaGetLastError();
+    free_direct_forcing(h);
+    return rc;
+  }
+  h->df_nl = cnt[0];
+  return IILBM_OK;
+}
+
 int launch_direct_forcing(iilbm_lattice *h) {
   const bool odd = h->step & 1;
   const DfArgs a = df_args(h);
-  const size_t smem = direct_forcing_smem(h, a.ww, a.wh, a.n);
+  const size_t smem = direct_forcing_smem(h, a.nb, a.n);
   const double is = std::ldexp(1.0, -h->cfg.storage_scale_log2);
   cudaError_t e = cudaSuccess;
   switch (h->cfg.storage) {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "iilbm_internal.cuh"
+#include "interface_dev.cuh"
 #include "mlp_dev.cuh"
 
 #include <cmath>
@@ -11,6 +12,16 @@ namespace iilbm {
 
 // Where the force iteration starts (G^(0)).
 enum { WS_GIVEN = 0, WS_PREVIOUS = 1, WS_MLP = 2 };
+
+// A cut link of a fixed body's polygon: the link x - e_i -> x crosses segment
+// k -> k+1 at parameter t (in the arithmetic type's precision, as the interface phase
+// computes it) with sign s; its destination x is band node b.  The body does not move,
+// so the records are found once, when the interface is set.
+struct DfLink {
+  double t;
+  int b, k;
+  int i, s;
+};
 
 struct DfArgs {
   const double *X, *UD, *G0;
@@ -21,7 +32,15 @@ struct DfArgs {
   int n;
   double eta, dX, tol;
   int max_iters;
-  int wx0, wy0, ww, wh;  // window origin and size (lattice nodes)
+  // the band: every node a marker stencil or a cut link touches, as sorted keys
+  // y * nx + x; st[16 k + l] is the band index of stencil node l of marker k (-1 off
+  // the lattice); links[nl] the cut links (nl = 0 in IB-LBM)
+  const int *band;
+  int nb;
+  const int *st;
+  const DfLink *links;
+  int nl;
+  int jump;               // II-LBM: the normal part acts through the jump
   double bodyx, bodyy, rho0;
   int ws_mode;            // WS_GIVEN: G0; WS_PREVIOUS: the G of the last iteration (in G);
                           // WS_MLP: the network's proposal from the step's features
@@ -33,18 +52,18 @@ struct DfArgs {
 
 constexpr int DF_THREADS = 1024;
 
-// Shared memory of the force iteration: the window fields u*, 1/(2 rho) and two force
-// fields g (7 W values of T), the stencil of every marker (16 n weights T and window indices), and the marker
-// arrays G, U, U^D, G dX and U* (2 n values of T each).
-// With the network's proposal (mlp), the per-marker feature blocks and two activation
-// buffers (6 + 2 x 64 floats per marker) follow.
+// Shared memory of the force iteration on a band of nb nodes with n markers: per band
+// node rho*, j* (3 values) and three correction sets (density, momentum: 3 values
+// each), the stencil of every marker (16 n weights and band indices), and the marker
+// arrays G, U, U^D, G of the pass start, U*, normals (2 n values each) and Fn (n).
+// With the network's proposal (mlp), the per-marker feature blocks, two activation
+// buffers and the transposed hidden-layer weights follow.
 template <typename T>
-__host__ __device__ inline size_t df_smem_bytes(int W, int n, bool mlp = false) {
-  // u*, 1/(2 rho) and the force fields: three (x, y) fields in FP32, two in FP64
-  size_t b = (sizeof(T) == 4 ? 9 : 7) * (size_t)W * sizeof(T);
+__host__ __device__ inline size_t df_smem_bytes(int nb, int n, bool mlp = false) {
+  size_t b = 12 * (size_t)nb * sizeof(T);
   b += 16 * (size_t)n * (sizeof(T) + sizeof(int));
   b = (b + 15) & ~(size_t)15;
-  b += 10 * (size_t)n * sizeof(T);
+  b += 13 * (size_t)n * sizeof(T);
   b = (b + 15) & ~(size_t)15;
   if (mlp) b += ((size_t)n * (MLP_BLOCK + 2 * MLP_H) + (MLP_IN + 2 * MLP_H) * MLP_H) * sizeof(float);
   return b + 16;
@@ -64,42 +83,64 @@ template <> struct BitsOf<double> {
   __device__ static double val(U b) { return __longlong_as_double((long long)b); }
 };
 
+// The jump of one cut link for the jump strengths FnA, FnB at the segment's ends (the
+// interface phase's arithmetic, segment_links).
+template <typename T>
+__device__ __forceinline__ T df_link_coef(const DfLink &L, T FnA, T FnB) {
+  if (sizeof(T) == 8)
+    return T((double)L.s * 3.0 * wt<double>(L.i) * ((1.0 - L.t) * (double)FnA + L.t * (double)FnB));
+  const float t = (float)L.t;
+  return T((float)L.s * 3.0f * wt<float>(L.i) * ((1.0f - t) * (float)FnA + t * (float)FnB));
+}
+
 // The whole force iteration of one body by one CTA of DF_THREADS threads; smem_raw is
-// the CTA's dynamic shared memory (df_smem_bytes<T>(ww * wh, n)).
+// the CTA's dynamic shared memory (df_smem_bytes<T>(nb, n)).
 //
-// The markers do not move within the iteration, so each marker's 4 x 4 stencil
-// (window indices and weights phi(x - X) phi(y - Y), from the FP64 position) is formed
-// once; a pass is then the spread (Eq. 17) of G dX, the interpolation (Eq. 20) of
-// u* + g / (2 rho), the residual max_k |U^D - U_k| and the update G += eta (U^D - U)
-// (Eq. 18), all in the arithmetic type T (FP64 for FP64 storage; FP32 otherwise, where
-// GB300's FP64 pipe would cost a whole warp's time even for the few lanes that hold a
-// marker).  U* (the interpolation with G = 0) is recorded for the learned warm start.
+// The iteration (Eq. 18 repeated) sees G through the operator the step applies it
+// with: a pass forms the step's forcing of the current G -- in II-LBM the jump of its
+// normal part Fn_k = G_k . n_k on the cut links (Eq. 47 with Eq. 32), which changes the
+// density and momentum of the links' destinations, and the spread of its tangential
+// part (Eq. 46); in IB-LBM the spread of the whole G (Eq. 17) -- and interpolates the
+// velocity the collision will then use, u = (j* + dj + g/2) / (rho* + drho) (Eqs. 24,
+// 20), with j* = sum_i e_i f~_i + body/2 and rho* from the streamed state f~.  Then
+// G += eta (U^D - U).
+//
+// The markers do not move, so each marker's 4 x 4 stencil (band indices and weights
+// phi(x - X) phi(y - Y), from the FP64 position) is formed once per call.  Everything
+// runs in the arithmetic type T (FP64 for FP64 storage; FP32 otherwise, where GB300's
+// FP64 pipe would cost a whole warp's time even for the few lanes that hold a marker).
+// A pass: the 16 lanes of a marker interpolate from the current correction set; after
+// the xor butterfly each holds the same U_k, so they update G_k and spread its new
+// (tangential) part into the next set at once, and the marker's first lane records U_k,
+// the residual |U^D - U_k| and the new Fn_k; the set after next is cleared meanwhile.
+// Barrier; a pass whose residual (taken before its update) is below the tolerance puts
+// the G it started from back and ends the iteration (the result of checking before
+// updating); otherwise the cut links add the new jump to the next set, and a second
+// barrier (none without cut links) completes it.  U* (the interpolation with G = 0)
+// is recorded for the learned warm start.
 template <typename S>
 __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, const Geom &geo,
                                                    bool odd, const DfArgs &a, double inv_scale,
                                                    unsigned char *smem_raw) {
   using T = typename Store<S>::T;
   using B = typename BitsOf<T>::U;
-  const int W = a.ww * a.wh, n = a.n;
-  T *usx = reinterpret_cast<T *>(smem_raw);
-  T *usy = usx + W;
-  T *h2r = usy + W;  // 1 / (2 rho)
-  T *gx = h2r + W;  // force field of the even passes (FP32: of passes 0, 3, 6, ...)
-  T *gy = gx + W;
-  T *gx2 = gy + W;  // force field of the odd passes (FP32: of passes 1, 4, 7, ...)
-  T *gy2 = gx2 + W;
-  T *gx3 = gy2 + W;  // FP32 only: the third field (passes 2, 5, 8, ...)
-  T *gy3 = gx3 + W;
-  T *pw = sizeof(T) == 4 ? gy3 + W : gy2 + W;       // stencil weights [16 n]
-  int *pc = reinterpret_cast<int *>(pw + 16 * n);   // stencil window indices [16 n]
+  const int NB = a.nb, n = a.n;
+  T *rs = reinterpret_cast<T *>(smem_raw);  // rho* = rho0 + drho*
+  T *jsx = rs + NB;                         // j* (with body / 2)
+  T *jsy = jsx + NB;
+  T *cset = jsy + NB;  // three correction sets of 3 NB values: drho, djx + gx/2, djy + gy/2
+  T *pw = cset + 9 * NB;                            // stencil weights [16 n]
+  int *pc = reinterpret_cast<int *>(pw + 16 * n);   // stencil band indices [16 n]
   size_t off = (size_t)(reinterpret_cast<unsigned char *>(pc + 16 * n) - smem_raw);
   off = (off + 15) & ~(size_t)15;
   T *Gk = reinterpret_cast<T *>(smem_raw + off);    // [2 n] each
   T *Uk = Gk + 2 * n;
   T *UDk = Uk + 2 * n;
-  T *GdX = UDk + 2 * n;                             // G dX, what the spread moves
-  T *Us = GdX + 2 * n;                              // U*
-  size_t off2 = (size_t)(reinterpret_cast<unsigned char *>(Us + 2 * n) - smem_raw);
+  T *Gp = UDk + 2 * n;                              // G at the start of the pass
+  T *Us = Gp + 2 * n;                               // U*
+  T *nrm = Us + 2 * n;                              // outward unit normals
+  T *Fnk = nrm + 2 * n;                             // [n] jump strengths of the new G
+  size_t off2 = (size_t)(reinterpret_cast<unsigned char *>(Fnk + n) - smem_raw);
   off2 = (off2 + 15) & ~(size_t)15;
   // WS_MLP scratch: the transposed weights first (16-byte aligned for 16-byte loads),
   // then the per-marker feature blocks and two activation buffers
@@ -123,38 +164,21 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   __syncthreads();
   const T is = cst[0], rho0 = cst[1], bodyx = cst[2], bodyy = cst[3], eta = cst[4], dX = cst[5];
 
-  // u*, 1/(2 rho) on the window (zero outside the lattice: no stencil node lies there)
-  for (int c = tid; c < W; c += DF_THREADS) {
-    const int x = a.wx0 + c % a.ww, y = a.wy0 + c / a.ww;
-    T ux = T(0), uy = T(0), hr = T(0);
-    const bool in = geo.bc == IILBM_BC_PERIODIC
-                        ? true
-                        : (y >= 0 && y < geo.ny && (geo.bc != IILBM_BC_CHANNEL || (x >= 0 && x < geo.nx)));
-    if (in) {
-      const int xi = geo.bc == IILBM_BC_CHANNEL ? x : wrap(x, geo.nx);
-      const int yi = geo.bc == IILBM_BC_PERIODIC ? wrap(y, geo.ny) : y;
-      T f[9];
+  // rho*, j* on the band (every band node lies on the lattice); corrections cleared
+  for (int c = tid; c < NB; c += DF_THREADS) {
+    const int key = a.band[c];
+    const int y = key / geo.nx, x = key - y * geo.nx;
+    T f[9];
 #pragma unroll
-      for (int i = 0; i < 9; i++) f[i] = Store<S>::ld(A[aa_loc(geo, odd, i, xi, yi)]) * is;
-      const T d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-      const T rho = rho0 + d;
-      ux = ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]) + T(0.5) * bodyx) / rho;
-      uy = ((f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]) + T(0.5) * bodyy) / rho;
-      hr = T(0.5) / rho;
-    }
-    usx[c] = ux;
-    usy[c] = uy;
-    h2r[c] = hr;
-    gx[c] = T(0);
-    gy[c] = T(0);
-    gx2[c] = T(0);
-    gy2[c] = T(0);
-    if (sizeof(T) == 4) {
-      gx3[c] = T(0);
-      gy3[c] = T(0);
-    }
+    for (int i = 0; i < 9; i++) f[i] = Store<S>::ld(A[aa_loc(geo, odd, i, x, y)]) * is;
+    const T d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    rs[c] = rho0 + d;
+    jsx[c] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]) + T(0.5) * bodyx;
+    jsy[c] = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]) + T(0.5) * bodyy;
+#pragma unroll
+    for (int q = 0; q < 9; q++) cset[q * NB + c] = T(0);
   }
-  // stencils, one thread per marker
+  // stencils, one thread per marker (an entry off the lattice gets weight 0)
   for (int k = tid; k < n; k += DF_THREADS) {
     const double Xk = a.X[2 * k], Yk = a.X[2 * k + 1];
     const int bx = (int)floor(Xk) - 1, by = (int)floor(Yk) - 1;
@@ -166,33 +190,65 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
     }
 #pragma unroll
     for (int l = 0; l < 16; l++) {
-      pw[16 * k + l] = wx[l & 3] * wy[l >> 2];
-      pc[16 * k + l] = (by + (l >> 2) - a.wy0) * a.ww + (bx + (l & 3) - a.wx0);
+      const int b = a.st[16 * k + l];
+      pw[16 * k + l] = b < 0 ? T(0) : wx[l & 3] * wy[l >> 2];
+      pc[16 * k + l] = b < 0 ? 0 : b;
     }
+    // outward normal of the counter-clockwise polygon (as the marker pass forms it)
+    const int kp = k + 1 == n ? 0 : k + 1, km = k == 0 ? n - 1 : k - 1;
+    const T tx = T(a.X[2 * kp] - a.X[2 * km]), ty = T(a.X[2 * kp + 1] - a.X[2 * km + 1]);
+    const T tl = sqrt(tx * tx + ty * ty);
+    nrm[2 * k] = ty / tl;
+    nrm[2 * k + 1] = -tx / tl;
   }
   // marker arrays, one thread per component: the start of the iteration, U^D
   const double *g0 = a.ws_mode == WS_PREVIOUS ? a.G : a.G0;
   for (int k = tid; k < 2 * n; k += DF_THREADS) {
-    if (sizeof(T) == 8) {
-      Gk[k] = T(g0[k]);
-      GdX[k] = T(g0[k] * a.dX);
-    } else {
-      Gk[k] = T(g0[k]);
-      GdX[k] = Gk[k] * dX;
-    }
+    Gk[k] = T(g0[k]);
     UDk[k] = T(a.UD[k]);
   }
   __syncthreads();
 
+  T *cur = cset, *nxt = cset + 3 * NB, *clr = cset + 6 * NB;
   const int npairs = 16 * n;
+  // u at band node c from correction set F
+  auto vel = [&](const T *F, int c, T &ux, T &uy) {
+    const T ir = T(1) / (rs[c] + F[c]);
+    ux = (jsx[c] + F[NB + c]) * ir;
+    uy = (jsy[c] + F[2 * NB + c]) * ir;
+  };
+  // the point force of marker k for force G (the tangential part in II-LBM), times dX/2
+  auto half_point_force = [&](int k, T gx, T gy, T &px, T &py, T &fn) {
+    fn = gx * nrm[2 * k] + gy * nrm[2 * k + 1];  // |X_s| = 1 for a rigid body
+    if (a.jump) {
+      px = (gx - fn * nrm[2 * k]) * dX * T(0.5);
+      py = (gy - fn * nrm[2 * k + 1]) * dX * T(0.5);
+    } else {
+      px = gx * dX * T(0.5);
+      py = gy * dX * T(0.5);
+    }
+  };
+  // cut links of the current jump strengths into set F
+  auto add_links = [&](T *F) {
+    for (int l = tid; l < a.nl; l += DF_THREADS) {
+      const DfLink L = a.links[l];
+      const int kp = L.k + 1 == n ? 0 : L.k + 1;
+      const T c = df_link_coef<T>(L, Fnk[L.k], Fnk[kp]);
+      atomicAdd(&F[L.b], c);
+      if (cx(L.i)) atomicAdd(&F[NB + L.b], T(cx(L.i)) * c);
+      if (cy(L.i)) atomicAdd(&F[2 * NB + L.b], T(cy(L.i)) * c);
+    }
+  };
+
   // U* = interp(u*), 16 consecutive threads per marker
   for (int base = 0; base < npairs; base += DF_THREADS) {
     const int q = base + tid;
     T sx = T(0), sy = T(0);
     if (q < npairs) {
-      const int c = pc[q];
-      sx = usx[c] * pw[q];
-      sy = usy[c] * pw[q];
+      T ux, uy;
+      vel(cur, pc[q], ux, uy);
+      sx = ux * pw[q];
+      sy = uy * pw[q];
     }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) {
@@ -230,187 +286,100 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
     __syncthreads();
     for (int k = tid; k < 2 * n; k += DF_THREADS) {
       const int o = k & 1;
-      const float g = act1[k] * a.mlp_norm[NORM_OUT_SCALE + o] + a.mlp_norm[NORM_OUT_MEAN + o];
-      Gk[k] = T(g);
-      if (sizeof(T) == 8) GdX[k] = T((double)g * a.dX);
-      else GdX[k] = Gk[k] * dX;
-    }
-    __syncthreads();
-  }
-
-  // the start G^(0) spread (Eq. 17) into the field of pass 0
-  for (int q = tid; q < npairs; q += DF_THREADS) {
-    const T w = pw[q];
-    if (w != T(0)) {
-      const int k = q >> 4, c = pc[q];
-      atomicAdd(&gx[c], GdX[2 * k] * w);
-      atomicAdd(&gy[c], GdX[2 * k + 1] * w);
+      Gk[k] = T(act1[k] * a.mlp_norm[NORM_OUT_SCALE + o] + a.mlp_norm[NORM_OUT_MEAN + o]);
     }
   }
   __syncthreads();
+
+  // the forcing of the start G^(0) into the current set: spread, then the cut links
+  for (int q = tid; q < npairs; q += DF_THREADS) {
+    const int k = q >> 4;
+    T px, py, fn;
+    half_point_force(k, Gk[2 * k], Gk[2 * k + 1], px, py, fn);
+    if ((q & 15) == 0) Fnk[k] = fn;
+    const T w = pw[q];
+    if (w != T(0)) {
+      atomicAdd(&cur[NB + pc[q]], px * w);
+      atomicAdd(&cur[2 * NB + pc[q]], py * w);
+    }
+  }
+  __syncthreads();
+  if (a.nl) {
+    add_links(cur);
+    __syncthreads();
+  }
 
   int it = 0;
   B rm = 0;
   // stop once the residual's bit pattern is below the tolerance's (both non-negative)
   const bool stop_on_tol = a.tol > 0.0;
   const B tol_bits = BitsOf<T>::of(T(a.tol));
-  if constexpr (sizeof(T) == 4) {
-    // FP32: one barrier per pass.  The 16 lanes of a marker interpolate u* + g / (2 rho)
-    // (Eq. 20) from the pass's field; after the xor butterfly each holds the same U_k,
-    // so they form G += eta (U^D - U) (Eq. 18) and spread the new G dX into the next
-    // pass's field at once, without waiting for the residual; meanwhile the field of
-    // the pass after next is cleared (three fields in turn).  The barrier then makes the
-    // spread complete and the warps' residual maxima visible; a pass whose residual
-    // (taken before its update) is below the tolerance puts the G it started from
-    // back, so the result is the one of checking before updating.
-    T *Gp = GdX;  // G at the start of the pass, for that roll-back (GdX is free by now)
-    // the fields in turn: read (fx), spread into (ox), cleared (zx)
-    T *fx = gx, *fy = gy, *ox = gx2, *oy = gy2, *zx = gx3, *zy = gy3;
-    for (it = 0; it < a.max_iters; it++) {
-      B r = 0;
-      for (int base = 0; base < npairs; base += DF_THREADS) {
-        const int q = base + tid, k = q >> 4;
-        T sx = T(0), sy = T(0);
-        if (q < npairs) {
-          const int c = pc[q];
-          const T w = pw[q];
-          sx = (usx[c] + fx[c] * h2r[c]) * w;
-          sy = (usy[c] + fy[c] * h2r[c]) * w;
-        }
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-          sx += __shfl_xor_sync(0xffffffffu, sx, o, 16);
-          sy += __shfl_xor_sync(0xffffffffu, sy, o, 16);
-        }
-        T gxo = T(0), gyo = T(0), nx = T(0), ny = T(0);
-        if (q < npairs) {
-          gxo = Gk[2 * k];
-          gyo = Gk[2 * k + 1];
-          nx = gxo + eta * (UDk[2 * k] - sx);
-          ny = gyo + eta * (UDk[2 * k + 1] - sy);
-        }
-        __syncwarp();  // every lane of the marker has read the old G
-        if (q < npairs) {
-          if ((q & 15) == 0) {
-            Uk[2 * k] = sx;
-            Uk[2 * k + 1] = sy;
-            r = max(r, max(BitsOf<T>::of(fabs(UDk[2 * k] - sx)),
-                           BitsOf<T>::of(fabs(UDk[2 * k + 1] - sy))));
-            Gp[2 * k] = gxo;
-            Gp[2 * k + 1] = gyo;
-            Gk[2 * k] = nx;
-            Gk[2 * k + 1] = ny;
-          }
-          const T w = pw[q];
-          if (w != T(0)) {
-            const int c = pc[q];
-            atomicAdd(&ox[c], nx * dX * w);
-            atomicAdd(&oy[c], ny * dX * w);
-          }
-        }
-      }
-      for (int c = tid; c < W; c += DF_THREADS) {
-        zx[c] = T(0);
-        zy[c] = T(0);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) r = max(r, (B)__shfl_xor_sync(0xffffffffu, r, o));
-      if (lane == 0) red[it & 1][tid >> 5] = r;  // two sets: a warp may run a pass ahead
-      __syncthreads();
-      rm = lane < DF_THREADS / 32 ? red[it & 1][lane] : B(0);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) rm = max(rm, (B)__shfl_xor_sync(0xffffffffu, rm, o));
-      if (stop_on_tol && rm < tol_bits) {  // uniform
-        for (int k = tid; k < 2 * n; k += DF_THREADS) Gk[k] = Gp[k];
-        __syncthreads();
-        break;
-      }
-      T *tx = fx, *ty = fy;  // rotate: spread-into -> read, cleared -> spread-into
-      fx = ox;
-      fy = oy;
-      ox = zx;
-      oy = zy;
-      zx = tx;
-      zy = ty;
-    }
-  } else {
-  // FP64: each pass interpolates u* + g / (2 rho) (Eq. 20) from the pass's field and
-  // takes the residual (clearing the other field meanwhile); then, unless converged,
-  // updates G += eta (U^D - U) (Eq. 18) and spreads the new G dX into the other field --
-  // the 16 lanes of a marker form the same update, its first lane stores it.  Two
-  // barriers.
   for (it = 0; it < a.max_iters; it++) {
-    const bool odd_pass = it & 1;
-    const T *fx = odd_pass ? gx2 : gx, *fy = odd_pass ? gy2 : gy;
-    T *ox = odd_pass ? gx : gx2, *oy = odd_pass ? gy : gy2;
     B r = 0;
     for (int base = 0; base < npairs; base += DF_THREADS) {
-      const int q = base + tid;
+      const int q = base + tid, k = q >> 4;
       T sx = T(0), sy = T(0);
       if (q < npairs) {
-        const int c = pc[q];
-        const T w = pw[q];
-        sx = (usx[c] + fx[c] * h2r[c]) * w;
-        sy = (usy[c] + fy[c] * h2r[c]) * w;
+        T ux, uy;
+        vel(cur, pc[q], ux, uy);
+        sx = ux * pw[q];
+        sy = uy * pw[q];
       }
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) {
         sx += __shfl_xor_sync(0xffffffffu, sx, o, 16);
         sy += __shfl_xor_sync(0xffffffffu, sy, o, 16);
       }
-      if (q < npairs && (q & 15) == 0) {
-        const int k = q >> 4;
-        Uk[2 * k] = sx;
-        Uk[2 * k + 1] = sy;
-        r = max(r, max(BitsOf<T>::of(fabs(UDk[2 * k] - sx)),
-                       BitsOf<T>::of(fabs(UDk[2 * k + 1] - sy))));
-      }
-    }
-    for (int c = tid; c < W; c += DF_THREADS) {
-      ox[c] = T(0);
-      oy[c] = T(0);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r = max(r, (B)__shfl_xor_sync(0xffffffffu, r, o));
-    if (lane == 0) red[0][tid >> 5] = r;
-    __syncthreads();
-    // every warp reduces the warp maxima itself
-    rm = lane < DF_THREADS / 32 ? red[0][lane] : B(0);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rm = max(rm, (B)__shfl_xor_sync(0xffffffffu, rm, o));
-    if (stop_on_tol && rm < tol_bits) break;  // uniform
-    for (int base = 0; base < npairs; base += DF_THREADS) {
-      const int q = base + tid;
-      const int k = q >> 4;
-      T nx = T(0), ny = T(0);
+      T gxo = T(0), gyo = T(0), nx = T(0), ny = T(0);
       if (q < npairs) {
-        nx = Gk[2 * k] + eta * (UDk[2 * k] - Uk[2 * k]);
-        ny = Gk[2 * k + 1] + eta * (UDk[2 * k + 1] - Uk[2 * k + 1]);
+        gxo = Gk[2 * k];
+        gyo = Gk[2 * k + 1];
+        nx = gxo + eta * (UDk[2 * k] - sx);
+        ny = gyo + eta * (UDk[2 * k + 1] - sy);
       }
       __syncwarp();  // every lane of the marker has read the old G
       if (q < npairs) {
+        T px, py, fn;
+        half_point_force(k, nx, ny, px, py, fn);
         if ((q & 15) == 0) {
+          Uk[2 * k] = sx;
+          Uk[2 * k + 1] = sy;
+          r = max(r, max(BitsOf<T>::of(fabs(UDk[2 * k] - sx)),
+                         BitsOf<T>::of(fabs(UDk[2 * k + 1] - sy))));
+          Gp[2 * k] = gxo;
+          Gp[2 * k + 1] = gyo;
           Gk[2 * k] = nx;
           Gk[2 * k + 1] = ny;
-        }
-        T px, py;
-        if (sizeof(T) == 8) {
-          px = T((double)nx * a.dX);
-          py = T((double)ny * a.dX);
-        } else {
-          px = nx * dX;
-          py = ny * dX;
+          Fnk[k] = fn;
         }
         const T w = pw[q];
         if (w != T(0)) {
-          const int c = pc[q];
-          atomicAdd(&ox[c], px * w);
-          atomicAdd(&oy[c], py * w);
+          atomicAdd(&nxt[NB + pc[q]], px * w);
+          atomicAdd(&nxt[2 * NB + pc[q]], py * w);
         }
       }
     }
+    for (int c = tid; c < 3 * NB; c += DF_THREADS) clr[c] = T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = max(r, (B)__shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0) red[it & 1][tid >> 5] = r;  // two sets: a warp may run a pass ahead
     __syncthreads();
-  }
+    rm = lane < DF_THREADS / 32 ? red[it & 1][lane] : B(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rm = max(rm, (B)__shfl_xor_sync(0xffffffffu, rm, o));
+    if (stop_on_tol && rm < tol_bits) {  // uniform
+      for (int k = tid; k < 2 * n; k += DF_THREADS) Gk[k] = Gp[k];
+      __syncthreads();
+      break;
+    }
+    if (a.nl) {
+      add_links(nxt);
+      __syncthreads();
+    }
+    T *t0 = cur;  // rotate: next -> current, cleared -> next, current -> to clear
+    cur = nxt;
+    nxt = clr;
+    clr = t0;
   }
   for (int k = tid; k < 2 * n; k += DF_THREADS) {
     a.G[k] = (double)Gk[k];
@@ -421,6 +390,48 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
     *a.iters = it;
     *a.res = (double)BitsOf<T>::val(rm);
   }
+}
+
+// Cut-link records of segment k of a fixed body (one warp): every crossing's band
+// index (binary search of the sorted band keys), direction, sign and parameter,
+// appended to links[] (capacity cap; *count may exceed it, which the host reports).
+template <typename T, typename GG>
+__device__ __forceinline__ void df_segment_links(const double *__restrict__ X, int n, int k,
+                                                 int lane, const GG &geo,
+                                                 const int *__restrict__ band, int nb,
+                                                 DfLink *links, int *count, int cap,
+                                                 int *missing) {
+  const int kp = k + 1 == n ? 0 : k + 1;
+  const long long ax = __double2ll_rn(X[2 * k] * QSCALE), ay = __double2ll_rn(X[2 * k + 1] * QSCALE);
+  const long long bx = __double2ll_rn(X[2 * kp] * QSCALE), by = __double2ll_rn(X[2 * kp + 1] * QSCALE);
+  segment_crossings<T>(ax, ay, bx, by, lane, geo, [&](int i, int dx, int dy, int s1, T t) {
+    const int key = dy * geo.nx + dx;
+    int lo = 0, hi = nb - 1, b = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int v = band[mid];
+      if (v == key) {
+        b = mid;
+        break;
+      }
+      if (v < key) lo = mid + 1;
+      else hi = mid - 1;
+    }
+    if (b < 0) {
+      atomicAdd(missing, 1);
+      return;
+    }
+    const int slot = atomicAdd(count, 1);
+    if (slot < cap) {
+      DfLink L;
+      L.t = (double)t;
+      L.b = b;
+      L.k = k;
+      L.i = i;
+      L.s = s1;
+      links[slot] = L;
+    }
+  });
 }
 
 // Raw (unnormalised) features [n][30] of every marker from the U* of the most recent

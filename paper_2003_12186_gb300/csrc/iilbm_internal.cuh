@@ -209,7 +209,13 @@ struct iilbm_lattice {
   float re;                     // WS_MLP: the Reynolds-number feature
   int *d_mdf_iters;
   double *d_mdf_res;
-  int df_win[4];      // direct forcing window: x0, y0, width, height
+  // direct forcing of a fixed body: the band of nodes its iteration touches (sorted keys
+  // y * nx + x), each stencil node's band index, and the cut-link records (DfLink)
+  int *df_band;
+  int df_nb;
+  int *df_st;
+  void *df_links;
+  int df_nl;
   double *d_res;      // direct forcing residual scratch
   // diagnostics
   bool timing;
@@ -241,7 +247,9 @@ int launch_interp_interface(iilbm_lattice *h, cudaStream_t s);
 int launch_channel_bc(iilbm_lattice *h);
 int launch_direct_forcing(iilbm_lattice *h);
 int launch_df_features(iilbm_lattice *h, float re, float *F);
-size_t direct_forcing_smem(const iilbm_lattice *h, int ww, int wh, int n);
+size_t direct_forcing_smem(const iilbm_lattice *h, int nb, int n);
+int setup_direct_forcing(iilbm_lattice *h, const double *hx);
+void free_direct_forcing(iilbm_lattice *h);
 struct DfArgs;
 DfArgs df_args(const iilbm_lattice *h);
 const float *mlp_params(const struct iilbm_mlp *M);

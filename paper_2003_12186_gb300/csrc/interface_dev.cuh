@@ -241,96 +241,119 @@ __device__ __forceinline__ void interface_marker(const double *__restrict__ X,
 // 64-bit ballot; a candidate link then costs two bit lookups, and only links whose ends
 // straddle the line take the two link-side tests.
 
+// Every lattice link x - e_i -> x that crosses segment A -> B (snapped coordinates),
+// enumerated by the 32 lanes of a warp; each crossing calls emit(i, dx, dy, s, t) with
+// the destination node (dx, dy) wrapped onto the lattice, the sign s (+1 when the link
+// leaves the interior, the left of A -> B) and the crossing parameter t along A -> B in
+// the arithmetic type T (FP64 for FP64 storage: an FP32 quotient refined by one Newton
+// step; FP32 otherwise: |o3|, |o3 - o4| < 2^31 fit the int casts, and converting each to
+// FP32 rounds it with a relative error of at most 2^-24, so t carries a few FP32 ulps).
+// Links whose source or destination lies outside a non-periodic lattice are skipped.
+// Returns this lane's number of crossings.  Every lane of the warp must call this.
+template <typename T, typename GG, typename Emit>
+__device__ __forceinline__ int segment_crossings(long long ax, long long ay, long long bx,
+                                                 long long by, int lane, const GG &geo,
+                                                 Emit &&emit) {
+  const long long Q = (long long)QSCALE;
+  auto qceil = [](long long v) { return (int)-((-v) >> 24); };
+  int found = 0;
+  // destinations x of links that can reach the segment: with the node displaced by
+  // (eps, eps^2) the link x - e_i -> x spans [x - 1 + eps, x + 1 + eps] at most on
+  // each axis, which meets [min, max] only for ceil(min) - 1 <= x <= ceil(max)
+  const int x0 = qceil(min(ax, bx)) - 1, x1 = qceil(max(ax, bx));
+  const int y0 = qceil(min(ay, by)) - 1, y1 = qceil(max(ay, by));
+  const int W = x1 - x0 + 1, H = y1 - y0 + 1;
+  const int ncand = W * H * 8;
+  // node signs on the grid [x0-1, x1+1] x [y0-1, y1+1] (GW x GH nodes)
+  const int GW = W + 2, GH = H + 2;
+  const bool fast = GW * GH <= 64;
+  unsigned lo = 0u, hi = 0u;
+  if (fast) {
+    bool p0 = false, p1 = false;
+    if (lane < GW * GH)
+      p0 = orient_seg_node(ax, ay, bx, by, (long long)(x0 - 1 + lane % GW) * Q,
+                           (long long)(y0 - 1 + lane / GW) * Q) > 0;
+    if (lane + 32 < GW * GH)
+      p1 = orient_seg_node(ax, ay, bx, by, (long long)(x0 - 1 + (lane + 32) % GW) * Q,
+                           (long long)(y0 - 1 + (lane + 32) / GW) * Q) > 0;
+    lo = __ballot_sync(0xffffffffu, p0);
+    hi = __ballot_sync(0xffffffffu, p1);
+  }
+  auto node_sign = [&](int qx, int qy) {
+    if (fast) {
+      const int idx = (qy - y0 + 1) * GW + (qx - x0 + 1);
+      const unsigned bit = idx < 32 ? (lo >> idx) & 1u : (hi >> (idx - 32)) & 1u;
+      return bit ? 1 : -1;
+    }
+    return orient_seg_node(ax, ay, bx, by, (long long)qx * Q, (long long)qy * Q);
+  };
+  // cell -> (column, row) of the W-wide box by an FP32 quotient: (cell + 1/2) / W is
+  // at least 1/(2W) away from an integer, far above its rounding error (W <= 19)
+  const float invW = 1.0f / (float)W;
+  for (int c = lane; c < ncand; c += 32) {
+    const int i = 1 + (c & 7);
+    const int cell = c >> 3;
+    const int gy = (int)(((float)cell + 0.5f) * invW), gx = cell - gy * W;
+    const int qx = x0 + gx, qy = y0 + gy;  // destination node
+    const int ex = cx(i), ey = cy(i);
+    const int s1 = node_sign(qx - ex, qy - ey);
+    const int s2 = node_sign(qx, qy);
+    if (s1 == s2) continue;
+    const long long Px = (long long)(qx - ex) * Q, Py = (long long)(qy - ey) * Q;
+    long long o3, o4;
+    const int s3 = orient_link_pt(Px, Py, ex, ey, ax, ay, o3);
+    const int s4 = orient_link_pt(Px, Py, ex, ey, bx, by, o4);
+    if (s3 == s4) continue;
+    // destination and source inside the lattice (periodic axes wrap)
+    const int xs = qx - ex, ys = qy - ey;
+    if (geo.bc == IILBM_BC_CHANNEL && (qx < 0 || qx >= geo.nx || xs < 0 || xs >= geo.nx))
+      continue;
+    if (geo.bc != IILBM_BC_PERIODIC && (qy < 0 || qy >= geo.ny || ys < 0 || ys >= geo.ny))
+      continue;
+    T t;
+    if (sizeof(T) == 8) {
+      const double num = (double)o3, dd = (double)(o3 - o4);
+      const float rf = 1.0f / (float)dd;
+      double td = (double)((float)num * rf);
+      td = fma(num - td * dd, (double)rf, td);
+      t = T(fmin(fmax(td, 0.0), 1.0));
+    } else {
+      const float num = (float)(int)o3, dd = (float)(int)(o3 - o4);
+      t = T(fminf(fmaxf(num / dd, 0.0f), 1.0f));
+    }
+    const int dx = geo.bc == IILBM_BC_CHANNEL ? qx : wrap(qx, geo.nx);
+    const int dy = geo.bc == IILBM_BC_PERIODIC ? wrap(qy, geo.ny) : qy;
+    emit(i, dx, dy, s1, t);
+    found++;
+  }
+  return found;
+}
+
+// The jump of Eq. 32 on every link crossing segment A -> B (Fn linear along it):
+// s w_i/c_s^2 Fn(t) added to the jump field of the link's destination (Eq. 47), and the
+// flags of the tiles of the segment's footprint.
 template <typename T, typename GG>
 __device__ __forceinline__ void segment_links(long long ax, long long ay, long long bx,
                                               long long by, double FnA, double FnB, int lane,
                                               int jump, const GG &geo, T *Jf,
                                               const TileBuf &tb, unsigned tag) {
   const bool inside = ax != XQ_OUT && bx != XQ_OUT;
-  const long long Q = (long long)QSCALE;
   const long long QMAX = (long long)(MAX_SEGMENT * QSCALE);
   // floor / ceil of a snapped coordinate in lattice units
   auto qfloor = [](long long v) { return (int)(v >> 24); };
   auto qceil = [](long long v) { return (int)-((-v) >> 24); };
   int found = 0;
   if (jump && inside && llabs(bx - ax) < QMAX && llabs(by - ay) < QMAX) {
-    // destinations x of links that can reach the segment: with the node displaced by
-    // (eps, eps^2) the link x - e_i -> x spans [x - 1 + eps, x + 1 + eps] at most on
-    // each axis, which meets [min, max] only for ceil(min) - 1 <= x <= ceil(max)
-    const int x0 = qceil(min(ax, bx)) - 1, x1 = qceil(max(ax, bx));
-    const int y0 = qceil(min(ay, by)) - 1, y1 = qceil(max(ay, by));
-    const int W = x1 - x0 + 1, H = y1 - y0 + 1;
-    const int ncand = W * H * 8;
-    // node signs on the grid [x0-1, x1+1] x [y0-1, y1+1] (GW x GH nodes)
-    const int GW = W + 2, GH = H + 2;
-    const bool fast = GW * GH <= 64;
-    unsigned lo = 0u, hi = 0u;
-    if (fast) {
-      bool p0 = false, p1 = false;
-      if (lane < GW * GH)
-        p0 = orient_seg_node(ax, ay, bx, by, (long long)(x0 - 1 + lane % GW) * Q,
-                             (long long)(y0 - 1 + lane / GW) * Q) > 0;
-      if (lane + 32 < GW * GH)
-        p1 = orient_seg_node(ax, ay, bx, by, (long long)(x0 - 1 + (lane + 32) % GW) * Q,
-                             (long long)(y0 - 1 + (lane + 32) / GW) * Q) > 0;
-      lo = __ballot_sync(0xffffffffu, p0);
-      hi = __ballot_sync(0xffffffffu, p1);
-    }
-    auto node_sign = [&](int qx, int qy) {
-      if (fast) {
-        const int idx = (qy - y0 + 1) * GW + (qx - x0 + 1);
-        const unsigned bit = idx < 32 ? (lo >> idx) & 1u : (hi >> (idx - 32)) & 1u;
-        return bit ? 1 : -1;
-      }
-      return orient_seg_node(ax, ay, bx, by, (long long)qx * Q, (long long)qy * Q);
-    };
     const float fA = (float)FnA, fB = (float)FnB;  // FP32 path: converted once per warp
-    // cell -> (column, row) of the W-wide box by an FP32 quotient: (cell + 1/2) / W is
-    // at least 1/(2W) away from an integer, far above its rounding error (W <= 19)
-    const float invW = 1.0f / (float)W;
-    for (int c = lane; c < ncand; c += 32) {
-      const int i = 1 + (c & 7);
-      const int cell = c >> 3;
-      const int gy = (int)(((float)cell + 0.5f) * invW), gx = cell - gy * W;
-      const int qx = x0 + gx, qy = y0 + gy;  // destination node
-      const int ex = cx(i), ey = cy(i);
-      const int s1 = node_sign(qx - ex, qy - ey);
-      const int s2 = node_sign(qx, qy);
-      if (s1 == s2) continue;
-      const long long Px = (long long)(qx - ex) * Q, Py = (long long)(qy - ey) * Q;
-      long long o3, o4;
-      const int s3 = orient_link_pt(Px, Py, ex, ey, ax, ay, o3);
-      const int s4 = orient_link_pt(Px, Py, ex, ey, bx, by, o4);
-      if (s3 == s4) continue;
-      // destination and source inside the lattice (periodic axes wrap)
-      const int xs = qx - ex, ys = qy - ey;
-      if (geo.bc == IILBM_BC_CHANNEL && (qx < 0 || qx >= geo.nx || xs < 0 || xs >= geo.nx))
-        continue;
-      if (geo.bc != IILBM_BC_PERIODIC && (qy < 0 || qy >= geo.ny || ys < 0 || ys >= geo.ny))
-        continue;
-      // coefficient s w_i/c_s^2 Fn(t), t = o3 / (o3 - o4) along A -> B (Fn linear along
-      // the segment).  FP64 for FP64 storage (an FP32 quotient refined by one Newton
-      // step); FP32 otherwise: |o3|, |o3 - o4| < 2^31 fit the int casts, and converting
-      // each to FP32 rounds it with a relative error of at most 2^-24, so t carries a
-      // few FP32 ulps.
+    found = segment_crossings<T>(ax, ay, bx, by, lane, geo, [&](int i, int dx, int dy, int s1,
+                                                                T t) {
       T coef;
-      if (sizeof(T) == 8) {
-        const double num = (double)o3, dd = (double)(o3 - o4);
-        const float rf = 1.0f / (float)dd;
-        double t = (double)((float)num * rf);
-        t = fma(num - t * dd, (double)rf, t);
-        t = fmin(fmax(t, 0.0), 1.0);
-        coef = T((double)s1 * 3.0 * wt<double>(i) * ((1.0 - t) * FnA + t * FnB));
-      } else {
-        const float num = (float)(int)o3, dd = (float)(int)(o3 - o4);
-        const float t = fminf(fmaxf(num / dd, 0.0f), 1.0f);
-        coef = T((float)s1 * 3.0f * wt<float>(i) * ((1.0f - t) * fA + t * fB));
-      }
-      const int dx = geo.bc == IILBM_BC_CHANNEL ? qx : wrap(qx, geo.nx);
-      const int dy = geo.bc == IILBM_BC_PERIODIC ? wrap(qy, geo.ny) : qy;
+      if (sizeof(T) == 8)
+        coef = T((double)s1 * 3.0 * wt<double>(i) * ((1.0 - (double)t) * FnA + (double)t * FnB));
+      else
+        coef = T((float)s1 * 3.0f * wt<float>(i) * ((1.0f - (float)t) * fA + (float)t * fB));
       atomicAdd(&Jf[(long long)(i - 1) * geo.plane + (long long)dy * geo.pitch + dx], coef);
-      found++;
-    }
+    });
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) found += __shfl_xor_sync(0xffffffffu, found, o);

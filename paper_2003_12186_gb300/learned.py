@@ -33,17 +33,13 @@ def _parabola(nx, ny, u_max):
 
 
 def make_channel(sim, tol=TOL, max_passes=MAX_PASSES):
-    """FP32 MRT channel with the cylinder of `sim`, started from the parabolic inflow.
-
-    The whole body force is spread (no jump): the force iteration models the body's
-    effect on the flow by the spread force alone, so run to the tolerance it is the
-    force the step applies.  With the normal part moved into the jump instead, the
-    converged force carries components the spread-and-interpolate operator barely
-    sees, the jump applies them undamped, and the channel diverges within tens to
-    hundreds of steps (the FP64 oracle does the same)."""
+    """FP32 MRT channel with the cylinder of `sim`, started from the parabolic inflow:
+    II-LBM, the normal part of the body force through the jump and the tangential part
+    spread; the force iteration sees the force through that same operator, so run to
+    the tolerance it gives the step's collision velocity no slip at the markers."""
     g = iilbm.Lattice(sim["nx"], sim["ny"], collision=iilbm.MRT, storage="f32", tau=sim["tau"],
                       s=W.mrt_rates(sim["tau"]), bc=iilbm.BC_CHANNEL, u_max=sim["u_max"],
-                      jump=0)
+                      jump=1)
     g.init_equilibrium(None, _parabola(sim["nx"], sim["ny"], sim["u_max"]), None)
     g.set_interface(sim["X"], model=iilbm.DIRECT, moves=False, dX=sim["dX"], eta=2.0,
                     mdf_iters=max_passes, mdf_tol=tol, aux=np.zeros((sim["n"], 2)))

@@ -59,4 +59,5 @@ def assert_jump_fields_agree(Jg, Jo, rel):
     assert np.array_equal(sg, so), (f"cut-link sets differ: {int((sg & ~so).sum())} only on "
                                     f"the GPU, {int((so & ~sg).sum())} only in the oracle")
     assert so.sum() > 0
-    assert np.abs(Jg - Jo).max() <= rel * np.abs(Jo).max()
+    d = float(np.abs(Jg - Jo).max() / np.abs(Jo).max())
+    assert d <= rel, f"jump values differ by {d:.3e} of the largest (bound {rel:.1e})"

@@ -254,12 +254,14 @@ def test_ellipse2048_fp32_full_size(orc):
 def test_jump_field_matches_oracle(orc, storage):
     """The jump the interface phase adds (Eq. 47 with Eq. 32) for a moving membrane, at
     the start and after 40 steps: the same cut links as the oracle's records (set
-    compared exactly) with the same values (FP64 to 1e-14 of the largest; FP32, whose
-    crossing parameter is an FP32 quotient, to 2e-6)."""
+    compared exactly) with the same values.  FP64: to 1e-11 of the largest -- the spring
+    force is a second difference of coordinates of size R (~50) that is ~dX^2/R, so
+    evaluations in a different association differ by ~ulp(R) R / dX^2 relative, ~4e-13
+    here; FP32, whose crossing parameter is an FP32 quotient, to 2e-6."""
     w = W.ellipse_scaled(256, storage)
     g, o = make_pair(orc, 256, 256, collision="mrt", storage=storage, tau=w["tau"])
     set_membrane(orc, g, o, w["X"], "spring", w["kappa"], w["dX"])
-    rel = 1e-14 if storage == "f64" else 2e-6
+    rel = 1e-11 if storage == "f64" else 2e-6
     for steps in (0, 40):
         g.step(steps)
         o.step(steps)

@@ -20,9 +20,10 @@ variant, graph replay); the line also carries the same lattices stepped one by o
 --workload channel: flow past the fixed cylinder (D = 40 at x = 256, y = 128.5, 126
 markers) in the 1024 x 256 MRT channel, parabolic inflow u_max = 0.05, tau from Re,
 FP32, the normal force through the jump and the tangential force by direct forcing with
-5 force updates per step, Re 20 by default (--re; at Re 100, tau = 0.56, this coupling
-diverges after about 500 steps, in the FP64 oracle as on the GPU).  Its state (19 MB)
-fits in L2, so its roofline is flagged so.
+5 force updates per step (the updates see the force through the jump, as the step
+applies it), Re 20 by default (--re 100: tau = 0.56).  --history H adds an untimed
+drag / lift record of H steps (mean C_D, lift amplitude, Strouhal number).  Its state
+(19 MB) fits in L2, so its roofline is flagged so.
 
 --workload learned: 64 rigid-cylinder channels (512 x 128, D uniform in [16, 32], Re
 uniform in [10, 150], markers 1.5 lattice units apart, FP32) with the direct-forcing
@@ -70,6 +71,8 @@ def parse():
     ap.add_argument("--workload", default="ellipse",
                     choices=["ellipse", "batched", "learned", "channel"])
     ap.add_argument("--re", type=float, default=20.0, help="Reynolds number (channel)")
+    ap.add_argument("--history", type=int, default=0,
+                    help="channel: steps of drag / lift history after the timed region")
     ap.add_argument("--count", type=int, default=256, help="simulations of the batched sweep")
     a = ap.parse_args()
     if a.steps is None:
@@ -844,6 +847,34 @@ def run_channel(args):
     g.iilbm_set_timing(False)
     clk = clocks.stop()
     F = g.iilbm_get_body_force()
+    # drag / lift history (untimed): the force every 20 steps over args.history steps,
+    # C = 2 F / (rho U^2 D) with U = u_max (Eqs. 52-53), St = f D / U from the lift's
+    # mean-crossing period (Eq. 51)
+    hist = None
+    if args.history > 0:
+        cd, cl = [], []
+        for _ in range(args.history // 20):
+            g.step(20)
+            Fx, Fy = g.iilbm_get_body_force()
+            cd.append(2 * Fx / (w["u_max"] ** 2 * w["D"]))
+            cl.append(2 * Fy / (w["u_max"] ** 2 * w["D"]))
+        cd, cl = np.array(cd), np.array(cl)
+        c = cl - cl.mean()
+        up = np.nonzero((c[:-1] < 0) & (c[1:] >= 0))[0]
+        st = None
+        if len(up) >= 3:
+            period = 20.0 * (up[-1] - up[0]) / (len(up) - 1)
+            st = w["D"] / (period * w["u_max"])
+        hist = {"steps": args.history, "every": 20, "C_D_mean": round(float(cd.mean()), 4),
+                "C_D_amplitude": round(float((cd.max() - cd.min()) / 2), 4),
+                "C_L_amplitude": round(float((cl.max() - cl.min()) / 2), 4),
+                "C_L_mean": round(float(cl.mean()), 4),
+                "St": None if st is None else round(float(st), 4),
+                "lift_periods": max(len(up) - 1, 0),
+                "context": "paper, section 4.3 (its own setup: uniform inflow, D = 80 in "
+                           "[0, 40D] x [0, 20D]): Re 100 C_D 1.417, C_L +-0.344, St 0.169; "
+                           "here a confined channel (blockage 0.16) with a parabolic inflow, "
+                           "coefficients on u_max"}
     cells = nx * ny
     value = whole_job_mlups(cells, args.steps, world, ms * 1e-3)
     peak, peak_kind = peaks()
@@ -877,7 +908,8 @@ def run_channel(args):
                           "l2": "working set (19 MB) fits in L2: the roofline is not an HBM bound"},
                "drag_lift": {"Fx": F[0], "Fy": F[1],
                              "C_D": 2 * F[0] / (w["u_max"] ** 2 * 40.0),
-                             "note": "after warmup + the timed steps, from the parabolic start"},
+                             "note": "after warmup + the timed steps, from the parabolic start",
+                             "history": hist},
                "roofline": {"bound": "hbm", "achieved": round(lean_bytes / sc_avg / 1e9, 1),
                             "peak": peak, "unit": "GB/s",
                             "frac": round(lean_bytes / sc_avg / 1e9 / peak, 4), "traffic": None,

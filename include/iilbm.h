@@ -46,7 +46,6 @@ enum { IILBM_SRT = 0, IILBM_MRT = 1 };
 /* Storage precision of the shifted populations df_i = f_i - w_i rho0.  Arithmetic
  * is FP64 for IILBM_F64 and FP32 for the others. */
 enum { IILBM_F64 = 0, IILBM_F32 = 1, IILBM_F16 = 2, IILBM_BF16 = 3 };
-enum { IILBM_ROUND_NEAREST = 0, IILBM_ROUND_STOCHASTIC = 1 };
 /* Boundaries: periodic box; walls at y = -1/2, ny - 1/2 (halfway bounce-back) and
  * periodic x; channel = walls plus parabolic inflow at x = 0 and outflow at nx - 1. */
 enum { IILBM_BC_PERIODIC = 0, IILBM_BC_WALLS_Y = 1, IILBM_BC_CHANNEL = 2 };
@@ -62,9 +61,7 @@ typedef struct {
   int32_t jump;         /* 1: II-LBM (normal force through the jump of Eq. 32, tangential
                            part spread, Eq. 46); 0: IB-LBM with Guo forcing (whole G spread) */
   int32_t storage_scale_log2; /* stored value = df * 2^k (exact); 0 for F32/F64 */
-  int32_t rounding;     /* F16 / BF16 storage: IILBM_ROUND_NEAREST (even) or
-                           IILBM_ROUND_STOCHASTIC (unbiased: the rounding error is zero on
-                           average, so it does not accumulate step after step) */
+  int32_t reserved;
   double tau;           /* relaxation time lambda, nu = c_s^2 (lambda - 1/2) (Eq. 7); > 0.5 */
   double s[9];          /* MRT rates in the Lallemand-Luo moment order
                            (rho, e, eps, jx, qx, jy, qy, pxx, pxy) */

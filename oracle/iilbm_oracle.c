@@ -74,6 +74,9 @@ typedef struct {
   double eta;      /* direct-forcing gain (ORC_DIRECT) */
   int mdf_iters;   /* direct forcing: maximum iterations */
   double mdf_tol;  /* direct forcing: stop when max_k |U^D - U_k| < tol (0: run all) */
+  int curve;       /* interface for the jump: 0 the marker polygon; m >= 1 the cubic
+                      spline through the markers (normals, |X_s|, Fn along it), its
+                      crossings taken on m chords per segment */
   double *X;       /* [n][2] */
   double *Gp;      /* prescribed G [n][2] (ORC_PRESCRIBED) / warm-start G (ORC_DIRECT) */
   double *UD;      /* desired velocity [n][2] (ORC_DIRECT) */
@@ -323,6 +326,79 @@ void orc_spring_forces(const orc_iface *I, double *G) {
   }
 }
 
+/* -------------------------------------------------- cubic spline interface ---
+ * For flexible boundaries the paper represents the interface by a cubic spline (after
+ * Lee & LeVeque, end of section 3.2).  Reading: the periodic interpolating cubic spline
+ * through the markers, parametrised by the marker index (s = k at marker k, the
+ * markers being about equally spaced), in uniform B-spline form
+ *   v(k + t) = c_{k-1} (1-t)^3/6 + c_k (3t^3 - 6t^2 + 4)/6
+ *            + c_{k+1} (-3t^3 + 3t^2 + 3t + 1)/6 + c_{k+2} t^3/6,   0 <= t < 1,
+ * whose interpolation conditions v(k) = (c_{k-1} + 4 c_k + c_{k+1})/6 = v_k form a
+ * cyclic tridiagonal system for the coefficients c. */
+
+/* Coefficients c[k*stride] of the periodic spline through v[k*stride], k < n (n >= 3):
+ * the cyclic system (c_{k-1} + 4 c_k + c_{k+1}) = 6 v_k solved by the Sherman-Morrison
+ * formula around a tridiagonal (Thomas) solve. */
+void orc_spline_coeffs(const double *v, int n, int stride, double *c) {
+  /* A = T + u w^T, u = (g, 0, .., 0, 1), w = (1, 0, .., 0, 1/g), g = -4: T is the
+   * tridiagonal part with its first and last diagonal entries changed so that u w^T
+   * restores the two corner entries (each 1). */
+  const double g = -4.0;
+  double *diag = (double *)malloc(n * sizeof(double));
+  double *y = (double *)malloc(n * sizeof(double)), *z = (double *)malloc(n * sizeof(double));
+  double *rhs = (double *)malloc(n * sizeof(double)), *u = (double *)malloc(n * sizeof(double));
+  double *cp = (double *)malloc(n * sizeof(double)), *dp = (double *)malloc(n * sizeof(double));
+  for (int k = 0; k < n; k++) { diag[k] = 4.0; rhs[k] = 6.0 * v[k * stride]; u[k] = 0.0; }
+  diag[0] -= g;
+  diag[n - 1] -= 1.0 / g;
+  u[0] = g;
+  u[n - 1] = 1.0;
+  /* Thomas solves of T y = rhs and T z = u (sub- and super-diagonal entries 1) */
+  for (int pass = 0; pass < 2; pass++) {
+    const double *b = pass == 0 ? rhs : u;
+    double *x = pass == 0 ? y : z;
+    cp[0] = 1.0 / diag[0];
+    dp[0] = b[0] / diag[0];
+    for (int k = 1; k < n; k++) {
+      double m = diag[k] - cp[k - 1];
+      cp[k] = 1.0 / m;
+      dp[k] = (b[k] - dp[k - 1]) / m;
+    }
+    x[n - 1] = dp[n - 1];
+    for (int k = n - 2; k >= 0; k--) x[k] = dp[k] - cp[k] * x[k + 1];
+  }
+  double wy = y[0] + y[n - 1] / g, wz = z[0] + z[n - 1] / g;
+  double f = wy / (1.0 + wz);
+  for (int k = 0; k < n; k++) c[k * stride] = y[k] - f * z[k];
+  free(diag); free(y); free(z); free(rhs); free(u); free(cp); free(dp);
+}
+
+/* The spline (deriv = 0) or its derivative d/ds (deriv = 1) at s (any real, periodic
+ * with period n) from coefficients c[k*stride]. */
+double orc_spline_eval(const double *c, int n, int stride, double s, int deriv) {
+  double fl = floor(s);
+  double t = s - fl;
+  int k = (int)fl;
+  double b[4];
+  if (!deriv) {
+    b[0] = (1 - t) * (1 - t) * (1 - t) / 6.0;
+    b[1] = (3 * t * t * t - 6 * t * t + 4) / 6.0;
+    b[2] = (-3 * t * t * t + 3 * t * t + 3 * t + 1) / 6.0;
+    b[3] = t * t * t / 6.0;
+  } else {
+    b[0] = -(1 - t) * (1 - t) / 2.0;
+    b[1] = 1.5 * t * t - 2 * t;
+    b[2] = -1.5 * t * t + t + 0.5;
+    b[3] = t * t / 2.0;
+  }
+  double r = 0;
+  for (int j = 0; j < 4; j++) {
+    int q = ((k - 1 + j) % n + n) % n;
+    r += c[q * stride] * b[j];
+  }
+  return r;
+}
+
 /* Normal / tangential split, Eqs. 31-32 and Eq. 46.
  * n_k: outward unit normal of the counter-clockwise polygon at marker k, the
  * central tangent X_{k+1} - X_{k-1} turned by -90 degrees (Eq. 31 in 2D).
@@ -334,18 +410,33 @@ void orc_spring_forces(const orc_iface *I, double *G) {
 void orc_normal_split(const orc_iface *I, const double *G, double *Fn, double *Gpar,
                       double *nrm) {
   int n = I->n;
+  double *cx = NULL;
+  if (I->curve > 0) {  /* spline interface: tangents X'(k) of the spline */
+    cx = (double *)malloc(2 * n * sizeof(double));
+    orc_spline_coeffs(I->X, n, 2, cx);
+    orc_spline_coeffs(I->X + 1, n, 2, cx + 1);
+  }
   for (int k = 0; k < n; k++) {
     int kp = (k + 1) % n, km = (k + n - 1) % n;
-    double tx = I->X[2 * kp] - I->X[2 * km], ty = I->X[2 * kp + 1] - I->X[2 * km + 1];
+    double tx, ty, Xs;
+    if (cx) {  /* X'(k) = (c_{k+1} - c_{k-1}) / 2; |X_s| = |X'(k)| / dX */
+      tx = orc_spline_eval(cx, n, 2, k, 1);
+      ty = orc_spline_eval(cx + 1, n, 2, k, 1);
+    } else {   /* central difference of the polygon: |X_s| = |X_{k+1} - X_{k-1}| / (2 dX) */
+      tx = I->X[2 * kp] - I->X[2 * km];
+      ty = I->X[2 * kp + 1] - I->X[2 * km + 1];
+    }
     double tl = sqrt(tx * tx + ty * ty);
     double nx = ty / tl, ny = -tx / tl;
-    double Xs = I->moves ? tl / (2.0 * I->dX) : 1.0;
+    if (cx) Xs = I->moves ? tl / I->dX : 1.0;
+    else Xs = I->moves ? tl / (2.0 * I->dX) : 1.0;
     double Gn = G[2 * k] * nx + G[2 * k + 1] * ny;
     Fn[k] = Gn / Xs;
     Gpar[2 * k] = G[2 * k] - Gn * nx;
     Gpar[2 * k + 1] = G[2 * k + 1] - Gn * ny;
     if (nrm) { nrm[2 * k] = nx; nrm[2 * k + 1] = ny; }
   }
+  free(cx);
 }
 
 /* ------------------------------------------------------------ cut links ----
@@ -440,6 +531,53 @@ int orc_cut_links(const orc_cfg *c, const double *X, int n, const double *Fn,
           cnt++;
         }
   }
+  return cnt;
+}
+
+/* Cut links of the spline interface (curve = m chords per segment): the spline
+ * through the markers is replaced by the polygon of its points X(k + j/m), j < m, and
+ * every crossing of a chord (k, j) at chord parameter t, found as orc_cut_links finds
+ * them, lies at spline parameter s = k + (j + t)/m, where Fn(s) is the periodic spline
+ * through the markers' Fn_k.  Same records and return as orc_cut_links. */
+int orc_cut_links_spline(const orc_cfg *c, const double *X, int n, const double *Fn, int m,
+                         int *cell, int *dir, double *coef, int cap) {
+  int N = n * m, cnt = 0;
+  double *cx = (double *)malloc(2 * n * sizeof(double)), *cf = (double *)malloc(n * sizeof(double));
+  double *P = (double *)malloc(2 * N * sizeof(double));
+  orc_spline_coeffs(X, n, 2, cx);
+  orc_spline_coeffs(X + 1, n, 2, cx + 1);
+  orc_spline_coeffs(Fn, n, 1, cf);
+  for (int k = 0; k < n; k++)
+    for (int j = 0; j < m; j++) {
+      double sp = k + (double)j / m;
+      P[2 * (k * m + j)] = orc_spline_eval(cx, n, 2, sp, 0);
+      P[2 * (k * m + j) + 1] = orc_spline_eval(cx + 1, n, 2, sp, 0);
+    }
+  for (int q = 0; q < N && cnt >= 0; q++) {
+    int qp = (q + 1) % N;
+    int64_t ax = orc_quantize(P[2 * q]), ay = orc_quantize(P[2 * q + 1]);
+    int64_t bx = orc_quantize(P[2 * qp]), by = orc_quantize(P[2 * qp + 1]);
+    double minx = fmin(P[2 * q], P[2 * qp]), maxx = fmax(P[2 * q], P[2 * qp]);
+    double miny = fmin(P[2 * q + 1], P[2 * qp + 1]), maxy = fmax(P[2 * q + 1], P[2 * qp + 1]);
+    int x0 = (int)floor(minx) - 1, x1 = (int)ceil(maxx) + 1;
+    int y0 = (int)floor(miny) - 1, y1 = (int)ceil(maxy) + 1;
+    for (int qy = y0; qy <= y1 && cnt >= 0; qy++)
+      for (int qx = x0; qx <= x1 && cnt >= 0; qx++)
+        for (int i = 1; i < 9; i++) {
+          int sg; double t;
+          if (!orc_link_crosses(ax, ay, bx, by, qx - EX[i], qy - EY[i], i, &sg, &t)) continue;
+          int xd = wrap_axis(qx, c->nx, periodic_x(c)), yd = wrap_axis(qy, c->ny, periodic_y(c));
+          int xs = wrap_axis(qx - EX[i], c->nx, periodic_x(c)), ys = wrap_axis(qy - EY[i], c->ny, periodic_y(c));
+          if (xd < 0 || yd < 0 || xs < 0 || ys < 0) continue;
+          if (cnt >= cap) { cnt = -1; break; }
+          double F = orc_spline_eval(cf, n, 1, (q + t) / m, 0);
+          cell[cnt] = yd * c->nx + xd;
+          dir[cnt] = i;
+          coef[cnt] = (double)sg * WT[i] * INV_CS2 * F;
+          cnt++;
+        }
+  }
+  free(cx); free(cf); free(P);
   return cnt;
 }
 
@@ -611,10 +749,11 @@ static int apply_forcing(const orc_cfg *c, const orc_iface *I, const double *G,
   orc_normal_split(I, G, Fn, Gpar, NULL);
   double *P = (double *)malloc(2 * n * sizeof(double));
   if (c->jump) {
-    int cap = 64 * n + 64;
+    int cap = 64 * n * (I->curve > 0 ? I->curve : 1) + 64;
     int *cell = (int *)malloc(cap * sizeof(int)), *dir = (int *)malloc(cap * sizeof(int));
     double *coef = (double *)malloc(cap * sizeof(double));
-    m = orc_cut_links(c, I->X, n, Fn, cell, dir, coef, cap);
+    m = I->curve > 0 ? orc_cut_links_spline(c, I->X, n, Fn, I->curve, cell, dir, coef, cap)
+                     : orc_cut_links(c, I->X, n, Fn, cell, dir, coef, cap);
     for (int r = 0; r < m; r++) f[dir[r] * N + cell[r]] += coef[r];
     free(cell); free(dir); free(coef);
     for (int k = 0; k < 2 * n; k++) P[k] = Gpar[k] * I->dX;
@@ -770,6 +909,11 @@ void orc_get_markers(const orc_state *S, double *X, double *G, double *U, double
   if (Fn) memcpy(Fn, S->Fn, n * sizeof(double));
 }
 
+/* Interface representation for the jump (orc_iface.curve) of the current interface. */
+void orc_set_curve(orc_state *S, int curve) {
+  if (S->has_iface) S->I.curve = curve;
+}
+
 int orc_mdf_iters(const orc_state *S) { return S->mdf_last_iters; }
 void orc_set_ws_previous(orc_state *S, int on) { S->ws_previous = on; }
 void orc_get_ustar(const orc_state *S, double *out) {
@@ -797,9 +941,9 @@ void orc_spring_forces_arr(const double *X, int n, int model, double kappa, doub
   orc_spring_forces(&I, G);
 }
 void orc_normal_split_arr(const double *X, int n, int moves, double dX, const double *G,
-                          double *Fn, double *Gpar, double *nrm) {
+                          double *Fn, double *Gpar, double *nrm, int curve) {
   orc_iface I;
   memset(&I, 0, sizeof I);
-  I.n = n; I.moves = moves; I.dX = dX; I.X = (double *)X;
+  I.n = n; I.moves = moves; I.dX = dX; I.X = (double *)X; I.curve = curve;
   orc_normal_split(&I, G, Fn, Gpar, nrm);
 }

@@ -119,7 +119,14 @@ def _bind(L):
     L.orc_interp.argtypes = [C.POINTER(_Cfg), _D, C.c_int, _D, _D, _D]
     L.orc_spring_forces_arr.argtypes = [_D, C.c_int, C.c_int, C.c_double, C.c_double,
                                         C.c_double, _D]
-    L.orc_normal_split_arr.argtypes = [_D, C.c_int, C.c_int, C.c_double, _D, _D, _D, _D]
+    L.orc_normal_split_arr.argtypes = [_D, C.c_int, C.c_int, C.c_double, _D, _D, _D, _D,
+                                       C.c_int]
+    L.orc_set_curve.argtypes = [C.c_void_p, C.c_int]
+    L.orc_spline_coeffs.argtypes = [_D, C.c_int, C.c_int, _D]
+    L.orc_spline_eval.argtypes = [_D, C.c_int, C.c_int, C.c_double, C.c_int]
+    L.orc_spline_eval.restype = C.c_double
+    L.orc_cut_links_spline.argtypes = [C.POINTER(_Cfg), _D, C.c_int, _D, C.c_int, _I, _I, _D,
+                                       C.c_int]
     return L
 
 
@@ -248,14 +255,45 @@ def spring_forces(X, model=SPRING, kappa=1.0, dX=1.0, l0=1.0):
     return G
 
 
-def normal_split(X, G, moves=True, dX=1.0):
-    """(Fn, Gpar, normals) of Eqs. 31-32 and 46."""
+def normal_split(X, G, moves=True, dX=1.0, curve=0):
+    """(Fn, Gpar, normals) of Eqs. 31-32 and 46 (curve > 0: from the spline interface)."""
     X = _f64(X).reshape(-1, 2)
     G = _f64(G).reshape(-1, 2)
     n = X.shape[0]
     Fn, Gpar, nrm = np.zeros(n), np.zeros((n, 2)), np.zeros((n, 2))
-    lib().orc_normal_split_arr(_p(X), n, int(moves), dX, _p(G), _p(Fn), _p(Gpar), _p(nrm))
+    lib().orc_normal_split_arr(_p(X), n, int(moves), dX, _p(G), _p(Fn), _p(Gpar), _p(nrm),
+                               int(curve))
     return Fn, Gpar, nrm
+
+
+def spline_coeffs(v):
+    """B-spline coefficients of the periodic cubic spline through v[k] (k < n)."""
+    v = _f64(v).ravel()
+    c = np.zeros_like(v)
+    lib().orc_spline_coeffs(_p(v), v.size, 1, _p(c))
+    return c
+
+
+def spline_eval(c, s, deriv=0):
+    c = _f64(c).ravel()
+    return lib().orc_spline_eval(_p(c), c.size, 1, float(s), int(deriv))
+
+
+def cut_links_spline(cfg: _Cfg, X, Fn, m, cap=None):
+    """Cut-link records of the spline interface through the markers X (m chords per
+    segment), jump strengths from the spline of Fn."""
+    X = _f64(X).reshape(-1, 2)
+    Fn = _f64(Fn)
+    n = X.shape[0]
+    cap = cap or 64 * n * m + 64
+    cell = np.zeros(cap, np.int32)
+    d = np.zeros(cap, np.int32)
+    coef = np.zeros(cap)
+    k = lib().orc_cut_links_spline(C.byref(cfg), _p(X), n, _p(Fn), int(m),
+                                   cell.ctypes.data_as(_I), d.ctypes.data_as(_I), _p(coef), cap)
+    if k < 0:
+        raise RuntimeError("cut-link capacity exceeded")
+    return cell[:k].copy(), d[:k].copy(), coef[:k].copy()
 
 
 def polygon_area(X) -> float:
@@ -301,7 +339,7 @@ class Oracle:
         return df
 
     def set_interface(self, X, model=SPRING, moves=True, kappa=0.0, dX=1.0, l0=1.0, eta=2.0,
-                      mdf_iters=0, mdf_tol=0.0, G=None, UD=None):
+                      mdf_iters=0, mdf_tol=0.0, G=None, UD=None, curve=0):
         X = _f64(X).reshape(-1, 2)
         n = X.shape[0]
         Gp = None if G is None else _f64(G).reshape(n, 2)
@@ -309,6 +347,7 @@ class Oracle:
         self._L.orc_set_interface(self._h, _p(X), n, model, int(moves), kappa, dX, l0, eta,
                                 mdf_iters, mdf_tol, None if Gp is None else _p(Gp),
                                 None if UDa is None else _p(UDa))
+        self._L.orc_set_curve(self._h, int(curve))
         self.n_markers = n
 
     def step(self, n=1):

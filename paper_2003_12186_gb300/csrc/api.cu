@@ -180,8 +180,6 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
   if (c.bc == IILBM_BC_CHANNEL && !(std::abs(c.u_max) < 0.5)) return IILBM_ERR_INVALID_ARG;
   if (!(c.tau > 0.5) || !(c.rho0 > 0) || std::abs(c.storage_scale_log2) > 30)
     return IILBM_ERR_INVALID_ARG;
-  if (c.rounding != IILBM_ROUND_NEAREST && c.rounding != IILBM_ROUND_STOCHASTIC)
-    return IILBM_ERR_INVALID_ARG;
   if (c.collision == IILBM_MRT)
     for (int i = 0; i < 9; i++)
       if (!(c.s[i] >= 0.0 && c.s[i] < 2.0)) return IILBM_ERR_INVALID_ARG;
@@ -234,7 +232,6 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
             cudaMalloc(&h->A, 9 * (size_t)g.plane * h->sbytes) == cudaSuccess &&
             cudaMalloc(&h->uf, 2 * (size_t)g.plane * h->tbytes) == cudaSuccess &&
             cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&h->d_seed, 2 * sizeof(unsigned)) == cudaSuccess &&
             cudaMalloc(&h->d_mdf_iters, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->d_mdf_res, sizeof(double)) == cudaSuccess &&
             cudaMalloc(&h->d_tiles_total, sizeof(unsigned long long)) == cudaSuccess;
@@ -253,7 +250,6 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
   int rc = IILBM_OK;
   if (cudaMemsetAsync(h->A, 0, 9 * (size_t)g.plane * h->sbytes, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream) != cudaSuccess ||
-      cudaMemsetAsync(h->d_seed, 0, 2 * sizeof(unsigned), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_mdf_iters, 0, sizeof(int), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_mdf_res, 0, sizeof(double), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_tiles_total, 0, sizeof(unsigned long long), h->stream) != cudaSuccess)
@@ -278,7 +274,7 @@ int iilbm_destroy(iilbm_t h) {
   void *bufs[] = {h->A, h->uf, h->Jb[0], h->Jb[1], h->gb[0], h->gb[1], h->flagsb[0], h->flagsb[1],
                   h->tile_list[0], h->tile_list[1], h->tile_count[0], h->tile_count[1],
                   h->tagb[0], h->tagb[1],
-                  h->d_status, h->d_seed, h->d_mdf_iters, h->d_mdf_res, h->d_tiles_total};
+                  h->d_status, h->d_mdf_iters, h->d_mdf_res, h->d_tiles_total};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);

@@ -562,7 +562,7 @@ int iilbm_create_batch(iilbm_batch_t *out, const iilbm_t *lattices, int32_t coun
     d.jump = h->cfg.jump;
     d.ip = h->ip;
     const iilbm_config &c = h->cfg;
-    d.p = make_collp<float>(c, h->d_seed);
+    d.p = make_collp<float>(c);
     d.status = h->d_status;
     d.tiles_total = h->d_tiles_total;
     d.u_max = c.u_max;

@@ -76,34 +76,8 @@ __device__ inline T phi4(T r) {
 }
 
 // ------------------------------------------------------------ storage types
-// Wellons' "lowbias32" integer hash (xorshift-multiply, published constants): the
-// random bits of stochastic rounding, from an element's offset and the step's seed.
-__host__ __device__ constexpr unsigned mix32(unsigned x) {
-  x ^= x >> 16;
-  x *= 0x7feb352du;
-  x ^= x >> 15;
-  x *= 0x846ca68bu;
-  x ^= x >> 16;
-  return x;
-}
-
-// Stochastic rounding of an FP32 value to a 16-bit type that keeps its top 23 - DROP
-// mantissa bits: 8 random bits r8 are added to the FP32 bit pattern just below the kept
-// bits and the result is then truncated toward zero, so |v| rounds up with a probability
-// equal to its dropped fraction (to 1/256) and the rounding error is zero on average
-// (round to nearest makes the same error every step a slowly varying field takes the
-// same value, a bias that accumulates).  Inf and NaN pass unchanged; a carry into the
-// exponent rounds up to the next binade, as it should.
-template <int DROP>
-__device__ __forceinline__ float sr_dither(float v, unsigned r8) {
-  const unsigned b = __float_as_uint(v);
-  if ((b & 0x7f800000u) == 0x7f800000u) return v;
-  return __uint_as_float(b + (r8 << (DROP - 8)));
-}
-
 // Populations are stored as df * 2^k in S and computed in T (double for FP64
-// storage, float otherwise).  The 16-bit types also store with stochastic rounding
-// (st_sr, 8 random bits).
+// storage, float otherwise).
 template <typename S> struct Store;
 template <> struct Store<double> {
   using T = double;
@@ -119,17 +93,11 @@ template <> struct Store<__half> {
   using T = float;
   __device__ static float ld(__half v) { return __half2float(v); }
   __device__ static __half st(float v) { return __float2half_rn(v); }
-  __device__ static __half st_sr(float v, unsigned r8) {
-    return __float2half_rz(sr_dither<13>(v, r8));
-  }
 };
 template <> struct Store<__nv_bfloat16> {
   using T = float;
   __device__ static float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
   __device__ static __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
-  __device__ static __nv_bfloat16 st_sr(float v, unsigned r8) {
-    return __float2bfloat16_rz(sr_dither<16>(v, r8));
-  }
 };
 
 // Geometry of one lattice as the kernels see it.
@@ -227,8 +195,6 @@ struct iilbm_lattice {
   long long step;     // time level of the state; AA parity = step & 1
   bool prepared;      // jump / force of the current state already in J, g
   int *d_status;      // latched device status bits
-  unsigned *d_seed;   // stochastic rounding: the seed of the even / odd step (advanced by
-                      // the block that updates tile 0)
   // interface
   int nm;
   iilbm_interface_params ip;

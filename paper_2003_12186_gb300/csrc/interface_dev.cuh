@@ -61,13 +61,17 @@ struct MarkerForce {
   bool bad;
 };
 
-// (x, y): marker j; (xp, yp), (xm, ym): its successor and predecessor on the polygon.
+// (x, y): marker j; (xp, yp), (xm, ym): its successor and predecessor on the polygon;
+// (tgx, tgy) the tangent the normal is taken from and |X_s| = |tangent| / tg_len (the
+// polygon's central difference X_{j+1} - X_{j-1} with tg_len = 2 dX, or the spline's
+// derivative X'(j) with tg_len = dX).
 template <typename T, typename GG>
-__device__ inline MarkerForce<T> marker_force_at(double x, double y, double xp, double yp,
-                                                 double xm, double ym,
-                                                 const double *__restrict__ aux, int j,
-                                                 const iilbm_interface_params &ip, int jump,
-                                                 const GG &geo) {
+__device__ inline MarkerForce<T> marker_force_tangent(double x, double y, double xp, double yp,
+                                                      double xm, double ym, double tgx,
+                                                      double tgy, double tg_len,
+                                                      const double *__restrict__ aux, int j,
+                                                      const iilbm_interface_params &ip,
+                                                      int jump, const GG &geo) {
   MarkerForce<T> m;
   const double dax = xp - x, day = yp - y, dbx = x - xm, dby = y - ym;  // segments k, k-1
   // validity: finite, inside the representable / valid region, short segments
@@ -92,11 +96,11 @@ __device__ inline MarkerForce<T> marker_force_at(double x, double y, double xp, 
     gx = T(aux[2 * j]);
     gy = T(aux[2 * j + 1]);
   }
-  const T tx = T(xp - xm), ty = T(yp - ym);
+  const T tx = T(tgx), ty = T(tgy);
   const T tl = sqrt(tx * tx + ty * ty);
   m.nx = ty / tl;  // outward for a counter-clockwise polygon
   m.ny = -tx / tl;
-  const T xs = ip.moves ? tl / T(2.0 * ip.dX) : T(1);
+  const T xs = ip.moves ? tl / T(tg_len) : T(1);
   const T gn = gx * m.nx + gy * m.ny;
   m.gx = gx;
   m.gy = gy;
@@ -110,6 +114,17 @@ __device__ inline MarkerForce<T> marker_force_at(double x, double y, double xp, 
     m.py = gy * dX;
   }
   return m;
+}
+
+// The polygon's marker force: normal from the central difference X_{j+1} - X_{j-1}.
+template <typename T, typename GG>
+__device__ inline MarkerForce<T> marker_force_at(double x, double y, double xp, double yp,
+                                                 double xm, double ym,
+                                                 const double *__restrict__ aux, int j,
+                                                 const iilbm_interface_params &ip, int jump,
+                                                 const GG &geo) {
+  return marker_force_tangent<T>(x, y, xp, yp, xm, ym, xp - xm, yp - ym, 2.0 * ip.dX, aux, j,
+                                 ip, jump, geo);
 }
 
 template <typename T, typename GG>
@@ -184,13 +199,26 @@ __device__ inline bool in_region(double x, double y) {
 
 // The marker pass of the batched executor, one thread per marker j of its flattened
 // list: force, split, snapped coordinates, and the spread of P_j over the stencil.
+// cs: the spline coefficients of the marker coordinates (the spline interface: the
+// normal from the spline's tangent X'(j) = (c_{j+1} - c_{j-1}) / 2, |X_s| = |X'(j)| / dX),
+// or null (the polygon).
 template <typename T, typename GG>
 __device__ __forceinline__ void interface_marker(const double *__restrict__ X,
                                                  const double *__restrict__ aux, int n, int j,
                                                  const iilbm_interface_params &ip, int jump,
                                                  const GG &geo, T *gf, double *G, double *Fn,
-                                                 double *nrm, long long *Xq, int *status) {
-  const MarkerForce<T> m = marker_force<T>(X, aux, n, j, ip, jump, geo);
+                                                 double *nrm, long long *Xq, int *status,
+                                                 const double *__restrict__ cs = nullptr) {
+  MarkerForce<T> m;
+  if (cs) {
+    const int jp = j + 1 == n ? 0 : j + 1, jm = j == 0 ? n - 1 : j - 1;
+    m = marker_force_tangent<T>(X[2 * j], X[2 * j + 1], X[2 * jp], X[2 * jp + 1], X[2 * jm],
+                                X[2 * jm + 1], 0.5 * (cs[2 * jp] - cs[2 * jm]),
+                                0.5 * (cs[2 * jp + 1] - cs[2 * jm + 1]), ip.dX, aux, j, ip, jump,
+                                geo);
+  } else {
+    m = marker_force<T>(X, aux, n, j, ip, jump, geo);
+  }
   if (m.bad) atomicOr(status, ST_INTERFACE);
   G[2 * j] = (double)m.gx;
   G[2 * j + 1] = (double)m.gy;
@@ -329,14 +357,15 @@ __device__ __forceinline__ int segment_crossings(long long ax, long long ay, lon
   return found;
 }
 
-// The jump of Eq. 32 on every link crossing segment A -> B (Fn linear along it):
-// s w_i/c_s^2 Fn(t) added to the jump field of the link's destination (Eq. 47), and the
-// flags of the tiles of the segment's footprint.
-template <typename T, typename GG>
-__device__ __forceinline__ void segment_links(long long ax, long long ay, long long bx,
-                                              long long by, double FnA, double FnB, int lane,
-                                              int jump, const GG &geo, T *Jf,
-                                              const TileBuf &tb, unsigned tag) {
+// The jump of Eq. 32 on every link crossing segment A -> B: coef(i, s, t) (the jump
+// s w_i/c_s^2 Fn at crossing parameter t) added to the jump field of the link's
+// destination (Eq. 47), the crossings counted, and the flags of the tiles of the
+// segment's footprint set.
+template <typename T, typename GG, typename Coef>
+__device__ __forceinline__ void segment_jump(long long ax, long long ay, long long bx,
+                                             long long by, int lane, int jump, const GG &geo,
+                                             T *Jf, const TileBuf &tb, unsigned tag,
+                                             Coef &&coef) {
   const bool inside = ax != XQ_OUT && bx != XQ_OUT;
   const long long QMAX = (long long)(MAX_SEGMENT * QSCALE);
   // floor / ceil of a snapped coordinate in lattice units
@@ -344,15 +373,10 @@ __device__ __forceinline__ void segment_links(long long ax, long long ay, long l
   auto qceil = [](long long v) { return (int)-((-v) >> 24); };
   int found = 0;
   if (jump && inside && llabs(bx - ax) < QMAX && llabs(by - ay) < QMAX) {
-    const float fA = (float)FnA, fB = (float)FnB;  // FP32 path: converted once per warp
     found = segment_crossings<T>(ax, ay, bx, by, lane, geo, [&](int i, int dx, int dy, int s1,
                                                                 T t) {
-      T coef;
-      if (sizeof(T) == 8)
-        coef = T((double)s1 * 3.0 * wt<double>(i) * ((1.0 - (double)t) * FnA + (double)t * FnB));
-      else
-        coef = T((float)s1 * 3.0f * wt<float>(i) * ((1.0f - (float)t) * fA + (float)t * fB));
-      atomicAdd(&Jf[(long long)(i - 1) * geo.plane + (long long)dy * geo.pitch + dx], coef);
+      atomicAdd(&Jf[(long long)(i - 1) * geo.plane + (long long)dy * geo.pitch + dx],
+                coef(i, s1, t));
     });
   }
 #pragma unroll
@@ -375,6 +399,20 @@ __device__ __forceinline__ void segment_links(long long ax, long long ay, long l
       flag_tile(tb, row * geo.ntx + col, tag);
     }
   }
+}
+
+// The polygon's segment pass: Fn linear along the segment, s w_i/c_s^2 Fn(t).
+template <typename T, typename GG>
+__device__ __forceinline__ void segment_links(long long ax, long long ay, long long bx,
+                                              long long by, double FnA, double FnB, int lane,
+                                              int jump, const GG &geo, T *Jf,
+                                              const TileBuf &tb, unsigned tag) {
+  const float fA = (float)FnA, fB = (float)FnB;  // FP32 path: converted once per warp
+  segment_jump<T>(ax, ay, bx, by, lane, jump, geo, Jf, tb, tag, [&](int i, int s1, T t) -> T {
+    if (sizeof(T) == 8)
+      return T((double)s1 * 3.0 * wt<double>(i) * ((1.0 - (double)t) * FnA + (double)t * FnB));
+    return T((float)s1 * 3.0f * wt<float>(i) * ((1.0f - (float)t) * fA + (float)t * fB));
+  });
 }
 
 // The segment pass of segment k -> k+1 from the marker pass's outputs in global memory.

@@ -226,7 +226,7 @@ static void sc_launch_bc(iilbm_lattice *h, cudaStream_t forced_stream) {
   const int b = h->step & 1;
   T *J = (T *)h->Jb[b], *gf = (T *)h->gb[b];
   const unsigned *fl = h->flagsb[b];
-  const CollP<T> p = make_collp<T>(h->cfg, h->d_seed);
+  const CollP<T> p = make_collp<T>(h->cfg);
   constexpr int V = Vec<S>::V;
   const int nyt = (g.ny + TILE_Y - 1) / TILE_Y;
   const bool vec = h->vector_sc && g.nx % V == 0;

@@ -19,16 +19,11 @@ struct CollP {
   T rho0;
   T scale, inv_scale;        // storage scale 2^k and 2^-k
   T bodyx, bodyy;
-  int sr;                    // 16-bit storage: stochastic rounding of the stored values
-  unsigned *seed;            // its seeds by step parity (the lattice's d_seed)
 };
 
 template <typename T>
-CollP<T> make_collp(const iilbm_config &c, unsigned *seed = nullptr) {
+CollP<T> make_collp(const iilbm_config &c) {
   CollP<T> p;
-  p.sr = seed != nullptr && c.rounding == IILBM_ROUND_STOCHASTIC &&
-         (c.storage == IILBM_F16 || c.storage == IILBM_BF16);
-  p.seed = seed;
   p.omega = T(1.0 / c.tau);
   p.s1 = T(c.s[1]); p.s2 = T(c.s[2]); p.s4 = T(c.s[4]); p.s6 = T(c.s[6]);
   p.s7 = T(c.s[7]); p.s8 = T(c.s[8]);
@@ -226,17 +221,6 @@ __device__ inline void vst(S *p, const typename Store<S>::T *v) {
   *reinterpret_cast<Pack<S, V> *>(p) = t;
 }
 
-// vst with stochastic rounding (16-bit storage, V <= 4): value j takes byte j of the
-// 32 random bits h.
-template <typename S, int V>
-__device__ inline void vst_sr(S *p, const typename Store<S>::T *v, unsigned h) {
-  static_assert(sizeof(S) == 2 && V <= 4, "stochastic rounding of 16-bit storage");
-  Pack<S, V> t;
-#pragma unroll
-  for (int j = 0; j < V; j++) t.v[j] = Store<S>::st_sr(v[j], (h >> (8 * j)) & 0xffu);
-  *reinterpret_cast<Pack<S, V> *>(p) = t;
-}
-
 // V consecutive arithmetic values (jump / force fields), one aligned access.
 template <typename T, int V>
 __device__ inline void stT(T *p, const T *v) {
@@ -312,23 +296,12 @@ __device__ __forceinline__ void sc_scalar_block(S *__restrict__ A,
     gf[here] = T(0);
     gf[P + here] = T(0);
   }
-  // stochastic rounding: the step's seed (the block of tile 0 advances the next one)
-  const bool sr = sizeof(S) == 2 && p.sr;
-  const unsigned seed = sr ? p.seed[ODD ? 1 : 0] * 0x9E3779B9u : 0u;
-  if (sr && xb == 0 && yb == 0 && threadIdx.x == 0 && threadIdx.y == 0)
-    p.seed[ODD ? 0 : 1] = p.seed[ODD ? 1 : 0] + 1u;
 #pragma unroll
   for (int i = 0; i < 9; i++) {
     long long dst = opp(i) * P + here;
     if (ODD) {
       const bool to_wall = (cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m);
       if (!to_wall) dst = i * P + row[1 + cy(i)] + col[1 + cx(i)];
-    }
-    if constexpr (sizeof(S) == 2) {
-      if (sr) {
-        A[dst] = Store<S>::st_sr(f[i], mix32(seed ^ (unsigned)dst) & 0xffu);
-        continue;
-      }
     }
     A[dst] = Store<S>::st(f[i]);
   }
@@ -454,38 +427,15 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
     stT<T, V>(gf + P + here, z);
   }
 
-  // stochastic rounding of 16-bit storage: random bits from each element's offset and
-  // the step's seed; the block of tile 0 advances the next step's seed
-  const bool sr = sizeof(S) == 2 && p.sr;
-  const unsigned seed = sr ? p.seed[ODD ? 1 : 0] * 0x9E3779B9u : 0u;
-  if (sr && xb == 0 && yb == 0 && threadIdx.x == 0) p.seed[ODD ? 0 : 1] = p.seed[ODD ? 1 : 0] + 1u;
-  auto put = [&](long long off, const T *v) {
-    if constexpr (sizeof(S) == 2) {
-      if (sr) {
-        vst_sr<S, V>(A + off, v, mix32(seed ^ (unsigned)off));
-        return;
-      }
-    }
-    vst<S, V>(A + off, v);
-  };
-  auto put1 = [&](long long off, T v) {
-    if constexpr (sizeof(S) == 2) {
-      if (sr) {
-        A[off] = Store<S>::st_sr(v, mix32(seed ^ (unsigned)off) & 0xffu);
-        return;
-      }
-    }
-    A[off] = Store<S>::st(v);
-  };
 #pragma unroll
   for (int i = 0; i < 9; i++) {
     const bool to_wall = ODD && ((cy(i) > 0 && wall_p) || (cy(i) < 0 && wall_m));
     if (!ODD || to_wall) {
-      if (active) put(opp(i) * P + here, f[i]);
+      if (active) vst<S, V>(A + opp(i) * P + here, f[i]);
     } else {
       const long long base = i * P + row[1 + cy(i)];
       if (cx(i) == 0) {
-        if (active) put(base + x0, f[i]);
+        if (active) vst<S, V>(A + base + x0, f[i]);
       } else if (cx(i) > 0) {  // destination x + 1
         const T in = __shfl_up_sync(0xffffffffu, f[i][V - 1], 1);
         if (active) {
@@ -494,12 +444,12 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
             v[0] = in;
 #pragma unroll
             for (int j = 1; j < V; j++) v[j] = f[i][j - 1];
-            put(base + x0, v);
+            vst<S, V>(A + base + x0, v);
           } else {
 #pragma unroll
-            for (int j = 0; j < V - 1; j++) put1(base + x0 + 1 + j, f[i][j]);
+            for (int j = 0; j < V - 1; j++) A[base + x0 + 1 + j] = Store<S>::st(f[i][j]);
           }
-          if (edge_r) put1(base + xr, f[i][V - 1]);
+          if (edge_r) A[base + xr] = Store<S>::st(f[i][V - 1]);
         }
       } else {  // destination x - 1
         const T in = __shfl_down_sync(0xffffffffu, f[i][0], 1);
@@ -509,12 +459,12 @@ __device__ __forceinline__ void sc_vec_block(S *__restrict__ A,
 #pragma unroll
             for (int j = 0; j < V - 1; j++) v[j] = f[i][j + 1];
             v[V - 1] = in;
-            put(base + x0, v);
+            vst<S, V>(A + base + x0, v);
           } else {
 #pragma unroll
-            for (int j = 1; j < V; j++) put1(base + x0 + j - 1, f[i][j]);
+            for (int j = 1; j < V; j++) A[base + x0 + j - 1] = Store<S>::st(f[i][j]);
           }
-          if (lane == 0) put1(base + xl, f[i][0]);
+          if (lane == 0) A[base + xl] = Store<S>::st(f[i][0]);
         }
       }
     }

@@ -339,7 +339,14 @@ def test_mass_is_conserved_with_the_jump(orc, collision):
     assert abs(o.get_df().sum() - m0) < 1e-14
 
 
-def _uniform_normal_force_case(orc, jump, init_exact, steps):
+def _spline_points(orc, X, m):
+    """The points X(k + j / m) of the periodic spline through the markers."""
+    cx, cy = orc.spline_coeffs(X[:, 0]), orc.spline_coeffs(X[:, 1])
+    s = np.arange(len(X) * m) / m
+    return np.stack([[orc.spline_eval(cx, t) for t in s], [orc.spline_eval(cy, t) for t in s]], 1)
+
+
+def _uniform_normal_force_case(orc, jump, init_exact, steps, curve=0):
     nx = ny = 40
     R, F = 10.0, -2e-3
     X = W.circle_markers(20.3, 19.8, R, 64)
@@ -349,9 +356,11 @@ def _uniform_normal_force_case(orc, jump, init_exact, steps):
     if init_exact:
         # f_i(x) = w_i rho(x); the stored state is the streamed part f_i - [[f_i]],
         # which for uniform Fn equals w_i rho(x - e_i).  rho_out - rho_in = Fn/c_s^2.
+        # The interface is the polygon, or (curve = m) the polygon of the spline's points
         inside = np.array([[1 if (x - 20.3) ** 2 + (y - 19.8) ** 2 < (R - 1) ** 2 else 0
                             for x in range(nx)] for y in range(ny)])
-        wind = np.array([[orc.winding(X, x, y) for x in range(nx)] for y in range(ny)])
+        P = X if curve == 0 else _spline_points(orc, X, curve)
+        wind = np.array([[orc.winding(P, x, y) for x in range(nx)] for y in range(ny)])
         assert np.all(wind[inside == 1] == 1)
         rho = 1.0 - wind * F * 3
         df = np.zeros((9, ny, nx))
@@ -359,16 +368,18 @@ def _uniform_normal_force_case(orc, jump, init_exact, steps):
             df[i] = float(WT[i]) * (np.roll(rho, (ey, ex), axis=(0, 1)) - 1.0)
         o.set_df(df)
     o.set_interface(X, model=orc.PRESCRIBED, moves=False, dX=W.polygon_perimeter(X) / 64,
-                    G=F * n)
+                    G=F * n, curve=curve)
     o.step(steps)
     return o
 
 
-def test_uniform_normal_force_exact_fixed_point(orc):
+@pytest.mark.parametrize("curve", [0, 4])
+def test_uniform_normal_force_exact_fixed_point(orc, curve):
     """Section 4.1's exact solution u = 0 with a piecewise-constant pressure: with the
-    jump of Eq. 32 on the polygon's cut links, the exact state is a fixed point of the
-    II-LBM step (to rounding)."""
-    o = _uniform_normal_force_case(orc, 1, True, 30)
+    jump of Eq. 32 on the cut links of the interface (the marker polygon, or the cubic
+    spline through the markers taken on 4 chords per segment), the exact state is a
+    fixed point of the II-LBM step (to rounding)."""
+    o = _uniform_normal_force_case(orc, 1, True, 30, curve)
     r, ux, uy = o.step_macros()
     assert max(np.abs(ux).max(), np.abs(uy).max()) < 1e-16
     inside = r[20, 20]
@@ -509,3 +520,97 @@ def test_rigid_cylinder_channel_stays_bounded_at_re100(orc):
     assert res < 2e-4
     Fx = -o.markers()["G"][:, 0].sum() * w["dX"]
     assert Fx > 0
+
+
+# ------------------------------------------------------------ spline interface
+def test_spline_interpolates_and_solves_its_system(orc):
+    """The periodic spline passes through every value (v(k) = v_k), its coefficients
+    satisfy the defining cyclic system (c_{k-1} + 4 c_k + c_{k+1}) / 6 = v_k, and it
+    has period n."""
+    for n in (3, 4, 7, 64):
+        v = np.random.default_rng(n).normal(size=n)
+        c = orc.spline_coeffs(v)
+        assert np.allclose((np.roll(c, 1) + 4 * c + np.roll(c, -1)) / 6, v, rtol=0, atol=1e-14)
+        assert max(abs(orc.spline_eval(c, k) - v[k]) for k in range(n)) < 1e-14
+        for s in (0.3, 1.7):
+            assert abs(orc.spline_eval(c, s) - orc.spline_eval(c, s + n)) < 1e-13
+
+
+def test_spline_converges_at_fourth_order(orc):
+    """For samples of a smooth periodic function the spline between the samples (at
+    half-integer parameters) and its derivative converge at least at the cubic spline's
+    orders on refinement: value error ~h^4, derivative error ~h^3 (at the half-integers
+    of a uniform periodic spline the derivative is superconvergent, ~h^4)."""
+    ev, ed = [], []
+    for n in (16, 32, 64):
+        k = np.arange(n)
+        f = lambda t: np.sin(2 * np.pi * t / n) + 0.5 * np.cos(4 * np.pi * t / n)
+        df = lambda t: (2 * np.pi / n) * (np.cos(2 * np.pi * t / n)
+                                          - np.sin(4 * np.pi * t / n))
+        c = orc.spline_coeffs(f(k))
+        s = k + 0.5
+        ev.append(max(abs(orc.spline_eval(c, t) - f(t)) for t in s))
+        ed.append(max(abs(orc.spline_eval(c, t, 1) / (2 * np.pi / n)
+                          - df(t) / (2 * np.pi / n)) for t in s))
+    for e, order in ((ev, 4), (ed, 3)):
+        rates = [np.log2(e[i] / e[i + 1]) for i in range(2)]
+        assert all(r > order - 0.3 for r in rates), (e, rates)
+    assert ev[-1] < 1e-5 and ed[-1] < 1e-4
+
+
+def test_spline_normals_of_an_ellipse_converge_faster_than_the_polygons(orc):
+    """Markers equally spaced in arc length on an ellipse: the normal split's normals
+    from the spline tangent approach the ellipse's exact normals at the markers at
+    fourth order; the polygon's central difference only at second order.  (Equal steps
+    in the ellipse's angle parameter would make the central difference exactly tangent,
+    so the markers follow arc length.)"""
+    errs = {0: [], 1: []}
+    for n in (32, 64, 128):
+        a, b = 20.0, 11.0
+        X = W.ellipse_markers(0.0, 0.0, a, b, n)
+        nex = np.stack([X[:, 0] / a ** 2, X[:, 1] / b ** 2], 1)
+        nex /= np.linalg.norm(nex, axis=1, keepdims=True)
+        for curve in (0, 1):
+            _, _, nrm = orc.normal_split(X, np.zeros((n, 2)), True, 1.0, curve=curve)
+            errs[curve].append(np.abs(nrm - nex).max())
+    r_poly = np.log2(errs[0][-2] / errs[0][-1])
+    r_spl = np.log2(errs[1][-2] / errs[1][-1])
+    assert abs(r_poly - 2) < 0.3 and abs(r_spl - 4) < 0.4, (errs, r_poly, r_spl)
+    assert errs[1][-1] < 0.01 * errs[0][-1]
+
+
+def test_spline_cut_links_follow_the_curve(orc):
+    """The cut links of the spline interface (8 chords per segment) of a circle sampled
+    by 40 markers: every link whose ends lie on opposite sides of the exact circle by
+    more than the spline's distance from it carries one record, signed by the side of
+    its source (interior to exterior +1), and no link with both ends on one side does;
+    a constant Fn gives s w_i/c_s^2 Fn exactly."""
+    nx = ny = 48
+    c0, R, n, Fn = np.array([23.6, 24.3]), 11.2, 40, -1.5e-3
+    X = W.circle_markers(c0[0], c0[1], R, n)
+    cfg = orc.make_cfg(nx, ny)
+    cell, d, coef = orc.cut_links_spline(cfg, X, np.full(n, Fn), 8)
+    P = _spline_points(orc, X, 8)
+    dev = np.abs(np.linalg.norm(P - c0, axis=1) - R).max()
+    assert dev < 2e-4  # the spline hugs the circle (the polygon is 0.03 inside it)
+    E = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+    WT = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+    rec = {}
+    for cl, i, cf in zip(cell, d, coef):
+        rec.setdefault((int(cl), int(i)), []).append(cf)
+    margin = 3 * dev + 1e-9
+    for y in range(ny):
+        for x in range(nx):
+            r1 = np.hypot(x - c0[0], y - c0[1]) - R
+            for i in range(1, 9):
+                xs, ys = x - E[i][0], y - E[i][1]
+                r0 = np.hypot(xs - c0[0], ys - c0[1]) - R
+                key = (y * nx + x, i)
+                if r0 < -margin and r1 > margin:
+                    assert len(rec.get(key, [])) == 1
+                    assert abs(rec[key][0] - 3 * WT[i] * Fn) < 1e-14 * abs(Fn)
+                elif r0 > margin and r1 < -margin:
+                    assert len(rec.get(key, [])) == 1
+                    assert abs(rec[key][0] + 3 * WT[i] * Fn) < 1e-14 * abs(Fn)
+                elif (r0 > margin and r1 > margin) or (r0 < -margin and r1 < -margin):
+                    assert key not in rec

@@ -79,7 +79,11 @@ typedef struct {
   double rest_length;   /* l0 of the rest-length spring */
   double eta;           /* direct-forcing gain of Eq. 18 */
   int32_t mdf_iters;    /* direct forcing: maximum passes */
-  int32_t reserved;
+  int32_t curve;        /* interface of the jump: 0 the marker polygon (Fn linear along each
+                           segment); m = 1..16 the periodic cubic spline through the markers
+                           (end of section 3.2): normals and |X_s| from its tangent, Fn along
+                           it from the spline of the markers' Fn, crossings on m chords per
+                           segment.  Not for DIRECT (a rigid body keeps the polygon). */
   double mdf_tol;       /* direct forcing: stop when max_k |U^D - U_k| < tol (0: all passes) */
 } iilbm_interface_params;
 
@@ -226,8 +230,8 @@ int iilbm_get_macros_noalloc(iilbm_t h, double *drho, double *ux, double *uy);
  * markers for the interface phase and the interpolation, one CTA per fixed body for
  * direct forcing), replayed from CUDA graphs.  It is built from existing lattice
  * handles that share storage (F32, F16 or BF16), collision model and boundary kind,
- * have nx a multiple of 4 and the same step parity; sizes, rates, interfaces and
- * force models may differ.  The lattices stay owned by the caller.  While batched,
+ * have nx a multiple of 4 and the same step parity, and whose interfaces (if any) are
+ * marker polygons (curve = 0); sizes, rates, interfaces and force models may differ.  The lattices stay owned by the caller.  While batched,
  * iilbm_step, iilbm_set_interface, iilbm_init_equilibrium, iilbm_set_populations,
  * iilbm_set_option and iilbm_destroy on them return INVALID_ARG; read-outs run on the
  * batch's stream after its work.  Destroy the batch before its lattices.

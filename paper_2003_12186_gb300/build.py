@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libiilbm.so")
 SOURCES = ["lattice.cu", "interface.cu", "forcing.cu", "batch.cu", "mlp.cu", "api.cu"]
 HEADERS = ["iilbm_internal.cuh", "lattice_dev.cuh", "interface_dev.cuh", "forcing_dev.cuh",
-           "mlp_dev.cuh",
+           "mlp_dev.cuh", "spline_dev.cuh",
            os.path.join("..", "..", "include", "iilbm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

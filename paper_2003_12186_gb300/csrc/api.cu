@@ -52,8 +52,8 @@ int read_status(iilbm_lattice *h) {
 }
 
 void free_interface(iilbm_lattice *h) {
-  double **bufs[] = {&h->X,  &h->aux, &h->G,     &h->Fn, &h->U,
-                     &h->nrm, &h->G0, &h->Gdf, &h->Ustar, &h->Xp};
+  double **bufs[] = {&h->X,  &h->aux, &h->G,     &h->Fn,    &h->U,    &h->nrm,
+                     &h->G0, &h->Gdf, &h->Ustar, &h->Xp, &h->spl_c, &h->spl_f};
   for (double **b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
@@ -300,6 +300,10 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
     if (p->model == IILBM_SPRING_REST && !(p->rest_length > 0)) return IILBM_ERR_INVALID_ARG;
     if ((p->model == IILBM_PRESCRIBED || p->model == IILBM_DIRECT) && !aux)
       return IILBM_ERR_INVALID_ARG;
+    // the spline interface is for flexible boundaries: a directly forced (rigid) body
+    // keeps the polygon
+    if (p->curve < 0 || p->curve > 16 || (p->curve > 0 && p->model == IILBM_DIRECT))
+      return IILBM_ERR_INVALID_ARG;
   }
   int rc = clear_fields(h);
   if (rc) return rc;
@@ -325,7 +329,8 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
               cudaMalloc(&h->Fn, (size_t)n * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&h->Xq, b2) == cudaSuccess && cudaMalloc(&h->U, b2) == cudaSuccess &&
               cudaMalloc(&h->nrm, b2) == cudaSuccess && cudaMalloc(&h->Xp, b2) == cudaSuccess &&
-              cudaMalloc(&h->Xqp, b2) == cudaSuccess;
+              cudaMalloc(&h->Xqp, b2) == cudaSuccess && cudaMalloc(&h->spl_c, b2) == cudaSuccess &&
+              cudaMalloc(&h->spl_f, b2 / 2) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       free_interface(h);
@@ -438,7 +443,9 @@ namespace {
 // force iteration; a channel adds its boundary kernel.
 long long kernels_per_step(const iilbm_lattice *h) {
   long long k = 1 + (h->cfg.bc == IILBM_BC_CHANNEL ? 1 : 0);
-  if (h->nm > 0) k += pipelined(h) ? 2 : 3 + (h->ip.model == IILBM_DIRECT ? 1 : 0);
+  if (h->nm > 0)
+    k += pipelined(h) ? 2
+                      : 3 + (h->ip.model == IILBM_DIRECT ? 1 : 0) + (h->ip.curve > 0 ? 3 : 0);
   return k;
 }
 

@@ -203,6 +203,7 @@ struct iilbm_lattice {
   double *Xp;         // X, Xq of the level being interpolated, for the fused phase
   long long *Xqp;
   double *G0, *Gdf;   // direct forcing: warm start and converged force
+  double *spl_c, *spl_f;  // spline interface: coefficients of X [n][2] and of Fn [n]
   double *Ustar;      // direct forcing: interpolated velocity without the body's force
   int ws_mode;        // direct forcing: where the iteration starts (WS_*)
   const struct iilbm_mlp *mlp;  // WS_MLP: the network proposing G^(0)
@@ -232,7 +233,7 @@ namespace iilbm {
 // fused with the interpolation (direct forcing needs the next state first, so its
 // interface phase waits for the next step's force iteration).
 inline bool pipelined(const iilbm_lattice *h) {
-  return h->overlap && h->nm > 0 && h->ip.model != IILBM_DIRECT;
+  return h->overlap && h->nm > 0 && h->ip.model != IILBM_DIRECT && h->ip.curve == 0;
 }
 
 int launch_stream_collide(iilbm_lattice *h, cudaStream_t forced_stream);

@@ -48,7 +48,7 @@ class iilbm_config(C.Structure):
 class iilbm_interface_params(C.Structure):
     _fields_ = [("model", C.c_int32), ("moves", C.c_int32), ("stiffness", C.c_double),
                 ("dX", C.c_double), ("rest_length", C.c_double), ("eta", C.c_double),
-                ("mdf_iters", C.c_int32), ("reserved", C.c_int32), ("mdf_tol", C.c_double)]
+                ("mdf_iters", C.c_int32), ("curve", C.c_int32), ("mdf_tol", C.c_double)]
 
 
 _lib = None
@@ -234,8 +234,10 @@ class Lattice:
 
     # ---------------------------------------------------------------- state
     def iilbm_set_interface(self, X, model=SPRING, moves=True, stiffness=0.0, dX=1.0,
-                            rest_length=1.0, eta=2.0, mdf_iters=0, mdf_tol=0.0, aux=None):
+                            rest_length=1.0, eta=2.0, mdf_iters=0, mdf_tol=0.0, aux=None,
+                            curve=0):
         p = iilbm_interface_params()
+        p.curve = curve
         p.model, p.moves, p.stiffness, p.dX, p.rest_length = model, int(moves), stiffness, dX, \
             rest_length
         p.eta, p.mdf_iters, p.mdf_tol = eta, mdf_iters, mdf_tol

@@ -41,12 +41,16 @@ def vel_error(g, o, uref=1e-6):
     return max(rel_err(ug, uo, uref), rel_err(vg, vo, uref))
 
 
-def oracle_jump_field(orc, o):
+def oracle_jump_field(orc, o, curve=0):
     """The oracle's jump of the current state, J[i-1][y][x] (i = 1..8): its cut-link
-    records summed per link (a link crossed twice carries both records)."""
+    records summed per link (a link crossed twice carries both records); curve = m for
+    the spline interface on m chords per segment."""
     o.current_macros()  # runs the current state's interface phase
     m = o.markers()
-    cell, d, coef = orc.cut_links(o.cfg, m["X"], m["Fn"])
+    if curve > 0:
+        cell, d, coef = orc.cut_links_spline(o.cfg, m["X"], m["Fn"], curve)
+    else:
+        cell, d, coef = orc.cut_links(o.cfg, m["X"], m["Fn"])
     J = np.zeros((8, o.ny * o.nx))
     np.add.at(J, (d - 1, cell), coef)
     return J.reshape(8, o.ny, o.nx), len(cell)

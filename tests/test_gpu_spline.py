@@ -38,7 +38,7 @@ def test_spline_membrane_matches_oracle(orc, storage, curve):
     g, o = make_pair(orc, 128, 128, collision="mrt", storage=storage, tau=0.7)
     g.set_interface(X, model=iilbm.SPRING, stiffness=0.02, dX=dX, curve=curve)
     o.set_interface(X, model=orc.SPRING, kappa=0.02, dX=dX, curve=curve)
-    Jo, _ = oracle_jump_field(orc, o)
+    Jo, _ = oracle_jump_field(orc, o, curve)
     assert_jump_fields_agree(g.iilbm_get_jump(), Jo, 1e-11 if storage == "f64" else 2e-6)
     umax = 0.0
     for _ in range(3):
@@ -50,7 +50,7 @@ def test_spline_membrane_matches_oracle(orc, storage, curve):
             assert np.abs(g.get_markers()["X"] - o.markers()["X"]).max() < 1e-11
     assert umax > 1e-5  # the membrane moves
     assert vel_error(g, o, umax) < (1e-11 if storage == "f64" else 1e-5)
-    Jo, count = oracle_jump_field(orc, o)
+    Jo, count = oracle_jump_field(orc, o, curve)
     assert_jump_fields_agree(g.iilbm_get_jump(), Jo, 1e-10 if storage == "f64" else 2e-6)
     assert g.iilbm_get_cut_link_count() == count
 

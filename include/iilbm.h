@@ -47,8 +47,17 @@ enum { IILBM_SRT = 0, IILBM_MRT = 1 };
  * is FP64 for IILBM_F64 and FP32 for the others. */
 enum { IILBM_F64 = 0, IILBM_F32 = 1, IILBM_F16 = 2, IILBM_BF16 = 3 };
 /* Boundaries: periodic box; walls at y = -1/2, ny - 1/2 (halfway bounce-back) and
- * periodic x; channel = walls plus parabolic inflow at x = 0 and outflow at nx - 1. */
-enum { IILBM_BC_PERIODIC = 0, IILBM_BC_WALLS_Y = 1, IILBM_BC_CHANNEL = 2 };
+ * periodic x; channel = walls plus parabolic inflow at x = 0 and outflow at nx - 1;
+ * the boxes of the paper's section 4 (4.1: open, 4.2: no-slip walls), whose edge nodes
+ * are set every step by non-equilibrium extrapolation from their inward neighbour
+ * (diagonal at a corner): BOX_OUTFLOW rho = rho0 with the neighbour's velocity,
+ * BOX_WALL u = 0 with the neighbour's density.  A box is not batched. */
+enum { IILBM_BC_PERIODIC = 0, IILBM_BC_WALLS_Y = 1, IILBM_BC_CHANNEL = 2,
+       IILBM_BC_BOX_OUTFLOW = 3, IILBM_BC_BOX_WALL = 4 };
+/* Force term of the lattice Boltzmann equation: Guo's (Eqs. 21-22, velocity Eq. 24,
+ * the default) or the simple external force term (Eq. 16, velocity sum e f / rho), the
+ * one the paper's II-LBM uses outside its section 4.2.  Direct forcing needs Guo's. */
+enum { IILBM_FORCE_GUO = 0, IILBM_FORCE_SIMPLE = 1 };
 /* Lagrangian force models: Eq. 19 spring; rest-length spring; a prescribed force;
  * direct forcing Eq. 18 (iterated). */
 enum { IILBM_SPRING = 0, IILBM_SPRING_REST = 1, IILBM_PRESCRIBED = 2, IILBM_DIRECT = 3 };
@@ -61,7 +70,7 @@ typedef struct {
   int32_t jump;         /* 1: II-LBM (normal force through the jump of Eq. 32, tangential
                            part spread, Eq. 46); 0: IB-LBM with Guo forcing (whole G spread) */
   int32_t storage_scale_log2; /* stored value = df * 2^k (exact); 0 for F32/F64 */
-  int32_t reserved;
+  int32_t force;        /* IILBM_FORCE_GUO or IILBM_FORCE_SIMPLE */
   double tau;           /* relaxation time lambda, nu = c_s^2 (lambda - 1/2) (Eq. 7); > 0.5 */
   double s[9];          /* MRT rates in the Lallemand-Luo moment order
                            (rho, e, eps, jx, qx, jy, qy, pxx, pxy) */
@@ -100,9 +109,11 @@ int iilbm_destroy(iilbm_t h);
  * (PRESCRIBED) or the desired velocity U^D (DIRECT), else ignored (may be NULL).
  * The markers are copied; the caller keeps ownership.  Every segment must be
  * shorter than 16 lattice units and every marker at least 3 nodes from a
- * non-periodic edge.  DIRECT needs a fixed body (moves = 0), eta > 0, and a body
- * whose bounding box plus 4 nodes fits the forcing kernel's shared memory (about
- * 75 x 75 nodes in FP32, 60 x 60 in FP64).  n = 0 removes the interface.
+ * non-periodic edge.  DIRECT needs a fixed body (moves = 0), eta > 0, Guo's force term,
+ * and a body whose band (every node of a marker's 4 x 4 stencil and every candidate
+ * destination of its cut links) fits the forcing kernel's shared memory: 12 values per
+ * band node plus 29 per marker, at most 227 KB (a D = 80 cylinder of 251 markers: 200 KB
+ * in FP64, 108 KB in FP32).  n = 0 removes the interface.
  * Sections 2.2.2 (Eqs. 17-20) and 3 (Eqs. 31-32, 46-47).
  * Errors: INVALID_ARG, INTERFACE, OOM, CUDA. */
 int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n,

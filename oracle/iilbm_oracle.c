@@ -48,7 +48,9 @@ static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 
 /* ---------------------------------------------------------------- config --- */
 enum { ORC_SRT = 0, ORC_MRT = 1 };
-enum { ORC_BC_PERIODIC = 0, ORC_BC_WALLS_Y = 1, ORC_BC_CHANNEL = 2 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_WALLS_Y = 1, ORC_BC_CHANNEL = 2, ORC_BC_BOX_OUTFLOW = 3,
+       ORC_BC_BOX_WALL = 4 };
+enum { ORC_FORCE_GUO = 0, ORC_FORCE_SIMPLE = 1 };
 enum { ORC_SPRING = 0, ORC_SPRING_REST = 1, ORC_PRESCRIBED = 2, ORC_DIRECT = 3 };
 
 typedef struct {
@@ -62,6 +64,8 @@ typedef struct {
   double body_x, body_y; /* uniform body force density added to g */
   int jump;        /* 1: II-LBM (normal force through the jump, tangential spread);
                       0: IB-LBM with Guo forcing (whole G spread) */
+  int force;       /* ORC_FORCE_GUO (Eqs. 21-24) or ORC_FORCE_SIMPLE (the simple
+                      external force term of Eq. 16, u = sum e f / rho) */
 } orc_cfg;
 
 typedef struct {
@@ -215,6 +219,31 @@ void orc_cell_macros(const double *dfc, double rho0, double gx, double gy,
 void orc_collide_cell(const orc_cfg *c, const double *M, const double *Minv,
                       const double *dfc, double gx, double gy, double *out) {
   double drho, ux, uy, dfeq[9], Gt[9];
+  if (c->force == ORC_FORCE_SIMPLE) {
+    /* Eq. 16 with Eq. 14 / 15: u = sum e f / rho, the relaxation, then the simple
+     * external force term (1/c_s^2) w_i e_i . g added to every population */
+    orc_cell_macros(dfc, c->rho0, 0.0, 0.0, &drho, &ux, &uy);
+    orc_feq_shifted(drho, c->rho0, ux, uy, dfeq);
+    if (c->collision == ORC_SRT) {
+      for (int i = 0; i < 9; i++) out[i] = dfc[i] - (dfc[i] - dfeq[i]) / c->tau;
+    } else {
+      double m[9], meq[9], ms[9];
+      for (int r = 0; r < 9; r++) {
+        m[r] = meq[r] = 0;
+        for (int i = 0; i < 9; i++) {
+          m[r] += M[r * 9 + i] * dfc[i];
+          meq[r] += M[r * 9 + i] * dfeq[i];
+        }
+      }
+      for (int r = 0; r < 9; r++) ms[r] = m[r] - c->s[r] * (m[r] - meq[r]);
+      for (int i = 0; i < 9; i++) {
+        out[i] = 0;
+        for (int r = 0; r < 9; r++) out[i] += Minv[i * 9 + r] * ms[r];
+      }
+    }
+    for (int i = 0; i < 9; i++) out[i] += WT[i] * INV_CS2 * (EX[i] * gx + EY[i] * gy);
+    return;
+  }
   orc_cell_macros(dfc, c->rho0, gx, gy, &drho, &ux, &uy);
   orc_feq_shifted(drho, c->rho0, ux, uy, dfeq);
   orc_guo_source(ux, uy, gx, gy, Gt);
@@ -262,6 +291,7 @@ static int wrap_axis(int v, int n, int periodic) {
 }
 static int periodic_x(const orc_cfg *c) { return c->bc == ORC_BC_PERIODIC || c->bc == ORC_BC_WALLS_Y; }
 static int periodic_y(const orc_cfg *c) { return c->bc == ORC_BC_PERIODIC; }
+static int is_box(const orc_cfg *c) { return c->bc == ORC_BC_BOX_OUTFLOW || c->bc == ORC_BC_BOX_WALL; }
 
 /* Force spreading, Eq. 17 / Eq. 46: g(x) += sum_k P_k delta_h(x - X_k), where
  * P_k = G_k Delta X is the point force of marker k (lattice units, Delta x = 1). */
@@ -619,8 +649,10 @@ static void stream(const orc_cfg *c, const double *fs, double *out) {
     for (int y = 0; y < ny; y++)
       for (int x = 0; x < nx; x++) {
         int sx = x - EX[i], sy = y - EY[i];
-        int wy = (sy < 0 || sy >= ny) && !periodic_y(c);
-        int wx = (sx < 0 || sx >= nx) && !periodic_x(c);
+        /* a box streams as if periodic: what reaches its boundary nodes from the far
+         * side is replaced by box_bc */
+        int wy = (sy < 0 || sy >= ny) && !periodic_y(c) && !is_box(c);
+        int wx = (sx < 0 || sx >= nx) && !periodic_x(c) && !is_box(c);
         double v;
         if (wy) {
           v = fs[OPP[i] * N + y * nx + x];
@@ -656,6 +688,30 @@ static void channel_bc(const orc_cfg *c, double *df) {
     for (int i = 0; i < 9; i++)
       if (EX[i] < 0) df[i * N + y * nx + nx - 1] = df[i * N + y * nx + nx - 2];
   }
+}
+
+/* Box boundaries of the paper's section 4 setups, non-equilibrium extrapolation
+ * (Guo, Zheng & Shi): every node b on the box's edge takes
+ *   f_i(b) = f_eq_i(rho_b, u_b) + [f_i(n) - f_eq_i(rho(n), u(n))]
+ * from its inward neighbour n (b plus the inward normal; diagonal at a corner), with
+ * ORC_BC_BOX_OUTFLOW: rho_b = rho0, u_b = u(n) (an open boundary at the reference
+ * pressure, section 4.1); ORC_BC_BOX_WALL: u_b = 0, rho_b = rho(n) (no-slip walls,
+ * section 4.2).  Applied to the streamed state; rho(n), u(n) from the streamed
+ * populations of n (no force acts near the box's edge). */
+static void box_bc(const orc_cfg *c, double *df) {
+  int nx = c->nx, ny = c->ny, N = nx * ny;
+  for (int y = 0; y < ny; y++)
+    for (int x = 0; x < nx; x++) {
+      if (x != 0 && x != nx - 1 && y != 0 && y != ny - 1) continue;
+      int px = x + (x == 0) - (x == nx - 1), py = y + (y == 0) - (y == ny - 1);
+      double fn[9], r, ux, uy, eb[9], en[9];
+      for (int i = 0; i < 9; i++) fn[i] = df[i * N + py * nx + px];
+      orc_cell_macros(fn, c->rho0, 0.0, 0.0, &r, &ux, &uy);
+      orc_feq_shifted(r, c->rho0, ux, uy, en);
+      if (c->bc == ORC_BC_BOX_OUTFLOW) orc_feq_shifted(0.0, c->rho0, ux, uy, eb);
+      else orc_feq_shifted(r, c->rho0, 0.0, 0.0, eb);
+      for (int i = 0; i < 9; i++) df[i * N + y * nx + x] = eb[i] + (fn[i] - en[i]);
+    }
 }
 
 /* --------------------------------------------------------------- state ---- */
@@ -854,7 +910,10 @@ int orc_prepare(orc_state *S) {
   for (int p = 0; p < N; p++) {
     double dfc[9];
     for (int i = 0; i < 9; i++) dfc[i] = S->f[i * N + p];
-    orc_cell_macros(dfc, c->rho0, S->gx[p], S->gy[p], &S->rho[p], &S->ux[p], &S->uy[p]);
+    /* the velocity the collision uses: (sum e f + g/2) / rho (Guo), sum e f / rho (simple) */
+    double hx = c->force == ORC_FORCE_SIMPLE ? 0.0 : S->gx[p];
+    double hy = c->force == ORC_FORCE_SIMPLE ? 0.0 : S->gy[p];
+    orc_cell_macros(dfc, c->rho0, hx, hy, &S->rho[p], &S->ux[p], &S->uy[p]);
   }
   if (S->has_iface) orc_interp(c, S->I.X, S->I.n, S->ux, S->uy, S->U);
   return 0;
@@ -872,6 +931,7 @@ void orc_advance(orc_state *S) {
   }
   stream(c, S->tmp, S->df);
   if (c->bc == ORC_BC_CHANNEL) channel_bc(c, S->df);
+  if (is_box(c)) box_bc(c, S->df);
   if (S->has_iface && S->I.moves)
     for (int k = 0; k < 2 * S->I.n; k++) S->I.X[k] += S->U[k];
   S->step++;

@@ -29,7 +29,8 @@ _lib = None
 _lib_omp = None
 
 SRT, MRT = 0, 1
-BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL = 0, 1, 2
+BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL, BC_BOX_OUTFLOW, BC_BOX_WALL = 0, 1, 2, 3, 4
+FORCE_GUO, FORCE_SIMPLE = 0, 1
 SPRING, SPRING_REST, PRESCRIBED, DIRECT = 0, 1, 2, 3
 # Lallemand-Luo D2Q9 rates quoted in section 2.2.1 (s7 = s8 = 1/tau set per case)
 PAPER_MRT_RATES = (0.0, 1.63, 1.14, 0.0, 1.92, 0.0, 1.92, None, None)
@@ -60,7 +61,7 @@ class _Cfg(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("collision", C.c_int), ("tau", C.c_double),
                 ("s", C.c_double * 9), ("rho0", C.c_double), ("bc", C.c_int),
                 ("u_max", C.c_double), ("body_x", C.c_double), ("body_y", C.c_double),
-                ("jump", C.c_int)]
+                ("jump", C.c_int), ("force", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -145,11 +146,12 @@ def _f64(a) -> np.ndarray:
 
 
 def make_cfg(nx, ny, collision=SRT, tau=0.8, s=None, rho0=1.0, bc=BC_PERIODIC, u_max=0.0,
-             body=(0.0, 0.0), jump=1) -> _Cfg:
+             body=(0.0, 0.0), jump=1, force=FORCE_GUO) -> _Cfg:
     c = _Cfg()
     c.nx, c.ny, c.collision, c.tau, c.rho0, c.bc, c.u_max = nx, ny, collision, tau, rho0, bc, u_max
     c.body_x, c.body_y = body
     c.jump = jump
+    c.force = force
     rates = mrt_rates(tau) if s is None else s
     for i in range(9):
         c.s[i] = rates[i]

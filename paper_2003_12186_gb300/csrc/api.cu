@@ -175,8 +175,8 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
   if (c.nx < 4 || c.ny < 4 || c.nx > 32768 || c.ny > 32768) return IILBM_ERR_INVALID_ARG;
   if (c.collision != IILBM_SRT && c.collision != IILBM_MRT) return IILBM_ERR_INVALID_ARG;
   if (!storage_bytes(c.storage)) return IILBM_ERR_INVALID_ARG;
-  if (c.bc != IILBM_BC_PERIODIC && c.bc != IILBM_BC_WALLS_Y && c.bc != IILBM_BC_CHANNEL)
-    return IILBM_ERR_INVALID_ARG;
+  if (c.bc < IILBM_BC_PERIODIC || c.bc > IILBM_BC_BOX_WALL) return IILBM_ERR_INVALID_ARG;
+  if (c.force != IILBM_FORCE_GUO && c.force != IILBM_FORCE_SIMPLE) return IILBM_ERR_INVALID_ARG;
   if (c.bc == IILBM_BC_CHANNEL && !(std::abs(c.u_max) < 0.5)) return IILBM_ERR_INVALID_ARG;
   if (!(c.tau > 0.5) || !(c.rho0 > 0) || std::abs(c.storage_scale_log2) > 30)
     return IILBM_ERR_INVALID_ARG;
@@ -204,7 +204,10 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
   g.pitch = (c.nx + (c.bc == IILBM_BC_CHANNEL ? 2 : 0) + 31) / 32 * 32;
   g.plane = (long long)g.pitch * c.ny;
   g.ntx = (c.nx + TILE_X - 1) / TILE_X;
-  g.bc = c.bc;
+  const bool box = c.bc == IILBM_BC_BOX_OUTFLOW || c.bc == IILBM_BC_BOX_WALL;
+  g.bc = box ? IILBM_BC_PERIODIC : c.bc;  // a box streams periodically; its edge is rewritten
+  h->igeom = g;
+  if (box) h->igeom.bc = IILBM_BC_CHANNEL;  // for the interface: bounded in x and in y
   h->ntiles = g.ntx * ((c.ny + TILE_Y - 1) / TILE_Y);
   h->sbytes = storage_bytes(c.storage);
   h->tbytes = c.storage == IILBM_F64 ? 8 : 4;
@@ -304,6 +307,8 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
     // keeps the polygon
     if (p->curve < 0 || p->curve > 16 || (p->curve > 0 && p->model == IILBM_DIRECT))
       return IILBM_ERR_INVALID_ARG;
+    // direct forcing is built on Guo's half-force velocity (section 3, reading 13)
+    if (p->model == IILBM_DIRECT && h->cfg.force != IILBM_FORCE_GUO) return IILBM_ERR_INVALID_ARG;
   }
   int rc = clear_fields(h);
   if (rc) return rc;
@@ -364,8 +369,8 @@ int iilbm_set_interface(iilbm_t h, const double *xy, int32_t n, const iilbm_inte
     bad = !std::isfinite(x) || !std::isfinite(y) || std::abs(x) > MAX_COORD ||
           std::abs(y) > MAX_COORD || !(dx * dx + dy * dy < MAX_SEGMENT * MAX_SEGMENT) ||
           (dx == 0 && dy == 0);
-    if (h->cfg.bc != IILBM_BC_PERIODIC) bad = bad || y < 3.0 || y > h->cfg.ny - 4.0;
-    if (h->cfg.bc == IILBM_BC_CHANNEL) bad = bad || x < 3.0 || x > h->cfg.nx - 4.0;
+    if (h->igeom.bc != IILBM_BC_PERIODIC) bad = bad || y < 3.0 || y > h->cfg.ny - 4.0;
+    if (h->igeom.bc == IILBM_BC_CHANNEL) bad = bad || x < 3.0 || x > h->cfg.nx - 4.0;
   }
   if (bad) {
     std::free(hx);
@@ -442,7 +447,10 @@ namespace {
 // (pipelined), or the interpolation, the interface kernel and, for direct forcing, the
 // force iteration; a channel adds its boundary kernel.
 long long kernels_per_step(const iilbm_lattice *h) {
-  long long k = 1 + (h->cfg.bc == IILBM_BC_CHANNEL ? 1 : 0);
+  long long k = 1 + (h->cfg.bc == IILBM_BC_CHANNEL || h->cfg.bc == IILBM_BC_BOX_OUTFLOW ||
+                             h->cfg.bc == IILBM_BC_BOX_WALL
+                         ? 1
+                         : 0);
   if (h->nm > 0)
     k += pipelined(h) ? 2
                       : 3 + (h->ip.model == IILBM_DIRECT ? 1 : 0) + (h->ip.curve > 0 ? 3 : 0);

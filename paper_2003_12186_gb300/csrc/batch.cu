@@ -487,7 +487,7 @@ int iilbm_create_batch(iilbm_batch_t *out, const iilbm_t *lattices, int32_t coun
   for (int s = 0; s < count; s++) {
     iilbm_lattice *h = lattices[s];
     if (!h || h->in_batch || h->cfg.storage == IILBM_F64 || h->cfg.storage != h0->cfg.storage ||
-        h->geom.nx % 4 != 0 || (h->nm > 0 && h->ip.curve > 0) ||
+        h->geom.nx % 4 != 0 || (h->nm > 0 && h->ip.curve > 0) || h->cfg.bc != h->geom.bc ||
         h->cfg.collision != h0->cfg.collision || h->cfg.bc != h0->cfg.bc ||
         h->device != h0->device || ((h->step ^ h0->step) & 1))
       return IILBM_ERR_INVALID_ARG;

@@ -123,7 +123,7 @@ void free_direct_forcing(iilbm_lattice *h) {
 // INTERFACE if the iteration's shared memory would exceed 227 KB.
 int setup_direct_forcing(iilbm_lattice *h, const double *hx) {
   free_direct_forcing(h);
-  const Geom &g = h->geom;
+  const Geom &g = h->igeom;  // the interface's view: a box is bounded on every side
   const int n = h->nm;
   std::vector<int> keys;
   keys.reserve(16 * (size_t)n * 2);

@@ -154,7 +154,9 @@ __device__ inline long long aa_loc(const Geom &g, bool odd, int i, int x, int y)
 // ------------------------------------------------------------------ handle
 struct iilbm_lattice {
   iilbm_config cfg;
-  iilbm::Geom geom;
+  iilbm::Geom geom;   // the populations' geometry (a box streams periodically)
+  iilbm::Geom igeom;  // the interface's: as geom, but a box is bounded on every side (its
+                      // bc reads as a channel's: clipped in x and in y)
   int device;
   cudaStream_t stream;
   bool own_stream;

@@ -50,13 +50,13 @@ static void launch_interface_bc(iilbm_lattice *h, int buf, cudaStream_t s) {
   const InterpIn<T> in{(const T *)h->uf, h->Xp, h->Xqp, h->U, h->ip.moves};
   const int blocks = (n + SEGS_PER_BLOCK - 1) / SEGS_PER_BLOCK;
   k_interface<T, INTERP, BC><<<blocks, 32 * IFACE_WARPS, 0, s>>>(
-      h->X, aux, n, h->ip, h->cfg.jump, GeomC<BC>(h->geom), (T *)h->gb[buf], (T *)h->Jb[buf], tb,
+      h->X, aux, n, h->ip, h->cfg.jump, GeomC<BC>(h->igeom), (T *)h->gb[buf], (T *)h->Jb[buf], tb,
       h->G, h->Fn, h->nrm, h->Xq, h->d_status, in);
 }
 
 template <typename T, bool INTERP>
 static int launch_interface(iilbm_lattice *h, int buf, cudaStream_t s) {
-  switch (h->geom.bc) {
+  switch (h->igeom.bc) {
     case IILBM_BC_PERIODIC: launch_interface_bc<T, INTERP, IILBM_BC_PERIODIC>(h, buf, s); break;
     case IILBM_BC_WALLS_Y: launch_interface_bc<T, INTERP, IILBM_BC_WALLS_Y>(h, buf, s); break;
     default: launch_interface_bc<T, INTERP, IILBM_BC_CHANNEL>(h, buf, s);
@@ -138,17 +138,17 @@ static void launch_spline_bc(iilbm_lattice *h, int buf, cudaStream_t s) {
                    h->d_tiles_total};
   k_spline_coeffs<<<(2 * n + 127) / 128, 128, 0, s>>>(h->X, n, 2, 2, h->spl_c);
   k_spline_markers<T, BC><<<(n + 127) / 128, 128, 0, s>>>(
-      h->X, aux, n, h->ip, h->cfg.jump, GeomC<BC>(h->geom), (T *)h->gb[buf], h->G, h->Fn, h->nrm,
+      h->X, aux, n, h->ip, h->cfg.jump, GeomC<BC>(h->igeom), (T *)h->gb[buf], h->G, h->Fn, h->nrm,
       h->Xq, h->d_status, h->spl_c);
   k_spline_coeffs<<<(n + 127) / 128, 128, 0, s>>>(h->Fn, n, 1, 1, h->spl_f);
   const long long threads = 32LL * n * m;
   k_spline_segments<T, BC><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
-      h->spl_c, h->spl_f, n, m, h->cfg.jump, GeomC<BC>(h->geom), (T *)h->Jb[buf], tb);
+      h->spl_c, h->spl_f, n, m, h->cfg.jump, GeomC<BC>(h->igeom), (T *)h->Jb[buf], tb);
 }
 
 template <typename T>
 static int launch_spline(iilbm_lattice *h, int buf, cudaStream_t s) {
-  switch (h->geom.bc) {
+  switch (h->igeom.bc) {
     case IILBM_BC_PERIODIC: launch_spline_bc<T, IILBM_BC_PERIODIC>(h, buf, s); break;
     case IILBM_BC_WALLS_Y: launch_spline_bc<T, IILBM_BC_WALLS_Y>(h, buf, s); break;
     default: launch_spline_bc<T, IILBM_BC_CHANNEL>(h, buf, s);

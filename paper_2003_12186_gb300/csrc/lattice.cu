@@ -102,14 +102,16 @@ __device__ inline void node_macros(const S *A, const typename Store<S>::T *Jf,
   for (int i = 0; i < 9; i++) f[i] = Store<S>::ld(A[aa_loc(geo, odd, i, x, y)]) * p.inv_scale;
 #pragma unroll
   for (int i = 1; i < 9; i++) f[i] += Jf[(i - 1) * geo.plane + here];
+  // the collision's velocity: (j + g/2) / rho with Guo's force, j / rho with the simple one
+  const T h = p.he ? T(0) : T(0.5);
   const T gx = p.bodyx + gf[here], gy = p.bodyy + gf[geo.plane + here];
   const T d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
   const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
   const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
   const T ir = T(1) / (p.rho0 + d);
   drho = double(d);
-  ux = double((jx + T(0.5) * gx) * ir);
-  uy = double((jy + T(0.5) * gy) * ir);
+  ux = double((jx + h * gx) * ir);
+  uy = double((jy + h * gy) * ir);
 }
 
 // Velocity interpolation U_k = sum_x u(x) delta_h(x - X_k) (Eq. 20), one thread per
@@ -203,6 +205,27 @@ __global__ void k_channel_bc(S *A, const Geom geo, const CollP<typename Store<S>
   if (y < geo.ny) channel_bc_row<S>(A, geo, p, odd, u_max, y);
 }
 
+// The edge of a box (the outflow or walled boxes of section 4), one thread per edge node:
+// the bottom and top rows, then the left and right columns without their corners.
+template <typename S>
+__global__ void k_box_bc(S *A, const Geom geo, const CollP<typename Store<S>::T> p, bool odd,
+                         bool outflow) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nx = geo.nx, ny = geo.ny;
+  int x, y;
+  if (t < 2 * nx) {
+    x = t % nx;
+    y = t < nx ? 0 : ny - 1;
+  } else if (t < 2 * nx + 2 * (ny - 2)) {
+    const int r = t - 2 * nx;
+    x = r < ny - 2 ? 0 : nx - 1;
+    y = 1 + r % (ny - 2);
+  } else {
+    return;
+  }
+  box_bc_node<S>(A, geo, p, odd, outflow, x, y);
+}
+
 // ------------------------------------------------------------------ dispatch
 template <typename F>
 static int dispatch_storage(int storage, F &&f) {
@@ -284,22 +307,29 @@ int launch_interp(iilbm_lattice *h, cudaStream_t s) {
   if (h->nm == 0) return IILBM_OK;
   const int blocks = (h->nm + 127) / 128;
   if (h->cfg.storage == IILBM_F64)
-    k_interp<double><<<blocks, 128, 0, s>>>((const double *)h->uf, h->geom, h->X, h->Xq, h->nm,
+    k_interp<double><<<blocks, 128, 0, s>>>((const double *)h->uf, h->igeom, h->X, h->Xq, h->nm,
                                             h->U, h->ip.moves);
   else
-    k_interp<float><<<blocks, 128, 0, s>>>((const float *)h->uf, h->geom, h->X, h->Xq, h->nm,
+    k_interp<float><<<blocks, 128, 0, s>>>((const float *)h->uf, h->igeom, h->X, h->Xq, h->nm,
                                            h->U, h->ip.moves);
   return last_error();
 }
 
 int launch_channel_bc(iilbm_lattice *h) {
-  if (h->geom.bc != IILBM_BC_CHANNEL) return IILBM_OK;
+  const bool box = h->cfg.bc == IILBM_BC_BOX_OUTFLOW || h->cfg.bc == IILBM_BC_BOX_WALL;
+  if (h->geom.bc != IILBM_BC_CHANNEL && !box) return IILBM_OK;
   const bool odd = h->step & 1;  // the state just produced
   return dispatch_storage(h->cfg.storage, [&](auto *tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     using T = typename Store<S>::T;
-    k_channel_bc<S><<<(h->geom.ny + 127) / 128, 128, 0, h->stream>>>(
-        (S *)h->A, h->geom, make_collp<T>(h->cfg), odd, h->cfg.u_max);
+    if (box) {
+      const int edge = 2 * h->geom.nx + 2 * (h->geom.ny - 2);
+      k_box_bc<S><<<(edge + 127) / 128, 128, 0, h->stream>>>(
+          (S *)h->A, h->geom, make_collp<T>(h->cfg), odd, h->cfg.bc == IILBM_BC_BOX_OUTFLOW);
+    } else {
+      k_channel_bc<S><<<(h->geom.ny + 127) / 128, 128, 0, h->stream>>>(
+          (S *)h->A, h->geom, make_collp<T>(h->cfg), odd, h->cfg.u_max);
+    }
     return last_error();
   });
 }

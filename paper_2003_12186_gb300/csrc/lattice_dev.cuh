@@ -19,11 +19,13 @@ struct CollP {
   T rho0;
   T scale, inv_scale;        // storage scale 2^k and 2^-k
   T bodyx, bodyy;
+  int he;                    // the simple force term (Eq. 16) instead of Guo's (Eqs. 21-24)
 };
 
 template <typename T>
 CollP<T> make_collp(const iilbm_config &c) {
   CollP<T> p;
+  p.he = c.force == IILBM_FORCE_SIMPLE;
   p.omega = T(1.0 / c.tau);
   p.s1 = T(c.s[1]); p.s2 = T(c.s[2]); p.s4 = T(c.s[4]); p.s6 = T(c.s[6]);
   p.s7 = T(c.s[7]); p.s8 = T(c.s[8]);
@@ -48,7 +50,9 @@ CollP<T> make_collp(const iilbm_config &c) {
 // times 2^k, bit for bit, with no conversion multiply per population.  Returns the
 // unscaled drho; ux_out, uy_out are the unscaled velocity.
 // BODY = false: the force is zero (lean tiles without a body force) and Guo's source
-// terms are left out.
+// terms are left out.  With p.he (the simple external force term of Eq. 16) the
+// velocity is j / rho, the relaxation has no source, and (1/c_s^2) w_i e_i . g is added
+// to every population afterwards.
 // PP is CollP<T>, or a volatile view of one in shared memory (the batched kernels:
 // every rate is then re-read where it is used instead of held in a register).
 template <typename T, int COLL, typename PP = CollP<T>, bool BODY = true>
@@ -60,7 +64,8 @@ __device__ __forceinline__ T collide(T f[9], T gx, T gy, const PP &p, T &ux_out,
   const T drho = drs * p.inv_scale;
   const T rho = p.rho0 + drho;
   const T irs = (T(1) / rho) * p.inv_scale;                   // 1 / (2^k rho)
-  const T jxh = BODY ? jx + T(0.5) * gx : jx, jyh = BODY ? jy + T(0.5) * gy : jy;  // rho u
+  const bool guo = BODY && !p.he;
+  const T jxh = guo ? jx + T(0.5) * gx : jx, jyh = guo ? jy + T(0.5) * gy : jy;  // rho u
   const T ux = jxh * irs, uy = jyh * irs;
   ux_out = ux;
   uy_out = uy;
@@ -76,7 +81,8 @@ __device__ __forceinline__ T collide(T f[9], T gx, T gy, const PP &p, T &ux_out,
       f[i] = f[i] - om * (f[i] - feq);
       if (BODY) {
         const T eg = T(cx(i)) * gx + T(cy(i)) * gy;
-        f[i] += fo * (wt<T>(i) * (T(3) * (eg - ug) + T(9) * eu * eg));
+        if (guo) f[i] += fo * (wt<T>(i) * (T(3) * (eg - ug) + T(9) * eu * eg));
+        else f[i] += wt<T>(i) * (T(3) * eg);
       }
     }
   } else {
@@ -99,7 +105,7 @@ __device__ __forceinline__ T collide(T f[9], T gx, T gy, const PP &p, T &ux_out,
     T d1 = -p.s1 * (m1 - e1), d2 = -p.s2 * (m2 - e2), d4 = -p.s4 * (m4 - e4);
     T d6 = -p.s6 * (m6 - e6), d7 = -p.s7 * (m7 - e7), d8 = -p.s8 * (m8 - e8);
     T a3 = T(0), a5 = T(0);
-    if (BODY) {
+    if (guo) {
       // moments of Guo's source
       const T ug = ux * gx + uy * gy;
       const T F1 = T(6) * ug, F2 = T(-6) * ug, F4 = -gx, F6 = -gy;
@@ -129,6 +135,18 @@ __device__ __forceinline__ T collide(T f[9], T gx, T gy, const PP &p, T &ux_out,
       f[6] += c - (a3 + a4) + (a5 + a6) - a8;
       f[7] += c - (a3 + a4) - (a5 + a6) + a8;
       f[8] += c + (a3 + a4) - (a5 + a6) - a8;
+      if (!guo) {  // the simple force term, (1/c_s^2) w_i e_i . g
+        const T ax = gx * T(1.0 / 3), ay = gy * T(1.0 / 3);
+        const T dx = gx * T(1.0 / 12), dy = gy * T(1.0 / 12);
+        f[1] += ax;
+        f[2] += ay;
+        f[3] -= ax;
+        f[4] -= ay;
+        f[5] += dx + dy;
+        f[6] += dy - dx;
+        f[7] -= dx + dy;
+        f[8] += dx - dy;
+      }
     } else {
       f[1] += b - T(2) * a4 + a7;
       f[2] += b - T(2) * a6 - a7;
@@ -531,6 +549,38 @@ __device__ __forceinline__ void channel_bc_row(S *A, const Geom &geo,
 #pragma unroll
   for (int q = 0; q < 3; q++)
     A[aa_loc(geo, odd, out[q], geo.nx - 1, y)] = A[aa_loc(geo, odd, out[q], geo.nx - 2, y)];
+}
+
+// Box boundary node (x, y) on the streamed state, non-equilibrium extrapolation from its
+// inward neighbour n (the diagonal one at a corner):
+//   f_i = f_eq_i(rho_b, u_b) + [f_i(n) - f_eq_i(rho(n), u(n))],
+// outflow: rho_b = rho0, u_b = u(n); wall: u_b = 0, rho_b = rho(n).  The box streams
+// periodically (geo.bc periodic), so what the edge received from the far side is
+// replaced here.
+template <typename S>
+__device__ __forceinline__ void box_bc_node(S *A, const Geom &geo,
+                                            const CollP<typename Store<S>::T> &p, bool odd,
+                                            bool outflow, int x, int y) {
+  using T = typename Store<S>::T;
+  const int px = x + (x == 0) - (x == geo.nx - 1), py = y + (y == 0) - (y == geo.ny - 1);
+  T f[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) f[i] = Store<S>::ld(A[aa_loc(geo, odd, i, px, py)]) * p.inv_scale;
+  const T d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const T rho = p.rho0 + d;
+  const T ux = ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7])) / rho;
+  const T uy = ((f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8])) / rho;
+  const T u2 = ux * ux + uy * uy;
+  const T db = outflow ? T(0) : d, rb = p.rho0 + db;
+  const T ubx = outflow ? ux : T(0), uby = outflow ? uy : T(0);
+  const T ub2 = ubx * ubx + uby * uby;
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    const T eu = T(cx(i)) * ux + T(cy(i)) * uy, eb = T(cx(i)) * ubx + T(cy(i)) * uby;
+    const T feq_n = wt<T>(i) * (d + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * u2));
+    const T feq_b = wt<T>(i) * (db + rb * (T(3) * eb + T(4.5) * eb * eb - T(1.5) * ub2));
+    A[aa_loc(geo, odd, i, x, y)] = Store<S>::st((feq_b + (f[i] - feq_n)) * p.scale);
+  }
 }
 
 }  // namespace iilbm

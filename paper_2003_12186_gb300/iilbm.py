@@ -22,7 +22,8 @@ OK = 0
  ERR_CAPACITY, ERR_NO_DEVICE) = range(-1, -9, -1)
 SRT, MRT = 0, 1
 F64, F32, F16, BF16 = 0, 1, 2, 3
-BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL = 0, 1, 2
+BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL, BC_BOX_OUTFLOW, BC_BOX_WALL = 0, 1, 2, 3, 4
+FORCE_GUO, FORCE_SIMPLE = 0, 1
 SPRING, SPRING_REST, PRESCRIBED, DIRECT = 0, 1, 2, 3
 OPT_CUDA_GRAPH, OPT_OVERLAP, OPT_VECTOR_KERNEL, OPT_FORCED_BLOCKS = 0, 1, 2, 3
 WS_GIVEN, WS_PREVIOUS, WS_MLP = 0, 1, 2
@@ -40,7 +41,7 @@ class IilbmError(RuntimeError):
 class iilbm_config(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("collision", C.c_int32),
                 ("storage", C.c_int32), ("bc", C.c_int32), ("jump", C.c_int32),
-                ("storage_scale_log2", C.c_int32), ("reserved", C.c_int32),
+                ("storage_scale_log2", C.c_int32), ("force", C.c_int32),
                 ("tau", C.c_double), ("s", C.c_double * 9), ("rho0", C.c_double),
                 ("u_max", C.c_double), ("body", C.c_double * 2), ("stream", C.c_void_p)]
 
@@ -192,7 +193,7 @@ class Lattice:
 
     def __init__(self, nx, ny, collision=MRT, storage=F32, tau=0.8, s=None, rho0=1.0,
                  bc=BC_PERIODIC, jump=1, u_max=0.0, body=(0.0, 0.0), stream=None,
-                 storage_scale_log2=None):
+                 storage_scale_log2=None, force=FORCE_GUO):
         L = load()
         cfg = iilbm_config()
         cfg.nx, cfg.ny = nx, ny
@@ -202,6 +203,7 @@ class Lattice:
         if storage_scale_log2 is None:
             storage_scale_log2 = {F64: 0, F32: 0, F16: 12, BF16: 0}[cfg.storage]
         cfg.storage_scale_log2 = storage_scale_log2
+        cfg.force = force
         cfg.tau, cfg.rho0, cfg.u_max = tau, rho0, u_max
         rates = s if s is not None else [0.0, 1.63, 1.14, 0.0, 1.92, 0.0, 1.92, 1 / tau, 1 / tau]
         for i in range(9):

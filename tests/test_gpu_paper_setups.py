@@ -1,0 +1,191 @@
+"""The paper's own setups (section 4): the boxes bounded by non-equilibrium extrapolation
+(4.1 open, 4.2 walled), the simple external force term (Eq. 16), and section 4.1's
+uniform normal force on a circle, whose exact velocity is zero -- the II-LBM's error and
+its order against the IB-LBM's (Table 1).  CUDA path against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2003_12186_gb300 import iilbm
+from paper_2003_12186_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    iilbm.load()
+
+
+BOX = {"outflow": (iilbm.BC_BOX_OUTFLOW, "BC_BOX_OUTFLOW"),
+       "wall": (iilbm.BC_BOX_WALL, "BC_BOX_WALL")}
+
+
+@pytest.mark.parametrize("box", ["outflow", "wall"])
+@pytest.mark.parametrize("collision", ["srt", "mrt"])
+def test_box_matches_oracle_fp64(orc, box, collision):
+    """A box's edge rewritten every step from a random state: populations equal the
+    oracle's to 1e-15 at both step parities."""
+    nx, ny, tau = 37, 26, 0.7
+    s = W.mrt_rates(tau) if collision == "mrt" else [1 / tau] * 9
+    c = iilbm.MRT if collision == "mrt" else iilbm.SRT
+    g = iilbm.Lattice(nx, ny, collision=c, storage="f64", tau=tau, s=s, bc=BOX[box][0])
+    o = orc.Oracle(nx, ny, collision=orc.MRT if collision == "mrt" else orc.SRT, tau=tau, s=s,
+                   bc=getattr(orc, BOX[box][1]))
+    df = W.random_df(nx, ny, 1e-3, 5)
+    g.set_populations(df)
+    o.set_df(df)
+    for n in (1, 1, 3, 20):
+        g.step(n)
+        o.step(n)
+        assert np.abs(g.get_populations() - o.get_df()).max() < 1e-15
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("collision", ["srt", "mrt"])
+def test_simple_force_membrane_matches_oracle(orc, storage, collision):
+    """A moving membrane (IB-LBM: the whole force spread, so the force term acts) with the
+    simple external force term, in a walled box: FP64 populations to 1e-13, FP32
+    velocity to 1e-5."""
+    nx, ny, tau, n = 64, 60, 0.8, 60
+    s = W.mrt_rates(tau) if collision == "mrt" else [1 / tau] * 9
+    c = iilbm.MRT if collision == "mrt" else iilbm.SRT
+    X = W.ellipse_markers(31.7, 30.2, 14.0, 9.0, n)
+    dX = W.polygon_perimeter(X) / n
+    g = iilbm.Lattice(nx, ny, collision=c, storage=storage, tau=tau, s=s, bc=iilbm.BC_BOX_WALL,
+                      force=iilbm.FORCE_SIMPLE, jump=0)
+    o = orc.Oracle(nx, ny, collision=orc.MRT if collision == "mrt" else orc.SRT, tau=tau, s=s,
+                   bc=orc.BC_BOX_WALL, force=orc.FORCE_SIMPLE, jump=0)
+    g.set_interface(X, model=iilbm.SPRING, stiffness=0.02, dX=dX)
+    o.set_interface(X, model=orc.SPRING, kappa=0.02, dX=dX)
+    for _ in range(3):
+        g.step(30)
+        o.step(30)
+    if storage == "f64":
+        assert np.abs(g.get_populations() - o.get_df()).max() < 1e-13
+    _, ug, vg = g.get_macros()
+    _, uo, vo = o.current_macros()
+    ref = max(np.abs(uo).max(), np.abs(vo).max())
+    assert ref > 1e-5
+    tol = 1e-11 if storage == "f64" else 1e-5
+    assert max(np.abs(ug - uo).max(), np.abs(vg - vo).max()) < tol * ref
+
+
+# The circle's centre off the lattice's nodes (the box's centre plus this offset), so that
+# no node lies on the circle, where the exact solution's pressure is not defined.
+CENTRE_OFFSET = (0.37, 0.21)
+
+
+def exact_state(N, D, F):
+    """The exact solution's populations: u = 0, rho = rho0 + F / c_s^2 inside the circle
+    (radius D/2 about the box's centre) and rho0 outside, as the stored (streamed)
+    state f_i(x) = w_i rho(x - e_i) -- the jump added on the cut links then restores
+    w_i rho(x) wherever the discrete interface and the circle agree."""
+    E = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+    WT = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+    yy, xx = np.mgrid[0:N, 0:N]
+    cx, cy = D + CENTRE_OFFSET[0], D + CENTRE_OFFSET[1]
+    drho = np.where((xx - cx) ** 2 + (yy - cy) ** 2 < (D / 2.0) ** 2, 3.0 * F, 0.0)
+    return np.stack([WT[i] * np.roll(drho, (ey, ex), axis=(0, 1)) for i, (ex, ey) in enumerate(E)])
+
+
+def uniform_normal_force(D, jump, lib="gpu", orc=None, storage="f64", curve=0, spacing=1.0):
+    """Section 4.1: a circle of diameter D at the centre of [-D, D]^2 (a (2D+1)^2 box with
+    open edges), Re = 100, nu = 0.05 (tau 0.65), U = nu Re / D, a uniform normal force of
+    magnitude rho U^2 per unit length pointing inwards, markers about one lattice unit
+    apart, the simple force term.  Reading: the run starts from the exact solution (u = 0,
+    the piecewise-constant pressure of the exact circle), so the velocity at t_end = D / U
+    measures how well the discrete interface holds it.  Returns the lattice (or oracle)
+    after t_end steps and U."""
+    N = 2 * D + 1
+    nu, Re = 0.05, 100.0
+    U = nu * Re / D
+    F = U * U
+    tau = 0.5 + 3 * nu
+    n = int(round(math.pi * D / spacing))
+    c0 = np.array([D + CENTRE_OFFSET[0], D + CENTRE_OFFSET[1]])
+    X = W.circle_markers(c0[0], c0[1], D / 2.0, n)
+    nrm = (X - c0) / np.linalg.norm(X - c0, axis=1, keepdims=True)
+    G = -F * nrm
+    dX = W.polygon_perimeter(X) / n
+    steps = int(round(D / U))
+    s = W.mrt_rates(tau)
+    df = exact_state(N, D, F)
+    if lib == "gpu":
+        g = iilbm.Lattice(N, N, collision=iilbm.MRT, storage=storage, tau=tau, s=s,
+                          bc=iilbm.BC_BOX_OUTFLOW, force=iilbm.FORCE_SIMPLE, jump=jump)
+        g.set_populations(df)
+        g.set_interface(X, model=iilbm.PRESCRIBED, moves=False, dX=dX, aux=G, curve=curve)
+    else:
+        g = orc.Oracle(N, N, collision=orc.MRT, tau=tau, s=s, bc=orc.BC_BOX_OUTFLOW,
+                       force=orc.FORCE_SIMPLE, jump=jump)
+        g.set_df(df)
+        g.set_interface(X, model=orc.PRESCRIBED, moves=False, dX=dX, G=G, curve=curve)
+    g.step(steps)
+    return g, U
+
+
+def velocity_errors(g, U, oracle=False):
+    if oracle:
+        _, ux, uy = g.current_macros()
+    else:
+        _, ux, uy = g.get_macros()
+    l2 = math.sqrt(float(np.mean(ux ** 2 + uy ** 2))) / U
+    linf = float(max(np.abs(ux).max(), np.abs(uy).max())) / U
+    return l2, linf
+
+
+def test_uniform_normal_force_d20_matches_oracle(orc):
+    """Section 4.1 at D = 20 (41 x 41 box, 80 steps) in both methods: the GPU's velocity
+    field equals the oracle's to 1e-12 of U."""
+    for jump in (1, 0):
+        g, U = uniform_normal_force(20, jump)
+        o, _ = uniform_normal_force(20, jump, "oracle", orc)
+        _, ug, vg = g.get_macros()
+        _, uo, vo = o.current_macros()
+        assert max(np.abs(ug - uo).max(), np.abs(vg - vo).max()) < 1e-12 * U
+
+
+def test_table1_uniform_normal_force_errors_and_orders():
+    """Table 1's comparison on D = 20, 40, 80, 160: the velocity error (exact solution
+    u = 0) at t_end = D / U in L2 and L-infinity, normalised by U.  The II-LBM's jump of a
+    uniform normal force is exact, so it keeps the exact state wherever the discrete
+    interface classifies the nodes as the circle does: with markers one lattice unit apart
+    its error is at rounding level or set by the few nodes that fall between the marker
+    polygon and the circle, and stays orders of magnitude below the IB-LBM's (the same
+    force spread by the delta kernel, which falls at about first order; the paper: IB
+    0.95-1.40, II ~2.0 from errors of 1e-6 .. 3e-8).  With markers two lattice units
+    apart (the spacing section 4.2 gives the II-LBM) the polygon sits visibly inside the
+    circle and the cubic spline on 4 chords per segment holds the exact state better.
+    Printed with -s."""
+    Ds = (20, 40, 80, 160)
+    rows = {}
+    for D in Ds:
+        for key, kw in (("II", dict(jump=1)), ("IB", dict(jump=0)),
+                        ("II-polygon-2", dict(jump=1, spacing=2.0)),
+                        ("II-spline-2", dict(jump=1, spacing=2.0, curve=4))):
+            g, U = uniform_normal_force(D, **kw)
+            rows[(D, key)] = velocity_errors(g, U)
+    for key in ("II", "IB", "II-polygon-2", "II-spline-2"):
+        line = []
+        for k, D in enumerate(Ds):
+            l2, li = rows[(D, key)]
+            order = ""
+            if k:
+                p2 = rows[(Ds[k - 1], key)][0]
+                if p2 > 1e-13 and l2 > 1e-13:
+                    order = f" (order {math.log2(p2 / l2):.2f})"
+            line.append(f"D={D}: L2 {l2:.3e} Linf {li:.3e}{order}")
+        print(f"table1 {key}: " + "; ".join(line))
+    for D in Ds:
+        assert rows[(D, "II")][0] < 0.01 * rows[(D, "IB")][0]
+        assert rows[(D, "II")][1] < 0.01 * rows[(D, "IB")][1]
+    ib = [rows[(D, "IB")][0] for D in Ds]
+    assert all(math.log2(ib[k] / ib[k + 1]) > 0.5 for k in range(3)), ib
+    poly = sum(rows[(D, "II-polygon-2")][1] for D in Ds)
+    spl = sum(rows[(D, "II-spline-2")][1] for D in Ds)
+    assert spl <= poly

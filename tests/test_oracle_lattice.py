@@ -230,3 +230,72 @@ def test_channel_outflow_copies_exactly_the_unknown_populations(orc):
     # the copy is not vacuous: the two columns' unknown populations differ before it
     assert any(streamed(i, nx - 1 - 1, y) != post[y, nx - 1, i]
                for y in range(ny) for i in (3, 6, 7))
+
+
+# ------------------------------------------------- the paper's boxes, simple force
+@pytest.mark.parametrize("collision", ["srt", "mrt"])
+def test_simple_force_adds_exact_momentum(orc, collision):
+    """The simple external force term (Eq. 16: (1/c_s^2) w_i e_i . g per population)
+    adds exactly g to the momentum each step and the velocity is sum e f / rho, so a
+    uniform body force in a periodic box gives u(t) = t g / rho0 at the collision of step
+    t (the Guo form gives (t + 1/2) g / rho0, pinned above)."""
+    c = orc.MRT if collision == "mrt" else orc.SRT
+    for g in ((1e-5, 0.0), (2e-6, -3e-6)):
+        o = orc.Oracle(12, 10, collision=c, tau=0.7, s=W.mrt_rates(0.7), body=g,
+                       force=orc.FORCE_SIMPLE)
+        for t in (1, 4, 9):
+            o.step(1 if t == 1 else (t - (1 if t == 4 else 4)))
+            _, ux, uy = o.current_macros()
+            assert np.allclose(ux, t * g[0], rtol=1e-12, atol=0)
+            assert np.allclose(uy, t * g[1], rtol=1e-12, atol=1e-22)
+
+
+def _box_macros(o, x, y):
+    df = o.get_df()[:, y, x]
+    E = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+    d = df.sum()
+    ux = sum(e[0] * f for e, f in zip(E, df)) / (1.0 + d)
+    uy = sum(e[1] * f for e, f in zip(E, df)) / (1.0 + d)
+    return d, ux, uy
+
+
+@pytest.mark.parametrize("bc", ["wall", "outflow"])
+def test_box_boundary_nodes_carry_the_prescribed_values(orc, bc):
+    """Non-equilibrium extrapolation on the four sides of a box: the non-equilibrium part
+    copied from the inward neighbour has zero mass and momentum, so every edge node
+    carries exactly (to rounding) u = 0 and the neighbour's density on a wall, and the
+    reference density with the neighbour's velocity at an outflow; corners take the
+    diagonal neighbour.  From a random state, after every step."""
+    nx, ny = 13, 9
+    kind = orc.BC_BOX_WALL if bc == "wall" else orc.BC_BOX_OUTFLOW
+    o = orc.Oracle(nx, ny, collision=orc.MRT, tau=0.75, s=W.mrt_rates(0.75), bc=kind)
+    o.set_df(W.random_df(nx, ny, 1e-3, 11))
+    for _ in range(3):
+        o.step(1)
+        for y in range(ny):
+            for x in range(nx):
+                if 0 < x < nx - 1 and 0 < y < ny - 1:
+                    continue
+                px, py = x + (x == 0) - (x == nx - 1), y + (y == 0) - (y == ny - 1)
+                d, ux, uy = _box_macros(o, x, y)
+                dn, uxn, uyn = _box_macros(o, px, py)
+                if bc == "wall":
+                    assert abs(ux) < 1e-17 and abs(uy) < 1e-17 and abs(d - dn) < 1e-17
+                else:
+                    assert abs(d) < 1e-17 and abs(ux - uxn) < 1e-16 and abs(uy - uyn) < 1e-16
+
+
+def test_box_wall_keeps_rest_and_damps_a_disturbance(orc):
+    """A wall box at rest stays at rest bitwise; a disturbance inside it decays (the
+    walls take its momentum: no node keeps a velocity above 1% of the start's after
+    2000 steps)."""
+    nx, ny = 24, 20
+    o = orc.Oracle(nx, ny, collision=orc.MRT, tau=0.7, s=W.mrt_rates(0.7), bc=orc.BC_BOX_WALL)
+    o.step(20)
+    assert np.all(o.get_df() == 0.0)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    u0 = 0.01 * np.sin(np.pi * xx / (nx - 1)) * np.sin(np.pi * yy / (ny - 1))
+    o.init_equilibrium(None, u0, None)
+    o.step(2000)
+    _, ux, uy = o.step_macros()
+    assert np.hypot(ux, uy).max() < 0.01 * 0.01

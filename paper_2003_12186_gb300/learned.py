@@ -50,11 +50,11 @@ def generate(count=64, seed=1, spin_up=400, records=64, every=100, nx=512, ny=12
     """Samples (X [N][30] FP32 features, T [N][2] FP32 converged forces) from `records`
     recorded steps of `count` channels; returns X, T and the channel of each sample."""
     sims = W.learned_channels(count, seed, nx=nx, ny=ny)
+    # the label is the force the plain iteration (zero start) reaches at the tolerance:
+    # the operator of the iteration has near-null directions, along which the converged
+    # force depends on the start -- a previous-step start carries an arbitrary, drifting
+    # component there that no network can predict from the features
     lat = [make_channel(s) for s in sims]
-    for g in lat:
-        # the label is the force at the tolerance, whatever the start: start from the
-        # previous step's force, which gets there in the fewest passes
-        g.iilbm_set_warm_start_mode(iilbm.WS_PREVIOUS)
     Xs, Ts, Ss = [], [], []
     with iilbm.Batch(lat) as B:
         B.step(spin_up)

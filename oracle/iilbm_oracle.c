@@ -107,7 +107,19 @@ typedef struct {
   double *Gprev;   /* kept here, instead of from Gp */
   int ncut;        /* cut-link crossings of the most recent prepare */
   long step;
+  /* rigid body (section 2.3) carrying a directly forced interface */
+  int has_body;
+  int body_mode;     /* ORC_BODY_PRESCRIBED_X or ORC_BODY_FREE */
+  int body_dof;      /* FREE: free degrees of freedom, bits 1 x, 2 y, 4 rotation */
+  double body_A, body_umax;              /* PRESCRIBED_X: amplitude, peak velocity */
+  double body_m, body_I, body_Vs;        /* mass, moment of inertia, area */
+  double body_k[3], body_c[3];           /* spring and damper per degree of freedom */
+  double Xc0[2], Xc[2], Uc[2], Ucp[2], ac[2], th, Wb, Wbp, wb;  /* state */
+  double Fext[3];                        /* the last F_ext (x, y) and T_ext (Eqs. 25-26) */
+  double *X0;                            /* marker offsets from Xc0 at theta = 0 */
 } orc_state;
+
+enum { ORC_BODY_PRESCRIBED_X = 1, ORC_BODY_FREE = 2 };
 
 /* ------------------------------------------------------------ MRT matrix ---
  * Lallemand & Luo D2Q9 moment basis (cited in section 2.1.1 / 2.2.1): rows are
@@ -733,6 +745,9 @@ orc_state *orc_create(const orc_cfg *cfg) {
 }
 
 static void free_iface(orc_state *S) {
+  free(S->X0);
+  S->X0 = NULL;
+  S->has_body = 0;
   if (!S->has_iface) return;
   free(S->I.X); free(S->I.Gp); free(S->I.UD);
   free(S->G); free(S->Fn); free(S->Gpar); free(S->U); free(S->Ustar); free(S->Gprev);
@@ -937,9 +952,113 @@ void orc_advance(orc_state *S) {
   S->step++;
 }
 
+/* ---------------------------------------------------------- rigid body -------
+ * A rigid body carrying a directly forced interface (section 2.3).  Its markers are
+ * the body's reference polygon X0 (offsets from the centre Xc0, at angle 0) placed at
+ * the centre Xc and angle theta; the desired velocity of marker k is the body's,
+ * U^D_k = U_c + W x (X_k - X_c).  After a step whose force iteration gave G:
+ *   F_ext = -sum_k G_k dX + rho_f V_s (U_c(t) - U_c(t-1))                 (Eq. 25)
+ *   T_ext = -sum_k (X_k - X_c) x G_k dX + (rho_f/rho_s) I_s (W(t) - W(t-1))  (Eq. 26)
+ * and, for a free body, on each free degree of freedom with its spring k and damper c
+ * (the paper's 1-DOF oscillator of section 4.5, Eq. 54, in dimensional form):
+ *   m a(t+1) = F_ext - k (X_c - X_c0) - c U_c,  I_s w(t+1) = T_ext - k theta - c W
+ *                                                                         (Eq. 27)
+ *   U_c(t+1) = U_c(t) + a(t+1),  W(t+1) = W(t) + w(t+1)                   (Eq. 28)
+ *   X_c(t+1) = X_c(t) + U_c(t) + (a(t) + a(t+1))/2, the same for theta     (Eq. 29)
+ * A prescribed body follows section 4.4's harmonic translation in x:
+ *   X_c(t) = X_c0 - A sin(U_max t / A),  U_c(t) = -U_max cos(U_max t / A). */
+int orc_set_body(orc_state *S, int mode, int dof, double A, double umax, double m, double I,
+                 double Vs, const double *k, const double *c) {
+  if (!S->has_iface || S->I.model != ORC_DIRECT) return -1;
+  int n = S->I.n;
+  free(S->X0);
+  S->X0 = (double *)malloc(2 * n * sizeof(double));
+  double cx = 0, cy = 0;
+  for (int q = 0; q < n; q++) { cx += S->I.X[2 * q]; cy += S->I.X[2 * q + 1]; }
+  cx /= n; cy /= n;
+  for (int q = 0; q < n; q++) {
+    S->X0[2 * q] = S->I.X[2 * q] - cx;
+    S->X0[2 * q + 1] = S->I.X[2 * q + 1] - cy;
+  }
+  S->has_body = 1;
+  S->body_mode = mode; S->body_dof = dof; S->body_A = A; S->body_umax = umax;
+  S->body_m = m; S->body_I = I; S->body_Vs = Vs;
+  for (int d = 0; d < 3; d++) { S->body_k[d] = k ? k[d] : 0; S->body_c[d] = c ? c[d] : 0; }
+  S->Xc0[0] = S->Xc[0] = cx; S->Xc0[1] = S->Xc[1] = cy;
+  S->Uc[0] = S->Uc[1] = S->Ucp[0] = S->Ucp[1] = S->ac[0] = S->ac[1] = 0;
+  S->th = S->Wb = S->Wbp = S->wb = 0;
+  S->Fext[0] = S->Fext[1] = S->Fext[2] = 0;
+  if (mode == ORC_BODY_PRESCRIBED_X) S->Uc[0] = S->Ucp[0] = -umax;  /* U_c(0) */
+  /* the markers and their desired velocity at t = 0 */
+  for (int q = 0; q < n; q++) {
+    double rx = S->I.X[2 * q] - S->Xc[0], ry = S->I.X[2 * q + 1] - S->Xc[1];
+    S->I.UD[2 * q] = S->Uc[0] - S->Wb * ry;
+    S->I.UD[2 * q + 1] = S->Uc[1] + S->Wb * rx;
+  }
+  return 0;
+}
+
+/* The body's update after a step (the force G of that step's iteration), then its
+ * markers and desired velocities at the new time level. */
+static void body_update(orc_state *S) {
+  orc_iface *I = &S->I;
+  int n = I->n;
+  double Fx = 0, Fy = 0, T = 0;
+  for (int q = 0; q < n; q++) {
+    double rx = I->X[2 * q] - S->Xc[0], ry = I->X[2 * q + 1] - S->Xc[1];
+    Fx -= S->G[2 * q] * I->dX;
+    Fy -= S->G[2 * q + 1] * I->dX;
+    T -= (rx * S->G[2 * q + 1] - ry * S->G[2 * q]) * I->dX;
+  }
+  double rho_f = S->c.rho0;
+  Fx += rho_f * S->body_Vs * (S->Uc[0] - S->Ucp[0]);
+  Fy += rho_f * S->body_Vs * (S->Uc[1] - S->Ucp[1]);
+  T += rho_f * S->body_Vs / S->body_m * S->body_I * (S->Wb - S->Wbp);  /* rho_f/rho_s = rho_f V_s / m */
+  S->Fext[0] = Fx; S->Fext[1] = Fy; S->Fext[2] = T;
+  double t1 = (double)(S->step);  /* the new time level */
+  S->Ucp[0] = S->Uc[0]; S->Ucp[1] = S->Uc[1]; S->Wbp = S->Wb;
+  if (S->body_mode == ORC_BODY_PRESCRIBED_X) {
+    double A = S->body_A, um = S->body_umax;
+    S->Xc[0] = S->Xc0[0] - A * sin(um * t1 / A);
+    S->Uc[0] = -um * cos(um * t1 / A);
+  } else {
+    double F[3] = {Fx, Fy, T};
+    double inert[3] = {S->body_m, S->body_m, S->body_I};
+    double *pos[3] = {&S->Xc[0], &S->Xc[1], &S->th};
+    double *vel[3] = {&S->Uc[0], &S->Uc[1], &S->Wb};
+    double *acc[3] = {&S->ac[0], &S->ac[1], &S->wb};
+    double org[3] = {S->Xc0[0], S->Xc0[1], 0.0};
+    for (int d = 0; d < 3; d++) {
+      if (!(S->body_dof & (1 << d))) continue;
+      double a1 = (F[d] - S->body_k[d] * (*pos[d] - org[d]) - S->body_c[d] * (*vel[d])) / inert[d];
+      double v0 = *vel[d], a0 = *acc[d];
+      *vel[d] = v0 + a1;
+      *pos[d] = *pos[d] + v0 + 0.5 * (a0 + a1);
+      *acc[d] = a1;
+    }
+  }
+  double cth = cos(S->th), sth = sin(S->th);
+  for (int q = 0; q < n; q++) {
+    double ox = S->X0[2 * q], oy = S->X0[2 * q + 1];
+    I->X[2 * q] = S->Xc[0] + cth * ox - sth * oy;
+    I->X[2 * q + 1] = S->Xc[1] + sth * ox + cth * oy;
+    double rx = I->X[2 * q] - S->Xc[0], ry = I->X[2 * q + 1] - S->Xc[1];
+    I->UD[2 * q] = S->Uc[0] - S->Wb * ry;
+    I->UD[2 * q + 1] = S->Uc[1] + S->Wb * rx;
+  }
+}
+
+/* Body state: X_c, Y_c, theta, U_x, U_y, W, F_x, F_y, T (the last F_ext, T_ext). */
+void orc_get_body(const orc_state *S, double *out) {
+  double v[9] = {S->Xc[0], S->Xc[1], S->th, S->Uc[0], S->Uc[1], S->Wb,
+                 S->Fext[0], S->Fext[1], S->Fext[2]};
+  memcpy(out, v, sizeof v);
+}
+
 int orc_step(orc_state *S) {
   if (orc_prepare(S)) return -1;
   orc_advance(S);
+  if (S->has_body) body_update(S);
   return 0;
 }
 

@@ -32,6 +32,7 @@ SRT, MRT = 0, 1
 BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL, BC_BOX_OUTFLOW, BC_BOX_WALL = 0, 1, 2, 3, 4
 FORCE_GUO, FORCE_SIMPLE = 0, 1
 SPRING, SPRING_REST, PRESCRIBED, DIRECT = 0, 1, 2, 3
+BODY_PRESCRIBED_X, BODY_FREE = 1, 2
 # Lallemand-Luo D2Q9 rates quoted in section 2.2.1 (s7 = s8 = 1/tau set per case)
 PAPER_MRT_RATES = (0.0, 1.63, 1.14, 0.0, 1.92, 0.0, 1.92, None, None)
 
@@ -123,6 +124,9 @@ def _bind(L):
     L.orc_normal_split_arr.argtypes = [_D, C.c_int, C.c_int, C.c_double, _D, _D, _D, _D,
                                        C.c_int]
     L.orc_set_curve.argtypes = [C.c_void_p, C.c_int]
+    L.orc_set_body.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                               C.c_double, C.c_double, _D, _D]
+    L.orc_get_body.argtypes = [C.c_void_p, _D]
     L.orc_spline_coeffs.argtypes = [_D, C.c_int, C.c_int, _D]
     L.orc_spline_eval.argtypes = [_D, C.c_int, C.c_int, C.c_double, C.c_int]
     L.orc_spline_eval.restype = C.c_double
@@ -395,3 +399,17 @@ class Oracle:
 
     def mdf_stats(self):
         return self._L.orc_mdf_iters(self._h), self._L.orc_mdf_residual(self._h)
+
+    def set_body(self, mode, dof=0, A=0.0, umax=0.0, mass=1.0, inertia=1.0, volume=0.0,
+                 spring=(0.0, 0.0, 0.0), damping=(0.0, 0.0, 0.0)):
+        """Make the directly forced interface a rigid body (section 2.3)."""
+        k, c = _f64(spring), _f64(damping)
+        if self._L.orc_set_body(self._h, mode, dof, A, umax, mass, inertia, volume, _p(k),
+                                _p(c)) != 0:
+            raise RuntimeError("a rigid body needs a directly forced interface")
+
+    def body(self):
+        """(X_c, Y_c, theta, U_x, U_y, W, F_x, F_y, T) of the rigid body."""
+        out = np.zeros(9)
+        self._L.orc_get_body(self._h, _p(out))
+        return out

@@ -189,3 +189,72 @@ def test_table1_uniform_normal_force_errors_and_orders():
     poly = sum(rows[(D, "II-polygon-2")][1] for D in Ds)
     spl = sum(rows[(D, "II-spline-2")][1] for D in Ds)
     assert spl <= poly
+
+
+def elastic_ellipse(L, method, lib="gpu", orc=None, storage="f64"):
+    """Section 4.2: an elliptical elastic interface in a walled box of side L (no-slip
+    walls by non-equilibrium extrapolation), centred, semi-axes 0.35 L and 0.25^2/0.35 L
+    (the equilibrium circle's radius is 0.25 L), zero-rest-length springs (Eq. 19) of
+    nondimensional stiffness kappa / (U^2 L) = 0.1, nu = 0.02, Re = 100, U = nu Re / L.
+    method: "IB" (the simple force term, markers dx/3 apart on the equilibrium circle),
+    "IB-G" (Guo's force term), "II" (the jump, markers 2 dx apart, cubic spline on 4
+    chords per segment, simple force term).  Returns the lattice (or oracle), the
+    markers' initial polygon and U."""
+    nu, Re = 0.02, 100.0
+    U = nu * Re / L
+    kappa = 0.1 * U * U * L
+    tau = 0.5 + 3 * nu
+    dX = 2.0 if method == "II" else 1.0 / 3.0
+    n = int(round(2 * math.pi * 0.25 * L / dX))
+    dX = 2 * math.pi * 0.25 * L / n
+    a, b = 0.35 * L, 0.25 ** 2 / 0.35 * L
+    X = W.ellipse_markers(0.5 * L + 0.13, 0.5 * L + 0.07, a, b, n)
+    force = "SIMPLE" if method != "IB-G" else "GUO"
+    jump = 1 if method == "II" else 0
+    curve = 4 if method == "II" else 0
+    s = W.mrt_rates(tau)
+    if lib == "gpu":
+        g = iilbm.Lattice(L, L, collision=iilbm.MRT, storage=storage, tau=tau, s=s,
+                          bc=iilbm.BC_BOX_WALL, force=getattr(iilbm, "FORCE_" + force),
+                          jump=jump)
+        g.set_interface(X, model=iilbm.SPRING, stiffness=kappa, dX=dX, curve=curve)
+    else:
+        g = orc.Oracle(L, L, collision=orc.MRT, tau=tau, s=s, bc=orc.BC_BOX_WALL,
+                       force=getattr(orc, "FORCE_" + force), jump=jump)
+        g.set_interface(X, model=orc.SPRING, kappa=kappa, dX=dX, curve=curve)
+    return g, X, U
+
+
+@pytest.mark.parametrize("method", ["IB", "IB-G", "II"])
+def test_elastic_ellipse_matches_oracle(orc, method):
+    """Section 4.2's setup at L = 80, 200 steps, FP64: markers and populations equal the
+    oracle's."""
+    g, X, _ = elastic_ellipse(80, method)
+    o, _, _ = elastic_ellipse(80, method, "oracle", orc)
+    g.step(200)
+    o.step(200)
+    assert np.abs(g.get_markers()["X"] - o.markers()["X"]).max() < 1e-11
+    assert np.abs(g.get_populations() - o.get_df()).max() < 1e-13
+
+
+def test_table2_area_loss():
+    """Table 2's comparison at L = 80 (t_end = 30 L / U = 96 000 steps): the area loss per
+    unit nondimensional time dV / (L U dt) and the total loss V / L^2 of the IB-LBM
+    (simple force), the IB-LBM with Guo's force and the II-LBM.  The II-LBM conserves the
+    enclosed area orders of magnitude better (the paper at L = 240: 8.82e-4, 1.78e-3,
+    6.28e-7 per unit time; 2.87e-2, 5.51e-2, 2.35e-5 in total).  Printed with -s."""
+    L = 80
+    out = {}
+    for method in ("IB", "IB-G", "II"):
+        g, X0, U = elastic_ellipse(L, method, storage="f32")
+        steps = int(round(30 * L / U))
+        g.step(steps)
+        a0 = 0.5 * abs(np.sum(X0[:, 0] * np.roll(X0[:, 1], -1) - np.roll(X0[:, 0], -1) * X0[:, 1]))
+        X = g.get_markers()["X"]
+        a1 = 0.5 * abs(np.sum(X[:, 0] * np.roll(X[:, 1], -1) - np.roll(X[:, 0], -1) * X[:, 1]))
+        total = (a0 - a1) / L ** 2
+        rate = (a0 - a1) / (L * U * steps)
+        out[method] = (rate, total)
+        print(f"table2 L={L} {method}: area loss per unit time {rate:.3e}, total {total:.3e}")
+    assert abs(out["II"][1]) < 0.01 * abs(out["IB"][1])
+    assert abs(out["II"][1]) < 0.01 * abs(out["IB-G"][1])

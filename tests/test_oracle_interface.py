@@ -614,3 +614,86 @@ def test_spline_cut_links_follow_the_curve(orc):
                     assert abs(rec[key][0] + 3 * WT[i] * Fn) < 1e-14 * abs(Fn)
                 elif (r0 > margin and r1 > margin) or (r0 < -margin and r1 < -margin):
                     assert key not in rec
+
+
+# ---------------------------------------------------------------- rigid bodies
+def _body_case(orc, mode, jump=0, dof=3, u0=0.01, D=10.0, n=32, rho_s=2.0, steps=0):
+    nx = ny = 48
+    X = W.circle_markers(23.7, 24.2, D / 2, n)
+    dX = W.polygon_perimeter(X) / n
+    o = orc.Oracle(nx, ny, collision=orc.MRT, tau=0.8, s=W.mrt_rates(0.8), jump=jump)
+    o.init_equilibrium(None, np.full(nx * ny, u0), None)
+    o.set_interface(X, model=orc.DIRECT, moves=False, dX=dX, eta=2.0, mdf_iters=5,
+                    UD=np.zeros((n, 2)))
+    Vs = np.pi * D * D / 4
+    m = rho_s * Vs
+    o.set_body(mode, dof=dof, A=3.0, umax=0.02, mass=m, inertia=m * D * D / 8, volume=Vs)
+    o.step(steps)
+    return o, X, m, Vs
+
+
+def _fluid_momentum(o):
+    df = o.get_df()
+    E = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+    return np.array([sum(e[0] * df[i].sum() for i, e in enumerate(E)),
+                     sum(e[1] * df[i].sum() for i, e in enumerate(E))])
+
+
+def test_free_body_conserves_momentum_with_the_fluid(orc):
+    """A free rigid body (section 2.3) in a periodic box with a uniform stream, the whole
+    force spread (IB form): the fluid gains exactly sum_k G_k dX each step (the delta
+    kernel's partition of unity; Guo's term adds exactly g), and the body's Eq. 25 (with
+    its internal-fluid inertia term) and Eqs. 27-29 then make
+        Q(t) = P_fluid(t) + m U_c(t) - rho_f V_s U_c(t - 1)
+    constant to rounding.  A sign error in the force, or a missing or misplaced inertia
+    term, breaks it.  The stream drags the body along (U_x > 0).  Density ratio 10: the
+    explicit inertia term of Eq. 25 lets light bodies oscillate unstably (this IB form at
+    rho_s / rho_f <= 2.55, the II-LBM form at 1.5 but not at 2.55)."""
+    o, X, m, Vs = _body_case(orc, orc.BODY_FREE, rho_s=10.0)
+    Q0 = _fluid_momentum(o)
+    Ucp = np.zeros(2)
+    for _ in range(60):
+        o.step(1)
+        Uc = o.body()[3:5]
+        Q = _fluid_momentum(o) + m * Uc - Vs * Ucp
+        assert np.abs(Q - Q0).max() < 1e-13 * np.abs(Q0).max()
+        Ucp = Uc
+    assert Uc[0] > 1e-5 and abs(Uc[1]) < 1e-3 * Uc[0]
+
+
+def test_prescribed_translation_moves_the_markers_rigidly(orc):
+    """Section 4.4's prescribed harmonic translation: after t steps the centre sits at
+    X_c0 - A sin(U_max t / A), every marker keeps its offset from the centre exactly, and
+    the body's velocity is -U_max cos(U_max t / A)."""
+    o, X, _, _ = _body_case(orc, orc.BODY_PRESCRIBED_X, jump=1, u0=0.0)
+    c0 = X.mean(0)
+    T = 38
+    o.step(T)
+    b = o.body()
+    A, um = 3.0, 0.02
+    assert abs(b[0] - (c0[0] - A * np.sin(um * T / A))) < 1e-12
+    assert abs(b[3] + um * np.cos(um * T / A)) < 1e-15 and b[1] == c0[1]
+    Xt = o.markers()["X"]
+    assert np.abs((Xt - b[:2]) - (X - c0)).max() < 1e-12
+
+
+def test_free_body_at_the_papers_density_ratio_is_stable(orc):
+    """At the density ratio of section 4.5 (8 / pi) a free body carried by a stream in the
+    II-LBM settles into a smooth drift (no growing oscillation of its velocity over 300
+    steps)."""
+    o, _, _, _ = _body_case(orc, orc.BODY_FREE, jump=1, rho_s=8 / np.pi)
+    u = []
+    for _ in range(300):
+        o.step(1)
+        u.append(o.body()[3])
+    u = np.array(u)
+    assert np.all(np.isfinite(u)) and 0 < u[-1] < 0.02
+    assert np.abs(np.diff(u[-100:])).max() < 1e-4
+
+
+def test_free_body_at_rest_stays_at_rest(orc):
+    """A free body in fluid at rest feels no force: it, and the fluid, stay at rest."""
+    o, X, _, _ = _body_case(orc, orc.BODY_FREE, jump=1, u0=0.0, dof=7, steps=40)
+    b = o.body()
+    assert np.abs(b[3:9]).max() == 0.0 and np.abs(o.markers()["X"] - X).max() == 0.0
+    assert np.abs(o.get_df()).max() == 0.0

@@ -178,9 +178,51 @@ int iilbm_set_warm_start_mode(iilbm_t h, int32_t mode);
 int iilbm_get_unforced_velocity(iilbm_t h, double *Ustar);
 
 /* Force of the fluid on the body, F = -sum_k G_k dX (Eq. 25 without the internal
- * inertia term; the body is fixed), from the most recent Lagrangian force.  Drag and
+ * inertia term), from the most recent Lagrangian force.  Drag and
  * lift coefficients follow as 2 F / (rho U^2 D) (Eqs. 52-53).  Synchronises. */
 int iilbm_get_body_force(iilbm_t h, double *F);
+
+/* A rigid body carrying the directly forced interface (section 2.3).  The current
+ * markers become the body's reference shape: its centre X_c0 is their mean and each
+ * marker keeps its offset from it at angle 0.  After every step the library reduces the
+ * step's Lagrangian force G to
+ *   F_ext = -sum_k G_k dX + rho0 V_s (U_c(t) - U_c(t-1))                      (Eq. 25)
+ *   T_ext = -sum_k (X_k - X_c) x G_k dX + (rho0 V_s / m) I_s (W(t) - W(t-1))   (Eq. 26)
+ * moves the body, places every marker rigidly (X_k = X_c + R(theta) X0_k) and gives it
+ * the body's velocity as its desired velocity, U^D_k = U_c + W x (X_k - X_c).  The force
+ * iteration then rebuilds its band of nodes and cut links in every step.
+ *   IILBM_BODY_PRESCRIBED_X  harmonic translation in x (section 4.4):
+ *       X_c(t) = X_c0 - amplitude sin(u_max t / amplitude), U_c(t) = -u_max cos(u_max t /
+ *       amplitude), t the lattice's time level (U_c(0) = -u_max).
+ *   IILBM_BODY_FREE          on each degree of freedom set in dof (1 x, 2 y, 4 rotation)
+ *       a spring k = spring[d] about the start and a damper c = damping[d] (the
+ *       oscillator of section 4.5):  m a(t+1) = F_ext - k (X_c - X_c0) - c U_c,
+ *       I_s w(t+1) = T_ext - k theta - c W (Eq. 27); U_c(t+1) = U_c(t) + a(t+1) (Eq. 28);
+ *       X_c(t+1) = X_c(t) + U_c(t) + (a(t) + a(t+1)) / 2 (Eq. 29), the same for theta.
+ * mass m > 0, inertia I_s > 0 (FREE; ignored when PRESCRIBED_X), volume V_s >= 0 the
+ * body's area.  The explicit scheme is unstable for a light body (mass below about 2.6
+ * rho0 V_s in a resting fluid).  The body stays until iilbm_set_interface replaces the
+ * interface.  Synchronises.  Errors: INVALID_ARG (no directly forced interface, batched
+ * lattice, bad mode or parameters), CAPACITY (the moving band's shared memory exceeds
+ * 227 KB), OOM, CUDA. */
+enum { IILBM_BODY_PRESCRIBED_X = 1, IILBM_BODY_FREE = 2 };
+typedef struct {
+  int32_t mode;         /* IILBM_BODY_PRESCRIBED_X or IILBM_BODY_FREE */
+  int32_t dof;          /* FREE: free degrees of freedom, bits 1 x, 2 y, 4 rotation */
+  double amplitude;     /* PRESCRIBED_X: A > 0 */
+  double u_max;         /* PRESCRIBED_X: peak velocity */
+  double mass;          /* FREE: m */
+  double inertia;       /* FREE: I_s */
+  double volume;        /* V_s, the body's area (internal-fluid inertia of Eqs. 25-26) */
+  double spring[3];     /* FREE: k per degree of freedom (x, y, rotation) */
+  double damping[3];    /* FREE: c per degree of freedom */
+} iilbm_body_params;
+int iilbm_set_rigid_body(iilbm_t h, const iilbm_body_params *bp);
+
+/* The body's state after the most recent step: state[9] = X_c, Y_c, theta, U_x, U_y, W,
+ * F_x, F_y, T (the last F_ext, T_ext of Eqs. 25-26; host pointer).  Synchronises.
+ * INVALID_ARG without a body. */
+int iilbm_get_rigid_body(iilbm_t h, double *state);
 
 /* The jump of the current state's interface on the streamed populations (Eq. 47 with
  * Eq. 32): J[i-1][y][x] = the sum of s w_i/c_s^2 Fn(crossing) over the crossings of the

@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 using namespace iilbm;
 
@@ -62,6 +63,7 @@ void free_interface(iilbm_lattice *h) {
   if (h->Xqp) cudaFree(h->Xqp);
   h->Xq = h->Xqp = nullptr;
   free_direct_forcing(h);
+  free_body(h);
   h->nm = 0;
 }
 
@@ -453,7 +455,8 @@ long long kernels_per_step(const iilbm_lattice *h) {
                          : 0);
   if (h->nm > 0)
     k += pipelined(h) ? 2
-                      : 3 + (h->ip.model == IILBM_DIRECT ? 1 : 0) + (h->ip.curve > 0 ? 3 : 0);
+                      : 3 + (h->ip.model == IILBM_DIRECT ? 1 : 0) + (h->ip.curve > 0 ? 3 : 0) +
+                            (h->body ? 1 : 0);
   return k;
 }
 
@@ -496,6 +499,7 @@ int one_step(iilbm_lattice *h, int ev_slot) {
   }
   h->step++;
   if ((rc = launch_channel_bc(h))) return rc;  // inflow / outflow of the new state
+  if ((rc = launch_body_update(h))) return rc;  // a rigid body moves to the new level
   h->prepared = pipe || h->nm == 0;
   return IILBM_OK;
 }
@@ -852,6 +856,101 @@ int iilbm_synchronize(iilbm_t h) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------- rigid body
+// Make the directly forced interface a rigid body (include/iilbm.h).
+extern "C" int iilbm_set_rigid_body(iilbm_t h, const iilbm_body_params *bp) {
+  if (!h || !bp || h->in_batch || h->nm == 0 || h->ip.model != IILBM_DIRECT)
+    return IILBM_ERR_INVALID_ARG;
+  if (bp->mode != IILBM_BODY_PRESCRIBED_X && bp->mode != IILBM_BODY_FREE)
+    return IILBM_ERR_INVALID_ARG;
+  if (bp->mode == IILBM_BODY_PRESCRIBED_X && !(bp->amplitude > 0 && std::isfinite(bp->u_max)))
+    return IILBM_ERR_INVALID_ARG;
+  if (bp->mode == IILBM_BODY_FREE &&
+      (!(bp->mass > 0) || !(bp->inertia > 0) || !(bp->volume >= 0) || bp->dof < 0 || bp->dof > 7))
+    return IILBM_ERR_INVALID_ARG;
+  int rc = drain_all(h);  // the force iteration's launches change: recapture
+  if (rc) return rc;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return IILBM_ERR_CUDA;
+  drop_graph(h);
+  const int n = h->nm;
+  std::vector<double> X(2 * (size_t)n), X0(2 * (size_t)n), UD(2 * (size_t)n);
+  if (cudaMemcpy(X.data(), h->X, X.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return IILBM_ERR_CUDA;
+  double cxm = 0, cym = 0, r = 0;
+  for (int q = 0; q < n; q++) {
+    cxm += X[2 * q];
+    cym += X[2 * q + 1];
+  }
+  cxm /= n;
+  cym /= n;
+  for (int q = 0; q < n; q++) {
+    X0[2 * q] = X[2 * q] - cxm;
+    X0[2 * q + 1] = X[2 * q + 1] - cym;
+    r = std::max(r, std::hypot(X0[2 * q], X0[2 * q + 1]));
+  }
+  iilbm_body_dev b{};
+  b.mode = bp->mode;
+  b.dof = bp->dof;
+  b.A = bp->amplitude;
+  b.umax = bp->u_max;
+  b.m = bp->mode == IILBM_BODY_FREE ? bp->mass : 1.0;
+  b.I = bp->mode == IILBM_BODY_FREE ? bp->inertia : 1.0;
+  b.Vs = bp->volume;
+  b.rho_f = h->cfg.rho0;
+  for (int d = 0; d < 3; d++) {
+    b.k[d] = bp->spring[d];
+    b.c[d] = bp->damping[d];
+  }
+  b.t = h->step;  // the prescribed motion is a function of the lattice's time level
+  b.Xc0[0] = b.Xc[0] = cxm;
+  b.Xc0[1] = b.Xc[1] = cym;
+  if (bp->mode == IILBM_BODY_PRESCRIBED_X) b.Uc[0] = b.Ucp[0] = -bp->u_max;
+  for (int q = 0; q < n; q++) {  // the desired velocity of the state at t = 0
+    UD[2 * q] = b.Uc[0] - b.W * (X[2 * q + 1] - cym);
+    UD[2 * q + 1] = b.Uc[1] + b.W * (X[2 * q] - cxm);
+  }
+  // capacities: the band and the cut links of the body wherever it moves (the set-up
+  // band's sizes with a margin), the bitmap of a window around its circumcircle
+  free_body(h);
+  const int side = (int)std::ceil(2 * r) + 10;
+  h->body_words = (side * side + 31) / 32 + 1;
+  h->body_nb = h->df_nb + h->df_nb / 3 + 64;
+  h->body_nl = h->df_nl + h->df_nl / 3 + 64;
+  if (cudaMalloc(&h->body, sizeof(iilbm_body_dev)) != cudaSuccess ||
+      cudaMalloc(&h->body_X0, X0.size() * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    free_body(h);
+    return IILBM_ERR_OOM;
+  }
+  if (direct_forcing_smem(h, h->body_nb, n) > 227 * 1024) {  // with the body's capacities
+    free_body(h);
+    return IILBM_ERR_CAPACITY;
+  }
+  if (cudaMemcpy(h->body, &b, sizeof b, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->body_X0, X0.data(), X0.size() * sizeof(double), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(h->aux, UD.data(), UD.size() * sizeof(double), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    free_body(h);
+    return IILBM_ERR_CUDA;
+  }
+  return IILBM_OK;
+}
+
+extern "C" int iilbm_get_rigid_body(iilbm_t h, double *state) {
+  if (!h || !state || !h->body) return IILBM_ERR_INVALID_ARG;
+  iilbm_body_dev b;
+  if (cudaMemcpyAsync(&b, h->body, sizeof b, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return IILBM_ERR_CUDA;
+  }
+  const double v[9] = {b.Xc[0], b.Xc[1], b.th, b.Uc[0], b.Uc[1], b.W, b.F[0], b.F[1], b.F[2]};
+  for (int q = 0; q < 9; q++) state[q] = v[q];
+  return IILBM_OK;
+}
+
 
 // ------------------------------------------------------ no-allocation read-out
 // iilbm_get_macros_noalloc: the macroscopic read-out of iilbm_get_macros without any

@@ -28,11 +28,15 @@ __global__ void __launch_bounds__(DF_THREADS)
   direct_forcing_cta<S>(A, geo, odd, a, inv_scale, smem_raw);
 }
 
-// Shared memory of the forcing kernel for a band of nb nodes and n markers.
+// Shared memory of the forcing kernel for a band of nb nodes and n markers (a moving
+// body: its capacities instead, plus the band's construction).
 size_t direct_forcing_smem(const iilbm_lattice *h, int nb, int n) {
   const bool mlp = h->ws_mode == WS_MLP;
-  return h->cfg.storage == IILBM_F64 ? df_smem_bytes<double>(nb, n, mlp)
-                                     : df_smem_bytes<float>(nb, n, mlp);
+  if (h->body) nb = h->body_nb;
+  size_t b = h->cfg.storage == IILBM_F64 ? df_smem_bytes<double>(nb, n, mlp)
+                                         : df_smem_bytes<float>(nb, n, mlp);
+  if (h->body) b += df_move_bytes(h->body_words, h->body_nb, h->body_nl);
+  return b;
 }
 
 // The force iteration's arguments for lattice h.
@@ -56,6 +60,12 @@ DfArgs df_args(const iilbm_lattice *h) {
   a.st = h->df_st;
   a.links = (const DfLink *)h->df_links;
   a.nl = h->df_nl;
+  a.moving = h->body != nullptr;
+  a.words_max = a.moving ? h->body_words : 0;
+  a.nb_max = a.moving ? h->body_nb : 0;
+  a.nl_max = a.moving ? h->body_nl : 0;
+  a.ig = h->igeom;
+  a.status = h->d_status;
   a.jump = h->cfg.jump;
   a.bodyx = h->cfg.body[0];
   a.bodyy = h->cfg.body[1];
@@ -248,6 +258,110 @@ int launch_direct_forcing(iilbm_lattice *h) {
   }
   return IILBM_OK;
 }
+
+// ---------------------------------------------------------------- rigid body
+// After a step: F_ext = -sum G dX + rho_f V_s (U_c(t) - U_c(t-1)) and T_ext (Eqs. 25-26)
+// reduced over the markers; the body's update (Eqs. 27-29 for a free body with its
+// springs and dampers, section 4.4's harmonic translation for a prescribed one); then
+// every marker placed rigidly, X_k = X_c + R(theta) X0_k, and given the body's velocity
+// as its desired velocity, U^D_k = U_c + W x (X_k - X_c).
+__global__ void __launch_bounds__(256)
+    k_body_update(iilbm_body_dev *b, double *X, double *UD, const double *__restrict__ G,
+                  const double *__restrict__ X0, int n, double dX) {
+  __shared__ double red[3][8];
+  __shared__ double pose[5];  // X_c, Y_c, theta, U_x, U_y (then W in pose[4 + 1])
+  __shared__ double wnew;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double xc = b->Xc[0], yc = b->Xc[1];
+  double fx = 0, fy = 0, tq = 0;
+  for (int q = tid; q < n; q += blockDim.x) {
+    const double rx = X[2 * q] - xc, ry = X[2 * q + 1] - yc;
+    fx -= G[2 * q] * dX;
+    fy -= G[2 * q + 1] * dX;
+    tq -= (rx * G[2 * q + 1] - ry * G[2 * q]) * dX;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    tq += __shfl_xor_sync(0xffffffffu, tq, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = fx;
+    red[1][warp] = fy;
+    red[2][warp] = tq;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    fx = fy = tq = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      fx += red[0][w];
+      fy += red[1][w];
+      tq += red[2][w];
+    }
+    fx += b->rho_f * b->Vs * (b->Uc[0] - b->Ucp[0]);
+    fy += b->rho_f * b->Vs * (b->Uc[1] - b->Ucp[1]);
+    tq += b->rho_f * b->Vs / b->m * b->I * (b->W - b->Wp);
+    b->F[0] = fx;
+    b->F[1] = fy;
+    b->F[2] = tq;
+    b->t += 1;
+    b->Ucp[0] = b->Uc[0];
+    b->Ucp[1] = b->Uc[1];
+    b->Wp = b->W;
+    if (b->mode == IILBM_BODY_PRESCRIBED_X) {
+      const double tt = (double)b->t;
+      b->Xc[0] = b->Xc0[0] - b->A * sin(b->umax * tt / b->A);
+      b->Uc[0] = -b->umax * cos(b->umax * tt / b->A);
+    } else {
+      const double F[3] = {fx, fy, tq}, inert[3] = {b->m, b->m, b->I};
+      double *pos[3] = {&b->Xc[0], &b->Xc[1], &b->th};
+      double *vel[3] = {&b->Uc[0], &b->Uc[1], &b->W};
+      double *acc[3] = {&b->ac[0], &b->ac[1], &b->wdot};
+      const double org[3] = {b->Xc0[0], b->Xc0[1], 0.0};
+      for (int d = 0; d < 3; d++) {
+        if (!(b->dof & (1 << d))) continue;
+        const double a1 = (F[d] - b->k[d] * (*pos[d] - org[d]) - b->c[d] * (*vel[d])) / inert[d];
+        const double v0 = *vel[d], a0 = *acc[d];
+        *vel[d] = v0 + a1;
+        *pos[d] = *pos[d] + v0 + 0.5 * (a0 + a1);
+        *acc[d] = a1;
+      }
+    }
+    pose[0] = b->Xc[0];
+    pose[1] = b->Xc[1];
+    pose[2] = b->th;
+    pose[3] = b->Uc[0];
+    pose[4] = b->Uc[1];
+    wnew = b->W;
+  }
+  __syncthreads();
+  const double ct = cos(pose[2]), st = sin(pose[2]);
+  for (int q = tid; q < n; q += blockDim.x) {
+    const double ox = X0[2 * q], oy = X0[2 * q + 1];
+    const double x = pose[0] + ct * ox - st * oy, y = pose[1] + st * ox + ct * oy;
+    X[2 * q] = x;
+    X[2 * q + 1] = y;
+    UD[2 * q] = pose[3] - wnew * (y - pose[1]);
+    UD[2 * q + 1] = pose[4] + wnew * (x - pose[0]);
+  }
+}
+
+int launch_body_update(iilbm_lattice *h) {
+  if (!h->body) return IILBM_OK;
+  k_body_update<<<1, 256, 0, h->stream>>>(h->body, h->X, h->aux, h->Gdf, h->body_X0, h->nm,
+                                          h->ip.dX);
+  return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
+}
+
+void free_body(iilbm_lattice *h) {
+  if (h->body) cudaFree(h->body);
+  if (h->body_X0) cudaFree(h->body_X0);
+  h->body = nullptr;
+  h->body_X0 = nullptr;
+  h->body_words = h->body_nb = h->body_nl = 0;
+}
+
 
 __global__ void k_df_features(const double *__restrict__ X, const double *__restrict__ UD,
                               const double *__restrict__ Ustar, int n, double dX, float re,

@@ -40,6 +40,13 @@ struct DfArgs {
   const int *st;
   const DfLink *links;
   int nl;
+  // a moving (rigid) body: the band and the cut links are rebuilt in the CTA from the
+  // current markers every call, into shared memory of these capacities (words of the
+  // bitmap of the body's window, band nodes, cut links); ig is the interface's geometry
+  int moving;
+  int words_max, nb_max, nl_max;
+  Geom ig;
+  int *status;
   int jump;               // II-LBM: the normal part acts through the jump
   double bodyx, bodyy, rho0;
   int ws_mode;            // WS_GIVEN: G0; WS_PREVIOUS: the G of the last iteration (in G);
@@ -69,6 +76,14 @@ __host__ __device__ inline size_t df_smem_bytes(int nb, int n, bool mlp = false)
   return b + 16;
 }
 
+// What a moving body adds: the window's bitmap and its word prefix sums, each band
+// node's window position, and the cut-link records (after the rest, 16-byte aligned).
+__host__ __device__ inline size_t df_move_bytes(int words, int nb, int nl) {
+  size_t b = (2 * (size_t)words + (size_t)nb) * sizeof(int);
+  b = (b + 15) & ~(size_t)15;
+  return b + (size_t)nl * sizeof(DfLink) + 16;
+}
+
 // Bit pattern of a non-negative value of T; such patterns order as the values do, so
 // the residual's maximum is taken with integer maxima.
 template <typename T> struct BitsOf;
@@ -91,6 +106,180 @@ __device__ __forceinline__ T df_link_coef(const DfLink &L, T FnA, T FnB) {
     return T((double)L.s * 3.0 * wt<double>(L.i) * ((1.0 - L.t) * (double)FnA + L.t * (double)FnB));
   const float t = (float)L.t;
   return T((float)L.s * 3.0f * wt<float>(L.i) * ((1.0f - t) * (float)FnA + t * (float)FnB));
+}
+
+// Is node (x, y) (unwrapped) on the lattice, as the interface sees it?
+__device__ inline bool df_on_lattice(const DfArgs &a, int x, int y) {
+  const bool px = a.ig.bc != IILBM_BC_CHANNEL, py = a.ig.bc == IILBM_BC_PERIODIC;
+  return (px || (x >= 0 && x < a.ig.nx)) && (py || (y >= 0 && y < a.ig.ny));
+}
+
+// Band index of node (x, y) of a moving body's window (-1 off the lattice, outside the
+// window or unmarked), from the bitmap and its word prefix sums.
+__device__ inline int df_window_index(const DfArgs &a, const unsigned *bits, const int *wpre,
+                                      const int *mv, int x, int y) {
+  const int lx = x - mv[0], ly = y - mv[1];
+  if (!df_on_lattice(a, x, y) || lx < 0 || ly < 0 || lx >= mv[2] || ly >= mv[3]) return -1;
+  const int p = ly * mv[2] + lx, w = p >> 5, b = p & 31;
+  const unsigned word = bits[w];
+  if (!(word >> b & 1u)) return -1;
+  return wpre[w] + __popc(word & ((1u << b) - 1u));
+}
+
+// A moving body's band, built by the whole CTA from the current markers: the window
+// [floor(min X) - 3, floor(max X) + 4] on each axis; a bitmap of the window's nodes that a
+// marker stencil or a cut link of the current polygon can touch; the band index of each
+// as the number of marked nodes before it (word popcounts, prefix-summed); each band
+// node's window position; and the cut links found by the interface phase's crossing
+// enumeration, one warp per segment.  Returns false (uniformly) if a capacity is
+// exceeded.  mv: window x0, y0, width, height, band nodes, cut links, failed flag.
+template <typename T>
+__device__ bool df_build_band(const DfArgs &a, unsigned *bits, int *wpre, int *bpos,
+                              DfLink *slinks, int *mv) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n = a.n;
+  __shared__ double ext[4][DF_THREADS / 32];
+  double lx = 1e300, hx = -1e300, ly = 1e300, hy = -1e300;
+  int bad = 0;  // a marker that is not finite, is outside the coordinate range, or whose
+                // segment is too long: no band (the status reports it)
+  for (int k = tid; k < n; k += DF_THREADS) {
+    const int kp = k + 1 == n ? 0 : k + 1;
+    const double x = a.X[2 * k], y = a.X[2 * k + 1];
+    const double ex = a.X[2 * kp] - x, ey = a.X[2 * kp + 1] - y;
+    bad |= !(fabs(x) <= MAX_COORD && fabs(y) <= MAX_COORD &&
+             ex * ex + ey * ey < MAX_SEGMENT * MAX_SEGMENT);
+    lx = fmin(lx, x);
+    hx = fmax(hx, x);
+    ly = fmin(ly, y);
+    hy = fmax(hy, y);
+  }
+  if (__syncthreads_or(bad)) return false;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lx = fmin(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+    hx = fmax(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+    ly = fmin(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+    hy = fmax(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+  }
+  if (lane == 0) {
+    ext[0][warp] = lx;
+    ext[1][warp] = hx;
+    ext[2][warp] = ly;
+    ext[3][warp] = hy;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < DF_THREADS / 32; w++) {
+      lx = fmin(lx, ext[0][w]);
+      hx = fmax(hx, ext[1][w]);
+      ly = fmin(ly, ext[2][w]);
+      hy = fmax(hy, ext[3][w]);
+    }
+    mv[0] = (int)floor(lx) - 3;
+    mv[1] = (int)floor(ly) - 3;
+    mv[2] = (int)floor(hx) + 4 - mv[0] + 1;
+    mv[3] = (int)floor(hy) + 4 - mv[1] + 1;
+    mv[5] = 0;
+    // the window must fit its bitmap, and on a periodic axis be narrower than the lattice
+    // (two window positions would be one node)
+    const bool px = a.ig.bc != IILBM_BC_CHANNEL, py = a.ig.bc == IILBM_BC_PERIODIC;
+    mv[6] = (mv[2] * mv[3] + 31) / 32 > a.words_max || (px && mv[2] > a.ig.nx) ||
+            (py && mv[3] > a.ig.ny);
+  }
+  __syncthreads();
+  if (mv[6]) return false;
+  const int words = (mv[2] * mv[3] + 31) / 32;
+  for (int w = tid; w < words; w += DF_THREADS) bits[w] = 0u;
+  __syncthreads();
+  auto mark = [&](int x, int y) {
+    if (!df_on_lattice(a, x, y)) return;
+    const int wx = x - mv[0], wy = y - mv[1];
+    if (wx < 0 || wy < 0 || wx >= mv[2] || wy >= mv[3]) {  // cannot happen: the window
+      mv[6] = 1;                                            // covers every marked node
+      return;
+    }
+    const int p = wy * mv[2] + wx;
+    atomicOr(&bits[p >> 5], 1u << (p & 31));
+  };
+  for (int k = tid; k < n; k += DF_THREADS) {  // stencils
+    const int bx = (int)floor(a.X[2 * k]) - 1, by = (int)floor(a.X[2 * k + 1]) - 1;
+    for (int l = 0; l < 16; l++) mark(bx + (l & 3), by + (l >> 2));
+  }
+  if (a.jump)
+    for (int k = tid; k < n; k += DF_THREADS) {  // the destinations a cut link can reach
+      const int kp = k + 1 == n ? 0 : k + 1;
+      const long long ax = __double2ll_rn(a.X[2 * k] * QSCALE), ay = __double2ll_rn(a.X[2 * k + 1] * QSCALE);
+      const long long bx = __double2ll_rn(a.X[2 * kp] * QSCALE), by = __double2ll_rn(a.X[2 * kp + 1] * QSCALE);
+      auto qceil = [](long long v) { return (int)-((-v) >> 24); };
+      const int x0 = qceil(min(ax, bx)) - 1, x1 = qceil(max(ax, bx));
+      const int y0 = qceil(min(ay, by)) - 1, y1 = qceil(max(ay, by));
+      for (int y = y0; y <= y1; y++)
+        for (int x = x0; x <= x1; x++) mark(x, y);
+    }
+  __syncthreads();
+  if (mv[6]) return false;
+  if (warp == 0) {  // word prefix sums of the bitmap
+    int base = 0;
+    for (int w0 = 0; w0 < words; w0 += 32) {
+      const int w = w0 + lane;
+      const int c = w < words ? __popc(bits[w]) : 0;
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (w < words) wpre[w] = base + incl - c;
+      base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) {
+      mv[4] = base;
+      mv[6] = base > a.nb_max;
+    }
+  }
+  __syncthreads();
+  if (mv[6]) return false;
+  for (int w = tid; w < words; w += DF_THREADS) {
+    unsigned word = bits[w];
+    int p = wpre[w];
+    while (word) {
+      const int b = __ffs(word) - 1;
+      bpos[p++] = w * 32 + b;
+      word &= word - 1u;
+    }
+  }
+  if (a.jump)
+    for (int k = warp; k < n; k += DF_THREADS / 32) {  // cut links, a warp per segment
+      const int kp = k + 1 == n ? 0 : k + 1;
+      const long long ax = __double2ll_rn(a.X[2 * k] * QSCALE), ay = __double2ll_rn(a.X[2 * k + 1] * QSCALE);
+      const long long bx = __double2ll_rn(a.X[2 * kp] * QSCALE), by = __double2ll_rn(a.X[2 * kp + 1] * QSCALE);
+      segment_crossings<T>(ax, ay, bx, by, lane, a.ig, [&](int i, int dx, int dy, int s1, T t) {
+        // back to the window's (unwrapped) coordinates
+        int x = dx, y = dy;
+        if (a.ig.bc != IILBM_BC_CHANNEL) {
+          if (x - mv[0] >= a.ig.nx) x -= a.ig.nx;
+          if (x < mv[0]) x += a.ig.nx;
+        }
+        if (a.ig.bc == IILBM_BC_PERIODIC) {
+          if (y - mv[1] >= a.ig.ny) y -= a.ig.ny;
+          if (y < mv[1]) y += a.ig.ny;
+        }
+        const int b = df_window_index(a, bits, wpre, mv, x, y);
+        const int slot = atomicAdd(&mv[5], 1);
+        if (b < 0 || slot >= a.nl_max) {
+          mv[6] = 1;
+          return;
+        }
+        DfLink L;
+        L.t = (double)t;
+        L.b = b;
+        L.k = k;
+        L.i = i;
+        L.s = s1;
+        slinks[slot] = L;
+      });
+    }
+  __syncthreads();
+  return !mv[6];
 }
 
 // The whole force iteration of one body by one CTA of DF_THREADS threads; smem_raw is
@@ -124,7 +313,8 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
                                                    unsigned char *smem_raw) {
   using T = typename Store<S>::T;
   using B = typename BitsOf<T>::U;
-  const int NB = a.nb, n = a.n;
+  const int NB = a.moving ? a.nb_max : a.nb;  // stride of the band's arrays
+  const int n = a.n;
   T *rs = reinterpret_cast<T *>(smem_raw);  // rho* = rho0 + drho*
   T *jsx = rs + NB;                         // j* (with body / 2)
   T *jsy = jsx + NB;
@@ -150,6 +340,18 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   float *blk = wt3 + MLP_H * MLP_H;
   float *act0 = blk + MLP_BLOCK * n;
   float *act1 = act0 + MLP_H * n;
+  // a moving body's band, built below (after the network's scratch when it is used)
+  size_t off3 = off2;
+  if (a.ws_mode == WS_MLP)
+    off3 += ((size_t)n * (MLP_BLOCK + 2 * MLP_H) + (MLP_IN + 2 * MLP_H) * MLP_H) * sizeof(float);
+  off3 = (off3 + 15) & ~(size_t)15;
+  unsigned *bits = reinterpret_cast<unsigned *>(smem_raw + off3);  // window bitmap
+  int *wpre = reinterpret_cast<int *>(bits + a.words_max);           // band nodes before word
+  int *bpos = wpre + a.words_max;                                    // window position
+  size_t off4 = (size_t)(reinterpret_cast<unsigned char *>(bpos + a.nb_max) - smem_raw);
+  off4 = (off4 + 15) & ~(size_t)15;
+  DfLink *slinks = reinterpret_cast<DfLink *>(smem_raw + off4);
+  __shared__ int mv[8];  // window x0, y0, width, height; band nodes; cut links; failed
   __shared__ B red[2][DF_THREADS / 32];
   __shared__ T cst[6];  // 2^-k, rho0, body force, eta, dX: converted once, by one thread
   const int tid = threadIdx.x, lane = tid & 31;
@@ -164,10 +366,32 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   __syncthreads();
   const T is = cst[0], rho0 = cst[1], bodyx = cst[2], bodyy = cst[3], eta = cst[4], dX = cst[5];
 
+  if (a.moving && !df_build_band<T>(a, bits, wpre, bpos, slinks, mv)) {
+    if (tid == 0) atomicOr(a.status, ST_CAPACITY);
+    return;  // uniform: the band or its cut links exceed the capacities
+  }
+  const int nb = a.moving ? mv[4] : a.nb;
+  const int nl = a.moving ? mv[5] : a.nl;
+  const DfLink *links = a.moving ? slinks : a.links;
+  // lattice node of band node c
+  auto band_node = [&](int c, int &x, int &y) {
+    if (a.moving) {
+      const int pos = bpos[c], ly = pos / mv[2];
+      x = mv[0] + pos - ly * mv[2];
+      y = mv[1] + ly;
+      if (a.ig.bc != IILBM_BC_CHANNEL) x = wrap(x, geo.nx);
+      if (a.ig.bc == IILBM_BC_PERIODIC) y = wrap(y, geo.ny);
+    } else {
+      const int key = a.band[c];
+      y = key / geo.nx;
+      x = key - y * geo.nx;
+    }
+  };
+
   // rho*, j* on the band (every band node lies on the lattice); corrections cleared
-  for (int c = tid; c < NB; c += DF_THREADS) {
-    const int key = a.band[c];
-    const int y = key / geo.nx, x = key - y * geo.nx;
+  for (int c = tid; c < nb; c += DF_THREADS) {
+    int x, y;
+    band_node(c, x, y);
     T f[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) f[i] = Store<S>::ld(A[aa_loc(geo, odd, i, x, y)]) * is;
@@ -190,7 +414,8 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
     }
 #pragma unroll
     for (int l = 0; l < 16; l++) {
-      const int b = a.st[16 * k + l];
+      const int b = a.moving ? df_window_index(a, bits, wpre, mv, bx + (l & 3), by + (l >> 2))
+                             : a.st[16 * k + l];
       pw[16 * k + l] = b < 0 ? T(0) : wx[l & 3] * wy[l >> 2];
       pc[16 * k + l] = b < 0 ? 0 : b;
     }
@@ -230,8 +455,8 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
   };
   // cut links of the current jump strengths into set F
   auto add_links = [&](T *F) {
-    for (int l = tid; l < a.nl; l += DF_THREADS) {
-      const DfLink L = a.links[l];
+    for (int l = tid; l < nl; l += DF_THREADS) {
+      const DfLink L = links[l];
       const int kp = L.k + 1 == n ? 0 : L.k + 1;
       const T c = df_link_coef<T>(L, Fnk[L.k], Fnk[kp]);
       atomicAdd(&F[L.b], c);
@@ -304,7 +529,7 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
     }
   }
   __syncthreads();
-  if (a.nl) {
+  if (nl) {
     add_links(cur);
     __syncthreads();
   }
@@ -372,7 +597,7 @@ __device__ __forceinline__ void direct_forcing_cta(const S *__restrict__ A, cons
       __syncthreads();
       break;
     }
-    if (a.nl) {
+    if (nl) {
       add_links(nxt);
       __syncthreads();
     }

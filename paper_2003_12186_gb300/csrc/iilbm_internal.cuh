@@ -151,6 +151,18 @@ __device__ inline long long aa_loc(const Geom &g, bool odd, int i, int x, int y)
 
 }  // namespace iilbm
 
+// The rigid body of section 2.3 carrying a directly forced interface: its state on the
+// device (one CTA updates it after every step, so graph replay carries it along).
+struct iilbm_body_dev {
+  int mode, dof;
+  double A, umax, m, I, Vs, rho_f;
+  double k[3], c[3];
+  double Xc0[2], Xc[2], Uc[2], Ucp[2], ac[2];
+  double th, W, Wp, wdot;
+  double F[3];      // the last F_ext (x, y) and T_ext
+  long long t;      // time level of the state
+};
+
 // ------------------------------------------------------------------ handle
 struct iilbm_lattice {
   iilbm_config cfg;
@@ -219,6 +231,12 @@ struct iilbm_lattice {
   int *df_st;
   void *df_links;
   int df_nl;
+  // a rigid body carrying the directly forced interface (iilbm_set_rigid_body): its
+  // state on the device, the markers' offsets from its centre at angle 0, and the
+  // capacities of the band the force iteration rebuilds every step
+  struct iilbm_body_dev *body;
+  double *body_X0;
+  int body_words, body_nb, body_nl;
   double *d_res;      // direct forcing residual scratch
   // diagnostics
   bool timing;
@@ -249,6 +267,8 @@ int launch_interface_phase(iilbm_lattice *h, int buf, cudaStream_t s);
 int launch_interp_interface(iilbm_lattice *h, cudaStream_t s);
 int launch_channel_bc(iilbm_lattice *h);
 int launch_direct_forcing(iilbm_lattice *h);
+int launch_body_update(iilbm_lattice *h);
+void free_body(iilbm_lattice *h);
 int launch_df_features(iilbm_lattice *h, float re, float *F);
 size_t direct_forcing_smem(const iilbm_lattice *h, int nb, int n);
 int setup_direct_forcing(iilbm_lattice *h, const double *hx);

@@ -28,6 +28,7 @@ SPRING, SPRING_REST, PRESCRIBED, DIRECT = 0, 1, 2, 3
 OPT_CUDA_GRAPH, OPT_OVERLAP, OPT_VECTOR_KERNEL, OPT_FORCED_BLOCKS = 0, 1, 2, 3
 WS_GIVEN, WS_PREVIOUS, WS_MLP = 0, 1, 2
 MLP_PARAMS, MLP_FEATURES = 10434, 30
+BODY_PRESCRIBED_X, BODY_FREE = 1, 2
 STORAGE = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
 STORAGE_BYTES = {F64: 8, F32: 4, F16: 2, BF16: 2}
 
@@ -50,6 +51,13 @@ class iilbm_interface_params(C.Structure):
     _fields_ = [("model", C.c_int32), ("moves", C.c_int32), ("stiffness", C.c_double),
                 ("dX", C.c_double), ("rest_length", C.c_double), ("eta", C.c_double),
                 ("mdf_iters", C.c_int32), ("curve", C.c_int32), ("mdf_tol", C.c_double)]
+
+
+class iilbm_body_params(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("dof", C.c_int32), ("amplitude", C.c_double),
+                ("u_max", C.c_double), ("mass", C.c_double), ("inertia", C.c_double),
+                ("volume", C.c_double), ("spring", C.c_double * 3),
+                ("damping", C.c_double * 3)]
 
 
 _lib = None
@@ -83,6 +91,8 @@ SIGNATURES = {
                         C.c_float, C.c_float, _P],
     "iilbm_get_unforced_velocity": [_H, _P],
     "iilbm_get_body_force": [_H, C.POINTER(C.c_double)],
+    "iilbm_set_rigid_body": [_H, C.POINTER(iilbm_body_params)],
+    "iilbm_get_rigid_body": [_H, C.POINTER(C.c_double)],
     "iilbm_get_cut_link_count": [_H, C.POINTER(C.c_int32)],
     "iilbm_get_jump": [_H, _P],
     "iilbm_set_timing": [_H, C.c_int32],
@@ -365,6 +375,24 @@ class Lattice:
         F = (C.c_double * 2)()
         _check("iilbm_get_body_force", self._L.iilbm_get_body_force(self._h, F))
         return F[0], F[1]
+
+    def iilbm_set_rigid_body(self, mode, dof=0, amplitude=0.0, u_max=0.0, mass=1.0,
+                             inertia=1.0, volume=0.0, spring=(0.0, 0.0, 0.0),
+                             damping=(0.0, 0.0, 0.0)):
+        """Make the directly forced interface a rigid body (section 2.3): BODY_PRESCRIBED_X
+        (harmonic translation of section 4.4) or BODY_FREE (Eqs. 27-29 with springs and
+        dampers on the degrees of freedom in dof: 1 x, 2 y, 4 rotation)."""
+        bp = iilbm_body_params(int(mode), int(dof), float(amplitude), float(u_max),
+                               float(mass), float(inertia), float(volume),
+                               (C.c_double * 3)(*[float(v) for v in spring]),
+                               (C.c_double * 3)(*[float(v) for v in damping]))
+        _check("iilbm_set_rigid_body", self._L.iilbm_set_rigid_body(self._h, C.byref(bp)))
+
+    def iilbm_get_rigid_body(self):
+        """Body state: dict of Xc, Yc, theta, Ux, Uy, W, Fx, Fy, T (the last F_ext, T_ext)."""
+        v = (C.c_double * 9)()
+        _check("iilbm_get_rigid_body", self._L.iilbm_get_rigid_body(self._h, v))
+        return dict(zip(("Xc", "Yc", "theta", "Ux", "Uy", "W", "Fx", "Fy", "T"), list(v)))
 
     def iilbm_get_jump(self, out=None):
         """Jump field J[8][ny][nx] (directions 1..8) of the current state's interface."""

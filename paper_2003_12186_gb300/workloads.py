@@ -166,3 +166,77 @@ def learned_channels(count: int = 64, seed: int = 0, nx: int = 512, ny: int = 12
         out.append(dict(nx=nx, ny=ny, D=D, xc=xc, yc=yc, re=re, n=n, X=X, u_max=u_max,
                         tau=0.5 + 3.0 * u_max * D / re, dX=polygon_perimeter(X) / n))
     return out
+
+
+# ------------------------------------------------------------ three dimensions
+# Closed triangulated surfaces for the D3Q19 lattice: vertices float64 [n, 3] in lattice
+# units, triangles int32 [m, 3] ordered counter-clockwise seen from outside.
+
+def d3q19_rates(tau: float) -> list:
+    """The D3Q19 MRT rates of section 2.2.1 (d'Humieres moment order): s1 = 1.19,
+    s2 = s10 = s12 = 1.4, s4 = s6 = s8 = 1.2, s9 = s11 = s13..s15 = 1/tau,
+    s16..s18 = 1.98; the conserved moments' rates 0."""
+    s = [0.0] * 19
+    s[1] = 1.19
+    s[2] = s[10] = s[12] = 1.4
+    s[4] = s[6] = s[8] = 1.2
+    s[9] = s[11] = s[13] = s[14] = s[15] = 1.0 / tau
+    s[16] = s[17] = s[18] = 1.98
+    return s
+
+
+def icosphere(level: int):
+    """Unit sphere: the icosahedron with each triangle split into four `level` times,
+    new vertices pushed out to the sphere.  Returns (vertices [n, 3], triangles [m, 3]),
+    10 * 4**level + 2 vertices."""
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    V = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t),
+         (0, -1, -t), (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    V = [np.array(v, float) / np.linalg.norm(v) for v in V]
+    F = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+         (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+         (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        mid = {}
+
+        def midpoint(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in mid:
+                p = V[a] + V[b]
+                V.append(p / np.linalg.norm(p))
+                mid[key] = len(V) - 1
+            return mid[key]
+
+        G = []
+        for a, b, c in F:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            G += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        F = G
+    X = np.array(V)
+    T = np.array(F, np.int32)
+    # orient every triangle outward (its normal along its centroid)
+    A, B, C = X[T[:, 0]], X[T[:, 1]], X[T[:, 2]]
+    flip = np.einsum("ij,ij->i", np.cross(B - A, C - A), A + B + C) < 0
+    T[flip] = T[flip][:, [0, 2, 1]]
+    return X, T
+
+
+def ellipsoid_surface(centre, axes, level: int, seed: int | None = None):
+    """An icosphere scaled to the semi-axes (a, b, c) and moved to centre; with a seed,
+    turned by a random rotation first (generic position against the lattice)."""
+    X, T = icosphere(level)
+    X = X * np.asarray(axes, float)
+    if seed is not None:
+        rng = np.random.default_rng(seed)
+        q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+        q = q * np.sign(np.diag(r))
+        if np.linalg.det(q) < 0:
+            q[:, 0] = -q[:, 0]
+        X = X @ q.T
+    return X + np.asarray(centre, float), T
+
+
+def random_df3(nx: int, ny: int, nz: int, amp: float, seed: int) -> np.ndarray:
+    """Random shifted D3Q19 populations df[19, nz, ny, nx] of amplitude amp."""
+    rng = np.random.default_rng(seed)
+    return amp * rng.standard_normal((19, nz, ny, nx))

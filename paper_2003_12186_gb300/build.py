@@ -14,10 +14,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libiilbm.so")
-SOURCES = ["lattice.cu", "interface.cu", "forcing.cu", "batch.cu", "mlp.cu", "api.cu"]
+SOURCES = ["lattice.cu", "interface.cu", "forcing.cu", "batch.cu", "mlp.cu", "api.cu",
+           "lattice3d.cu"]
 HEADERS = ["iilbm_internal.cuh", "lattice_dev.cuh", "interface_dev.cuh", "forcing_dev.cuh",
            "mlp_dev.cuh", "spline_dev.cuh",
-           os.path.join("..", "..", "include", "iilbm.h")]
+           os.path.join("..", "..", "include", "iilbm.h"),
+           os.path.join("..", "..", "include", "iilbm3d.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -1,0 +1,1210 @@
+// lattice3d.cu -- the three-dimensional II-LBM on the D3Q19 lattice (arXiv 2003.12186:
+// the D3Q19 velocity set and weights of sections 2.1 and 2.2.1, its MRT rates of section
+// 2.2.1, and the jump conditions of section 3.1, which the paper derives in three
+// dimensions).  C ABI in include/iilbm3d.h.
+//
+// One step, all on the lattice's stream:
+//   k3_vertex        one thread per vertex: surface normal and area from the incident
+//                    triangles, the Lagrangian force (prescribed or surface tension), the
+//                    normal split Fn = G.n / J, the spread of the tangential part (the
+//                    whole G in IB-LBM) into g, and the flags of the tiles the vertex's
+//                    4 x 4 x 4 support touches;
+//   k3_cut           one warp per triangle: every link x - e_i -> x that crosses it (exact
+//                    integer predicate with symbolic tie-breaks) adds s w_i/c_s^2 Fn to the
+//                    streamed population f_i(x) in place (Eq. 47);
+//   k3_stream_collide one thread per node, blocks of 128 nodes along x (a tile): AA-pattern
+//                    in-place streaming, SRT or MRT collision; flagged tiles also read and
+//                    clear g (Guo's term or the simple force term) and record the
+//                    collision's velocity for the interpolation;
+//   k3_interp        one thread per vertex: U = interp(u) (Eq. 20), X += U for a moving
+//                    surface.
+// Between steps the stored populations carry no jump: the jump of the next step's
+// surface is added at the start of that step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/iilbm3d.h"
+
+namespace iilbm3d {
+
+// ---------------------------------------------------------------- D3Q19 lattice
+// 0 rest; 1..6 = +x, -x, +y, -y, +z, -z; 7..18 the edge diagonals in opposite pairs.
+__host__ __device__ constexpr int ex(int i) {
+  return i == 1 || i == 7 || i == 9 || i == 11 || i == 13
+             ? 1
+             : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14 ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int i) {
+  return i == 3 || i == 7 || i == 10 || i == 15 || i == 17
+             ? 1
+             : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18 ? -1 : 0);
+}
+__host__ __device__ constexpr int ez(int i) {
+  return i == 5 || i == 11 || i == 14 || i == 15 || i == 18
+             ? 1
+             : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17 ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i & 1 ? i + 1 : i - 1); }
+template <typename T>
+__host__ __device__ constexpr T wt(int i) {
+  return i == 0 ? T(1) / T(3) : (i <= 6 ? T(1) / T(18) : T(1) / T(36));
+}
+static_assert(ex(opp(7)) == -ex(7) && ey(opp(9)) == -ey(9) && ez(opp(13)) == -ez(13), "pairs");
+static_assert(ex(17) == 0 && ey(17) == 1 && ez(17) == -1, "velocity 17");
+
+// d'Humieres' D3Q19 moment basis (section 2.2.1 cites it): row r evaluated on velocity i.
+__host__ __device__ constexpr int mrow(int r, int i) {
+  const int x = ex(i), y = ey(i), z = ez(i), e2 = x * x + y * y + z * z;
+  return r == 0    ? 1
+         : r == 1  ? 19 * e2 - 30
+         : r == 2  ? (21 * e2 * e2 - 53 * e2 + 24) / 2
+         : r == 3  ? x
+         : r == 4  ? (5 * e2 - 9) * x
+         : r == 5  ? y
+         : r == 6  ? (5 * e2 - 9) * y
+         : r == 7  ? z
+         : r == 8  ? (5 * e2 - 9) * z
+         : r == 9  ? 3 * x * x - e2
+         : r == 10 ? (3 * e2 - 5) * (3 * x * x - e2)
+         : r == 11 ? y * y - z * z
+         : r == 12 ? (3 * e2 - 5) * (y * y - z * z)
+         : r == 13 ? x * y
+         : r == 14 ? y * z
+         : r == 15 ? x * z
+         : r == 16 ? (y * y - z * z) * x
+         : r == 17 ? (z * z - x * x) * y
+                   : (x * x - y * y) * z;
+}
+__host__ __device__ constexpr int mnorm(int r) {
+  int s = 0;
+  for (int i = 0; i < 19; i++) s += mrow(r, i) * mrow(r, i);
+  return s;
+}
+__host__ __device__ constexpr bool conserved(int r) { return r == 0 || r == 3 || r == 5 || r == 7; }
+static_assert(mnorm(0) == 19 && mnorm(1) == 2394 && mnorm(2) == 252 && mnorm(3) == 10, "norms");
+
+constexpr int TX = 128;              // tile: 128 nodes along x (one block of the stream-collide)
+constexpr double QS = 1048576.0;     // crossing predicate: coordinates snapped to 2^-20
+constexpr int QBITS = 20;
+constexpr double MAX_EDGE = 8.0;
+constexpr double MAX_COORD = 4096.0;
+constexpr int ST_NONFINITE = 1, ST_INTERFACE = 2;
+
+struct Geom3 {
+  int nx, ny, nz, ntx;
+  long long plane;  // nodes
+};
+
+__host__ __device__ inline int wrapn(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+__host__ __device__ inline long long nodeix(const Geom3 &g, int x, int y, int z) {
+  return ((long long)z * g.ny + y) * g.nx + x;
+}
+// Where the streamed population f_i of node (x, y, z) lives at the current parity of the
+// AA pattern: even levels in place, odd levels in the opposite slot of the upstream node.
+__device__ __forceinline__ long long aa_read(const Geom3 &g, bool odd, int i, int x, int y, int z) {
+  if (!odd) return i * g.plane + nodeix(g, x, y, z);
+  return opp(i) * g.plane +
+         nodeix(g, wrapn(x - ex(i), g.nx), wrapn(y - ey(i), g.ny), wrapn(z - ez(i), g.nz));
+}
+
+template <typename T>
+struct Coll3 {
+  T omega;     // SRT: 1 / lambda
+  T s[19];     // MRT rates (conserved moments' unused)
+  T rho0;
+  T body[3];
+};
+
+// ------------------------------------------------------------------- collision
+// One node's collision, shifted populations in place (the oracle's definitions):
+//   rho = rho0 + sum f, j = sum e f; u = (j + g/2) / rho (Guo, Eq. 24) or j / rho (simple);
+//   f_eq_i = w_i (drho + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u^2));
+//   SRT: f -= omega (f - f_eq) - (1 - omega/2) Gt   (Eqs. 14, 21)
+//   MRT: f -= M^-1 [S M (f - f_eq) - (I - S/2) M Gt] (Eqs. 15, 22), M^-1 = M^T / |row|^2,
+//        the transforms unrolled over the constant integer basis;
+//   simple force term: no Gt, then 3 w_i e_i.g added (Eq. 16).
+// FORCED = false: g = 0 and the force terms are left out.
+template <typename T, bool MRT, bool FORCED, bool SIMPLE>
+__device__ __forceinline__ T collide3(T f[19], T gx, T gy, T gz, const Coll3<T> &p, T &ux,
+                                      T &uy, T &uz) {
+  T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+  for (int i = 0; i < 19; i++) {
+    drho += f[i];
+    if (ex(i)) jx += ex(i) > 0 ? f[i] : -f[i];
+    if (ey(i)) jy += ey(i) > 0 ? f[i] : -f[i];
+    if (ez(i)) jz += ez(i) > 0 ? f[i] : -f[i];
+  }
+  const T rho = p.rho0 + drho, inv = T(1) / rho;
+  const T h = FORCED && !SIMPLE ? T(0.5) : T(0);
+  ux = (jx + h * gx) * inv;
+  uy = (jy + h * gy) * inv;
+  uz = (jz + h * gz) * inv;
+  const T u2 = ux * ux + uy * uy + uz * uz;
+  T d[19];
+#pragma unroll
+  for (int i = 0; i < 19; i++) {
+    const T eu = T(ex(i)) * ux + T(ey(i)) * uy + T(ez(i)) * uz;
+    d[i] = f[i] - wt<T>(i) * (drho + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * u2));
+  }
+  T Gt[19];
+  if (FORCED && !SIMPLE) {
+#pragma unroll
+    for (int i = 0; i < 19; i++) {
+      const T eu = T(ex(i)) * ux + T(ey(i)) * uy + T(ez(i)) * uz;
+      const T eg = T(ex(i)) * gx + T(ey(i)) * gy + T(ez(i)) * gz;
+      const T ug = ux * gx + uy * gy + uz * gz;
+      Gt[i] = wt<T>(i) * (T(3) * (eg - ug) + T(9) * eu * eg);
+    }
+  }
+  if (!MRT) {
+#pragma unroll
+    for (int i = 0; i < 19; i++) {
+      f[i] -= p.omega * d[i];
+      if (FORCED && !SIMPLE) f[i] += (T(1) - T(0.5) * p.omega) * Gt[i];
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 19; r++) {
+      T c = T(0);
+      if (!conserved(r)) {
+        T a = T(0);
+#pragma unroll
+        for (int i = 0; i < 19; i++)
+          if (mrow(r, i)) a += T(mrow(r, i)) * d[i];
+        c = p.s[r] * a;
+      }
+      if (FORCED && !SIMPLE) {
+        T b = T(0);
+#pragma unroll
+        for (int i = 0; i < 19; i++)
+          if (mrow(r, i)) b += T(mrow(r, i)) * Gt[i];
+        c -= (conserved(r) ? T(1) : T(1) - T(0.5) * p.s[r]) * b;
+      }
+      c *= T(1) / T(mnorm(r));
+#pragma unroll
+      for (int i = 0; i < 19; i++)
+        if (mrow(r, i)) f[i] -= T(mrow(r, i)) * c;
+    }
+  }
+  if (FORCED && SIMPLE) {
+#pragma unroll
+    for (int i = 0; i < 19; i++) {
+      const T eg = T(ex(i)) * gx + T(ey(i)) * gy + T(ez(i)) * gz;
+      f[i] += T(3) * wt<T>(i) * eg;
+    }
+  }
+  return drho;
+}
+
+}  // namespace iilbm3d
+
+// ---------------------------------------------------------------------- handle
+struct iilbm3d_lattice {
+  iilbm3d_config cfg;
+  iilbm3d::Geom3 geo;
+  int device;
+  cudaStream_t stream;
+  bool own_stream;
+  bool f64;           // storage (and arithmetic) FP64, else FP32
+  void *A;            // [19][plane] populations
+  void *gf;           // [3][plane] spread force (arithmetic type), zero outside flagged tiles
+  void *uf;           // [3][plane] collision velocity on flagged tiles
+  unsigned *flags;    // [ntiles] tile carries a spread force / marker support
+  int *d_status;
+  int *d_count;       // cut-link crossings of the most recent surface pass
+  long long step;     // time level; AA parity = step & 1
+  bool prepared;      // the current level's vertex pass already ran (g, flags, Fn)
+  // surface
+  int n, m;
+  iilbm3d_surface_params sp;
+  double *X, *Gp, *G, *U, *Fn, *Aref;
+  int *tri, *vt_start, *vt_list;  // triangles; each vertex's triangles (CSR, ascending)
+  // graphs: two steps from an even level
+  cudaGraphExec_t gexec;
+  // timing
+  bool timing;
+  std::vector<cudaEvent_t> ev;
+  int nev;
+  double sc_ms;
+  int sc_launches;
+  long long kernels;
+};
+
+namespace iilbm3d {
+
+// --------------------------------------------------------------- stream-collide
+// Tile (blockIdx.x, y, z) = nodes x in [128 blockIdx.x, +128) of row (y, z).  A flagged tile
+// reads the spread force (and clears it and its flag for the next step), collides with it
+// and records the collision's velocity u for the interpolation.
+template <typename T, bool MRT, bool SIMPLE, bool BODY>
+__global__ void __launch_bounds__(TX)
+    k3_stream_collide(T *__restrict__ A, const Geom3 g, int odd, const Coll3<T> p,
+                      unsigned *__restrict__ flags, T *__restrict__ gf, T *__restrict__ uf,
+                      int *__restrict__ status) {
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+  const long long tile = ((long long)z * g.ny + y) * g.ntx + blockIdx.x;
+  const bool forced = flags[tile] != 0u;
+  __syncthreads();  // every thread has read the flag before it is cleared
+  if (forced && threadIdx.x == 0) flags[tile] = 0u;
+  if (x >= g.nx) return;
+  const long long c = nodeix(g, x, y, z);
+  long long loc[19];
+  T f[19];
+#pragma unroll
+  for (int i = 0; i < 19; i++) {
+    loc[i] = aa_read(g, odd, i, x, y, z);
+    f[i] = A[loc[i]];
+  }
+  T ux, uy, uz, drho;
+  if (forced || BODY) {
+    T gx = p.body[0], gy = p.body[1], gz = p.body[2];
+    if (forced) {
+      gx += gf[c];
+      gy += gf[g.plane + c];
+      gz += gf[2 * g.plane + c];
+      gf[c] = T(0);
+      gf[g.plane + c] = T(0);
+      gf[2 * g.plane + c] = T(0);
+    }
+    drho = collide3<T, MRT, true, SIMPLE>(f, gx, gy, gz, p, ux, uy, uz);
+    if (forced) {
+      uf[c] = ux;
+      uf[g.plane + c] = uy;
+      uf[2 * g.plane + c] = uz;
+    }
+  } else {
+    drho = collide3<T, MRT, false, SIMPLE>(f, T(0), T(0), T(0), p, ux, uy, uz);
+  }
+  if (!(fabs((double)drho) < 1e30)) atomicOr(status, ST_NONFINITE);
+  // post-collision f_i goes where the streamed f_opp(i) was read (in place)
+#pragma unroll
+  for (int i = 0; i < 19; i++) A[loc[opp(i)]] = f[i];
+}
+
+}  // namespace iilbm3d
+
+namespace iilbm3d {
+
+// Peskin's four-point kernel (the delta function the paper names after Eq. 6).
+__device__ __forceinline__ double phi4(double r) {
+  const double a = fabs(r);
+  if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) * 0.125;
+  if (a <= 2.0) return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) * 0.125;
+  return 0.0;
+}
+
+__device__ __forceinline__ int wrapfull(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// ------------------------------------------------------------------ vertex pass
+// Vertex k: from its triangles (ascending), N_t = (B - A) x (C - A), the current area
+// a_k = sum |N_t| / 6 and normal n_k = sum N_t / |sum N_t|; the force G_k (prescribed, or
+// surface tension -gamma sum_t (1/2) N_t/|N_t| x (X_q - X_p) / Aref_k for t = (k, p, q));
+// Fn_k = G_k.n_k / (a_k / Aref_k); the spread of P_k = (G_k - (G_k.n_k) n_k) Aref_k (II-LBM)
+// or G_k Aref_k (IB-LBM) over its 4 x 4 x 4 support, and the flags of the tiles there.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k3_vertex(const double *__restrict__ X, int n, const int *__restrict__ tri,
+              const int *__restrict__ vt_start, const int *__restrict__ vt_list,
+              const double *__restrict__ Aref, int model, double gamma,
+              const double *__restrict__ Gp, int jump, const Geom3 g, double *__restrict__ G,
+              double *__restrict__ Fn, T *__restrict__ gf, unsigned *__restrict__ flags,
+              int *__restrict__ status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double xk = X[3 * k], yk = X[3 * k + 1], zk = X[3 * k + 2];
+  if (!(fabs(xk) < MAX_COORD && fabs(yk) < MAX_COORD && fabs(zk) < MAX_COORD)) {
+    atomicOr(status, ST_INTERFACE);
+    return;
+  }
+  double ns[3] = {0.0, 0.0, 0.0}, area = 0.0, Gk[3] = {0.0, 0.0, 0.0};
+  for (int q = vt_start[k]; q < vt_start[k + 1]; q++) {
+    const int t = vt_list[q];
+    const int v0 = tri[3 * t], v1 = tri[3 * t + 1], v2 = tri[3 * t + 2];
+    const double *A = X + 3 * v0, *B = X + 3 * v1, *C = X + 3 * v2;
+    const double u[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+    const double v[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+    const double N[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2],
+                         u[0] * v[1] - u[1] * v[0]};
+    const double l = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    area += l / 6.0;
+    ns[0] += N[0];
+    ns[1] += N[1];
+    ns[2] += N[2];
+    if (model == IILBM3D_TENSION) {
+      const int p = v0 == k ? v1 : (v1 == k ? v2 : v0);
+      const int r = v0 == k ? v2 : (v1 == k ? v0 : v1);
+      const double h[3] = {N[0] / l, N[1] / l, N[2] / l};
+      const double e[3] = {X[3 * r] - X[3 * p], X[3 * r + 1] - X[3 * p + 1],
+                           X[3 * r + 2] - X[3 * p + 2]};
+      const double dA[3] = {0.5 * (h[1] * e[2] - h[2] * e[1]), 0.5 * (h[2] * e[0] - h[0] * e[2]),
+                            0.5 * (h[0] * e[1] - h[1] * e[0])};
+      Gk[0] -= gamma * dA[0];
+      Gk[1] -= gamma * dA[1];
+      Gk[2] -= gamma * dA[2];
+    }
+  }
+  const double ln = sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
+  const double nk[3] = {ns[0] / ln, ns[1] / ln, ns[2] / ln};
+  const double ar = Aref[k];
+  if (model == IILBM3D_TENSION) {
+    Gk[0] /= ar;
+    Gk[1] /= ar;
+    Gk[2] /= ar;
+  } else {
+    Gk[0] = Gp[3 * k];
+    Gk[1] = Gp[3 * k + 1];
+    Gk[2] = Gp[3 * k + 2];
+  }
+  G[3 * k] = Gk[0];
+  G[3 * k + 1] = Gk[1];
+  G[3 * k + 2] = Gk[2];
+  const double gn = Gk[0] * nk[0] + Gk[1] * nk[1] + Gk[2] * nk[2];
+  Fn[k] = gn / (area / ar);
+  double P[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) P[d] = (jump ? Gk[d] - gn * nk[d] : Gk[d]) * ar;
+  const int bx = (int)floor(xk) - 1, by = (int)floor(yk) - 1, bz = (int)floor(zk) - 1;
+  double wx[4], wy[4], wz[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    wx[q] = phi4((double)(bx + q) - xk);
+    wy[q] = phi4((double)(by + q) - yk);
+    wz[q] = phi4((double)(bz + q) - zk);
+  }
+  for (int dz = 0; dz < 4; dz++) {
+    const int z = wrapfull(bz + dz, g.nz);
+    for (int dy = 0; dy < 4; dy++) {
+      const int y = wrapfull(by + dy, g.ny);
+      int last = -1;
+      for (int dx = 0; dx < 4; dx++) {
+        const int x = wrapfull(bx + dx, g.nx);
+        const double w = wx[dx] * wy[dy] * wz[dz];
+        const long long c = nodeix(g, x, y, z);
+        atomicAdd(&gf[c], T(P[0] * w));
+        atomicAdd(&gf[g.plane + c], T(P[1] * w));
+        atomicAdd(&gf[2 * g.plane + c], T(P[2] * w));
+        const int tx = x / TX;
+        if (tx != last) {
+          flags[((long long)z * g.ny + y) * g.ntx + tx] = 1u;
+          last = tx;
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ cut links
+// The exact crossing predicate (coordinates snapped to 2^-20, every lattice node displaced
+// by (eps, eps^2, eps^3), eps -> 0+): the plane side of a node is the sign of the first
+// non-zero of (N.(X - A), N_x, N_y, N_z); the side of the displaced link line about edge
+// U -> V that of (det[d, U - P, V - P], -w_x, -w_y, -w_z), w = (V - U) x d.
+__device__ __forceinline__ int plane_side(const long long *A, const long long *N, const long long *Xq) {
+  const __int128 r = (__int128)N[0] * (Xq[0] - A[0]) + (__int128)N[1] * (Xq[1] - A[1]) +
+                     (__int128)N[2] * (Xq[2] - A[2]);
+  if (r != 0) return r > 0 ? 1 : -1;
+  for (int d = 0; d < 3; d++)
+    if (N[d] != 0) return N[d] > 0 ? 1 : -1;
+  return 0;
+}
+__device__ __forceinline__ int edge_side(const long long *P, int dx, int dy, int dz,
+                                         const long long *U, const long long *V, long long &det) {
+  const long long a[3] = {U[0] - P[0], U[1] - P[1], U[2] - P[2]};
+  const long long b[3] = {V[0] - P[0], V[1] - P[1], V[2] - P[2]};
+  const long long o = dx * (a[1] * b[2] - a[2] * b[1]) + dy * (a[2] * b[0] - a[0] * b[2]) +
+                      dz * (a[0] * b[1] - a[1] * b[0]);
+  det = o;
+  if (o != 0) return o > 0 ? 1 : -1;
+  const long long e[3] = {V[0] - U[0], V[1] - U[1], V[2] - U[2]};
+  const long long w[3] = {e[1] * dz - e[2] * dy, e[2] * dx - e[0] * dz, e[0] * dy - e[1] * dx};
+  for (int k = 0; k < 3; k++)
+    if (w[k] != 0) return w[k] > 0 ? -1 : 1;
+  return 0;
+}
+
+// One warp per triangle: every candidate link (destinations in [ceil(min) - 1, ceil(max)]
+// per axis, 18 directions) tested; a crossing adds coef = s w_i / c_s^2 Fn(crossing), Fn
+// interpolated barycentrically over the triangle, to the streamed population in place
+// (INPLACE) or to the field J[i-1][node] (read-outs).
+template <bool INPLACE, typename S>
+__global__ void __launch_bounds__(128)
+    k3_cut(const double *__restrict__ X, const int *__restrict__ tri, int m,
+           const double *__restrict__ Fn, const Geom3 g, int odd, S *__restrict__ A,
+           double *__restrict__ J, int *__restrict__ count, int *__restrict__ status) {
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (t >= m) return;
+  const int vi[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
+  long long q[3][3];
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 3; j++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const double v = X[3 * vi[j] + a];
+      ok = ok && fabs(v) < MAX_COORD;
+      q[j][a] = __double2ll_rn(v * QS);
+    }
+  const long long lim = (long long)(MAX_EDGE * QS);
+#pragma unroll
+  for (int j = 0; j < 3; j++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const long long d = q[(j + 1) % 3][a] - q[j][a];
+      ok = ok && d < lim && -d < lim;
+    }
+  if (!ok) {
+    if (lane == 0) atomicOr(status, ST_INTERFACE);
+    return;
+  }
+  const long long u[3] = {q[1][0] - q[0][0], q[1][1] - q[0][1], q[1][2] - q[0][2]};
+  const long long v[3] = {q[2][0] - q[0][0], q[2][1] - q[0][1], q[2][2] - q[0][2]};
+  const long long N[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2],
+                          u[0] * v[1] - u[1] * v[0]};
+  int lo[3], ext[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const long long mn = min(q[0][a], min(q[1][a], q[2][a]));
+    const long long mx = max(q[0][a], max(q[1][a], q[2][a]));
+    lo[a] = (int)(-((-mn) >> QBITS)) - 1;
+    ext[a] = (int)(-((-mx) >> QBITS)) - lo[a] + 1;
+  }
+  const int ncand = ext[0] * ext[1] * ext[2] * 18;
+  const long long Sx = 1LL << QBITS;
+  int found = 0;
+  for (int c = lane; c < ncand; c += 32) {
+    const int i = 1 + c % 18, cell = c / 18;
+    const int x = lo[0] + cell % ext[0], y = lo[1] + (cell / ext[0]) % ext[1];
+    const int z = lo[2] + cell / (ext[0] * ext[1]);
+    const int dx = ex(i), dy = ey(i), dz = ez(i);
+    const long long Q[3] = {x * Sx, y * Sx, z * Sx};
+    const long long P[3] = {Q[0] - dx * Sx, Q[1] - dy * Sx, Q[2] - dz * Sx};
+    const int sP = plane_side(q[0], N, P), sQ = plane_side(q[0], N, Q);
+    if (sP == sQ || sP == 0 || sQ == 0) continue;
+    long long vAB, vBC, vCA;
+    const int e1 = edge_side(P, dx, dy, dz, q[0], q[1], vAB);
+    const int e2 = edge_side(P, dx, dy, dz, q[1], q[2], vBC);
+    const int e3 = edge_side(P, dx, dy, dz, q[2], q[0], vCA);
+    if (e1 == 0 || e1 != e2 || e2 != e3) continue;
+    const double s = (double)vAB + (double)vBC + (double)vCA;
+    const double fc = ((double)vBC / s) * Fn[vi[0]] + ((double)vCA / s) * Fn[vi[1]] +
+                      ((double)vAB / s) * Fn[vi[2]];
+    const double coef = (double)sQ * wt<double>(i) * 3.0 * fc;
+    const int xw = wrapfull(x, g.nx), yw = wrapfull(y, g.ny), zw = wrapfull(z, g.nz);
+    if (INPLACE)
+      atomicAdd(&A[aa_read(g, odd != 0, i, xw, yw, zw)], S(coef));
+    else
+      atomicAdd(&J[(long long)(i - 1) * g.plane + nodeix(g, xw, yw, zw)], coef);
+    found++;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) found += __shfl_xor_sync(0xffffffffu, found, o);
+  if (lane == 0 && found) atomicAdd(count, found);
+}
+
+// ------------------------------------------------------------------ interpolation
+// U_k = sum over the 4 x 4 x 4 support of u(x) phi phi phi (Eq. 20), u the collision's
+// velocity recorded by the flagged tiles; X_k += U_k for a moving surface.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k3_interp(const T *__restrict__ uf, const Geom3 g, double *__restrict__ X, int n,
+              double *__restrict__ U, int moves) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double xk = X[3 * k], yk = X[3 * k + 1], zk = X[3 * k + 2];
+  if (!(fabs(xk) < MAX_COORD && fabs(yk) < MAX_COORD && fabs(zk) < MAX_COORD)) return;
+  const int bx = (int)floor(xk) - 1, by = (int)floor(yk) - 1, bz = (int)floor(zk) - 1;
+  double wx[4], wy[4], wz[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    wx[q] = phi4((double)(bx + q) - xk);
+    wy[q] = phi4((double)(by + q) - yk);
+    wz[q] = phi4((double)(bz + q) - zk);
+  }
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int dz = 0; dz < 4; dz++) {
+    const int z = wrapfull(bz + dz, g.nz);
+    for (int dy = 0; dy < 4; dy++) {
+      const int y = wrapfull(by + dy, g.ny);
+      for (int dx = 0; dx < 4; dx++) {
+        const long long c = nodeix(g, wrapfull(bx + dx, g.nx), y, z);
+        const double w = wx[dx] * wy[dy] * wz[dz];
+        s0 += (double)uf[c] * w;
+        s1 += (double)uf[g.plane + c] * w;
+        s2 += (double)uf[2 * g.plane + c] * w;
+      }
+    }
+  }
+  U[3 * k] = s0;
+  U[3 * k + 1] = s1;
+  U[3 * k + 2] = s2;
+  if (moves) {
+    X[3 * k] = xk + s0;
+    X[3 * k + 1] = yk + s1;
+    X[3 * k + 2] = zk + s2;
+  }
+}
+
+// ------------------------------------------------------------- conversions, read-out
+// FP64 natural layout df[i][node] <-> the stored populations at the current AA parity.
+template <typename S>
+__global__ void k3_store(S *__restrict__ A, const double *__restrict__ df, const Geom3 g, int odd) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.plane) return;
+  const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
+  for (int i = 0; i < 19; i++) A[aa_read(g, odd != 0, i, x, y, z)] = S(df[i * g.plane + c]);
+}
+template <typename S>
+__global__ void k3_load(const S *__restrict__ A, double *__restrict__ df, const Geom3 g, int odd) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.plane) return;
+  const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
+  for (int i = 0; i < 19; i++) df[i * g.plane + c] = (double)A[aa_read(g, odd != 0, i, x, y, z)];
+}
+// drho and u (Eq. 24) from the stored populations plus the jump field J (may be null) and
+// the spread force plus the body force; h = 1/2 (Guo) or 0 (simple force term).
+template <typename S>
+__global__ void k3_macros(const S *__restrict__ A, const double *__restrict__ J,
+                          const S *__restrict__ gf, const Geom3 g, int odd, double rho0,
+                          double bx, double by, double bz, double h, double *__restrict__ out) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.plane) return;
+  const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
+  double s = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+  for (int i = 0; i < 19; i++) {
+    double f = (double)A[aa_read(g, odd != 0, i, x, y, z)];
+    if (J && i > 0) f += J[(long long)(i - 1) * g.plane + c];
+    s += f;
+    jx += ex(i) * f;
+    jy += ey(i) * f;
+    jz += ez(i) * f;
+  }
+  const double gx = bx + (double)gf[c], gy = by + (double)gf[g.plane + c],
+               gz = bz + (double)gf[2 * g.plane + c];
+  out[c] = s;
+  out[g.plane + c] = (jx + h * gx) / (rho0 + s);
+  out[2 * g.plane + c] = (jy + h * gy) / (rho0 + s);
+  out[3 * g.plane + c] = (jz + h * gz) / (rho0 + s);
+}
+
+}  // namespace iilbm3d
+
+namespace iilbm3d {
+
+template <typename S>
+__global__ void k3_equilibrium(S *__restrict__ A, const Geom3 g, int odd, double rho0,
+                               const double *__restrict__ drho, const double *__restrict__ ux,
+                               const double *__restrict__ uy, const double *__restrict__ uz) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.plane) return;
+  const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
+  const double d = drho ? drho[c] : 0.0, u0 = ux ? ux[c] : 0.0, u1 = uy ? uy[c] : 0.0,
+               u2 = uz ? uz[c] : 0.0;
+  const double rho = rho0 + d, uu = u0 * u0 + u1 * u1 + u2 * u2;
+  for (int i = 0; i < 19; i++) {
+    const double eu = ex(i) * u0 + ey(i) * u1 + ez(i) * u2;
+    const double poly = eu * 3.0 + eu * eu * 4.5 - uu * 1.5;
+    A[aa_read(g, odd != 0, i, x, y, z)] = S(wt<double>(i) * (d + rho * poly));
+  }
+}
+
+}  // namespace iilbm3d
+
+// ------------------------------------------------------------------------ host
+namespace {
+using namespace iilbm3d;
+using H = iilbm3d_lattice;
+
+#define CK3(call)                        \
+  do {                                   \
+    cudaError_t e_ = (call);             \
+    if (e_ != cudaSuccess) {             \
+      cudaGetLastError();                \
+      return IILBM_ERR_CUDA;             \
+    }                                    \
+  } while (0)
+#define RC3(expr)          \
+  do {                     \
+    int r_ = (expr);       \
+    if (r_) return r_;     \
+  } while (0)
+
+unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename S>
+Coll3<S> coll_params(const H *h) {
+  Coll3<S> p;
+  p.omega = S(1.0 / h->cfg.tau);
+  for (int r = 0; r < 19; r++) p.s[r] = S(h->cfg.s[r]);
+  p.rho0 = S(h->cfg.rho0);
+  for (int d = 0; d < 3; d++) p.body[d] = S(h->cfg.body[d]);
+  return p;
+}
+
+bool has_body(const H *h) { return h->cfg.body[0] != 0.0 || h->cfg.body[1] != 0.0 || h->cfg.body[2] != 0.0; }
+
+template <typename S, bool MRT, bool SIMPLE>
+void launch_sc_t(H *h, cudaStream_t s) {
+  const Geom3 &g = h->geo;
+  const dim3 grid(g.ntx, g.ny, g.nz);
+  const Coll3<S> p = coll_params<S>(h);
+  if (has_body(h))
+    k3_stream_collide<S, MRT, SIMPLE, true><<<grid, TX, 0, s>>>(
+        (S *)h->A, g, (int)(h->step & 1), p, h->flags, (S *)h->gf, (S *)h->uf, h->d_status);
+  else
+    k3_stream_collide<S, MRT, SIMPLE, false><<<grid, TX, 0, s>>>(
+        (S *)h->A, g, (int)(h->step & 1), p, h->flags, (S *)h->gf, (S *)h->uf, h->d_status);
+}
+
+template <typename S>
+void launch_sc_s(H *h, cudaStream_t s) {
+  const bool mrt = h->cfg.collision == IILBM_MRT, simple = h->cfg.force == IILBM_FORCE_SIMPLE;
+  if (mrt && simple) launch_sc_t<S, true, true>(h, s);
+  else if (mrt) launch_sc_t<S, true, false>(h, s);
+  else if (simple) launch_sc_t<S, false, true>(h, s);
+  else launch_sc_t<S, false, false>(h, s);
+}
+
+void launch_sc(H *h) {
+  if (h->f64) launch_sc_s<double>(h, h->stream);
+  else launch_sc_s<float>(h, h->stream);
+}
+
+void launch_vertex(H *h) {
+  const Geom3 &g = h->geo;
+  const unsigned b = blocks_for(h->n, 128);
+  if (h->f64)
+    k3_vertex<double><<<b, 128, 0, h->stream>>>(h->X, h->n, h->tri, h->vt_start, h->vt_list, h->Aref,
+                                                h->sp.model, h->sp.gamma, h->Gp, h->cfg.jump, g,
+                                                h->G, h->Fn, (double *)h->gf, h->flags, h->d_status);
+  else
+    k3_vertex<float><<<b, 128, 0, h->stream>>>(h->X, h->n, h->tri, h->vt_start, h->vt_list, h->Aref,
+                                               h->sp.model, h->sp.gamma, h->Gp, h->cfg.jump, g,
+                                               h->G, h->Fn, (float *)h->gf, h->flags, h->d_status);
+}
+
+// the jump of the current level: in place into the populations (J null) or into J
+void launch_cut(H *h, double *J) {
+  const unsigned b = blocks_for((long long)h->m * 32, 128);
+  const int odd = (int)(h->step & 1);
+  if (J) {
+    if (h->f64)
+      k3_cut<false, double><<<b, 128, 0, h->stream>>>(h->X, h->tri, h->m, h->Fn, h->geo, odd,
+                                                      (double *)h->A, J, h->d_count, h->d_status);
+    else
+      k3_cut<false, float><<<b, 128, 0, h->stream>>>(h->X, h->tri, h->m, h->Fn, h->geo, odd,
+                                                     (float *)h->A, J, h->d_count, h->d_status);
+  } else {
+    if (h->f64)
+      k3_cut<true, double><<<b, 128, 0, h->stream>>>(h->X, h->tri, h->m, h->Fn, h->geo, odd,
+                                                     (double *)h->A, nullptr, h->d_count, h->d_status);
+    else
+      k3_cut<true, float><<<b, 128, 0, h->stream>>>(h->X, h->tri, h->m, h->Fn, h->geo, odd,
+                                                    (float *)h->A, nullptr, h->d_count, h->d_status);
+  }
+}
+
+void launch_interp(H *h) {
+  const unsigned b = blocks_for(h->n, 128);
+  if (h->f64)
+    k3_interp<double><<<b, 128, 0, h->stream>>>((const double *)h->uf, h->geo, h->X, h->n, h->U,
+                                                h->sp.moves);
+  else
+    k3_interp<float><<<b, 128, 0, h->stream>>>((const float *)h->uf, h->geo, h->X, h->n, h->U,
+                                               h->sp.moves);
+}
+
+// One time step (see the file's head).  The stream-collide is bracketed by timing events
+// when timing is on (eager steps only).
+int one_step(H *h) {
+  if (h->n > 0) {
+    if (!h->prepared) launch_vertex(h);
+    CK3(cudaMemsetAsync(h->d_count, 0, sizeof(int), h->stream));
+    if (h->cfg.jump) launch_cut(h, nullptr);
+  }
+  if (h->timing) {
+    if (2 * h->nev + 2 > (int)h->ev.size()) {
+      for (int q = 0; q < 64; q++) {
+        cudaEvent_t e;
+        CK3(cudaEventCreate(&e));
+        h->ev.push_back(e);
+      }
+    }
+    CK3(cudaEventRecord(h->ev[2 * h->nev], h->stream));
+  }
+  launch_sc(h);
+  if (h->timing) {
+    CK3(cudaEventRecord(h->ev[2 * h->nev + 1], h->stream));
+    h->nev++;
+    h->kernels += h->n > 0 ? (h->cfg.jump ? 4 : 3) - (h->prepared ? 1 : 0) : 1;
+  }
+  if (h->n > 0) launch_interp(h);
+  CK3(cudaGetLastError());
+  h->step++;
+  h->prepared = false;
+  return IILBM_OK;
+}
+
+void drop_graph(H *h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+}
+
+// Two steps from an even level, captured once and replayed.
+int capture_pair(H *h) {
+  cudaGraph_t graph = nullptr;
+  CK3(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = one_step(h);
+  if (!rc) rc = one_step(h);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  h->step -= 2;  // capture only recorded the launches
+  if (rc || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc ? rc : IILBM_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&h->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->gexec = nullptr;
+    cudaGetLastError();
+    return IILBM_ERR_CUDA;
+  }
+  return IILBM_OK;
+}
+
+int read_status3(H *h) {
+  int st = 0;
+  CK3(cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK3(cudaStreamSynchronize(h->stream));
+  if (st & ST_NONFINITE) return IILBM_ERR_NONFINITE;
+  if (st & ST_INTERFACE) return IILBM_ERR_INTERFACE;
+  return IILBM_OK;
+}
+
+void free_surface(H *h) {
+  void *p[] = {h->X, h->Gp, h->G, h->U, h->Fn, h->Aref, h->tri, h->vt_start, h->vt_list};
+  for (void *q : p)
+    if (q) cudaFree(q);
+  h->X = h->Gp = h->G = h->U = h->Fn = h->Aref = nullptr;
+  h->tri = h->vt_start = h->vt_list = nullptr;
+  h->n = h->m = 0;
+}
+
+// FP64 [count] from host or device memory into a fresh device buffer (caller frees).
+int to_device(const double *src, size_t count, cudaStream_t s, double **out) {
+  *out = nullptr;
+  if (!src) return IILBM_OK;
+  if (cudaMalloc(out, count * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return IILBM_ERR_OOM;
+  }
+  if (cudaMemcpyAsync(*out, src, count * sizeof(double), cudaMemcpyDefault, s) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(*out);
+    *out = nullptr;
+    return IILBM_ERR_CUDA;
+  }
+  return IILBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
+  if (!out || !cfg) return IILBM_ERR_INVALID_ARG;
+  *out = nullptr;
+  const iilbm3d_config &c = *cfg;
+  const int lim[3] = {c.nx, c.ny, c.nz};
+  for (int a = 0; a < 3; a++)
+    if (lim[a] < 4 || lim[a] > 2048) return IILBM_ERR_INVALID_ARG;
+  if ((long long)c.nx * c.ny * c.nz > (1LL << 31)) return IILBM_ERR_INVALID_ARG;
+  if (c.collision != IILBM_SRT && c.collision != IILBM_MRT) return IILBM_ERR_INVALID_ARG;
+  if (c.storage != IILBM_F64 && c.storage != IILBM_F32) return IILBM_ERR_INVALID_ARG;
+  if ((c.jump != 0 && c.jump != 1) || (c.force != IILBM_FORCE_GUO && c.force != IILBM_FORCE_SIMPLE))
+    return IILBM_ERR_INVALID_ARG;
+  if (!(c.tau > 0.5 && c.tau < 1e6) || !(c.rho0 > 0.0 && std::isfinite(c.rho0)))
+    return IILBM_ERR_INVALID_ARG;
+  for (int d = 0; d < 3; d++)
+    if (!std::isfinite(c.body[d])) return IILBM_ERR_INVALID_ARG;
+  if (c.collision == IILBM_MRT)
+    for (int r = 0; r < 19; r++)
+      if (!conserved(r) && !(c.s[r] > 0.0 && c.s[r] < 2.0)) return IILBM_ERR_INVALID_ARG;
+  int ndev = 0, dev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return IILBM_ERR_NO_DEVICE;
+  }
+  CK3(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK3(cudaGetDeviceProperties(&prop, dev));
+  if (prop.major != 10 || prop.minor != 3) return IILBM_ERR_NO_DEVICE;
+  H *h = new (std::nothrow) H();
+  if (!h) return IILBM_ERR_OOM;
+  h->cfg = c;
+  h->device = dev;
+  h->f64 = c.storage == IILBM_F64;
+  Geom3 &g = h->geo;
+  g.nx = c.nx;
+  g.ny = c.ny;
+  g.nz = c.nz;
+  g.ntx = (c.nx + TX - 1) / TX;
+  g.plane = (long long)c.nx * c.ny * c.nz;
+  const size_t sb = h->f64 ? 8 : 4;
+  const size_t ntiles = (size_t)g.ntx * c.ny * c.nz;
+  bool ok = true;
+  if (c.stream) {
+    h->stream = (cudaStream_t)c.stream;
+  } else {
+    ok = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) == cudaSuccess;
+    h->own_stream = ok;
+  }
+  ok = ok && cudaMalloc(&h->A, 19 * g.plane * sb) == cudaSuccess &&
+       cudaMalloc(&h->gf, 3 * g.plane * sb) == cudaSuccess &&
+       cudaMalloc(&h->uf, 3 * g.plane * sb) == cudaSuccess &&
+       cudaMalloc(&h->flags, ntiles * sizeof(unsigned)) == cudaSuccess &&
+       cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
+       cudaMalloc(&h->d_count, sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(h->A, 0, 19 * g.plane * sb, h->stream) == cudaSuccess &&
+       cudaMemsetAsync(h->gf, 0, 3 * g.plane * sb, h->stream) == cudaSuccess &&
+       cudaMemsetAsync(h->uf, 0, 3 * g.plane * sb, h->stream) == cudaSuccess &&
+       cudaMemsetAsync(h->flags, 0, ntiles * sizeof(unsigned), h->stream) == cudaSuccess &&
+       cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream) == cudaSuccess &&
+       cudaMemsetAsync(h->d_count, 0, sizeof(int), h->stream) == cudaSuccess &&
+       cudaStreamSynchronize(h->stream) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    iilbm3d_destroy(h);
+    return IILBM_ERR_OOM;
+  }
+  *out = h;
+  return IILBM_OK;
+}
+
+int iilbm3d_destroy(iilbm3d_t h) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graph(h);
+  free_surface(h);
+  void *p[] = {h->A, h->gf, h->uf, h->flags, h->d_status, h->d_count};
+  for (void *q : p)
+    if (q) cudaFree(q);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  cudaGetLastError();
+  delete h;
+  return IILBM_OK;
+}
+
+int iilbm3d_set_surface(iilbm3d_t h, const double *X, int32_t n, const int32_t *tri, int32_t m,
+                        const iilbm3d_surface_params *p, const double *G) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  if (n > 0 && (!X || !tri || !p || m < 4 || n < 4 || n > (1 << 24) || m > (1 << 25)))
+    return IILBM_ERR_INVALID_ARG;
+  if (n > 0 && (p->model != IILBM3D_PRESCRIBED && p->model != IILBM3D_TENSION))
+    return IILBM_ERR_INVALID_ARG;
+  if (n > 0 && ((p->model == IILBM3D_PRESCRIBED && !G) || (p->moves != 0 && p->moves != 1) ||
+                !std::isfinite(p->gamma)))
+    return IILBM_ERR_INVALID_ARG;
+  CK3(cudaStreamSynchronize(h->stream));
+  drop_graph(h);
+  free_surface(h);
+  // clear what a prepared level left behind
+  const size_t sb = h->f64 ? 8 : 4;
+  const size_t ntiles = (size_t)h->geo.ntx * h->geo.ny * h->geo.nz;
+  CK3(cudaMemsetAsync(h->gf, 0, 3 * h->geo.plane * sb, h->stream));
+  CK3(cudaMemsetAsync(h->flags, 0, ntiles * sizeof(unsigned), h->stream));
+  h->prepared = false;
+  if (n == 0) return IILBM_OK;
+  std::vector<double> hx(3 * (size_t)n), hg;
+  std::vector<int> ht(3 * (size_t)m);
+  CK3(cudaMemcpy(hx.data(), X, hx.size() * sizeof(double), cudaMemcpyDefault));
+  CK3(cudaMemcpy(ht.data(), tri, ht.size() * sizeof(int), cudaMemcpyDefault));
+  if (p->model == IILBM3D_PRESCRIBED) {
+    hg.resize(3 * (size_t)n);
+    CK3(cudaMemcpy(hg.data(), G, hg.size() * sizeof(double), cudaMemcpyDefault));
+  }
+  for (double v : hx)
+    if (!(std::fabs(v) < MAX_COORD)) return IILBM_ERR_INTERFACE;
+  // reference vertex areas (a third of each triangle's), triangles per vertex (ascending)
+  std::vector<double> aref(n, 0.0);
+  std::vector<int> cnt(n + 1, 0);
+  for (int t = 0; t < m; t++) {
+    const int v[3] = {ht[3 * t], ht[3 * t + 1], ht[3 * t + 2]};
+    for (int j = 0; j < 3; j++)
+      if (v[j] < 0 || v[j] >= n) return IILBM_ERR_INVALID_ARG;
+    if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2]) return IILBM_ERR_INTERFACE;
+    const double *A = &hx[3 * v[0]], *B = &hx[3 * v[1]], *C = &hx[3 * v[2]];
+    const double *E[3][2] = {{A, B}, {B, C}, {C, A}};
+    for (int j = 0; j < 3; j++) {
+      double l2 = 0;
+      for (int a = 0; a < 3; a++) l2 += (E[j][1][a] - E[j][0][a]) * (E[j][1][a] - E[j][0][a]);
+      if (!(l2 < MAX_EDGE * MAX_EDGE) || l2 == 0.0) return IILBM_ERR_INTERFACE;
+    }
+    const double u[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+    const double w[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+    const double N[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+    const double a = std::sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]) / 6.0;
+    if (!(a > 0.0)) return IILBM_ERR_INTERFACE;
+    for (int j = 0; j < 3; j++) {
+      aref[v[j]] += a;
+      cnt[v[j] + 1]++;
+    }
+  }
+  for (int k = 0; k < n; k++) {
+    if (cnt[k + 1] == 0) return IILBM_ERR_INTERFACE;  // a vertex on no triangle
+    cnt[k + 1] += cnt[k];
+  }
+  std::vector<int> fill(cnt.begin(), cnt.end() - 1), list(3 * (size_t)m);
+  for (int t = 0; t < m; t++)
+    for (int j = 0; j < 3; j++) list[fill[ht[3 * t + j]]++] = t;
+  const size_t b3 = 3 * (size_t)n * sizeof(double);
+  bool ok = cudaMalloc(&h->X, b3) == cudaSuccess && cudaMalloc(&h->Gp, b3) == cudaSuccess &&
+            cudaMalloc(&h->G, b3) == cudaSuccess && cudaMalloc(&h->U, b3) == cudaSuccess &&
+            cudaMalloc(&h->Fn, n * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&h->Aref, n * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&h->tri, 3 * (size_t)m * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->vt_start, (n + 1) * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->vt_list, 3 * (size_t)m * sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_surface(h);
+    return IILBM_ERR_OOM;
+  }
+  h->n = n;
+  h->m = m;
+  h->sp = *p;
+  ok = cudaMemcpy(h->X, hx.data(), b3, cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemset(h->Gp, 0, b3) == cudaSuccess && cudaMemset(h->G, 0, b3) == cudaSuccess &&
+       cudaMemset(h->U, 0, b3) == cudaSuccess &&
+       cudaMemset(h->Fn, 0, n * sizeof(double)) == cudaSuccess &&
+       cudaMemcpy(h->Aref, aref.data(), n * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(h->tri, ht.data(), ht.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(h->vt_start, cnt.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(h->vt_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice) ==
+           cudaSuccess;
+  if (ok && !hg.empty()) ok = cudaMemcpy(h->Gp, hg.data(), b3, cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_surface(h);
+    return IILBM_ERR_CUDA;
+  }
+  return IILBM_OK;
+}
+
+int iilbm3d_init_equilibrium(iilbm3d_t h, const double *drho, const double *ux, const double *uy,
+                             const double *uz) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  const long long N = h->geo.plane;
+  double *d[4] = {nullptr, nullptr, nullptr, nullptr};
+  const double *src[4] = {drho, ux, uy, uz};
+  int rc = IILBM_OK;
+  for (int q = 0; q < 4 && !rc; q++) rc = to_device(src[q], (size_t)N, h->stream, &d[q]);
+  if (!rc) {
+    const unsigned b = blocks_for(N, 256);
+    if (h->f64)
+      k3_equilibrium<double><<<b, 256, 0, h->stream>>>((double *)h->A, h->geo, (int)(h->step & 1),
+                                                       h->cfg.rho0, d[0], d[1], d[2], d[3]);
+    else
+      k3_equilibrium<float><<<b, 256, 0, h->stream>>>((float *)h->A, h->geo, (int)(h->step & 1),
+                                                      h->cfg.rho0, d[0], d[1], d[2], d[3]);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) rc = IILBM_ERR_CUDA;
+  }
+  for (double *q : d)
+    if (q) cudaFree(q);
+  h->prepared = false;  // the level's state changed: its surface pass runs again
+  return rc;
+}
+
+int iilbm3d_set_populations(iilbm3d_t h, const double *df) {
+  if (!h || !df) return IILBM_ERR_INVALID_ARG;
+  double *d = nullptr;
+  int rc = to_device(df, 19 * (size_t)h->geo.plane, h->stream, &d);
+  if (rc) return rc;
+  const unsigned b = blocks_for(h->geo.plane, 256);
+  if (h->f64) k3_store<double><<<b, 256, 0, h->stream>>>((double *)h->A, d, h->geo, (int)(h->step & 1));
+  else k3_store<float><<<b, 256, 0, h->stream>>>((float *)h->A, d, h->geo, (int)(h->step & 1));
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) rc = IILBM_ERR_CUDA;
+  cudaFree(d);
+  return rc;
+}
+
+int iilbm3d_get_populations(iilbm3d_t h, double *df) {
+  if (!h || !df) return IILBM_ERR_INVALID_ARG;
+  double *d = nullptr;
+  const size_t cnt = 19 * (size_t)h->geo.plane;
+  if (cudaMalloc(&d, cnt * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return IILBM_ERR_OOM;
+  }
+  const unsigned b = blocks_for(h->geo.plane, 256);
+  if (h->f64) k3_load<double><<<b, 256, 0, h->stream>>>((const double *)h->A, d, h->geo, (int)(h->step & 1));
+  else k3_load<float><<<b, 256, 0, h->stream>>>((const float *)h->A, d, h->geo, (int)(h->step & 1));
+  int rc = IILBM_OK;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(df, d, cnt * sizeof(double), cudaMemcpyDefault, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    rc = IILBM_ERR_CUDA;
+  }
+  cudaFree(d);
+  return rc ? rc : read_status3(h);
+}
+
+int iilbm3d_step(iilbm3d_t h, int32_t n) {
+  if (!h || n < 0) return IILBM_ERR_INVALID_ARG;
+  while (n > 0) {
+    const bool graph_ok = !h->timing && !h->prepared && (h->step & 1) == 0 && n >= 2;
+    if (graph_ok) {
+      if (!h->gexec) RC3(capture_pair(h));
+      CK3(cudaGraphLaunch(h->gexec, h->stream));
+      h->step += 2;
+      n -= 2;
+    } else {
+      RC3(one_step(h));
+      n -= 1;
+    }
+  }
+  return IILBM_OK;
+}
+
+// The vertex pass of the current level, once (its g and flags then await the step).
+static int prepare_level(H *h) {
+  if (h->n > 0 && !h->prepared) {
+    launch_vertex(h);
+    CK3(cudaGetLastError());
+    h->prepared = true;
+  }
+  return IILBM_OK;
+}
+
+// The jump field of the current level into the device buffer J (zeroed here).
+static int jump_field(H *h, double *J) {
+  CK3(cudaMemsetAsync(J, 0, 18 * (size_t)h->geo.plane * sizeof(double), h->stream));
+  if (h->n > 0 && h->cfg.jump) {
+    RC3(prepare_level(h));
+    CK3(cudaMemsetAsync(h->d_count, 0, sizeof(int), h->stream));
+    launch_cut(h, J);
+    CK3(cudaGetLastError());
+  }
+  return IILBM_OK;
+}
+
+int iilbm3d_get_macros(iilbm3d_t h, double *drho, double *ux, double *uy, double *uz) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  const size_t N = (size_t)h->geo.plane;
+  double *J = nullptr, *out = nullptr;
+  const bool want_j = h->n > 0 && h->cfg.jump;
+  if ((want_j && cudaMalloc(&J, 18 * N * sizeof(double)) != cudaSuccess) ||
+      cudaMalloc(&out, 4 * N * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    if (J) cudaFree(J);
+    return IILBM_ERR_OOM;
+  }
+  int rc = want_j ? jump_field(h, J) : prepare_level(h);
+  if (!rc) {
+    const double hh = h->cfg.force == IILBM_FORCE_SIMPLE ? 0.0 : 0.5;
+    const unsigned b = blocks_for((long long)N, 256);
+    if (h->f64)
+      k3_macros<double><<<b, 256, 0, h->stream>>>((const double *)h->A, J, (const double *)h->gf,
+                                                  h->geo, (int)(h->step & 1), h->cfg.rho0,
+                                                  h->cfg.body[0], h->cfg.body[1], h->cfg.body[2], hh, out);
+    else
+      k3_macros<float><<<b, 256, 0, h->stream>>>((const float *)h->A, J, (const float *)h->gf,
+                                                 h->geo, (int)(h->step & 1), h->cfg.rho0,
+                                                 h->cfg.body[0], h->cfg.body[1], h->cfg.body[2], hh, out);
+    double *dst[4] = {drho, ux, uy, uz};
+    if (cudaGetLastError() != cudaSuccess) rc = IILBM_ERR_CUDA;
+    for (int q = 0; q < 4 && !rc; q++)
+      if (dst[q] &&
+          cudaMemcpyAsync(dst[q], out + q * N, N * sizeof(double), cudaMemcpyDefault, h->stream) != cudaSuccess)
+        rc = IILBM_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = IILBM_ERR_CUDA;
+  }
+  cudaGetLastError();
+  if (J) cudaFree(J);
+  cudaFree(out);
+  return rc ? rc : read_status3(h);
+}
+
+int iilbm3d_get_markers(iilbm3d_t h, double *X, double *G, double *U, double *Fn) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  const size_t b3 = 3 * (size_t)h->n * sizeof(double);
+  if (h->n > 0) {
+    if (X) CK3(cudaMemcpyAsync(X, h->X, b3, cudaMemcpyDefault, h->stream));
+    if (G) CK3(cudaMemcpyAsync(G, h->G, b3, cudaMemcpyDefault, h->stream));
+    if (U) CK3(cudaMemcpyAsync(U, h->U, b3, cudaMemcpyDefault, h->stream));
+    if (Fn) CK3(cudaMemcpyAsync(Fn, h->Fn, h->n * sizeof(double), cudaMemcpyDefault, h->stream));
+  }
+  return read_status3(h);
+}
+
+int iilbm3d_get_jump(iilbm3d_t h, double *J) {
+  if (!h || !J) return IILBM_ERR_INVALID_ARG;
+  const size_t cnt = 18 * (size_t)h->geo.plane;
+  double *d = nullptr;
+  if (cudaMalloc(&d, cnt * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return IILBM_ERR_OOM;
+  }
+  int rc = jump_field(h, d);
+  if (!rc && (cudaMemcpyAsync(J, d, cnt * sizeof(double), cudaMemcpyDefault, h->stream) != cudaSuccess ||
+              cudaStreamSynchronize(h->stream) != cudaSuccess))
+    rc = IILBM_ERR_CUDA;
+  cudaGetLastError();
+  cudaFree(d);
+  return rc ? rc : read_status3(h);
+}
+
+int iilbm3d_get_cut_link_count(iilbm3d_t h, int32_t *count) {
+  if (!h || !count) return IILBM_ERR_INVALID_ARG;
+  int c = 0;
+  CK3(cudaMemcpyAsync(&c, h->d_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK3(cudaStreamSynchronize(h->stream));
+  *count = c;
+  return IILBM_OK;
+}
+
+int iilbm3d_set_timing(iilbm3d_t h, int32_t enable) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  CK3(cudaStreamSynchronize(h->stream));
+  h->timing = enable != 0;
+  h->nev = 0;
+  h->sc_ms = 0.0;
+  h->sc_launches = 0;
+  h->kernels = 0;
+  return IILBM_OK;
+}
+
+int iilbm3d_get_timing(iilbm3d_t h, double *stream_collide_ms, int32_t *launches, int64_t *kernels) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  CK3(cudaStreamSynchronize(h->stream));
+  for (int e = 0; e < h->nev; e++) {
+    float ms = 0.f;
+    CK3(cudaEventElapsedTime(&ms, h->ev[2 * e], h->ev[2 * e + 1]));
+    h->sc_ms += ms;
+  }
+  h->sc_launches += h->nev;
+  h->nev = 0;
+  if (stream_collide_ms) *stream_collide_ms = h->sc_ms;
+  if (launches) *launches = h->sc_launches;
+  if (kernels) *kernels = h->kernels;
+  return IILBM_OK;
+}
+
+int iilbm3d_synchronize(iilbm3d_t h) {
+  if (!h) return IILBM_ERR_INVALID_ARG;
+  return read_status3(h);
+}
+
+}  // extern "C"

@@ -32,6 +32,14 @@ method generates (other channels, another seed) proposes the iteration's start; 
 reports its end-to-end MLUPS and force passes per step next to the plain iteration
 (start zero) and the previous-step start, on the same channels.
 
+--workload membrane3d: the three-dimensional method on the D3Q19 lattice -- a 256^3
+periodic MRT box (tau 0.6, d'Humieres rates of section 2.2.1) holding a surface-tension
+ellipsoid (semi-axes 0.31, 0.25, 0.22 of the box, a seeded rotation, 40 962 vertices, edges
+about one lattice unit) whose vertices move with the fluid; FP32 populations (--storage f64
+runs FP64).  One step: vertex forces and normal split, the jump on every cut link of the
+triangulation, tangential spreading, the stream-collide, interpolation and the vertex
+update.  --size3 sets the box's side.
+
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
 """
 from __future__ import annotations
@@ -69,14 +77,15 @@ def parse():
     ap.add_argument("--no-hbm-check", action="store_true",
                     help="skip the 4096^2 out-of-L2 lean stream-collide measurement")
     ap.add_argument("--workload", default="ellipse",
-                    choices=["ellipse", "batched", "learned", "channel"])
+                    choices=["ellipse", "batched", "learned", "channel", "membrane3d"])
+    ap.add_argument("--size3", type=int, default=256, help="membrane3d: nodes per axis")
     ap.add_argument("--re", type=float, default=20.0, help="Reynolds number (channel)")
     ap.add_argument("--history", type=int, default=0,
                     help="channel: steps of drag / lift history after the timed region")
     ap.add_argument("--count", type=int, default=256, help="simulations of the batched sweep")
     a = ap.parse_args()
     if a.steps is None:
-        a.steps = 20000 if a.workload == "ellipse" else 2000
+        a.steps = {"ellipse": 20000, "membrane3d": 200}.get(a.workload, 2000)
     return a
 
 
@@ -921,10 +930,206 @@ def run_channel(args):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------- three dimensions
+def membrane3d_config(args, w):
+    sb = 8 if args.storage == "f64" else 4
+    n = w["n"]
+    return {"workload": f"membrane3d_{n}^3_tension_ellipsoid", "lattice": [n, n, n],
+            "vertices": len(w["X"]), "triangles": len(w["T"]), "collision": "mrt (d'Humieres D3Q19)",
+            "tau": w["tau"], "gamma": w["gamma"], "storage": args.storage,
+            "arithmetic": "f64" if args.storage == "f64" else "f32",
+            "l2": f"inputs larger than L2 ({19 * sb * n ** 3 / 2**20:.0f} MiB populations vs "
+                  f"129 MiB L2)"}
+
+
+def oracle3d_rate(w, max_seconds, parallel):
+    from oracle import oracle3d as O3
+    n = w["n"]
+    o = O3.Oracle3D(n, n, n, parallel=parallel, collision=O3.MRT, tau=w["tau"])
+    o.set_surface(w["X"], w["T"], model=O3.TENSION, moves=True, gamma=w["gamma"])
+    steps, t0 = 0, time.perf_counter()
+    while steps < 1 or time.perf_counter() - t0 < max_seconds:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt / 1e6, steps, dt
+
+
+def run_membrane3d(args):
+    """The D3Q19 II-LBM membrane: a surface-tension ellipsoid in a periodic n^3 box."""
+    import torch
+    from paper_2003_12186_gb300 import iilbm3d
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ts = torch.cuda.Stream()
+    torch.cuda.set_stream(ts)
+    w = W.membrane_3d(args.size3)
+    n = w["n"]
+    cells = n ** 3
+    sb = 8 if args.storage == "f64" else 4
+    if args.storage not in ("f32", "f64"):
+        raise SystemExit("membrane3d stores FP32 or FP64 populations")
+
+    def lattice():
+        g = iilbm3d.Lattice3D(n, n, n, collision=iilbm3d.MRT, storage=args.storage, tau=w["tau"],
+                              stream=ts.cuda_stream)
+        return g
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    g = lattice()
+    g.set_surface(w["X"], w["T"], model=iilbm3d.TENSION, moves=True, gamma=w["gamma"])
+    g.step(args.warmup)  # captures the two-step graph
+    g.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    clocks.begin()
+    e0.record(ts)
+    g.step(args.steps)
+    e1.record(ts)
+    barrier()
+    clocks.end()
+    ms = e0.elapsed_time(e1)
+    # second region: eager steps with CUDA events around every stream-collide launch
+    K2 = min(args.steps, 100)
+    g.set_timing(True)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    f0.record(ts)
+    g.step(K2)
+    f1.record(ts)
+    barrier()
+    ms2 = f0.elapsed_time(f1)
+    sc_ms, sc_n, kernels = g.get_timing()
+    g.set_timing(False)
+    clk = clocks.stop()
+    cut = g.get_cut_link_count()
+    ms, = max_over_ranks([ms], dist)
+    value = whole_job_mlups(cells, args.steps, world, ms * 1e-3)
+    peak, peak_kind = peaks()
+    alg = 2 * 19 * sb * cells
+    sc_avg = sc_ms / max(sc_n, 1) * 1e-3
+    achieved = alg / sc_avg / 1e9
+    step_ach = alg / (ms / args.steps * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "k3_stream_collide (every node, flagged tiles with the spread force)",
+                "peak_source": peak_kind, "alg_bytes_per_launch": alg,
+                "avg_launch_us": round(sc_avg * 1e6, 2),
+                "timed_in": f"second region of {K2} eager steps with CUDA events around each "
+                            f"stream-collide ({ms2 / K2 * 1e3:.1f} us/step there)",
+                "step_achieved": round(step_ach, 1), "step_frac": round(step_ach / peak, 4),
+                "frac_nominal_8tbs": round(achieved / NOMINAL_HBM_GBS, 4)}
+    tr = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr):
+        d = json.load(open(tr)).get(f"membrane3d_{n}_{args.storage}")
+        if d:
+            roofline["traffic"] = d
+    del g
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        g2 = lattice()
+        Xin = torch.from_numpy(np.ascontiguousarray(w["X"])).pin_memory()
+        Xout = torch.empty((len(w["X"]), 3), dtype=torch.float64).pin_memory()
+        u = [torch.empty((n, n, n), dtype=torch.float64).pin_memory() for _ in range(3)]
+        K3 = min(args.steps, 100)
+        g2.set_surface(Xin.numpy(), w["T"], model=iilbm3d.TENSION, moves=True, gamma=w["gamma"])
+        g2.step(2)
+        g2.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        g2.set_surface(Xin.numpy(), w["T"], model=iilbm3d.TENSION, moves=True, gamma=w["gamma"])
+        for _ in range(K3):
+            g2.step(1)
+            g2.get_markers_into(X=Xout)
+        _, ux, uy, uz = g2.get_macros()
+        for a, b in zip(u, (ux, uy, uz)):
+            a.copy_(torch.from_numpy(b))
+        barrier()
+        dt = time.perf_counter() - t0
+        dt, = max_over_ranks([dt], dist)
+        h2d = Xin.numel() * 8 + w["T"].size * 4
+        d2h = K3 * Xout.numel() * 8 + 3 * cells * 8
+        e2e = {"value": round(whole_job_mlups(cells, K3, world, dt), 1), "unit": "MLUPS",
+               "h2d_bytes_per_step": round(h2d / K3, 1), "d2h_bytes_per_step": round(d2h / K3, 1),
+               "note": "inside the region: the surface installed from host memory, per step "
+                       "iilbm3d_step(1) + vertex read-back to pinned host, final velocity "
+                       "field read-back"}
+        del g2
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import oracle3d as O3
+        try:
+            rp, stp, dtp = oracle3d_rate(w, 8.0, True)
+            cpu = {"value": round(rp, 4), "unit": "MLUPS", "cores": O3.omp_threads(),
+                   "kind": "oracle", "sample": f"{stp} FP64 oracle steps of the same "
+                   f"{n}^3 workload, {dtp:.1f} s, OpenMP build"}
+        except RuntimeError:
+            r1, st1, dt1 = oracle3d_rate(w, 10.0, False)
+            cpu = {"value": round(r1, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                   "sample": f"{st1} FP64 oracle steps of the same {n}^3 workload, "
+                   f"{dt1:.1f} s, one thread"}
+    if rank == 0:
+        out = {"metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+               "data": "synthetic", "config": membrane3d_config(args, w),
+               "cut_links_per_step": cut, "roofline": roofline, "cpu_baseline": cpu,
+               "e2e": e2e, "clocks": clk,
+               "gpu_launches": int(kernels / max(sc_n, 1) * args.steps)}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference3d(args):
+    """Reference arm of the 3-D workload: the 3-D oracle (OpenMP build), rank 0 only, a
+    bounded number of steps of the same configuration."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    from oracle import oracle3d as O3
+    try:
+        O3.lib(parallel=True)
+        par = True
+    except RuntimeError:
+        par = False
+    w = W.membrane_3d(args.size3)
+    rate, steps, dt = oracle3d_rate(w, 20.0, par)
+    cores = O3.omp_threads() if par else 1
+    sample = (f"{steps} FP64 oracle steps of the {w['n']}^3 membrane, "
+              + (f"OpenMP build on {cores} threads" if par else "one thread"))
+    out = {"metric": "MLUPS", "value": round(rate, 4), "unit": "MLUPS", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference", "config": membrane3d_config(args, w),
+           "cpu_baseline": {"value": round(rate, 4), "unit": "MLUPS", "cores": cores,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(rate, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.impl == "reference" and args.workload == "membrane3d":
+        run_reference3d(args)
+    elif args.impl == "reference":
         run_reference(args)
+    elif args.workload == "membrane3d":
+        run_membrane3d(args)
     elif args.workload == "batched":
         run_batched(args)
     elif args.workload == "learned":

@@ -12,10 +12,11 @@
 //   k3_cut           one warp per triangle: every link x - e_i -> x that crosses it (exact
 //                    integer predicate with symbolic tie-breaks) adds s w_i/c_s^2 Fn to the
 //                    streamed population f_i(x) in place (Eq. 47);
-//   k3_stream_collide one thread per node, blocks of 128 nodes along x (a tile): AA-pattern
-//                    in-place streaming, SRT or MRT collision; flagged tiles also read and
-//                    clear g (Guo's term or the simple force term) and record the
-//                    collision's velocity for the interpolation;
+//   k3_sc_lean       one thread per node, blocks of 32 x 4 nodes (a tile): AA-pattern
+//                    in-place streaming, SRT or MRT collision, on every tile not flagged;
+//   k3_sc_forced     the flagged tiles, from the list the vertex pass built: the same with
+//                    g (Guo's term or the simple force term), which it clears, and the
+//                    collision's velocity recorded for the interpolation;
 //   k3_interp        one thread per vertex: U = interp(u) (Eq. 20), X += U for a moving
 //                    surface.
 // Between steps the stored populations carry no jump: the jump of the next step's
@@ -27,6 +28,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/iilbm3d.h"
@@ -87,17 +89,67 @@ __host__ __device__ constexpr int mnorm(int r) {
   return s;
 }
 __host__ __device__ constexpr bool conserved(int r) { return r == 0 || r == 3 || r == 5 || r == 7; }
+// Parity of a basis row under e -> -e: even rows take equal values on opposite directions,
+// odd rows opposite values (every row of the basis is one or the other).
+__host__ __device__ constexpr bool row_even(int r) {
+  for (int i = 1; i < 19; i++)
+    if (mrow(r, opp(i)) != mrow(r, i)) return false;
+  return true;
+}
+__host__ __device__ constexpr bool row_odd(int r) {
+  for (int i = 0; i < 19; i++)
+    if (mrow(r, opp(i)) != -mrow(r, i)) return false;
+  return true;
+}
+__host__ __device__ constexpr bool rows_have_parity() {
+  for (int r = 0; r < 19; r++)
+    if (row_even(r) == row_odd(r)) return false;
+  return true;
+}
+static_assert(rows_have_parity(), "every basis row is even or odd");
 static_assert(mnorm(0) == 19 && mnorm(1) == 2394 && mnorm(2) == 252 && mnorm(3) == 10, "norms");
 
-constexpr int TX = 128;              // tile: 128 nodes along x (one block of the stream-collide)
+// Compile-time loop: f(std::integral_constant<int, k>) for k = B .. E-1, so every basis
+// entry, weight and velocity component inside is a constant expression (a constexpr
+// function called with a loop counter is not guaranteed to be folded).
+template <int B, int E, typename F>
+__host__ __device__ __forceinline__ void static_for(F &&f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// The velocity components as 2-bit fields (e + 1) of one word per axis, for directions
+// that are only known at run time.
+__host__ __device__ constexpr unsigned long long pack_e(int axis) {
+  unsigned long long v = 0;
+  for (int i = 0; i < 19; i++) {
+    const int e = axis == 0 ? ex(i) : (axis == 1 ? ey(i) : ez(i));
+    v |= (unsigned long long)(e + 1) << (2 * i);
+  }
+  return v;
+}
+constexpr unsigned long long EXP = pack_e(0), EYP = pack_e(1), EZP = pack_e(2);
+__host__ __device__ inline int exr(int i) { return (int)((EXP >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ inline int eyr(int i) { return (int)((EYP >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ inline int ezr(int i) { return (int)((EZP >> (2 * i)) & 3ull) - 1; }
+
+// A tile is TX x TY nodes of one z-plane: one 128-thread block of the stream-collide, one
+// warp per row of 32 consecutive x (each warp access a full 128-byte line in FP32).
+constexpr int TX = 32, TY = 4, TB = TX * TY;
 constexpr double QS = 1048576.0;     // crossing predicate: coordinates snapped to 2^-20
 constexpr int QBITS = 20;
 constexpr double MAX_EDGE = 8.0;
+// The candidate destinations of a triangle span ceil(max) - ceil(min) + 2 <= 10 nodes per
+// axis (edges below 8 per axis); widened by one node on each side: at most 12.
+constexpr int CUT_BOX = 12;
 constexpr double MAX_COORD = 4096.0;
 constexpr int ST_NONFINITE = 1, ST_INTERFACE = 2;
+constexpr long long XQ_OUT = 1LL << 62;  // snapped coordinate of a vertex out of range
 
 struct Geom3 {
-  int nx, ny, nz, ntx;
+  int nx, ny, nz, ntx, nty;  // nodes; tiles along x and y
   long long plane;  // nodes
 };
 
@@ -110,8 +162,70 @@ __host__ __device__ inline long long nodeix(const Geom3 &g, int x, int y, int z)
 __device__ __forceinline__ long long aa_read(const Geom3 &g, bool odd, int i, int x, int y, int z) {
   if (!odd) return i * g.plane + nodeix(g, x, y, z);
   return opp(i) * g.plane +
-         nodeix(g, wrapn(x - ex(i), g.nx), wrapn(y - ey(i), g.ny), wrapn(z - ez(i), g.nz));
+         nodeix(g, wrapn(x - exr(i), g.nx), wrapn(y - eyr(i), g.ny), wrapn(z - ezr(i), g.nz));
 }
+// The same for a compile-time direction I (the stream-collide's unrolled loops).
+template <int I>
+__device__ __forceinline__ long long aa_read_c(const Geom3 &g, bool odd, int x, int y, int z) {
+  constexpr int X = ex(I), Y = ey(I), Z = ez(I), O = opp(I);
+  if (!odd) return I * g.plane + nodeix(g, x, y, z);
+  return O * g.plane + nodeix(g, X ? wrapn(x - X, g.nx) : x, Y ? wrapn(y - Y, g.ny) : y,
+                              Z ? wrapn(z - Z, g.nz) : z);
+}
+
+// The spread force g and the collision velocity u of the flagged nodes: FP32 as one float4
+// per node (x, y, z, unused: one vector atomic per spread contribution, one 16-byte access
+// per node), FP64 as three planes of the node count.
+template <typename T>
+struct Vec3;
+template <>
+struct Vec3<float> {
+  __device__ static void add(float *b, long long, long long c, float x, float y, float z) {
+    atomicAdd(reinterpret_cast<float4 *>(b) + c, make_float4(x, y, z, 0.f));
+  }
+  __device__ static void take(float *b, long long, long long c, float &x, float &y, float &z) {
+    float4 *q = reinterpret_cast<float4 *>(b) + c;
+    const float4 v = *q;
+    *q = make_float4(0.f, 0.f, 0.f, 0.f);
+    x = v.x;
+    y = v.y;
+    z = v.z;
+  }
+  __device__ static void put(float *b, long long, long long c, float x, float y, float z) {
+    reinterpret_cast<float4 *>(b)[c] = make_float4(x, y, z, 0.f);
+  }
+  __device__ static void get(const float *b, long long, long long c, float &x, float &y, float &z) {
+    const float4 v = reinterpret_cast<const float4 *>(b)[c];
+    x = v.x;
+    y = v.y;
+    z = v.z;
+  }
+};
+template <>
+struct Vec3<double> {
+  __device__ static void add(double *b, long long pl, long long c, double x, double y, double z) {
+    atomicAdd(b + c, x);
+    atomicAdd(b + pl + c, y);
+    atomicAdd(b + 2 * pl + c, z);
+  }
+  __device__ static void take(double *b, long long pl, long long c, double &x, double &y, double &z) {
+    x = b[c];
+    y = b[pl + c];
+    z = b[2 * pl + c];
+    b[c] = b[pl + c] = b[2 * pl + c] = 0.0;
+  }
+  __device__ static void put(double *b, long long pl, long long c, double x, double y, double z) {
+    b[c] = x;
+    b[pl + c] = y;
+    b[2 * pl + c] = z;
+  }
+  __device__ static void get(const double *b, long long pl, long long c, double &x, double &y,
+                             double &z) {
+    x = b[c];
+    y = b[pl + c];
+    z = b[2 * pl + c];
+  }
+};
 
 template <typename T>
 struct Coll3 {
@@ -130,75 +244,138 @@ struct Coll3 {
 //        the transforms unrolled over the constant integer basis;
 //   simple force term: no Gt, then 3 w_i e_i.g added (Eq. 16).
 // FORCED = false: g = 0 and the force terms are left out.
+// Opposite directions pair as (2k - 1, 2k), k = 1..9.  The collision works on the pair sums
+// and differences of f - f_eq (and of Guo's source): even basis rows see only the sums,
+// odd rows only the differences, so the transform to moments and back takes about half
+// the operations of the plain 19 x 19 products.
 template <typename T, bool MRT, bool FORCED, bool SIMPLE>
 __device__ __forceinline__ T collide3(T f[19], T gx, T gy, T gz, const Coll3<T> &p, T &ux,
                                       T &uy, T &uz) {
-  T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
-#pragma unroll
-  for (int i = 0; i < 19; i++) {
-    drho += f[i];
-    if (ex(i)) jx += ex(i) > 0 ? f[i] : -f[i];
-    if (ey(i)) jy += ey(i) > 0 ? f[i] : -f[i];
-    if (ez(i)) jz += ez(i) > 0 ? f[i] : -f[i];
-  }
+  T ps[10], pd[10];
+  T drho = f[0], jx = T(0), jy = T(0), jz = T(0);
+  static_for<1, 10>([&](auto kc) {
+    constexpr int k = decltype(kc)::value, i = 2 * k - 1;
+    ps[k] = f[i] + f[i + 1];
+    pd[k] = f[i] - f[i + 1];
+    drho += ps[k];
+    if constexpr (ex(i) > 0) jx += pd[k];
+    if constexpr (ex(i) < 0) jx -= pd[k];
+    if constexpr (ey(i) > 0) jy += pd[k];
+    if constexpr (ey(i) < 0) jy -= pd[k];
+    if constexpr (ez(i) > 0) jz += pd[k];
+    if constexpr (ez(i) < 0) jz -= pd[k];
+  });
   const T rho = p.rho0 + drho, inv = T(1) / rho;
-  const T h = FORCED && !SIMPLE ? T(0.5) : T(0);
-  ux = (jx + h * gx) * inv;
-  uy = (jy + h * gy) * inv;
-  uz = (jz + h * gz) * inv;
+  constexpr bool GUO = FORCED && !SIMPLE;
+  ux = (GUO ? jx + T(0.5) * gx : jx) * inv;
+  uy = (GUO ? jy + T(0.5) * gy : jy) * inv;
+  uz = (GUO ? jz + T(0.5) * gz : jz) * inv;
   const T u2 = ux * ux + uy * uy + uz * uz;
-  T d[19];
-#pragma unroll
-  for (int i = 0; i < 19; i++) {
+  // f_eq_i = w_i (base + rho (3 e.u + 4.5 (e.u)^2)), base = drho - 1.5 rho u^2
+  const T base = drho - T(1.5) * rho * u2;
+  T ds[10], da[10];  // pair sums / differences of f - f_eq; ds[0] = the rest population's
+  ds[0] = f[0] - wt<T>(0) * base;
+  da[0] = T(0);
+  static_for<1, 10>([&](auto kc) {
+    constexpr int k = decltype(kc)::value, i = 2 * k - 1;
+    constexpr T w = wt<T>(i);
     const T eu = T(ex(i)) * ux + T(ey(i)) * uy + T(ez(i)) * uz;
-    d[i] = f[i] - wt<T>(i) * (drho + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * u2));
-  }
-  T Gt[19];
-  if (FORCED && !SIMPLE) {
-#pragma unroll
-    for (int i = 0; i < 19; i++) {
+    ds[k] = ps[k] - T(2) * w * (base + T(4.5) * rho * eu * eu);
+    da[k] = pd[k] - T(6) * w * rho * eu;
+  });
+  T gs[10], ga[10];  // the same for Guo's source Gt_i = w_i (3 (e_i - u).g + 9 (e_i.u)(e_i.g))
+  if constexpr (GUO) {
+    const T ug = ux * gx + uy * gy + uz * gz;
+    gs[0] = wt<T>(0) * T(-3) * ug;
+    ga[0] = T(0);
+    static_for<1, 10>([&](auto kc) {
+      constexpr int k = decltype(kc)::value, i = 2 * k - 1;
+      constexpr T w = wt<T>(i);
       const T eu = T(ex(i)) * ux + T(ey(i)) * uy + T(ez(i)) * uz;
       const T eg = T(ex(i)) * gx + T(ey(i)) * gy + T(ez(i)) * gz;
-      const T ug = ux * gx + uy * gy + uz * gz;
-      Gt[i] = wt<T>(i) * (T(3) * (eg - ug) + T(9) * eu * eg);
-    }
+      gs[k] = w * (T(18) * eu * eg - T(6) * ug);
+      ga[k] = T(6) * w * eg;
+    });
   }
-  if (!MRT) {
-#pragma unroll
-    for (int i = 0; i < 19; i++) {
-      f[i] -= p.omega * d[i];
-      if (FORCED && !SIMPLE) f[i] += (T(1) - T(0.5) * p.omega) * Gt[i];
-    }
+  if constexpr (!MRT) {
+    const T om = p.omega, fo = T(1) - T(0.5) * p.omega;
+    f[0] -= om * ds[0];
+    if constexpr (GUO) f[0] += fo * gs[0];
+    static_for<1, 10>([&](auto kc) {
+      constexpr int k = decltype(kc)::value, i = 2 * k - 1;
+      T e = om * ds[k], o = om * da[k];
+      if constexpr (GUO) {
+        e -= fo * gs[k];
+        o -= fo * ga[k];
+      }
+      f[i] -= T(0.5) * (e + o);
+      f[i + 1] -= T(0.5) * (e - o);
+    });
   } else {
-#pragma unroll
-    for (int r = 0; r < 19; r++) {
+    T E[10], O[10];  // back-transform accumulators of the even and odd rows per pair
+    static_for<0, 10>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      E[k] = T(0);
+      O[k] = T(0);
+    });
+    static_for<0, 19>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      constexpr bool EVEN = row_even(r);
+      constexpr T inv_norm = T(1) / T(mnorm(r));
       T c = T(0);
-      if (!conserved(r)) {
+      if constexpr (!conserved(r)) {
         T a = T(0);
-#pragma unroll
-        for (int i = 0; i < 19; i++)
-          if (mrow(r, i)) a += T(mrow(r, i)) * d[i];
+        static_for<0, 10>([&](auto kc) {
+          constexpr int k = decltype(kc)::value, i = k == 0 ? 0 : 2 * k - 1;
+          constexpr int m = mrow(r, i);
+          const T v = EVEN ? ds[k] : da[k];
+          if constexpr (m == 1) a += v;
+          else if constexpr (m == -1) a -= v;
+          else if constexpr (m != 0) a += T(m) * v;
+        });
         c = p.s[r] * a;
       }
-      if (FORCED && !SIMPLE) {
+      if constexpr (GUO) {
         T b = T(0);
-#pragma unroll
-        for (int i = 0; i < 19; i++)
-          if (mrow(r, i)) b += T(mrow(r, i)) * Gt[i];
+        static_for<0, 10>([&](auto kc) {
+          constexpr int k = decltype(kc)::value, i = k == 0 ? 0 : 2 * k - 1;
+          constexpr int m = mrow(r, i);
+          const T v = EVEN ? gs[k] : ga[k];
+          if constexpr (m == 1) b += v;
+          else if constexpr (m == -1) b -= v;
+          else if constexpr (m != 0) b += T(m) * v;
+        });
         c -= (conserved(r) ? T(1) : T(1) - T(0.5) * p.s[r]) * b;
       }
-      c *= T(1) / T(mnorm(r));
-#pragma unroll
-      for (int i = 0; i < 19; i++)
-        if (mrow(r, i)) f[i] -= T(mrow(r, i)) * c;
-    }
+      if constexpr (!conserved(r) || GUO) {
+        c *= inv_norm;
+        static_for<0, 10>([&](auto kc) {
+          constexpr int k = decltype(kc)::value, i = k == 0 ? 0 : 2 * k - 1;
+          constexpr int m = mrow(r, i);
+          T &acc = EVEN ? E[k] : O[k];
+          if constexpr (m == 1) acc += c;
+          else if constexpr (m == -1) acc -= c;
+          else if constexpr (m != 0) acc += T(m) * c;
+        });
+      }
+    });
+    // pair sums and differences: a pair's sum carries the even rows twice over,
+    // (E + O) to its first direction and (E - O) to its second
+    f[0] -= E[0];
+    static_for<1, 10>([&](auto kc) {
+      constexpr int k = decltype(kc)::value, i = 2 * k - 1;
+      f[i] -= E[k] + O[k];
+      f[i + 1] -= E[k] - O[k];
+    });
   }
-  if (FORCED && SIMPLE) {
-#pragma unroll
-    for (int i = 0; i < 19; i++) {
-      const T eg = T(ex(i)) * gx + T(ey(i)) * gy + T(ez(i)) * gz;
-      f[i] += T(3) * wt<T>(i) * eg;
-    }
+  if constexpr (FORCED && SIMPLE) {
+    static_for<1, 10>([&](auto kc) {
+      constexpr int k = decltype(kc)::value, i = 2 * k - 1;
+      constexpr T w3 = T(3) * wt<T>(i);
+      const T t = w3 * (T(ex(i)) * gx + T(ey(i)) * gy + T(ez(i)) * gz);
+      f[i] += t;
+      f[i + 1] -= t;
+    });
   }
   return drho;
 }
@@ -214,9 +391,11 @@ struct iilbm3d_lattice {
   bool own_stream;
   bool f64;           // storage (and arithmetic) FP64, else FP32
   void *A;            // [19][plane] populations
-  void *gf;           // [3][plane] spread force (arithmetic type), zero outside flagged tiles
-  void *uf;           // [3][plane] collision velocity on flagged tiles
+  void *gf;           // spread force (arithmetic type; Vec3 layout), zero outside flagged tiles
+  void *uf;           // collision velocity on flagged tiles (Vec3 layout)
   unsigned *flags;    // [ntiles] tile carries a spread force / marker support
+  int *tile_list;     // [ntiles] the flagged tiles of the current level, in flagging order
+  int *tile_count;    // their number
   int *d_status;
   int *d_count;       // cut-link crossings of the most recent surface pass
   long long step;     // time level; AA parity = step & 1
@@ -225,6 +404,8 @@ struct iilbm3d_lattice {
   int n, m;
   iilbm3d_surface_params sp;
   double *X, *Gp, *G, *U, *Fn, *Aref;
+  void *Fnt;          // Fn in the arithmetic type (FP32 lattices: a copy; FP64: Fn itself)
+  long long *Xq;      // [n][3] vertex coordinates snapped to 2^-20 (the vertex pass)
   int *tri, *vt_start, *vt_list;  // triangles; each vertex's triangles (CSR, ascending)
   // graphs: two steps from an even level
   cudaGraphExec_t gexec;
@@ -240,52 +421,74 @@ struct iilbm3d_lattice {
 namespace iilbm3d {
 
 // --------------------------------------------------------------- stream-collide
-// Tile (blockIdx.x, y, z) = nodes x in [128 blockIdx.x, +128) of row (y, z).  A flagged tile
-// reads the spread force (and clears it and its flag for the next step), collides with it
-// and records the collision's velocity u for the interpolation.
-template <typename T, bool MRT, bool SIMPLE, bool BODY>
-__global__ void __launch_bounds__(TX)
-    k3_stream_collide(T *__restrict__ A, const Geom3 g, int odd, const Coll3<T> p,
-                      unsigned *__restrict__ flags, T *__restrict__ gf, T *__restrict__ uf,
-                      int *__restrict__ status) {
-  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-  const long long tile = ((long long)z * g.ny + y) * g.ntx + blockIdx.x;
-  const bool forced = flags[tile] != 0u;
-  __syncthreads();  // every thread has read the flag before it is cleared
-  if (forced && threadIdx.x == 0) flags[tile] = 0u;
-  if (x >= g.nx) return;
-  const long long c = nodeix(g, x, y, z);
-  long long loc[19];
+// One node: AA-pattern load of its streamed populations, collision, in-place store.
+// FORCED: the spread force of the node (cleared for the next step) plus the body force;
+// RECORD: the collision's velocity is kept for the interpolation.
+template <typename T, bool MRT, bool SIMPLE, bool FORCED, bool RECORD>
+__device__ __forceinline__ void sc_node(T *__restrict__ A, const Geom3 &g, int odd,
+                                        const Coll3<T> &p, int x, int y, int z,
+                                        T *__restrict__ gf, T *__restrict__ uf,
+                                        int *__restrict__ status) {
   T f[19];
-#pragma unroll
-  for (int i = 0; i < 19; i++) {
-    loc[i] = aa_read(g, odd, i, x, y, z);
-    f[i] = A[loc[i]];
-  }
+  static_for<0, 19>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    f[i] = A[aa_read_c<i>(g, odd, x, y, z)];
+  });
   T ux, uy, uz, drho;
-  if (forced || BODY) {
+  if constexpr (FORCED) {
     T gx = p.body[0], gy = p.body[1], gz = p.body[2];
-    if (forced) {
-      gx += gf[c];
-      gy += gf[g.plane + c];
-      gz += gf[2 * g.plane + c];
-      gf[c] = T(0);
-      gf[g.plane + c] = T(0);
-      gf[2 * g.plane + c] = T(0);
+    if constexpr (RECORD) {
+      T sx, sy, sz;
+      Vec3<T>::take(gf, g.plane, nodeix(g, x, y, z), sx, sy, sz);
+      gx += sx;
+      gy += sy;
+      gz += sz;
     }
     drho = collide3<T, MRT, true, SIMPLE>(f, gx, gy, gz, p, ux, uy, uz);
-    if (forced) {
-      uf[c] = ux;
-      uf[g.plane + c] = uy;
-      uf[2 * g.plane + c] = uz;
-    }
+    if constexpr (RECORD) Vec3<T>::put(uf, g.plane, nodeix(g, x, y, z), ux, uy, uz);
   } else {
     drho = collide3<T, MRT, false, SIMPLE>(f, T(0), T(0), T(0), p, ux, uy, uz);
   }
   if (!(fabs((double)drho) < 1e30)) atomicOr(status, ST_NONFINITE);
   // post-collision f_i goes where the streamed f_opp(i) was read (in place)
-#pragma unroll
-  for (int i = 0; i < 19; i++) A[loc[opp(i)]] = f[i];
+  static_for<0, 19>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    A[aa_read_c<opp(i)>(g, odd, x, y, z)] = f[i];
+  });
+}
+
+// Tile (blockIdx.x, blockIdx.y, z) = nodes [32 blockIdx.x, +32) x [4 blockIdx.y, +4) of
+// plane z.  The lean kernel updates every tile the vertex pass did not flag (with the body force alone when
+// there is one); the forced kernel takes the flagged tiles from the vertex pass's list.
+// AA-pattern locations belong to one node each per step, so the two kernels' node sets
+// touch disjoint memory.
+template <typename T, bool MRT, bool SIMPLE, bool BODY>
+__global__ void __launch_bounds__(TB, sizeof(T) == 4 ? 10 : 4)
+    k3_sc_lean(T *__restrict__ A, const Geom3 g, int odd, const Coll3<T> p,
+               const unsigned *__restrict__ flags, int *__restrict__ status) {
+  const int x = blockIdx.x * TX + (threadIdx.x & (TX - 1));
+  const int y = blockIdx.y * TY + (threadIdx.x / TX), z = blockIdx.z;
+  if (flags[((long long)z * g.nty + blockIdx.y) * g.ntx + blockIdx.x] != 0u) return;  // whole block
+  if (x >= g.nx || y >= g.ny) return;
+  sc_node<T, MRT, SIMPLE, BODY, false>(A, g, odd, p, x, y, z, nullptr, nullptr, status);
+}
+
+template <typename T, bool MRT, bool SIMPLE>
+__global__ void __launch_bounds__(TB)
+    k3_sc_forced(T *__restrict__ A, const Geom3 g, int odd, const Coll3<T> p,
+                 unsigned *__restrict__ flags, const int *__restrict__ tile_list,
+                 const int *__restrict__ tile_count, T *__restrict__ gf, T *__restrict__ uf,
+                 int *__restrict__ status) {
+  const int cnt = *tile_count;
+  for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
+    const int tile = tile_list[k];
+    const int tx = tile % g.ntx, rest = tile / g.ntx;
+    const int ty = rest % g.nty, z = rest / g.nty;
+    const int x = tx * TX + (threadIdx.x & (TX - 1)), y = ty * TY + (threadIdx.x / TX);
+    if (x < g.nx && y < g.ny)
+      sc_node<T, MRT, SIMPLE, true, true>(A, g, odd, p, x, y, z, gf, uf, status);
+    if (threadIdx.x == 0) flags[tile] = 0u;  // the lean kernel has finished reading it
+  }
 }
 
 }  // namespace iilbm3d
@@ -293,11 +496,12 @@ __global__ void __launch_bounds__(TX)
 namespace iilbm3d {
 
 // Peskin's four-point kernel (the delta function the paper names after Eq. 6).
-__device__ __forceinline__ double phi4(double r) {
-  const double a = fabs(r);
-  if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) * 0.125;
-  if (a <= 2.0) return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) * 0.125;
-  return 0.0;
+template <typename T>
+__device__ __forceinline__ T phi4t(T r) {
+  const T a = fabs(r);
+  if (a <= T(1)) return (T(3) - T(2) * a + sqrt(T(1) + T(4) * a - T(4) * a * a)) * T(0.125);
+  if (a <= T(2)) return (T(5) - T(2) * a - sqrt(T(-7) + T(12) * a - T(4) * a * a)) * T(0.125);
+  return T(0);
 }
 
 __device__ __forceinline__ int wrapfull(int v, int n) {
@@ -318,84 +522,95 @@ __global__ void __launch_bounds__(128)
               const double *__restrict__ Aref, int model, double gamma,
               const double *__restrict__ Gp, int jump, const Geom3 g, double *__restrict__ G,
               double *__restrict__ Fn, T *__restrict__ gf, unsigned *__restrict__ flags,
-              int *__restrict__ status) {
+              int *__restrict__ tile_list, int *__restrict__ tile_count, T *__restrict__ Fnt,
+              long long *__restrict__ Xq, int *__restrict__ status) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const double xk = X[3 * k], yk = X[3 * k + 1], zk = X[3 * k + 2];
   if (!(fabs(xk) < MAX_COORD && fabs(yk) < MAX_COORD && fabs(zk) < MAX_COORD)) {
     atomicOr(status, ST_INTERFACE);
+    Xq[3 * k] = Xq[3 * k + 1] = Xq[3 * k + 2] = XQ_OUT;  // its triangles get no cut links
     return;
   }
-  double ns[3] = {0.0, 0.0, 0.0}, area = 0.0, Gk[3] = {0.0, 0.0, 0.0};
+  // the snapped coordinates of the crossing predicate, once per vertex
+  Xq[3 * k] = __double2ll_rn(xk * QS);
+  Xq[3 * k + 1] = __double2ll_rn(yk * QS);
+  Xq[3 * k + 2] = __double2ll_rn(zk * QS);
+  // geometry in the arithmetic type from FP64 coordinate differences
+  T ns[3] = {T(0), T(0), T(0)}, area = T(0), Gk[3] = {T(0), T(0), T(0)};
+  const T gam = T(gamma);
   for (int q = vt_start[k]; q < vt_start[k + 1]; q++) {
     const int t = vt_list[q];
     const int v0 = tri[3 * t], v1 = tri[3 * t + 1], v2 = tri[3 * t + 2];
     const double *A = X + 3 * v0, *B = X + 3 * v1, *C = X + 3 * v2;
-    const double u[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
-    const double v[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
-    const double N[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2],
-                         u[0] * v[1] - u[1] * v[0]};
-    const double l = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
-    area += l / 6.0;
+    const T u[3] = {T(B[0] - A[0]), T(B[1] - A[1]), T(B[2] - A[2])};
+    const T v[3] = {T(C[0] - A[0]), T(C[1] - A[1]), T(C[2] - A[2])};
+    const T N[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+    const T l = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    area += l / T(6);
     ns[0] += N[0];
     ns[1] += N[1];
     ns[2] += N[2];
     if (model == IILBM3D_TENSION) {
       const int p = v0 == k ? v1 : (v1 == k ? v2 : v0);
       const int r = v0 == k ? v2 : (v1 == k ? v0 : v1);
-      const double h[3] = {N[0] / l, N[1] / l, N[2] / l};
-      const double e[3] = {X[3 * r] - X[3 * p], X[3 * r + 1] - X[3 * p + 1],
-                           X[3 * r + 2] - X[3 * p + 2]};
-      const double dA[3] = {0.5 * (h[1] * e[2] - h[2] * e[1]), 0.5 * (h[2] * e[0] - h[0] * e[2]),
-                            0.5 * (h[0] * e[1] - h[1] * e[0])};
-      Gk[0] -= gamma * dA[0];
-      Gk[1] -= gamma * dA[1];
-      Gk[2] -= gamma * dA[2];
+      const T h[3] = {N[0] / l, N[1] / l, N[2] / l};
+      const T e[3] = {T(X[3 * r] - X[3 * p]), T(X[3 * r + 1] - X[3 * p + 1]),
+                      T(X[3 * r + 2] - X[3 * p + 2])};
+      const T dA[3] = {T(0.5) * (h[1] * e[2] - h[2] * e[1]), T(0.5) * (h[2] * e[0] - h[0] * e[2]),
+                       T(0.5) * (h[0] * e[1] - h[1] * e[0])};
+      Gk[0] -= gam * dA[0];
+      Gk[1] -= gam * dA[1];
+      Gk[2] -= gam * dA[2];
     }
   }
-  const double ln = sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
-  const double nk[3] = {ns[0] / ln, ns[1] / ln, ns[2] / ln};
-  const double ar = Aref[k];
+  const T ln = sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
+  const T nk[3] = {ns[0] / ln, ns[1] / ln, ns[2] / ln};
+  const T ar = T(Aref[k]);
   if (model == IILBM3D_TENSION) {
     Gk[0] /= ar;
     Gk[1] /= ar;
     Gk[2] /= ar;
   } else {
-    Gk[0] = Gp[3 * k];
-    Gk[1] = Gp[3 * k + 1];
-    Gk[2] = Gp[3 * k + 2];
+    Gk[0] = T(Gp[3 * k]);
+    Gk[1] = T(Gp[3 * k + 1]);
+    Gk[2] = T(Gp[3 * k + 2]);
   }
-  G[3 * k] = Gk[0];
-  G[3 * k + 1] = Gk[1];
-  G[3 * k + 2] = Gk[2];
-  const double gn = Gk[0] * nk[0] + Gk[1] * nk[1] + Gk[2] * nk[2];
-  Fn[k] = gn / (area / ar);
-  double P[3];
+  G[3 * k] = (double)Gk[0];
+  G[3 * k + 1] = (double)Gk[1];
+  G[3 * k + 2] = (double)Gk[2];
+  const T gn = Gk[0] * nk[0] + Gk[1] * nk[1] + Gk[2] * nk[2];
+  const T fnk = gn / (area / ar);
+  Fn[k] = (double)fnk;
+  Fnt[k] = fnk;
+  T Pt[3];
 #pragma unroll
-  for (int d = 0; d < 3; d++) P[d] = (jump ? Gk[d] - gn * nk[d] : Gk[d]) * ar;
+  for (int d = 0; d < 3; d++) Pt[d] = (jump ? Gk[d] - gn * nk[d] : Gk[d]) * ar;
   const int bx = (int)floor(xk) - 1, by = (int)floor(yk) - 1, bz = (int)floor(zk) - 1;
-  double wx[4], wy[4], wz[4];
+  // kernel weights in the arithmetic type (the offsets taken in FP64 from the position)
+  T wx[4], wy[4], wz[4];
 #pragma unroll
   for (int q = 0; q < 4; q++) {
-    wx[q] = phi4((double)(bx + q) - xk);
-    wy[q] = phi4((double)(by + q) - yk);
-    wz[q] = phi4((double)(bz + q) - zk);
+    wx[q] = phi4t<T>(T((double)(bx + q) - xk));
+    wy[q] = phi4t<T>(T((double)(by + q) - yk));
+    wz[q] = phi4t<T>(T((double)(bz + q) - zk));
   }
+#pragma unroll
   for (int dz = 0; dz < 4; dz++) {
     const int z = wrapfull(bz + dz, g.nz);
+#pragma unroll
     for (int dy = 0; dy < 4; dy++) {
       const int y = wrapfull(by + dy, g.ny);
       int last = -1;
+#pragma unroll
       for (int dx = 0; dx < 4; dx++) {
         const int x = wrapfull(bx + dx, g.nx);
-        const double w = wx[dx] * wy[dy] * wz[dz];
-        const long long c = nodeix(g, x, y, z);
-        atomicAdd(&gf[c], T(P[0] * w));
-        atomicAdd(&gf[g.plane + c], T(P[1] * w));
-        atomicAdd(&gf[2 * g.plane + c], T(P[2] * w));
+        const T w = wx[dx] * wy[dy] * wz[dz];
+        Vec3<T>::add(gf, g.plane, nodeix(g, x, y, z), Pt[0] * w, Pt[1] * w, Pt[2] * w);
         const int tx = x / TX;
         if (tx != last) {
-          flags[((long long)z * g.ny + y) * g.ntx + tx] = 1u;
+          const int tile = (int)(((long long)z * g.nty + y / TY) * g.ntx + tx);
+          if (atomicExch(&flags[tile], 1u) == 0u) tile_list[atomicAdd(tile_count, 1)] = tile;
           last = tx;
         }
       }
@@ -406,16 +621,8 @@ __global__ void __launch_bounds__(128)
 // ------------------------------------------------------------------ cut links
 // The exact crossing predicate (coordinates snapped to 2^-20, every lattice node displaced
 // by (eps, eps^2, eps^3), eps -> 0+): the plane side of a node is the sign of the first
-// non-zero of (N.(X - A), N_x, N_y, N_z); the side of the displaced link line about edge
-// U -> V that of (det[d, U - P, V - P], -w_x, -w_y, -w_z), w = (V - U) x d.
-__device__ __forceinline__ int plane_side(const long long *A, const long long *N, const long long *Xq) {
-  const __int128 r = (__int128)N[0] * (Xq[0] - A[0]) + (__int128)N[1] * (Xq[1] - A[1]) +
-                     (__int128)N[2] * (Xq[2] - A[2]);
-  if (r != 0) return r > 0 ? 1 : -1;
-  for (int d = 0; d < 3; d++)
-    if (N[d] != 0) return N[d] > 0 ? 1 : -1;
-  return 0;
-}
+// non-zero of (N.(X - A), N_x, N_y, N_z) (in k3_cut); the side of the displaced link line
+// about edge U -> V that of (det[d, U - P, V - P], -w_x, -w_y, -w_z), w = (V - U) x d.
 __device__ __forceinline__ int edge_side(const long long *P, int dx, int dy, int dz,
                                          const long long *U, const long long *V, long long &det) {
   const long long a[3] = {U[0] - P[0], U[1] - P[1], U[2] - P[2]};
@@ -436,22 +643,25 @@ __device__ __forceinline__ int edge_side(const long long *P, int dx, int dy, int
 // interpolated barycentrically over the triangle, to the streamed population in place
 // (INPLACE) or to the field J[i-1][node] (read-outs).
 template <bool INPLACE, typename S>
-__global__ void __launch_bounds__(128)
-    k3_cut(const double *__restrict__ X, const int *__restrict__ tri, int m,
-           const double *__restrict__ Fn, const Geom3 g, int odd, S *__restrict__ A,
+__global__ void __launch_bounds__(128, 6)
+    k3_cut(const long long *__restrict__ Xq, const int *__restrict__ tri, int m,
+           const S *__restrict__ Fn, const Geom3 g, int odd, S *__restrict__ A,
            double *__restrict__ J, int *__restrict__ count, int *__restrict__ status) {
+  // per warp: the plane sides of the widened candidate box; the per-axis edge bound below
+  // (< 8 lattice units) keeps the box within CUT_BOX^3 nodes
+  __shared__ signed char cut_sides[4][CUT_BOX * CUT_BOX * CUT_BOX];
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (t >= m) return;
   const int vi[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
   long long q[3][3];
   bool ok = true;
+  const long long qmax = (long long)(MAX_COORD * QS);
 #pragma unroll
   for (int j = 0; j < 3; j++)
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-      const double v = X[3 * vi[j] + a];
-      ok = ok && fabs(v) < MAX_COORD;
-      q[j][a] = __double2ll_rn(v * QS);
+      q[j][a] = Xq[3 * vi[j] + a];
+      ok = ok && q[j][a] < qmax && -q[j][a] < qmax;
     }
   const long long lim = (long long)(MAX_EDGE * QS);
 #pragma unroll
@@ -477,33 +687,72 @@ __global__ void __launch_bounds__(128)
     lo[a] = (int)(-((-mn) >> QBITS)) - 1;
     ext[a] = (int)(-((-mx) >> QBITS)) - lo[a] + 1;
   }
-  const int ncand = ext[0] * ext[1] * ext[2] * 18;
+  // the plane side of node X + delta: sign of N.(X - A), ties by the first non-zero of
+  // (N_x, N_y, N_z) (the same for every node); computed once per node of the candidate
+  // box widened by one node (every link's source lies there) into the warp's table
+  const int tie = N[0] ? (N[0] > 0 ? 1 : -1) : (N[1] ? (N[1] > 0 ? 1 : -1) : (N[2] > 0 ? 1 : -1));
+  const int E0 = ext[0] + 2, E1 = ext[1] + 2, E2 = ext[2] + 2;
+  signed char *side = cut_sides[threadIdx.x >> 5];
   const long long Sx = 1LL << QBITS;
+  // N.(X - A) is affine in the node's offset (a, b, c) from the widened box's corner X0:
+  // r0 + (a N_x + b N_y + c N_z) 2^20, the bracket below 2^56 in 64 bits
+  const __int128 r0 = (__int128)N[0] * ((long long)(lo[0] - 1) * Sx - q[0][0]) +
+                      (__int128)N[1] * ((long long)(lo[1] - 1) * Sx - q[0][1]) +
+                      (__int128)N[2] * ((long long)(lo[2] - 1) * Sx - q[0][2]);
+  // box index -> (a, b, c) by FP32 quotients: (k + 1/2) / E is at least 1/(2E) from an
+  // integer (E <= 12, k < 1728), far beyond the quotient's rounding error
+  const float iE0 = 1.0f / (float)E0, iE01 = 1.0f / (float)(E0 * E1);
+  for (int c = lane; c < E0 * E1 * E2; c += 32) {
+    const int cz = (int)(((float)c + 0.5f) * iE01), rem = c - cz * E0 * E1;
+    const int b = (int)(((float)rem + 0.5f) * iE0), a = rem - b * E0;
+    const long long L = a * N[0] + b * N[1] + cz * N[2];
+    const __int128 r = r0 + ((__int128)L << QBITS);
+    side[c] = (signed char)(r > 0 ? 1 : (r < 0 ? -1 : tie));
+  }
+  __syncwarp();
   int found = 0;
-  for (int c = lane; c < ncand; c += 32) {
-    const int i = 1 + c % 18, cell = c / 18;
-    const int x = lo[0] + cell % ext[0], y = lo[1] + (cell / ext[0]) % ext[1];
-    const int z = lo[2] + cell / (ext[0] * ext[1]);
-    const int dx = ex(i), dy = ey(i), dz = ez(i);
-    const long long Q[3] = {x * Sx, y * Sx, z * Sx};
-    const long long P[3] = {Q[0] - dx * Sx, Q[1] - dy * Sx, Q[2] - dz * Sx};
-    const int sP = plane_side(q[0], N, P), sQ = plane_side(q[0], N, Q);
-    if (sP == sQ || sP == 0 || sQ == 0) continue;
-    long long vAB, vBC, vCA;
-    const int e1 = edge_side(P, dx, dy, dz, q[0], q[1], vAB);
-    const int e2 = edge_side(P, dx, dy, dz, q[1], q[2], vBC);
-    const int e3 = edge_side(P, dx, dy, dz, q[2], q[0], vCA);
-    if (e1 == 0 || e1 != e2 || e2 != e3) continue;
-    const double s = (double)vAB + (double)vBC + (double)vCA;
-    const double fc = ((double)vBC / s) * Fn[vi[0]] + ((double)vCA / s) * Fn[vi[1]] +
-                      ((double)vAB / s) * Fn[vi[2]];
-    const double coef = (double)sQ * wt<double>(i) * 3.0 * fc;
-    const int xw = wrapfull(x, g.nx), yw = wrapfull(y, g.ny), zw = wrapfull(z, g.nz);
-    if (INPLACE)
-      atomicAdd(&A[aa_read(g, odd != 0, i, xw, yw, zw)], S(coef));
-    else
-      atomicAdd(&J[(long long)(i - 1) * g.plane + nodeix(g, xw, yw, zw)], coef);
-    found++;
+  // lanes over the destinations: the directions whose link ends lie on opposite sides of
+  // the plane (two table reads each, constant offsets) form a mask; only those get the
+  // three edge tests
+  const int nn = ext[0] * ext[1] * ext[2];
+  const float iX = 1.0f / (float)ext[0], iXY = 1.0f / (float)(ext[0] * ext[1]);
+  for (int cidx = lane; cidx < nn; cidx += 32) {
+    const int gz = (int)(((float)cidx + 0.5f) * iXY), rem = cidx - gz * ext[0] * ext[1];
+    const int gy = (int)(((float)rem + 0.5f) * iX), gx = rem - gy * ext[0];
+    const int base = (gx + 1) + E0 * ((gy + 1) + E1 * (gz + 1));
+    const int sQ = side[base];
+    unsigned mask = 0u;
+    static_for<1, 19>([&](auto ic) {
+      constexpr int i = decltype(ic)::value;
+      const int off = ex(i) + E0 * (ey(i) + E1 * ez(i));
+      if (side[base - off] != sQ) mask |= 1u << i;
+    });
+    const int x = lo[0] + gx, y = lo[1] + gy, z = lo[2] + gz;
+    while (mask) {
+      const int i = __ffs(mask) - 1;
+      mask &= mask - 1u;
+      const int dx = exr(i), dy = eyr(i), dz = ezr(i);
+      const long long P[3] = {(long long)(x - dx) * Sx, (long long)(y - dy) * Sx,
+                              (long long)(z - dz) * Sx};
+      long long vAB, vBC, vCA;
+      const int e1 = edge_side(P, dx, dy, dz, q[0], q[1], vAB);
+      const int e2 = edge_side(P, dx, dy, dz, q[1], q[2], vBC);
+      const int e3 = edge_side(P, dx, dy, dz, q[2], q[0], vCA);
+      if (e1 == 0 || e1 != e2 || e2 != e3) continue;
+      // Fn at the crossing: the barycentric mean of the vertices' Fn (one division), in the
+      // arithmetic type (GB300's FP64 pipe would make this the kernel's cost in FP32 runs)
+      const S sum = S(vAB) + S(vBC) + S(vCA);
+      const S fc = (S(vBC) * Fn[vi[0]] + S(vCA) * Fn[vi[1]] + S(vAB) * Fn[vi[2]]) / sum;
+      const S coef = S(sQ) * (S(3) * wt<S>(i)) * fc;
+      const int xw = (unsigned)x < (unsigned)g.nx ? x : wrapfull(x, g.nx);
+      const int yw = (unsigned)y < (unsigned)g.ny ? y : wrapfull(y, g.ny);
+      const int zw = (unsigned)z < (unsigned)g.nz ? z : wrapfull(z, g.nz);
+      if constexpr (INPLACE)
+        atomicAdd(&A[aa_read(g, odd != 0, i, xw, yw, zw)], S(coef));
+      else
+        atomicAdd(&J[(long long)(i - 1) * g.plane + nodeix(g, xw, yw, zw)], (double)coef);
+      found++;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) found += __shfl_xor_sync(0xffffffffu, found, o);
@@ -522,34 +771,38 @@ __global__ void __launch_bounds__(128)
   const double xk = X[3 * k], yk = X[3 * k + 1], zk = X[3 * k + 2];
   if (!(fabs(xk) < MAX_COORD && fabs(yk) < MAX_COORD && fabs(zk) < MAX_COORD)) return;
   const int bx = (int)floor(xk) - 1, by = (int)floor(yk) - 1, bz = (int)floor(zk) - 1;
-  double wx[4], wy[4], wz[4];
+  T wx[4], wy[4], wz[4];
 #pragma unroll
   for (int q = 0; q < 4; q++) {
-    wx[q] = phi4((double)(bx + q) - xk);
-    wy[q] = phi4((double)(by + q) - yk);
-    wz[q] = phi4((double)(bz + q) - zk);
+    wx[q] = phi4t<T>(T((double)(bx + q) - xk));
+    wy[q] = phi4t<T>(T((double)(by + q) - yk));
+    wz[q] = phi4t<T>(T((double)(bz + q) - zk));
   }
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  T s0 = T(0), s1 = T(0), s2 = T(0);
+#pragma unroll
   for (int dz = 0; dz < 4; dz++) {
     const int z = wrapfull(bz + dz, g.nz);
+#pragma unroll
     for (int dy = 0; dy < 4; dy++) {
       const int y = wrapfull(by + dy, g.ny);
+#pragma unroll
       for (int dx = 0; dx < 4; dx++) {
-        const long long c = nodeix(g, wrapfull(bx + dx, g.nx), y, z);
-        const double w = wx[dx] * wy[dy] * wz[dz];
-        s0 += (double)uf[c] * w;
-        s1 += (double)uf[g.plane + c] * w;
-        s2 += (double)uf[2 * g.plane + c] * w;
+        T u0, u1, u2;
+        Vec3<T>::get(uf, g.plane, nodeix(g, wrapfull(bx + dx, g.nx), y, z), u0, u1, u2);
+        const T w = wx[dx] * wy[dy] * wz[dz];
+        s0 += u0 * w;
+        s1 += u1 * w;
+        s2 += u2 * w;
       }
     }
   }
-  U[3 * k] = s0;
-  U[3 * k + 1] = s1;
-  U[3 * k + 2] = s2;
+  U[3 * k] = (double)s0;
+  U[3 * k + 1] = (double)s1;
+  U[3 * k + 2] = (double)s2;
   if (moves) {
-    X[3 * k] = xk + s0;
-    X[3 * k + 1] = yk + s1;
-    X[3 * k + 2] = zk + s2;
+    X[3 * k] = xk + (double)s0;
+    X[3 * k + 1] = yk + (double)s1;
+    X[3 * k + 2] = zk + (double)s2;
   }
 }
 
@@ -587,8 +840,9 @@ __global__ void k3_macros(const S *__restrict__ A, const double *__restrict__ J,
     jy += ey(i) * f;
     jz += ez(i) * f;
   }
-  const double gx = bx + (double)gf[c], gy = by + (double)gf[g.plane + c],
-               gz = bz + (double)gf[2 * g.plane + c];
+  S sx, sy, sz;
+  Vec3<S>::get(gf, g.plane, c, sx, sy, sz);
+  const double gx = bx + (double)sx, gy = by + (double)sy, gz = bz + (double)sz;
   out[c] = s;
   out[g.plane + c] = (jx + h * gx) / (rho0 + s);
   out[2 * g.plane + c] = (jy + h * gy) / (rho0 + s);
@@ -654,14 +908,20 @@ bool has_body(const H *h) { return h->cfg.body[0] != 0.0 || h->cfg.body[1] != 0.
 template <typename S, bool MRT, bool SIMPLE>
 void launch_sc_t(H *h, cudaStream_t s) {
   const Geom3 &g = h->geo;
-  const dim3 grid(g.ntx, g.ny, g.nz);
+  const dim3 grid(g.ntx, g.nty, g.nz);
   const Coll3<S> p = coll_params<S>(h);
+  const int odd = (int)(h->step & 1);
   if (has_body(h))
-    k3_stream_collide<S, MRT, SIMPLE, true><<<grid, TX, 0, s>>>(
-        (S *)h->A, g, (int)(h->step & 1), p, h->flags, (S *)h->gf, (S *)h->uf, h->d_status);
+    k3_sc_lean<S, MRT, SIMPLE, true><<<grid, TB, 0, s>>>((S *)h->A, g, odd, p, h->flags, h->d_status);
   else
-    k3_stream_collide<S, MRT, SIMPLE, false><<<grid, TX, 0, s>>>(
-        (S *)h->A, g, (int)(h->step & 1), p, h->flags, (S *)h->gf, (S *)h->uf, h->d_status);
+    k3_sc_lean<S, MRT, SIMPLE, false><<<grid, TB, 0, s>>>((S *)h->A, g, odd, p, h->flags, h->d_status);
+  if (h->n > 0) {
+    const long long ntiles = (long long)g.ntx * g.nty * g.nz;
+    const unsigned blocks = (unsigned)std::min<long long>(ntiles, 152LL * 16);
+    k3_sc_forced<S, MRT, SIMPLE><<<blocks, TB, 0, s>>>((S *)h->A, g, odd, p, h->flags,
+                                                        h->tile_list, h->tile_count,
+                                                        (S *)h->gf, (S *)h->uf, h->d_status);
+  }
 }
 
 template <typename S>
@@ -681,14 +941,18 @@ void launch_sc(H *h) {
 void launch_vertex(H *h) {
   const Geom3 &g = h->geo;
   const unsigned b = blocks_for(h->n, 128);
+  cudaMemsetAsync(h->tile_count, 0, sizeof(int), h->stream);
   if (h->f64)
     k3_vertex<double><<<b, 128, 0, h->stream>>>(h->X, h->n, h->tri, h->vt_start, h->vt_list, h->Aref,
                                                 h->sp.model, h->sp.gamma, h->Gp, h->cfg.jump, g,
-                                                h->G, h->Fn, (double *)h->gf, h->flags, h->d_status);
+                                                h->G, h->Fn, (double *)h->gf, h->flags,
+                                                h->tile_list, h->tile_count, h->Fn, h->Xq, h->d_status);
   else
     k3_vertex<float><<<b, 128, 0, h->stream>>>(h->X, h->n, h->tri, h->vt_start, h->vt_list, h->Aref,
                                                h->sp.model, h->sp.gamma, h->Gp, h->cfg.jump, g,
-                                               h->G, h->Fn, (float *)h->gf, h->flags, h->d_status);
+                                               h->G, h->Fn, (float *)h->gf, h->flags,
+                                               h->tile_list, h->tile_count, (float *)h->Fnt,
+                                               h->Xq, h->d_status);
 }
 
 // the jump of the current level: in place into the populations (J null) or into J
@@ -697,17 +961,17 @@ void launch_cut(H *h, double *J) {
   const int odd = (int)(h->step & 1);
   if (J) {
     if (h->f64)
-      k3_cut<false, double><<<b, 128, 0, h->stream>>>(h->X, h->tri, h->m, h->Fn, h->geo, odd,
+      k3_cut<false, double><<<b, 128, 0, h->stream>>>(h->Xq, h->tri, h->m, (double *)h->Fnt, h->geo, odd,
                                                       (double *)h->A, J, h->d_count, h->d_status);
     else
-      k3_cut<false, float><<<b, 128, 0, h->stream>>>(h->X, h->tri, h->m, h->Fn, h->geo, odd,
+      k3_cut<false, float><<<b, 128, 0, h->stream>>>(h->Xq, h->tri, h->m, (float *)h->Fnt, h->geo, odd,
                                                      (float *)h->A, J, h->d_count, h->d_status);
   } else {
     if (h->f64)
-      k3_cut<true, double><<<b, 128, 0, h->stream>>>(h->X, h->tri, h->m, h->Fn, h->geo, odd,
+      k3_cut<true, double><<<b, 128, 0, h->stream>>>(h->Xq, h->tri, h->m, (double *)h->Fnt, h->geo, odd,
                                                      (double *)h->A, nullptr, h->d_count, h->d_status);
     else
-      k3_cut<true, float><<<b, 128, 0, h->stream>>>(h->X, h->tri, h->m, h->Fn, h->geo, odd,
+      k3_cut<true, float><<<b, 128, 0, h->stream>>>(h->Xq, h->tri, h->m, (float *)h->Fnt, h->geo, odd,
                                                     (float *)h->A, nullptr, h->d_count, h->d_status);
   }
 }
@@ -744,7 +1008,7 @@ int one_step(H *h) {
   if (h->timing) {
     CK3(cudaEventRecord(h->ev[2 * h->nev + 1], h->stream));
     h->nev++;
-    h->kernels += h->n > 0 ? (h->cfg.jump ? 4 : 3) - (h->prepared ? 1 : 0) : 1;
+    h->kernels += h->n > 0 ? (h->cfg.jump ? 5 : 4) - (h->prepared ? 1 : 0) : 1;
   }
   if (h->n > 0) launch_interp(h);
   CK3(cudaGetLastError());
@@ -791,6 +1055,10 @@ int read_status3(H *h) {
 }
 
 void free_surface(H *h) {
+  if (h->Fnt && h->Fnt != (void *)h->Fn) cudaFree(h->Fnt);
+  h->Fnt = nullptr;
+  if (h->Xq) cudaFree(h->Xq);
+  h->Xq = nullptr;
   void *p[] = {h->X, h->Gp, h->G, h->U, h->Fn, h->Aref, h->tri, h->vt_start, h->vt_list};
   for (void *q : p)
     if (q) cudaFree(q);
@@ -859,9 +1127,10 @@ int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
   g.ny = c.ny;
   g.nz = c.nz;
   g.ntx = (c.nx + TX - 1) / TX;
+  g.nty = (c.ny + TY - 1) / TY;
   g.plane = (long long)c.nx * c.ny * c.nz;
   const size_t sb = h->f64 ? 8 : 4;
-  const size_t ntiles = (size_t)g.ntx * c.ny * c.nz;
+  const size_t ntiles = (size_t)g.ntx * g.nty * c.nz;
   bool ok = true;
   if (c.stream) {
     h->stream = (cudaStream_t)c.stream;
@@ -870,15 +1139,18 @@ int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
     h->own_stream = ok;
   }
   ok = ok && cudaMalloc(&h->A, 19 * g.plane * sb) == cudaSuccess &&
-       cudaMalloc(&h->gf, 3 * g.plane * sb) == cudaSuccess &&
-       cudaMalloc(&h->uf, 3 * g.plane * sb) == cudaSuccess &&
+       cudaMalloc(&h->gf, 4 * g.plane * sb) == cudaSuccess &&
+       cudaMalloc(&h->uf, 4 * g.plane * sb) == cudaSuccess &&
        cudaMalloc(&h->flags, ntiles * sizeof(unsigned)) == cudaSuccess &&
+       cudaMalloc(&h->tile_list, ntiles * sizeof(int)) == cudaSuccess &&
+       cudaMalloc(&h->tile_count, sizeof(int)) == cudaSuccess &&
        cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
        cudaMalloc(&h->d_count, sizeof(int)) == cudaSuccess;
   ok = ok && cudaMemsetAsync(h->A, 0, 19 * g.plane * sb, h->stream) == cudaSuccess &&
-       cudaMemsetAsync(h->gf, 0, 3 * g.plane * sb, h->stream) == cudaSuccess &&
-       cudaMemsetAsync(h->uf, 0, 3 * g.plane * sb, h->stream) == cudaSuccess &&
+       cudaMemsetAsync(h->gf, 0, 4 * g.plane * sb, h->stream) == cudaSuccess &&
+       cudaMemsetAsync(h->uf, 0, 4 * g.plane * sb, h->stream) == cudaSuccess &&
        cudaMemsetAsync(h->flags, 0, ntiles * sizeof(unsigned), h->stream) == cudaSuccess &&
+       cudaMemsetAsync(h->tile_count, 0, sizeof(int), h->stream) == cudaSuccess &&
        cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream) == cudaSuccess &&
        cudaMemsetAsync(h->d_count, 0, sizeof(int), h->stream) == cudaSuccess &&
        cudaStreamSynchronize(h->stream) == cudaSuccess;
@@ -896,7 +1168,7 @@ int iilbm3d_destroy(iilbm3d_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graph(h);
   free_surface(h);
-  void *p[] = {h->A, h->gf, h->uf, h->flags, h->d_status, h->d_count};
+  void *p[] = {h->A, h->gf, h->uf, h->flags, h->tile_list, h->tile_count, h->d_status, h->d_count};
   for (void *q : p)
     if (q) cudaFree(q);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -921,9 +1193,10 @@ int iilbm3d_set_surface(iilbm3d_t h, const double *X, int32_t n, const int32_t *
   free_surface(h);
   // clear what a prepared level left behind
   const size_t sb = h->f64 ? 8 : 4;
-  const size_t ntiles = (size_t)h->geo.ntx * h->geo.ny * h->geo.nz;
-  CK3(cudaMemsetAsync(h->gf, 0, 3 * h->geo.plane * sb, h->stream));
+  const size_t ntiles = (size_t)h->geo.ntx * h->geo.nty * h->geo.nz;
+  CK3(cudaMemsetAsync(h->gf, 0, 4 * h->geo.plane * sb, h->stream));
   CK3(cudaMemsetAsync(h->flags, 0, ntiles * sizeof(unsigned), h->stream));
+  CK3(cudaMemsetAsync(h->tile_count, 0, sizeof(int), h->stream));
   h->prepared = false;
   if (n == 0) return IILBM_OK;
   std::vector<double> hx(3 * (size_t)n), hg;
@@ -972,6 +1245,8 @@ int iilbm3d_set_surface(iilbm3d_t h, const double *X, int32_t n, const int32_t *
   bool ok = cudaMalloc(&h->X, b3) == cudaSuccess && cudaMalloc(&h->Gp, b3) == cudaSuccess &&
             cudaMalloc(&h->G, b3) == cudaSuccess && cudaMalloc(&h->U, b3) == cudaSuccess &&
             cudaMalloc(&h->Fn, n * sizeof(double)) == cudaSuccess &&
+            (h->f64 || cudaMalloc(&h->Fnt, n * sizeof(float)) == cudaSuccess) &&
+            cudaMalloc(&h->Xq, 3 * (size_t)n * sizeof(long long)) == cudaSuccess &&
             cudaMalloc(&h->Aref, n * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&h->tri, 3 * (size_t)m * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->vt_start, (n + 1) * sizeof(int)) == cudaSuccess &&
@@ -981,6 +1256,7 @@ int iilbm3d_set_surface(iilbm3d_t h, const double *X, int32_t n, const int32_t *
     free_surface(h);
     return IILBM_ERR_OOM;
   }
+  if (h->f64) h->Fnt = h->Fn;
   h->n = n;
   h->m = m;
   h->sp = *p;

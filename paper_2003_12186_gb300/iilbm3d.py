@@ -168,6 +168,13 @@ class Lattice3D:
             self._h, self._p(X, 3 * n), self._p(G, 3 * n), self._p(U, 3 * n), self._p(Fn, n)))
         return dict(X=X, G=G, U=U, Fn=Fn)
 
+    def get_markers_into(self, X=None, G=None, U=None, Fn=None):
+        """The vertex arrays into caller buffers (numpy or torch, host or the lattice's
+        device; None skips one)."""
+        n = self.n
+        _check("iilbm3d_get_markers", self._L.iilbm3d_get_markers(
+            self._h, self._p(X, 3 * n), self._p(G, 3 * n), self._p(U, 3 * n), self._p(Fn, n)))
+
     def get_jump(self, out=None):
         out = np.zeros((18, self.nz, self.ny, self.nx)) if out is None else out
         _check("iilbm3d_get_jump", self._L.iilbm3d_get_jump(self._h, self._p(out, 18 * self.N)))

@@ -240,3 +240,16 @@ def random_df3(nx: int, ny: int, nz: int, amp: float, seed: int) -> np.ndarray:
     """Random shifted D3Q19 populations df[19, nz, ny, nx] of amplitude amp."""
     rng = np.random.default_rng(seed)
     return amp * rng.standard_normal((19, nz, ny, nx))
+
+
+def membrane_3d(n: int = 256, seed: int = 17):
+    """The three-dimensional membrane workload: an n^3 periodic D3Q19 box (MRT, tau 0.6)
+    holding a surface-tension ellipsoid with semi-axes 0.31 n, 0.25 n, 0.22 n at the box's
+    centre (offset from the nodes), turned by a seeded rotation, triangulated so that its
+    edges are about one lattice unit (icosphere level 6 at n = 256, 40 962 vertices), at
+    rest; gamma = 1e-3 lattice units."""
+    level = max(3, int(round(math.log2(n / 256.0))) + 6)
+    c = (n / 2 + 0.37, n / 2 + 0.21, n / 2 + 0.13)
+    X, T = ellipsoid_surface(c, (0.31 * n, 0.25 * n, 0.22 * n), level, seed=seed)
+    return {"name": f"membrane3d_{n}", "n": n, "X": X, "T": T, "tau": 0.6, "gamma": 1e-3,
+            "level": level}

@@ -424,16 +424,21 @@ namespace iilbm3d {
 // One node: AA-pattern load of its streamed populations, collision, in-place store.
 // FORCED: the spread force of the node (cleared for the next step) plus the body force;
 // RECORD: the collision's velocity is kept for the interpolation.
-template <typename T, bool MRT, bool SIMPLE, bool FORCED, bool RECORD>
-__device__ __forceinline__ void sc_node(T *__restrict__ A, const Geom3 &g, int odd,
-                                        const Coll3<T> &p, int x, int y, int z,
-                                        T *__restrict__ gf, T *__restrict__ uf,
-                                        int *__restrict__ status) {
-  T f[19];
+template <typename T>
+__device__ __forceinline__ void sc_load(const T *__restrict__ A, const Geom3 &g, int odd, int x,
+                                        int y, int z, T f[19]) {
   static_for<0, 19>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
     f[i] = A[aa_read_c<i>(g, odd, x, y, z)];
   });
+}
+
+// Collision and in-place store of one node whose streamed populations are in f.
+template <typename T, bool MRT, bool SIMPLE, bool FORCED, bool RECORD>
+__device__ __forceinline__ void sc_finish(T *__restrict__ A, const Geom3 &g, int odd,
+                                          const Coll3<T> &p, int x, int y, int z, T f[19],
+                                          T *__restrict__ gf, T *__restrict__ uf,
+                                          int *__restrict__ status) {
   T ux, uy, uz, drho;
   if constexpr (FORCED) {
     T gx = p.body[0], gy = p.body[1], gz = p.body[2];
@@ -455,6 +460,16 @@ __device__ __forceinline__ void sc_node(T *__restrict__ A, const Geom3 &g, int o
     constexpr int i = decltype(ic)::value;
     A[aa_read_c<opp(i)>(g, odd, x, y, z)] = f[i];
   });
+}
+
+template <typename T, bool MRT, bool SIMPLE, bool FORCED, bool RECORD>
+__device__ __forceinline__ void sc_node(T *__restrict__ A, const Geom3 &g, int odd,
+                                        const Coll3<T> &p, int x, int y, int z,
+                                        T *__restrict__ gf, T *__restrict__ uf,
+                                        int *__restrict__ status) {
+  T f[19];
+  sc_load<T>(A, g, odd, x, y, z, f);
+  sc_finish<T, MRT, SIMPLE, FORCED, RECORD>(A, g, odd, p, x, y, z, f, gf, uf, status);
 }
 
 // Tile (blockIdx.x, blockIdx.y, z) = nodes [32 blockIdx.x, +32) x [4 blockIdx.y, +4) of
@@ -620,37 +635,59 @@ __global__ void __launch_bounds__(128)
 
 // ------------------------------------------------------------------ cut links
 // The exact crossing predicate (coordinates snapped to 2^-20, every lattice node displaced
-// by (eps, eps^2, eps^3), eps -> 0+): the plane side of a node is the sign of the first
-// non-zero of (N.(X - A), N_x, N_y, N_z) (in k3_cut); the side of the displaced link line
-// about edge U -> V that of (det[d, U - P, V - P], -w_x, -w_y, -w_z), w = (V - U) x d.
-__device__ __forceinline__ int edge_side(const long long *P, int dx, int dy, int dz,
-                                         const long long *U, const long long *V, long long &det) {
-  const long long a[3] = {U[0] - P[0], U[1] - P[1], U[2] - P[2]};
-  const long long b[3] = {V[0] - P[0], V[1] - P[1], V[2] - P[2]};
-  const long long o = dx * (a[1] * b[2] - a[2] * b[1]) + dy * (a[2] * b[0] - a[0] * b[2]) +
-                      dz * (a[0] * b[1] - a[1] * b[0]);
+// by (eps, eps^2, eps^3), eps -> 0+):
+//  - plane side of node X: the sign of the first non-zero of (N.(X - A), N_x, N_y, N_z),
+//    N = (B - A) x (C - A);
+//  - side of the displaced link line P + t d about the edge U -> V: the sign of the first
+//    non-zero of (det[d, U - P, V - P], d x (V - U)).
+// The link crosses the triangle iff its ends lie on opposite sides of the plane and the
+// line on the same side of all three edges; its sign s is the plane side of the
+// destination.  In coordinates relative to a corner O of the triangle's candidate box,
+// (U - P) x (V - P) = U' x V' + (V - U) x P', so with P' = 2^20 p (p a small integer
+// vector) det = d.(U' x V') + 2^20 p.(d x (V - U)): per edge one cross product per
+// triangle and a few small multiply-adds per link.
+struct CutEdge {
+  long long K[3];  // U' x V' (below 2^51)
+  long long D[3];  // V - U (below 2^23 per axis)
+};
+
+// Side of the link (direction d, source offset p from O) about edge e; det receives the
+// undisplaced determinant (for the barycentric coordinates).
+__device__ __forceinline__ int cut_edge_side(const CutEdge &e, int dx, int dy, int dz, int px,
+                                             int py, int pz, long long &det) {
+  const long long c0 = dy * e.D[2] - dz * e.D[1];  // d x (V - U)
+  const long long c1 = dz * e.D[0] - dx * e.D[2];
+  const long long c2 = dx * e.D[1] - dy * e.D[0];
+  const long long o = (dx * e.K[0] + dy * e.K[1] + dz * e.K[2]) +
+                      ((px * c0 + py * c1 + pz * c2) << QBITS);
   det = o;
   if (o != 0) return o > 0 ? 1 : -1;
-  const long long e[3] = {V[0] - U[0], V[1] - U[1], V[2] - U[2]};
-  const long long w[3] = {e[1] * dz - e[2] * dy, e[2] * dx - e[0] * dz, e[0] * dy - e[1] * dx};
-  for (int k = 0; k < 3; k++)
-    if (w[k] != 0) return w[k] > 0 ? -1 : 1;
+  if (c0 != 0) return c0 > 0 ? 1 : -1;
+  if (c1 != 0) return c1 > 0 ? 1 : -1;
+  if (c2 != 0) return c2 > 0 ? 1 : -1;
   return 0;
 }
 
-// One warp per triangle: every candidate link (destinations in [ceil(min) - 1, ceil(max)]
-// per axis, 18 directions) tested; a crossing adds coef = s w_i / c_s^2 Fn(crossing), Fn
-// interpolated barycentrically over the triangle, to the streamed population in place
-// (INPLACE) or to the field J[i-1][node] (read-outs).
+// One warp per triangle.  The candidate destinations x span [ceil(min) - 1, ceil(max)] per
+// axis (the displaced link spans at most [x - 1 + eps, x + 1 + eps]); the warp tabulates
+// the plane side of every node of that box widened by one node (every source lies there,
+// N.(X - A) affine in the node's offset), then, a round of 32 destinations at a time,
+// marks the directions whose link ends straddle the plane, gathers those (node,
+// direction) candidates into a list, and tests them with all 32 lanes.  A crossing adds
+// coef = s w_i / c_s^2 Fn(crossing), Fn the barycentric mean of the vertices' Fn, to the
+// streamed population in place (INPLACE) or to the field J[i-1][node] (read-outs).
+constexpr int CUT_LIST = 32 * 18;  // candidates of one round at most
 template <bool INPLACE, typename S>
-__global__ void __launch_bounds__(128, 6)
+__global__ void __launch_bounds__(128, 4)
     k3_cut(const long long *__restrict__ Xq, const int *__restrict__ tri, int m,
            const S *__restrict__ Fn, const Geom3 g, int odd, S *__restrict__ A,
            double *__restrict__ J, int *__restrict__ count, int *__restrict__ status) {
-  // per warp: the plane sides of the widened candidate box; the per-axis edge bound below
-  // (< 8 lattice units) keeps the box within CUT_BOX^3 nodes
+  // per warp: the plane sides of the widened box (the per-axis edge bound below keeps it
+  // within CUT_BOX^3 nodes) and the round's candidate list
   __shared__ signed char cut_sides[4][CUT_BOX * CUT_BOX * CUT_BOX];
+  __shared__ unsigned cut_list[4][CUT_LIST];
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int wslot = threadIdx.x >> 5;
   if (t >= m) return;
   const int vi[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
   long long q[3][3];
@@ -675,10 +712,6 @@ __global__ void __launch_bounds__(128, 6)
     if (lane == 0) atomicOr(status, ST_INTERFACE);
     return;
   }
-  const long long u[3] = {q[1][0] - q[0][0], q[1][1] - q[0][1], q[1][2] - q[0][2]};
-  const long long v[3] = {q[2][0] - q[0][0], q[2][1] - q[0][1], q[2][2] - q[0][2]};
-  const long long N[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2],
-                          u[0] * v[1] - u[1] * v[0]};
   int lo[3], ext[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
@@ -687,18 +720,34 @@ __global__ void __launch_bounds__(128, 6)
     lo[a] = (int)(-((-mn) >> QBITS)) - 1;
     ext[a] = (int)(-((-mx) >> QBITS)) - lo[a] + 1;
   }
-  // the plane side of node X + delta: sign of N.(X - A), ties by the first non-zero of
-  // (N_x, N_y, N_z) (the same for every node); computed once per node of the candidate
-  // box widened by one node (every link's source lies there) into the warp's table
+  const long long Sx = 1LL << QBITS;
+  // vertices relative to the widened box's corner O = (lo - 1) 2^20
+  long long r[3][3];
+#pragma unroll
+  for (int j = 0; j < 3; j++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) r[j][a] = q[j][a] - (long long)(lo[a] - 1) * Sx;
+  const long long u[3] = {r[1][0] - r[0][0], r[1][1] - r[0][1], r[1][2] - r[0][2]};
+  const long long v[3] = {r[2][0] - r[0][0], r[2][1] - r[0][1], r[2][2] - r[0][2]};
+  const long long N[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2],
+                          u[0] * v[1] - u[1] * v[0]};
+  CutEdge E[3];
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    const long long *U = r[j], *V = r[(j + 1) % 3];
+    E[j].K[0] = U[1] * V[2] - U[2] * V[1];
+    E[j].K[1] = U[2] * V[0] - U[0] * V[2];
+    E[j].K[2] = U[0] * V[1] - U[1] * V[0];
+    E[j].D[0] = V[0] - U[0];
+    E[j].D[1] = V[1] - U[1];
+    E[j].D[2] = V[2] - U[2];
+  }
+  // plane sides: N.(X - A) at X = O + 2^20 (a, b, c) is r0 + 2^20 (a N_x + b N_y + c N_z)
   const int tie = N[0] ? (N[0] > 0 ? 1 : -1) : (N[1] ? (N[1] > 0 ? 1 : -1) : (N[2] > 0 ? 1 : -1));
   const int E0 = ext[0] + 2, E1 = ext[1] + 2, E2 = ext[2] + 2;
-  signed char *side = cut_sides[threadIdx.x >> 5];
-  const long long Sx = 1LL << QBITS;
-  // N.(X - A) is affine in the node's offset (a, b, c) from the widened box's corner X0:
-  // r0 + (a N_x + b N_y + c N_z) 2^20, the bracket below 2^56 in 64 bits
-  const __int128 r0 = (__int128)N[0] * ((long long)(lo[0] - 1) * Sx - q[0][0]) +
-                      (__int128)N[1] * ((long long)(lo[1] - 1) * Sx - q[0][1]) +
-                      (__int128)N[2] * ((long long)(lo[2] - 1) * Sx - q[0][2]);
+  signed char *side = cut_sides[wslot];
+  unsigned *list = cut_list[wslot];
+  const __int128 r0 = -((__int128)N[0] * r[0][0] + (__int128)N[1] * r[0][1] + (__int128)N[2] * r[0][2]);
   // box index -> (a, b, c) by FP32 quotients: (k + 1/2) / E is at least 1/(2E) from an
   // integer (E <= 12, k < 1728), far beyond the quotient's rounding error
   const float iE0 = 1.0f / (float)E0, iE01 = 1.0f / (float)(E0 * E1);
@@ -706,53 +755,76 @@ __global__ void __launch_bounds__(128, 6)
     const int cz = (int)(((float)c + 0.5f) * iE01), rem = c - cz * E0 * E1;
     const int b = (int)(((float)rem + 0.5f) * iE0), a = rem - b * E0;
     const long long L = a * N[0] + b * N[1] + cz * N[2];
-    const __int128 r = r0 + ((__int128)L << QBITS);
-    side[c] = (signed char)(r > 0 ? 1 : (r < 0 ? -1 : tie));
+    const __int128 rr = r0 + ((__int128)L << QBITS);
+    side[c] = (signed char)(rr > 0 ? 1 : (rr < 0 ? -1 : tie));
   }
   __syncwarp();
   int found = 0;
-  // lanes over the destinations: the directions whose link ends lie on opposite sides of
-  // the plane (two table reads each, constant offsets) form a mask; only those get the
-  // three edge tests
   const int nn = ext[0] * ext[1] * ext[2];
   const float iX = 1.0f / (float)ext[0], iXY = 1.0f / (float)(ext[0] * ext[1]);
-  for (int cidx = lane; cidx < nn; cidx += 32) {
-    const int gz = (int)(((float)cidx + 0.5f) * iXY), rem = cidx - gz * ext[0] * ext[1];
-    const int gy = (int)(((float)rem + 0.5f) * iX), gx = rem - gy * ext[0];
-    const int base = (gx + 1) + E0 * ((gy + 1) + E1 * (gz + 1));
-    const int sQ = side[base];
+  for (int base0 = 0; base0 < nn; base0 += 32) {
+    // this round's destinations: one per lane, its straddling directions as a mask
+    const int cidx = base0 + lane;
     unsigned mask = 0u;
-    static_for<1, 19>([&](auto ic) {
-      constexpr int i = decltype(ic)::value;
-      const int off = ex(i) + E0 * (ey(i) + E1 * ez(i));
-      if (side[base - off] != sQ) mask |= 1u << i;
-    });
-    const int x = lo[0] + gx, y = lo[1] + gy, z = lo[2] + gz;
+    int a = 0, b = 0, cz = 0;
+    if (cidx < nn) {
+      cz = (int)(((float)cidx + 0.5f) * iXY);
+      const int rem = cidx - cz * ext[0] * ext[1];
+      b = (int)(((float)rem + 0.5f) * iX);
+      a = rem - b * ext[0];
+      a++, b++, cz++;  // offsets in the widened box
+      const int base = a + E0 * (b + E1 * cz);
+      const int sQ = side[base];
+      static_for<1, 19>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const int off = ex(i) + E0 * (ey(i) + E1 * ez(i));
+        if (side[base - off] != sQ) mask |= 1u << i;
+      });
+    }
+    // gather: (a, b, c, i) packed, each lane's candidates at its prefix position
+    const int cnt = __popc(mask);
+    int pre = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int vv = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= o) pre += vv;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    int slot = pre - cnt;
     while (mask) {
       const int i = __ffs(mask) - 1;
       mask &= mask - 1u;
+      list[slot++] = (unsigned)i | ((unsigned)a << 5) | ((unsigned)b << 9) | ((unsigned)cz << 13);
+    }
+    __syncwarp();
+    for (int j = lane; j < total; j += 32) {
+      const unsigned e = list[j];
+      const int i = (int)(e & 31u), qa = (int)((e >> 5) & 15u), qb = (int)((e >> 9) & 15u);
+      const int qc = (int)((e >> 13) & 15u);
       const int dx = exr(i), dy = eyr(i), dz = ezr(i);
-      const long long P[3] = {(long long)(x - dx) * Sx, (long long)(y - dy) * Sx,
-                              (long long)(z - dz) * Sx};
+      const int px = qa - dx, py = qb - dy, pz = qc - dz;  // the link's source, from O
       long long vAB, vBC, vCA;
-      const int e1 = edge_side(P, dx, dy, dz, q[0], q[1], vAB);
-      const int e2 = edge_side(P, dx, dy, dz, q[1], q[2], vBC);
-      const int e3 = edge_side(P, dx, dy, dz, q[2], q[0], vCA);
+      const int e1 = cut_edge_side(E[0], dx, dy, dz, px, py, pz, vAB);
+      const int e2 = cut_edge_side(E[1], dx, dy, dz, px, py, pz, vBC);
+      const int e3 = cut_edge_side(E[2], dx, dy, dz, px, py, pz, vCA);
       if (e1 == 0 || e1 != e2 || e2 != e3) continue;
+      const int sQ = side[qa + E0 * (qb + E1 * qc)];
       // Fn at the crossing: the barycentric mean of the vertices' Fn (one division), in the
       // arithmetic type (GB300's FP64 pipe would make this the kernel's cost in FP32 runs)
       const S sum = S(vAB) + S(vBC) + S(vCA);
       const S fc = (S(vBC) * Fn[vi[0]] + S(vCA) * Fn[vi[1]] + S(vAB) * Fn[vi[2]]) / sum;
       const S coef = S(sQ) * (S(3) * wt<S>(i)) * fc;
+      const int x = lo[0] - 1 + qa, y = lo[1] - 1 + qb, z = lo[2] - 1 + qc;
       const int xw = (unsigned)x < (unsigned)g.nx ? x : wrapfull(x, g.nx);
       const int yw = (unsigned)y < (unsigned)g.ny ? y : wrapfull(y, g.ny);
       const int zw = (unsigned)z < (unsigned)g.nz ? z : wrapfull(z, g.nz);
       if constexpr (INPLACE)
-        atomicAdd(&A[aa_read(g, odd != 0, i, xw, yw, zw)], S(coef));
+        atomicAdd(&A[aa_read(g, odd != 0, i, xw, yw, zw)], coef);
       else
         atomicAdd(&J[(long long)(i - 1) * g.plane + nodeix(g, xw, yw, zw)], (double)coef);
       found++;
     }
+    __syncwarp();
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) found += __shfl_xor_sync(0xffffffffu, found, o);

@@ -32,7 +32,7 @@ extern "C" {
 typedef struct iilbm3d_lattice *iilbm3d_t;
 
 typedef struct {
-  int32_t nx, ny, nz;   /* lattice nodes, each 4 <= n <= 2048; nx * ny * nz <= 2^31 */
+  int32_t nx, ny, nz;   /* lattice nodes, each 4 <= n <= 2048; nx * ny * nz < 2^31 */
   int32_t collision;    /* IILBM_SRT or IILBM_MRT (d'Humieres D3Q19 basis, section 2.2.1) */
   int32_t storage;      /* IILBM_F64 or IILBM_F32 (the arithmetic follows the storage) */
   int32_t jump;         /* 1: II-LBM (the normal force through the jump of Eq. 32 on

@@ -424,19 +424,50 @@ namespace iilbm3d {
 // One node: AA-pattern load of its streamed populations, collision, in-place store.
 // FORCED: the spread force of the node (cleared for the next step) plus the body force;
 // RECORD: the collision's velocity is kept for the interpolation.
-template <typename T>
-__device__ __forceinline__ void sc_load(const T *__restrict__ A, const Geom3 &g, int odd, int x,
-                                        int y, int z, T f[19]) {
+// The AA-pattern locations of one node (ODD: the level's parity, a compile-time constant
+// of the kernel): at even levels the node's own index plus i planes; at odd levels the
+// opposite slot at node (x - ex, y - ey, z - ez), from the three wrapped coordinates per
+// axis kept once per thread.  Node indices are below 2^31 (the lattice's limit) and are
+// formed in 32 bits.
+struct NodeLoc {
+  int c;                    // even levels: the node's index
+  int xs[3], ys[3], zs[3];  // odd levels: x - d, y - d, z - d wrapped, index d + 1
+};
+template <bool ODD>
+__device__ __forceinline__ void node_loc(const Geom3 &g, int x, int y, int z, NodeLoc &L) {
+  if constexpr (!ODD) {
+    L.c = (z * g.ny + y) * g.nx + x;
+  } else {
+    L.xs[0] = wrapn(x + 1, g.nx), L.xs[1] = x, L.xs[2] = wrapn(x - 1, g.nx);
+    L.ys[0] = wrapn(y + 1, g.ny), L.ys[1] = y, L.ys[2] = wrapn(y - 1, g.ny);
+    L.zs[0] = wrapn(z + 1, g.nz), L.zs[1] = z, L.zs[2] = wrapn(z - 1, g.nz);
+  }
+}
+// Location of the streamed f_I of the node (compile-time direction I).
+template <int I, bool ODD>
+__device__ __forceinline__ long long loc_of(const Geom3 &g, const NodeLoc &L) {
+  if constexpr (!ODD) {
+    return I * g.plane + L.c;
+  } else {
+    constexpr int X = ex(I), Y = ey(I), Z = ez(I);
+    const int node = (L.zs[Z + 1] * g.ny + L.ys[Y + 1]) * g.nx + L.xs[X + 1];
+    return opp(I) * g.plane + node;
+  }
+}
+
+template <typename T, bool ODD>
+__device__ __forceinline__ void sc_load(const T *__restrict__ A, const Geom3 &g,
+                                        const NodeLoc &L, T f[19]) {
   static_for<0, 19>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
-    f[i] = A[aa_read_c<i>(g, odd, x, y, z)];
+    f[i] = A[loc_of<i, ODD>(g, L)];
   });
 }
 
 // Collision and in-place store of one node whose streamed populations are in f.
-template <typename T, bool MRT, bool SIMPLE, bool FORCED, bool RECORD>
-__device__ __forceinline__ void sc_finish(T *__restrict__ A, const Geom3 &g, int odd,
-                                          const Coll3<T> &p, int x, int y, int z, T f[19],
+template <typename T, bool ODD, bool MRT, bool SIMPLE, bool FORCED, bool RECORD>
+__device__ __forceinline__ void sc_finish(T *__restrict__ A, const Geom3 &g, const Coll3<T> &p,
+                                          const NodeLoc &L, long long c, T f[19],
                                           T *__restrict__ gf, T *__restrict__ uf,
                                           int *__restrict__ status) {
   T ux, uy, uz, drho;
@@ -444,32 +475,42 @@ __device__ __forceinline__ void sc_finish(T *__restrict__ A, const Geom3 &g, int
     T gx = p.body[0], gy = p.body[1], gz = p.body[2];
     if constexpr (RECORD) {
       T sx, sy, sz;
-      Vec3<T>::take(gf, g.plane, nodeix(g, x, y, z), sx, sy, sz);
+      Vec3<T>::take(gf, g.plane, c, sx, sy, sz);
       gx += sx;
       gy += sy;
       gz += sz;
     }
     drho = collide3<T, MRT, true, SIMPLE>(f, gx, gy, gz, p, ux, uy, uz);
-    if constexpr (RECORD) Vec3<T>::put(uf, g.plane, nodeix(g, x, y, z), ux, uy, uz);
+    if constexpr (RECORD) Vec3<T>::put(uf, g.plane, c, ux, uy, uz);
   } else {
     drho = collide3<T, MRT, false, SIMPLE>(f, T(0), T(0), T(0), p, ux, uy, uz);
   }
-  if (!(fabs((double)drho) < 1e30)) atomicOr(status, ST_NONFINITE);
+  if (!(fabs(drho) < T(1e30))) atomicOr(status, ST_NONFINITE);  // also NaN
   // post-collision f_i goes where the streamed f_opp(i) was read (in place)
   static_for<0, 19>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
-    A[aa_read_c<opp(i)>(g, odd, x, y, z)] = f[i];
+    A[loc_of<opp(i), ODD>(g, L)] = f[i];
   });
 }
 
-template <typename T, bool MRT, bool SIMPLE, bool FORCED, bool RECORD>
-__device__ __forceinline__ void sc_node(T *__restrict__ A, const Geom3 &g, int odd,
-                                        const Coll3<T> &p, int x, int y, int z,
-                                        T *__restrict__ gf, T *__restrict__ uf,
-                                        int *__restrict__ status) {
+template <typename T, bool ODD, bool MRT, bool SIMPLE, bool FORCED, bool RECORD>
+__device__ __forceinline__ void sc_node(T *__restrict__ A, const Geom3 &g, const Coll3<T> &p,
+                                        int x, int y, int z, T *__restrict__ gf,
+                                        T *__restrict__ uf, int *__restrict__ status) {
   T f[19];
-  sc_load<T>(A, g, odd, x, y, z, f);
-  sc_finish<T, MRT, SIMPLE, FORCED, RECORD>(A, g, odd, p, x, y, z, f, gf, uf, status);
+  {
+    NodeLoc L;
+    node_loc<ODD>(g, x, y, z, L);
+    sc_load<T, ODD>(A, g, L, f);
+  }
+  // the stores' locations are formed again from coordinates the compiler cannot see
+  // through, so it does not keep nineteen addresses live across the collision
+  int xo = x, yo = y, zo = z;
+  if constexpr (!RECORD) asm volatile("" : "+r"(xo), "+r"(yo), "+r"(zo));  // the lean kernel
+  NodeLoc L;
+  node_loc<ODD>(g, xo, yo, zo, L);
+  sc_finish<T, ODD, MRT, SIMPLE, FORCED, RECORD>(A, g, p, L, nodeix(g, xo, yo, zo), f, gf, uf,
+                                                 status);
 }
 
 // Tile (blockIdx.x, blockIdx.y, z) = nodes [32 blockIdx.x, +32) x [4 blockIdx.y, +4) of
@@ -477,20 +518,20 @@ __device__ __forceinline__ void sc_node(T *__restrict__ A, const Geom3 &g, int o
 // there is one); the forced kernel takes the flagged tiles from the vertex pass's list.
 // AA-pattern locations belong to one node each per step, so the two kernels' node sets
 // touch disjoint memory.
-template <typename T, bool MRT, bool SIMPLE, bool BODY>
-__global__ void __launch_bounds__(TB, sizeof(T) == 4 ? 10 : 4)
-    k3_sc_lean(T *__restrict__ A, const Geom3 g, int odd, const Coll3<T> p,
+template <typename T, bool ODD, bool MRT, bool SIMPLE, bool BODY>
+__global__ void __launch_bounds__(TB, sizeof(T) == 4 ? 8 : 4)
+    k3_sc_lean(T *__restrict__ A, const Geom3 g, const Coll3<T> p,
                const unsigned *__restrict__ flags, int *__restrict__ status) {
   const int x = blockIdx.x * TX + (threadIdx.x & (TX - 1));
   const int y = blockIdx.y * TY + (threadIdx.x / TX), z = blockIdx.z;
   if (flags[((long long)z * g.nty + blockIdx.y) * g.ntx + blockIdx.x] != 0u) return;  // whole block
   if (x >= g.nx || y >= g.ny) return;
-  sc_node<T, MRT, SIMPLE, BODY, false>(A, g, odd, p, x, y, z, nullptr, nullptr, status);
+  sc_node<T, ODD, MRT, SIMPLE, BODY, false>(A, g, p, x, y, z, nullptr, nullptr, status);
 }
 
-template <typename T, bool MRT, bool SIMPLE>
-__global__ void __launch_bounds__(TB)
-    k3_sc_forced(T *__restrict__ A, const Geom3 g, int odd, const Coll3<T> p,
+template <typename T, bool ODD, bool MRT, bool SIMPLE>
+__global__ void __launch_bounds__(TB, sizeof(T) == 4 ? 4 : 2)
+    k3_sc_forced(T *__restrict__ A, const Geom3 g, const Coll3<T> p,
                  unsigned *__restrict__ flags, const int *__restrict__ tile_list,
                  const int *__restrict__ tile_count, T *__restrict__ gf, T *__restrict__ uf,
                  int *__restrict__ status) {
@@ -501,7 +542,7 @@ __global__ void __launch_bounds__(TB)
     const int ty = rest % g.nty, z = rest / g.nty;
     const int x = tx * TX + (threadIdx.x & (TX - 1)), y = ty * TY + (threadIdx.x / TX);
     if (x < g.nx && y < g.ny)
-      sc_node<T, MRT, SIMPLE, true, true>(A, g, odd, p, x, y, z, gf, uf, status);
+      sc_node<T, ODD, MRT, SIMPLE, true, true>(A, g, p, x, y, z, gf, uf, status);
     if (threadIdx.x == 0) flags[tile] = 0u;  // the lean kernel has finished reading it
   }
 }
@@ -648,18 +689,19 @@ __global__ void __launch_bounds__(128)
 // triangle and a few small multiply-adds per link.
 struct CutEdge {
   long long K[3];  // U' x V' (below 2^51)
-  long long D[3];  // V - U (below 2^23 per axis)
+  int D[3];        // V - U (below 2^23 per axis)
 };
 
 // Side of the link (direction d, source offset p from O) about edge e; det receives the
 // undisplaced determinant (for the barycentric coordinates).
 __device__ __forceinline__ int cut_edge_side(const CutEdge &e, int dx, int dy, int dz, int px,
                                              int py, int pz, long long &det) {
-  const long long c0 = dy * e.D[2] - dz * e.D[1];  // d x (V - U)
-  const long long c1 = dz * e.D[0] - dx * e.D[2];
-  const long long c2 = dx * e.D[1] - dy * e.D[0];
+  const int c0 = dy * e.D[2] - dz * e.D[1];  // d x (V - U), below 2^24
+  const int c1 = dz * e.D[0] - dx * e.D[2];
+  const int c2 = dx * e.D[1] - dy * e.D[0];
+  // p (below 12 per axis) . (d x (V - U)): below 2^30
   const long long o = (dx * e.K[0] + dy * e.K[1] + dz * e.K[2]) +
-                      ((px * c0 + py * c1 + pz * c2) << QBITS);
+                      ((long long)(px * c0 + py * c1 + pz * c2) << QBITS);
   det = o;
   if (o != 0) return o > 0 ? 1 : -1;
   if (c0 != 0) return c0 > 0 ? 1 : -1;
@@ -678,7 +720,7 @@ __device__ __forceinline__ int cut_edge_side(const CutEdge &e, int dx, int dy, i
 // streamed population in place (INPLACE) or to the field J[i-1][node] (read-outs).
 constexpr int CUT_LIST = 32 * 18;  // candidates of one round at most
 template <bool INPLACE, typename S>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, 5)
     k3_cut(const long long *__restrict__ Xq, const int *__restrict__ tri, int m,
            const S *__restrict__ Fn, const Geom3 g, int odd, S *__restrict__ A,
            double *__restrict__ J, int *__restrict__ count, int *__restrict__ status) {
@@ -738,9 +780,9 @@ __global__ void __launch_bounds__(128, 4)
     E[j].K[0] = U[1] * V[2] - U[2] * V[1];
     E[j].K[1] = U[2] * V[0] - U[0] * V[2];
     E[j].K[2] = U[0] * V[1] - U[1] * V[0];
-    E[j].D[0] = V[0] - U[0];
-    E[j].D[1] = V[1] - U[1];
-    E[j].D[2] = V[2] - U[2];
+    E[j].D[0] = (int)(V[0] - U[0]);
+    E[j].D[1] = (int)(V[1] - U[1]);
+    E[j].D[2] = (int)(V[2] - U[2]);
   }
   // plane sides: N.(X - A) at X = O + 2^20 (a, b, c) is r0 + 2^20 (a N_x + b N_y + c N_z)
   const int tie = N[0] ? (N[0] > 0 ? 1 : -1) : (N[1] ? (N[1] > 0 ? 1 : -1) : (N[2] > 0 ? 1 : -1));
@@ -977,23 +1019,28 @@ Coll3<S> coll_params(const H *h) {
 
 bool has_body(const H *h) { return h->cfg.body[0] != 0.0 || h->cfg.body[1] != 0.0 || h->cfg.body[2] != 0.0; }
 
-template <typename S, bool MRT, bool SIMPLE>
-void launch_sc_t(H *h, cudaStream_t s) {
+template <typename S, bool ODD, bool MRT, bool SIMPLE>
+void launch_sc_p(H *h, cudaStream_t s) {
   const Geom3 &g = h->geo;
   const dim3 grid(g.ntx, g.nty, g.nz);
   const Coll3<S> p = coll_params<S>(h);
-  const int odd = (int)(h->step & 1);
   if (has_body(h))
-    k3_sc_lean<S, MRT, SIMPLE, true><<<grid, TB, 0, s>>>((S *)h->A, g, odd, p, h->flags, h->d_status);
+    k3_sc_lean<S, ODD, MRT, SIMPLE, true><<<grid, TB, 0, s>>>((S *)h->A, g, p, h->flags, h->d_status);
   else
-    k3_sc_lean<S, MRT, SIMPLE, false><<<grid, TB, 0, s>>>((S *)h->A, g, odd, p, h->flags, h->d_status);
+    k3_sc_lean<S, ODD, MRT, SIMPLE, false><<<grid, TB, 0, s>>>((S *)h->A, g, p, h->flags, h->d_status);
   if (h->n > 0) {
     const long long ntiles = (long long)g.ntx * g.nty * g.nz;
     const unsigned blocks = (unsigned)std::min<long long>(ntiles, 152LL * 16);
-    k3_sc_forced<S, MRT, SIMPLE><<<blocks, TB, 0, s>>>((S *)h->A, g, odd, p, h->flags,
-                                                        h->tile_list, h->tile_count,
-                                                        (S *)h->gf, (S *)h->uf, h->d_status);
+    k3_sc_forced<S, ODD, MRT, SIMPLE><<<blocks, TB, 0, s>>>((S *)h->A, g, p, h->flags,
+                                                             h->tile_list, h->tile_count,
+                                                             (S *)h->gf, (S *)h->uf, h->d_status);
   }
+}
+
+template <typename S, bool MRT, bool SIMPLE>
+void launch_sc_t(H *h, cudaStream_t s) {
+  if (h->step & 1) launch_sc_p<S, true, MRT, SIMPLE>(h, s);
+  else launch_sc_p<S, false, MRT, SIMPLE>(h, s);
 }
 
 template <typename S>
@@ -1168,7 +1215,7 @@ int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
   const int lim[3] = {c.nx, c.ny, c.nz};
   for (int a = 0; a < 3; a++)
     if (lim[a] < 4 || lim[a] > 2048) return IILBM_ERR_INVALID_ARG;
-  if ((long long)c.nx * c.ny * c.nz > (1LL << 31)) return IILBM_ERR_INVALID_ARG;
+  if ((long long)c.nx * c.ny * c.nz >= (1LL << 31)) return IILBM_ERR_INVALID_ARG;
   if (c.collision != IILBM_SRT && c.collision != IILBM_MRT) return IILBM_ERR_INVALID_ARG;
   if (c.storage != IILBM_F64 && c.storage != IILBM_F32) return IILBM_ERR_INVALID_ARG;
   if ((c.jump != 0 && c.jump != 1) || (c.force != IILBM_FORCE_GUO && c.force != IILBM_FORCE_SIMPLE))

@@ -113,6 +113,12 @@ def workload(size, storage):
 # coefficients 10, back-transform 36; a division counts as one flop).
 FP64_PEAK_TFLOPS = round(152 * 2 * 2 * 2.07e9 / 1e12, 4)
 FP64_MRT_FLOPS_PER_NODE = 126
+# The D3Q19 MRT collision without force, per node, as the pair-symmetric form computes
+# it: pair sums and differences 18, density and momentum 24, density, reciprocal,
+# velocity and the equilibrium's base 13, the nine pairs' equilibrium terms 96, the
+# moments (83 terms, 27 of them with a non-unit coefficient, and the rates and norms of
+# 15 rows) 140, the back-transform and the pairs' reassembly 147.
+D3Q19_MRT_FLOPS_PER_NODE = 438
 
 
 def max_over_ranks(values, dist, device="cuda"):
@@ -1036,6 +1042,18 @@ def run_membrane3d(args):
         d = json.load(open(tr)).get(f"membrane3d_{n}_{args.storage}")
         if d:
             roofline["traffic"] = d
+    if args.storage == "f64":
+        # FP64 arithmetic is bound by GB300's FP64 pipe, not by HBM: the roof is the FP64
+        # rate, the work the D3Q19 MRT collision's algorithmic flops per node (counted
+        # from the pair-symmetric collision without force; the forced tiles are a few %)
+        flops = D3Q19_MRT_FLOPS_PER_NODE * cells
+        hbm = {("hbm_" + k): roofline[k] for k in ("achieved", "peak", "frac")}
+        roofline.update({"bound": "alu", "achieved": round(flops / sc_avg / 1e12, 4),
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": round(flops / sc_avg / 1e12 / FP64_PEAK_TFLOPS, 4),
+                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x "
+                                        "2.07 GHz (nominal FP64 rate of GB300)",
+                         "flops_per_node": D3Q19_MRT_FLOPS_PER_NODE, **hbm})
     del g
     e2e = None
     if not args.no_e2e:

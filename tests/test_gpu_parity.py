@@ -273,9 +273,10 @@ def test_precision_report(orc):
     """The ellipse membrane (MRT, tau 0.6) scaled to 256^2, 1000 steps, in every storage
     precision against one FP64 oracle run: relative L2 and L-infinity velocity errors and
     the enclosed-area loss (printed; run with -s).  Bars: FP64 within 1e-10 (the
-    conditioning floor of a long membrane run is ~1e-12), FP32 within 1e-5.  The 16-bit
-    storages are reported: FP16 holds 1e-3 to about 300 steps (tested above) and reaches
-    ~2.5e-3 here; BF16 (8-bit mantissa) ~1e-2."""
+    conditioning floor of a long membrane run is ~1e-12), FP32 within 1e-5.  FP16 storage:
+    relative L2 within 1e-3 over the 1000 steps (measured 4.5e-4); its L-infinity error
+    reaches 2.5e-3 - 2.6e-3 here (1e-3 holds to about 300 steps, tested above), bounded at
+    3e-3.  BF16 (8-bit mantissa): L2 within 1e-2, L-infinity within 2e-2."""
     steps = 1000
     w = W.ellipse_scaled(256, "f64")
     o = orc.Oracle(256, 256, collision=orc.MRT, tau=w["tau"], s=W.mrt_rates(w["tau"]))
@@ -303,4 +304,5 @@ def test_precision_report(orc):
               f"(oracle {ao:.3e})")
     assert rows["f64"][1] < 1e-10 and abs(rows["f64"][2] - ao) < 1e-10
     assert rows["f32"][1] < 1e-5
-    assert rows["f16"][1] < 1e-2 and rows["bf16"][1] < 1e-1
+    assert rows["f16"][0] < 1e-3 and rows["f16"][1] < 3e-3
+    assert rows["bf16"][0] < 1e-2 and rows["bf16"][1] < 2e-2

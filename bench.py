@@ -36,7 +36,7 @@ reports its end-to-end MLUPS and force passes per step next to the plain iterati
 periodic MRT box (tau 0.6, d'Humieres rates of section 2.2.1) holding a surface-tension
 ellipsoid (semi-axes 0.31, 0.25, 0.22 of the box, a seeded rotation, 40 962 vertices, edges
 about one lattice unit) whose vertices move with the fluid; FP32 populations (--storage f64
-runs FP64).  One step: vertex forces and normal split, the jump on every cut link of the
+runs FP64; f16 / bf16 store 16-bit populations with FP32 arithmetic).  One step: vertex forces and normal split, the jump on every cut link of the
 triangulation, tangential spreading, the stream-collide, interpolation and the vertex
 update.  --size3 sets the box's side.
 
@@ -938,7 +938,7 @@ def run_channel(args):
 
 # ------------------------------------------------------- three dimensions
 def membrane3d_config(args, w):
-    sb = 8 if args.storage == "f64" else 4
+    sb = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[args.storage]
     n = w["n"]
     return {"workload": f"membrane3d_{n}^3_tension_ellipsoid", "lattice": [n, n, n],
             "vertices": len(w["X"]), "triangles": len(w["T"]), "collision": "mrt (d'Humieres D3Q19)",
@@ -978,9 +978,7 @@ def run_membrane3d(args):
     w = W.membrane_3d(args.size3)
     n = w["n"]
     cells = n ** 3
-    sb = 8 if args.storage == "f64" else 4
-    if args.storage not in ("f32", "f64"):
-        raise SystemExit("membrane3d stores FP32 or FP64 populations")
+    sb = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[args.storage]
 
     def lattice():
         g = iilbm3d.Lattice3D(n, n, n, collision=iilbm3d.MRT, storage=args.storage, tau=w["tau"],

@@ -34,11 +34,13 @@ typedef struct iilbm3d_lattice *iilbm3d_t;
 typedef struct {
   int32_t nx, ny, nz;   /* lattice nodes, each 4 <= n <= 2048; nx * ny * nz < 2^31 */
   int32_t collision;    /* IILBM_SRT or IILBM_MRT (d'Humieres D3Q19 basis, section 2.2.1) */
-  int32_t storage;      /* IILBM_F64 or IILBM_F32 (the arithmetic follows the storage) */
+  int32_t storage;      /* IILBM_F64 / F32 / F16 / BF16: the populations' storage; the
+                           arithmetic is FP64 for F64 and FP32 for the others */
   int32_t jump;         /* 1: II-LBM (the normal force through the jump of Eq. 32 on
                            every cut link, the tangential part spread); 0: IB-LBM */
   int32_t force;        /* IILBM_FORCE_GUO (Eqs. 21-22) or IILBM_FORCE_SIMPLE (Eq. 16) */
-  int32_t reserved;     /* 0 */
+  int32_t storage_scale_log2; /* F16 / BF16: stored value = df * 2^k (exact), |k| <= 24;
+                           0 for F32 / F64 */
   double tau;           /* relaxation time lambda, nu = (lambda - 1/2) / 3; > 0.5 */
   double s[19];         /* MRT rates in the d'Humieres moment order (rho, e, eps, j_x, q_x,
                            j_y, q_y, j_z, q_z, 3p_xx, 3pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz,

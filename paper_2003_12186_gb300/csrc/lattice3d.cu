@@ -21,6 +21,8 @@
 //                    surface.
 // Between steps the stored populations carry no jump: the jump of the next step's
 // surface is added at the start of that step.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -227,8 +229,47 @@ struct Vec3<double> {
   }
 };
 
+// Storage of the populations: FP64 and FP32 as the arithmetic type, FP16 and BF16 with FP32
+// arithmetic.  FP16 values are kept times 2^k (the lattice's scale; exact), so the small
+// shifted deviations sit in its normal range; ld / st convert, add adds in storage units.
+template <typename S>
+struct St3;
+template <>
+struct St3<double> {
+  using T = double;
+  static constexpr bool SCALED = false;
+  __device__ static double ld(double v) { return v; }
+  __device__ static double st(double v) { return v; }
+  __device__ static void add(double *a, double v) { atomicAdd(a, v); }
+};
+template <>
+struct St3<float> {
+  using T = float;
+  static constexpr bool SCALED = false;
+  __device__ static float ld(float v) { return v; }
+  __device__ static float st(float v) { return v; }
+  __device__ static void add(float *a, float v) { atomicAdd(a, v); }
+};
+template <>
+struct St3<__half> {
+  using T = float;
+  static constexpr bool SCALED = true;
+  __device__ static float ld(__half v) { return __half2float(v); }
+  __device__ static __half st(float v) { return __float2half_rn(v); }
+  __device__ static void add(__half *a, float v) { atomicAdd(a, __float2half_rn(v)); }
+};
+template <>
+struct St3<__nv_bfloat16> {
+  using T = float;
+  static constexpr bool SCALED = true;
+  __device__ static float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ static __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+  __device__ static void add(__nv_bfloat16 *a, float v) { atomicAdd(a, __float2bfloat16_rn(v)); }
+};
+
 template <typename T>
 struct Coll3 {
+  T scale, inv_scale;  // stored value = population x scale (2^k; 1 unless 16-bit storage)
   T omega;     // SRT: 1 / lambda
   T s[19];     // MRT rates (conserved moments' unused)
   T rho0;
@@ -389,8 +430,10 @@ struct iilbm3d_lattice {
   int device;
   cudaStream_t stream;
   bool own_stream;
-  bool f64;           // storage (and arithmetic) FP64, else FP32
-  void *A;            // [19][plane] populations
+  bool f64;           // arithmetic FP64 (FP64 storage), else FP32
+  int storage;        // IILBM_F64 / F32 / F16 / BF16
+  double scale;       // stored population = df x scale (16-bit storage: 2^k; else 1)
+  void *A;            // [19][plane] populations in the storage type
   void *gf;           // spread force (arithmetic type; Vec3 layout), zero outside flagged tiles
   void *uf;           // collision velocity on flagged tiles (Vec3 layout)
   unsigned *flags;    // [ntiles] tile carries a spread force / marker support
@@ -455,18 +498,20 @@ __device__ __forceinline__ long long loc_of(const Geom3 &g, const NodeLoc &L) {
   }
 }
 
-template <typename T, bool ODD>
-__device__ __forceinline__ void sc_load(const T *__restrict__ A, const Geom3 &g,
-                                        const NodeLoc &L, T f[19]) {
+template <typename S, bool ODD, typename T = typename St3<S>::T>
+__device__ __forceinline__ void sc_load(const S *__restrict__ A, const Geom3 &g,
+                                        const NodeLoc &L, T f[19], T inv_scale) {
   static_for<0, 19>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
-    f[i] = A[loc_of<i, ODD>(g, L)];
+    f[i] = St3<S>::ld(A[loc_of<i, ODD>(g, L)]);
+    if constexpr (St3<S>::SCALED) f[i] *= inv_scale;
   });
 }
 
 // Collision and in-place store of one node whose streamed populations are in f.
-template <typename T, bool ODD, bool MRT, bool SIMPLE, bool FORCED, bool RECORD>
-__device__ __forceinline__ void sc_finish(T *__restrict__ A, const Geom3 &g, const Coll3<T> &p,
+template <typename S, bool ODD, bool MRT, bool SIMPLE, bool FORCED, bool RECORD,
+          typename T = typename St3<S>::T>
+__device__ __forceinline__ void sc_finish(S *__restrict__ A, const Geom3 &g, const Coll3<T> &p,
                                           const NodeLoc &L, long long c, T f[19],
                                           T *__restrict__ gf, T *__restrict__ uf,
                                           int *__restrict__ status) {
@@ -489,19 +534,20 @@ __device__ __forceinline__ void sc_finish(T *__restrict__ A, const Geom3 &g, con
   // post-collision f_i goes where the streamed f_opp(i) was read (in place)
   static_for<0, 19>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
-    A[loc_of<opp(i), ODD>(g, L)] = f[i];
+    A[loc_of<opp(i), ODD>(g, L)] = St3<S>::st(St3<S>::SCALED ? f[i] * p.scale : f[i]);
   });
 }
 
-template <typename T, bool ODD, bool MRT, bool SIMPLE, bool FORCED, bool RECORD>
-__device__ __forceinline__ void sc_node(T *__restrict__ A, const Geom3 &g, const Coll3<T> &p,
+template <typename S, bool ODD, bool MRT, bool SIMPLE, bool FORCED, bool RECORD,
+          typename T = typename St3<S>::T>
+__device__ __forceinline__ void sc_node(S *__restrict__ A, const Geom3 &g, const Coll3<T> &p,
                                         int x, int y, int z, T *__restrict__ gf,
                                         T *__restrict__ uf, int *__restrict__ status) {
   T f[19];
   {
     NodeLoc L;
     node_loc<ODD>(g, x, y, z, L);
-    sc_load<T, ODD>(A, g, L, f);
+    sc_load<S, ODD>(A, g, L, f, p.inv_scale);
   }
   // the stores' locations are formed again from coordinates the compiler cannot see
   // through, so it does not keep nineteen addresses live across the collision
@@ -509,7 +555,7 @@ __device__ __forceinline__ void sc_node(T *__restrict__ A, const Geom3 &g, const
   if constexpr (!RECORD) asm volatile("" : "+r"(xo), "+r"(yo), "+r"(zo));  // the lean kernel
   NodeLoc L;
   node_loc<ODD>(g, xo, yo, zo, L);
-  sc_finish<T, ODD, MRT, SIMPLE, FORCED, RECORD>(A, g, p, L, nodeix(g, xo, yo, zo), f, gf, uf,
+  sc_finish<S, ODD, MRT, SIMPLE, FORCED, RECORD>(A, g, p, L, nodeix(g, xo, yo, zo), f, gf, uf,
                                                  status);
 }
 
@@ -518,20 +564,21 @@ __device__ __forceinline__ void sc_node(T *__restrict__ A, const Geom3 &g, const
 // there is one); the forced kernel takes the flagged tiles from the vertex pass's list.
 // AA-pattern locations belong to one node each per step, so the two kernels' node sets
 // touch disjoint memory.
-template <typename T, bool ODD, bool MRT, bool SIMPLE, bool BODY>
+template <typename S, bool ODD, bool MRT, bool SIMPLE, bool BODY,
+          typename T = typename St3<S>::T>
 __global__ void __launch_bounds__(TB, sizeof(T) == 4 ? 8 : 4)
-    k3_sc_lean(T *__restrict__ A, const Geom3 g, const Coll3<T> p,
+    k3_sc_lean(S *__restrict__ A, const Geom3 g, const Coll3<T> p,
                const unsigned *__restrict__ flags, int *__restrict__ status) {
   const int x = blockIdx.x * TX + (threadIdx.x & (TX - 1));
   const int y = blockIdx.y * TY + (threadIdx.x / TX), z = blockIdx.z;
   if (flags[((long long)z * g.nty + blockIdx.y) * g.ntx + blockIdx.x] != 0u) return;  // whole block
   if (x >= g.nx || y >= g.ny) return;
-  sc_node<T, ODD, MRT, SIMPLE, BODY, false>(A, g, p, x, y, z, nullptr, nullptr, status);
+  sc_node<S, ODD, MRT, SIMPLE, BODY, false, T>(A, g, p, x, y, z, nullptr, nullptr, status);
 }
 
-template <typename T, bool ODD, bool MRT, bool SIMPLE>
+template <typename S, bool ODD, bool MRT, bool SIMPLE, typename T = typename St3<S>::T>
 __global__ void __launch_bounds__(TB, sizeof(T) == 4 ? 4 : 2)
-    k3_sc_forced(T *__restrict__ A, const Geom3 g, const Coll3<T> p,
+    k3_sc_forced(S *__restrict__ A, const Geom3 g, const Coll3<T> p,
                  unsigned *__restrict__ flags, const int *__restrict__ tile_list,
                  const int *__restrict__ tile_count, T *__restrict__ gf, T *__restrict__ uf,
                  int *__restrict__ status) {
@@ -542,7 +589,7 @@ __global__ void __launch_bounds__(TB, sizeof(T) == 4 ? 4 : 2)
     const int ty = rest % g.nty, z = rest / g.nty;
     const int x = tx * TX + (threadIdx.x & (TX - 1)), y = ty * TY + (threadIdx.x / TX);
     if (x < g.nx && y < g.ny)
-      sc_node<T, ODD, MRT, SIMPLE, true, true>(A, g, p, x, y, z, gf, uf, status);
+      sc_node<S, ODD, MRT, SIMPLE, true, true>(A, g, p, x, y, z, gf, uf, status);
     if (threadIdx.x == 0) flags[tile] = 0u;  // the lean kernel has finished reading it
   }
 }
@@ -717,12 +764,13 @@ __device__ __forceinline__ int cut_edge_side(const CutEdge &e, int dx, int dy, i
 // marks the directions whose link ends straddle the plane, gathers those (node,
 // direction) candidates into a list, and tests them with all 32 lanes.  A crossing adds
 // coef = s w_i / c_s^2 Fn(crossing), Fn the barycentric mean of the vertices' Fn, to the
-// streamed population in place (INPLACE) or to the field J[i-1][node] (read-outs).
+// streamed population in place (INPLACE; times the storage scale) or to the field
+// J[i-1][node] (read-outs).  S is the storage type, T the arithmetic type.
 constexpr int CUT_LIST = 32 * 18;  // candidates of one round at most
-template <bool INPLACE, typename S>
+template <bool INPLACE, typename S, typename T = typename St3<S>::T>
 __global__ void __launch_bounds__(128, 5)
     k3_cut(const long long *__restrict__ Xq, const int *__restrict__ tri, int m,
-           const S *__restrict__ Fn, const Geom3 g, int odd, S *__restrict__ A,
+           const T *__restrict__ Fn, const Geom3 g, int odd, S *__restrict__ A, T scale,
            double *__restrict__ J, int *__restrict__ count, int *__restrict__ status) {
   // per warp: the plane sides of the widened box (the per-axis edge bound below keeps it
   // within CUT_BOX^3 nodes) and the round's candidate list
@@ -853,15 +901,15 @@ __global__ void __launch_bounds__(128, 5)
       const int sQ = side[qa + E0 * (qb + E1 * qc)];
       // Fn at the crossing: the barycentric mean of the vertices' Fn (one division), in the
       // arithmetic type (GB300's FP64 pipe would make this the kernel's cost in FP32 runs)
-      const S sum = S(vAB) + S(vBC) + S(vCA);
-      const S fc = (S(vBC) * Fn[vi[0]] + S(vCA) * Fn[vi[1]] + S(vAB) * Fn[vi[2]]) / sum;
-      const S coef = S(sQ) * (S(3) * wt<S>(i)) * fc;
+      const T sum = T(vAB) + T(vBC) + T(vCA);
+      const T fc = (T(vBC) * Fn[vi[0]] + T(vCA) * Fn[vi[1]] + T(vAB) * Fn[vi[2]]) / sum;
+      const T coef = T(sQ) * (T(3) * wt<T>(i)) * fc;
       const int x = lo[0] - 1 + qa, y = lo[1] - 1 + qb, z = lo[2] - 1 + qc;
       const int xw = (unsigned)x < (unsigned)g.nx ? x : wrapfull(x, g.nx);
       const int yw = (unsigned)y < (unsigned)g.ny ? y : wrapfull(y, g.ny);
       const int zw = (unsigned)z < (unsigned)g.nz ? z : wrapfull(z, g.nz);
       if constexpr (INPLACE)
-        atomicAdd(&A[aa_read(g, odd != 0, i, xw, yw, zw)], coef);
+        St3<S>::add(&A[aa_read(g, odd != 0, i, xw, yw, zw)], St3<S>::SCALED ? coef * scale : coef);
       else
         atomicAdd(&J[(long long)(i - 1) * g.plane + nodeix(g, xw, yw, zw)], (double)coef);
       found++;
@@ -921,41 +969,54 @@ __global__ void __launch_bounds__(128)
 }
 
 // ------------------------------------------------------------- conversions, read-out
-// FP64 natural layout df[i][node] <-> the stored populations at the current AA parity.
+// FP64 natural layout df[i][node] <-> the stored populations at the current AA parity
+// (stored = df x scale, rounded once to the storage type).
 template <typename S>
-__global__ void k3_store(S *__restrict__ A, const double *__restrict__ df, const Geom3 g, int odd) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.plane) return;
-  const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
-  for (int i = 0; i < 19; i++) A[aa_read(g, odd != 0, i, x, y, z)] = S(df[i * g.plane + c]);
+__device__ __forceinline__ S to_store(double v, double scale) {
+  return St3<S>::st((typename St3<S>::T)(v * scale));
 }
 template <typename S>
-__global__ void k3_load(const S *__restrict__ A, double *__restrict__ df, const Geom3 g, int odd) {
+__device__ __forceinline__ double from_store(S v, double inv_scale) {
+  return (double)St3<S>::ld(v) * inv_scale;
+}
+template <typename S>
+__global__ void k3_store(S *__restrict__ A, const double *__restrict__ df, const Geom3 g, int odd,
+                         double scale) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.plane) return;
   const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
-  for (int i = 0; i < 19; i++) df[i * g.plane + c] = (double)A[aa_read(g, odd != 0, i, x, y, z)];
+  for (int i = 0; i < 19; i++)
+    A[aa_read(g, odd != 0, i, x, y, z)] = to_store<S>(df[i * g.plane + c], scale);
+}
+template <typename S>
+__global__ void k3_load(const S *__restrict__ A, double *__restrict__ df, const Geom3 g, int odd,
+                        double inv_scale) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.plane) return;
+  const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
+  for (int i = 0; i < 19; i++)
+    df[i * g.plane + c] = from_store<S>(A[aa_read(g, odd != 0, i, x, y, z)], inv_scale);
 }
 // drho and u (Eq. 24) from the stored populations plus the jump field J (may be null) and
 // the spread force plus the body force; h = 1/2 (Guo) or 0 (simple force term).
-template <typename S>
-__global__ void k3_macros(const S *__restrict__ A, const double *__restrict__ J,
-                          const S *__restrict__ gf, const Geom3 g, int odd, double rho0,
+template <typename S, typename T = typename St3<S>::T>
+__global__ void k3_macros(const S *__restrict__ A, double inv_scale, const double *__restrict__ J,
+                          const T *__restrict__ gf, const Geom3 g, int odd, double rho0,
                           double bx, double by, double bz, double h, double *__restrict__ out) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.plane) return;
   const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
   double s = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
   for (int i = 0; i < 19; i++) {
-    double f = (double)A[aa_read(g, odd != 0, i, x, y, z)];
+    double f = from_store<S>(A[aa_read(g, odd != 0, i, x, y, z)], inv_scale);
     if (J && i > 0) f += J[(long long)(i - 1) * g.plane + c];
     s += f;
     jx += ex(i) * f;
     jy += ey(i) * f;
     jz += ez(i) * f;
   }
-  S sx, sy, sz;
-  Vec3<S>::get(gf, g.plane, c, sx, sy, sz);
+  T sx, sy, sz;
+  Vec3<T>::get(gf, g.plane, c, sx, sy, sz);
   const double gx = bx + (double)sx, gy = by + (double)sy, gz = bz + (double)sz;
   out[c] = s;
   out[g.plane + c] = (jx + h * gx) / (rho0 + s);
@@ -968,7 +1029,7 @@ __global__ void k3_macros(const S *__restrict__ A, const double *__restrict__ J,
 namespace iilbm3d {
 
 template <typename S>
-__global__ void k3_equilibrium(S *__restrict__ A, const Geom3 g, int odd, double rho0,
+__global__ void k3_equilibrium(S *__restrict__ A, const Geom3 g, int odd, double rho0, double scale,
                                const double *__restrict__ drho, const double *__restrict__ ux,
                                const double *__restrict__ uy, const double *__restrict__ uz) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -980,7 +1041,7 @@ __global__ void k3_equilibrium(S *__restrict__ A, const Geom3 g, int odd, double
   for (int i = 0; i < 19; i++) {
     const double eu = ex(i) * u0 + ey(i) * u1 + ez(i) * u2;
     const double poly = eu * 3.0 + eu * eu * 4.5 - uu * 1.5;
-    A[aa_read(g, odd != 0, i, x, y, z)] = S(wt<double>(i) * (d + rho * poly));
+    A[aa_read(g, odd != 0, i, x, y, z)] = to_store<S>(wt<double>(i) * (d + rho * poly), scale);
   }
 }
 
@@ -1007,23 +1068,37 @@ using H = iilbm3d_lattice;
 
 unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-template <typename S>
-Coll3<S> coll_params(const H *h) {
-  Coll3<S> p;
-  p.omega = S(1.0 / h->cfg.tau);
-  for (int r = 0; r < 19; r++) p.s[r] = S(h->cfg.s[r]);
-  p.rho0 = S(h->cfg.rho0);
-  for (int d = 0; d < 3; d++) p.body[d] = S(h->cfg.body[d]);
+template <typename T>
+Coll3<T> coll_params(const H *h) {
+  Coll3<T> p;
+  p.scale = T(h->scale);
+  p.inv_scale = T(1.0 / h->scale);
+  p.omega = T(1.0 / h->cfg.tau);
+  for (int r = 0; r < 19; r++) p.s[r] = T(h->cfg.s[r]);
+  p.rho0 = T(h->cfg.rho0);
+  for (int d = 0; d < 3; d++) p.body[d] = T(h->cfg.body[d]);
   return p;
+}
+
+// f(S{}) with S the lattice's storage type.
+template <typename F>
+void with_storage(const H *h, F &&f) {
+  switch (h->storage) {
+    case IILBM_F64: f(double{}); break;
+    case IILBM_F32: f(float{}); break;
+    case IILBM_F16: f(__half{}); break;
+    default: f(__nv_bfloat16{}); break;
+  }
 }
 
 bool has_body(const H *h) { return h->cfg.body[0] != 0.0 || h->cfg.body[1] != 0.0 || h->cfg.body[2] != 0.0; }
 
 template <typename S, bool ODD, bool MRT, bool SIMPLE>
 void launch_sc_p(H *h, cudaStream_t s) {
+  using T = typename St3<S>::T;
   const Geom3 &g = h->geo;
   const dim3 grid(g.ntx, g.nty, g.nz);
-  const Coll3<S> p = coll_params<S>(h);
+  const Coll3<T> p = coll_params<T>(h);
   if (has_body(h))
     k3_sc_lean<S, ODD, MRT, SIMPLE, true><<<grid, TB, 0, s>>>((S *)h->A, g, p, h->flags, h->d_status);
   else
@@ -1033,7 +1108,7 @@ void launch_sc_p(H *h, cudaStream_t s) {
     const unsigned blocks = (unsigned)std::min<long long>(ntiles, 152LL * 16);
     k3_sc_forced<S, ODD, MRT, SIMPLE><<<blocks, TB, 0, s>>>((S *)h->A, g, p, h->flags,
                                                              h->tile_list, h->tile_count,
-                                                             (S *)h->gf, (S *)h->uf, h->d_status);
+                                                             (T *)h->gf, (T *)h->uf, h->d_status);
   }
 }
 
@@ -1053,8 +1128,7 @@ void launch_sc_s(H *h, cudaStream_t s) {
 }
 
 void launch_sc(H *h) {
-  if (h->f64) launch_sc_s<double>(h, h->stream);
-  else launch_sc_s<float>(h, h->stream);
+  with_storage(h, [&](auto tag) { launch_sc_s<decltype(tag)>(h, h->stream); });
 }
 
 void launch_vertex(H *h) {
@@ -1079,20 +1153,22 @@ void launch_cut(H *h, double *J) {
   const unsigned b = blocks_for((long long)h->m * 32, 128);
   const int odd = (int)(h->step & 1);
   if (J) {
+    // read-out: the field only (the populations are not touched)
     if (h->f64)
-      k3_cut<false, double><<<b, 128, 0, h->stream>>>(h->Xq, h->tri, h->m, (double *)h->Fnt, h->geo, odd,
-                                                      (double *)h->A, J, h->d_count, h->d_status);
+      k3_cut<false, double><<<b, 128, 0, h->stream>>>(h->Xq, h->tri, h->m, (double *)h->Fnt, h->geo,
+                                                      odd, nullptr, 1.0, J, h->d_count, h->d_status);
     else
-      k3_cut<false, float><<<b, 128, 0, h->stream>>>(h->Xq, h->tri, h->m, (float *)h->Fnt, h->geo, odd,
-                                                     (float *)h->A, J, h->d_count, h->d_status);
-  } else {
-    if (h->f64)
-      k3_cut<true, double><<<b, 128, 0, h->stream>>>(h->Xq, h->tri, h->m, (double *)h->Fnt, h->geo, odd,
-                                                     (double *)h->A, nullptr, h->d_count, h->d_status);
-    else
-      k3_cut<true, float><<<b, 128, 0, h->stream>>>(h->Xq, h->tri, h->m, (float *)h->Fnt, h->geo, odd,
-                                                    (float *)h->A, nullptr, h->d_count, h->d_status);
+      k3_cut<false, float><<<b, 128, 0, h->stream>>>(h->Xq, h->tri, h->m, (float *)h->Fnt, h->geo,
+                                                     odd, nullptr, 1.0f, J, h->d_count, h->d_status);
+    return;
   }
+  with_storage(h, [&](auto tag) {
+    using S = decltype(tag);
+    using T = typename St3<S>::T;
+    k3_cut<true, S><<<b, 128, 0, h->stream>>>(h->Xq, h->tri, h->m, (const T *)h->Fnt, h->geo, odd,
+                                             (S *)h->A, T(h->scale), nullptr, h->d_count,
+                                             h->d_status);
+  });
 }
 
 void launch_interp(H *h) {
@@ -1217,7 +1293,10 @@ int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
     if (lim[a] < 4 || lim[a] > 2048) return IILBM_ERR_INVALID_ARG;
   if ((long long)c.nx * c.ny * c.nz >= (1LL << 31)) return IILBM_ERR_INVALID_ARG;
   if (c.collision != IILBM_SRT && c.collision != IILBM_MRT) return IILBM_ERR_INVALID_ARG;
-  if (c.storage != IILBM_F64 && c.storage != IILBM_F32) return IILBM_ERR_INVALID_ARG;
+  if (c.storage < IILBM_F64 || c.storage > IILBM_BF16) return IILBM_ERR_INVALID_ARG;
+  const bool half = c.storage == IILBM_F16 || c.storage == IILBM_BF16;
+  if (half ? (c.storage_scale_log2 < -24 || c.storage_scale_log2 > 24) : c.storage_scale_log2 != 0)
+    return IILBM_ERR_INVALID_ARG;
   if ((c.jump != 0 && c.jump != 1) || (c.force != IILBM_FORCE_GUO && c.force != IILBM_FORCE_SIMPLE))
     return IILBM_ERR_INVALID_ARG;
   if (!(c.tau > 0.5 && c.tau < 1e6) || !(c.rho0 > 0.0 && std::isfinite(c.rho0)))
@@ -1241,6 +1320,8 @@ int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
   h->cfg = c;
   h->device = dev;
   h->f64 = c.storage == IILBM_F64;
+  h->storage = c.storage;
+  h->scale = std::ldexp(1.0, c.storage_scale_log2);
   Geom3 &g = h->geo;
   g.nx = c.nx;
   g.ny = c.ny;
@@ -1248,7 +1329,8 @@ int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
   g.ntx = (c.nx + TX - 1) / TX;
   g.nty = (c.ny + TY - 1) / TY;
   g.plane = (long long)c.nx * c.ny * c.nz;
-  const size_t sb = h->f64 ? 8 : 4;
+  const size_t sb = h->f64 ? 8 : 4;                      // arithmetic type
+  const size_t sa = c.storage == IILBM_F64 ? 8 : (half ? 2 : 4);  // storage type
   const size_t ntiles = (size_t)g.ntx * g.nty * c.nz;
   bool ok = true;
   if (c.stream) {
@@ -1257,7 +1339,7 @@ int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
     ok = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) == cudaSuccess;
     h->own_stream = ok;
   }
-  ok = ok && cudaMalloc(&h->A, 19 * g.plane * sb) == cudaSuccess &&
+  ok = ok && cudaMalloc(&h->A, 19 * g.plane * sa) == cudaSuccess &&
        cudaMalloc(&h->gf, 4 * g.plane * sb) == cudaSuccess &&
        cudaMalloc(&h->uf, 4 * g.plane * sb) == cudaSuccess &&
        cudaMalloc(&h->flags, ntiles * sizeof(unsigned)) == cudaSuccess &&
@@ -1265,7 +1347,7 @@ int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
        cudaMalloc(&h->tile_count, sizeof(int)) == cudaSuccess &&
        cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
        cudaMalloc(&h->d_count, sizeof(int)) == cudaSuccess;
-  ok = ok && cudaMemsetAsync(h->A, 0, 19 * g.plane * sb, h->stream) == cudaSuccess &&
+  ok = ok && cudaMemsetAsync(h->A, 0, 19 * g.plane * sa, h->stream) == cudaSuccess &&
        cudaMemsetAsync(h->gf, 0, 4 * g.plane * sb, h->stream) == cudaSuccess &&
        cudaMemsetAsync(h->uf, 0, 4 * g.plane * sb, h->stream) == cudaSuccess &&
        cudaMemsetAsync(h->flags, 0, ntiles * sizeof(unsigned), h->stream) == cudaSuccess &&
@@ -1407,12 +1489,11 @@ int iilbm3d_init_equilibrium(iilbm3d_t h, const double *drho, const double *ux, 
   for (int q = 0; q < 4 && !rc; q++) rc = to_device(src[q], (size_t)N, h->stream, &d[q]);
   if (!rc) {
     const unsigned b = blocks_for(N, 256);
-    if (h->f64)
-      k3_equilibrium<double><<<b, 256, 0, h->stream>>>((double *)h->A, h->geo, (int)(h->step & 1),
-                                                       h->cfg.rho0, d[0], d[1], d[2], d[3]);
-    else
-      k3_equilibrium<float><<<b, 256, 0, h->stream>>>((float *)h->A, h->geo, (int)(h->step & 1),
-                                                      h->cfg.rho0, d[0], d[1], d[2], d[3]);
+    with_storage(h, [&](auto tag) {
+      using S = decltype(tag);
+      k3_equilibrium<S><<<b, 256, 0, h->stream>>>((S *)h->A, h->geo, (int)(h->step & 1), h->cfg.rho0,
+                                                   h->scale, d[0], d[1], d[2], d[3]);
+    });
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) rc = IILBM_ERR_CUDA;
   }
   for (double *q : d)
@@ -1427,8 +1508,10 @@ int iilbm3d_set_populations(iilbm3d_t h, const double *df) {
   int rc = to_device(df, 19 * (size_t)h->geo.plane, h->stream, &d);
   if (rc) return rc;
   const unsigned b = blocks_for(h->geo.plane, 256);
-  if (h->f64) k3_store<double><<<b, 256, 0, h->stream>>>((double *)h->A, d, h->geo, (int)(h->step & 1));
-  else k3_store<float><<<b, 256, 0, h->stream>>>((float *)h->A, d, h->geo, (int)(h->step & 1));
+  with_storage(h, [&](auto tag) {
+    using S = decltype(tag);
+    k3_store<S><<<b, 256, 0, h->stream>>>((S *)h->A, d, h->geo, (int)(h->step & 1), h->scale);
+  });
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) rc = IILBM_ERR_CUDA;
   cudaFree(d);
   return rc;
@@ -1443,8 +1526,11 @@ int iilbm3d_get_populations(iilbm3d_t h, double *df) {
     return IILBM_ERR_OOM;
   }
   const unsigned b = blocks_for(h->geo.plane, 256);
-  if (h->f64) k3_load<double><<<b, 256, 0, h->stream>>>((const double *)h->A, d, h->geo, (int)(h->step & 1));
-  else k3_load<float><<<b, 256, 0, h->stream>>>((const float *)h->A, d, h->geo, (int)(h->step & 1));
+  with_storage(h, [&](auto tag) {
+    using S = decltype(tag);
+    k3_load<S><<<b, 256, 0, h->stream>>>((const S *)h->A, d, h->geo, (int)(h->step & 1),
+                                         1.0 / h->scale);
+  });
   int rc = IILBM_OK;
   if (cudaGetLastError() != cudaSuccess ||
       cudaMemcpyAsync(df, d, cnt * sizeof(double), cudaMemcpyDefault, h->stream) != cudaSuccess ||
@@ -1510,14 +1596,13 @@ int iilbm3d_get_macros(iilbm3d_t h, double *drho, double *ux, double *uy, double
   if (!rc) {
     const double hh = h->cfg.force == IILBM_FORCE_SIMPLE ? 0.0 : 0.5;
     const unsigned b = blocks_for((long long)N, 256);
-    if (h->f64)
-      k3_macros<double><<<b, 256, 0, h->stream>>>((const double *)h->A, J, (const double *)h->gf,
-                                                  h->geo, (int)(h->step & 1), h->cfg.rho0,
-                                                  h->cfg.body[0], h->cfg.body[1], h->cfg.body[2], hh, out);
-    else
-      k3_macros<float><<<b, 256, 0, h->stream>>>((const float *)h->A, J, (const float *)h->gf,
-                                                 h->geo, (int)(h->step & 1), h->cfg.rho0,
-                                                 h->cfg.body[0], h->cfg.body[1], h->cfg.body[2], hh, out);
+    with_storage(h, [&](auto tag) {
+      using S = decltype(tag);
+      using T = typename St3<S>::T;
+      k3_macros<S><<<b, 256, 0, h->stream>>>((const S *)h->A, 1.0 / h->scale, J, (const T *)h->gf,
+                                             h->geo, (int)(h->step & 1), h->cfg.rho0, h->cfg.body[0],
+                                             h->cfg.body[1], h->cfg.body[2], hh, out);
+    });
     double *dst[4] = {drho, ux, uy, uz};
     if (cudaGetLastError() != cudaSuccess) rc = IILBM_ERR_CUDA;
     for (int q = 0; q < 4 && !rc; q++)

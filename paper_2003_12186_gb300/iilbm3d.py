@@ -11,8 +11,12 @@ import ctypes as C
 import numpy as np
 
 from . import iilbm
-from .iilbm import (F32, F64, FORCE_GUO, FORCE_SIMPLE, MRT, SRT, STORAGE, IilbmError,  # noqa: F401
-                    _check, _current_device, _ptr)
+from .iilbm import (BF16, F16, F32, F64, FORCE_GUO, FORCE_SIMPLE, MRT, SRT, STORAGE,  # noqa: F401
+                    IilbmError, _check, _current_device, _ptr)
+
+# stored value = df * 2^k for 16-bit storage: FP16 keeps the small shifted deviations in
+# its normal range; BF16 has FP32's exponent range
+DEFAULT_SCALE_LOG2 = {F64: 0, F32: 0, F16: 12, BF16: 0}
 
 PRESCRIBED, TENSION = 0, 1
 
@@ -20,7 +24,7 @@ PRESCRIBED, TENSION = 0, 1
 class iilbm3d_config(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("collision", C.c_int32), ("storage", C.c_int32), ("jump", C.c_int32),
-                ("force", C.c_int32), ("reserved", C.c_int32), ("tau", C.c_double),
+                ("force", C.c_int32), ("storage_scale_log2", C.c_int32), ("tau", C.c_double),
                 ("s", C.c_double * 19), ("rho0", C.c_double), ("body", C.c_double * 3),
                 ("stream", C.c_void_p)]
 
@@ -81,13 +85,16 @@ class Lattice3D:
     """One D3Q19 II-LBM lattice (handle of iilbm3d_create)."""
 
     def __init__(self, nx, ny, nz, collision=MRT, storage=F32, tau=0.8, s=None, rho0=1.0,
-                 jump=1, force=FORCE_GUO, body=(0.0, 0.0, 0.0), stream=None):
+                 jump=1, force=FORCE_GUO, body=(0.0, 0.0, 0.0), stream=None,
+                 storage_scale_log2=None):
         L = load()
         c = iilbm3d_config()
         c.nx, c.ny, c.nz = nx, ny, nz
         c.collision = collision
         c.storage = STORAGE[storage] if isinstance(storage, str) else storage
-        c.jump, c.force, c.reserved = jump, force, 0
+        c.jump, c.force = jump, force
+        c.storage_scale_log2 = (DEFAULT_SCALE_LOG2.get(c.storage, 0) if storage_scale_log2 is None
+                                else storage_scale_log2)
         c.tau, c.rho0 = tau, rho0
         rates = s if s is not None else paper_rates(tau)
         for r in range(19):

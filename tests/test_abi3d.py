@@ -43,8 +43,9 @@ def _cfg(**kw):
 
 def test_invalid_configs_rejected_before_device_use():
     L = iilbm3d.load()
-    for bad in (dict(nx=2), dict(nz=4096), dict(tau=0.5), dict(storage=2), dict(collision=3),
-                dict(jump=2), dict(force=5), dict(rho0=0.0)):
+    for bad in (dict(nx=2), dict(nz=4096), dict(tau=0.5), dict(storage=4), dict(storage=-1),
+                dict(collision=3), dict(jump=2), dict(force=5), dict(rho0=0.0),
+                dict(storage_scale_log2=3), dict(storage=iilbm3d.F16, storage_scale_log2=25)):
         h = C.c_void_p()
         assert L.iilbm3d_create(C.byref(h), C.byref(_cfg(**bad))) == -1, bad
         assert not h.value

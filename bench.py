@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
     ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--tma", type=int, default=0, choices=[0, 1, 2],
+                    help="FP32 lean stream-collide of interior tiles by bulk tensor copies: "
+                         "0 never (default), 1 every step, 2 odd steps only")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-hbm-check", action="store_true",
@@ -374,9 +377,11 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- GPU arm
-def make_lattice(iilbm, w, stream):
+def make_lattice(iilbm, w, stream, tma=0):
     g = iilbm.Lattice(w["nx"], w["ny"], collision=iilbm.MRT, storage=w["storage"],
                       tau=w["tau"], s=W.mrt_rates(w["tau"]), stream=stream)
+    if tma:
+        g.set_option(iilbm.OPT_TMA_KERNEL, tma)
     return g
 
 
@@ -400,7 +405,7 @@ def run_ours(args):
     sbytes = iilbm.STORAGE_BYTES[iilbm.STORAGE[args.storage]]
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    g = make_lattice(iilbm, w, stream)
+    g = make_lattice(iilbm, w, stream, args.tma)
     g.set_interface(w["X"], model=iilbm.SPRING, stiffness=w["kappa"], dX=w["dX"])
     g.step(args.warmup)  # the first call captures the step graphs
     g.synchronize()
@@ -452,7 +457,9 @@ def run_ours(args):
     achieved = alg_bytes / sc_avg_s / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "k_stream_collide_vec (lean)", "peak_source": peak_kind,
+                "kernel": ("k_stream_collide_tma + k_stream_collide_vec_edge (lean, TMA "
+                           f"mode {args.tma})" if args.tma else "k_stream_collide_vec (lean)"),
+                "peak_source": peak_kind,
                 "flagged_tiles_per_step": round(tiles / max(sc_n, 1), 1),
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_us": round(sc_avg_s * 1e6, 2),
                 "timed_in": "second timed region of the same steps with per-launch CUDA "
@@ -491,7 +498,7 @@ def run_ours(args):
         del g
         torch.cuda.synchronize()
         w4 = workload(4096, args.storage)
-        g4 = make_lattice(iilbm, w4, stream)
+        g4 = make_lattice(iilbm, w4, stream, args.tma)
         g4.set_interface(w4["X"], model=iilbm.SPRING, stiffness=w4["kappa"], dX=w4["dX"])
         g4.step(max(args.warmup, 8))
         K4 = 256
@@ -523,7 +530,7 @@ def run_ours(args):
         if "g" in locals():
             del g
         torch.cuda.synchronize()
-        g2 = make_lattice(iilbm, w, stream)
+        g2 = make_lattice(iilbm, w, stream, args.tma)
         nm = len(w["X"])
         Xin = torch.from_numpy(np.ascontiguousarray(w["X"])).pin_memory()
         Xout = torch.empty((nm, 2), dtype=torch.float64).pin_memory()

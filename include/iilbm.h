@@ -245,7 +245,7 @@ int iilbm_set_timing(iilbm_t h, int32_t enable);
 int iilbm_get_timing(iilbm_t h, double *stream_collide_ms, int32_t *stream_collide_launches,
                      int64_t *kernel_launches, int64_t *flagged_tiles);
 
-/* Execution options (all on by default; for A/B measurements and tests):
+/* Execution options (on by default but the TMA kernel; for A/B measurements and tests):
  *  IILBM_OPT_CUDA_GRAPH     replay steps from captured CUDA graphs (iilbm_step);
  *  IILBM_OPT_OVERLAP        run the forced stream-collide, then the interpolation
  *                           fused with the next step's interface phase (one kernel),
@@ -253,6 +253,12 @@ int iilbm_get_timing(iilbm_t h, double *stream_collide_ms, int32_t *stream_colli
  *                           stream-collide runs (direct forcing: the forced
  *                           stream-collide and the interpolation only);
  *  IILBM_OPT_VECTOR_KERNEL  vectorised stream-collide (else one node per thread);
+ *  IILBM_OPT_TMA_KERNEL     FP32 storage: the lean stream-collide of interior tiles moves
+ *                           its populations with bulk tensor copies through shared
+ *                           memory (the other tiles keep the vectorised kernel);
+ *                           value 1 every step, 2 odd steps only, 0 never (the default:
+ *                           on GB300 it runs as fast as the vectorised kernel alone and
+ *                           slower beside the side stream's kernels);
  *  IILBM_OPT_FORCED_BLOCKS  blocks of the forced stream-collide, which stride over the
  *                           flagged tiles (value > 0; 0 restores the default, two per
  *                           SM): fewer blocks hold fewer of the SMs' registers while the
@@ -260,7 +266,7 @@ int iilbm_get_timing(iilbm_t h, double *stream_collide_ms, int32_t *stream_colli
  * Results agree either way up to the order of floating-point atomic additions.
  * Synchronises the handle's stream. */
 enum { IILBM_OPT_CUDA_GRAPH = 0, IILBM_OPT_OVERLAP = 1, IILBM_OPT_VECTOR_KERNEL = 2,
-       IILBM_OPT_FORCED_BLOCKS = 3 };
+       IILBM_OPT_FORCED_BLOCKS = 3, IILBM_OPT_TMA_KERNEL = 4 };
 int iilbm_set_option(iilbm_t h, int32_t option, int32_t value);
 
 /* No-allocation read-out (the paper has no counterpart; this is a service of the

@@ -17,7 +17,7 @@ LIB = os.path.join(OUT_DIR, "libiilbm.so")
 SOURCES = ["lattice.cu", "interface.cu", "forcing.cu", "batch.cu", "mlp.cu", "api.cu",
            "lattice3d.cu"]
 HEADERS = ["iilbm_internal.cuh", "lattice_dev.cuh", "interface_dev.cuh", "forcing_dev.cuh",
-           "mlp_dev.cuh", "spline_dev.cuh",
+           "mlp_dev.cuh", "spline_dev.cuh", "sc_tma_dev.cuh",
            os.path.join("..", "..", "include", "iilbm.h"),
            os.path.join("..", "..", "include", "iilbm3d.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

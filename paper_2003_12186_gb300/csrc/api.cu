@@ -224,6 +224,8 @@ int iilbm_create_lattice(iilbm_t *out, const iilbm_config *cfg) {
     h->own_stream = true;
   }
   h->vector_sc = true;
+  h->tma_sc = 0;
+  h->tmap_A = nullptr;
   h->overlap = true;
   h->use_graph = true;
   h->forced_grid = std::max(1, std::min(h->ntiles, 2 * prop.multiProcessorCount));
@@ -444,12 +446,13 @@ int iilbm_get_populations(iilbm_t h, double *df) {
 
 namespace {
 
-// Kernels launched by one step: lean stream-collide; with an interface also the
+// Kernels launched by one step: lean stream-collide (two launches with the TMA kernel:
+// interior and edge tiles); with an interface also the
 // forced stream-collide and the interpolation fused with the next interface phase
 // (pipelined), or the interpolation, the interface kernel and, for direct forcing, the
 // force iteration; a channel adds its boundary kernel.
-long long kernels_per_step(const iilbm_lattice *h) {
-  long long k = 1 + (h->cfg.bc == IILBM_BC_CHANNEL || h->cfg.bc == IILBM_BC_BOX_OUTFLOW ||
+long long kernels_per_step(const iilbm_lattice *h, bool odd) {
+  long long k = (uses_tma_sc(h, odd) ? 2 : 1) + (h->cfg.bc == IILBM_BC_CHANNEL || h->cfg.bc == IILBM_BC_BOX_OUTFLOW ||
                              h->cfg.bc == IILBM_BC_BOX_WALL
                          ? 1
                          : 0);
@@ -457,6 +460,13 @@ long long kernels_per_step(const iilbm_lattice *h) {
     k += pipelined(h) ? 2
                       : 3 + (h->ip.model == IILBM_DIRECT ? 1 : 0) + (h->ip.curve > 0 ? 3 : 0) +
                             (h->body ? 1 : 0);
+  return k;
+}
+
+// Kernels launched by the len steps from time level step0.
+long long kernels_over(const iilbm_lattice *h, long long step0, int len) {
+  long long k = 0;
+  for (int q = 0; q < len; q++) k += kernels_per_step(h, ((step0 + q) & 1) != 0);
   return k;
 }
 
@@ -607,7 +617,7 @@ int iilbm_step(iilbm_t h, int32_t n) {
         h->ring_pending[k][r] = true;
         h->ring_next[k] = (r + 1) % GRAPH_RING;
         h->sc_launches += len;
-        h->kernel_launches += len * kernels_per_step(h);
+        h->kernel_launches += kernels_over(h, h->step - len, len);
       }
       continue;
     }
@@ -617,11 +627,12 @@ int iilbm_step(iilbm_t h, int32_t n) {
       if (h->nev == EAGER_PAIRS && (rc = drain_events(h))) return rc;
       slot = EAGER_EV0 + 2 * h->nev;
     }
+    const long long step0 = h->step;
     if ((rc = one_step(h, slot))) return rc;
     if (h->timing) {
       h->nev++;
       h->sc_launches++;
-      h->kernel_launches += kernels_per_step(h);
+      h->kernel_launches += kernels_over(h, step0, 1);
     }
     n--;
   }
@@ -636,6 +647,10 @@ int iilbm_set_option(iilbm_t h, int32_t option, int32_t value) {
     case IILBM_OPT_CUDA_GRAPH: h->use_graph = value != 0; break;
     case IILBM_OPT_OVERLAP: h->overlap = value != 0; break;
     case IILBM_OPT_VECTOR_KERNEL: h->vector_sc = value != 0; break;
+    case IILBM_OPT_TMA_KERNEL:
+      if (value < 0 || value > 2) return IILBM_ERR_INVALID_ARG;
+      h->tma_sc = value;
+      break;
     case IILBM_OPT_FORCED_BLOCKS: {
       if (value < 0) return IILBM_ERR_INVALID_ARG;
       cudaDeviceProp prop;

@@ -2,6 +2,7 @@
 // units of the II-LBM library (lattice constants, storage conversions, handle).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -191,6 +192,10 @@ struct iilbm_lattice {
   int forced_grid;    // blocks of the forced stream-collide (strides over the list)
   // execution
   bool vector_sc;     // vectorised stream-collide when nx is a multiple of its width
+  int tma_sc;         // FP32: interior tiles by the TMA stream-collide (sc_tma_dev.cuh):
+                      // 0 never, 1 every step, 2 odd steps only
+  const void *tmap_A; // the population array the tensor maps below describe
+  CUtensorMap tmap[3];  // boxes 136 x 8, 128 x 8, 124 x 8 of [9][ny][pitch]
   bool overlap;       // next interface phase on the side stream during stream-collide
   bool use_graph;     // replay steps from CUDA graphs (GRAPH_KINDS lengths)
   cudaStream_t side;
@@ -257,6 +262,7 @@ inline bool pipelined(const iilbm_lattice *h) {
 }
 
 int launch_stream_collide(iilbm_lattice *h, cudaStream_t forced_stream);
+bool uses_tma_sc(const iilbm_lattice *h, bool odd);
 int launch_interp(iilbm_lattice *h, cudaStream_t s);
 int launch_macros(iilbm_lattice *h, double *drho, double *ux, double *uy);
 int launch_set_populations(iilbm_lattice *h, const double *df, bool equilibrium,

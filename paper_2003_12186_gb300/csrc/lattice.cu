@@ -15,6 +15,9 @@
 // so one array suffices and every step moves 2 x 9 values per node.
 #include "interface_dev.cuh"
 #include "lattice_dev.cuh"
+#include "sc_tma_dev.cuh"
+
+#include <cudaTypedefs.h>
 
 #include <cmath>
 
@@ -242,6 +245,93 @@ static int last_error() {
   return cudaGetLastError() == cudaSuccess ? IILBM_OK : IILBM_ERR_CUDA;
 }
 
+// The interior tiles of the TMA stream-collide (see sc_tma_dev.cuh); false if none.
+static bool tma_tiles(const Geom &g, TmaTiles &t) {
+  t.tx0 = 1;
+  t.ntx_i = g.nx >= TMA_W + TMA_W + 2 * TMA_HALO ? (g.nx - TMA_W - TMA_HALO) / TMA_W : 0;
+  t.ty0 = 1;
+  t.nty_i = g.ny >= 2 * TMA_R + 1 ? (g.ny - TMA_R - 1) / TMA_R : 0;
+  return t.ntx_i > 0 && t.nty_i > 0;
+}
+
+bool uses_tma_sc(const iilbm_lattice *h, bool odd) {
+  TmaTiles t;
+  return (h->tma_sc == 1 || (h->tma_sc == 2 && odd)) && h->vector_sc && h->cfg.storage == IILBM_F32 && h->geom.nx % 4 == 0 &&
+         tma_tiles(h->geom, t);
+}
+
+// Tensor maps of the FP32 populations, dims (nx, ny, 9) with the row pitch and plane
+// strides, boxes 136 x 8, 128 x 8 and 124 x 8 (no swizzle, no out-of-bounds use).
+static bool tma_maps(iilbm_lattice *h) {
+  if (h->tmap_A == h->A) return true;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const Geom &g = h->geom;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, 9};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * sizeof(float),
+                                 (cuuint64_t)g.plane * sizeof(float)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const cuuint32_t width[3] = {TMA_LW_ODD, TMA_W, TMA_SW};
+  for (int q = 0; q < 3; q++) {
+    const cuuint32_t box[3] = {width[q], TMA_R, 1};
+    if (encode(&h->tmap[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->A, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return false;
+  }
+  h->tmap_A = h->A;
+  return true;
+}
+
+// The lean stream-collide as the TMA kernel over the interior tiles plus the register
+// path over the rest; false (nothing launched) where it does not apply.
+template <typename S, int COLL, bool ODD, int BC, bool BODY>
+static bool sc_launch_tma(iilbm_lattice *h, const unsigned *fl, const unsigned *tag,
+                          const CollP<typename Store<S>::T> &p) {
+  if constexpr (!std::is_same<S, float>::value) {
+    return false;
+  } else {
+    TmaTiles t;
+    if (!uses_tma_sc(h, ODD) || !tma_tiles(h->geom, t) || !tma_maps(h)) return false;
+    const Geom &g = h->geom;
+    auto kern = k_stream_collide_tma<COLL, ODD, BODY>;
+    constexpr size_t smem = TmaSmem<ODD>::bytes;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    static int sms = 0;
+    if (!sms) {
+      cudaDeviceProp prop;
+      if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return false;
+      sms = prop.multiProcessorCount;
+    }
+    const int interior = t.ntx_i * t.nty_i;
+    const int nty = (g.ny + TILE_Y - 1) / TILE_Y;
+    const int grid = std::min(interior, sms);
+    if ((interior + grid - 1) / grid > 32 * TMA_MASK_WORDS) return false;  // beyond the mask
+    kern<<<grid, TMA_THREADS, smem, h->stream>>>(
+        h->tmap[ODD ? 0 : 1], h->tmap[1], h->tmap[2], (float *)h->A, fl, tag, g, t, p,
+        h->d_status);
+    k_stream_collide_vec_edge<S, COLL, ODD, BC, BODY>
+        <<<g.ntx * nty - interior, 32 * VEC_ROWS, 0, h->stream>>>((S *)h->A, fl, tag, g, p,
+                                                                  h->d_status, t, nty);
+    return true;
+  }
+}
+
 template <typename S, int COLL, bool ODD, int BC>
 static void sc_launch_bc(iilbm_lattice *h, cudaStream_t forced_stream) {
   using T = typename Store<S>::T;
@@ -254,7 +344,11 @@ static void sc_launch_bc(iilbm_lattice *h, cudaStream_t forced_stream) {
   const int nyt = (g.ny + TILE_Y - 1) / TILE_Y;
   const bool vec = h->vector_sc && g.nx % V == 0;
   const dim3 vgrid((g.nx + 32 * V - 1) / (32 * V), nyt);
-  if (vec && h->cfg.body[0] == 0.0 && h->cfg.body[1] == 0.0)
+  const bool body = h->cfg.body[0] != 0.0 || h->cfg.body[1] != 0.0;
+  if (vec && (body ? sc_launch_tma<S, COLL, ODD, BC, true>(h, fl, h->tagb[b], p)
+                   : sc_launch_tma<S, COLL, ODD, BC, false>(h, fl, h->tagb[b], p))) {
+    // interior tiles by TMA, the rest by the register path
+  } else if (vec && !body)
     k_stream_collide_vec<S, COLL, ODD, BC, false><<<vgrid, 32 * VEC_ROWS, 0, h->stream>>>(
         (S *)h->A, fl, h->tagb[b], g, p, h->d_status);
   else if (vec)

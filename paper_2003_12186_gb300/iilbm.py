@@ -25,7 +25,7 @@ F64, F32, F16, BF16 = 0, 1, 2, 3
 BC_PERIODIC, BC_WALLS_Y, BC_CHANNEL, BC_BOX_OUTFLOW, BC_BOX_WALL = 0, 1, 2, 3, 4
 FORCE_GUO, FORCE_SIMPLE = 0, 1
 SPRING, SPRING_REST, PRESCRIBED, DIRECT = 0, 1, 2, 3
-OPT_CUDA_GRAPH, OPT_OVERLAP, OPT_VECTOR_KERNEL, OPT_FORCED_BLOCKS = 0, 1, 2, 3
+OPT_CUDA_GRAPH, OPT_OVERLAP, OPT_VECTOR_KERNEL, OPT_FORCED_BLOCKS, OPT_TMA_KERNEL = 0, 1, 2, 3, 4
 WS_GIVEN, WS_PREVIOUS, WS_MLP = 0, 1, 2
 MLP_PARAMS, MLP_FEATURES = 10434, 30
 BODY_PRESCRIBED_X, BODY_FREE = 1, 2

@@ -55,6 +55,58 @@ def test_vector_kernel_matches_scalar(storage, bc, shape):
         assert np.abs(a - b).max() <= 64 * ULP[storage] * scale
 
 
+@pytest.mark.parametrize("collision", ["srt", "mrt"])
+@pytest.mark.parametrize("bc", ["periodic", "walls"])
+@pytest.mark.parametrize("body", [False, True])
+@pytest.mark.parametrize("shape", [(264, 17), (520, 40), (392, 33), (1024, 72)])
+def test_tma_kernel_matches_vector(collision, bc, body, shape):
+    """FP32: the TMA stream-collide of the interior tiles (with the register path on the
+    rest) against the register path everywhere, seven steps of random data at both
+    parities, on lattices with one interior tile, several, and a ragged last tile
+    column: equal up to the compiler's multiply-add contraction (64 ulps of the field's
+    scale); a wrong box offset, shift or edge store would differ by O(1)."""
+    nx, ny = shape
+    df = W.random_df(nx, ny, 2e-3, 3 * nx + ny)
+    out = []
+    for tma in (0, 1):
+        g = iilbm.Lattice(nx, ny, collision=iilbm.SRT if collision == "srt" else iilbm.MRT,
+                          storage="f32", tau=0.7, s=W.mrt_rates(0.7),
+                          bc=iilbm.BC_PERIODIC if bc == "periodic" else iilbm.BC_WALLS_Y,
+                          body=(1e-5, -3e-6) if body else (0.0, 0.0))
+        g.set_option(iilbm.OPT_TMA_KERNEL, tma)
+        g.set_populations(df)
+        res = []
+        for n in (1, 1, 2, 3):
+            g.step(n)
+            res.append(g.get_populations())
+        g.synchronize()
+        out.append(res)
+    for a, b in zip(*out):
+        assert np.abs(a - b).max() <= 64 * ULP["f32"] * np.abs(a).max()
+
+
+def test_tma_kernel_with_a_membrane_matches_the_oracle(orc):
+    """A moving FP32 membrane on a 512 x 320 lattice (its flagged tiles inside the TMA
+    kernel's interior rectangle, left to the forced kernel): 40 steps with and without
+    the TMA kernel, both within 1e-5 of the oracle's velocity, and the launch count per
+    step one higher with it (interior and edge tiles)."""
+    w = W.ellipse_scaled(320, "f32")
+    X = w["X"] + np.array([96.0, 0.0])
+    for tma in (1, 0):
+        g, o = make_pair(orc, 512, 320, collision="mrt", storage="f32", tau=w["tau"])
+        g.set_option(iilbm.OPT_TMA_KERNEL, tma)
+        set_membrane(orc, g, o, X, "spring", w["kappa"], w["dX"])
+        g.step(2)
+        g.iilbm_set_timing(True)
+        g.step(38)
+        ms, n, k = g.iilbm_get_timing()
+        assert n == 38 and k == 38 * (4 if tma else 3) and ms > 0
+        o.step(40)
+        umax = np.abs(o.markers()["U"]).max()
+        assert vel_error(g, o, max(umax, 1e-6)) < 1e-5
+        assert np.abs(g.get_markers()["X"] - o.markers()["X"]).max() < 1e-7
+
+
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_graph_and_overlap_match_eager(orc, storage):
     """70 steps (two 32-step graph replays plus eager steps) of a moving membrane, in

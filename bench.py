@@ -477,8 +477,11 @@ def run_ours(args):
     tr = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr):
         d = json.load(open(tr)).get(f"ellipse{args.size}_{args.storage}")
-        if d:
+        if d and not args.tma:
             roofline["traffic"] = d
+            # the same fraction counted in the DRAM bytes of a captured launch
+            roofline["dram_achieved"] = round(d / sc_avg_s / 1e9, 1)
+            roofline["dram_frac"] = round(d / sc_avg_s / 1e9 / peak, 4)
     if args.storage == "f64":
         # FP64 arithmetic: GB300 runs FP64 at about 1.25 TFLOP/s (152 SMs x 2 FP64 FMA per
         # clock x 2 flops x 2.07 GHz), so the FP64 stream-collide is bound by the FP64

@@ -3,12 +3,13 @@
 // 2.2.1, and the jump conditions of section 3.1, which the paper derives in three
 // dimensions).  C ABI in include/iilbm3d.h.
 //
-// One step, all on the lattice's stream:
+// One step (the vertex pass, the cut links and the lean kernel on the lattice's stream; the
+// forced kernel and the interpolation on a second stream beside the lean kernel):
 //   k3_vertex        one thread per vertex: surface normal and area from the incident
 //                    triangles, the Lagrangian force (prescribed or surface tension), the
 //                    normal split Fn = G.n / J, the spread of the tangential part (the
 //                    whole G in IB-LBM) into g, and the flags of the tiles the vertex's
-//                    4 x 4 x 4 support touches;
+//                    4 x 4 x 4 support touches (marked with the level's tag 1 + (n & 1));
 //   k3_cut           one warp per triangle: every link x - e_i -> x that crosses it (exact
 //                    integer predicate with symbolic tie-breaks) adds s w_i/c_s^2 Fn to the
 //                    streamed population f_i(x) in place (Eq. 47);
@@ -16,7 +17,8 @@
 //                    in-place streaming, SRT or MRT collision, on every tile not flagged;
 //   k3_sc_forced     the flagged tiles, from the list the vertex pass built: the same with
 //                    g (Guo's term or the simple force term), which it clears, and the
-//                    collision's velocity recorded for the interpolation;
+//                    collision's velocity recorded for the interpolation; it also clears
+//                    the previous level's marks;
 //   k3_interp        one thread per vertex: U = interp(u) (Eq. 20), X += U for a moving
 //                    surface.
 // Between steps the stored populations carry no jump: the jump of the next step's
@@ -34,6 +36,12 @@
 #include <vector>
 
 #include "../../include/iilbm3d.h"
+
+// Blocks per SM of the forced stream-collide, which runs beside the lean one: each
+// forced block holds an SM's registers that lean blocks would otherwise use.
+#ifndef K3_FORCED_BLOCKS_PER_SM
+#define K3_FORCED_BLOCKS_PER_SM 16
+#endif
 
 namespace iilbm3d {
 
@@ -436,9 +444,14 @@ struct iilbm3d_lattice {
   void *A;            // [19][plane] populations in the storage type
   void *gf;           // spread force (arithmetic type; Vec3 layout), zero outside flagged tiles
   void *uf;           // collision velocity on flagged tiles (Vec3 layout)
-  unsigned *flags;    // [ntiles] tile carries a spread force / marker support
-  int *tile_list;     // [ntiles] the flagged tiles of the current level, in flagging order
-  int *tile_count;    // their number
+  unsigned *flags;    // [ntiles] tile flagged at level n iff it holds tag(n) = 1 + (n & 1)
+  int *tile_list;     // [2][ntiles] the flagged tiles of the levels of each parity, in
+                      // flagging order
+  int *tile_count;    // [2] their numbers
+  long long ntiles;
+  int sms;            // the device's multiprocessors
+  cudaStream_t side;  // forced stream-collide and interpolation, beside the lean kernel
+  cudaEvent_t ev_fork, ev_forced, ev_join;
   int *d_status;
   int *d_count;       // cut-link crossings of the most recent surface pass
   long long step;     // time level; AA parity = step & 1
@@ -568,10 +581,10 @@ template <typename S, bool ODD, bool MRT, bool SIMPLE, bool BODY,
           typename T = typename St3<S>::T>
 __global__ void __launch_bounds__(TB, sizeof(T) == 4 ? 8 : 4)
     k3_sc_lean(S *__restrict__ A, const Geom3 g, const Coll3<T> p,
-               const unsigned *__restrict__ flags, int *__restrict__ status) {
+               const unsigned *__restrict__ flags, unsigned tag, int *__restrict__ status) {
   const int x = blockIdx.x * TX + (threadIdx.x & (TX - 1));
   const int y = blockIdx.y * TY + (threadIdx.x / TX), z = blockIdx.z;
-  if (flags[((long long)z * g.nty + blockIdx.y) * g.ntx + blockIdx.x] != 0u) return;  // whole block
+  if (flags[((long long)z * g.nty + blockIdx.y) * g.ntx + blockIdx.x] == tag) return;  // whole block
   if (x >= g.nx || y >= g.ny) return;
   sc_node<S, ODD, MRT, SIMPLE, BODY, false, T>(A, g, p, x, y, z, nullptr, nullptr, status);
 }
@@ -580,8 +593,14 @@ template <typename S, bool ODD, bool MRT, bool SIMPLE, typename T = typename St3
 __global__ void __launch_bounds__(TB, sizeof(T) == 4 ? 4 : 2)
     k3_sc_forced(S *__restrict__ A, const Geom3 g, const Coll3<T> p,
                  unsigned *__restrict__ flags, const int *__restrict__ tile_list,
-                 const int *__restrict__ tile_count, T *__restrict__ gf, T *__restrict__ uf,
-                 int *__restrict__ status) {
+                 const int *__restrict__ tile_count, const int *__restrict__ prev_list,
+                 const int *__restrict__ prev_count, unsigned prev_tag, T *__restrict__ gf,
+                 T *__restrict__ uf, int *__restrict__ status) {
+  // the previous level's marks go back to 0 (a tile flagged again holds this level's
+  // tag and keeps it): the next level's vertex pass then finds only 0 or this tag
+  const int pc = *prev_count;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < pc; k += gridDim.x * blockDim.x)
+    atomicCAS(&flags[prev_list[k]], prev_tag, 0u);
   const int cnt = *tile_count;
   for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
     const int tile = tile_list[k];
@@ -590,7 +609,6 @@ __global__ void __launch_bounds__(TB, sizeof(T) == 4 ? 4 : 2)
     const int x = tx * TX + (threadIdx.x & (TX - 1)), y = ty * TY + (threadIdx.x / TX);
     if (x < g.nx && y < g.ny)
       sc_node<S, ODD, MRT, SIMPLE, true, true>(A, g, p, x, y, z, gf, uf, status);
-    if (threadIdx.x == 0) flags[tile] = 0u;  // the lean kernel has finished reading it
   }
 }
 
@@ -625,7 +643,8 @@ __global__ void __launch_bounds__(128)
               const double *__restrict__ Aref, int model, double gamma,
               const double *__restrict__ Gp, int jump, const Geom3 g, double *__restrict__ G,
               double *__restrict__ Fn, T *__restrict__ gf, unsigned *__restrict__ flags,
-              int *__restrict__ tile_list, int *__restrict__ tile_count, T *__restrict__ Fnt,
+              unsigned tag, int *__restrict__ tile_list, int *__restrict__ tile_count,
+              T *__restrict__ Fnt,
               long long *__restrict__ Xq, int *__restrict__ status) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
@@ -713,7 +732,7 @@ __global__ void __launch_bounds__(128)
         const int tx = x / TX;
         if (tx != last) {
           const int tile = (int)(((long long)z * g.nty + y / TY) * g.ntx + tx);
-          if (atomicExch(&flags[tile], 1u) == 0u) tile_list[atomicAdd(tile_count, 1)] = tile;
+          if (atomicExch(&flags[tile], tag) != tag) tile_list[atomicAdd(tile_count, 1)] = tile;
           last = tx;
         }
       }
@@ -837,16 +856,20 @@ __global__ void __launch_bounds__(128, 5)
   const int E0 = ext[0] + 2, E1 = ext[1] + 2, E2 = ext[2] + 2;
   signed char *side = cut_sides[wslot];
   unsigned *list = cut_list[wslot];
+  // r0 = 2^20 q + m with q = floor(r0 / 2^20), 0 <= m < 2^20 (|r0| < 2^73, |q| < 2^53), so
+  // r0 + 2^20 L = 2^20 (q + L) + m has the sign of q + L, or of m where q + L = 0: one
+  // 128-bit product per triangle, 64-bit sums per node (|L| < 2^53)
   const __int128 r0 = -((__int128)N[0] * r[0][0] + (__int128)N[1] * r[0][1] + (__int128)N[2] * r[0][2]);
+  const long long q0 = (long long)(r0 >> QBITS);
+  const bool m_pos = ((unsigned long long)r0 & ((1ull << QBITS) - 1ull)) != 0ull;
   // box index -> (a, b, c) by FP32 quotients: (k + 1/2) / E is at least 1/(2E) from an
   // integer (E <= 12, k < 1728), far beyond the quotient's rounding error
   const float iE0 = 1.0f / (float)E0, iE01 = 1.0f / (float)(E0 * E1);
   for (int c = lane; c < E0 * E1 * E2; c += 32) {
     const int cz = (int)(((float)c + 0.5f) * iE01), rem = c - cz * E0 * E1;
     const int b = (int)(((float)rem + 0.5f) * iE0), a = rem - b * E0;
-    const long long L = a * N[0] + b * N[1] + cz * N[2];
-    const __int128 rr = r0 + ((__int128)L << QBITS);
-    side[c] = (signed char)(rr > 0 ? 1 : (rr < 0 ? -1 : tie));
+    const long long t = q0 + (a * N[0] + b * N[1] + cz * N[2]);
+    side[c] = (signed char)(t > 0 ? 1 : (t < 0 ? -1 : (m_pos ? 1 : tie)));
   }
   __syncwarp();
   int found = 0;
@@ -1093,59 +1116,73 @@ void with_storage(const H *h, F &&f) {
 
 bool has_body(const H *h) { return h->cfg.body[0] != 0.0 || h->cfg.body[1] != 0.0 || h->cfg.body[2] != 0.0; }
 
+// Tag of the flagged tiles of level n (flags hold 0, or the tag of the level that marked
+// them, cleared one level later).
+unsigned level_tag(long long n) { return 1u + (unsigned)(n & 1); }
+
+// The lean stream-collide on stream s (every tile without this level's tag); forced: the
+// flagged tiles instead, on its own stream, with the previous level's marks cleared.
 template <typename S, bool ODD, bool MRT, bool SIMPLE>
-void launch_sc_p(H *h, cudaStream_t s) {
+void launch_sc_p(H *h, cudaStream_t s, bool forced) {
   using T = typename St3<S>::T;
   const Geom3 &g = h->geo;
-  const dim3 grid(g.ntx, g.nty, g.nz);
   const Coll3<T> p = coll_params<T>(h);
-  if (has_body(h))
-    k3_sc_lean<S, ODD, MRT, SIMPLE, true><<<grid, TB, 0, s>>>((S *)h->A, g, p, h->flags, h->d_status);
-  else
-    k3_sc_lean<S, ODD, MRT, SIMPLE, false><<<grid, TB, 0, s>>>((S *)h->A, g, p, h->flags, h->d_status);
-  if (h->n > 0) {
-    const long long ntiles = (long long)g.ntx * g.nty * g.nz;
-    const unsigned blocks = (unsigned)std::min<long long>(ntiles, 152LL * 16);
-    k3_sc_forced<S, ODD, MRT, SIMPLE><<<blocks, TB, 0, s>>>((S *)h->A, g, p, h->flags,
-                                                             h->tile_list, h->tile_count,
-                                                             (T *)h->gf, (T *)h->uf, h->d_status);
+  const int b = (int)(h->step & 1);
+  if (!forced) {
+    const dim3 grid(g.ntx, g.nty, g.nz);
+    const unsigned tag = level_tag(h->step);
+    if (has_body(h))
+      k3_sc_lean<S, ODD, MRT, SIMPLE, true><<<grid, TB, 0, s>>>((S *)h->A, g, p, h->flags, tag,
+                                                                h->d_status);
+    else
+      k3_sc_lean<S, ODD, MRT, SIMPLE, false><<<grid, TB, 0, s>>>((S *)h->A, g, p, h->flags, tag,
+                                                                 h->d_status);
+  } else {
+    const unsigned blocks =
+        (unsigned)std::min<long long>(h->ntiles, (long long)h->sms * K3_FORCED_BLOCKS_PER_SM);
+    k3_sc_forced<S, ODD, MRT, SIMPLE><<<blocks, TB, 0, s>>>(
+        (S *)h->A, g, p, h->flags, h->tile_list + b * h->ntiles, h->tile_count + b,
+        h->tile_list + (b ^ 1) * h->ntiles, h->tile_count + (b ^ 1), level_tag(h->step + 1),
+        (T *)h->gf, (T *)h->uf, h->d_status);
   }
 }
 
 template <typename S, bool MRT, bool SIMPLE>
-void launch_sc_t(H *h, cudaStream_t s) {
-  if (h->step & 1) launch_sc_p<S, true, MRT, SIMPLE>(h, s);
-  else launch_sc_p<S, false, MRT, SIMPLE>(h, s);
+void launch_sc_t(H *h, cudaStream_t s, bool forced) {
+  if (h->step & 1) launch_sc_p<S, true, MRT, SIMPLE>(h, s, forced);
+  else launch_sc_p<S, false, MRT, SIMPLE>(h, s, forced);
 }
 
 template <typename S>
-void launch_sc_s(H *h, cudaStream_t s) {
+void launch_sc_s(H *h, cudaStream_t s, bool forced) {
   const bool mrt = h->cfg.collision == IILBM_MRT, simple = h->cfg.force == IILBM_FORCE_SIMPLE;
-  if (mrt && simple) launch_sc_t<S, true, true>(h, s);
-  else if (mrt) launch_sc_t<S, true, false>(h, s);
-  else if (simple) launch_sc_t<S, false, true>(h, s);
-  else launch_sc_t<S, false, false>(h, s);
+  if (mrt && simple) launch_sc_t<S, true, true>(h, s, forced);
+  else if (mrt) launch_sc_t<S, true, false>(h, s, forced);
+  else if (simple) launch_sc_t<S, false, true>(h, s, forced);
+  else launch_sc_t<S, false, false>(h, s, forced);
 }
 
-void launch_sc(H *h) {
-  with_storage(h, [&](auto tag) { launch_sc_s<decltype(tag)>(h, h->stream); });
+void launch_sc(H *h, cudaStream_t s, bool forced) {
+  with_storage(h, [&](auto tag) { launch_sc_s<decltype(tag)>(h, s, forced); });
 }
 
 void launch_vertex(H *h) {
   const Geom3 &g = h->geo;
   const unsigned b = blocks_for(h->n, 128);
-  cudaMemsetAsync(h->tile_count, 0, sizeof(int), h->stream);
+  const int par = (int)(h->step & 1);
+  int *list = h->tile_list + par * h->ntiles, *count = h->tile_count + par;
+  const unsigned tag = level_tag(h->step);
+  cudaMemsetAsync(count, 0, sizeof(int), h->stream);
   if (h->f64)
     k3_vertex<double><<<b, 128, 0, h->stream>>>(h->X, h->n, h->tri, h->vt_start, h->vt_list, h->Aref,
                                                 h->sp.model, h->sp.gamma, h->Gp, h->cfg.jump, g,
-                                                h->G, h->Fn, (double *)h->gf, h->flags,
-                                                h->tile_list, h->tile_count, h->Fn, h->Xq, h->d_status);
+                                                h->G, h->Fn, (double *)h->gf, h->flags, tag,
+                                                list, count, h->Fn, h->Xq, h->d_status);
   else
     k3_vertex<float><<<b, 128, 0, h->stream>>>(h->X, h->n, h->tri, h->vt_start, h->vt_list, h->Aref,
                                                h->sp.model, h->sp.gamma, h->Gp, h->cfg.jump, g,
-                                               h->G, h->Fn, (float *)h->gf, h->flags,
-                                               h->tile_list, h->tile_count, (float *)h->Fnt,
-                                               h->Xq, h->d_status);
+                                               h->G, h->Fn, (float *)h->gf, h->flags, tag,
+                                               list, count, (float *)h->Fnt, h->Xq, h->d_status);
 }
 
 // the jump of the current level: in place into the populations (J null) or into J
@@ -1171,20 +1208,25 @@ void launch_cut(H *h, double *J) {
   });
 }
 
-void launch_interp(H *h) {
+void launch_interp(H *h, cudaStream_t s) {
   const unsigned b = blocks_for(h->n, 128);
   if (h->f64)
-    k3_interp<double><<<b, 128, 0, h->stream>>>((const double *)h->uf, h->geo, h->X, h->n, h->U,
-                                                h->sp.moves);
+    k3_interp<double><<<b, 128, 0, s>>>((const double *)h->uf, h->geo, h->X, h->n, h->U,
+                                        h->sp.moves);
   else
-    k3_interp<float><<<b, 128, 0, h->stream>>>((const float *)h->uf, h->geo, h->X, h->n, h->U,
-                                               h->sp.moves);
+    k3_interp<float><<<b, 128, 0, s>>>((const float *)h->uf, h->geo, h->X, h->n, h->U,
+                                       h->sp.moves);
 }
 
-// One time step (see the file's head).  The stream-collide is bracketed by timing events
-// when timing is on (eager steps only).
+// One time step (see the file's head).  Main stream: vertex pass, cut links, then the lean
+// stream-collide; the side stream (highest priority), forked after the cut links: the
+// forced stream-collide of the flagged tiles, then the interpolation and vertex update.
+// The two touch disjoint tiles (a node's AA reads and writes are its own), and the main
+// stream joins the side stream at the end of the step.  With timing on, an event pair
+// brackets both stream-collide kernels (eager steps only).
 int one_step(H *h) {
-  if (h->n > 0) {
+  const bool surf = h->n > 0;
+  if (surf) {
     if (!h->prepared) launch_vertex(h);
     CK3(cudaMemsetAsync(h->d_count, 0, sizeof(int), h->stream));
     if (h->cfg.jump) launch_cut(h, nullptr);
@@ -1199,13 +1241,22 @@ int one_step(H *h) {
     }
     CK3(cudaEventRecord(h->ev[2 * h->nev], h->stream));
   }
-  launch_sc(h);
+  if (surf) {
+    CK3(cudaEventRecord(h->ev_fork, h->stream));
+    CK3(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    launch_sc(h, h->side, true);
+    if (h->timing) CK3(cudaEventRecord(h->ev_forced, h->side));
+    launch_interp(h, h->side);
+    CK3(cudaEventRecord(h->ev_join, h->side));
+  }
+  launch_sc(h, h->stream, false);
   if (h->timing) {
+    if (surf) CK3(cudaStreamWaitEvent(h->stream, h->ev_forced, 0));
     CK3(cudaEventRecord(h->ev[2 * h->nev + 1], h->stream));
     h->nev++;
-    h->kernels += h->n > 0 ? (h->cfg.jump ? 5 : 4) - (h->prepared ? 1 : 0) : 1;
+    h->kernels += surf ? (h->cfg.jump ? 5 : 4) - (h->prepared ? 1 : 0) : 1;
   }
-  if (h->n > 0) launch_interp(h);
+  if (surf) CK3(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   CK3(cudaGetLastError());
   h->step++;
   h->prepared = false;
@@ -1319,6 +1370,7 @@ int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
   if (!h) return IILBM_ERR_OOM;
   h->cfg = c;
   h->device = dev;
+  h->sms = prop.multiProcessorCount;
   h->f64 = c.storage == IILBM_F64;
   h->storage = c.storage;
   h->scale = std::ldexp(1.0, c.storage_scale_log2);
@@ -1332,10 +1384,19 @@ int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
   const size_t sb = h->f64 ? 8 : 4;                      // arithmetic type
   const size_t sa = c.storage == IILBM_F64 ? 8 : (half ? 2 : 4);  // storage type
   const size_t ntiles = (size_t)g.ntx * g.nty * c.nz;
+  h->ntiles = (long long)ntiles;
   bool ok = true;
-  if (c.stream) {
+  // the side stream at the highest priority, so the forced tiles' few blocks are
+  // dispatched ahead of the lean stream-collide's backlog
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  ok = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
+       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&h->ev_forced, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && c.stream) {
     h->stream = (cudaStream_t)c.stream;
-  } else {
+  } else if (ok) {
     ok = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) == cudaSuccess;
     h->own_stream = ok;
   }
@@ -1343,15 +1404,15 @@ int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
        cudaMalloc(&h->gf, 4 * g.plane * sb) == cudaSuccess &&
        cudaMalloc(&h->uf, 4 * g.plane * sb) == cudaSuccess &&
        cudaMalloc(&h->flags, ntiles * sizeof(unsigned)) == cudaSuccess &&
-       cudaMalloc(&h->tile_list, ntiles * sizeof(int)) == cudaSuccess &&
-       cudaMalloc(&h->tile_count, sizeof(int)) == cudaSuccess &&
+       cudaMalloc(&h->tile_list, 2 * ntiles * sizeof(int)) == cudaSuccess &&
+       cudaMalloc(&h->tile_count, 2 * sizeof(int)) == cudaSuccess &&
        cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
        cudaMalloc(&h->d_count, sizeof(int)) == cudaSuccess;
   ok = ok && cudaMemsetAsync(h->A, 0, 19 * g.plane * sa, h->stream) == cudaSuccess &&
        cudaMemsetAsync(h->gf, 0, 4 * g.plane * sb, h->stream) == cudaSuccess &&
        cudaMemsetAsync(h->uf, 0, 4 * g.plane * sb, h->stream) == cudaSuccess &&
        cudaMemsetAsync(h->flags, 0, ntiles * sizeof(unsigned), h->stream) == cudaSuccess &&
-       cudaMemsetAsync(h->tile_count, 0, sizeof(int), h->stream) == cudaSuccess &&
+       cudaMemsetAsync(h->tile_count, 0, 2 * sizeof(int), h->stream) == cudaSuccess &&
        cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream) == cudaSuccess &&
        cudaMemsetAsync(h->d_count, 0, sizeof(int), h->stream) == cudaSuccess &&
        cudaStreamSynchronize(h->stream) == cudaSuccess;
@@ -1367,12 +1428,17 @@ int iilbm3d_create(iilbm3d_t *out, const iilbm3d_config *cfg) {
 int iilbm3d_destroy(iilbm3d_t h) {
   if (!h) return IILBM_ERR_INVALID_ARG;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->side) cudaStreamSynchronize(h->side);
   drop_graph(h);
   free_surface(h);
   void *p[] = {h->A, h->gf, h->uf, h->flags, h->tile_list, h->tile_count, h->d_status, h->d_count};
   for (void *q : p)
     if (q) cudaFree(q);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  cudaEvent_t own[] = {h->ev_fork, h->ev_forced, h->ev_join};
+  for (cudaEvent_t e : own)
+    if (e) cudaEventDestroy(e);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   cudaGetLastError();
   delete h;
@@ -1397,7 +1463,7 @@ int iilbm3d_set_surface(iilbm3d_t h, const double *X, int32_t n, const int32_t *
   const size_t ntiles = (size_t)h->geo.ntx * h->geo.nty * h->geo.nz;
   CK3(cudaMemsetAsync(h->gf, 0, 4 * h->geo.plane * sb, h->stream));
   CK3(cudaMemsetAsync(h->flags, 0, ntiles * sizeof(unsigned), h->stream));
-  CK3(cudaMemsetAsync(h->tile_count, 0, sizeof(int), h->stream));
+  CK3(cudaMemsetAsync(h->tile_count, 0, 2 * sizeof(int), h->stream));
   h->prepared = false;
   if (n == 0) return IILBM_OK;
   std::vector<double> hx(3 * (size_t)n), hg;

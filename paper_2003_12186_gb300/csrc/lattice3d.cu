@@ -42,6 +42,10 @@
 #ifndef K3_FORCED_BLOCKS_PER_SM
 #define K3_FORCED_BLOCKS_PER_SM 16
 #endif
+// Resident blocks per SM the FP32 forced kernel is compiled for (its register budget).
+#ifndef K3_FORCED_MIN_BLOCKS
+#define K3_FORCED_MIN_BLOCKS 4
+#endif
 
 namespace iilbm3d {
 
@@ -590,7 +594,7 @@ __global__ void __launch_bounds__(TB, sizeof(T) == 4 ? 8 : 4)
 }
 
 template <typename S, bool ODD, bool MRT, bool SIMPLE, typename T = typename St3<S>::T>
-__global__ void __launch_bounds__(TB, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(TB, sizeof(T) == 4 ? K3_FORCED_MIN_BLOCKS : 2)
     k3_sc_forced(S *__restrict__ A, const Geom3 g, const Coll3<T> p,
                  unsigned *__restrict__ flags, const int *__restrict__ tile_list,
                  const int *__restrict__ tile_count, const int *__restrict__ prev_list,

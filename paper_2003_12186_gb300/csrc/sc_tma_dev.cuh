@@ -5,20 +5,20 @@
 // flag tiles) round-robin.  Thread 0 moves every tile with bulk tensor copies: each
 // population plane's box is loaded into shared memory (a four-stage ring, an mbarrier per
 // stage: three tiles in flight while one computes) and, after the collision, stored back
-// from an output area.  The 16
-// warps never address global memory for the bulk of the data: they read the streamed
-// populations from shared memory with the AA shift folded into the index, collide, and
-// write the post-collision values into the output boxes.  Loads of the next tiles are in
-// flight while a tile computes, so the memory system sees the same bytes in flight whatever
-// the parity.
+// from an output area.  The 16 warps never address global memory for the bulk of the
+// data: they read the streamed populations from shared memory with the AA shift folded
+// into the index, collide, and write the post-collision values into the output boxes.
+// Loads of the next tiles are in flight while a tile computes, so the memory system sees
+// the same bytes in flight whatever the parity.
 //
 // The odd step reads slot opp(i) of x - e_i and writes slot i of x + e_i.  Its load box of
 // a plane is 136 nodes wide, from x = xb - 4 (a 16-byte boundary; every row needs only one
 // node beyond the tile on one side).  Its store box of a plane with e_x = +-1 covers the
 // 124 aligned nodes the tile writes alone (xb + 4 .. xb + 127 for e_x = +1, xb .. xb + 123
 // for e_x = -1); the four remaining values of each row land next to a neighbouring tile's
-// values inside one 16-byte segment and are written by the threads with plain stores, as
-// the register-path kernel writes them at its warp ends.  Every (plane, row, column) is
+// values inside one 16-byte segment: they go to an edge slot after the box in shared
+// memory and from there to global memory with plain stores, as the register-path kernel
+// writes them at its warp ends.  Every (plane, row, column) is
 // written by exactly one node, and a node's read set is its write set (the AA pattern), so
 // the tiles need no ordering among themselves or with the edge tiles of the other launch.
 //

@@ -825,15 +825,18 @@ __global__ void __launch_bounds__(128, 5)
     if (lane == 0) atomicOr(status, ST_INTERFACE);
     return;
   }
-  int lo[3], ext[3];
+  int lo[3], ext[3], bmn[3], bmx[3];
+  const long long Sx = 1LL << QBITS;
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     const long long mn = min(q[0][a], min(q[1][a], q[2][a]));
     const long long mx = max(q[0][a], max(q[1][a], q[2][a]));
     lo[a] = (int)(-((-mn) >> QBITS)) - 1;
     ext[a] = (int)(-((-mx) >> QBITS)) - lo[a] + 1;
+    // the triangle's bounding box relative to O = (lo - 1) 2^20 (below 2^24)
+    bmn[a] = (int)(mn - (long long)(lo[a] - 1) * Sx);
+    bmx[a] = (int)(mx - (long long)(lo[a] - 1) * Sx);
   }
-  const long long Sx = 1LL << QBITS;
   // vertices relative to the widened box's corner O = (lo - 1) 2^20
   long long r[3][3];
 #pragma unroll
@@ -892,10 +895,24 @@ __global__ void __launch_bounds__(128, 5)
       a++, b++, cz++;  // offsets in the widened box
       const int base = a + E0 * (b + E1 * cz);
       const int sQ = side[base];
+      // A link that crosses the triangle meets its bounding box.  The displaced link
+      // from s to d spans [min + eps, max + eps] per axis, which meets [mn, mx] iff
+      // 2^20 min < mx and 2^20 max >= mn; okX[e + 1]: that test for the component e.
+      const int o[3] = {a, b, cz};
+      bool ok[3][3];
+#pragma unroll
+      for (int ax = 0; ax < 3; ax++) {
+        const int P = o[ax] << QBITS;
+        const bool lt = P < bmx[ax], ge = P >= bmn[ax];
+        ok[ax][0] = lt && (P + (1 << QBITS)) >= bmn[ax];  // e = -1: source at d + 1
+        ok[ax][1] = lt && ge;                              // e = 0
+        ok[ax][2] = (P - (1 << QBITS)) < bmx[ax] && ge;    // e = +1: source at d - 1
+      }
       static_for<1, 19>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         const int off = ex(i) + E0 * (ey(i) + E1 * ez(i));
-        if (side[base - off] != sQ) mask |= 1u << i;
+        if (ok[0][ex(i) + 1] && ok[1][ey(i) + 1] && ok[2][ez(i) + 1] && side[base - off] != sQ)
+          mask |= 1u << i;
       });
     }
     // gather: (a, b, c, i) packed, each lane's candidates at its prefix position

@@ -1585,7 +1585,8 @@ int iilbm3d_init_equilibrium(iilbm3d_t h, const double *drho, const double *ux, 
   }
   for (double *q : d)
     if (q) cudaFree(q);
-  h->prepared = false;  // the level's state changed: its surface pass runs again
+  // the vertex pass of the level (g, flags, G, Fn) depends on the surface only: a pass
+  // that already ran stays valid (running it again would spread g twice)
   return rc;
 }
 

@@ -161,14 +161,20 @@ def test_moving_tension_surface_fp32():
 
 
 def test_graph_replay_and_read_outs_do_not_change_the_run():
-    """Steps replayed from graphs equal eager steps (timing on runs eagerly), and reading
-    the macroscopic fields or the jump between steps changes nothing."""
+    """Steps replayed from graphs equal eager steps (timing on runs eagerly); reading the
+    macroscopic fields or the jump between steps, or a read-out followed by a fresh
+    equilibrium before the first step, changes nothing: populations, vertices and the
+    G and Fn the read-out returns (those of the last step's level)."""
     n = 16
     X, T = W.ellipsoid_surface((8.1, 7.9, 8.2), (4.0, 3.2, 2.8), 2, seed=14)
     runs = []
-    for mode in ("graph", "eager", "reads"):
+    for mode in ("graph", "eager", "reads", "restart"):
         g = iilbm3d.Lattice3D(n, n, n, storage="f64")
         g.set_surface(X, T, model=iilbm3d.TENSION, moves=True, gamma=2e-3)
+        if mode == "restart":
+            # a read-out runs the level's vertex pass; a fresh equilibrium keeps it valid
+            g.get_jump()
+            g.init_equilibrium()
         if mode == "eager":
             g.set_timing(True)
         for k in (5, 1, 8, 3):
@@ -179,10 +185,13 @@ def test_graph_replay_and_read_outs_do_not_change_the_run():
                     g.step(1)
             else:
                 g.step(k)
-        runs.append((g.get_populations(), g.get_markers()["X"]))
-    for df, Xg in runs[1:]:
+        m = g.get_markers()
+        runs.append((g.get_populations(), m["X"], m["Fn"], m["G"]))
+    for df, Xg, Fn, G in runs[1:]:
         assert np.abs(df - runs[0][0]).max() < 1e-17
         assert np.abs(Xg - runs[0][1]).max() < 1e-14
+        assert np.abs(Fn - runs[0][2]).max() <= 1e-14 * np.abs(runs[0][2]).max()
+        assert np.abs(G - runs[0][3]).max() <= 1e-14 * np.abs(runs[0][3]).max()
 
 
 def test_surface_validation():

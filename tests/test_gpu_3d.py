@@ -290,3 +290,26 @@ def test_jump_field_fp32_matches_the_oracle():
     mask = (Jo != 0)
     assert (mask == (Jg != 0)).all()
     assert np.abs(Jg - Jo).max() < 1e-6 * np.abs(Jo).max()
+
+
+def test_full_size_membrane_fp32_matches_the_oracle():
+    """The benchmark's own workload and launch configuration (256^3 surface-tension
+    ellipsoid, 40 962 vertices, FP32, MRT, graph replay of two steps): after four steps
+    the cut-link count equals the oracle's exactly, and the vertices and every population
+    agree with the FP64 oracle to FP32 rounding."""
+    w = W.membrane_3d(256)
+    n = w["n"]
+    g = iilbm3d.Lattice3D(n, n, n, collision=iilbm3d.MRT, storage="f32", tau=w["tau"])
+    try:
+        o = o3.Oracle3D(n, n, n, parallel=True, collision=o3.MRT, tau=w["tau"])
+    except RuntimeError:  # no OpenMP build: the serial oracle
+        o = o3.Oracle3D(n, n, n, collision=o3.MRT, tau=w["tau"])
+    g.set_surface(w["X"], w["T"], model=iilbm3d.TENSION, moves=True, gamma=w["gamma"])
+    o.set_surface(w["X"], w["T"], model=o3.TENSION, moves=True, gamma=w["gamma"])
+    g.step(4)
+    o.step(4)
+    assert g.get_cut_link_count() == o.cut_link_count() > 500000
+    mg, mo = g.get_markers(), o.markers()
+    assert np.abs(mg["X"] - mo["X"]).max() < 1e-6
+    dg, do = g.get_populations(), o.get_df()
+    assert np.abs(dg - do).max() <= 1e-5 * np.abs(do).max()

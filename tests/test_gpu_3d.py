@@ -294,8 +294,9 @@ def test_jump_field_fp32_matches_the_oracle():
 
 def test_full_size_membrane_fp32_matches_the_oracle():
     """The benchmark's own workload and launch configuration (256^3 surface-tension
-    ellipsoid, 40 962 vertices, FP32, MRT, graph replay of two steps): after four steps
-    the cut-link count equals the oracle's exactly, and the vertices and every population
+    ellipsoid, 40 962 vertices, FP32, MRT, graph replay of two steps): the first level's
+    jump field crosses the same links as the oracle's (index work, exact); after four
+    steps the cut-link count equals the oracle's, and the vertices and every population
     agree with the FP64 oracle to FP32 rounding."""
     w = W.membrane_3d(256)
     n = w["n"]
@@ -306,6 +307,13 @@ def test_full_size_membrane_fp32_matches_the_oracle():
         o = o3.Oracle3D(n, n, n, collision=o3.MRT, tau=w["tau"])
     g.set_surface(w["X"], w["T"], model=iilbm3d.TENSION, moves=True, gamma=w["gamma"])
     o.set_surface(w["X"], w["T"], model=o3.TENSION, moves=True, gamma=w["gamma"])
+    # the first level's jump field: the same links in every direction, values to FP32
+    Jg = g.get_jump()
+    Jo, cnt = o.jump_field()
+    assert cnt > 500000 and g.get_cut_link_count() == cnt
+    assert ((Jg != 0) == (Jo != 0)).all()
+    assert np.abs(Jg - Jo).max() <= 1e-5 * np.abs(Jo).max()
+    del Jg, Jo
     g.step(4)
     o.step(4)
     assert g.get_cut_link_count() == o.cut_link_count() > 500000

@@ -783,13 +783,13 @@ __device__ __forceinline__ int cut_edge_side(const CutEdge &e, int dx, int dy, i
 // One warp per triangle.  The candidate destinations x span [ceil(min) - 1, ceil(max)] per
 // axis (the displaced link spans at most [x - 1 + eps, x + 1 + eps]); the warp tabulates
 // the plane side of every node of that box widened by one node (every source lies there,
-// N.(X - A) affine in the node's offset), then, a round of 32 destinations at a time,
+// N.(X - A) affine in the node's offset), then, a pass of 32 destinations at a time,
 // marks the directions whose link ends straddle the plane, gathers those (node,
 // direction) candidates into a list, and tests them with all 32 lanes.  A crossing adds
 // coef = s w_i / c_s^2 Fn(crossing), Fn the barycentric mean of the vertices' Fn, to the
 // streamed population in place (INPLACE; times the storage scale) or to the field
 // J[i-1][node] (read-outs).  S is the storage type, T the arithmetic type.
-constexpr int CUT_LIST = 32 * 18;  // candidates of one round at most
+constexpr int CUT_LIST = 32 * 18;  // candidates of one pass at most
 template <bool INPLACE, typename S, typename T = typename St3<S>::T>
 __global__ void __launch_bounds__(128, 5)
     k3_cut(const long long *__restrict__ Xq, const int *__restrict__ tri, int m,
@@ -883,7 +883,7 @@ __global__ void __launch_bounds__(128, 5)
   const int nn = ext[0] * ext[1] * ext[2];
   const float iX = 1.0f / (float)ext[0], iXY = 1.0f / (float)(ext[0] * ext[1]);
   for (int base0 = 0; base0 < nn; base0 += 32) {
-    // this round's destinations: one per lane, its straddling directions as a mask
+    // the destinations of this pass: one per lane, its straddling directions as a mask
     const int cidx = base0 + lane;
     unsigned mask = 0u;
     int a = 0, b = 0, cz = 0;

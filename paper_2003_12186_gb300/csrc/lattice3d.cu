@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(128, 5)
            const T *__restrict__ Fn, const Geom3 g, int odd, S *__restrict__ A, T scale,
            double *__restrict__ J, int *__restrict__ count, int *__restrict__ status) {
   // per warp: the plane sides of the widened box (the per-axis edge bound below keeps it
-  // within CUT_BOX^3 nodes) and the round's candidate list
+  // within CUT_BOX^3 nodes) and the pass's candidate list
   __shared__ signed char cut_sides[4][CUT_BOX * CUT_BOX * CUT_BOX];
   __shared__ unsigned cut_list[4][CUT_LIST];
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;

@@ -93,7 +93,10 @@ int iilbm3d_get_populations(iilbm3d_t h, double *df);
 /* Advance n >= 0 steps of section 3.2 in three dimensions: surface geometry and force,
  * normal split, the jump on every cut link of the triangulation (Eq. 47), tangential
  * spreading, the fused stream-collide, interpolation (Eq. 20) and the vertex update.
- * Asynchronous; replayed from CUDA graphs of two steps. */
+ * Asynchronous; replayed from CUDA graphs of two steps.  Inside each step the forced
+ * tiles and the interpolation run on a second stream the library owns, forked from the
+ * lattice's stream and joined back to it, so work queued on the lattice's stream after
+ * the call sees the finished step. */
 int iilbm3d_step(iilbm3d_t h, int32_t n);
 
 /* drho and u (Eq. 24) the next collision will use, from the populations plus the current
